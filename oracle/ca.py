@@ -1,0 +1,367 @@
+"""Plain FP64 CPU oracle of the cross-approximation (C-A) CUR method.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path imports, calls or
+executes this module: only ``tests/``, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` may use it.  It shares no code with the CUDA
+library and takes its inputs from the seeded generators in ``workloads``.
+
+What it computes (Pan, Luan, Svadlenka, Zhao, "Superfast Low-Rank
+Approximation and Least Squares Regression", arXiv:1611.01391):
+
+* Section 6.5, Primitive Algorithm: given row and column index sets I, J of an
+  m x n matrix M, the CUR generator is M[I, J]; its rank-k truncation is
+  inverted (pseudo-inverse) into the nucleus U and the approximation is C U R
+  with C = M[:, J], R = M[I, :].
+* Section 6.5, C-A iterations (dual form of Remark rec-atnsr, starting with a
+  vertical step): alternately fix a vertical strip M[:, J] and choose I inside
+  it, then fix the horizontal strip M[I, :] and choose J inside it.  One sweep
+  is one vertical plus one horizontal step (Section 12.2, Tests 2 and 4).
+* The generator inside a strip is a square l x l submatrix of locally maximal
+  volume (Section 12.2; the volume footnote of Section 6.5).  The sub-algorithm
+  used here is square maxvol: start from the rows chosen by Gaussian
+  elimination with partial pivoting on the very first strip, later from the
+  previous index set; repeatedly swap in the entry of largest modulus of
+  B = S X^{-1} while it exceeds 1 + delta.  Each swap of row i into position
+  j multiplies |det X| by |B_ij| (a rank-one update of X), so volume grows
+  monotonically and the loop terminates.
+* Appendix F: a posteriori error estimate on a random q x s submatrix of the
+  error matrix, with the observed mean and variance of its entries.
+
+Readings where the paper is silent (documented with the design):
+  |I| = |J| = l (square cross), truncation rank k <= l; delta = 1e-2 and a cap
+  of 64 l swaps per half-step; exact ties go to the smaller row, then the
+  smaller column; the nucleus keeps singular values > rank_tol * sigma_1.
+
+Entries are promoted to FP64 before any arithmetic.  Two source precisions
+exist: ``fp64`` evaluates generator entries in FP64 (the error reference) and
+``fp32`` evaluates them with FP32 operations in a fixed order (the entries a
+FP32 gather sees, for pivot-by-pivot comparison).
+
+Every decision is logged as (half_step, kind, i, j, v1, v2): v1 is the
+winning |value| and v2 the runner-up (GEPP, SWAP), or v1 the final max |B|
+(STOP, CAP).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+GEPP, SWAP, STOP, CAP = 0, 1, 2, 3
+
+
+class OracleSingular(RuntimeError):
+    """The strip has no nonsingular l x l submatrix reachable by GEPP."""
+
+
+# ---------------------------------------------------------------------------
+# Sources: entry access to M (Section 1.1: the matrix is reachable entry by
+# entry; a superfast method touches O((m + n) l) of its entries).
+# ---------------------------------------------------------------------------
+
+class Dense:
+    """Stored matrix; entries are the stored values promoted to FP64."""
+
+    def __init__(self, a):
+        self.a = np.asarray(a)
+        self.m, self.n = self.a.shape
+
+    def block(self, rows, cols):
+        return self.a[np.ix_(np.asarray(rows), np.asarray(cols))].astype(np.float64)
+
+
+class _Points:
+    def __init__(self, x, y, precision="fp64"):
+        self.x = np.asarray(x, dtype=np.float32)
+        self.y = np.asarray(y, dtype=np.float32)
+        if self.x.ndim == 1:
+            self.x = self.x[:, None]
+            self.y = self.y[:, None]
+        self.m, self.n = self.x.shape[0], self.y.shape[0]
+        if precision not in ("fp32", "fp64"):
+            raise ValueError(precision)
+        self.precision = precision
+
+    def _dist2(self, xs, ys):
+        # |x - y|^2 summed coordinate by coordinate, left to right, one
+        # rounding per operation in the chosen precision.
+        acc = None
+        for c in range(xs.shape[-1]):
+            d = xs[..., c] - ys[..., c]
+            sq = d * d
+            acc = sq if acc is None else acc + sq
+        return acc
+
+    def _pair(self, rows, cols):
+        xs = self.x[np.asarray(rows)][:, None, :]
+        ys = self.y[np.asarray(cols)][None, :, :]
+        if self.precision == "fp64":
+            xs = xs.astype(np.float64)
+            ys = ys.astype(np.float64)
+        return xs, ys
+
+
+class Cauchy(_Points):
+    """a_ij = 1 / (x_i - y_j) on 1-D points."""
+
+    def block(self, rows, cols):
+        xs, ys = self._pair(rows, cols)
+        d = xs[..., 0] - ys[..., 0]
+        one = np.float32(1.0) if self.precision == "fp32" else 1.0
+        return (one / d).astype(np.float64)
+
+
+class Gauss(_Points):
+    """a_ij = exp(-|x_i - y_j|^2 / h^2) on dim-D points."""
+
+    def __init__(self, x, y, h, precision="fp64"):
+        super().__init__(x, y, precision)
+        self.h = h
+
+    def block(self, rows, cols):
+        xs, ys = self._pair(rows, cols)
+        d2 = self._dist2(xs, ys)
+        if self.precision == "fp32":
+            h2 = np.float32(self.h) * np.float32(self.h)
+            return np.exp(-(d2 / h2)).astype(np.float64)
+        h2 = float(np.float32(self.h)) ** 2
+        return np.exp(-(d2 / h2))
+
+
+class InvDist(_Points):
+    """a_ij = 1 / |x_i - y_j| on dim-D points."""
+
+    def block(self, rows, cols):
+        xs, ys = self._pair(rows, cols)
+        d2 = self._dist2(xs, ys)
+        one = np.float32(1.0) if self.precision == "fp32" else 1.0
+        return (one / np.sqrt(d2)).astype(np.float64)
+
+
+def columns(src, J):
+    return src.block(np.arange(src.m), J)
+
+
+def rows(src, I):
+    return src.block(I, np.arange(src.n))
+
+
+# ---------------------------------------------------------------------------
+# Row selection inside a strip
+# ---------------------------------------------------------------------------
+
+def _runner_up(values, winner):
+    """Largest entry of ``values`` other than position ``winner`` (0 if none)."""
+    if values.size < 2:
+        return 0.0
+    rest = np.delete(values, winner)
+    return float(rest.max())
+
+
+def gepp_rows(S, trace=None, half_step=0):
+    """Pivot rows of Gaussian elimination with partial pivoting on the N x l
+    strip S: at step t take the free row of largest |entry| in column t of
+    the Schur complement (smallest row on ties), then eliminate column t from
+    the later columns of the free rows.  Returns the l pivot rows in order."""
+    W = np.array(S, dtype=np.float64, copy=True)
+    N, l = W.shape
+    if N < l:
+        raise ValueError("strip has fewer rows than columns")
+    free = np.ones(N, dtype=bool)
+    piv = []
+    for t in range(l):
+        mag = np.where(free, np.abs(W[:, t]), -1.0)
+        p = int(np.argmax(mag))
+        v1 = float(mag[p])
+        if trace is not None:
+            v2 = max(_runner_up(mag, p), 0.0)
+            trace.append((half_step, GEPP, p, t, v1, v2))
+        if not v1 > 0.0:
+            raise OracleSingular(f"zero pivot in column {t}")
+        piv.append(p)
+        free[p] = False
+        mult = W[free, t] / W[p, t]
+        W[np.ix_(free, np.arange(t + 1, l))] -= np.outer(mult, W[p, t + 1:])
+    return piv
+
+
+@dataclass
+class MaxvolResult:
+    I: list
+    swaps: int
+    converged: bool
+    max_b: float
+
+
+def maxvol(S, I0, delta=1e-2, max_swaps=None, trace=None, half_step=0):
+    """Square maxvol on the N x l strip S from initial row positions I0.
+
+    B = S X^{-1} with X = S[I, :] (LU with partial pivoting through
+    ``numpy.linalg.solve``).  While max |B_ij| > 1 + delta: put row i in
+    position j of I and apply the rank-one update
+        B <- B - B[:, j] (B[i, :] - e_j^T) / B_ij,
+    which is B recomputed for the new X.  Ties in the argmax go to the
+    smallest row, then the smallest column (row-major first maximum)."""
+    S = np.asarray(S, dtype=np.float64)
+    N, l = S.shape
+    if max_swaps is None:
+        max_swaps = 64 * l
+    I = [int(i) for i in I0]
+    X = S[I, :]
+    B = np.linalg.solve(X.T, S.T).T
+    swaps = 0
+    while True:
+        mag = np.abs(B).ravel()
+        p = int(np.argmax(mag))
+        v1 = float(mag[p])
+        i, j = divmod(p, l)
+        if v1 <= 1.0 + delta:
+            if trace is not None:
+                trace.append((half_step, STOP, i, j, v1, 0.0))
+            return MaxvolResult(I, swaps, True, v1)
+        if swaps >= max_swaps:
+            if trace is not None:
+                trace.append((half_step, CAP, i, j, v1, 0.0))
+            return MaxvolResult(I, swaps, False, v1)
+        if trace is not None:
+            trace.append((half_step, SWAP, i, j, v1, _runner_up(mag, p)))
+        pivot = B[i, j]
+        r = B[i, :].copy()
+        r[j] -= 1.0
+        B = B - np.outer(B[:, j], r) / pivot
+        I[j] = i
+        swaps += 1
+
+
+# ---------------------------------------------------------------------------
+# Nucleus (Primitive Algorithm, stages 2-3) and error estimates
+# ---------------------------------------------------------------------------
+
+def nucleus(X, k, rank_tol=1e-6):
+    """U = (X_k)^+ for the l x l CUR generator X: SVD X = P diag(sigma) Q^T,
+    keep the k_eff = min(k, #{sigma_j > rank_tol sigma_1}) leading triplets,
+    U = Q_k diag(1/sigma_k) P_k^T.  Returns (U, k_eff, sigma)."""
+    X = np.asarray(X, dtype=np.float64)
+    P, sigma, QT = np.linalg.svd(X)
+    if not sigma[0] > 0.0:
+        return np.zeros((X.shape[1], X.shape[0])), 0, sigma
+    k_eff = int(min(k, np.count_nonzero(sigma > rank_tol * sigma[0])))
+    U = (QT[:k_eff].T / sigma[:k_eff]) @ P[:, :k_eff].T
+    return U, k_eff, sigma
+
+
+def sampled_residual(src, C, U, R, sample_rows, sample_cols):
+    """Appendix F: error matrix E = M - C U R restricted to the q x s
+    submatrix (sample_rows, sample_cols).  Returns the relative Frobenius
+    estimate sqrt(sum E^2 / sum M^2), the sums, and the observed mean
+    mu_K = (1/K) sum E and variance sigma_K^2 = (1/K) sum (E - mu_K)^2."""
+    sr = np.asarray(sample_rows)
+    sc = np.asarray(sample_cols)
+    A = src.block(sr, sc)
+    E = A - (np.asarray(C)[sr] @ U) @ np.asarray(R)[:, sc]
+    K = E.size
+    sse = float(np.sum(E * E))
+    ssa = float(np.sum(A * A))
+    mu = float(np.sum(E)) / K
+    var = float(np.sum((E - mu) ** 2)) / K
+    rel = math.sqrt(sse / ssa) if ssa > 0 else math.inf
+    return {"rel": rel, "sse": sse, "ssa": ssa, "mu": mu, "var": var, "K": K}
+
+
+def full_residual(src, C, U, R, row_block=2048):
+    """||M - C U R||_F / ||M||_F over all entries, in FP64 row blocks."""
+    CU = np.asarray(C, dtype=np.float64) @ U
+    R = np.asarray(R, dtype=np.float64)
+    sse = 0.0
+    ssa = 0.0
+    cols = np.arange(src.n)
+    for r0 in range(0, src.m, row_block):
+        rr = np.arange(r0, min(src.m, r0 + row_block))
+        A = src.block(rr, cols)
+        E = A - CU[rr] @ R
+        sse += float(np.sum(E * E))
+        ssa += float(np.sum(A * A))
+    return math.sqrt(sse / ssa), sse, ssa
+
+
+# ---------------------------------------------------------------------------
+# The C-A driver
+# ---------------------------------------------------------------------------
+
+@dataclass
+class CrossResult:
+    I: list
+    J: list
+    C: np.ndarray
+    U: np.ndarray
+    R: np.ndarray
+    k_eff: int
+    sigma: np.ndarray
+    sweeps_done: int
+    swaps: list = field(default_factory=list)
+    converged: bool = True
+    trace: list = field(default_factory=list)
+    history: list = field(default_factory=list)
+    estimate: dict | None = None
+
+
+def cross_approximation(src, J0, k, sweeps, delta=1e-2, rank_tol=1e-6,
+                        max_swaps=None, tol=0.0, sample_rows=None,
+                        sample_cols=None, keep_trace=True):
+    """C-A iterations from the initial column set J0 (|J0| = l).
+
+    Sweep s: C = M[:, J]; on the first sweep I = GEPP rows of C; I = maxvol
+    of C from I; R = M[I, :]; J = maxvol of R^T from J.  After ``sweeps``
+    sweeps (or once the sampled estimate of the current CUR is <= tol),
+    C = M[:, J], R = M[I, :], U = (M[I, J]_k)^+."""
+    J = [int(j) for j in J0]
+    l = len(J)
+    if not (1 <= k <= l):
+        raise ValueError("need 1 <= k <= l")
+    trace = [] if keep_trace else None
+    swaps = []
+    history = []
+    converged = True
+    I = None
+    done = 0
+    estimate = None
+    for s in range(sweeps):
+        C = columns(src, J)
+        if s == 0:
+            I = gepp_rows(C, trace, half_step=2 * s)
+        res = maxvol(C, I, delta, max_swaps, trace, half_step=2 * s)
+        I = res.I
+        swaps.append(res.swaps)
+        converged &= res.converged
+        R = rows(src, I)
+        res = maxvol(R.T, J, delta, max_swaps, trace, half_step=2 * s + 1)
+        J = res.I
+        swaps.append(res.swaps)
+        converged &= res.converged
+        done = s + 1
+        history.append((list(I), list(J)))
+        if tol > 0.0 and sample_rows is not None:
+            Cf = columns(src, J)
+            U, _, _ = nucleus(src.block(I, J), k, rank_tol)
+            estimate = sampled_residual(src, Cf, U, R, sample_rows, sample_cols)
+            if estimate["rel"] <= tol:
+                break
+    C = columns(src, J)
+    R = rows(src, I)
+    U, k_eff, sigma = nucleus(src.block(I, J), k, rank_tol)
+    if sample_rows is not None:
+        estimate = sampled_residual(src, C, U, R, sample_rows, sample_cols)
+    return CrossResult(I=I, J=J, C=C, U=U, R=R, k_eff=k_eff, sigma=sigma,
+                       sweeps_done=done, swaps=swaps, converged=converged,
+                       trace=trace if trace is not None else [],
+                       history=history, estimate=estimate)
+
+
+def random_cross(src, I, J, k=None, rank_tol=0.0):
+    """Section 12.2, Tests 1: CUR with given (random) I, J and U = W[I, J]^{-1}
+    (k = l), or its rank-k truncated pseudo-inverse."""
+    X = src.block(I, J)
+    k = len(J) if k is None else k
+    U, k_eff, sigma = nucleus(X, k, rank_tol)
+    return columns(src, J), U, rows(src, I)

@@ -1,0 +1,108 @@
+"""The pins bite: plant a plausible mistake in a copy of an oracle function
+(a dropped term, a flipped sign, a transposed operand, a swapped factor) and
+check that at least one pin of ``test_oracle_pins`` then fails.  Mutants live
+only in this process, on the CPU."""
+import inspect
+
+import pytest
+
+import oracle
+import oracle.ca as ca
+from tests import test_oracle_pins as pins
+
+
+def _mutant(func, old, new):
+    src = inspect.getsource(func)
+    assert old in src, f"mutation anchor not found in {func.__name__}: {old!r}"
+    ns = dict(vars(ca))
+    exec(src.replace(old, new, 1), ns)
+    return ns[func.__name__]
+
+
+def _run_pins(checks):
+    """True when at least one check raises."""
+    for check in checks:
+        try:
+            check()
+        except Exception:
+            return True
+    return False
+
+
+MUTANTS = [
+    # maxvol: drop the -e_j term of the rank-one update
+    ("maxvol", "r[j] -= 1.0", "pass",
+     [lambda: pins.test_maxvol_volume_grows_by_recorded_factor(),
+      lambda: pins.test_maxvol_dominant_and_locally_maximal(3)]),
+    # maxvol: transposed operand when forming B
+    ("maxvol", "np.linalg.solve(X.T, S.T).T", "np.linalg.solve(X, S.T).T",
+     [lambda: pins.test_maxvol_volume_grows_by_recorded_factor(),
+      lambda: pins.test_exact_recovery_rank_l(60, 50, 5, 1)]),
+    # maxvol: update with the wrong column of B
+    ("maxvol", "np.outer(B[:, j], r)", "np.outer(B[:, (j + 1) % l], r)",
+     [lambda: pins.test_maxvol_volume_grows_by_recorded_factor()]),
+    # maxvol: position bookkeeping off (row stored in the wrong slot)
+    ("maxvol", "I[j] = i", "I[(j + 1) % l] = i",
+     [lambda: pins.test_maxvol_volume_grows_by_recorded_factor(),
+      lambda: pins.test_maxvol_dominant_and_locally_maximal(5)]),
+    # GEPP: wrong sign in the Schur complement update
+    ("gepp_rows", "-= np.outer(mult", "+= np.outer(mult",
+     [lambda: pins.test_gepp_pivots_match_lapack_getrf()]),
+    # GEPP: pivot chosen by signed value instead of modulus
+    ("gepp_rows", "np.abs(W[:, t])", "W[:, t]",
+     [lambda: pins.test_gepp_pivots_match_lapack_getrf()]),
+    # nucleus: left/right singular vectors swapped
+    ("nucleus", "(QT[:k_eff].T / sigma[:k_eff]) @ P[:, :k_eff].T",
+     "(P[:, :k_eff] / sigma[:k_eff]) @ QT[:k_eff]",
+     [lambda: pins.test_nucleus_against_constructed_svd(5),
+      lambda: pins.test_exact_recovery_rank_l(60, 50, 5, 1)]),
+    # nucleus: sigma instead of 1/sigma
+    ("nucleus", "/ sigma[:k_eff]", "* sigma[:k_eff]",
+     [lambda: pins.test_nucleus_against_constructed_svd(5)]),
+    # nucleus: truncation threshold ignored
+    ("nucleus", "min(k, np.count_nonzero(sigma > rank_tol * sigma[0]))", "k",
+     [lambda: pins.test_nucleus_against_constructed_svd(8)]),
+    # Appendix F: nucleus dropped from the residual
+    ("sampled_residual", "(np.asarray(C)[sr] @ U) @", "np.asarray(C)[sr] @",
+     [lambda: pins.test_sampled_residual_on_whole_matrix_equals_full()]),
+    # Appendix F: variance about zero instead of about the mean
+    ("sampled_residual", "np.sum((E - mu) ** 2)", "np.sum(E ** 2)",
+     [lambda: pins.test_sampled_residual_on_whole_matrix_equals_full()]),
+    # C-A: horizontal step chooses J inside R instead of R^T
+    ("cross_approximation", "maxvol(R.T, J,", "maxvol(R[:, :l], J,",
+     [lambda: pins.test_exact_recovery_rank_l(90, 120, 7, 3),
+      lambda: pins.test_rank_one_picks_largest_factors()]),
+]
+
+
+@pytest.mark.parametrize("idx", range(len(MUTANTS)))
+def test_mutant_is_caught(idx, monkeypatch):
+    name, old, new, checks = MUTANTS[idx]
+    bad = _mutant(getattr(ca, name), old, new)
+    monkeypatch.setattr(ca, name, bad)
+    monkeypatch.setattr(oracle, name, bad)
+    assert _run_pins(checks), f"mutant {name}: {old!r} -> {new!r} survived"
+
+
+def test_cauchy_sign_flip_is_caught(monkeypatch):
+    """A sign flip of every entry leaves det unchanged at even n; the pin
+    checks odd n too."""
+    import numpy as np
+
+    def flipped(self, rows, cols):
+        xs, ys = self._pair(rows, cols)
+        return (1.0 / (ys[..., 0] - xs[..., 0])).astype(np.float64)
+
+    monkeypatch.setattr(ca.Cauchy, "block", flipped)
+    assert _run_pins([lambda n=n: pins.test_cauchy_determinant_closed_form(n) for n in (3, 4, 5, 6)])
+
+
+def test_cauchy_index_swap_is_caught(monkeypatch):
+    import numpy as np
+
+    def swapped(self, rows, cols):
+        xs, ys = self._pair(cols, rows)
+        return (1.0 / (xs[..., 0] - ys[..., 0])).T.astype(np.float64)
+
+    monkeypatch.setattr(ca.Cauchy, "block", swapped)
+    assert _run_pins([pins.test_cauchy_known_entries])

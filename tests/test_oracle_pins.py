@@ -1,0 +1,303 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics
+(no GPU).  Each test names the property it checks and where it comes from."""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle as O
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rank_l(seed, m, n, l):
+    rng = W.rng_for(seed)
+    return rng.standard_normal((m, l)) @ rng.standard_normal((l, n))
+
+
+# --- Section 6.5: the Primitive algorithm is exact on rank-l inputs -----------
+
+@pytest.mark.parametrize("m,n,l,sweeps", [(60, 50, 5, 1), (90, 120, 7, 3), (40, 40, 1, 2)])
+def test_exact_recovery_rank_l(m, n, l, sweeps):
+    A = _rank_l(7 + l, m, n, l)
+    J0 = W.draw_indices(11 + l, n, l)
+    res = O.cross_approximation(O.Dense(A), J0, k=l, sweeps=sweeps, rank_tol=0.0)
+    rel, _, _ = O.full_residual(O.Dense(A), res.C, res.U, res.R)
+    assert res.k_eff == l
+    assert rel < 1e-12
+
+
+def test_interpolation_on_cross_k_equals_l():
+    """k = l and nonsingular X: (CUR)[I,:] = R and (CUR)[:,J] = C."""
+    A = W.lowrank_svd(3, 80, 70, r=6, noise_std=1e-3)
+    J0 = W.draw_indices(4, 70, 6)
+    res = O.cross_approximation(O.Dense(A), J0, k=6, sweeps=2, rank_tol=0.0)
+    cur = res.C @ res.U @ res.R
+    np.testing.assert_allclose(cur[res.I, :], res.R, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(cur[:, res.J], res.C, rtol=0, atol=1e-12)
+
+
+# --- Lemma 2.3 (letrnc): no rank-k approximation beats tau_{k+1} ---------------
+
+@pytest.mark.parametrize("k,l", [(8, 8), (6, 10)])
+def test_eckart_young_lower_bound(k, l):
+    A = W.lowrank_svd(5, 256, 256, r=8, noise_std=1e-4)
+    J0 = W.draw_indices(6, 256, l)
+    res = O.cross_approximation(O.Dense(A), J0, k=k, sweeps=3)
+    _, sse, ssa = O.full_residual(O.Dense(A), res.C, res.U, res.R)
+    s = np.linalg.svd(A, compute_uv=False)
+    tau = math.sqrt(float(np.sum(s[k:] ** 2)))
+    assert res.k_eff <= k
+    assert math.sqrt(sse) >= tau * (1 - 1e-12)
+    # and C-A is close to it on this input (a factor, not orders)
+    assert math.sqrt(sse) <= 4.0 * tau
+
+
+# --- maxvol against exhaustive search --------------------------------------------
+
+def _vol(S, I):
+    return abs(np.linalg.det(S[list(I), :]))
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_maxvol_dominant_and_locally_maximal(seed):
+    rng = W.rng_for(100 + seed)
+    N = int(rng.integers(4, 11))
+    l = int(rng.integers(1, 4))
+    S = rng.standard_normal((N, l))
+    delta = 1e-2
+    I0 = O.gepp_rows(S)
+    res = O.maxvol(S, I0, delta=delta)
+    assert res.converged
+    B = S @ np.linalg.inv(S[res.I, :])
+    assert np.max(np.abs(B)) <= 1 + delta + 1e-12          # dominance at exit
+    v = _vol(S, res.I)
+    for pos in range(l):                                      # no single swap gains > 1+delta
+        for i in range(N):
+            if i in res.I:
+                continue
+            J = list(res.I)
+            J[pos] = i
+            assert _vol(S, J) <= (1 + delta) * v * (1 + 1e-12)
+    # Hadamard: vol_max / vol <= ((1+delta) sqrt(l))^l for a dominant submatrix
+    vmax = max(_vol(S, c) for c in itertools.combinations(range(N), l))
+    assert vmax / v <= ((1 + delta) * math.sqrt(l)) ** l * (1 + 1e-12)
+
+
+def test_maxvol_single_column_is_global_argmax():
+    rng = W.rng_for(5)
+    for _ in range(20):
+        c = rng.standard_normal((30, 1))
+        res = O.maxvol(c, [int(rng.integers(0, 30))], delta=0.0)
+        assert res.I[0] == int(np.argmax(np.abs(c[:, 0])))
+
+
+def test_maxvol_volume_grows_by_recorded_factor():
+    """Each swap multiplies |det X| by exactly the recorded |B_ij|."""
+    rng = W.rng_for(9)
+    S = rng.standard_normal((200, 6))
+    I = list(W.draw_indices(10, 200, 6))
+    trace = []
+    res = O.maxvol(S, I, delta=1e-2, trace=trace)
+    swaps = [t for t in trace if t[1] == O.SWAP]
+    assert len(swaps) == res.swaps > 0
+    vol = _vol(S, I)
+    for (_, _, i, j, v1, v2) in swaps:
+        I[j] = i
+        new = _vol(S, I)
+        assert new / vol == pytest.approx(v1, rel=1e-9)
+        assert v1 > 1.01 and v2 <= v1
+        vol = new
+    assert I == res.I
+    assert trace[-1][1] == O.STOP and trace[-1][4] <= 1.01
+    # the exit state is dominant when B is recomputed from scratch
+    B = S @ np.linalg.inv(S[res.I, :])
+    assert np.max(np.abs(B)) <= 1.01 + 1e-12
+
+
+def test_gepp_pivots_match_lapack_getrf():
+    rng = W.rng_for(21)
+    for trial in range(10):
+        S = rng.standard_normal((50, 8))
+        lu, piv = scipy.linalg.lu_factor(S)
+        perm = list(range(50))
+        for t, p in enumerate(piv):
+            perm[t], perm[p] = perm[p], perm[t]
+        assert O.gepp_rows(S) == perm[:8]
+
+
+def test_gepp_zero_pivot_raises():
+    S = np.zeros((10, 3))
+    S[:, 0] = 1.0
+    with pytest.raises(O.OracleSingular):
+        O.gepp_rows(S)
+
+
+# --- nucleus: truncated pseudo-inverse (Primitive algorithm, stage 3) ----------
+
+def _orth(seed, n):
+    return W.haar_orthogonal(W.rng_for(seed), n)
+
+
+@pytest.mark.parametrize("k", [3, 5, 8])
+def test_nucleus_against_constructed_svd(k):
+    l = 8
+    P, Q = _orth(1, l), _orth(2, l)
+    s = np.array([5.0, 3.0, 2.0, 1.0, 0.5, 0.25, 1e-3, 1e-9])
+    X = P @ np.diag(s) @ Q.T
+    U, k_eff, sigma = O.nucleus(X, k, rank_tol=1e-6)
+    keep = min(k, 7)
+    assert k_eff == keep
+    np.testing.assert_allclose(sigma, s, rtol=1e-10, atol=1e-14 * s[0])
+    expect = Q[:, :keep] @ np.diag(1 / s[:keep]) @ P[:, :keep].T
+    np.testing.assert_allclose(U, expect, rtol=0, atol=1e-8 * np.abs(expect).max())
+    Xk = P[:, :keep] @ np.diag(s[:keep]) @ Q[:, :keep].T   # Moore-Penrose
+    np.testing.assert_allclose(Xk @ U @ Xk, Xk, atol=1e-10)
+    np.testing.assert_allclose(U @ Xk @ U, U, atol=1e-7 * np.abs(U).max())
+    np.testing.assert_allclose(Xk @ U, (Xk @ U).T, atol=1e-10)
+    np.testing.assert_allclose(U @ Xk, (U @ Xk).T, atol=1e-10)
+
+
+def test_cur_identity_on_svd_built_matrix():
+    """Appendix D.2: for M = S Sigma T^* of rank k, CUR equals M for any
+    nonsingular k x k cross."""
+    m, n, k = 40, 30, 4
+    S, T = _orth(3, m)[:, :k], _orth(4, n)[:, :k]
+    M = S @ np.diag([4.0, 2.0, 1.0, 0.5]) @ T.T
+    I, J = [0, 5, 9, 33], [2, 3, 17, 29]
+    C, U, R = O.random_cross(O.Dense(M), I, J)
+    np.testing.assert_allclose(C @ U @ R, M, atol=1e-12)
+
+
+# --- Appendix F: the sampled estimate -------------------------------------------
+
+def test_sampled_residual_on_whole_matrix_equals_full():
+    A = W.lowrank_svd(8, 64, 48, r=4, noise_std=1e-2)
+    src = O.Dense(A)
+    res = O.cross_approximation(src, W.draw_indices(9, 48, 5), k=4, sweeps=2)
+    est = O.sampled_residual(src, res.C, res.U, res.R, np.arange(64), np.arange(48))
+    rel, sse, ssa = O.full_residual(src, res.C, res.U, res.R)
+    assert est["rel"] == pytest.approx(rel, rel=1e-12)
+    E = A - res.C @ res.U @ res.R
+    assert est["mu"] == pytest.approx(E.mean(), rel=1e-10, abs=1e-15)
+    assert est["var"] == pytest.approx(E.var(), rel=1e-10)
+    assert est["K"] == 64 * 48
+
+
+# --- generators --------------------------------------------------------------------
+
+def _cauchy_closed_form_det(x, y):
+    xd, yd = np.asarray(x, np.float64), np.asarray(y, np.float64)
+    n = len(xd)
+    num = 1.0
+    for i in range(n):
+        for j in range(i + 1, n):
+            num *= (xd[j] - xd[i]) * (yd[i] - yd[j])
+    return num / np.prod(np.subtract.outer(xd, yd))
+
+
+@pytest.mark.parametrize("n", [3, 4, 5, 6])
+def test_cauchy_determinant_closed_form(n):
+    """det[1/(x_i - y_j)] = prod_{i<j} (x_j - x_i)(y_i - y_j) / prod_{i,j} (x_i - y_j).
+    Interlaced points keep the matrix well conditioned, so the numerical
+    determinant is accurate to ~1e-13; the sign is checked at odd and even n."""
+    x = (0.1 + 0.4 * np.arange(n)).astype(np.float32)
+    y = (0.3 + 0.4 * np.arange(n) + 0.05 * np.sin(np.arange(n))).astype(np.float32)
+    A = O.Cauchy(x, y, "fp64").block(range(n), range(n))
+    assert np.linalg.det(A) == pytest.approx(_cauchy_closed_form_det(x, y), rel=1e-10, abs=0)
+
+
+def test_cauchy_known_entries():
+    """a_ij = 1/(x_i - y_j) at hand-computed points, on a 2 x 3 block (the
+    determinant pin cannot see a transposition)."""
+    x = np.array([0.0, 1.0], np.float32)
+    y = np.array([2.0, 4.0, 3.0], np.float32)
+    expect = [[-1 / 2, -1 / 4, -1 / 3], [-1.0, -1 / 3, -1 / 2]]
+    np.testing.assert_allclose(O.Cauchy(x, y, "fp64").block([0, 1], [0, 1, 2]), expect,
+                               rtol=1e-15)
+
+
+def test_fp32_generators_round_once_per_operation():
+    x = np.array([0.1, 0.7], np.float32)
+    y = np.array([2.3, 2.9], np.float32)
+    a32 = O.Cauchy(x, y, "fp32").block([0, 1], [0, 1])
+    a64 = O.Cauchy(x, y, "fp64").block([0, 1], [0, 1])
+    assert a32.dtype == np.float64
+    assert np.all(a32 == a32.astype(np.float32))             # values are FP32
+    assert np.all(np.abs(a32 / a64 - 1) < 2 ** -22)
+
+
+def test_point_kernels_known_values():
+    x = np.array([[0.0, 0.0, 0.0]], np.float32)
+    y = np.array([[0.0, 0.0, 2.0], [3.0, 4.0, 0.0]], np.float32)
+    inv = O.InvDist(x, y, "fp64").block([0], [0, 1])
+    np.testing.assert_allclose(inv, [[0.5, 0.2]], rtol=1e-15)
+    g = O.Gauss(x, y, 2.0, "fp64").block([0], [0, 1])
+    np.testing.assert_allclose(g, [[math.exp(-1.0), math.exp(-25.0 / 4.0)]], rtol=1e-15)
+    inv32 = O.InvDist(x, y, "fp32").block([0], [0, 1])
+    np.testing.assert_array_equal(inv32, [[0.5, float(np.float32(0.2))]])
+
+
+# --- whole iteration: closed forms and the paper's table ----------------------
+
+def test_rank_one_picks_largest_factors():
+    rng = W.rng_for(77)
+    u, v = rng.standard_normal(50), rng.standard_normal(40)
+    A = np.outer(u, v)
+    res = O.cross_approximation(O.Dense(A), [3], k=1, sweeps=1, rank_tol=0.0)
+    assert res.I == [int(np.argmax(np.abs(u)))]
+    assert res.J == [int(np.argmax(np.abs(v)))]
+
+
+def _tb_ranrc_rows():
+    rows = []
+    with open(os.path.join(GOLDEN, "tb_ranrc.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            n, r, m1, s1, m2, s2 = line.split()
+            rows.append((int(n), int(r), float(m1), float(m2)))
+    return rows
+
+
+@pytest.mark.parametrize("n,r,paper_t1,paper_t2", [row for row in _tb_ranrc_rows() if row[0] == 256])
+def test_tb_ranrc_levels(n, r, paper_t1, paper_t2):
+    """Section 12.3 / Table tb_ranrc: five C-A loops beat a random cross by at
+    least 10x on average, and do at least as well as the printed Tests 2
+    mean; nothing beats sigma_{r+1} (the 1e-10 G3 floor)."""
+    e1, e2 = [], []
+    for s in range(30):
+        Wm = W.tb_ranrc(1000 + s, n, r)
+        src = O.Dense(Wm)
+        I = W.draw_indices(5000 + s, n, r)
+        J = W.draw_indices(9000 + s, n, r)
+        nw = np.linalg.norm(Wm, 2)
+        C, U, R = O.random_cross(src, I, J)
+        e1.append(np.linalg.norm(Wm - C @ U @ R, 2) / nw)
+        res = O.cross_approximation(src, J, k=r, sweeps=5, rank_tol=0.0)
+        e2.append(np.linalg.norm(Wm - res.C @ res.U @ res.R, 2) / nw)
+        sv = np.linalg.svd(Wm, compute_uv=False)
+        assert e2[-1] >= sv[r] / sv[0] * (1 - 1e-6)
+    assert np.mean(e1) >= 10 * np.mean(e2)
+    assert np.mean(e2) <= paper_t2
+
+
+# --- Appendix E: hard inputs -------------------------------------------------------
+
+def test_delta_matrix_is_missed_when_spike_is_not_touched():
+    """A rank-2 dense variant of a delta-matrix (Remark redltdns): any method
+    that never reads the spike row and column is off by >= 1/2 there."""
+    m, n = 40, 30
+    A = W.delta_matrix(m, n, 17, 23) - 0.5
+    res = O.cross_approximation(O.Dense(A), [0], k=1, sweeps=2, rank_tol=0.0)
+    assert 17 not in res.I and 23 not in res.J
+    cur = res.C @ res.U @ res.R
+    assert abs(A[17, 23] - cur[17, 23]) >= 0.5
+    # the Appendix F estimate sees it only if its sample contains the spike
+    miss = O.sampled_residual(O.Dense(A), res.C, res.U, res.R, np.arange(10), np.arange(10))
+    hit = O.sampled_residual(O.Dense(A), res.C, res.U, res.R, [17], [23])
+    assert miss["rel"] < 1e-12 and hit["rel"] >= 1.0
