@@ -1,0 +1,187 @@
+/*
+ * lra_cross.h -- C ABI of the GB300 cross-approximation (C-A) CUR library.
+ *
+ * Method: Pan, Luan, Svadlenka, Zhao, "Superfast Low-Rank Approximation and
+ * Least Squares Regression", arXiv:1611.01391.
+ *   - Problem statement (Section 5.1, Algorithm 5.1 preamble; Section 6.5):
+ *     an m x n matrix M reachable entry by entry, a target rank k and a cross
+ *     size l >= k; the result is a CUR approximation C U R.
+ *   - Primitive Algorithm (Section 6.5): C = M[:, J], R = M[I, :], the CUR
+ *     generator M[I, J] and the nucleus U = (M[I, J]_k)^+ (rank-k truncated
+ *     pseudo-inverse).
+ *   - C-A iterations (Section 6.5; dual start of Remark rec-atnsr): alternate
+ *     a vertical step (choose I inside M[:, J]) and a horizontal step (choose J
+ *     inside M[I, :]) for a fixed number of sweeps, or until the error
+ *     estimate drops below a tolerance.  Each step picks an l x l submatrix of
+ *     locally maximal volume (volume footnote of Section 6.5; Section 12.2).
+ *   - Appendix F: a posteriori error estimate on a random q x s submatrix of
+ *     the error matrix.
+ *
+ * Conventions
+ *   - Every call returns an lra_status (0 on success, negative on error);
+ *     no call aborts or throws.  lra_cross_last_error() gives a message.
+ *   - Indices are 0-based int32; matrices are row-major.
+ *   - Source buffers (dense matrix, point coordinates) are DEVICE pointers,
+ *     BORROWED: they must stay valid and unchanged until the job is DONE,
+ *     FAILED or cancelled.  Host arrays in lra_params are copied at submit.
+ *   - Outputs are caller-allocated (host or device, see lra_cur_out).
+ *   - A context owns one CUDA stream on one device; jobs run in submission
+ *     order on that stream.  Calls on one context are serialised internally.
+ *   - All computation happens in the library's CUDA kernels; there is no
+ *     CPU fallback.  Without a usable device, create fails with LRA_ECUDA.
+ */
+#ifndef LRA_CROSS_H
+#define LRA_CROSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LRA_OK = 0,
+  LRA_PENDING = 1,        /* job still queued or running                      */
+  LRA_EINVAL = -1,        /* bad argument (sizes, pointers, k > l, ...)       */
+  LRA_ENOMEM = -2,        /* device allocation failed                         */
+  LRA_EBUSY = -3,         /* admission refused: slots or memory budget full   */
+  LRA_ESINGULAR = -4,     /* a strip has no nonsingular l x l submatrix       */
+  LRA_ENONFINITE = -5,    /* an entry of M (or of B) is NaN or infinite       */
+  LRA_ETIMEOUT = -6,      /* a bounded device wait gave up                    */
+  LRA_ECUDA = -7,         /* CUDA runtime error                               */
+  LRA_ENOTFOUND = -8,     /* unknown job handle                               */
+  LRA_ECANCELED = -9,     /* job was cancelled                                */
+  LRA_ETOOLARGE = -10     /* strip exceeds the on-chip working-set limit      */
+} lra_status;
+
+typedef enum {
+  LRA_DENSE_F32 = 0,      /* a: float, m x n, row stride lda (elements)       */
+  LRA_DENSE_F64 = 1,      /* a: double, m x n, row stride lda; gathered as FP32 */
+  LRA_GEN_CAUCHY = 2,     /* a_ij = 1/(x_i - y_j); x: m floats, y: n floats   */
+  LRA_GEN_GAUSS = 3,      /* a_ij = exp(-|x_i - y_j|^2 / h^2), dim-D points   */
+  LRA_GEN_INVDIST = 4     /* a_ij = 1/|x_i - y_j|, dim-D points               */
+} lra_kind;
+
+/* Decision log entry kinds (lra_cur_out.trace). */
+enum { LRA_TRACE_GEPP = 0, LRA_TRACE_SWAP = 1, LRA_TRACE_STOP = 2, LRA_TRACE_CAP = 3 };
+
+/* lra_params.flags */
+enum { LRA_FLAG_PROFILE = 1 };   /* time every launch with CUDA events (lra_info.t_*_ms) */
+
+/* Job states (lra_info.state). */
+enum { LRA_STATE_RUNNING = 0, LRA_STATE_DONE = 1, LRA_STATE_FAILED = 2 };
+
+typedef struct lra_ctx lra_ctx;
+typedef uint64_t lra_job;
+
+typedef struct {
+  int32_t device;             /* CUDA device ordinal                                */
+  int32_t max_slots;          /* max jobs held at once (<= 0: 64)                   */
+  uint64_t mem_budget_bytes;  /* device-memory admission budget (0: unlimited)      */
+  void* stream;               /* cudaStream_t to run on, or NULL for an own stream  */
+} lra_ctx_params;
+
+typedef struct {
+  int32_t kind;               /* lra_kind                                           */
+  int32_t dim;                /* point dimension for LRA_GEN_GAUSS / _INVDIST (1..3) */
+  int64_t m, n;               /* matrix size                                        */
+  const void* a;              /* dense: device pointer                              */
+  int64_t lda;                /* dense: row stride in elements (>= n)               */
+  const float* x;             /* generators: device, m points (point-major, dim)    */
+  const float* y;             /* generators: device, n points                       */
+  float h;                    /* LRA_GEN_GAUSS width                                */
+} lra_source;
+
+typedef struct {
+  int32_t k;                  /* truncation rank, 1 <= k <= l                       */
+  int32_t l;                  /* cross size |I| = |J| = l, l <= 96, l <= min(m, n)  */
+  int32_t sweeps;             /* C-A sweeps (vertical + horizontal step), >= 1      */
+  int32_t max_swaps;          /* maxvol swap cap per half-step (<= 0: 64 l)         */
+  double delta;               /* maxvol stops when max |B| <= 1 + delta (> 0)       */
+  double rank_tol;            /* nucleus keeps sigma_j > rank_tol * sigma_1         */
+  double tol;                 /* > 0: stop after a sweep once the estimate <= tol   */
+  const int32_t* init_J;      /* host, l distinct column indices (initial J)        */
+  int64_t resid_q, resid_s;   /* Appendix F sample size (0: no estimate)            */
+  const int32_t* resid_rows;  /* host, resid_q distinct row indices                 */
+  const int32_t* resid_cols;  /* host, resid_s distinct column indices              */
+  int32_t trace_cap;          /* decisions to record (0: none)                      */
+  int32_t flags;              /* LRA_FLAG_* bits                                    */
+} lra_params;
+
+typedef struct {
+  int32_t state;              /* LRA_STATE_*                                        */
+  int32_t status;             /* lra_status of the job (LRA_OK when DONE)           */
+  int32_t sweeps_done;
+  int32_t k_eff;              /* kept singular triplets of the nucleus              */
+  int32_t swaps_total;        /* maxvol swaps over all half-steps                   */
+  int32_t converged;          /* 1 if no half-step hit the swap cap                 */
+  int32_t trace_len;          /* decisions recorded (<= trace_cap)                  */
+  int32_t reserved;
+  double est_rel_err;         /* Appendix F: sqrt(sum E^2 / sum M^2) on the sample  */
+  double est_mu;              /* observed mean of the sampled error entries         */
+  double est_var;             /* observed variance (1/K normalisation)              */
+  double sigma_max;           /* sigma_1 of the final cross                         */
+  double gpu_ms;              /* device time from first to last kernel of the job   */
+  int32_t kernel_launches;    /* kernels the job launched                           */
+  int32_t maxvol_launches;
+  double maxvol_flops;        /* algorithmic flops of all maxvol half-steps         */
+  double t_gather_ms;         /* with LRA_FLAG_PROFILE: device time per kernel class */
+  double t_maxvol_ms;
+  double t_cross_ms;
+  double t_resid_ms;
+} lra_info;
+
+typedef struct {
+  int32_t on_device;          /* 1: the pointers below are device pointers          */
+  int32_t* I;                 /* l row indices                                      */
+  int32_t* J;                 /* l column indices                                   */
+  double* U;                  /* l x l nucleus, row-major (C U R)                   */
+  double* sigma;              /* l singular values of M[I, J], descending (nullable) */
+  float* C;                   /* m x l, row-major (nullable)                        */
+  float* R;                   /* l x n, row-major (nullable)                        */
+  int32_t* trace;             /* 4 ints per decision: half_step, kind, i, j (nullable) */
+  double* trace_val;          /* 1 double per decision: winning |value| (nullable)  */
+} lra_cur_out;
+
+/* Create a context on params->device.  *out receives the handle. */
+lra_status lra_cross_create(lra_ctx** out, const lra_ctx_params* params);
+
+/* Wait for every job, free all device memory and the context. */
+lra_status lra_cross_destroy(lra_ctx* ctx);
+
+/* Validate, admit (slots and memory budget; LRA_EBUSY when full) and enqueue a
+ * full C-A solve on the context stream.  Non-blocking: returns once the work
+ * is queued.  *out receives the job handle. */
+lra_status lra_cross_submit(lra_ctx* ctx, const lra_source* src,
+                            const lra_params* params, lra_job* out);
+
+/* Non-blocking: LRA_PENDING while the job runs, else LRA_OK with *out filled
+ * (the job's own outcome is out->status). */
+lra_status lra_cross_poll(lra_ctx* ctx, lra_job job, lra_info* out);
+
+/* Blocking variant of lra_cross_poll. */
+lra_status lra_cross_wait(lra_ctx* ctx, lra_job job, lra_info* out);
+
+/* Copy I, J, U (and C, R, sigma, trace where non-NULL) of a finished job into
+ * caller buffers, then release the job's slot and device memory. */
+lra_status lra_cross_fetch_cur(lra_ctx* ctx, lra_job job, const lra_cur_out* out);
+
+/* Release a job: waits for its kernels to finish, then frees it. */
+lra_status lra_cross_cancel(lra_ctx* ctx, lra_job job);
+
+/* Bytes of device memory a job with these arguments holds while admitted. */
+lra_status lra_cross_footprint(const lra_source* src, const lra_params* params,
+                               uint64_t* bytes);
+
+/* Static message for a status code. */
+const char* lra_status_str(int32_t status);
+
+/* Message of the last failed call on ctx (thread-unsafe snapshot). */
+const char* lra_cross_last_error(lra_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LRA_CROSS_H */

@@ -230,6 +230,8 @@ def maxvol(S, I0, delta=1e-2, max_swaps=None, trace=None, half_step=0):
         r = B[i, :].copy()
         r[j] -= 1.0
         B = B - np.outer(B[:, j], r) / pivot
+        B[i, :] = 0.0          # B[I, :] is the identity for the new X
+        B[i, j] = 1.0
         I[j] = i
         swaps += 1
 

@@ -1,0 +1,175 @@
+"""GB300 cross-approximation (C-A) CUR library: thin Python binding.
+
+Every step of a solve runs in the CUDA kernels of ``_lib/liblra_cross.so``;
+this module only marshals arguments to the C ABI of ``include/lra_cross.h``
+(same function names).  PyTorch supplies device memory and streams.  There is
+no CPU path: importing fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"CUDA library missing: {LIB_PATH}. Build it first "
+        "(python -c 'import __graft_entry__ as g; g.build()').")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# ---- enums ----------------------------------------------------------------
+LRA_OK, LRA_PENDING = 0, 1
+LRA_EINVAL, LRA_ENOMEM, LRA_EBUSY, LRA_ESINGULAR = -1, -2, -3, -4
+LRA_ENONFINITE, LRA_ETIMEOUT, LRA_ECUDA, LRA_ENOTFOUND = -5, -6, -7, -8
+LRA_ECANCELED, LRA_ETOOLARGE = -9, -10
+
+LRA_DENSE_F32, LRA_DENSE_F64, LRA_GEN_CAUCHY, LRA_GEN_GAUSS, LRA_GEN_INVDIST = range(5)
+LRA_TRACE_GEPP, LRA_TRACE_SWAP, LRA_TRACE_STOP, LRA_TRACE_CAP = range(4)
+LRA_STATE_RUNNING, LRA_STATE_DONE, LRA_STATE_FAILED = range(3)
+LRA_FLAG_PROFILE = 1
+
+
+# ---- structs (layout of include/lra_cross.h) ------------------------------
+class lra_ctx_params(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("max_slots", ctypes.c_int32),
+                ("mem_budget_bytes", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
+
+
+class lra_source(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("dim", ctypes.c_int32),
+                ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("a", ctypes.c_void_p), ("lda", ctypes.c_int64),
+                ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("h", ctypes.c_float)]
+
+
+class lra_params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("l", ctypes.c_int32), ("sweeps", ctypes.c_int32),
+                ("max_swaps", ctypes.c_int32), ("delta", ctypes.c_double),
+                ("rank_tol", ctypes.c_double), ("tol", ctypes.c_double),
+                ("init_J", ctypes.c_void_p), ("resid_q", ctypes.c_int64),
+                ("resid_s", ctypes.c_int64), ("resid_rows", ctypes.c_void_p),
+                ("resid_cols", ctypes.c_void_p), ("trace_cap", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
+
+
+class lra_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("sweeps_done", ctypes.c_int32), ("k_eff", ctypes.c_int32),
+                ("swaps_total", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("trace_len", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("est_rel_err", ctypes.c_double), ("est_mu", ctypes.c_double),
+                ("est_var", ctypes.c_double), ("sigma_max", ctypes.c_double),
+                ("gpu_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int32),
+                ("maxvol_launches", ctypes.c_int32), ("maxvol_flops", ctypes.c_double),
+                ("t_gather_ms", ctypes.c_double), ("t_maxvol_ms", ctypes.c_double),
+                ("t_cross_ms", ctypes.c_double), ("t_resid_ms", ctypes.c_double)]
+
+
+class lra_cur_out(ctypes.Structure):
+    _fields_ = [("on_device", ctypes.c_int32), ("I", ctypes.c_void_p), ("J", ctypes.c_void_p),
+                ("U", ctypes.c_void_p), ("sigma", ctypes.c_void_p), ("C", ctypes.c_void_p),
+                ("R", ctypes.c_void_p), ("trace", ctypes.c_void_p), ("trace_val", ctypes.c_void_p)]
+
+
+_ctx_p = ctypes.c_void_p
+_job = ctypes.c_uint64
+
+
+def _sig(name, res, *args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = list(args)
+    return f
+
+
+_create = _sig("lra_cross_create", ctypes.c_int, ctypes.POINTER(_ctx_p), ctypes.POINTER(lra_ctx_params))
+_destroy = _sig("lra_cross_destroy", ctypes.c_int, _ctx_p)
+_submit = _sig("lra_cross_submit", ctypes.c_int, _ctx_p, ctypes.POINTER(lra_source),
+               ctypes.POINTER(lra_params), ctypes.POINTER(_job))
+_poll = _sig("lra_cross_poll", ctypes.c_int, _ctx_p, _job, ctypes.POINTER(lra_info))
+_wait = _sig("lra_cross_wait", ctypes.c_int, _ctx_p, _job, ctypes.POINTER(lra_info))
+_fetch = _sig("lra_cross_fetch_cur", ctypes.c_int, _ctx_p, _job, ctypes.POINTER(lra_cur_out))
+_cancel = _sig("lra_cross_cancel", ctypes.c_int, _ctx_p, _job)
+_footprint = _sig("lra_cross_footprint", ctypes.c_int, ctypes.POINTER(lra_source),
+                  ctypes.POINTER(lra_params), ctypes.POINTER(ctypes.c_uint64))
+_status_str = _sig("lra_status_str", ctypes.c_char_p, ctypes.c_int32)
+_last_error = _sig("lra_cross_last_error", ctypes.c_char_p, _ctx_p)
+
+EXPORTED = ["lra_cross_create", "lra_cross_destroy", "lra_cross_submit", "lra_cross_poll",
+            "lra_cross_wait", "lra_cross_fetch_cur", "lra_cross_cancel", "lra_cross_footprint",
+            "lra_status_str", "lra_cross_last_error"]
+
+
+class LraError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__(f"{lra_status_str(code)} ({code}){': ' + msg if msg else ''}")
+        self.code = code
+
+
+def lra_status_str(code: int) -> str:
+    return _status_str(int(code)).decode()
+
+
+def lra_cross_last_error(ctx) -> str:
+    return _last_error(ctx).decode()
+
+
+def _check(code, ctx=None, ok=(LRA_OK,)):
+    if code not in ok:
+        raise LraError(code, lra_cross_last_error(ctx) if ctx else "")
+    return code
+
+
+# ---- the C ABI, one function per entry point --------------------------------
+def lra_cross_create(device: int = 0, max_slots: int = 64, mem_budget_bytes: int = 0, stream=None):
+    p = lra_ctx_params(device, max_slots, mem_budget_bytes, stream or None)
+    ctx = _ctx_p()
+    _check(_create(ctypes.byref(ctx), ctypes.byref(p)))
+    return ctx
+
+
+def lra_cross_destroy(ctx) -> None:
+    _check(_destroy(ctx))
+
+
+def lra_cross_submit(ctx, src: lra_source, params: lra_params) -> int:
+    job = _job()
+    _check(_submit(ctx, ctypes.byref(src), ctypes.byref(params), ctypes.byref(job)), ctx)
+    return job.value
+
+
+def lra_cross_poll(ctx, job: int):
+    info = lra_info()
+    code = _poll(ctx, job, ctypes.byref(info))
+    _check(code, ctx, ok=(LRA_OK, LRA_PENDING))
+    return code, info
+
+
+def lra_cross_wait(ctx, job: int) -> lra_info:
+    info = lra_info()
+    _check(_wait(ctx, job, ctypes.byref(info)), ctx)
+    return info
+
+
+def lra_cross_fetch_cur(ctx, job: int, out: lra_cur_out) -> int:
+    return _check(_fetch(ctx, job, ctypes.byref(out)), ctx)
+
+
+def lra_cross_cancel(ctx, job: int) -> None:
+    _check(_cancel(ctx, job), ctx)
+
+
+def lra_cross_footprint(src: lra_source, params: lra_params) -> int:
+    b = ctypes.c_uint64()
+    _check(_footprint(ctypes.byref(src), ctypes.byref(params), ctypes.byref(b)))
+    return b.value
+
+
+from .api import Context, SolveResult, make_params, make_source  # noqa: E402
+
+__all__ = EXPORTED + ["Context", "SolveResult", "LraError", "make_params", "make_source",
+                      "lra_source", "lra_params", "lra_info", "lra_cur_out", "LIB_PATH"]

@@ -1,0 +1,128 @@
+"""Convenience layer over the C ABI: builds the argument structs from torch
+tensors / numpy arrays and runs submit -> wait -> fetch.  Argument
+marshalling only; the solve itself runs in the library's kernels."""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import (LRA_DENSE_F32, LRA_DENSE_F64, LRA_GEN_CAUCHY, LRA_GEN_GAUSS, LRA_GEN_INVDIST,
+               lra_cross_create, lra_cross_destroy, lra_cross_fetch_cur, lra_cross_submit,
+               lra_cross_wait, lra_cur_out, lra_info, lra_params, lra_source)
+
+_KINDS = {"dense": None, "cauchy": LRA_GEN_CAUCHY, "gauss": LRA_GEN_GAUSS,
+          "invdist": LRA_GEN_INVDIST}
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def make_source(kind: str, *, a=None, x=None, y=None, h: float = 0.0) -> lra_source:
+    """Source descriptor from device tensors (kept alive by the caller)."""
+    import torch
+    if kind == "dense":
+        if a.dtype not in (torch.float32, torch.float64) or not a.is_cuda or a.dim() != 2:
+            raise ValueError("dense source: 2-D float32/float64 CUDA tensor required")
+        if a.stride(1) != 1:
+            raise ValueError("dense source must be row-major")
+        k = LRA_DENSE_F32 if a.dtype == torch.float32 else LRA_DENSE_F64
+        return lra_source(k, 0, a.shape[0], a.shape[1], a.data_ptr(), a.stride(0), None, None, 0.0)
+    kd = _KINDS[kind]
+    if x.dtype != torch.float32 or y.dtype != torch.float32 or not x.is_cuda or not y.is_cuda:
+        raise ValueError("generator points: float32 CUDA tensors required")
+    if not (x.is_contiguous() and y.is_contiguous()):
+        raise ValueError("generator points must be contiguous")
+    dim = 1 if x.dim() == 1 else x.shape[1]
+    return lra_source(kd, dim, x.shape[0], y.shape[0], None, 0, x.data_ptr(), y.data_ptr(), float(h))
+
+
+@dataclass
+class _HostArrays:
+    J0: np.ndarray
+    rows: np.ndarray | None
+    cols: np.ndarray | None
+
+
+def make_params(k, l, sweeps, init_J, *, delta=1e-2, rank_tol=1e-6, tol=0.0, max_swaps=0,
+                resid_rows=None, resid_cols=None, trace_cap=0, profile=False):
+    """lra_params plus the host arrays it points to (keep both alive)."""
+    J0 = np.ascontiguousarray(init_J, dtype=np.int32)
+    rows = None if resid_rows is None else np.ascontiguousarray(resid_rows, dtype=np.int32)
+    cols = None if resid_cols is None else np.ascontiguousarray(resid_cols, dtype=np.int32)
+    p = lra_params()
+    p.k, p.l, p.sweeps, p.max_swaps = k, l, sweeps, max_swaps
+    p.delta, p.rank_tol, p.tol = delta, rank_tol, tol
+    p.init_J = J0.ctypes.data
+    if rows is not None:
+        p.resid_q, p.resid_s = len(rows), len(cols)
+        p.resid_rows, p.resid_cols = rows.ctypes.data, cols.ctypes.data
+    p.trace_cap = trace_cap
+    p.flags = 1 if profile else 0
+    return p, _HostArrays(J0, rows, cols)
+
+
+@dataclass
+class SolveResult:
+    I: np.ndarray
+    J: np.ndarray
+    U: np.ndarray
+    sigma: np.ndarray
+    info: lra_info
+    C: object = None
+    R: object = None
+    trace: np.ndarray | None = None
+    trace_val: np.ndarray | None = None
+
+
+class Context:
+    """One library context (one device, one stream)."""
+
+    def __init__(self, device=0, max_slots=64, mem_budget_bytes=0, stream=None):
+        self.ctx = lra_cross_create(device, max_slots, mem_budget_bytes, stream)
+
+    def close(self):
+        if self.ctx:
+            lra_cross_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, src, params):
+        return lra_cross_submit(self.ctx, src, params)
+
+    def fetch(self, job, l, m=None, n=None, want_strips=False, trace_cap=0, device=None):
+        """Fetch I, J, U, sigma (host numpy) and optionally C, R as device tensors."""
+        import torch
+        info = lra_cross_wait(self.ctx, job)
+        I = np.zeros(l, np.int32)
+        J = np.zeros(l, np.int32)
+        U = np.zeros((l, l), np.float64)
+        sigma = np.zeros(l, np.float64)
+        out = lra_cur_out()
+        out.on_device = 0
+        out.I, out.J, out.U, out.sigma = I.ctypes.data, J.ctypes.data, U.ctypes.data, sigma.ctypes.data
+        C = R = None
+        tr = tv = None
+        if want_strips:
+            C = torch.empty((m, l), dtype=torch.float32, device=device)
+            R = torch.empty((l, n), dtype=torch.float32, device=device)
+            out.C, out.R = C.data_ptr(), R.data_ptr()
+        if trace_cap:
+            tr = np.zeros((trace_cap, 4), np.int32)
+            tv = np.zeros(trace_cap, np.float64)
+            out.trace, out.trace_val = tr.ctypes.data, tv.ctypes.data
+        lra_cross_fetch_cur(self.ctx, job, out)
+        if tr is not None:
+            tr, tv = tr[:info.trace_len], tv[:info.trace_len]
+        return SolveResult(I, J, U, sigma, info, C, R, tr, tv)
+
+    def solve(self, src, params, l, m=None, n=None, want_strips=False, trace_cap=0, device=None):
+        job = self.submit(src, params)
+        return self.fetch(job, l, m, n, want_strips, trace_cap, device)

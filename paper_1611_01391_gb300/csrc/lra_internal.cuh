@@ -1,0 +1,148 @@
+// Internal device/host definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lra_cross.h"
+
+namespace lra {
+
+constexpr int kMaxL = 96;            // largest cross size handled on chip
+constexpr int kMaxGrid = 160;        // candidate slots per exchange buffer (>= SM count)
+constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded device waits: 2 s
+
+// ---------------------------------------------------------------------------
+// Entry access to M (Section 1.1: the matrix is reachable entry by entry).
+// ---------------------------------------------------------------------------
+struct SourceDev {
+  int kind;
+  int dim;
+  long long m, n;
+  const void* a;
+  long long lda;
+  const float* x;
+  const float* y;
+  float h2;          // h*h rounded to FP32 (Gaussian kernel)
+};
+
+// |x_i - y_j|^2 accumulated coordinate by coordinate with one rounding per
+// operation (no FMA contraction), so the value is reproducible bit for bit.
+__device__ __forceinline__ float dist2(const SourceDev& s, long long i, long long j) {
+  const float* xi = s.x + i * s.dim;
+  const float* yj = s.y + j * s.dim;
+  float d = __fsub_rn(xi[0], yj[0]);
+  float acc = __fmul_rn(d, d);
+  for (int c = 1; c < s.dim; ++c) {
+    d = __fsub_rn(xi[c], yj[c]);
+    acc = __fadd_rn(acc, __fmul_rn(d, d));
+  }
+  return acc;
+}
+
+template <int KIND>
+__device__ __forceinline__ float entry(const SourceDev& s, long long i, long long j) {
+  if constexpr (KIND == LRA_DENSE_F32) {
+    return __ldg(static_cast<const float*>(s.a) + i * s.lda + j);
+  } else if constexpr (KIND == LRA_DENSE_F64) {
+    return __double2float_rn(__ldg(static_cast<const double*>(s.a) + i * s.lda + j));
+  } else if constexpr (KIND == LRA_GEN_CAUCHY) {
+    return __fdiv_rn(1.0f, __fsub_rn(__ldg(s.x + i), __ldg(s.y + j)));
+  } else if constexpr (KIND == LRA_GEN_GAUSS) {
+    return expf(-__fdiv_rn(dist2(s, i, j), s.h2));
+  } else {
+    return __fdiv_rn(1.0f, __fsqrt_rn(dist2(s, i, j)));
+  }
+}
+
+// Calls F<KIND> with the source kind as a compile-time constant.
+#define LRA_DISPATCH_KIND(kind, BODY)                                   \
+  switch (kind) {                                                      \
+    case LRA_DENSE_F32: { constexpr int K = LRA_DENSE_F32; BODY; } break; \
+    case LRA_DENSE_F64: { constexpr int K = LRA_DENSE_F64; BODY; } break; \
+    case LRA_GEN_CAUCHY: { constexpr int K = LRA_GEN_CAUCHY; BODY; } break; \
+    case LRA_GEN_GAUSS: { constexpr int K = LRA_GEN_GAUSS; BODY; } break; \
+    default: { constexpr int K = LRA_GEN_INVDIST; BODY; } break;       \
+  }
+
+// ---------------------------------------------------------------------------
+// Per-job device state.
+// ---------------------------------------------------------------------------
+struct JobStatus {
+  int status;        // lra_status; kernels do nothing once it is not LRA_OK
+  int stop;          // tolerance reached: remaining sweeps are skipped
+  int sweeps_done;
+  int k_eff;
+  int swaps_total;
+  int converged;
+  int trace_len;
+  int trace_cap;
+  double est_rel, est_mu, est_var, est_sse, est_ssa;
+  double sigma_max;
+  double maxvol_flops;
+};
+
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+};
+
+// Candidate of one CTA in the grid-wide argmax exchange.
+struct Cand {
+  double val;        // |B_ij| (or -1 when the CTA has no candidate)
+  int idx;           // flat index i*l + j in the strip
+  int flags;         // bit 0: a non-finite value was seen
+};
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier for a cooperative (co-resident) launch.  The last CTA to
+// arrive resets the counter and bumps the generation; the others wait on the
+// generation with a 2 s deadline.  Returns false (and sets *timed_out, a
+// shared-memory flag) if the deadline passed.
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned int* gen_local,
+                                          int* timed_out) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int g = *gen_local;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&bar->count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      st_release_u32(&bar->gen, g + 1);
+    } else {
+      const unsigned long long t0 = globaltimer_ns();
+      while (ld_acquire_u32(&bar->gen) == g) {
+        if (globaltimer_ns() - t0 > kWaitNs) {
+          *timed_out = 1;
+          break;
+        }
+      }
+    }
+    *gen_local = g + 1;
+    __threadfence();
+  }
+  __syncthreads();
+  return *timed_out == 0;
+}
+
+__device__ __forceinline__ void set_status(JobStatus* js, int code) {
+  atomicCAS(&js->status, (int)LRA_OK, code);
+}
+
+}  // namespace lra

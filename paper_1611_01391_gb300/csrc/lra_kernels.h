@@ -1,0 +1,77 @@
+// Host-side launchers of the library's kernels (one per translation unit).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace lra {
+
+struct SourceDev;
+struct JobStatus;
+struct Cand;
+struct GridBarrier;
+
+cudaError_t launch_gather_cols(const SourceDev& s, const int* J, int l, float* C,
+                               const JobStatus* js, int skip_on_stop, int sms,
+                               cudaStream_t st);
+cudaError_t launch_gather_rows(const SourceDev& s, const int* I, int l, float* R,
+                               const JobStatus* js, int sms, cudaStream_t st);
+
+// One maxvol half-step on an N x l FP32 strip whose element (i, t) sits at
+// strip[i*si + t*st].  gepp = 1: Gauss-Jordan elimination with partial
+// pivoting selects the initial rows; gepp = 0: warm start from pos[] with xin
+// = inverse of the strip's cross S[pos, :] (row-major).  On exit pos[] holds
+// the selected rows.
+struct MaxvolArgs {
+  const float* strip;
+  long long N;
+  int l;
+  long long si, st;
+  int gepp;
+  int* pos;
+  const double* xin;
+  Cand* cand;
+  double* cand_rows;
+  GridBarrier* bar;
+  JobStatus* js;
+  int* trace_i;
+  double* trace_v;
+  int half_step;
+  double delta;
+  int max_swaps;
+  int rows_per_cta;
+};
+
+struct MaxvolPlan {
+  int grid;
+  int threads;
+  int rows_per_cta;
+  size_t smem;
+};
+
+// Grid and shared-memory plan for a strip; returns false if it cannot be
+// held on chip.
+bool plan_maxvol(long long N, int l, int sms, size_t smem_limit, MaxvolPlan* plan);
+cudaError_t launch_maxvol(MaxvolArgs a, const MaxvolPlan& plan, cudaStream_t st);
+
+// Inverse of the cross S[pos, :] of a strip (one CTA, FP64 Gauss-Jordan with
+// partial pivoting), row-major into xinv.
+cudaError_t launch_cross_inverse(const float* strip, long long si, long long st, const int* pos,
+                                 int l, double* xinv, JobStatus* js, cudaStream_t stream);
+
+// Nucleus of the final cross X = C[I, :] (one CTA, FP64 one-sided Jacobi SVD).
+cudaError_t launch_nucleus(const float* C, const int* I, int l, int k, double rank_tol,
+                           double* U, double* sigma, JobStatus* js, cudaStream_t st);
+
+// Appendix F sampled residual of C U R on rows x cols.
+cudaError_t launch_sampled_residual(const SourceDev& s, const int* rows, int q,
+                                    const int* cols, int sN, int l, const float* C,
+                                    const double* U, const float* R, float* CUq,
+                                    double* partials, int max_partials, JobStatus* js,
+                                    cudaStream_t st);
+int sampled_residual_partials(int q, int sN);
+
+// Small control kernels.
+cudaError_t launch_sweep_done(JobStatus* js, cudaStream_t st);
+cudaError_t launch_tol_check(JobStatus* js, double tol, cudaStream_t st);
+
+}  // namespace lra

@@ -1,0 +1,518 @@
+// Host runtime of the C ABI declared in include/lra_cross.h: contexts, job
+// admission, per-job device memory and the launch sequence of one C-A solve
+// (Section 6.5: C-A iterations, then the Primitive Algorithm's nucleus;
+// Appendix F: sampled error estimate).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "lra_internal.cuh"
+#include "lra_kernels.h"
+
+using namespace lra;
+
+namespace {
+
+struct Job {
+  lra_job id = 0;
+  SourceDev src{};
+  int l = 0, k = 0, sweeps = 0, max_swaps = 0, trace_cap = 0, slot = -1;
+  long long m = 0, n = 0, q = 0, s = 0;
+  double delta = 0, rank_tol = 0, tol = 0;
+  unsigned char* dmem = nullptr;
+  size_t bytes = 0;
+  JobStatus* js = nullptr;
+  GridBarrier* bar = nullptr;
+  int *J = nullptr, *I = nullptr, *rows = nullptr, *cols = nullptr, *trace_i = nullptr;
+  double *xbuf0 = nullptr, *xbuf1 = nullptr, *U = nullptr, *sigma = nullptr, *cand_rows = nullptr,
+         *trace_v = nullptr, *partials = nullptr;
+  float *C = nullptr, *R = nullptr, *CUq = nullptr;
+  Cand* cand = nullptr;
+  int n_partials = 0;
+  MaxvolPlan plan_col{}, plan_row{};
+  cudaEvent_t ev_start = nullptr, ev_end = nullptr;
+  int launches = 0, maxvol_launches = 0;
+  bool profile = false;
+  std::vector<std::pair<int, cudaEvent_t>> prof;  // (kernel class, event after the launch)
+};
+
+enum { kClsGather = 0, kClsMaxvol = 1, kClsCross = 2, kClsResid = 3, kClsOther = 4 };
+
+// Sub-buffer offsets of one job's single device allocation.
+struct Layout {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return o;
+  }
+};
+
+}  // namespace
+
+struct lra_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int sms = 0;
+  size_t smem_optin = 0;
+  int max_slots = 64;
+  uint64_t budget = 0;
+  uint64_t used_bytes = 0;
+  JobStatus* pinned = nullptr;  // one result slot per job slot
+  std::vector<int> free_slots;
+  std::mutex mu;
+  std::unordered_map<lra_job, Job*> jobs;
+  lra_job next_id = 1;
+  std::string last_error;
+};
+
+namespace {
+
+lra_status fail(lra_ctx* ctx, lra_status code, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  return code;
+}
+
+lra_status cuda_fail(lra_ctx* ctx, cudaError_t e, const char* what) {
+  return fail(ctx, e == cudaErrorMemoryAllocation ? LRA_ENOMEM : LRA_ECUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Validation shared by submit and footprint.
+lra_status validate(const lra_source* src, const lra_params* p, std::string* why) {
+  if (!src || !p) { *why = "null argument"; return LRA_EINVAL; }
+  if (src->kind < LRA_DENSE_F32 || src->kind > LRA_GEN_INVDIST) { *why = "unknown source kind"; return LRA_EINVAL; }
+  if (src->m < 1 || src->n < 1 || src->m > (1LL << 30) || src->n > (1LL << 30)) { *why = "bad matrix size"; return LRA_EINVAL; }
+  if (src->kind <= LRA_DENSE_F64) {
+    if (!src->a || src->lda < src->n) { *why = "dense source needs a and lda >= n"; return LRA_EINVAL; }
+  } else {
+    if (!src->x || !src->y) { *why = "generator needs x and y"; return LRA_EINVAL; }
+    if (src->kind != LRA_GEN_CAUCHY && (src->dim < 1 || src->dim > 3)) { *why = "dim must be 1..3"; return LRA_EINVAL; }
+    if (src->kind == LRA_GEN_GAUSS && !(src->h > 0.0f)) { *why = "h must be > 0"; return LRA_EINVAL; }
+  }
+  if (p->l < 1 || p->l > kMaxL) { *why = "l must be in 1..96"; return LRA_EINVAL; }
+  if (p->k < 1 || p->k > p->l) { *why = "k must be in 1..l"; return LRA_EINVAL; }
+  if (p->l > src->m || p->l > src->n) { *why = "l exceeds min(m, n)"; return LRA_EINVAL; }
+  if (p->sweeps < 1 || p->sweeps > 1000) { *why = "sweeps must be in 1..1000"; return LRA_EINVAL; }
+  if (!(p->delta > 0.0)) { *why = "delta must be > 0"; return LRA_EINVAL; }
+  if (!(p->rank_tol >= 0.0)) { *why = "rank_tol must be >= 0"; return LRA_EINVAL; }
+  if (!p->init_J) { *why = "init_J is required"; return LRA_EINVAL; }
+  if (p->resid_q < 0 || p->resid_s < 0 || (p->resid_q > 0) != (p->resid_s > 0)) { *why = "bad sample size"; return LRA_EINVAL; }
+  if (p->resid_q > 0 && (!p->resid_rows || !p->resid_cols || p->resid_q > src->m || p->resid_s > src->n)) {
+    *why = "bad sample index arrays"; return LRA_EINVAL;
+  }
+  if (p->tol > 0.0 && p->resid_q == 0) { *why = "tol needs a residual sample"; return LRA_EINVAL; }
+  if (p->trace_cap < 0) { *why = "trace_cap must be >= 0"; return LRA_EINVAL; }
+  return LRA_OK;
+}
+
+size_t layout_bytes(const lra_source* src, const lra_params* p, Job* j) {
+  const int l = p->l;
+  const long long q = p->resid_q, s = p->resid_s;
+  Layout L;
+  const size_t o_js = L.take(sizeof(JobStatus));
+  const size_t o_bar = L.take(sizeof(GridBarrier));
+  const size_t o_J = L.take(sizeof(int) * l);
+  const size_t o_I = L.take(sizeof(int) * l);
+  const size_t o_x0 = L.take(sizeof(double) * l * l);
+  const size_t o_x1 = L.take(sizeof(double) * l * l);
+  const size_t o_U = L.take(sizeof(double) * l * l);
+  const size_t o_sig = L.take(sizeof(double) * l);
+  const size_t o_cand = L.take(sizeof(Cand) * 2 * kMaxGrid);
+  const size_t o_candr = L.take(sizeof(double) * 2 * kMaxGrid * l);
+  const size_t o_ti = L.take(sizeof(int) * 4 * std::max(p->trace_cap, 1));
+  const size_t o_tv = L.take(sizeof(double) * std::max(p->trace_cap, 1));
+  const size_t o_rows = L.take(sizeof(int) * std::max<long long>(q, 1));
+  const size_t o_cols = L.take(sizeof(int) * std::max<long long>(s, 1));
+  const int np = q > 0 ? sampled_residual_partials((int)q, (int)s) : 1;
+  const size_t o_cuq = L.take(sizeof(float) * std::max<long long>(2 * q * l, 1));
+  const size_t o_part = L.take(sizeof(double) * 3 * np);
+  const size_t o_C = L.take(sizeof(float) * (size_t)src->m * l);
+  const size_t o_R = L.take(sizeof(float) * (size_t)src->n * l);
+  if (j) {
+    unsigned char* b = j->dmem;
+    j->js = reinterpret_cast<JobStatus*>(b + o_js);
+    j->bar = reinterpret_cast<GridBarrier*>(b + o_bar);
+    j->J = reinterpret_cast<int*>(b + o_J);
+    j->I = reinterpret_cast<int*>(b + o_I);
+    j->xbuf0 = reinterpret_cast<double*>(b + o_x0);
+    j->xbuf1 = reinterpret_cast<double*>(b + o_x1);
+    j->U = reinterpret_cast<double*>(b + o_U);
+    j->sigma = reinterpret_cast<double*>(b + o_sig);
+    j->cand = reinterpret_cast<Cand*>(b + o_cand);
+    j->cand_rows = reinterpret_cast<double*>(b + o_candr);
+    j->trace_i = reinterpret_cast<int*>(b + o_ti);
+    j->trace_v = reinterpret_cast<double*>(b + o_tv);
+    j->rows = reinterpret_cast<int*>(b + o_rows);
+    j->cols = reinterpret_cast<int*>(b + o_cols);
+    j->CUq = reinterpret_cast<float*>(b + o_cuq);
+    j->partials = reinterpret_cast<double*>(b + o_part);
+    j->C = reinterpret_cast<float*>(b + o_C);
+    j->R = reinterpret_cast<float*>(b + o_R);
+    j->n_partials = np;
+  }
+  return L.off;
+}
+
+bool distinct_in_range(const int32_t* v, long long count, long long bound) {
+  std::unordered_set<int32_t> seen;
+  for (long long i = 0; i < count; ++i) {
+    if (v[i] < 0 || v[i] >= bound) return false;
+    if (!seen.insert(v[i]).second) return false;
+  }
+  return true;
+}
+
+void release_job(lra_ctx* ctx, Job* j) {
+  if (j->dmem) cudaFreeAsync(j->dmem, ctx->stream);
+  if (j->ev_start) cudaEventDestroy(j->ev_start);
+  if (j->ev_end) cudaEventDestroy(j->ev_end);
+  for (auto& pe : j->prof) cudaEventDestroy(pe.second);
+  ctx->used_bytes -= j->bytes;
+  if (j->slot >= 0) ctx->free_slots.push_back(j->slot);
+  delete j;
+}
+
+// Enqueue the whole solve of one job on the context stream.
+cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
+  cudaStream_t st = ctx->stream;
+  cudaError_t e;
+  JobStatus init{};
+  init.status = LRA_OK;
+  init.converged = 1;
+  init.trace_cap = j->trace_cap;
+  if ((e = cudaMemcpyAsync(j->js, &init, sizeof(init), cudaMemcpyHostToDevice, st))) return e;
+  if ((e = cudaMemsetAsync(j->bar, 0, sizeof(GridBarrier), st))) return e;
+  if ((e = cudaMemcpyAsync(j->J, p->init_J, sizeof(int) * j->l, cudaMemcpyHostToDevice, st))) return e;
+  if (j->q > 0) {
+    if ((e = cudaMemcpyAsync(j->rows, p->resid_rows, sizeof(int) * j->q, cudaMemcpyHostToDevice, st))) return e;
+    if ((e = cudaMemcpyAsync(j->cols, p->resid_cols, sizeof(int) * j->s, cudaMemcpyHostToDevice, st))) return e;
+  }
+  MaxvolArgs col{};
+  col.strip = j->C; col.N = j->m; col.l = j->l; col.si = j->l; col.st = 1;
+  col.pos = j->I; col.cand = j->cand; col.cand_rows = j->cand_rows; col.bar = j->bar;
+  col.js = j->js; col.trace_i = j->trace_i; col.trace_v = j->trace_v;
+  col.delta = j->delta; col.max_swaps = j->max_swaps;
+  MaxvolArgs row = col;
+  row.strip = j->R; row.N = j->n; row.si = 1; row.st = j->n; row.pos = j->J;
+
+  // after(cls, n): n kernels of class cls were just enqueued
+  auto after = [&](int cls, int n) -> cudaError_t {
+    j->launches += n;
+    if (cls == kClsMaxvol) j->maxvol_launches += n;
+    if (!j->profile) return cudaSuccess;
+    cudaEvent_t ev;
+    cudaError_t r = cudaEventCreate(&ev);
+    if (r) return r;
+    j->prof.emplace_back(cls, ev);
+    return cudaEventRecord(ev, st);
+  };
+  if ((e = cudaEventRecord(j->ev_start, st))) return e;
+  for (int sw = 0; sw < j->sweeps; ++sw) {
+    if ((e = launch_gather_cols(j->src, j->J, j->l, j->C, j->js, 1, ctx->sms, st)) || (e = after(kClsGather, 1))) return e;
+    col.gepp = (sw == 0);
+    col.half_step = 2 * sw;
+    col.xin = j->xbuf0;   // inverse of A[I, J] (vertical strip's cross)
+    if (!col.gepp) {
+      if ((e = launch_cross_inverse(j->C, j->l, 1, j->I, j->l, j->xbuf0, j->js, st)) ||
+          (e = after(kClsCross, 1))) return e;
+    }
+    if ((e = launch_maxvol(col, j->plan_col, st)) || (e = after(kClsMaxvol, 1))) return e;
+    if ((e = launch_gather_rows(j->src, j->I, j->l, j->R, j->js, ctx->sms, st)) || (e = after(kClsGather, 1))) return e;
+    row.gepp = 0;
+    row.half_step = 2 * sw + 1;
+    row.xin = j->xbuf1;   // inverse of A[I, J]^T (horizontal strip's cross)
+    if ((e = launch_cross_inverse(j->R, 1, j->n, j->J, j->l, j->xbuf1, j->js, st)) ||
+        (e = after(kClsCross, 1))) return e;
+    if ((e = launch_maxvol(row, j->plan_row, st)) || (e = after(kClsMaxvol, 1))) return e;
+    if ((e = launch_sweep_done(j->js, st)) || (e = after(kClsOther, 1))) return e;
+    if (j->tol > 0.0 && sw + 1 < j->sweeps) {
+      if ((e = launch_gather_cols(j->src, j->J, j->l, j->C, j->js, 1, ctx->sms, st)) || (e = after(kClsGather, 1))) return e;
+      if ((e = launch_nucleus(j->C, j->I, j->l, j->k, j->rank_tol, j->U, j->sigma, j->js, st)) || (e = after(kClsCross, 1))) return e;
+      if ((e = launch_sampled_residual(j->src, j->rows, (int)j->q, j->cols, (int)j->s, j->l, j->C, j->U,
+                                       j->R, j->CUq, j->partials, j->n_partials, j->js, st)) ||
+          (e = after(kClsResid, 3))) return e;
+      if ((e = launch_tol_check(j->js, j->tol, st)) || (e = after(kClsOther, 1))) return e;
+    }
+  }
+  // final strips for the returned CUR: C = M[:, J] (R = M[I, :] is current)
+  if ((e = launch_gather_cols(j->src, j->J, j->l, j->C, j->js, 0, ctx->sms, st)) || (e = after(kClsGather, 1))) return e;
+  if ((e = launch_nucleus(j->C, j->I, j->l, j->k, j->rank_tol, j->U, j->sigma, j->js, st)) || (e = after(kClsCross, 1))) return e;
+  if (j->q > 0) {
+    if ((e = launch_sampled_residual(j->src, j->rows, (int)j->q, j->cols, (int)j->s, j->l, j->C, j->U,
+                                     j->R, j->CUq, j->partials, j->n_partials, j->js, st)) ||
+        (e = after(kClsResid, 3))) return e;
+  }
+  if ((e = cudaMemcpyAsync(ctx->pinned + j->slot, j->js, sizeof(JobStatus), cudaMemcpyDeviceToHost, st))) return e;
+  return cudaEventRecord(j->ev_end, st);
+}
+
+void fill_info(lra_ctx* ctx, Job* j, lra_info* out) {
+  const JobStatus& h = ctx->pinned[j->slot];
+  std::memset(out, 0, sizeof(*out));
+  out->status = h.status;
+  out->state = h.status == LRA_OK ? LRA_STATE_DONE : LRA_STATE_FAILED;
+  out->sweeps_done = h.sweeps_done;
+  out->k_eff = h.k_eff;
+  out->swaps_total = h.swaps_total;
+  out->converged = h.converged;
+  out->trace_len = h.trace_len;
+  out->est_rel_err = j->q > 0 ? h.est_rel : -1.0;
+  out->est_mu = h.est_mu;
+  out->est_var = h.est_var;
+  out->sigma_max = h.sigma_max;
+  float ms = 0.0f;
+  if (cudaEventElapsedTime(&ms, j->ev_start, j->ev_end) == cudaSuccess) out->gpu_ms = ms;
+  out->kernel_launches = j->launches;
+  out->maxvol_launches = j->maxvol_launches;
+  out->maxvol_flops = h.maxvol_flops;
+  double t[5] = {0, 0, 0, 0, 0};
+  cudaEvent_t prev = j->ev_start;
+  for (auto& pe : j->prof) {
+    float d = 0.0f;
+    if (cudaEventElapsedTime(&d, prev, pe.second) == cudaSuccess) t[pe.first] += d;
+    prev = pe.second;
+  }
+  out->t_gather_ms = t[kClsGather];
+  out->t_maxvol_ms = t[kClsMaxvol];
+  out->t_cross_ms = t[kClsCross];
+  out->t_resid_ms = t[kClsResid];
+}
+
+Job* find_job(lra_ctx* ctx, lra_job id) {
+  auto it = ctx->jobs.find(id);
+  return it == ctx->jobs.end() ? nullptr : it->second;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lra_status_str(int32_t s) {
+  switch (s) {
+    case LRA_OK: return "ok";
+    case LRA_PENDING: return "pending";
+    case LRA_EINVAL: return "invalid argument";
+    case LRA_ENOMEM: return "out of device memory";
+    case LRA_EBUSY: return "admission refused (slots or memory budget)";
+    case LRA_ESINGULAR: return "singular strip (no nonsingular l x l submatrix)";
+    case LRA_ENONFINITE: return "non-finite matrix entry";
+    case LRA_ETIMEOUT: return "device wait timed out";
+    case LRA_ECUDA: return "CUDA error";
+    case LRA_ENOTFOUND: return "unknown job";
+    case LRA_ECANCELED: return "cancelled";
+    case LRA_ETOOLARGE: return "strip too large for the on-chip working set";
+    default: return "unknown status";
+  }
+}
+
+const char* lra_cross_last_error(lra_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+lra_status lra_cross_create(lra_ctx** out, const lra_ctx_params* params) {
+  if (!out || !params) return LRA_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return LRA_ECUDA;
+  if (params->device < 0 || params->device >= ndev) return LRA_EINVAL;
+  lra_ctx* ctx = new lra_ctx();
+  ctx->device = params->device;
+  ctx->max_slots = params->max_slots > 0 ? params->max_slots : 64;
+  ctx->budget = params->mem_budget_bytes;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  cudaDeviceProp prop{};
+  if (!e) e = cudaGetDeviceProperties(&prop, ctx->device);
+  if (e) { delete ctx; return LRA_ECUDA; }
+  int coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
+  if (!coop) { delete ctx; return LRA_ECUDA; }
+  ctx->sms = prop.multiProcessorCount;
+  ctx->smem_optin = prop.sharedMemPerBlockOptin;
+  if (params->stream) {
+    ctx->stream = static_cast<cudaStream_t>(params->stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)) { delete ctx; return LRA_ECUDA; }
+    ctx->own_stream = true;
+  }
+  if (cudaMallocHost(&ctx->pinned, sizeof(JobStatus) * ctx->max_slots)) {
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return LRA_ENOMEM;
+  }
+  for (int s = ctx->max_slots - 1; s >= 0; --s) ctx->free_slots.push_back(s);
+  *out = ctx;
+  return LRA_OK;
+}
+
+lra_status lra_cross_destroy(lra_ctx* ctx) {
+  if (!ctx) return LRA_EINVAL;
+  {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& kv : ctx->jobs) release_job(ctx, kv.second);
+    ctx->jobs.clear();
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    cudaFreeHost(ctx->pinned);
+  }
+  delete ctx;
+  return LRA_OK;
+}
+
+lra_status lra_cross_footprint(const lra_source* src, const lra_params* params, uint64_t* bytes) {
+  std::string why;
+  lra_status s = validate(src, params, &why);
+  if (s != LRA_OK) return s;
+  if (!bytes) return LRA_EINVAL;
+  *bytes = layout_bytes(src, params, nullptr);
+  return LRA_OK;
+}
+
+lra_status lra_cross_submit(lra_ctx* ctx, const lra_source* src, const lra_params* p, lra_job* out) {
+  if (!ctx || !out) return LRA_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  std::string why;
+  lra_status s = validate(src, p, &why);
+  if (s != LRA_OK) return fail(ctx, s, why);
+  if (!distinct_in_range(p->init_J, p->l, src->n)) return fail(ctx, LRA_EINVAL, "init_J must be l distinct columns");
+  if (p->resid_q > 0 && (!distinct_in_range(p->resid_rows, p->resid_q, src->m) ||
+                         !distinct_in_range(p->resid_cols, p->resid_s, src->n)))
+    return fail(ctx, LRA_EINVAL, "residual sample indices must be distinct and in range");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e) return cuda_fail(ctx, e, "cudaSetDevice");
+
+  Job* j = new Job();
+  j->l = p->l; j->k = p->k; j->sweeps = p->sweeps;
+  j->max_swaps = p->max_swaps > 0 ? p->max_swaps : 64 * p->l;
+  j->trace_cap = p->trace_cap;
+  j->profile = (p->flags & LRA_FLAG_PROFILE) != 0;
+  j->m = src->m; j->n = src->n; j->q = p->resid_q; j->s = p->resid_s;
+  j->delta = p->delta; j->rank_tol = p->rank_tol; j->tol = p->tol;
+  j->src.kind = src->kind;
+  j->src.dim = src->kind == LRA_GEN_CAUCHY ? 1 : src->dim;
+  j->src.m = src->m; j->src.n = src->n; j->src.a = src->a; j->src.lda = src->lda;
+  j->src.x = src->x; j->src.y = src->y;
+  j->src.h2 = src->h * src->h;
+  if (!plan_maxvol(j->m, j->l, ctx->sms, ctx->smem_optin, &j->plan_col) ||
+      !plan_maxvol(j->n, j->l, ctx->sms, ctx->smem_optin, &j->plan_row)) {
+    delete j;
+    return fail(ctx, LRA_ETOOLARGE, "strip does not fit in the shared memory of the grid");
+  }
+  j->bytes = layout_bytes(src, p, nullptr);
+  if ((int)ctx->jobs.size() >= ctx->max_slots || ctx->free_slots.empty() ||
+      (ctx->budget && ctx->used_bytes + j->bytes > ctx->budget)) {
+    delete j;
+    return fail(ctx, LRA_EBUSY, "no free slot or memory budget exhausted");
+  }
+  if ((e = cudaMallocAsync(reinterpret_cast<void**>(&j->dmem), j->bytes, ctx->stream))) {
+    delete j;
+    return cuda_fail(ctx, e, "cudaMallocAsync");
+  }
+  layout_bytes(src, p, j);
+  j->slot = ctx->free_slots.back();
+  ctx->free_slots.pop_back();
+  ctx->used_bytes += j->bytes;
+  if ((e = cudaEventCreate(&j->ev_start)) || (e = cudaEventCreate(&j->ev_end)) ||
+      (e = enqueue_solve(ctx, j, p))) {
+    cudaStreamSynchronize(ctx->stream);
+    release_job(ctx, j);
+    return cuda_fail(ctx, e, "enqueue");
+  }
+  j->id = ctx->next_id++;
+  ctx->jobs[j->id] = j;
+  *out = j->id;
+  return LRA_OK;
+}
+
+lra_status lra_cross_poll(lra_ctx* ctx, lra_job id, lra_info* out) {
+  if (!ctx || !out) return LRA_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  Job* j = find_job(ctx, id);
+  if (!j) return fail(ctx, LRA_ENOTFOUND, "unknown job");
+  cudaSetDevice(ctx->device);
+  cudaError_t e = cudaEventQuery(j->ev_end);
+  if (e == cudaErrorNotReady) {
+    std::memset(out, 0, sizeof(*out));
+    out->state = LRA_STATE_RUNNING;
+    out->status = LRA_PENDING;
+    return LRA_PENDING;
+  }
+  if (e) return cuda_fail(ctx, e, "cudaEventQuery");
+  fill_info(ctx, j, out);
+  return LRA_OK;
+}
+
+lra_status lra_cross_wait(lra_ctx* ctx, lra_job id, lra_info* out) {
+  if (!ctx || !out) return LRA_EINVAL;
+  cudaEvent_t ev;
+  {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    Job* j = find_job(ctx, id);
+    if (!j) return fail(ctx, LRA_ENOTFOUND, "unknown job");
+    ev = j->ev_end;
+    cudaSetDevice(ctx->device);
+  }
+  cudaError_t e = cudaEventSynchronize(ev);
+  if (e) return cuda_fail(ctx, e, "cudaEventSynchronize");
+  return lra_cross_poll(ctx, id, out);
+}
+
+lra_status lra_cross_fetch_cur(lra_ctx* ctx, lra_job id, const lra_cur_out* out) {
+  if (!ctx || !out) return LRA_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  Job* j = find_job(ctx, id);
+  if (!j) return fail(ctx, LRA_ENOTFOUND, "unknown job");
+  cudaSetDevice(ctx->device);
+  cudaError_t e = cudaEventSynchronize(j->ev_end);
+  if (e) return cuda_fail(ctx, e, "cudaEventSynchronize");
+  const JobStatus& h = ctx->pinned[j->slot];
+  lra_status result = (lra_status)h.status;
+  if (result == LRA_OK) {
+    const int l = j->l;
+    struct Piece { void* dst; const void* src; size_t bytes; };
+    const int tl = std::min(h.trace_len, j->trace_cap);
+    Piece pieces[] = {
+        {out->I, j->I, sizeof(int) * l},
+        {out->J, j->J, sizeof(int) * l},
+        {out->U, j->U, sizeof(double) * l * l},
+        {out->sigma, j->sigma, sizeof(double) * l},
+        {out->C, j->C, sizeof(float) * (size_t)j->m * l},
+        {out->R, j->R, sizeof(float) * (size_t)j->n * l},
+        {out->trace, j->trace_i, sizeof(int) * 4 * (size_t)tl},
+        {out->trace_val, j->trace_v, sizeof(double) * (size_t)tl},
+    };
+    for (const Piece& pc : pieces) {
+      if (!pc.dst || pc.bytes == 0) continue;
+      if ((e = cudaMemcpyAsync(pc.dst, pc.src, pc.bytes, cudaMemcpyDefault, ctx->stream))) break;
+    }
+    if (!e) e = cudaStreamSynchronize(ctx->stream);
+    if (e) result = cuda_fail(ctx, e, "fetch copy");
+  } else {
+    fail(ctx, result, lra_status_str(result));
+  }
+  ctx->jobs.erase(id);
+  release_job(ctx, j);
+  return result;
+}
+
+lra_status lra_cross_cancel(lra_ctx* ctx, lra_job id) {
+  if (!ctx) return LRA_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  Job* j = find_job(ctx, id);
+  if (!j) return fail(ctx, LRA_ENOTFOUND, "unknown job");
+  cudaSetDevice(ctx->device);
+  cudaEventSynchronize(j->ev_end);
+  ctx->jobs.erase(id);
+  release_job(ctx, j);
+  return LRA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,58 @@
+"""Shared helpers of the GPU parity tests (no GPU needed to import)."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle as O
+
+# A decision is "separated" when its competing volume ratios differ by more
+# than this relative amount: swapping row i into position j multiplies the
+# volume by |B_ij|, so the candidates are the entries of |B| (GEPP: of the
+# pivot column); the stop test compares max |B| with 1 + delta.
+SEPARATION = 1e-6
+
+
+def separated(dec, delta):
+    hs, kind, i, j, v1, v2 = dec
+    if kind in (O.GEPP, O.SWAP):
+        return v1 > 0 and (v1 - v2) / v1 > SEPARATION
+    return abs(v1 - (1.0 + delta)) / (1.0 + delta) > SEPARATION
+
+
+def compare_traces(gpu_trace, oracle_trace, delta):
+    """Walk the two decision logs in order.  They must agree on every
+    decision up to the first one where they differ, and that decision must be
+    unseparated in the oracle's log (a genuine near-tie).  Returns
+    (number of decisions compared, index of the first divergence or None)."""
+    n = min(len(gpu_trace), len(oracle_trace))
+    for idx in range(n):
+        o = oracle_trace[idx]
+        g = gpu_trace[idx]
+        hs, kind, i, j = o[0], o[1], o[2], o[3]
+        if kind in (O.GEPP, O.SWAP):
+            same = (int(g[0]), int(g[1]), int(g[2]), int(g[3])) == (hs, kind, i, j)
+        else:
+            same = (int(g[0]), int(g[1])) == (hs, kind)
+        if not same:
+            assert not separated(o, delta), (
+                f"decision {idx} differs although separated: oracle {o}, gpu {tuple(g)}")
+            return idx, idx
+    assert len(gpu_trace) == len(oracle_trace), (
+        f"logs agree on {n} decisions but have lengths {len(gpu_trace)} vs {len(oracle_trace)}")
+    return n, None
+
+
+def rel_fro_error(A64, C, U, R):
+    """||A - C U R||_F / ||A||_F in FP64 from the returned factors."""
+    E = A64 - (np.asarray(C, np.float64) @ U) @ np.asarray(R, np.float64)
+    return float(np.linalg.norm(E) / np.linalg.norm(A64))
+
+
+def sampled_error(src64, C, U, R, rows, cols):
+    return O.sampled_residual(src64, np.asarray(C, np.float64), U, np.asarray(R, np.float64),
+                              rows, cols)["rel"]
+
+
+def error_ok(err_gpu, err_oracle):
+    """Within 1.05x of the FP64 oracle's error, or 1e-5 absolute."""
+    return err_gpu <= max(1.05 * err_oracle, 1e-5)
