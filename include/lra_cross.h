@@ -174,6 +174,40 @@ lra_status lra_cross_cancel(lra_ctx* ctx, lra_job job);
 lra_status lra_cross_footprint(const lra_source* src, const lra_params* params,
                                uint64_t* bytes);
 
+/* One maxvol half-step that allocates no device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc/cudaFree while they run, for instance because those calls may
+ * synchronise the whole device, or because another allocator (a framework's
+ * caching allocator, a serving process that reserved its memory up front)
+ * owns the device memory.
+ *
+ * It runs the same kernel as the maxvol step of lra_cross_submit on an N x l
+ * FP32 strip S held by the caller in device memory, element (i, t) at
+ * strip[i*row_stride + t*col_stride]:
+ *   xinv == NULL: Gauss-Jordan start with partial pivoting, then maxvol swaps;
+ *                 pos[0..l) receives the selected rows (device int32, output).
+ *   xinv != NULL: warm start from pos[0..l) (device int32, in/out) with xinv
+ *                 the row-major FP64 inverse of S[pos, :] (device, l x l).
+ * status_out (device int32[3]) receives {lra_status, swaps, converged}.
+ * Everything is enqueued on `stream` (cudaStream_t, NULL = legacy default);
+ * the call returns without waiting for the GPU.
+ *
+ * Scratch: a static device array of about 251 KB (candidate slots for 160
+ * CTAs, candidate rows of up to 96 FP64 entries, the grid barrier and the
+ * status word), present on every GPU that loads this library until exit.
+ * Limits: l <= 96, and the strip must fit the shared memory of <= 160 CTAs;
+ * otherwise LRA_ETOOLARGE is returned and nothing is launched.  Bad pointers
+ * or sizes return LRA_EINVAL.
+ * The first call on a device (with that device current) looks up the
+ * device address of the array; make that first call before any stream
+ * capture.  Every call shares the one array and clears what must start at
+ * zero: calls whose kernels overlap on the GPU race, so issue them on one
+ * stream (or otherwise serialise them). */
+lra_status lra_maxvol_noalloc(const float* strip, int64_t N, int32_t l,
+                              int64_t row_stride, int64_t col_stride, int32_t* pos,
+                              const double* xinv, double delta, int32_t max_swaps,
+                              int32_t* status_out, void* stream);
+
 /* Static message for a status code. */
 const char* lra_status_str(int32_t status);
 
