@@ -308,7 +308,8 @@ def run_ours(args, wl_name):
         "wall_s": t_wall,
         "gather_gbs": gather_gbs,
         "kernel_ms_per_step": {"maxvol": t_mv / len(infos), "gather": t_g / len(infos),
-                               "cross": t_x / len(infos), "resid": t_r / len(infos)},
+                               "inverse": sum(i.t_inverse_ms for i in infos) / len(infos),
+                               "nucleus": t_x / len(infos), "resid": t_r / len(infos)},
         "roofline": {"kernel": "maxvol_kernel", "bound": "alu", "achieved": achieved,
                      "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak if fp64_peak else None,
                      "traffic": None,

@@ -130,6 +130,7 @@ typedef struct {
   double t_maxvol_ms;
   double t_cross_ms;
   double t_resid_ms;
+  double t_inverse_ms;        /* fresh cross inverses before warm-started steps     */
 } lra_info;
 
 typedef struct {

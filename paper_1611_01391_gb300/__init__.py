@@ -66,7 +66,8 @@ class lra_info(ctypes.Structure):
                 ("gpu_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int32),
                 ("maxvol_launches", ctypes.c_int32), ("maxvol_flops", ctypes.c_double),
                 ("t_gather_ms", ctypes.c_double), ("t_maxvol_ms", ctypes.c_double),
-                ("t_cross_ms", ctypes.c_double), ("t_resid_ms", ctypes.c_double)]
+                ("t_cross_ms", ctypes.c_double), ("t_resid_ms", ctypes.c_double),
+                ("t_inverse_ms", ctypes.c_double)]
 
 
 class lra_cur_out(ctypes.Structure):

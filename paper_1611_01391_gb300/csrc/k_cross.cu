@@ -48,46 +48,67 @@ nucleus_kernel(const float* __restrict__ C, const int* __restrict__ I, int l, in
   }
   __syncthreads();
 
+  // Pairs of a round are handled by groups of 8 lanes (4 pairs per warp), so
+  // one FP64 instruction serves four rotations; the FP64 pipe is the limit.
   const int np = (l + 1) & ~1;                      // players incl. a dummy when l is odd
   const double tol = (double)l * DBL_EPSILON;
+  const int gl = lane & 7;
+  const int ngroups = nwarps * 4;
   for (int sweep = 0; sweep < 60; ++sweep) {
     if (tid == 0) *rotated = 0;
     __syncthreads();
     for (int round = 0; round < np - 1; ++round) {
-      for (int slot = warp; slot < np / 2; slot += nwarps) {
+      for (int base = warp * 4; base < np / 2; base += ngroups) {
+        const int slot = base + (lane >> 3);
         const int x0 = slot, x1 = np - 1 - slot;
         int p = (x0 == 0) ? 0 : ((x0 - 1 + round) % (np - 1)) + 1;
         int q = (x1 == 0) ? 0 : ((x1 - 1 + round) % (np - 1)) + 1;
-        if (p >= l || q >= l) continue;
         if (p > q) { const int t = p; p = q; q = t; }
+        const bool act = slot < np / 2 && q < l;
         double* wp = W + (size_t)p * l;
         double* wq = W + (size_t)q * l;
         double al = 0.0, be = 0.0, ga = 0.0;
-        for (int a = lane; a < l; a += 32) {
-          const double u = wp[a], v = wq[a];
-          al = fma(u, u, al);
-          be = fma(v, v, be);
-          ga = fma(u, v, ga);
+        if (act)
+          for (int a = gl; a < l; a += 8) {
+            const double u = wp[a], v = wq[a];
+            al = fma(u, u, al);
+            be = fma(v, v, be);
+            ga = fma(u, v, ga);
+          }
+#pragma unroll
+        for (int off = 4; off > 0; off >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, off);
+          be += __shfl_xor_sync(0xffffffffu, be, off);
+          ga += __shfl_xor_sync(0xffffffffu, ga, off);
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (al == 0.0 || be == 0.0 || fabs(ga) <= tol * sqrt(al) * sqrt(be)) continue;
+        if (!act || al == 0.0 || be == 0.0 || ga * ga <= tol * tol * al * be) continue;
+        // Rotation tangent t from the symmetric Jacobi step; an approximate t
+        // (FP32) still gives an exactly orthogonal rotation because c and s
+        // are formed from the same t in FP64: c = (1 + t^2)^{-1/2}, s = c t.
         const double zeta = (be - al) / (2.0 * ga);
-        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double c = 1.0 / sqrt(1.0 + t * t);
-        const double s = c * t;
+        const float zf = (float)zeta;
+        // |zeta| > 1e18 (columns of very different norms): t = 1/(2 zeta) to
+        // FP32 accuracy, and zeta^2 would overflow FP32.
+        const float tf = fabsf(zf) > 1e18f
+                             ? 0.5f / zf
+                             : (zf >= 0.0f ? 1.0f : -1.0f) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)));
+        const double t = (double)tf;
+        const double x = fma(t, t, 1.0);
+        double y = (double)rsqrtf((float)x);          // Newton-Raphson for x^{-1/2}
+        y = y * fma(-0.5 * x * y, y, 1.5);
+        y = y * fma(-0.5 * x * y, y, 1.5);
+        const double c = y, s = y * t;
         double* vp = V + (size_t)p * l;
         double* vq = V + (size_t)q * l;
-        for (int a = lane; a < l; a += 32) {
+        for (int a = gl; a < l; a += 8) {
           const double u = wp[a], v = wq[a];
-          wp[a] = c * u - s * v;
-          wq[a] = s * u + c * v;
-          const double x = vp[a], y = vq[a];
-          vp[a] = c * x - s * y;
-          vq[a] = s * x + c * y;
+          wp[a] = fma(c, u, -s * v);
+          wq[a] = fma(s, u, c * v);
+          const double xx = vp[a], yy = vq[a];
+          vp[a] = fma(c, xx, -s * yy);
+          vq[a] = fma(s, xx, c * yy);
         }
-        if (lane == 0) *rotated = 1;
+        if (gl == 0) *rotated = 1;
       }
       __syncthreads();
     }
@@ -150,7 +171,8 @@ cross_inverse_kernel(const float* __restrict__ strip, long long si, long long st
   const int w = 2 * l;
   double* A = reinterpret_cast<double*>(smem_raw);  // l x 2l, row-major
   double* f = A + (size_t)l * w;                    // column t before elimination
-  int* piv_row = reinterpret_cast<int*>(f + kMaxL);
+  double* recip = f + kMaxL;                        // 1 / pivot of the current step
+  int* piv_row = reinterpret_cast<int*>(recip + 1);
   int* bad = piv_row + 1;
   const int tid = threadIdx.x, nthr = blockDim.x;
   if (tid == 0) *bad = 0;
@@ -171,21 +193,31 @@ cross_inverse_kernel(const float* __restrict__ strip, long long si, long long st
     if (tid == 0) set_status(js, LRA_ENONFINITE);
     return;
   }
+  // Columns < t of the left half are already unit columns, so step t only
+  // touches columns t..2l-1 (width wt).  Magnitudes are compared on their
+  // IEEE bit patterns (integer compares), and row t is scaled by the FP64
+  // reciprocal of the pivot.
   for (int t = 0; t < l; ++t) {
     if (tid < 32) {  // pivot: largest |A[r][t]|, r >= t (smallest r on ties)
-      double best = -1.0;
-      int br = t;
+      unsigned long long best = 0ull;
+      int br = l;
       for (int r = t + tid; r < l; r += 32) {
-        const double v = fabs(A[(size_t)r * w + t]);
-        if (v > best) { best = v; br = r; }
+        const unsigned long long k =
+            (unsigned long long)__double_as_longlong(A[(size_t)r * w + t]) & 0x7fffffffffffffffull;
+        if (br == l || k > best) { best = k; br = r; }
       }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
-        const double ob = __shfl_down_sync(0xffffffffu, best, off);
+        const unsigned long long ob = __shfl_down_sync(0xffffffffu, best, off);
         const int orr = __shfl_down_sync(0xffffffffu, br, off);
-        if (ob > best || (ob == best && orr < br)) { best = ob; br = orr; }
+        if (orr < l && (br == l || ob > best || (ob == best && orr < br))) { best = ob; br = orr; }
       }
-      if (tid == 0) *piv_row = (best > 0.0) ? br : -1;
+      if (tid == 0) {
+        *piv_row = (best != 0ull && br < l) ? br : -1;
+        // one FP64 division for the whole step (all threads dividing would
+        // occupy the FP64 pipe for thousands of cycles)
+        if (br < l && best != 0ull) *recip = 1.0 / A[(size_t)br * w + t];
+      }
     }
     __syncthreads();
     const int p = *piv_row;
@@ -194,20 +226,20 @@ cross_inverse_kernel(const float* __restrict__ strip, long long si, long long st
       return;
     }
     if (p != t)
-      for (int c = tid; c < w; c += nthr) {
+      for (int c = t + tid; c < w; c += nthr) {
         const double x = A[(size_t)t * w + c];
         A[(size_t)t * w + c] = A[(size_t)p * w + c];
         A[(size_t)p * w + c] = x;
       }
     __syncthreads();
-    const double pv = A[(size_t)t * w + t];
-    __syncthreads();
-    for (int c = tid; c < w; c += nthr) A[(size_t)t * w + c] /= pv;
+    const double rp = *recip;
+    for (int c = t + tid; c < w; c += nthr) A[(size_t)t * w + c] *= rp;
     for (int r = tid; r < l; r += nthr) f[r] = (r == t) ? 0.0 : A[(size_t)r * w + t];
     __syncthreads();
-    for (int e = tid; e < l * w; e += nthr) {
-      const int r = e / w, c = e - r * w;
-      if (r != t) A[e] = fma(-f[r], A[(size_t)t * w + c], A[e]);
+    const int wt = w - t;
+    for (int e = tid; e < l * wt; e += nthr) {
+      const int r = e / wt, c = t + (e - r * wt);
+      if (r != t) A[(size_t)r * w + c] = fma(-f[r], A[(size_t)t * w + c], A[(size_t)r * w + c]);
     }
     __syncthreads();
   }
@@ -219,7 +251,7 @@ cross_inverse_kernel(const float* __restrict__ strip, long long si, long long st
 
 cudaError_t launch_cross_inverse(const float* strip, long long si, long long st, const int* pos,
                                  int l, double* xinv, JobStatus* js, cudaStream_t stream) {
-  const size_t smem = ((size_t)l * 2 * l + kMaxL) * sizeof(double) + 2 * sizeof(int);
+  const size_t smem = ((size_t)l * 2 * l + kMaxL + 1) * sizeof(double) + 2 * sizeof(int);
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(cross_inverse_kernel,

@@ -35,26 +35,33 @@ namespace lra {
 constexpr int kMaxvolThreads = 512;
 constexpr int kNone = 0x7fffffff;
 
+// Candidates are compared on k = the IEEE-754 bit pattern of |value| as an
+// unsigned 64-bit integer, which orders non-negative doubles exactly like
+// their values.  Integer compares keep the argmax off the FP64 pipe (a
+// double compare issues at the FP64 rate, 1/64 of FP32 on this part).
 struct Best {
-  double v;
+  unsigned long long k;
   int idx;
   int nf;
 };
 
+constexpr unsigned long long kAbsMask = 0x7fffffffffffffffull;
+constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
+
 __device__ __forceinline__ void consider(Best& b, double x, int idx) {
-  const double ax = fabs(x);
-  if (!(ax <= DBL_MAX)) {
+  const unsigned long long k = (unsigned long long)__double_as_longlong(x) & kAbsMask;
+  if (k >= kInfBits) {
     b.nf = 1;
-  } else if (ax > b.v || (ax == b.v && idx < b.idx)) {
-    b.v = ax;
+  } else if (k > b.k || (k == b.k && idx < b.idx)) {
+    b.k = k;
     b.idx = idx;
   }
 }
 
-__device__ __forceinline__ void merge(Best& b, double v, int idx, int nf) {
+__device__ __forceinline__ void merge(Best& b, unsigned long long k, int idx, int nf) {
   b.nf |= nf;
-  if (v > b.v || (v == b.v && idx < b.idx)) {
-    b.v = v;
+  if (k > b.k || (k == b.k && idx < b.idx)) {
+    b.k = k;
     b.idx = idx;
   }
 }
@@ -62,10 +69,10 @@ __device__ __forceinline__ void merge(Best& b, double v, int idx, int nf) {
 __device__ __forceinline__ Best warp_reduce(Best b) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    const double v = __shfl_down_sync(0xffffffffu, b.v, off);
+    const unsigned long long k = __shfl_down_sync(0xffffffffu, b.k, off);
     const int i = __shfl_down_sync(0xffffffffu, b.idx, off);
     const int f = __shfl_down_sync(0xffffffffu, b.nf, off);
-    merge(b, v, i, f);
+    merge(b, k, i, f);
   }
   return b;
 }
@@ -78,7 +85,7 @@ __device__ __forceinline__ void block_reduce(Best b, Best* red, Best* out) {
   __syncthreads();
   if (warp == 0) {
     const int nw = blockDim.x >> 5;
-    Best c = (lane < nw) ? red[lane] : Best{-1.0, kNone, 0};
+    Best c = (lane < nw) ? red[lane] : Best{0ull, kNone, 0};
     c = warp_reduce(c);
     if (lane == 0) *out = c;
   }
@@ -92,7 +99,58 @@ struct Ctl {
   int timed_out;
 };
 
-template <int GS>
+// Warm start of the rows of this CTA: W[r, :] = S[g, :] X^{-1}.  A group of
+// GS lanes owns a row; lane gl computes columns gl + GS c, c < NC, so every
+// issued DFMA is useful work (NC = ceil(l / GS) exactly).
+template <int GS, int NC, typename XPtr>
+__device__ __forceinline__ void warm_rows(const MaxvolArgs& a, double* B, int nrows, long long row0,
+                                          XPtr X) {
+  const int l = a.l;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  constexpr int kGpw = 32 / GS;
+  const int gl = lane % GS;
+  const int ngroups = nwarps * kGpw;
+  for (int base = warp * kGpw; base < nrows; base += ngroups) {
+    const int r = base + lane / GS;
+    const bool active = r < nrows;
+    const long long g = row0 + r;
+    double* brow = B + (size_t)r * l;
+    if (active)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int t = gl + GS * c;
+        if (t < l) brow[t] = (double)a.strip[g * a.si + (long long)t * a.st];
+      }
+    __syncwarp();
+    double acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+    if (active) {
+      for (int p = 0; p < l; ++p) {
+        const double sp = brow[p];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const int q = gl + GS * c;
+          if (q < l) acc[c] = fma(sp, X[(size_t)p * l + q], acc[c]);
+        }
+      }
+    }
+    __syncwarp();
+    if (active)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int q = gl + GS * c;
+        if (q < l) brow[q] = acc[c];
+      }
+  }
+}
+
+struct GlobalX {  // read-only path for an X^{-1} that does not fit on chip
+  const double* p;
+  __device__ __forceinline__ double operator[](size_t i) const { return __ldg(p + i); }
+};
+
+template <int GS, int NC>
 __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a) {
   if (a.js->status != LRA_OK || a.js->stop) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -108,14 +166,14 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
   double* colj = B + (size_t)rpc * l;                        // rpc
   double* rraw = colj + rpc;                                 // l
   double* rvec = rraw + kMaxL;                               // l
-  Best* red = reinterpret_cast<Best*>(rvec + kMaxL);         // 32
+  double* xs = rvec + kMaxL;                                 // l*l when staged
+  Best* red = reinterpret_cast<Best*>(xs + (a.stage_xinv ? (size_t)l * l : 0));  // 32
   Ctl* ctl = reinterpret_cast<Ctl*>(red + 32);
   int* pos_s = reinterpret_cast<int*>(ctl + 1);              // l
   unsigned char* used = reinterpret_cast<unsigned char*>(pos_s + kMaxL);  // rpc
 
   const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
   constexpr int kGpw = 32 / GS;
-  constexpr int kCols = (kMaxL + GS - 1) / GS;
   const int gl = lane % GS;
   const int ngroups = nwarps * kGpw;
 
@@ -134,36 +192,12 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
       B[e] = (double)a.strip[(row0 + r) * a.si + (long long)t * a.st];
     }
   } else {
-    for (int base = warp * kGpw; base < nrows; base += ngroups) {
-      const int r = base + lane / GS;
-      const bool active = r < nrows;
-      const long long g = row0 + r;
-      double* brow = B + (size_t)r * l;
-      if (active)
-        for (int t = gl; t < l; t += GS) brow[t] = (double)a.strip[g * a.si + (long long)t * a.st];
-      __syncwarp();
-      double acc[kCols];
-#pragma unroll
-      for (int c = 0; c < kCols; ++c) acc[c] = 0.0;
-      if (active) {
-        for (int p = 0; p < l; ++p) {
-          const double sp = brow[p];
-          const double* xr = a.xin + (size_t)p * l;
-#pragma unroll
-          for (int c = 0; c < kCols; ++c) {
-            const int q = gl + GS * c;
-            if (q < l) acc[c] = fma(sp, __ldg(xr + q), acc[c]);
-          }
-        }
-      }
-      __syncwarp();
-      if (active) {
-#pragma unroll
-        for (int c = 0; c < kCols; ++c) {
-          const int q = gl + GS * c;
-          if (q < l) brow[q] = acc[c];
-        }
-      }
+    if (a.stage_xinv) {
+      for (int e = tid; e < l * l; e += nthr) xs[e] = a.xin[e];
+      __syncthreads();
+      warm_rows<GS, NC>(a, B, nrows, row0, static_cast<const double*>(xs));
+    } else {
+      warm_rows<GS, NC>(a, B, nrows, row0, GlobalX{a.xin});
     }
     __syncthreads();
     // rows currently selected are exactly the unit vectors of B = S X^{-1}
@@ -176,7 +210,7 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
   __syncthreads();
 
   // ---- initial scan
-  Best mine{-1.0, kNone, 0};
+  Best mine{0ull, kNone, 0};
   bool gepp_phase = a.gepp != 0;
   for (int e = tid; e < nrows * l; e += nthr) {
     const int r = e / l, t = e - r * l;
@@ -191,7 +225,7 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
     if (G > 1) {
       const Best cb = ctl->cta_best;
       Cand* slot = a.cand + buf * kMaxGrid + cta;
-      if (tid == 0) *slot = Cand{cb.v, cb.idx, cb.nf};
+      if (tid == 0) *slot = Cand{cb.k, cb.idx, cb.nf};
       if (cb.idx != kNone && tid < l) {
         const int r = (int)(cb.idx / l - row0);
         a.cand_rows[((size_t)buf * kMaxGrid + cta) * l + tid] = B[(size_t)r * l + tid];
@@ -200,10 +234,10 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
         if (tid == 0) set_status(a.js, LRA_ETIMEOUT);
         return;
       }
-      Best c{-1.0, kNone, 0};
+      Best c{0ull, kNone, 0};
       for (int k = tid; k < G; k += nthr) {
         const Cand* p = a.cand + buf * kMaxGrid + k;
-        merge(c, __ldcg(&p->val), __ldcg(&p->idx), __ldcg(&p->flags));
+        merge(c, __ldcg(&p->key), __ldcg(&p->idx), __ldcg(&p->flags));
       }
       block_reduce(c, red, &ctl->win);
       win = ctl->win;
@@ -212,18 +246,19 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
     }
 
     // ---- decision (identical in every CTA)
+    const double wv = __longlong_as_double((long long)win.k);
     int kind;
     if (win.nf) {
       if (cta == 0 && tid == 0) set_status(a.js, LRA_ENONFINITE);
       return;
     }
     if (gepp_phase) {
-      if (!(win.v > 0.0) || win.idx == kNone) {
+      if (!(wv > 0.0) || win.idx == kNone) {
         if (cta == 0 && tid == 0) set_status(a.js, LRA_ESINGULAR);
         return;
       }
       kind = LRA_TRACE_GEPP;
-    } else if (win.v <= 1.0 + a.delta) {
+    } else if (wv <= 1.0 + a.delta) {
       kind = LRA_TRACE_STOP;
     } else if (swaps >= a.max_swaps) {
       kind = LRA_TRACE_CAP;
@@ -240,7 +275,7 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
         a.trace_i[4 * n + 1] = kind;
         a.trace_i[4 * n + 2] = (int)istar;
         a.trace_i[4 * n + 3] = jstar;
-        a.trace_v[n] = win.v;
+        a.trace_v[n] = wv;
         a.js->trace_len = n + 1;
       }
     }
@@ -271,25 +306,33 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
     // ---- fused update + scan for the next decision
     const bool next_gepp = gepp_phase && (step + 1 < l);
     const int next_col = step + 1;
-    mine = Best{-1.0, kNone, 0};
+    mine = Best{0ull, kNone, 0};
     for (int base = warp * kGpw; base < nrows; base += ngroups) {
       const int r = base + lane / GS;
       if (r < nrows) {
         const long long g = row0 + r;
         double* brow = B + (size_t)r * l;
         if (g == istar) {
-          for (int t = gl; t < l; t += GS) {
-            const double v = (t == jstar) ? 1.0 : 0.0;
-            brow[t] = v;
-            if (!next_gepp) consider(mine, v, (int)(g * l + t));
+#pragma unroll
+          for (int cc = 0; cc < NC; ++cc) {
+            const int t = gl + GS * cc;
+            if (t < l) {
+              const double v = (t == jstar) ? 1.0 : 0.0;
+              brow[t] = v;
+              if (!next_gepp) consider(mine, v, (int)(g * l + t));
+            }
           }
         } else {
           const double c = colj[r];
           const bool scan_row = !(next_gepp && used[r]);
-          for (int t = gl; t < l; t += GS) {
-            const double v = fma(-c, rvec[t], brow[t]);
-            brow[t] = v;
-            if (scan_row && (!next_gepp || t == next_col)) consider(mine, v, (int)(g * l + t));
+#pragma unroll
+          for (int cc = 0; cc < NC; ++cc) {
+            const int t = gl + GS * cc;
+            if (t < l) {
+              const double v = fma(-c, rvec[t], brow[t]);
+              brow[t] = v;
+              if (scan_row && (!next_gepp || t == next_col)) consider(mine, v, (int)(g * l + t));
+            }
           }
         }
       }
@@ -316,10 +359,10 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
   }
 }
 
-static size_t maxvol_smem(int rpc, int l) {
+static size_t maxvol_smem(int rpc, int l, bool stage_xinv) {
   size_t b = (size_t)rpc * l * sizeof(double) + (size_t)rpc * sizeof(double) +
-             2 * kMaxL * sizeof(double) + 32 * sizeof(Best) + sizeof(Ctl) +
-             kMaxL * sizeof(int) + (size_t)rpc;
+             2 * kMaxL * sizeof(double) + (stage_xinv ? (size_t)l * l * sizeof(double) : 0) +
+             32 * sizeof(Best) + sizeof(Ctl) + kMaxL * sizeof(int) + (size_t)rpc;
   return (b + 15) & ~(size_t)15;
 }
 
@@ -331,38 +374,54 @@ bool plan_maxvol(long long N, int l, int sms, size_t smem_limit, MaxvolPlan* pla
   if (g > kMaxGrid) g = kMaxGrid;
   for (;;) {
     const long long rpc = (N + g - 1) / g;
-    const size_t sm = maxvol_smem((int)rpc, l);
-    if (sm <= smem_limit) {
-      plan->grid = (int)g;
-      plan->rows_per_cta = (int)rpc;
-      plan->threads = kMaxvolThreads;
-      plan->smem = sm;
-      return true;
+    // stage X^{-1} in shared memory when it fits beside the chunk of W
+    for (int stage = 1; stage >= 0; --stage) {
+      const size_t sm = maxvol_smem((int)rpc, l, stage != 0);
+      if (sm <= smem_limit) {
+        plan->grid = (int)g;
+        plan->rows_per_cta = (int)rpc;
+        plan->threads = kMaxvolThreads;
+        plan->smem = sm;
+        plan->stage_xinv = stage;
+        return true;
+      }
     }
     if (g >= sms || g >= kMaxGrid) return false;
     ++g;
   }
 }
 
-template <int GS>
+template <int GS, int NC>
 static cudaError_t launch_gs(MaxvolArgs& a, const MaxvolPlan& plan, cudaStream_t st) {
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(maxvol_kernel<GS>,
+    cudaError_t e = cudaFuncSetAttribute(maxvol_kernel<GS, NC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(maxvol_kernel<GS>), dim3(plan.grid),
-                                     dim3(plan.threads), args, plan.smem, st);
+  return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(maxvol_kernel<GS, NC>),
+                                     dim3(plan.grid), dim3(plan.threads), args, plan.smem, st);
+}
+
+// Lanes per row group: 8 for l <= 24 (4 rows per warp), 16 for l <= 48,
+// 32 above; each lane then owns NC = ceil(l / GS) <= 3 columns.
+template <int GS>
+static cudaError_t launch_nc(MaxvolArgs& a, const MaxvolPlan& plan, cudaStream_t st) {
+  switch ((a.l + GS - 1) / GS) {
+    case 1: return launch_gs<GS, 1>(a, plan, st);
+    case 2: return launch_gs<GS, 2>(a, plan, st);
+    default: return launch_gs<GS, 3>(a, plan, st);
+  }
 }
 
 cudaError_t launch_maxvol(MaxvolArgs a, const MaxvolPlan& plan, cudaStream_t st) {
   a.rows_per_cta = plan.rows_per_cta;
-  if (a.l <= 8) return launch_gs<8>(a, plan, st);
-  if (a.l <= 16) return launch_gs<16>(a, plan, st);
-  return launch_gs<32>(a, plan, st);
+  a.stage_xinv = plan.stage_xinv;
+  if (a.l <= 24) return launch_nc<8>(a, plan, st);
+  if (a.l <= 48) return launch_nc<16>(a, plan, st);
+  return launch_nc<32>(a, plan, st);
 }
 
 }  // namespace lra

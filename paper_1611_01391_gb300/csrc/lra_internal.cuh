@@ -89,7 +89,7 @@ struct GridBarrier {
 
 // Candidate of one CTA in the grid-wide argmax exchange.
 struct Cand {
-  double val;        // |B_ij| (or -1 when the CTA has no candidate)
+  unsigned long long key;  // bit pattern of |B_ij| (0 with idx = INT_MAX: none)
   int idx;           // flat index i*l + j in the strip
   int flags;         // bit 0: a non-finite value was seen
 };

@@ -39,12 +39,14 @@ struct MaxvolArgs {
   double delta;
   int max_swaps;
   int rows_per_cta;
+  int stage_xinv;   // copy X^{-1} into shared memory for the warm start
 };
 
 struct MaxvolPlan {
   int grid;
   int threads;
   int rows_per_cta;
+  int stage_xinv;
   size_t smem;
 };
 

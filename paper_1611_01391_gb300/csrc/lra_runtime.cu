@@ -43,7 +43,7 @@ struct Job {
   std::vector<std::pair<int, cudaEvent_t>> prof;  // (kernel class, event after the launch)
 };
 
-enum { kClsGather = 0, kClsMaxvol = 1, kClsCross = 2, kClsResid = 3, kClsOther = 4 };
+enum { kClsGather = 0, kClsMaxvol = 1, kClsCross = 2, kClsResid = 3, kClsInverse = 4, kClsOther = 5 };
 
 // Sub-buffer offsets of one job's single device allocation.
 struct Layout {
@@ -223,7 +223,7 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
     col.xin = j->xbuf0;   // inverse of A[I, J] (vertical strip's cross)
     if (!col.gepp) {
       if ((e = launch_cross_inverse(j->C, j->l, 1, j->I, j->l, j->xbuf0, j->js, st)) ||
-          (e = after(kClsCross, 1))) return e;
+          (e = after(kClsInverse, 1))) return e;
     }
     if ((e = launch_maxvol(col, j->plan_col, st)) || (e = after(kClsMaxvol, 1))) return e;
     if ((e = launch_gather_rows(j->src, j->I, j->l, j->R, j->js, ctx->sms, st)) || (e = after(kClsGather, 1))) return e;
@@ -231,7 +231,7 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
     row.half_step = 2 * sw + 1;
     row.xin = j->xbuf1;   // inverse of A[I, J]^T (horizontal strip's cross)
     if ((e = launch_cross_inverse(j->R, 1, j->n, j->J, j->l, j->xbuf1, j->js, st)) ||
-        (e = after(kClsCross, 1))) return e;
+        (e = after(kClsInverse, 1))) return e;
     if ((e = launch_maxvol(row, j->plan_row, st)) || (e = after(kClsMaxvol, 1))) return e;
     if ((e = launch_sweep_done(j->js, st)) || (e = after(kClsOther, 1))) return e;
     if (j->tol > 0.0 && sw + 1 < j->sweeps) {
@@ -274,7 +274,7 @@ void fill_info(lra_ctx* ctx, Job* j, lra_info* out) {
   out->kernel_launches = j->launches;
   out->maxvol_launches = j->maxvol_launches;
   out->maxvol_flops = h.maxvol_flops;
-  double t[5] = {0, 0, 0, 0, 0};
+  double t[6] = {0, 0, 0, 0, 0, 0};
   cudaEvent_t prev = j->ev_start;
   for (auto& pe : j->prof) {
     float d = 0.0f;
@@ -285,6 +285,7 @@ void fill_info(lra_ctx* ctx, Job* j, lra_info* out) {
   out->t_maxvol_ms = t[kClsMaxvol];
   out->t_cross_ms = t[kClsCross];
   out->t_resid_ms = t[kClsResid];
+  out->t_inverse_ms = t[kClsInverse];
 }
 
 Job* find_job(lra_ctx* ctx, lra_job id) {
