@@ -312,7 +312,8 @@ def run_ours(args, wl_name):
                                "nucleus": t_x / len(infos), "resid": t_r / len(infos)},
         "roofline": {"kernel": "maxvol_kernel", "bound": "alu", "achieved": achieved,
                      "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak if fp64_peak else None,
-                     "traffic": None,
+                     "traffic": captured_traffic("k_maxvol.cu", "maxvol_cauchy65536.md"),
+                     "traffic_note": "DRAM bytes per maxvol launch from the committed ncu capture (null if the kernel changed since)",
                      "peak_source": f"FP64 FMA rate: {SMS} SMs x {FP64_FMA_PER_SM_CLK} FMA/clk x median SM clock {sm_mhz:.0f} MHz"},
         "gpu_launches": int(sum(i.kernel_launches for i in infos)),
         "clocks": clk,
@@ -334,6 +335,48 @@ def run_ours(args, wl_name):
                 line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                                         "sample": f"failed: {e}"}
         print(json.dumps(line), flush=True)
+
+
+def run_profile_solves(args, wl_name):
+    """N solves of the workload and nothing else: the command that ncu
+    captures (launch list, per-kernel counters)."""
+    import torch
+    import paper_1611_01391_gb300 as L
+    wl = WORKLOADS[wl_name]
+    inp = make_inputs(wl, 0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = L.Context(0, stream=stream.cuda_stream)
+    if wl["kind"] == "cauchy":
+        xd = torch.from_numpy(inp["x"]).cuda()
+        yd = torch.from_numpy(inp["y"]).cuda()
+        src = L.make_source("cauchy", x=xd, y=yd)
+    else:
+        ad = torch.from_numpy(inp["a"]).cuda()
+        src = L.make_source("dense", a=ad)
+    params, keep = L.make_params(wl["k"], wl["l"], wl["sweeps"], inp["J0"], resid_rows=inp["rows"],
+                                 resid_cols=inp["cols"])
+    for _ in range(args.profile_solves):
+        res = ctx.fetch(ctx.submit(src, params), wl["l"])
+        if res.info.status != 0:
+            raise RuntimeError(L.lra_status_str(res.info.status))
+    ctx.close()
+    print(f"profile solves done: {args.profile_solves} x {wl_name}", flush=True)
+
+
+def captured_traffic(kernel_file, summary):
+    """DRAM bytes per launch from a committed ncu summary, or None when the
+    kernel source changed since that capture (its sha256 is recorded)."""
+    import hashlib
+    try:
+        text = open(os.path.join(ROOT, "profiles", summary)).read()
+        src = open(os.path.join(ROOT, "paper_1611_01391_gb300", "csrc", kernel_file), "rb").read()
+    except OSError:
+        return None
+    fields = dict(ln.split(":", 1) for ln in text.splitlines() if ln.startswith(("traffic_bytes_per_launch:", "source_sha256:")))
+    if fields.get("source_sha256", "").strip() != hashlib.sha256(src).hexdigest():
+        return None
+    return float(fields["traffic_bytes_per_launch"])
 
 
 def run_reference(args, wl_name):
@@ -365,7 +408,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cauchy65536")
+    ap.add_argument("--profile-solves", type=int, default=0,
+                    help="run this many solves and exit (the command ncu captures)")
     args = ap.parse_args()
+    if args.profile_solves:
+        run_profile_solves(args, args.workload)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
