@@ -67,7 +67,12 @@ typedef enum {
 enum { LRA_TRACE_GEPP = 0, LRA_TRACE_SWAP = 1, LRA_TRACE_STOP = 2, LRA_TRACE_CAP = 3 };
 
 /* lra_params.flags */
-enum { LRA_FLAG_PROFILE = 1 };   /* time every launch with CUDA events (lra_info.t_*_ms) */
+enum {
+  LRA_FLAG_PROFILE = 1,        /* time every launch with CUDA events (lra_info.t_*_ms)     */
+  LRA_FLAG_FULL_RESIDUAL = 2   /* also compute ||M - CUR||_F / ||M||_F over all m n entries
+                                  (LRA_DENSE_F32 sources with lda % 4 == 0 and a 16-byte
+                                  aligned base; tcgen05 tensor cores); lra_info.full_rel_err */
+};
 
 /* Job states (lra_info.state). */
 enum { LRA_STATE_RUNNING = 0, LRA_STATE_DONE = 1, LRA_STATE_FAILED = 2 };
@@ -131,6 +136,8 @@ typedef struct {
   double t_cross_ms;
   double t_resid_ms;
   double t_inverse_ms;        /* fresh cross inverses before warm-started steps     */
+  double full_rel_err;        /* LRA_FLAG_FULL_RESIDUAL: ||M - CUR||_F / ||M||_F (else -1) */
+  double t_fullres_ms;        /* with LRA_FLAG_PROFILE: full-residual kernels       */
 } lra_info;
 
 typedef struct {

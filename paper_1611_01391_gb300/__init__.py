@@ -31,6 +31,7 @@ LRA_DENSE_F32, LRA_DENSE_F64, LRA_GEN_CAUCHY, LRA_GEN_GAUSS, LRA_GEN_INVDIST = r
 LRA_TRACE_GEPP, LRA_TRACE_SWAP, LRA_TRACE_STOP, LRA_TRACE_CAP = range(4)
 LRA_STATE_RUNNING, LRA_STATE_DONE, LRA_STATE_FAILED = range(3)
 LRA_FLAG_PROFILE = 1
+LRA_FLAG_FULL_RESIDUAL = 2
 
 
 # ---- structs (layout of include/lra_cross.h) ------------------------------
@@ -67,7 +68,8 @@ class lra_info(ctypes.Structure):
                 ("maxvol_launches", ctypes.c_int32), ("maxvol_flops", ctypes.c_double),
                 ("t_gather_ms", ctypes.c_double), ("t_maxvol_ms", ctypes.c_double),
                 ("t_cross_ms", ctypes.c_double), ("t_resid_ms", ctypes.c_double),
-                ("t_inverse_ms", ctypes.c_double)]
+                ("t_inverse_ms", ctypes.c_double), ("full_rel_err", ctypes.c_double),
+                ("t_fullres_ms", ctypes.c_double)]
 
 
 class lra_cur_out(ctypes.Structure):

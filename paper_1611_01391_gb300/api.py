@@ -47,7 +47,7 @@ class _HostArrays:
 
 
 def make_params(k, l, sweeps, init_J, *, delta=1e-2, rank_tol=1e-6, tol=0.0, max_swaps=0,
-                resid_rows=None, resid_cols=None, trace_cap=0, profile=False):
+                resid_rows=None, resid_cols=None, trace_cap=0, profile=False, full_residual=False):
     """lra_params plus the host arrays it points to (keep both alive)."""
     J0 = np.ascontiguousarray(init_J, dtype=np.int32)
     rows = None if resid_rows is None else np.ascontiguousarray(resid_rows, dtype=np.int32)
@@ -60,7 +60,7 @@ def make_params(k, l, sweeps, init_J, *, delta=1e-2, rank_tol=1e-6, tol=0.0, max
         p.resid_q, p.resid_s = len(rows), len(cols)
         p.resid_rows, p.resid_cols = rows.ctypes.data, cols.ctypes.data
     p.trace_cap = trace_cap
-    p.flags = 1 if profile else 0
+    p.flags = (1 if profile else 0) | (2 if full_residual else 0)
     return p, _HostArrays(J0, rows, cols)
 
 

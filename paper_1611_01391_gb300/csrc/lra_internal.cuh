@@ -80,6 +80,7 @@ struct JobStatus {
   double est_rel, est_mu, est_var, est_sse, est_ssa;
   double sigma_max;
   double maxvol_flops;
+  double full_sse, full_ssa, full_rel;
 };
 
 struct GridBarrier {

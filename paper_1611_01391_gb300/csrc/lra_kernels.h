@@ -72,6 +72,13 @@ cudaError_t launch_sampled_residual(const SourceDev& s, const int* rows, int q,
                                     cudaStream_t st);
 int sampled_residual_partials(int q, int sN);
 
+// Full residual ||A - C U R||_F / ||A||_F of a stored FP32 matrix on the
+// tensor cores (tcgen05); ws holds fullres_workspace_bytes(m, n, l, grid_cap).
+size_t fullres_workspace_bytes(long long m, long long n, int l, int grid_cap);
+cudaError_t launch_full_residual(const float* A, long long lda, long long m, long long n, int l,
+                                 const float* C, const double* U, const float* R, void* ws,
+                                 int grid_cap, JobStatus* js, cudaStream_t st);
+
 // Small control kernels.
 cudaError_t launch_sweep_done(JobStatus* js, cudaStream_t st);
 cudaError_t launch_tol_check(JobStatus* js, double tol, cudaStream_t st);

@@ -40,10 +40,13 @@ struct Job {
   cudaEvent_t ev_start = nullptr, ev_end = nullptr;
   int launches = 0, maxvol_launches = 0;
   bool profile = false;
+  bool full_res = false;
+  void* fr_ws = nullptr;
   std::vector<std::pair<int, cudaEvent_t>> prof;  // (kernel class, event after the launch)
 };
 
-enum { kClsGather = 0, kClsMaxvol = 1, kClsCross = 2, kClsResid = 3, kClsInverse = 4, kClsOther = 5 };
+enum { kClsGather = 0, kClsMaxvol = 1, kClsCross = 2, kClsResid = 3, kClsInverse = 4, kClsFullres = 5,
+       kClsOther = 6 };
 
 // Sub-buffer offsets of one job's single device allocation.
 struct Layout {
@@ -111,6 +114,13 @@ lra_status validate(const lra_source* src, const lra_params* p, std::string* why
   }
   if (p->tol > 0.0 && p->resid_q == 0) { *why = "tol needs a residual sample"; return LRA_EINVAL; }
   if (p->trace_cap < 0) { *why = "trace_cap must be >= 0"; return LRA_EINVAL; }
+  if (p->flags & LRA_FLAG_FULL_RESIDUAL) {
+    if (src->kind != LRA_DENSE_F32 || src->lda % 4 != 0 ||
+        (reinterpret_cast<uintptr_t>(src->a) & 15) != 0) {
+      *why = "full residual needs a dense FP32 source with lda % 4 == 0 and a 16-byte aligned base";
+      return LRA_EINVAL;
+    }
+  }
   return LRA_OK;
 }
 
@@ -137,6 +147,8 @@ size_t layout_bytes(const lra_source* src, const lra_params* p, Job* j) {
   const size_t o_part = L.take(sizeof(double) * 3 * np);
   const size_t o_C = L.take(sizeof(float) * (size_t)src->m * l);
   const size_t o_R = L.take(sizeof(float) * (size_t)src->n * l);
+  const bool fr = (p->flags & LRA_FLAG_FULL_RESIDUAL) != 0;
+  const size_t o_fr = fr ? L.take(fullres_workspace_bytes(src->m, src->n, l, kMaxGrid)) : 0;
   if (j) {
     unsigned char* b = j->dmem;
     j->js = reinterpret_cast<JobStatus*>(b + o_js);
@@ -158,6 +170,7 @@ size_t layout_bytes(const lra_source* src, const lra_params* p, Job* j) {
     j->C = reinterpret_cast<float*>(b + o_C);
     j->R = reinterpret_cast<float*>(b + o_R);
     j->n_partials = np;
+    j->fr_ws = fr ? (void*)(b + o_fr) : nullptr;
   }
   return L.off;
 }
@@ -246,6 +259,11 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
   // final strips for the returned CUR: C = M[:, J] (R = M[I, :] is current)
   if ((e = launch_gather_cols(j->src, j->J, j->l, j->C, j->js, 0, ctx->sms, st)) || (e = after(kClsGather, 1))) return e;
   if ((e = launch_nucleus(j->C, j->I, j->l, j->k, j->rank_tol, j->U, j->sigma, j->js, st)) || (e = after(kClsCross, 1))) return e;
+  if (j->full_res) {
+    if ((e = launch_full_residual(static_cast<const float*>(j->src.a), j->src.lda, j->m, j->n, j->l, j->C,
+                                  j->U, j->R, j->fr_ws, std::min(ctx->sms, kMaxGrid), j->js, st)) ||
+        (e = after(kClsFullres, 5))) return e;
+  }
   if (j->q > 0) {
     if ((e = launch_sampled_residual(j->src, j->rows, (int)j->q, j->cols, (int)j->s, j->l, j->C, j->U,
                                      j->R, j->CUq, j->partials, j->n_partials, j->js, st)) ||
@@ -274,7 +292,7 @@ void fill_info(lra_ctx* ctx, Job* j, lra_info* out) {
   out->kernel_launches = j->launches;
   out->maxvol_launches = j->maxvol_launches;
   out->maxvol_flops = h.maxvol_flops;
-  double t[6] = {0, 0, 0, 0, 0, 0};
+  double t[7] = {0, 0, 0, 0, 0, 0, 0};
   cudaEvent_t prev = j->ev_start;
   for (auto& pe : j->prof) {
     float d = 0.0f;
@@ -286,6 +304,8 @@ void fill_info(lra_ctx* ctx, Job* j, lra_info* out) {
   out->t_cross_ms = t[kClsCross];
   out->t_resid_ms = t[kClsResid];
   out->t_inverse_ms = t[kClsInverse];
+  out->t_fullres_ms = t[kClsFullres];
+  out->full_rel_err = j->full_res ? h.full_rel : -1.0;
 }
 
 Job* find_job(lra_ctx* ctx, lra_job id) {
@@ -395,6 +415,7 @@ lra_status lra_cross_submit(lra_ctx* ctx, const lra_source* src, const lra_param
   j->max_swaps = p->max_swaps > 0 ? p->max_swaps : 64 * p->l;
   j->trace_cap = p->trace_cap;
   j->profile = (p->flags & LRA_FLAG_PROFILE) != 0;
+  j->full_res = (p->flags & LRA_FLAG_FULL_RESIDUAL) != 0;
   j->m = src->m; j->n = src->n; j->q = p->resid_q; j->s = p->resid_s;
   j->delta = p->delta; j->rank_tol = p->rank_tol; j->tol = p->tol;
   j->src.kind = src->kind;
