@@ -37,6 +37,9 @@ WORKLOADS = {
     "cauchy65536": dict(kind="cauchy", m=65536, n=65536, k=16, l=24, sweeps=4, q=1000, s=1000,
                         seed_off=2),
     "dense256": dict(kind="dense64", m=256, n=256, k=8, l=8, sweeps=3, q=256, s=256, seed_off=1),
+    # stored FP32 32768^2 = G1 G2^T / 8 + N(0, 1e-4^2), full residual on the tensor cores
+    "dense32768": dict(kind="dense32", m=32768, n=32768, k=64, l=96, sweeps=4, q=1000, s=1000,
+                       seed_off=3, full=True),
 }
 
 
@@ -72,7 +75,8 @@ def make_inputs(wl, rank=0):
     if wl["kind"] == "cauchy":
         inp["x"], inp["y"] = W.cauchy_points(seed, m, n)
     else:
-        inp["a"] = W.lowrank_svd(seed, m, n, r=8, noise_std=1e-4)
+        inp["a"] = (W.factor_gaussian(seed, m, n, 64, 1e-4) if wl["kind"] == "dense32"
+                    else W.lowrank_svd(seed, m, n, r=8, noise_std=1e-4))
     return inp
 
 
@@ -207,7 +211,8 @@ def run_ours(args, wl_name):
         ad = torch.from_numpy(inp["a"]).to(dev)
         src = L.make_source("dense", a=ad)
     params, keep = L.make_params(k, l, sweeps, inp["J0"], resid_rows=inp["rows"],
-                                 resid_cols=inp["cols"], profile=True)
+                                 resid_cols=inp["cols"], profile=True,
+                                 full_residual=wl.get("full", False))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def one_step():
@@ -292,6 +297,24 @@ def run_ours(args, wl_name):
                 ts.append(t1 - t0)
         e2e = {"value": len(ts) / sum(ts) * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
+    else:
+        ah = torch.from_numpy(inp["a"]).pin_memory()
+        ad2 = torch.empty_like(ad)
+        src2 = L.make_source("dense", a=ad2)
+        h2d = ah.numel() * ah.element_size() + 4 * (l + wl["q"] + wl["s"])
+        d2h = 4 * 2 * l + 8 * l * l + 8 * l + 144
+        ts = []
+        for it in range(min(args.warmup, 1) + args.steps):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            ad2.copy_(ah, non_blocking=True)
+            r2 = ctx.fetch(ctx.submit(src2, params), l)
+            assert r2.info.status == 0
+            t1 = time.perf_counter()
+            if it >= min(args.warmup, 1):
+                ts.append(t1 - t0)
+        e2e = {"value": len(ts) / sum(ts) * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
 
     lat = sorted(step_ms)
     line = {
@@ -312,15 +335,26 @@ def run_ours(args, wl_name):
                                "nucleus": t_x / len(infos), "resid": t_r / len(infos)},
         "roofline": {"kernel": "maxvol_kernel", "bound": "alu", "achieved": achieved,
                      "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak if fp64_peak else None,
-                     "traffic": captured_traffic("k_maxvol.cu", "maxvol_cauchy65536.md"),
+                     "traffic": captured_traffic("k_maxvol.cu", f"maxvol_{wl_name}.md"),
                      "traffic_note": "DRAM bytes per maxvol launch from the committed ncu capture (null if the kernel changed since)",
                      "peak_source": f"FP64 FMA rate: {SMS} SMs x {FP64_FMA_PER_SM_CLK} FMA/clk x median SM clock {sm_mhz:.0f} MHz"},
         "gpu_launches": int(sum(i.kernel_launches for i in infos)),
         "clocks": clk,
         "e2e": e2e,
         "swaps_per_solve": statistics.mean(i.swaps_total for i in infos),
+        "full_rel_err": infos[-1].full_rel_err,
         "est_rel_err": infos[-1].est_rel_err,
     }
+    if wl.get("full"):
+        t_fr = sum(i.t_fullres_ms for i in infos) / len(infos)
+        gbs = m * n * 4 / (t_fr / 1e3) / 1e9 if t_fr > 0 else 0.0
+        line["kernel_ms_per_step"]["full_residual"] = t_fr
+        line["roofline_full_residual"] = {
+            "kernel": "fullres_kernel (+ operand split kernels)", "bound": "hbm", "achieved": gbs,
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+            "traffic": captured_traffic("k_fullres.cu", f"fullres_{wl_name}.md"),
+            "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+            "algorithmic_bytes": m * n * 4}
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
@@ -355,7 +389,7 @@ def run_profile_solves(args, wl_name):
         ad = torch.from_numpy(inp["a"]).cuda()
         src = L.make_source("dense", a=ad)
     params, keep = L.make_params(wl["k"], wl["l"], wl["sweeps"], inp["J0"], resid_rows=inp["rows"],
-                                 resid_cols=inp["cols"])
+                                 resid_cols=inp["cols"], full_residual=wl.get("full", False))
     for _ in range(args.profile_solves):
         res = ctx.fetch(ctx.submit(src, params), wl["l"])
         if res.info.status != 0:

@@ -274,3 +274,31 @@ def test_repeat_is_bit_identical(ctx):
     assert np.array_equal(a.I, b.I) and np.array_equal(a.J, b.J)
     assert np.array_equal(a.U, b.U)
     assert a.info.est_rel_err == b.info.est_rel_err
+
+
+# ---------------------------------------------------------------------------
+# Stored FP32 32768 x 32768 (the benchmark's stored workload, same bytes):
+# decision log, index sets and the tensor-core full residual against FP64
+# ---------------------------------------------------------------------------
+
+def test_dense_32768_full_size_parity(ctx):
+    import bench
+    wl = bench.WORKLOADS["dense32768"]
+    inp = bench.make_inputs(wl, 0)
+    A = inp["a"]
+    m, n, k, l, sw = wl["m"], wl["n"], wl["k"], wl["l"], wl["sweeps"]
+    params, keep = L.make_params(k, l, sw, inp["J0"], trace_cap=8192, full_residual=True,
+                                 resid_rows=inp["rows"], resid_cols=inp["cols"])
+    res = ctx.solve(L.make_source("dense", a=torch.from_numpy(A).to(DEV)), params, l, m, n,
+                    want_strips=True, trace_cap=8192, device=DEV)
+    assert res.info.status == 0
+    ref = O.cross_approximation(O.Dense(A), inp["J0"], k=k, sweeps=sw, delta=DELTA)
+    ncmp, div = compare_traces(res.trace, ref.trace, DELTA)
+    assert ncmp >= l
+    if div is None:
+        assert list(res.I) == ref.I and list(res.J) == ref.J
+    C, R = res.C.cpu().numpy(), res.R.cpu().numpy()
+    full64 = O.full_residual(O.Dense(A), C.astype(np.float64), res.U, R.astype(np.float64))[0]
+    assert res.info.full_rel_err == pytest.approx(full64, rel=2e-3)
+    err_ref = O.full_residual(O.Dense(A), ref.C, ref.U, ref.R)[0]
+    assert error_ok(res.info.full_rel_err, err_ref)
