@@ -40,6 +40,14 @@ WORKLOADS = {
     # stored FP32 32768^2 = G1 G2^T / 8 + N(0, 1e-4^2), full residual on the tensor cores
     "dense32768": dict(kind="dense32", m=32768, n=32768, k=64, l=96, sweeps=4, q=1000, s=1000,
                        seed_off=3, full=True),
+    # 4096 far-field blocks of 1/|x - y| over 2^20 points (octree, leaf <= 2048),
+    # rank-adaptive to 1e-6 with k <= 64, one persistent launch
+    "octree4096": dict(form="batch", npoints=1 << 20, leaf=2048, n_pairs=4096, l_init=16, l_max=96,
+                       k_max=64, sweeps=2, tol=1e-6, q=32, seed_off=4, plain_subset=256),
+    # Poisson stream of requests: sides log-uniform in 256..16384, k in {8,16,32,64},
+    # Cauchy / Gaussian / 1/|x - y| generators, 40 GB admission budget
+    "serve": dict(form="serve", count=400, min_side=256, max_side=16384, budget_gb=40, slots=64,
+                  streams=8, rates=(0.5, 0.8, 0.95), seed_off=5, plain_subset=400),
 }
 
 
@@ -166,10 +174,65 @@ print(json.dumps({{"n": n, "total_s": sum(times), "times": times}}))
 """
 
 
+CPU_BATCH_SNIPPET = r"""
+import os, sys, time, json
+sys.path.insert(0, {root!r})
+import numpy as np
+import oracle as O
+from bench import WORKLOADS, make_batch_inputs
+wl = WORKLOADS[{wl!r}]
+pts, blocks, jc, sr, sc = make_batch_inputs(wl)
+s64 = O.InvDist(pts, pts, "fp64")
+class Sub:
+    def __init__(s, r0, m, c0, n): s.r0, s.m, s.c0, s.n = r0, m, c0, n
+    def block(s, rows, cols): return s64.block(s.r0 + np.asarray(rows), s.c0 + np.asarray(cols))
+order = np.random.default_rng(0).permutation(len(blocks))   # unbiased sample of block sizes
+t0 = time.perf_counter(); n = 0; times = []
+for b in order:
+    r0, m, c0, n_ = (int(v) for v in blocks[b])
+    t1 = time.perf_counter()
+    sub = Sub(r0, m, c0, n_)
+    I, J, U, ke, sg, l, sw = O.cross_approximation_adaptive(sub, jc[b], wl["l_init"], wl["l_max"], wl["k_max"],
+                                                            wl["sweeps"], wl["tol"])
+    O.sampled_residual(sub, sub.block(sr[b], J), U, sub.block(I, sc[b]), sr[b], sc[b])
+    times.append(time.perf_counter() - t1); n += 1
+    if (time.perf_counter() - t0 > {budget} and n >= {min_n}) or n >= {max_n}:
+        break
+print(json.dumps({{"n": n, "total_s": sum(times), "times": times}}))
+"""
+
+CPU_SERVE_SNIPPET = r"""
+import os, sys, time, json
+sys.path.insert(0, {root!r})
+import numpy as np
+import oracle as O, workloads as W
+from bench import WORKLOADS
+wl = WORKLOADS[{wl!r}]
+reqs = W.serving_requests(W.BASE_SEED + wl["seed_off"], wl["count"], wl["min_side"], wl["max_side"])
+t0 = time.perf_counter(); n = 0; times = []
+for r in reqs:
+    t1 = time.perf_counter()
+    if r["kind"] == "cauchy":
+        src = O.Cauchy(r["x"], r["y"], "fp64")
+    elif r["kind"] == "gauss":
+        src = O.Gauss(r["x"], r["y"], r["h"], "fp64")
+    else:
+        src = O.InvDist(r["x"], r["y"], "fp64")
+    O.cross_approximation(src, r["J0"], k=r["k"], sweeps=r["sweeps"], sample_rows=r["rows"],
+                          sample_cols=r["cols"], keep_trace=False)
+    times.append(time.perf_counter() - t1); n += 1
+    if (time.perf_counter() - t0 > {budget} and n >= {min_n}) or n >= {max_n}:
+        break
+print(json.dumps({{"n": n, "total_s": sum(times), "times": times}}))
+"""
+
+
 def run_oracle(wl_name, budget_s=12.0, min_n=1, max_n=1000):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    code = CPU_SNIPPET.format(root=ROOT, wl=wl_name, budget=budget_s, min_n=min_n, max_n=max_n)
+    form = WORKLOADS[wl_name].get("form", "plain")
+    snippet = {"plain": CPU_SNIPPET, "batch": CPU_BATCH_SNIPPET, "serve": CPU_SERVE_SNIPPET}[form]
+    code = snippet.format(root=ROOT, wl=wl_name, budget=budget_s, min_n=min_n, max_n=max_n)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
                        timeout=900)
     if r.returncode != 0:
@@ -371,6 +434,332 @@ def run_ours(args, wl_name):
         print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# batched form: many far-field blocks in one persistent launch
+# ---------------------------------------------------------------------------
+
+def make_batch_inputs(wl):
+    import workloads as W
+    seed = W.BASE_SEED + wl["seed_off"]
+    pts, blocks = W.octree_block_pairs(seed, npoints=wl["npoints"], leaf=wl["leaf"],
+                                       n_pairs=wl["n_pairs"])
+    jc, sr, sc = W.block_candidates(seed + 1, blocks, wl["l_max"], wl["q"])
+    return pts, blocks, jc, sr, sc
+
+
+def fp32_peak_tflops(sm_mhz):
+    # 128 FP32 FMA lanes per SM per clock
+    return SMS * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def run_batch(args, wl_name):
+    import numpy as np
+    import torch
+    import paper_1611_01391_gb300 as L
+    from paper_1611_01391_gb300.api import _batch_fetch, make_batch_params
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = WORKLOADS[wl_name]
+    pts, blocks, jc, sr, sc = make_batch_inputs(wl)
+    nb = len(blocks)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = L.Context(local, stream=stream.cuda_stream)
+    d = torch.from_numpy(pts).to(dev)
+    src = L.make_source("invdist", x=d, y=d)
+    p, keep = make_batch_params(wl["l_init"], wl["l_max"], wl["k_max"], wl["sweeps"], wl["tol"], jc, sr, sc)
+    blocks64 = np.ascontiguousarray(blocks, dtype=np.int64)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        return L.lra_cross_submit_batch(ctx.ctx, src, blocks64, p)
+
+    for _ in range(args.warmup):
+        r = _batch_fetch(ctx.ctx, step(), nb, wl["l_max"])
+        assert np.all(r.status == 0), np.unique(r.status)
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.3)
+    evs, res = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        job = step()
+        b.record(stream)
+        evs.append((a, b))
+        res.append(_batch_fetch(ctx.ctx, job, nb, wl["l_max"]))
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    step_ms = [x.elapsed_time(y) for x, y in evs]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    r = res[-1]
+    assert np.all(r.status == 0)
+    value = world * nb * args.steps / (total_ms / 1e3)
+    kern_ms = statistics.mean(x.info.gpu_ms for x in res)
+    flops = statistics.mean(x.info.maxvol_flops for x in res)
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    fp32_peak = fp32_peak_tflops(sm_mhz)
+    achieved = flops / (kern_ms / 1e3) / 1e12
+
+    # plain one-job-per-launch C-A on a subset of the same blocks, each at the
+    # batch's final cross size and rank rule, queued back to back on the stream
+    sub = np.linspace(0, nb - 1, min(wl["plain_subset"], nb)).astype(int)
+    plain_src, plain_par, hold = [], [], []
+    for b in sub:
+        r0, m, c0, n = (int(v) for v in blocks[b])
+        lb = int(r.l[b])
+        xs, ys = d[r0:r0 + m], d[c0:c0 + n]
+        plain_src.append(L.make_source("invdist", x=xs, y=ys))
+        pp, kk = L.make_params(min(wl["k_max"], lb), lb, wl["sweeps"], jc[b, :lb], rank_tol=wl["tol"],
+                               resid_rows=sr[b], resid_cols=sc[b])
+        plain_par.append(pp)
+        hold.append((xs, ys, kk))
+    plain_err = []
+    for rep in range(2):             # first pass warms up
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b_ = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        jobs = [ctx.submit(s_, p_) for s_, p_ in zip(plain_src, plain_par)]
+        b_.record(stream)
+        outs = [ctx.fetch(j, int(r.l[b])) for j, b in zip(jobs, sub)]
+        plain_ms = a.elapsed_time(b_)
+        plain_err = [o.info.est_rel_err for o in outs]
+        assert all(o.info.status == 0 for o in outs)
+    plain_value = len(sub) / (plain_ms / 1e3)
+
+    # end to end: points from pinned host memory, results back to the host
+    ph = torch.from_numpy(pts).pin_memory()
+    d2 = torch.empty_like(d)
+    src2 = L.make_source("invdist", x=d2, y=d2)
+    ts = []
+    for it in range(1 + args.steps):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        d2.copy_(ph, non_blocking=True)
+        r2 = _batch_fetch(ctx.ctx, L.lra_cross_submit_batch(ctx.ctx, src2, blocks64, p), nb, wl["l_max"])
+        t1 = time.perf_counter()
+        assert np.all(r2.status == 0)
+        if it >= 1:
+            ts.append(t1 - t0)
+    lm = wl["l_max"]
+    h2d = pts.nbytes + blocks64.nbytes + jc.nbytes + sr.nbytes + sc.nbytes
+    d2h = nb * (4 * 4 + 2 * 4 * lm + 8 * lm * lm + 4 * lm + 8)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    lat = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": wl_name, "generator": "invdist 1/|x-y|", "points": wl["npoints"],
+                   "leaf": wl["leaf"], "blocks": nb,
+                   "block_sides": [int(blocks[:, [1, 3]].min()), int(blocks[:, [1, 3]].max())],
+                   "l_init": wl["l_init"], "l_max": wl["l_max"], "k_max": wl["k_max"], "tol": wl["tol"],
+                   "sweeps": wl["sweeps"], "error_sample": f"{wl['q']}x{wl['q']} per block",
+                   "precision": "FP32 entries, strips and maxvol; double-float Jacobi nucleus, FP64 U",
+                   "l2": "flushed before every step (256 MiB write)", "parallelism": f"replicas{world}"},
+        "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+        "plain_one_job_per_launch": {
+            "value": plain_value, "unit": "blocks/s", "blocks": int(len(sub)),
+            "est_rel_err_max": float(max(plain_err)), "est_rel_err_mean": float(np.mean(plain_err)),
+            "note": "same blocks, each a separate C-A job at the batch's final l, queued back to back"},
+        "speedup_vs_plain": value / plain_value,
+        "est_rel_err_max": float(r.est_err.max()), "est_rel_err_mean": float(r.est_err.mean()),
+        "est_rel_err_max_subset": float(r.est_err[sub].max()),
+        "l_hist": {str(k): int(v) for k, v in zip(*np.unique(r.l, return_counts=True))},
+        "k_eff_mean": float(r.k_eff.mean()),
+        "roofline": {"kernel": "batch_kernel", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                     "peak_source": f"FP32 FMA rate: {SMS} SMs x 128 FMA/clk x median SM clock {sm_mhz:.0f} MHz",
+                     "note": "elimination/update FLOPs counted by the kernel; the decision chain (one cluster barrier per pivot) bounds it"},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "e2e": {"value": nb * len(ts) / sum(ts), "unit": "blocks/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+    }
+    if world == 1:
+        try:
+            ob = run_oracle(wl_name)
+            line["cpu_baseline"] = {"value": ob["n"] / ob["total_s"], "unit": "blocks/s", "cores": 1,
+                                    "kind": "oracle",
+                                    "sample": f"{ob['n']} block(s) of the same set, FP64 numpy rank-adaptive C-A, 1 thread"}
+        except Exception as e:  # report, do not hide
+            line["cpu_baseline"] = {"value": None, "unit": "blocks/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"failed: {e}"}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# served form: a Poisson stream of independent requests, continuous batching
+# ---------------------------------------------------------------------------
+
+def _serve_prepare(L, torch, reqs, dev):
+    out = []
+    for r in reqs:
+        xd = torch.from_numpy(r["x"]).to(dev)
+        yd = torch.from_numpy(r["y"]).to(dev)
+        src = L.make_source(r["kind"], x=xd, y=yd, h=r["h"])
+        p, keep = L.make_params(r["k"], r["l"], r["sweeps"], r["J0"], resid_rows=r["rows"],
+                                resid_cols=r["cols"])
+        out.append((src, p, (xd, yd, keep)))
+    return out
+
+
+def _serve_run(L, ctx, prep, reqs, arrivals, launches):
+    """Open loop over arrival times (None: all at t = 0, closed loop).
+    Submits each request once it has arrived and admission succeeds, polls
+    the in-flight jobs, fetches finished ones.  Returns (makespan s,
+    latencies s, est errors)."""
+    n = len(prep)
+    pending = 0                       # next request not yet submitted
+    inflight = {}                     # job -> request index
+    lat = [None] * n
+    errs = [None] * n
+    t0 = time.perf_counter()
+    arr = [0.0] * n if arrivals is None else list(arrivals)
+    done = 0
+    while done < n:
+        now = time.perf_counter() - t0
+        while pending < n and arr[pending] <= now:
+            try:
+                j = ctx.submit(prep[pending][0], prep[pending][1])
+            except L.LraError as e:
+                if e.code != L.LRA_EBUSY:
+                    raise
+                break                 # admission full: retry after completions
+            inflight[j] = pending
+            pending += 1
+        for j in list(inflight):
+            code, info = L.lra_cross_poll(ctx.ctx, j)
+            if code == L.LRA_OK:
+                i = inflight.pop(j)
+                lat[i] = time.perf_counter() - t0 - arr[i]
+                res = ctx.fetch(j, reqs[i]["l"])
+                if res.info.status != 0:
+                    raise RuntimeError(f"request {i}: {L.lra_status_str(res.info.status)}")
+                errs[i] = res.info.est_rel_err
+                launches[0] += res.info.kernel_launches
+                done += 1
+    return time.perf_counter() - t0, lat, errs
+
+
+def _pct(xs, q):
+    s = sorted(xs)
+    return s[min(len(s) - 1, max(0, int(math.ceil(q * len(s))) - 1))]
+
+
+def run_serve(args, wl_name):
+    import numpy as np
+    import torch
+    import paper_1611_01391_gb300 as L
+    import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = WORKLOADS[wl_name]
+    seed = W.BASE_SEED + wl["seed_off"] + 1000 * rank
+    reqs = W.serving_requests(seed, wl["count"], wl["min_side"], wl["max_side"])
+    prep = _serve_prepare(L, torch, reqs, dev)
+    budget = int(wl["budget_gb"] * (1 << 30))
+    ctx = L.Context(local, max_slots=wl["slots"], mem_budget_bytes=budget, n_streams=wl["streams"])
+    # warm-up: every request once on the served path
+    for _ in range(max(1, args.warmup // 3)):
+        _serve_run(L, ctx, prep, reqs, None, [0])
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.3)
+    # capacity: closed loop (everything queued at t = 0), K repetitions
+    caps, cap_lat = [], []
+    launches = [0]
+    for _ in range(args.steps):
+        mk, lat, errs = _serve_run(L, ctx, prep, reqs, None, launches)
+        caps.append(mk)
+        cap_lat += lat
+    capacity = len(prep) / statistics.median(caps)
+    # open loop at fractions of the measured capacity
+    sweep = []
+    for frac in wl["rates"]:
+        rate = frac * capacity
+        arr = W.poisson_arrivals(seed + int(1000 * frac), len(prep), rate)
+        mk, lat, errs_o = _serve_run(L, ctx, prep, reqs, arr, [0])
+        sweep.append({"offered_per_s": rate, "fraction_of_capacity": frac, "solves_per_s": len(prep) / mk,
+                      "p50_ms": 1e3 * _pct(lat, 0.5), "p99_ms": 1e3 * _pct(lat, 0.99)})
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    # plain: one job at a time on one stream, submit -> wait -> fetch
+    ctx1 = L.Context(local, n_streams=1)
+    sub = list(range(min(wl["plain_subset"], len(prep))))
+    for i in sub[:8]:
+        ctx1.fetch(ctx1.submit(prep[i][0], prep[i][1]), reqs[i]["l"])
+    t0 = time.perf_counter()
+    plain_lat, plain_err = [], []
+    for i in sub:
+        t1 = time.perf_counter()
+        res = ctx1.fetch(ctx1.submit(prep[i][0], prep[i][1]), reqs[i]["l"])
+        plain_lat.append(time.perf_counter() - t1)
+        plain_err.append(res.info.est_rel_err)
+    plain_value = len(sub) / (time.perf_counter() - t0)
+    ctx1.close()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    h2d = sum(r["x"].nbytes + r["y"].nbytes + 4 * (r["l"] + len(r["rows"]) + len(r["cols"])) for r in reqs)
+    d2h = sum(4 * 2 * r["l"] + 8 * r["l"] * r["l"] + 8 * r["l"] + 144 for r in reqs)
+    line = {
+        "metric": METRIC, "value": world * capacity, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(caps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl_name, "requests": len(prep), "sides": [wl["min_side"], wl["max_side"]],
+                   "k": [8, 16, 32, 64], "generators": ["cauchy", "gauss h=0.5", "invdist"],
+                   "admission_budget_gb": wl["budget_gb"], "slots": wl["slots"], "streams": wl["streams"],
+                   "timing": "host wall clock from first submit to last fetch (serving latency)",
+                   "l2": "inputs resident; requests run back to back (L2 not flushed between them)",
+                   "parallelism": f"replicas{world}"},
+        "p50_ms": 1e3 * _pct(cap_lat, 0.5), "p99_ms": 1e3 * _pct(cap_lat, 0.99),
+        "rate_sweep": sweep,
+        "plain_one_job_per_launch": {"value": plain_value, "unit": "solves/s",
+                                     "p50_ms": 1e3 * _pct(plain_lat, 0.5), "p99_ms": 1e3 * _pct(plain_lat, 0.99),
+                                     "est_rel_err_max": float(max(plain_err)),
+                                     "note": "same requests one at a time on one stream"},
+        "speedup_vs_plain": capacity / plain_value,
+        "est_rel_err_max": float(max(errs)),
+        "gpu_launches": int(launches[0]),
+        "clocks": clk,
+        "e2e": {"value": world * capacity, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h),
+                "note": "inputs resident on the device; results fetched to the host inside the timed loop"},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_profile_solves(args, wl_name):
     """N solves of the workload and nothing else: the command that ncu
     captures (launch list, per-kernel counters)."""
@@ -414,24 +803,32 @@ def captured_traffic(kernel_file, summary):
 
 
 def run_reference(args, wl_name):
+    """The FP64 CPU oracle as it stands, on this arm's workload.  A step is
+    one solve (plain), 8 blocks (batch) or 2 requests (serve)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     wl = WORKLOADS[wl_name]
-    total = args.warmup + args.steps
+    form = wl.get("form", "plain")
+    per_step = {"plain": 1, "batch": 8, "serve": 2}[form]
+    unit = "blocks/s" if form == "batch" else UNIT
+    total = (args.warmup + args.steps) * per_step
     ob = run_oracle(wl_name, budget_s=1e9, min_n=total, max_n=total)
-    times = ob["times"][args.warmup:]
+    times = ob["times"][args.warmup * per_step:]
     value = len(times) / sum(times)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+    if form == "plain":
+        cfg = {"workload": wl_name, "generator": wl["kind"], "m": wl["m"], "n": wl["n"], "k": wl["k"],
+               "l": wl["l"], "sweeps": wl["sweeps"], "error_sample": f"{wl['q']}x{wl['s']}"}
+    else:
+        cfg = {"workload": wl_name, **{k: v for k, v in wl.items() if k not in ("form", "seed_off")}}
+    line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times) * per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "impl": "reference",
-            "config": {"workload": wl_name, "generator": wl["kind"], "m": wl["m"], "n": wl["n"],
-                       "k": wl["k"], "l": wl["l"], "sweeps": wl["sweeps"],
-                       "error_sample": f"{wl['q']}x{wl['s']}"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{len(times)} full solve(s) per timed run, FP64 numpy, 1 thread"},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "data": "synthetic", "impl": "reference", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
+                             "sample": f"{len(times)} unit(s) ({per_step} per step) per timed run, FP64 numpy, 1 thread"},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -450,8 +847,13 @@ def main():
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    form = WORKLOADS[args.workload].get("form", "plain")
     if args.impl == "reference":
         run_reference(args, args.workload)
+    elif form == "batch":
+        run_batch(args, args.workload)
+    elif form == "serve":
+        run_serve(args, args.workload)
     else:
         run_ours(args, args.workload)
 

@@ -84,7 +84,10 @@ typedef struct {
   int32_t device;             /* CUDA device ordinal                                */
   int32_t max_slots;          /* max jobs held at once (<= 0: 64)                   */
   uint64_t mem_budget_bytes;  /* device-memory admission budget (0: unlimited)      */
-  void* stream;               /* cudaStream_t to run on, or NULL for an own stream  */
+  void* stream;               /* cudaStream_t to run every job on, or NULL: own streams */
+  int32_t n_streams;          /* own streams (1..32; <= 0: 1).  A job runs on the
+                                 least loaded one, so jobs submitted while others
+                                 run overlap on the device (continuous admission). */
 } lra_ctx_params;
 
 typedef struct {
@@ -151,6 +154,65 @@ typedef struct {
   int32_t* trace;             /* 4 ints per decision: half_step, kind, i, j (nullable) */
   double* trace_val;          /* 1 double per decision: winning |value| (nullable)  */
 } lra_cur_out;
+
+/* ---- Batched form: many blocks of one source in one launch --------------
+ * Section 9 (superfast multipole method): the generators of the neutered
+ * block columns / far-field blocks are low-rank approximations of many
+ * submatrices of one matrix, computed here by C-A iterations (Section 6.5)
+ * with the rank chosen per block.  Block b is the submatrix
+ * M[row0 : row0 + m, col0 : col0 + n] of the source (1 <= m, n <= 2048).
+ *
+ * Per block (reading of the paper for blocks of unknown rank):
+ *   - every strip starts from Gaussian elimination with partial pivoting and
+ *     then runs maxvol swaps (FP32);
+ *   - after `sweeps` sweeps, if the last pivot of the final vertical step
+ *     exceeds tol x the first pivot, the cross grows (x2, <= l_max) with the
+ *     next unused columns of cand_J and the sweeps repeat;
+ *   - nucleus U = (X_k)^+ with k_eff = min(k_max, #{sigma_j > tol sigma_1});
+ *   - Appendix F estimate on the sample rows x sample columns of the block. */
+typedef struct {
+  int64_t row0, m;            /* rows of M in the block                             */
+  int64_t col0, n;            /* columns of M in the block                          */
+} lra_block;
+
+typedef struct {
+  int32_t l_init;             /* first cross size (1..l_max)                        */
+  int32_t l_max;              /* largest cross size (<= 96)                         */
+  int32_t k_max;              /* largest kept rank (<= l_max)                       */
+  int32_t sweeps;             /* sweeps per cross size (>= 1)                       */
+  int32_t max_swaps;          /* maxvol swap cap per strip (<= 0: 64 l)             */
+  int32_t sample;             /* q: q x q sampled entries per block (0..64)         */
+  double tol;                 /* rank tolerance (relative)                          */
+  double delta;               /* maxvol stops when max |B| <= 1 + delta             */
+  const int32_t* cand_J;      /* host, n_blocks x l_max distinct local columns      */
+  const int32_t* sample_rows; /* host, n_blocks x q local rows (nullable if q = 0)  */
+  const int32_t* sample_cols; /* host, n_blocks x q local columns                   */
+  int32_t flags;              /* reserved, 0                                        */
+} lra_batch_params;
+
+typedef struct {
+  int32_t on_device;          /* 1: the pointers below are device pointers          */
+  int32_t* status;            /* n_blocks lra_status values                         */
+  int32_t* l;                 /* n_blocks final cross sizes                         */
+  int32_t* k_eff;             /* n_blocks kept ranks                                */
+  int32_t* swaps;             /* n_blocks maxvol swaps                              */
+  int32_t* I;                 /* n_blocks x l_max local rows (-1 past l)            */
+  int32_t* J;                 /* n_blocks x l_max local columns (-1 past l)         */
+  double* U;                  /* n_blocks x l_max x l_max, the l x l nucleus row-major
+                                 in the leading part of each block's slot (nullable);
+                                 FP64: with cond(X_k) up to 1/tol an FP32 nucleus
+                                 would dominate the error of C U R              */
+  float* sigma;               /* n_blocks x l_max singular values of the cross (nullable) */
+  double* est_err;            /* n_blocks Appendix F estimates (nullable)           */
+} lra_batch_out;
+
+/* Validate and enqueue one persistent launch over all blocks (LRA_EBUSY when
+ * admission fails).  Poll / wait / cancel work on the returned job. */
+lra_status lra_cross_submit_batch(lra_ctx* ctx, const lra_source* src, const lra_block* blocks,
+                                  int32_t n_blocks, const lra_batch_params* params, lra_job* out);
+
+/* Copy the per-block results of a finished batch job, then release it. */
+lra_status lra_cross_fetch_batch(lra_ctx* ctx, lra_job job, const lra_batch_out* out);
 
 /* Create a context on params->device.  *out receives the handle. */
 lra_status lra_cross_create(lra_ctx** out, const lra_ctx_params* params);

@@ -159,7 +159,7 @@ def _runner_up(values, winner):
     return float(rest.max())
 
 
-def gepp_rows(S, trace=None, half_step=0):
+def gepp_rows(S, trace=None, half_step=0, pivots=None):
     """Pivot rows of Gaussian elimination with partial pivoting on the N x l
     strip S: at step t take the free row of largest |entry| in column t of
     the Schur complement (smallest row on ties), then eliminate column t from
@@ -179,6 +179,8 @@ def gepp_rows(S, trace=None, half_step=0):
             trace.append((half_step, GEPP, p, t, v1, v2))
         if not v1 > 0.0:
             raise OracleSingular(f"zero pivot in column {t}")
+        if pivots is not None:
+            pivots.append(v1)
         piv.append(p)
         free[p] = False
         mult = W[free, t] / W[p, t]
@@ -358,6 +360,46 @@ def cross_approximation(src, J0, k, sweeps, delta=1e-2, rank_tol=1e-6,
                        sweeps_done=done, swaps=swaps, converged=converged,
                        trace=trace if trace is not None else [],
                        history=history, estimate=estimate)
+
+
+def cross_approximation_adaptive(src, J_cands, l_init, l_max, k_max, sweeps, tol,
+                                 delta=1e-2, max_swaps=None, growth=2.0):
+    """Rank-adaptive C-A for many small blocks (the reading used for the
+    far-field blocks of Section 9, whose ranks are not known in advance).
+
+    Every strip, not only the first, starts from the rows chosen by Gaussian
+    elimination with partial pivoting and then runs maxvol (Section 6.5 lets
+    each C-A step compute its generator by any algorithm).  After ``sweeps``
+    sweeps, if the last GEPP pivot of the final vertical step still exceeds
+    tol times the first one, the cross grows to min(l_max, growth l) by
+    appending the next unused candidate columns to J, and the sweeps repeat.
+    The nucleus keeps k_eff = min(k_max, #{sigma_j > tol sigma_1}).
+
+    Returns (I, J, U, k_eff, sigma, l, swaps)."""
+    J_cands = [int(j) for j in J_cands]
+    l = l_init
+    J = J_cands[:l]
+    swaps = 0
+    while True:
+        for s in range(sweeps):
+            C = columns(src, J)
+            piv = []
+            res = maxvol(C, gepp_rows(C, pivots=piv), delta, max_swaps)
+            I = res.I
+            swaps += res.swaps
+            Rt = rows(src, I).T
+            res = maxvol(Rt, gepp_rows(Rt), delta, max_swaps)
+            J = res.I
+            swaps += res.swaps
+        if l < l_max and piv[-1] > tol * piv[0]:
+            l_new = min(l_max, int(growth * l))
+            extra = [j for j in J_cands if j not in J][: l_new - l]
+            J = J + extra
+            l = len(J)
+            continue
+        break
+    U, k_eff, sigma = nucleus(src.block(I, J), k_max, tol)
+    return I, J, U, k_eff, sigma, l, swaps
 
 
 def random_cross(src, I, J, k=None, rank_tol=0.0):

@@ -37,7 +37,8 @@ LRA_FLAG_FULL_RESIDUAL = 2
 # ---- structs (layout of include/lra_cross.h) ------------------------------
 class lra_ctx_params(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("max_slots", ctypes.c_int32),
-                ("mem_budget_bytes", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
+                ("mem_budget_bytes", ctypes.c_uint64), ("stream", ctypes.c_void_p),
+                ("n_streams", ctypes.c_int32)]
 
 
 class lra_source(ctypes.Structure):
@@ -78,6 +79,26 @@ class lra_cur_out(ctypes.Structure):
                 ("R", ctypes.c_void_p), ("trace", ctypes.c_void_p), ("trace_val", ctypes.c_void_p)]
 
 
+class lra_block(ctypes.Structure):
+    _fields_ = [("row0", ctypes.c_int64), ("m", ctypes.c_int64),
+                ("col0", ctypes.c_int64), ("n", ctypes.c_int64)]
+
+
+class lra_batch_params(ctypes.Structure):
+    _fields_ = [("l_init", ctypes.c_int32), ("l_max", ctypes.c_int32), ("k_max", ctypes.c_int32),
+                ("sweeps", ctypes.c_int32), ("max_swaps", ctypes.c_int32), ("sample", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("delta", ctypes.c_double),
+                ("cand_J", ctypes.c_void_p), ("sample_rows", ctypes.c_void_p),
+                ("sample_cols", ctypes.c_void_p), ("flags", ctypes.c_int32)]
+
+
+class lra_batch_out(ctypes.Structure):
+    _fields_ = [("on_device", ctypes.c_int32), ("status", ctypes.c_void_p), ("l", ctypes.c_void_p),
+                ("k_eff", ctypes.c_void_p), ("swaps", ctypes.c_void_p), ("I", ctypes.c_void_p),
+                ("J", ctypes.c_void_p), ("U", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
+                ("est_err", ctypes.c_void_p)]
+
+
 _ctx_p = ctypes.c_void_p
 _job = ctypes.c_uint64
 
@@ -99,12 +120,17 @@ _fetch = _sig("lra_cross_fetch_cur", ctypes.c_int, _ctx_p, _job, ctypes.POINTER(
 _cancel = _sig("lra_cross_cancel", ctypes.c_int, _ctx_p, _job)
 _footprint = _sig("lra_cross_footprint", ctypes.c_int, ctypes.POINTER(lra_source),
                   ctypes.POINTER(lra_params), ctypes.POINTER(ctypes.c_uint64))
+_submit_batch = _sig("lra_cross_submit_batch", ctypes.c_int, _ctx_p, ctypes.POINTER(lra_source),
+                     ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(lra_batch_params),
+                     ctypes.POINTER(_job))
+_fetch_batch = _sig("lra_cross_fetch_batch", ctypes.c_int, _ctx_p, _job, ctypes.POINTER(lra_batch_out))
 _status_str = _sig("lra_status_str", ctypes.c_char_p, ctypes.c_int32)
 _last_error = _sig("lra_cross_last_error", ctypes.c_char_p, _ctx_p)
 
 EXPORTED = ["lra_cross_create", "lra_cross_destroy", "lra_cross_submit", "lra_cross_poll",
             "lra_cross_wait", "lra_cross_fetch_cur", "lra_cross_cancel", "lra_cross_footprint",
-            "lra_status_str", "lra_cross_last_error"]
+            "lra_status_str", "lra_cross_last_error", "lra_cross_submit_batch",
+            "lra_cross_fetch_batch"]
 
 
 class LraError(RuntimeError):
@@ -128,8 +154,9 @@ def _check(code, ctx=None, ok=(LRA_OK,)):
 
 
 # ---- the C ABI, one function per entry point --------------------------------
-def lra_cross_create(device: int = 0, max_slots: int = 64, mem_budget_bytes: int = 0, stream=None):
-    p = lra_ctx_params(device, max_slots, mem_budget_bytes, stream or None)
+def lra_cross_create(device: int = 0, max_slots: int = 64, mem_budget_bytes: int = 0, stream=None,
+                     n_streams: int = 1):
+    p = lra_ctx_params(device, max_slots, mem_budget_bytes, stream or None, n_streams)
     ctx = _ctx_p()
     _check(_create(ctypes.byref(ctx), ctypes.byref(p)))
     return ctx
@@ -166,13 +193,25 @@ def lra_cross_cancel(ctx, job: int) -> None:
     _check(_cancel(ctx, job), ctx)
 
 
+def lra_cross_submit_batch(ctx, src: lra_source, blocks, params: lra_batch_params) -> int:
+    """blocks: int64 array (n_blocks x 4: row0, m, col0, n), C-contiguous."""
+    job = _job()
+    _check(_submit_batch(ctx, ctypes.byref(src), blocks.ctypes.data, len(blocks), ctypes.byref(params),
+                         ctypes.byref(job)), ctx)
+    return job.value
+
+
+def lra_cross_fetch_batch(ctx, job: int, out: lra_batch_out) -> int:
+    return _check(_fetch_batch(ctx, job, ctypes.byref(out)), ctx)
+
+
 def lra_cross_footprint(src: lra_source, params: lra_params) -> int:
     b = ctypes.c_uint64()
     _check(_footprint(ctypes.byref(src), ctypes.byref(params), ctypes.byref(b)))
     return b.value
 
 
-from .api import Context, SolveResult, make_params, make_source  # noqa: E402
+from .api import BatchResult, Context, SolveResult, make_params, make_source  # noqa: E402
 
-__all__ = EXPORTED + ["Context", "SolveResult", "LraError", "make_params", "make_source",
+__all__ = EXPORTED + ["Context", "SolveResult", "BatchResult", "LraError", "make_params", "make_source",
                       "lra_source", "lra_params", "lra_info", "lra_cur_out", "LIB_PATH"]

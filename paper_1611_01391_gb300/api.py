@@ -9,7 +9,8 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import (LRA_DENSE_F32, LRA_DENSE_F64, LRA_GEN_CAUCHY, LRA_GEN_GAUSS, LRA_GEN_INVDIST,
-               lra_cross_create, lra_cross_destroy, lra_cross_fetch_cur, lra_cross_submit,
+               lra_batch_out, lra_batch_params, lra_cross_create, lra_cross_destroy,
+               lra_cross_fetch_batch, lra_cross_fetch_cur, lra_cross_submit, lra_cross_submit_batch,
                lra_cross_wait, lra_cur_out, lra_info, lra_params, lra_source)
 
 _KINDS = {"dense": None, "cauchy": LRA_GEN_CAUCHY, "gauss": LRA_GEN_GAUSS,
@@ -80,8 +81,8 @@ class SolveResult:
 class Context:
     """One library context (one device, one stream)."""
 
-    def __init__(self, device=0, max_slots=64, mem_budget_bytes=0, stream=None):
-        self.ctx = lra_cross_create(device, max_slots, mem_budget_bytes, stream)
+    def __init__(self, device=0, max_slots=64, mem_budget_bytes=0, stream=None, n_streams=1):
+        self.ctx = lra_cross_create(device, max_slots, mem_budget_bytes, stream, n_streams)
 
     def close(self):
         if self.ctx:
@@ -126,3 +127,57 @@ class Context:
     def solve(self, src, params, l, m=None, n=None, want_strips=False, trace_cap=0, device=None):
         job = self.submit(src, params)
         return self.fetch(job, l, m, n, want_strips, trace_cap, device)
+
+
+@dataclass
+class BatchResult:
+    status: np.ndarray
+    l: np.ndarray
+    k_eff: np.ndarray
+    swaps: np.ndarray
+    I: np.ndarray
+    J: np.ndarray
+    U: np.ndarray
+    sigma: np.ndarray
+    est_err: np.ndarray
+    info: lra_info
+
+
+def make_batch_params(l_init, l_max, k_max, sweeps, tol, cand_J, sample_rows=None, sample_cols=None,
+                      delta=1e-2, max_swaps=0):
+    """lra_batch_params plus the host arrays it points to (keep both alive)."""
+    cj = np.ascontiguousarray(cand_J, dtype=np.int32)
+    sr = None if sample_rows is None else np.ascontiguousarray(sample_rows, dtype=np.int32)
+    sc = None if sample_cols is None else np.ascontiguousarray(sample_cols, dtype=np.int32)
+    p = lra_batch_params()
+    p.l_init, p.l_max, p.k_max, p.sweeps, p.max_swaps = l_init, l_max, k_max, sweeps, max_swaps
+    p.sample = 0 if sr is None else sr.shape[1]
+    p.tol, p.delta = tol, delta
+    p.cand_J = cj.ctypes.data
+    if sr is not None:
+        p.sample_rows, p.sample_cols = sr.ctypes.data, sc.ctypes.data
+    p.flags = 0
+    return p, (cj, sr, sc)
+
+
+def _batch_fetch(ctx, job, nb, l_max):
+    info = lra_cross_wait(ctx, job)
+    r = BatchResult(np.zeros(nb, np.int32), np.zeros(nb, np.int32), np.zeros(nb, np.int32),
+                    np.zeros(nb, np.int32), np.zeros((nb, l_max), np.int32),
+                    np.zeros((nb, l_max), np.int32), np.zeros((nb, l_max, l_max), np.float64),
+                    np.zeros((nb, l_max), np.float32), np.zeros(nb, np.float64), info)
+    out = lra_batch_out()
+    out.on_device = 0
+    out.status, out.l, out.k_eff, out.swaps = (r.status.ctypes.data, r.l.ctypes.data,
+                                               r.k_eff.ctypes.data, r.swaps.ctypes.data)
+    out.I, out.J, out.U = r.I.ctypes.data, r.J.ctypes.data, r.U.ctypes.data
+    out.sigma, out.est_err = r.sigma.ctypes.data, r.est_err.ctypes.data
+    lra_cross_fetch_batch(ctx, job, out)
+    return r
+
+
+def solve_batch(context, src, blocks, params, l_max):
+    """Submit one batched launch and fetch every block's result (host arrays)."""
+    blocks = np.ascontiguousarray(blocks, dtype=np.int64)
+    job = lra_cross_submit_batch(context.ctx, src, blocks, params)
+    return _batch_fetch(context.ctx, job, len(blocks), l_max)

@@ -1,0 +1,468 @@
+// Batched C-A over thousands of blocks of one generated matrix: the
+// low-rank generators of the far-field (neutered) blocks of an HSS / FMM
+// matrix, the "bottleneck stage" of Section 9, computed by C-A iterations
+// (Section 6.5) in one persistent launch.
+//
+// Design:
+//   * One thread-block cluster of 4 CTAs solves one block at a time and pulls
+//     the next block index from a device work queue (an atomic counter), so
+//     uneven blocks balance themselves.  The strip of the current half-step
+//     (up to 2048 rows x l <= 96 FP32 values) is split across the 4 CTAs'
+//     shared memory and never leaves the chip.
+//   * Each decision: every CTA reduces its best candidate (packed
+//     |value|/index key, warp shuffles), publishes it and that row in its
+//     shared memory, one hardware cluster barrier, then every CTA reads the
+//     four candidates through distributed shared memory and updates its rows.
+//   * Every strip starts from Gauss-Jordan elimination with partial pivoting
+//     in FP32 and continues with maxvol swaps.  Elimination with partial
+//     pivoting is backward stable, so the FP32 B = S X^{-1} it produces is
+//     the exact B of a strip within FP32 rounding of the data; an explicit
+//     X^{-1} in FP32 would not be (its error grows with cond(X)).
+//   * Rank adaptivity: after the sweeps, if the last pivot of the final
+//     vertical step exceeds tol times the first, the cross grows (x2, up to
+//     l_max) with the block's next candidate columns and the sweeps repeat.
+//   * Nucleus: one-sided Jacobi SVD of the final cross in double-float
+//     arithmetic on one CTA (an FP32 SVD cannot resolve singular values near
+//     tol sigma_1 = 1e-6 sigma_1), k_eff = min(k_max, #{sigma_j > tol
+//     sigma_1}), U = (X_k)^+.
+//   * Appendix F estimate on a q x q sample of each block, with compensated
+//     FP32 products and FP64 sums.
+#include <cooperative_groups.h>
+
+#include <cfloat>
+
+#include "lra_internal.cuh"
+#include "lra_kernels.h"
+#include "svd_dd.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace lra {
+namespace {
+
+constexpr int kCS = 4;                    // CTAs per cluster
+constexpr int kBT = 256;                  // threads per CTA
+constexpr int kRowsPerCta = kMaxBatchSide / kCS;
+constexpr int kMaxQ = 64;                 // sample size per side
+
+struct BatchSmem {
+  float B[kRowsPerCta * kMaxL];           // strip chunk, row-major with stride l
+  float colj[kRowsPerCta];
+  float rrow[kMaxL];
+  float slot_row[2][kMaxL];               // published candidate rows (read by peers)
+  unsigned long long slot_key[2];
+  int slot_nf[2];
+  unsigned long long red_key[kBT / 32];
+  int red_nf[kBT / 32];
+  unsigned long long win_key;
+  int win_nf;
+  int pos[kMaxL];
+  int Iset[kMaxL], Jset[kMaxL];
+  unsigned char used[kRowsPerCta];
+  int blk;
+  int status;
+  float piv_first, piv_last;
+  int swaps;
+  int keff;
+  int lnew;
+  int status_aux;
+  double esum[2][kBT / 32];
+};
+// the nucleus (W, V, sigma, 1/sigma^2, order) and the estimate's operands
+// reuse the strip area once the sweeps are over
+static_assert(2 * kMaxL * kMaxL * sizeof(dd) + kMaxL * (sizeof(double) + sizeof(dd) + sizeof(int)) <=
+                  sizeof(BatchSmem::B), "nucleus area");
+static_assert(sizeof(float) * (2 * kMaxL * kMaxL + 4 * kMaxQ * kMaxL) <= sizeof(BatchSmem::B),
+              "estimate area");
+
+__device__ __forceinline__ unsigned long long pack_key(float v, int idx) {
+  return ((unsigned long long)(__float_as_uint(v) & 0x7fffffffu) << 32) | (unsigned)(~idx);
+}
+__device__ __forceinline__ int key_idx(unsigned long long k) { return ~(int)(unsigned)(k & 0xffffffffu); }
+__device__ __forceinline__ float key_val(unsigned long long k) { return __uint_as_float((unsigned)(k >> 32)); }
+
+__device__ __forceinline__ void consider_f(unsigned long long& best, int& nf, float v, int idx) {
+  if ((__float_as_uint(v) & 0x7fffffffu) >= 0x7f800000u) {
+    nf = 1;
+    return;
+  }
+  const unsigned long long k = pack_key(v, idx);
+  if (k > best) best = k;
+}
+
+// CTA-wide reduction of (key, nf); result in s->win_key / s->win_nf.
+__device__ __forceinline__ void cta_reduce(BatchSmem* s, unsigned long long key, int nf) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_down_sync(0xffffffffu, key, off);
+    nf |= __shfl_down_sync(0xffffffffu, nf, off);
+    if (o > key) key = o;
+  }
+  if (lane == 0) {
+    s->red_key[warp] = key;
+    s->red_nf[warp] = nf;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long k = 0ull;
+    int f = 0;
+    for (int w = 0; w < kBT / 32; ++w) {
+      if (s->red_key[w] > k) k = s->red_key[w];
+      f |= s->red_nf[w];
+    }
+    s->win_key = k;
+    s->win_nf = f;
+  }
+  __syncthreads();
+}
+
+// One strip of the C-A iteration on the cluster: load the N x l strip
+// (vertical: S[i][t] = M(row0 + i, col0 + other[t]); horizontal:
+// S[j][t] = M(row0 + other[t], col0 + j)), Gauss-Jordan start, maxvol.
+// Returns false when the block failed (s->status set identically in all
+// CTAs).  On return s->pos holds the selected strip rows.
+template <int KIND>
+__device__ bool half_step(const BatchArgs& a, cg::cluster_group& cl, BatchSmem* s, bool vertical,
+                          long long row0, long long col0, int N, int l, const int* other) {
+  const int rank = (int)cl.block_rank();
+  const int tid = threadIdx.x;
+  const int rpc = (N + kCS - 1) / kCS;
+  const int r0 = rank * rpc;
+  const int nr = max(0, min(rpc, N - r0));
+  for (int e = tid; e < nr * l; e += kBT) {
+    const int r = e / l, t = e - r * l;
+    const long long g = r0 + r;
+    s->B[e] = vertical ? entry<KIND>(a.src, row0 + g, col0 + other[t])
+                       : entry<KIND>(a.src, row0 + other[t], col0 + g);
+  }
+  for (int r = tid; r < nr; r += kBT) s->used[r] = 0;
+  __syncthreads();
+
+  unsigned long long mine = 0ull;
+  int nf = 0;
+  for (int r = tid; r < nr; r += kBT) consider_f(mine, nf, s->B[r * l], (r0 + r) * l);
+  bool gepp = true;
+  int step = 0, swaps = 0, buf = 0;
+  bool ok = true;
+  for (;;) {
+    cta_reduce(s, mine, nf);
+    const unsigned long long cb = s->win_key;
+    if (tid == 0) {
+      s->slot_key[buf] = cb;
+      s->slot_nf[buf] = s->win_nf;
+    }
+    if (cb != 0ull && tid < l) {
+      const int r = key_idx(cb) / l - r0;
+      s->slot_row[buf][tid] = s->B[r * l + tid];
+    }
+    cl.sync();
+    unsigned long long win = 0ull;
+    int wnf = 0, owner = 0;
+    for (int p = 0; p < kCS; ++p) {
+      const unsigned long long k = *cl.map_shared_rank(&s->slot_key[buf], p);
+      wnf |= *cl.map_shared_rank(&s->slot_nf[buf], p);
+      if (k > win) {
+        win = k;
+        owner = p;
+      }
+    }
+    const float wv = key_val(win);
+    int kind;  // 0 gepp, 1 swap, 2 stop
+    if (wnf) {
+      if (tid == 0) s->status = LRA_ENONFINITE;
+      ok = false;
+      break;
+    }
+    if (gepp) {
+      if (win == 0ull || !(wv > 0.0f)) {
+        if (tid == 0) s->status = LRA_ESINGULAR;
+        ok = false;
+        break;
+      }
+      if (vertical && tid == 0) {
+        if (step == 0) s->piv_first = wv;
+        if (step == l - 1) s->piv_last = wv;
+      }
+      kind = 0;
+    } else if (wv <= 1.0f + a.delta || swaps >= a.max_swaps) {
+      kind = 2;
+    } else {
+      kind = 1;
+    }
+    if (kind == 2) break;
+    const int idx = key_idx(win);
+    const int istar = idx / l, jstar = idx - istar * l;
+    if (tid < l) s->rrow[tid] = cl.map_shared_rank(&s->slot_row[buf][0], owner)[tid];
+    for (int r = tid; r < nr; r += kBT) s->colj[r] = s->B[r * l + jstar];
+    if (tid == 0) {
+      if (gepp && istar >= r0 && istar < r0 + nr) s->used[istar - r0] = 1;
+      s->pos[jstar] = istar;
+    }
+    __syncthreads();
+    const float piv = s->rrow[jstar];
+    __syncthreads();
+    if (tid < l) s->rrow[tid] = (s->rrow[tid] - (tid == jstar ? 1.0f : 0.0f)) / piv;
+    __syncthreads();
+    const bool next_gepp = gepp && (step + 1 < l);
+    const int next_col = step + 1;
+    mine = 0ull;
+    for (int e = tid; e < nr * l; e += kBT) {
+      const int r = e / l, t = e - r * l;
+      const int g = r0 + r;
+      float v;
+      if (g == istar) {
+        v = (t == jstar) ? 1.0f : 0.0f;
+        s->B[e] = v;
+        if (!next_gepp) consider_f(mine, nf, v, g * l + t);
+      } else {
+        v = fmaf(-s->colj[r], s->rrow[t], s->B[e]);
+        s->B[e] = v;
+        if (next_gepp ? (t == next_col && !s->used[r]) : true) consider_f(mine, nf, v, g * l + t);
+      }
+    }
+    if (gepp) {
+      if (++step == l) gepp = false;
+    } else {
+      ++swaps;
+    }
+    buf ^= 1;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    s->swaps += swaps;
+    // FP32 work of this strip: every decision updates the N x l strip
+    if (rank == 0) atomicAdd(&a.js->maxvol_flops, 2.0 * N * l * (double)(step + swaps));
+  }
+  cl.sync();  // peers finished reading this CTA's slots before they are reused
+  return ok;
+}
+
+__device__ __forceinline__ void two_sum_b(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+__device__ __forceinline__ void dot2_b(float x, float y, float& p, float& c) {
+  const float h = __fmul_rn(x, y);
+  const float r = fmaf(x, y, -h);
+  float q;
+  two_sum_b(p, h, p, q);
+  c = __fadd_rn(c, __fadd_rn(q, r));
+}
+
+template <int KIND>
+__global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kBT, 1) batch_kernel(BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char bsm[];
+  BatchSmem* s = reinterpret_cast<BatchSmem*>(bsm);
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (rank == 0 && tid == 0) s->blk = atomicAdd(a.queue, 1);
+    cl.sync();
+    const int b = *cl.map_shared_rank(&s->blk, 0);
+    if (b >= a.n_blocks) {
+      cl.sync();  // nobody leaves while a peer may still read the leader's index
+      break;
+    }
+    const long long row0 = a.blocks[4 * b + 0], m = a.blocks[4 * b + 1];
+    const long long col0 = a.blocks[4 * b + 2], n = a.blocks[4 * b + 3];
+    const int lmax_b = (int)min((long long)a.l_max, min(m, n));
+    int l = min(a.l_init, lmax_b);
+    for (int t = tid; t < l; t += kBT) s->Jset[t] = a.jcand[(size_t)b * a.l_max + t];
+    if (tid == 0) {
+      s->status = LRA_OK;
+      s->swaps = 0;
+      s->piv_first = s->piv_last = 0.f;
+    }
+    __syncthreads();
+    bool ok = true;
+    for (;;) {
+      for (int sw = 0; sw < a.sweeps && ok; ++sw) {
+        ok = half_step<KIND>(a, cl, s, true, row0, col0, (int)m, l, s->Jset);
+        if (!ok) break;
+        for (int t = tid; t < l; t += kBT) s->Iset[t] = s->pos[t];
+        __syncthreads();
+        ok = half_step<KIND>(a, cl, s, false, row0, col0, (int)n, l, s->Iset);
+        if (!ok) break;
+        for (int t = tid; t < l; t += kBT) s->Jset[t] = s->pos[t];
+        __syncthreads();
+      }
+      if (!ok) break;
+      if (l < lmax_b && s->piv_last > a.tol * s->piv_first) {
+        // grow: append the next candidate columns that are not in J
+        if (tid == 0) {
+          const int l_new = min(lmax_b, 2 * l);
+          int cnt = l;
+          for (int c = 0; c < a.l_max && cnt < l_new; ++c) {
+            const int j = a.jcand[(size_t)b * a.l_max + c];
+            bool in = false;
+            for (int t = 0; t < cnt; ++t) in |= (s->Jset[t] == j);
+            if (!in && j < n) s->Jset[cnt++] = j;
+          }
+          s->lnew = cnt;
+        }
+        __syncthreads();
+        l = s->lnew;
+        __syncthreads();
+        continue;
+      }
+      break;
+    }
+    if (rank == 0) {
+      if (tid == 0) {
+        a.out_status[b] = ok ? (int)LRA_OK : s->status;
+        a.out_l[b] = l;
+        a.out_swaps[b] = s->swaps;
+      }
+      if (ok) {
+        // nucleus on this CTA (double-float Jacobi SVD); the strip area is
+        // free now.  X is scaled by a power of two into [0.5, 1).
+        dd* W = reinterpret_cast<dd*>(s->B);
+        dd* V = W + kMaxL * kMaxL;
+        double* sig = reinterpret_cast<double*>(V + kMaxL * kMaxL);
+        dd* inv2 = reinterpret_cast<dd*>(sig + kMaxL);
+        int* order = reinterpret_cast<int*>(inv2 + kMaxL);
+        if (tid == 0) s->lnew = 0;
+        __syncthreads();
+        float amax = 0.0f;
+        for (int e = tid; e < l * l; e += kBT) {
+          const int p = e / l, q = e - p * l;
+          const float x = entry<KIND>(a.src, row0 + s->Iset[p], col0 + s->Jset[q]);
+          amax = fmaxf(amax, fabsf(x));
+          W[q * l + p] = dd_make(x);   // column q of X
+          V[q * l + p] = dd_make(p == q ? 1.0f : 0.0f);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+        if ((tid & 31) == 0 && amax > 0.0f) {
+          int ex;
+          frexpf(amax, &ex);
+          atomicMax(&s->lnew, ex + 1024);
+        }
+        for (int t = tid; t < a.l_max; t += kBT) {
+          a.out_I[(size_t)b * a.l_max + t] = t < l ? s->Iset[t] : -1;
+          a.out_J[(size_t)b * a.l_max + t] = t < l ? s->Jset[t] : -1;
+        }
+        __syncthreads();
+        const int ex = s->lnew ? s->lnew - 1024 : 0;
+        for (int e = tid; e < l * l; e += kBT) W[e].hi = ldexpf(W[e].hi, -ex);
+        __syncthreads();
+        jacobi_dd<kBT>(W, V, l, &s->status_aux);
+        jacobi_sigma<kBT>(W, l, sig, order);
+        if (tid == 0) {
+          const double s1 = sig[order[0]];
+          int ke = 0;
+          if (s1 > 0.0)
+            while (ke < a.k_max && ke < l && sig[order[ke]] > (double)a.tol * s1) ++ke;
+          s->keff = ke;
+          a.out_keff[b] = ke;
+        }
+        float* sg_out = a.out_sigma + (size_t)b * a.l_max;
+        for (int r = tid; r < l; r += kBT) {
+          const double sb = sig[order[r]];
+          inv2[r] = dd_from_double(sb > 0.0 ? 1.0 / (sb * sb) : 0.0);
+          sg_out[r] = (float)ldexp(sb, ex);
+        }
+        __syncthreads();
+        double* Ub = a.out_U + (size_t)b * a.l_max * a.l_max;
+        nucleus_from_svd<kBT>(W, V, l, s->keff, order, inv2,
+                              [&](int e, double v) { Ub[e] = ldexp(v, -ex); });
+        __syncthreads();
+        // Appendix F estimate on the q x q sample of this block
+        const int q = a.q;
+        if (q > 0) {
+          float* Us = s->B;                      // U (l x l) back from global: hi part
+          float* Usl = Us + kMaxL * kMaxL;       //   and lo part, U = hi + lo
+          float* Cs = Usl + kMaxL * kMaxL;       // q x l: M(row0 + sr, col0 + J)
+          float* Rs = Cs + kMaxQ * kMaxL;        // l x q: M(row0 + I, col0 + sc)
+          float* CUh = Rs + kMaxL * kMaxQ;       // q x l: (C U) hi
+          float* CUl = CUh + kMaxQ * kMaxL;      //        (C U) lo
+          const int* sr = a.srow + (size_t)b * q;
+          const int* sc = a.scol + (size_t)b * q;
+          __syncthreads();
+          for (int e = tid; e < l * l; e += kBT) {
+            const double u = Ub[e];
+            const float hi = (float)u;
+            Us[e] = hi;
+            Usl[e] = (float)(u - (double)hi);
+          }
+          for (int e = tid; e < q * l; e += kBT) {
+            const int i = e / l, t = e - i * l;
+            Cs[e] = entry<KIND>(a.src, row0 + sr[i], col0 + s->Jset[t]);
+            Rs[t * q + i] = entry<KIND>(a.src, row0 + s->Iset[t], col0 + sc[i]);
+          }
+          __syncthreads();
+          for (int e = tid; e < q * l; e += kBT) {
+            const int i = e / l, u = e - i * l;
+            float p = 0.f, c = 0.f;
+            for (int t = 0; t < l; ++t) {
+              dot2_b(Cs[i * l + t], Us[t * l + u], p, c);
+              c = __fmaf_rn(Cs[i * l + t], Usl[t * l + u], c);  // the lo part needs FP32 only
+            }
+            const float hi = __fadd_rn(p, c);
+            CUh[e] = hi;
+            CUl[e] = __fadd_rn(__fsub_rn(p, hi), c);  // rounding error of hi = p + c
+          }
+          __syncthreads();
+          double se = 0.0, sa = 0.0;
+          for (int e = tid; e < q * q; e += kBT) {
+            const int i = e / q, j = e - i * q;
+            float p = 0.f, c = 0.f;
+            for (int u = 0; u < l; ++u) {
+              dot2_b(CUh[i * l + u], Rs[u * q + j], p, c);
+              dot2_b(CUl[i * l + u], Rs[u * q + j], p, c);
+            }
+            const float mv = entry<KIND>(a.src, row0 + sr[i], col0 + sc[j]);
+            const double ev = ((double)mv - (double)p) - (double)c;
+            se += ev * ev;
+            sa += (double)mv * (double)mv;
+          }
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) {
+            se += __shfl_xor_sync(0xffffffffu, se, off);
+            sa += __shfl_xor_sync(0xffffffffu, sa, off);
+          }
+          if ((tid & 31) == 0) {  // fixed-order sum: reproducible bits
+            s->esum[0][tid >> 5] = se;
+            s->esum[1][tid >> 5] = sa;
+          }
+          __syncthreads();
+          if (tid == 0) {
+            double e2 = 0.0, a2 = 0.0;
+            for (int w = 0; w < kBT / 32; ++w) {
+              e2 += s->esum[0][w];
+              a2 += s->esum[1][w];
+            }
+            a.out_err[b] = a2 > 0.0 ? sqrt(e2 / a2) : 0.0;
+          }
+        }
+      }
+    }
+    cl.sync();  // block done: the leader may fetch the next block index
+  }
+}
+
+}  // namespace
+
+size_t batch_smem_bytes() { return sizeof(BatchSmem); }
+
+cudaError_t launch_batch(const BatchArgs& a, int sms, cudaStream_t st) {
+  const size_t smem = sizeof(BatchSmem);
+  const int grid = (sms / kCS) * kCS;
+  cudaError_t e = cudaSuccess;
+  LRA_DISPATCH_KIND(a.src.kind, ({
+    static bool attr = false;
+    if (!attr) {
+      e = cudaFuncSetAttribute(batch_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = (e == cudaSuccess);
+    }
+    if (e == cudaSuccess) batch_kernel<K><<<grid, kBT, smem, st>>>(a);
+  }));
+  if (e) return e;
+  return cudaGetLastError();
+}
+
+}  // namespace lra

@@ -2,27 +2,20 @@
 // Section 6.5): the l x l CUR generator X = M[I, J], its SVD X = P S Q^T, the
 // rank-k truncation and U = Q_k S_k^{-1} P_k^T.
 //
-// The SVD is the one-sided Jacobi method of Hestenes (1958), with the
-// rotation of Rutishauser's symmetric Jacobi step (Golub & Van Loan,
-// Algorithm 8.5.1) applied to column pairs: the columns of W = X V are
-// orthogonalised in place, sigma_b = ||W[:, b]||, P[:, b] = W[:, b] / sigma_b
-// and Q = V.  Pairs are visited in round-robin (circle) order so that the
-// l/2 rotations of a round are independent; one warp handles one pair.
-// Everything is FP64.
+// The SVD is the one-sided Jacobi method of Hestenes (1958) in double-float
+// arithmetic (svd_dd.cuh): the columns of W = X V are orthogonalised in
+// place, sigma_b = ||W[:, b]||, P[:, b] = W[:, b] / sigma_b and Q = V.  X is
+// first scaled by a power of two so that max |X| lies in [0.5, 1) (exact);
+// sigma and U are scaled back.
 #include <cfloat>
 
 #include "lra_kernels.h"
 #include "lra_internal.cuh"
+#include "svd_dd.cuh"
 
 namespace lra {
 
 constexpr int kNucThreads = 512;
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  return v;
-}
 
 __global__ void __launch_bounds__(kNucThreads, 1)
 nucleus_kernel(const float* __restrict__ C, const int* __restrict__ I, int l, int k,
@@ -30,131 +23,59 @@ nucleus_kernel(const float* __restrict__ C, const int* __restrict__ I, int l, in
                JobStatus* js) {
   if (js->status != LRA_OK) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* W = reinterpret_cast<double*>(smem_raw);  // column b at W + b*l
-  double* V = W + (size_t)l * l;                     // column b at V + b*l
-  double* sig = V + (size_t)l * l;                   // l
-  double* sig_sorted = sig + kMaxL;                  // l
-  int* order = reinterpret_cast<int*>(sig_sorted + kMaxL);  // l: order[rank] = column
-  int* rotated = order + kMaxL;
-  int* keff_s = rotated + 1;
+  dd* W = reinterpret_cast<dd*>(smem_raw);           // column b at W + b*l
+  dd* V = W + (size_t)l * l;                          // column b at V + b*l
+  double* sig = reinterpret_cast<double*>(V + (size_t)l * l);  // l
+  dd* inv2 = reinterpret_cast<dd*>(sig + kMaxL);      // l
+  int* order = reinterpret_cast<int*>(inv2 + kMaxL);  // l: order[rank] = column
+  int* flag = order + kMaxL;
+  int* keff_s = flag + 1;
+  int* scale_e = keff_s + 1;
 
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
-
+  if (tid == 0) *scale_e = 0;
+  __syncthreads();
+  // power-of-two scale so that max |X| is in [0.5, 1)
+  float amax = 0.0f;
+  for (int e = tid; e < l * l; e += nthr) {
+    const int a = e / l, b = e - a * l;
+    amax = fmaxf(amax, fabsf(C[(size_t)__ldg(I + a) * l + b]));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+  if ((tid & 31) == 0 && amax > 0.0f) {
+    int ex;
+    frexpf(amax, &ex);
+    atomicMax(scale_e, ex + 1024);  // offset keeps the stored value positive
+  }
+  __syncthreads();
+  const int ex = *scale_e ? *scale_e - 1024 : 0;
   for (int e = tid; e < l * l; e += nthr) {
     const int a = e / l, b = e - a * l;             // X[a][b] = C[I[a]][b]
-    W[(size_t)b * l + a] = (double)C[(size_t)__ldg(I + a) * l + b];
-    V[(size_t)b * l + a] = (a == b) ? 1.0 : 0.0;
+    W[(size_t)b * l + a] = dd_make(ldexpf(C[(size_t)__ldg(I + a) * l + b], -ex));
+    V[(size_t)b * l + a] = dd_make((a == b) ? 1.0f : 0.0f);
   }
   __syncthreads();
-
-  // Pairs of a round are handled by groups of 8 lanes (4 pairs per warp), so
-  // one FP64 instruction serves four rotations; the FP64 pipe is the limit.
-  const int np = (l + 1) & ~1;                      // players incl. a dummy when l is odd
-  const double tol = (double)l * DBL_EPSILON;
-  const int gl = lane & 7;
-  const int ngroups = nwarps * 4;
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    if (tid == 0) *rotated = 0;
-    __syncthreads();
-    for (int round = 0; round < np - 1; ++round) {
-      for (int base = warp * 4; base < np / 2; base += ngroups) {
-        const int slot = base + (lane >> 3);
-        const int x0 = slot, x1 = np - 1 - slot;
-        int p = (x0 == 0) ? 0 : ((x0 - 1 + round) % (np - 1)) + 1;
-        int q = (x1 == 0) ? 0 : ((x1 - 1 + round) % (np - 1)) + 1;
-        if (p > q) { const int t = p; p = q; q = t; }
-        const bool act = slot < np / 2 && q < l;
-        double* wp = W + (size_t)p * l;
-        double* wq = W + (size_t)q * l;
-        double al = 0.0, be = 0.0, ga = 0.0;
-        if (act)
-          for (int a = gl; a < l; a += 8) {
-            const double u = wp[a], v = wq[a];
-            al = fma(u, u, al);
-            be = fma(v, v, be);
-            ga = fma(u, v, ga);
-          }
-#pragma unroll
-        for (int off = 4; off > 0; off >>= 1) {
-          al += __shfl_xor_sync(0xffffffffu, al, off);
-          be += __shfl_xor_sync(0xffffffffu, be, off);
-          ga += __shfl_xor_sync(0xffffffffu, ga, off);
-        }
-        if (!act || al == 0.0 || be == 0.0 || ga * ga <= tol * tol * al * be) continue;
-        // Rotation tangent t from the symmetric Jacobi step; an approximate t
-        // (FP32) still gives an exactly orthogonal rotation because c and s
-        // are formed from the same t in FP64: c = (1 + t^2)^{-1/2}, s = c t.
-        const double zeta = (be - al) / (2.0 * ga);
-        const float zf = (float)zeta;
-        // |zeta| > 1e18 (columns of very different norms): t = 1/(2 zeta) to
-        // FP32 accuracy, and zeta^2 would overflow FP32.
-        const float tf = fabsf(zf) > 1e18f
-                             ? 0.5f / zf
-                             : (zf >= 0.0f ? 1.0f : -1.0f) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)));
-        const double t = (double)tf;
-        const double x = fma(t, t, 1.0);
-        double y = (double)rsqrtf((float)x);          // Newton-Raphson for x^{-1/2}
-        y = y * fma(-0.5 * x * y, y, 1.5);
-        y = y * fma(-0.5 * x * y, y, 1.5);
-        const double c = y, s = y * t;
-        double* vp = V + (size_t)p * l;
-        double* vq = V + (size_t)q * l;
-        for (int a = gl; a < l; a += 8) {
-          const double u = wp[a], v = wq[a];
-          wp[a] = fma(c, u, -s * v);
-          wq[a] = fma(s, u, c * v);
-          const double xx = vp[a], yy = vq[a];
-          vp[a] = fma(c, xx, -s * yy);
-          vq[a] = fma(s, xx, c * yy);
-        }
-        if (gl == 0) *rotated = 1;
-      }
-      __syncthreads();
-    }
-    if (*rotated == 0) break;
-    __syncthreads();
-  }
-
-  // singular values, descending order (ties: smaller column first)
-  for (int b = warp; b < l; b += nwarps) {
-    double ss = 0.0;
-    for (int a = lane; a < l; a += 32) ss = fma(W[(size_t)b * l + a], W[(size_t)b * l + a], ss);
-    ss = warp_sum(ss);
-    if (lane == 0) sig[b] = sqrt(ss);
-  }
-  __syncthreads();
-  for (int b = tid; b < l; b += nthr) {
-    int rank = 0;
-    for (int c = 0; c < l; ++c)
-      rank += (sig[c] > sig[b]) || (sig[c] == sig[b] && c < b);
-    order[rank] = b;
-    sig_sorted[rank] = sig[b];
-  }
-  __syncthreads();
+  jacobi_dd<kNucThreads>(W, V, l, flag);
+  jacobi_sigma<kNucThreads>(W, l, sig, order);
   if (tid == 0) {
-    const double s1 = sig_sorted[0];
+    const double s1 = sig[order[0]];
     int ke = 0;
     if (s1 > 0.0)
-      while (ke < k && ke < l && sig_sorted[ke] > rank_tol * s1) ++ke;
+      while (ke < k && ke < l && sig[order[ke]] > rank_tol * s1) ++ke;
     *keff_s = ke;
     js->k_eff = ke;
-    js->sigma_max = s1;
+    js->sigma_max = ldexp(s1, ex);
+  }
+  for (int r = tid; r < l; r += nthr) {
+    const double sb = sig[order[r]];
+    inv2[r] = dd_from_double(sb > 0.0 ? 1.0 / (sb * sb) : 0.0);
+    sigma_out[r] = ldexp(sb, ex);
   }
   __syncthreads();
   const int ke = *keff_s;
-  for (int b = tid; b < l; b += nthr) sigma_out[b] = sig_sorted[b];
-  // U[p][q] = sum_r V[b_r][p] * W[b_r][q] / sigma_{b_r}^2  (P = W / sigma)
-  for (int e = tid; e < l * l; e += nthr) {
-    const int p = e / l, q = e - p * l;
-    double acc = 0.0;
-    for (int r = 0; r < ke; ++r) {
-      const int b = order[r];
-      const double s = sig[b];
-      acc = fma(V[(size_t)b * l + p] / s, W[(size_t)b * l + q] / s, acc);
-    }
-    U[e] = acc;
-  }
+  nucleus_from_svd<kNucThreads>(W, V, l, ke, order, inv2,
+                                [&](int e, double v) { U[e] = ldexp(v, -ex); });
 }
 
 // X^{-1} of the cross X[a][b] = S[pos[a]][b] of an N x l strip (element
@@ -265,7 +186,8 @@ cudaError_t launch_cross_inverse(const float* strip, long long si, long long st,
 
 cudaError_t launch_nucleus(const float* C, const int* I, int l, int k, double rank_tol,
                            double* U, double* sigma, JobStatus* js, cudaStream_t st) {
-  const size_t smem = (2 * (size_t)l * l + 2 * kMaxL) * sizeof(double) + (kMaxL + 2) * sizeof(int);
+  const size_t smem = 2 * (size_t)l * l * sizeof(dd) + kMaxL * (sizeof(double) + sizeof(dd)) +
+                      (kMaxL + 3) * sizeof(int);
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(nucleus_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -83,6 +83,32 @@ struct JobStatus {
   double full_sse, full_ssa, full_rel;
 };
 
+// Batched C-A (many blocks of one source, one launch).
+constexpr int kMaxBatchSide = 2048;  // rows / columns of a block
+
+struct BatchArgs {
+  SourceDev src;
+  const long long* blocks;  // n_blocks x 4: row0, m, col0, n
+  int n_blocks;
+  const int* jcand;         // n_blocks x l_max candidate columns (local to the block)
+  const int* srow;          // n_blocks x q sample rows (local)
+  const int* scol;          // n_blocks x q sample columns (local)
+  int q;
+  int l_init, l_max, k_max, sweeps, max_swaps;
+  float tol, delta;
+  int* queue;               // work counter, zero at launch
+  int* out_status;
+  int* out_l;
+  int* out_keff;
+  int* out_swaps;
+  int* out_I;               // n_blocks x l_max
+  int* out_J;
+  double* out_U;            // n_blocks x l_max x l_max (l x l used, row-major)
+  float* out_sigma;         // n_blocks x l_max
+  double* out_err;          // n_blocks
+  JobStatus* js;            // maxvol_flops accumulates the elimination / update FLOPs
+};
+
 struct GridBarrier {
   unsigned int count;
   unsigned int gen;

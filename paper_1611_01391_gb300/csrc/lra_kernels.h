@@ -79,6 +79,11 @@ cudaError_t launch_full_residual(const float* A, long long lda, long long m, lon
                                  const float* C, const double* U, const float* R, void* ws,
                                  int grid_cap, JobStatus* js, cudaStream_t st);
 
+// Batched C-A: one persistent launch of 4-CTA clusters over a work queue.
+struct BatchArgs;
+size_t batch_smem_bytes();
+cudaError_t launch_batch(const BatchArgs& a, int sms, cudaStream_t st);
+
 // Small control kernels.
 cudaError_t launch_sweep_done(JobStatus* js, cudaStream_t st);
 cudaError_t launch_tol_check(JobStatus* js, double tol, cudaStream_t st);

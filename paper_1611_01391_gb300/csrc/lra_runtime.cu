@@ -43,6 +43,17 @@ struct Job {
   bool full_res = false;
   void* fr_ws = nullptr;
   std::vector<std::pair<int, cudaEvent_t>> prof;  // (kernel class, event after the launch)
+  cudaStream_t stream = nullptr;  // the context stream this job runs on
+  int stream_idx = -1;
+  // batched jobs
+  bool batch = false;
+  int n_blocks = 0, b_lmax = 0, b_q = 0;
+  long long* b_blocks = nullptr;
+  int *b_jcand = nullptr, *b_srow = nullptr, *b_scol = nullptr, *b_queue = nullptr;
+  int *b_status = nullptr, *b_l = nullptr, *b_keff = nullptr, *b_swaps = nullptr, *b_I = nullptr, *b_J = nullptr;
+  double* b_U = nullptr;
+  float* b_sigma = nullptr;
+  double* b_err = nullptr;
 };
 
 enum { kClsGather = 0, kClsMaxvol = 1, kClsCross = 2, kClsResid = 3, kClsInverse = 4, kClsFullres = 5,
@@ -62,8 +73,10 @@ struct Layout {
 
 struct lra_ctx {
   int device = 0;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;           // streams[0]
   bool own_stream = false;
+  std::vector<cudaStream_t> streams;       // jobs are spread over these
+  std::vector<int> stream_load;            // active jobs per stream
   int sms = 0;
   size_t smem_optin = 0;
   int max_slots = 64;
@@ -185,7 +198,8 @@ bool distinct_in_range(const int32_t* v, long long count, long long bound) {
 }
 
 void release_job(lra_ctx* ctx, Job* j) {
-  if (j->dmem) cudaFreeAsync(j->dmem, ctx->stream);
+  if (j->dmem) cudaFreeAsync(j->dmem, j->stream);
+  if (j->stream_idx >= 0) ctx->stream_load[j->stream_idx]--;
   if (j->ev_start) cudaEventDestroy(j->ev_start);
   if (j->ev_end) cudaEventDestroy(j->ev_end);
   for (auto& pe : j->prof) cudaEventDestroy(pe.second);
@@ -196,7 +210,7 @@ void release_job(lra_ctx* ctx, Job* j) {
 
 // Enqueue the whole solve of one job on the context stream.
 cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
-  cudaStream_t st = ctx->stream;
+  cudaStream_t st = j->stream;
   cudaError_t e;
   JobStatus init{};
   init.status = LRA_OK;
@@ -308,6 +322,30 @@ void fill_info(lra_ctx* ctx, Job* j, lra_info* out) {
   out->full_rel_err = j->full_res ? h.full_rel : -1.0;
 }
 
+SourceDev make_src(const lra_source* src) {
+  SourceDev d{};
+  d.kind = src->kind;
+  d.dim = src->kind == LRA_GEN_CAUCHY ? 1 : src->dim;
+  d.m = src->m;
+  d.n = src->n;
+  d.a = src->a;
+  d.lda = src->lda;
+  d.x = src->x;
+  d.y = src->y;
+  d.h2 = src->h * src->h;
+  return d;
+}
+
+// Least-loaded context stream for a new job (ties: lowest index).
+void assign_stream(lra_ctx* ctx, Job* j) {
+  size_t best = 0;
+  for (size_t i = 1; i < ctx->streams.size(); ++i)
+    if (ctx->stream_load[i] < ctx->stream_load[best]) best = i;
+  j->stream_idx = (int)best;
+  j->stream = ctx->streams[best];
+  ctx->stream_load[best]++;
+}
+
 Job* find_job(lra_ctx* ctx, lra_job id) {
   auto it = ctx->jobs.find(id);
   return it == ctx->jobs.end() ? nullptr : it->second;
@@ -358,12 +396,27 @@ lra_status lra_cross_create(lra_ctx** out, const lra_ctx_params* params) {
   ctx->smem_optin = prop.sharedMemPerBlockOptin;
   if (params->stream) {
     ctx->stream = static_cast<cudaStream_t>(params->stream);
+    ctx->streams.push_back(ctx->stream);
   } else {
-    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)) { delete ctx; return LRA_ECUDA; }
+    // own streams: jobs submitted while others run go to the least loaded
+    // stream, so their kernels overlap on the device
+    const int ns = std::max(1, std::min(32, params->n_streams));
+    for (int i = 0; i < ns; ++i) {
+      cudaStream_t s;
+      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) {
+        for (cudaStream_t t : ctx->streams) cudaStreamDestroy(t);
+        delete ctx;
+        return LRA_ECUDA;
+      }
+      ctx->streams.push_back(s);
+    }
+    ctx->stream = ctx->streams[0];
     ctx->own_stream = true;
   }
+  ctx->stream_load.assign(ctx->streams.size(), 0);
   if (cudaMallocHost(&ctx->pinned, sizeof(JobStatus) * ctx->max_slots)) {
-    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->own_stream)
+      for (cudaStream_t t : ctx->streams) cudaStreamDestroy(t);
     delete ctx;
     return LRA_ENOMEM;
   }
@@ -377,11 +430,12 @@ lra_status lra_cross_destroy(lra_ctx* ctx) {
   {
     std::lock_guard<std::mutex> lock(ctx->mu);
     cudaSetDevice(ctx->device);
-    cudaStreamSynchronize(ctx->stream);
+    for (cudaStream_t s : ctx->streams) cudaStreamSynchronize(s);
     for (auto& kv : ctx->jobs) release_job(ctx, kv.second);
     ctx->jobs.clear();
-    cudaStreamSynchronize(ctx->stream);
-    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    for (cudaStream_t s : ctx->streams) cudaStreamSynchronize(s);
+    if (ctx->own_stream)
+      for (cudaStream_t s : ctx->streams) cudaStreamDestroy(s);
     cudaFreeHost(ctx->pinned);
   }
   delete ctx;
@@ -418,11 +472,7 @@ lra_status lra_cross_submit(lra_ctx* ctx, const lra_source* src, const lra_param
   j->full_res = (p->flags & LRA_FLAG_FULL_RESIDUAL) != 0;
   j->m = src->m; j->n = src->n; j->q = p->resid_q; j->s = p->resid_s;
   j->delta = p->delta; j->rank_tol = p->rank_tol; j->tol = p->tol;
-  j->src.kind = src->kind;
-  j->src.dim = src->kind == LRA_GEN_CAUCHY ? 1 : src->dim;
-  j->src.m = src->m; j->src.n = src->n; j->src.a = src->a; j->src.lda = src->lda;
-  j->src.x = src->x; j->src.y = src->y;
-  j->src.h2 = src->h * src->h;
+  j->src = make_src(src);
   if (!plan_maxvol(j->m, j->l, ctx->sms, ctx->smem_optin, &j->plan_col) ||
       !plan_maxvol(j->n, j->l, ctx->sms, ctx->smem_optin, &j->plan_row)) {
     delete j;
@@ -434,7 +484,9 @@ lra_status lra_cross_submit(lra_ctx* ctx, const lra_source* src, const lra_param
     delete j;
     return fail(ctx, LRA_EBUSY, "no free slot or memory budget exhausted");
   }
-  if ((e = cudaMallocAsync(reinterpret_cast<void**>(&j->dmem), j->bytes, ctx->stream))) {
+  assign_stream(ctx, j);
+  if ((e = cudaMallocAsync(reinterpret_cast<void**>(&j->dmem), j->bytes, j->stream))) {
+    ctx->stream_load[j->stream_idx]--;
     delete j;
     return cuda_fail(ctx, e, "cudaMallocAsync");
   }
@@ -444,7 +496,7 @@ lra_status lra_cross_submit(lra_ctx* ctx, const lra_source* src, const lra_param
   ctx->used_bytes += j->bytes;
   if ((e = cudaEventCreate(&j->ev_start)) || (e = cudaEventCreate(&j->ev_end)) ||
       (e = enqueue_solve(ctx, j, p))) {
-    cudaStreamSynchronize(ctx->stream);
+    cudaStreamSynchronize(j->stream);
     release_job(ctx, j);
     return cuda_fail(ctx, e, "enqueue");
   }
@@ -488,6 +540,11 @@ lra_status lra_cross_wait(lra_ctx* ctx, lra_job id, lra_info* out) {
 }
 
 lra_status lra_cross_fetch_cur(lra_ctx* ctx, lra_job id, const lra_cur_out* out) {
+  if (ctx && out) {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    Job* j0 = find_job(ctx, id);
+    if (j0 && j0->batch) return fail(ctx, LRA_EINVAL, "batch job: use lra_cross_fetch_batch");
+  }
   if (!ctx || !out) return LRA_EINVAL;
   std::lock_guard<std::mutex> lock(ctx->mu);
   Job* j = find_job(ctx, id);
@@ -513,9 +570,9 @@ lra_status lra_cross_fetch_cur(lra_ctx* ctx, lra_job id, const lra_cur_out* out)
     };
     for (const Piece& pc : pieces) {
       if (!pc.dst || pc.bytes == 0) continue;
-      if ((e = cudaMemcpyAsync(pc.dst, pc.src, pc.bytes, cudaMemcpyDefault, ctx->stream))) break;
+      if ((e = cudaMemcpyAsync(pc.dst, pc.src, pc.bytes, cudaMemcpyDefault, j->stream))) break;
     }
-    if (!e) e = cudaStreamSynchronize(ctx->stream);
+    if (!e) e = cudaStreamSynchronize(j->stream);
     if (e) result = cuda_fail(ctx, e, "fetch copy");
   } else {
     fail(ctx, result, lra_status_str(result));
@@ -535,6 +592,197 @@ lra_status lra_cross_cancel(lra_ctx* ctx, lra_job id) {
   ctx->jobs.erase(id);
   release_job(ctx, j);
   return LRA_OK;
+}
+
+static lra_status validate_batch(const lra_source* src, const lra_block* blocks, int32_t nb,
+                                 const lra_batch_params* p, std::string* why) {
+  if (!src || !blocks || !p) { *why = "null argument"; return LRA_EINVAL; }
+  if (src->kind < LRA_DENSE_F32 || src->kind > LRA_GEN_INVDIST) { *why = "unknown source kind"; return LRA_EINVAL; }
+  if (src->kind <= LRA_DENSE_F64 ? (!src->a || src->lda < src->n) : (!src->x || !src->y)) {
+    *why = "source pointers"; return LRA_EINVAL;
+  }
+  if (src->kind == LRA_GEN_GAUSS || src->kind == LRA_GEN_INVDIST) {
+    if (src->dim < 1 || src->dim > 3) { *why = "dim must be 1..3"; return LRA_EINVAL; }
+  }
+  if (nb < 1) { *why = "n_blocks must be >= 1"; return LRA_EINVAL; }
+  if (p->l_max < 1 || p->l_max > kMaxL) { *why = "l_max must be in 1..96"; return LRA_EINVAL; }
+  if (p->l_init < 1 || p->l_init > p->l_max) { *why = "l_init must be in 1..l_max"; return LRA_EINVAL; }
+  if (p->k_max < 1 || p->k_max > p->l_max) { *why = "k_max must be in 1..l_max"; return LRA_EINVAL; }
+  if (p->sweeps < 1 || p->sweeps > 100) { *why = "sweeps must be in 1..100"; return LRA_EINVAL; }
+  if (p->sample < 0 || p->sample > 64) { *why = "sample must be in 0..64"; return LRA_EINVAL; }
+  if (!(p->delta > 0.0) || !(p->tol >= 0.0)) { *why = "delta > 0 and tol >= 0 required"; return LRA_EINVAL; }
+  if (!p->cand_J || (p->sample > 0 && (!p->sample_rows || !p->sample_cols))) {
+    *why = "candidate / sample arrays required"; return LRA_EINVAL;
+  }
+  for (int32_t b = 0; b < nb; ++b) {
+    const lra_block& k = blocks[b];
+    if (k.m < 1 || k.n < 1 || k.m > kMaxBatchSide || k.n > kMaxBatchSide || k.row0 < 0 || k.col0 < 0 ||
+        k.row0 + k.m > src->m || k.col0 + k.n > src->n) {
+      *why = "block " + std::to_string(b) + " out of range (sides 1..2048 inside the source)";
+      return LRA_EINVAL;
+    }
+    const long long lc = std::min<long long>(p->l_max, k.n);
+    if (!distinct_in_range(p->cand_J + (size_t)b * p->l_max, lc, k.n)) {
+      *why = "cand_J of block " + std::to_string(b) + " must hold distinct local columns";
+      return LRA_EINVAL;
+    }
+    if (p->sample > 0 && (p->sample > k.m || p->sample > k.n ||
+                          !distinct_in_range(p->sample_rows + (size_t)b * p->sample, p->sample, k.m) ||
+                          !distinct_in_range(p->sample_cols + (size_t)b * p->sample, p->sample, k.n))) {
+      *why = "sample indices of block " + std::to_string(b);
+      return LRA_EINVAL;
+    }
+  }
+  return LRA_OK;
+}
+
+lra_status lra_cross_submit_batch(lra_ctx* ctx, const lra_source* src, const lra_block* blocks,
+                                  int32_t nb, const lra_batch_params* p, lra_job* out) {
+  if (!ctx || !out) return LRA_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  std::string why;
+  lra_status st = validate_batch(src, blocks, nb, p, &why);
+  if (st != LRA_OK) return fail(ctx, st, why);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e) return cuda_fail(ctx, e, "cudaSetDevice");
+  Job* j = new Job();
+  j->batch = true;
+  j->n_blocks = nb;
+  j->b_lmax = p->l_max;
+  j->b_q = p->sample;
+  j->src = make_src(src);
+  j->m = src->m;
+  j->n = src->n;
+  const size_t L = (size_t)p->l_max, q = (size_t)p->sample, NB = (size_t)nb;
+  Layout lay;
+  const size_t o_js = lay.take(sizeof(JobStatus));
+  const size_t o_queue = lay.take(sizeof(int));
+  const size_t o_blocks = lay.take(sizeof(long long) * 4 * NB);
+  const size_t o_jc = lay.take(sizeof(int) * NB * L);
+  const size_t o_sr = lay.take(sizeof(int) * NB * std::max<size_t>(q, 1));
+  const size_t o_sc = lay.take(sizeof(int) * NB * std::max<size_t>(q, 1));
+  const size_t o_st = lay.take(sizeof(int) * NB);
+  const size_t o_l = lay.take(sizeof(int) * NB);
+  const size_t o_ke = lay.take(sizeof(int) * NB);
+  const size_t o_sw = lay.take(sizeof(int) * NB);
+  const size_t o_I = lay.take(sizeof(int) * NB * L);
+  const size_t o_J = lay.take(sizeof(int) * NB * L);
+  const size_t o_U = lay.take(sizeof(double) * NB * L * L);
+  const size_t o_sg = lay.take(sizeof(float) * NB * L);
+  const size_t o_er = lay.take(sizeof(double) * NB);
+  j->bytes = lay.off;
+  if ((int)ctx->jobs.size() >= ctx->max_slots || ctx->free_slots.empty() ||
+      (ctx->budget && ctx->used_bytes + j->bytes > ctx->budget)) {
+    delete j;
+    return fail(ctx, LRA_EBUSY, "no free slot or memory budget exhausted");
+  }
+  assign_stream(ctx, j);
+  if ((e = cudaMallocAsync(reinterpret_cast<void**>(&j->dmem), j->bytes, j->stream))) {
+    ctx->stream_load[j->stream_idx]--;
+    delete j;
+    return cuda_fail(ctx, e, "cudaMallocAsync");
+  }
+  unsigned char* base = j->dmem;
+  j->js = reinterpret_cast<JobStatus*>(base + o_js);
+  j->b_queue = reinterpret_cast<int*>(base + o_queue);
+  j->b_blocks = reinterpret_cast<long long*>(base + o_blocks);
+  j->b_jcand = reinterpret_cast<int*>(base + o_jc);
+  j->b_srow = reinterpret_cast<int*>(base + o_sr);
+  j->b_scol = reinterpret_cast<int*>(base + o_sc);
+  j->b_status = reinterpret_cast<int*>(base + o_st);
+  j->b_l = reinterpret_cast<int*>(base + o_l);
+  j->b_keff = reinterpret_cast<int*>(base + o_ke);
+  j->b_swaps = reinterpret_cast<int*>(base + o_sw);
+  j->b_I = reinterpret_cast<int*>(base + o_I);
+  j->b_J = reinterpret_cast<int*>(base + o_J);
+  j->b_U = reinterpret_cast<double*>(base + o_U);
+  j->b_sigma = reinterpret_cast<float*>(base + o_sg);
+  j->b_err = reinterpret_cast<double*>(base + o_er);
+  j->slot = ctx->free_slots.back();
+  ctx->free_slots.pop_back();
+  ctx->used_bytes += j->bytes;
+  cudaStream_t s = j->stream;
+  JobStatus init{};
+  init.status = LRA_OK;
+  init.converged = 1;
+  BatchArgs a{};
+  a.src = j->src;
+  a.blocks = j->b_blocks;
+  a.n_blocks = nb;
+  a.jcand = j->b_jcand;
+  a.srow = j->b_srow;
+  a.scol = j->b_scol;
+  a.q = p->sample;
+  a.l_init = p->l_init;
+  a.l_max = p->l_max;
+  a.k_max = p->k_max;
+  a.sweeps = p->sweeps;
+  a.max_swaps = p->max_swaps > 0 ? p->max_swaps : 64 * p->l_max;
+  a.tol = (float)p->tol;
+  a.delta = (float)p->delta;
+  a.queue = j->b_queue;
+  a.out_status = j->b_status;
+  a.out_l = j->b_l;
+  a.out_keff = j->b_keff;
+  a.out_swaps = j->b_swaps;
+  a.out_I = j->b_I;
+  a.out_J = j->b_J;
+  a.out_U = j->b_U;
+  a.out_sigma = j->b_sigma;
+  a.out_err = j->b_err;
+  a.js = j->js;
+  static_assert(sizeof(lra_block) == 4 * sizeof(long long), "lra_block layout");
+  if ((e = cudaEventCreate(&j->ev_start)) || (e = cudaEventCreate(&j->ev_end)) ||
+      (e = cudaMemcpyAsync(j->js, &init, sizeof(init), cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemsetAsync(j->b_queue, 0, sizeof(int), s)) ||
+      (e = cudaMemsetAsync(j->b_err, 0, sizeof(double) * NB, s)) ||
+      (e = cudaMemsetAsync(j->b_keff, 0, sizeof(int) * NB, s)) ||
+      (e = cudaMemcpyAsync(j->b_blocks, blocks, sizeof(lra_block) * NB, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(j->b_jcand, p->cand_J, sizeof(int) * NB * L, cudaMemcpyHostToDevice, s)) ||
+      (q > 0 && ((e = cudaMemcpyAsync(j->b_srow, p->sample_rows, sizeof(int) * NB * q, cudaMemcpyHostToDevice, s)) ||
+                 (e = cudaMemcpyAsync(j->b_scol, p->sample_cols, sizeof(int) * NB * q, cudaMemcpyHostToDevice, s)))) ||
+      (e = cudaEventRecord(j->ev_start, s)) || (e = launch_batch(a, ctx->sms, s)) ||
+      (e = cudaMemcpyAsync(ctx->pinned + j->slot, j->js, sizeof(JobStatus), cudaMemcpyDeviceToHost, s)) ||
+      (e = cudaEventRecord(j->ev_end, s))) {
+    cudaStreamSynchronize(s);
+    release_job(ctx, j);
+    return cuda_fail(ctx, e, "batch enqueue");
+  }
+  j->launches = 1;
+  j->id = ctx->next_id++;
+  ctx->jobs[j->id] = j;
+  *out = j->id;
+  return LRA_OK;
+}
+
+lra_status lra_cross_fetch_batch(lra_ctx* ctx, lra_job id, const lra_batch_out* out) {
+  if (!ctx || !out) return LRA_EINVAL;
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  Job* j = find_job(ctx, id);
+  if (!j) return fail(ctx, LRA_ENOTFOUND, "unknown job");
+  if (!j->batch) return fail(ctx, LRA_EINVAL, "not a batch job: use lra_cross_fetch_cur");
+  cudaSetDevice(ctx->device);
+  cudaError_t e = cudaEventSynchronize(j->ev_end);
+  if (e) return cuda_fail(ctx, e, "cudaEventSynchronize");
+  lra_status result = (lra_status)ctx->pinned[j->slot].status;
+  const size_t NB = (size_t)j->n_blocks, L = (size_t)j->b_lmax;
+  struct Piece { void* dst; const void* src; size_t bytes; };
+  Piece pieces[] = {
+      {out->status, j->b_status, sizeof(int) * NB}, {out->l, j->b_l, sizeof(int) * NB},
+      {out->k_eff, j->b_keff, sizeof(int) * NB},    {out->swaps, j->b_swaps, sizeof(int) * NB},
+      {out->I, j->b_I, sizeof(int) * NB * L},       {out->J, j->b_J, sizeof(int) * NB * L},
+      {out->U, j->b_U, sizeof(double) * NB * L * L}, {out->sigma, j->b_sigma, sizeof(float) * NB * L},
+      {out->est_err, j->b_err, sizeof(double) * NB},
+  };
+  for (const Piece& pc : pieces) {
+    if (!pc.dst) continue;
+    if ((e = cudaMemcpyAsync(pc.dst, pc.src, pc.bytes, cudaMemcpyDefault, j->stream))) break;
+  }
+  if (!e) e = cudaStreamSynchronize(j->stream);
+  if (e) result = cuda_fail(ctx, e, "fetch copy");
+  ctx->jobs.erase(id);
+  release_job(ctx, j);
+  return result;
 }
 
 }  // extern "C"

@@ -56,3 +56,13 @@ def sampled_error(src64, C, U, R, rows, cols):
 def error_ok(err_gpu, err_oracle):
     """Within 1.05x of the FP64 oracle's error, or 1e-5 absolute."""
     return err_gpu <= max(1.05 * err_oracle, 1e-5)
+
+
+class SubSource:
+    """The block M[row0 : row0 + m, col0 : col0 + n] of an oracle source."""
+
+    def __init__(self, src, row0, m, col0, n):
+        self.src, self.row0, self.col0, self.m, self.n = src, int(row0), int(col0), int(m), int(n)
+
+    def block(self, rows, cols):
+        return self.src.block(self.row0 + np.asarray(rows), self.col0 + np.asarray(cols))

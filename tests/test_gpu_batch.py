@@ -1,0 +1,91 @@
+"""Batched C-A (one persistent launch over many far-field blocks of the
+1/|x - y| kernel, Section 9) against the FP64 oracle's rank-adaptive rule."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from tests._parity import SubSource, error_ok
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1611_01391_gb300 as L  # noqa: E402
+from paper_1611_01391_gb300.api import make_batch_params, solve_batch  # noqa: E402
+
+L_INIT, L_MAX, K_MAX, SWEEPS, TOL, Q = 16, 96, 64, 2, 1e-6, 32
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = L.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def case():
+    pts, blocks = W.octree_block_pairs(W.BASE_SEED + 4, npoints=1 << 17, leaf=512, n_pairs=40)
+    jc, sr, sc = W.block_candidates(W.BASE_SEED + 5, blocks, L_MAX, Q)
+    return pts, blocks, jc, sr, sc
+
+
+def _run(ctx, pts, blocks, jc, sr, sc):
+    d = torch.from_numpy(pts).cuda()
+    src = L.make_source("invdist", x=d, y=d)
+    p, keep = make_batch_params(L_INIT, L_MAX, K_MAX, SWEEPS, TOL, jc, sr, sc)
+    return solve_batch(ctx, src, blocks, p, L_MAX)
+
+
+def _nucleus(r, b):
+    l = int(r.l[b])
+    return r.I[b, :l], r.J[b, :l], r.U[b].ravel()[: l * l].reshape(l, l).astype(np.float64)
+
+
+def test_batch_error_vs_oracle(ctx, case):
+    pts, blocks, jc, sr, sc = case
+    r = _run(ctx, pts, blocks, jc, sr, sc)
+    assert np.all(r.status == 0)
+    s64 = O.InvDist(pts, pts, "fp64")
+    same_rank = 0
+    for b, (r0, m, c0, n) in enumerate(blocks):
+        sub = SubSource(s64, r0, m, c0, n)
+        A = sub.block(np.arange(m), np.arange(n))
+        I, J, U = _nucleus(r, b)
+        err = np.linalg.norm(A - A[:, J] @ U @ A[I, :]) / np.linalg.norm(A)
+        oI, oJ, oU, ok, osig, ol, osw = O.cross_approximation_adaptive(sub, jc[b], L_INIT, L_MAX, K_MAX,
+                                                                       SWEEPS, TOL)
+        oerr = np.linalg.norm(A - A[:, oJ] @ oU @ A[oI, :]) / np.linalg.norm(A)
+        assert error_ok(err, oerr), (b, err, oerr)
+        same_rank += int(r.k_eff[b] == ok)
+        # the device's Appendix F estimate equals the FP64 one on its own factors
+        est = O.sampled_residual(sub, A[:, J], U, A[I, :], sr[b], sc[b])["rel"]
+        assert r.est_err[b] == pytest.approx(est, rel=1e-3, abs=1e-9)
+    assert same_rank >= 0.8 * len(blocks)
+
+
+def test_batch_subset_is_bit_identical(ctx, case):
+    """Each block's result does not depend on which other blocks share the
+    launch or which cluster picked it up."""
+    pts, blocks, jc, sr, sc = case
+    a = _run(ctx, pts, blocks, jc, sr, sc)
+    sel = np.arange(0, len(blocks), 3)
+    b = _run(ctx, pts, blocks[sel], jc[sel], sr[sel], sc[sel])
+    for name in ("l", "k_eff", "I", "J", "U", "est_err"):
+        np.testing.assert_array_equal(getattr(a, name)[sel], getattr(b, name))
+
+
+def test_batch_rejects_invalid_blocks(ctx, case):
+    pts, blocks, jc, sr, sc = case
+    bad = blocks.copy()
+    bad[0, 1] = 4096                     # side above 2048
+    with pytest.raises(L.LraError) as e:
+        _run(ctx, pts, bad, jc, sr, sc)
+    assert e.value.code == L.LRA_EINVAL
+    jbad = jc.copy()
+    jbad[1, 1] = jbad[1, 0]              # repeated candidate column
+    with pytest.raises(L.LraError):
+        _run(ctx, pts, blocks, jbad, sr, sc)

@@ -301,3 +301,29 @@ def test_delta_matrix_is_missed_when_spike_is_not_touched():
     miss = O.sampled_residual(O.Dense(A), res.C, res.U, res.R, np.arange(10), np.arange(10))
     hit = O.sampled_residual(O.Dense(A), res.C, res.U, res.R, [17], [23])
     assert miss["rel"] < 1e-12 and hit["rel"] >= 1.0
+
+
+# --- rank-adaptive rule (GEPP start on every strip, growing cross) ---------------
+
+def test_adaptive_grows_to_exact_rank_and_recovers():
+    r = 20
+    A = _rank_l(55, 300, 260, r)
+    jc = W.draw_indices(56, 260, 64)
+    I, J, U, k_eff, sigma, l, swaps = O.cross_approximation_adaptive(
+        O.Dense(A), jc, l_init=8, l_max=64, k_max=64, sweeps=2, tol=1e-10)
+    assert l == 32                  # 8 -> 16 -> 32; at 32 the pivots past rank 20 vanish
+    assert k_eff == r
+    C, R = A[:, J], A[I, :]
+    rel = np.linalg.norm(A - C @ U @ R) / np.linalg.norm(A)
+    assert rel < 1e-10
+
+
+def test_adaptive_respects_k_max_and_l_max():
+    A = W.factor_gaussian(57, 200, 180, 60, 0.0).astype(np.float64)
+    jc = W.draw_indices(58, 180, 48)
+    I, J, U, k_eff, sigma, l, swaps = O.cross_approximation_adaptive(
+        O.Dense(A), jc, l_init=12, l_max=48, k_max=30, sweeps=1, tol=1e-12)
+    assert l == 48 and k_eff == 30
+    s = np.linalg.svd(A, compute_uv=False)
+    err = np.linalg.norm(A - A[:, J] @ U @ A[I, :])
+    assert err >= np.sqrt(np.sum(s[30:] ** 2)) * (1 - 1e-9)     # Lemma 2.3

@@ -106,6 +106,163 @@ def draw_indices(seed: int, n: int, l: int, sort: bool = False) -> np.ndarray:
     return np.sort(idx) if sort else idx
 
 
+def morton3(ix, iy, iz, bits):
+    """Interleave the bits of three integer coordinate arrays (z-order)."""
+    code = np.zeros(ix.shape, dtype=np.int64)
+    for b in range(bits):
+        code |= ((ix >> b) & 1).astype(np.int64) << (3 * b + 2)
+        code |= ((iy >> b) & 1).astype(np.int64) << (3 * b + 1)
+        code |= ((iz >> b) & 1).astype(np.int64) << (3 * b)
+    return code
+
+
+def octree_block_pairs(seed: int, npoints: int = 1 << 20, leaf: int = 2048, n_pairs: int = 4096,
+                       eta: float = 1.0, depth: int = 6, min_size: int = 64):
+    """Far-field blocks of the kernel 1/|x - y| on a point cloud (the
+    multipole setting of Section 9).
+
+    Points are uniform in [0,1)^3 and sorted in z-order at ``depth`` levels,
+    so every octree box owns a contiguous range of the sorted array.  A box
+    is split while it holds more than ``leaf`` points.  A pair (X, Y) of
+    boxes of one level is admissible when max(diam X, diam Y) <= eta
+    dist(X, Y) (diam = box diagonal, dist = distance between the boxes); the
+    candidate blocks are the admissible pairs whose parents are not
+    admissible (the interaction lists of the adaptive tree) with between
+    ``min_size`` and ``leaf`` points on each side.  ``n_pairs`` of them are drawn without
+    replacement.
+
+    Returns (points (npoints x 3, FP32, sorted), blocks (n_pairs x 4 int64:
+    row0, m, col0, n as ranges of the sorted point array))."""
+    rng = rng_for(seed)
+    pts = rng.random((npoints, 3), dtype=np.float32)
+    cells = np.minimum((pts * (1 << depth)).astype(np.int64), (1 << depth) - 1)
+    code = morton3(cells[:, 0], cells[:, 1], cells[:, 2], depth)
+    order = np.argsort(code, kind="stable")
+    pts = pts[order]
+    code = code[order]
+
+    def box_range(level, key):
+        shift = 3 * (depth - level)
+        lo = key << shift
+        hi = (key + 1) << shift
+        return int(np.searchsorted(code, lo, "left")), int(np.searchsorted(code, hi, "left"))
+
+    def box_geom(level, key):
+        w = 1.0 / (1 << level)
+        ix = iy = iz = 0
+        for b in range(level):
+            ix |= ((key >> (3 * b + 2)) & 1) << b
+            iy |= ((key >> (3 * b + 1)) & 1) << b
+            iz |= ((key >> (3 * b)) & 1) << b
+        return np.array([ix, iy, iz]) * w, w
+
+    def admissible(g1, g2):
+        (c1, w1), (c2, w2) = g1, g2
+        gap = np.maximum(0.0, np.maximum(c1 - (c2 + w2), c2 - (c1 + w1)))
+        dist = float(np.sqrt(np.sum(gap * gap)))
+        diam = float(np.sqrt(3.0)) * max(w1, w2)
+        return dist > 0.0 and diam <= eta * dist
+
+    # adaptive tree: boxes per level that exist (and are split further)
+    levels = {0: [0]}
+    split = {}
+    for level in range(0, depth):
+        split[level] = []
+        for key in levels[level]:
+            a, b = box_range(level, key)
+            if b - a > leaf:
+                split[level].append(key)
+        levels[level + 1] = [(k << 3) | c for k in split[level] for c in range(8)
+                             if box_range(level + 1, (k << 3) | c)[1] > box_range(level + 1, (k << 3) | c)[0]]
+    cands = []
+    for level in range(1, depth + 1):
+        boxes = levels.get(level, [])
+        geo = {k: box_geom(level, k) for k in boxes}
+        rng_ = {k: box_range(level, k) for k in boxes}
+        parents = {}
+        for k in boxes:
+            parents.setdefault(k >> 3, []).append(k)
+        pkeys = sorted(parents)
+        pgeo = {p: box_geom(level - 1, p) for p in pkeys}
+        for i, p in enumerate(pkeys):
+            for q in pkeys:
+                if admissible(pgeo[p], pgeo[q]):
+                    continue  # handled at the parents' level
+                for x in parents[p]:
+                    for y in parents[q]:
+                        if x == y or not admissible(geo[x], geo[y]):
+                            continue
+                        (a0, a1), (b0, b1) = rng_[x], rng_[y]
+                        if min_size <= a1 - a0 <= leaf and min_size <= b1 - b0 <= leaf:
+                            cands.append((a0, a1 - a0, b0, b1 - b0))
+    cands = np.array(cands, dtype=np.int64)
+    pick = rng.choice(len(cands), size=min(n_pairs, len(cands)), replace=False)
+    return pts, cands[np.sort(pick)]
+
+
+def block_candidates(seed: int, blocks: np.ndarray, l_max: int, q: int):
+    """Per block: l_max distinct candidate columns (initial J and the columns
+    added when the cross grows) and q sample rows / q sample columns for the
+    Appendix F estimate, all local to the block, drawn without replacement."""
+    rng = rng_for(seed)
+    nb = len(blocks)
+    jc = np.zeros((nb, l_max), np.int32)
+    sr = np.zeros((nb, q), np.int32)
+    sc = np.zeros((nb, q), np.int32)
+    for b, (r0, m, c0, n) in enumerate(blocks):
+        jc[b] = rng.choice(n, size=l_max, replace=False) if n >= l_max else np.resize(rng.permutation(n), l_max)
+        sr[b] = np.sort(rng.choice(m, size=q, replace=False))
+        sc[b] = np.sort(rng.choice(n, size=q, replace=False))
+    return jc, sr, sc
+
+
+def serving_requests(seed: int, count: int, min_side: int = 256, max_side: int = 16384,
+                     ks=(8, 16, 32, 64), sweeps: int = 4, sample: int = 256):
+    """A stream of independent LRA requests for the served form.
+
+    Each request: generator uniform over {Cauchy 1/(x - y) with x ~ U[0,1],
+    y ~ U[2,3]; Gaussian exp(-|x - y|^2 / 0.25) on points in U[0,1]^3;
+    1/|x - y| between the clusters U[0,1]^3 and U[2,3]^3}, m and n
+    log-uniform in [min_side, max_side], k uniform over ``ks``,
+    l = min(96, ceil(1.5 k)), a random initial column set and a
+    sample x sample error sample."""
+    rng = rng_for(seed)
+    reqs = []
+    lo, hi = np.log(min_side), np.log(max_side)
+    for _ in range(count):
+        kind = ("cauchy", "gauss", "invdist")[int(rng.integers(0, 3))]
+        m = int(np.exp(rng.uniform(lo, hi)))
+        n = int(np.exp(rng.uniform(lo, hi)))
+        k = int(ks[int(rng.integers(0, len(ks)))])
+        l = min(96, int(np.ceil(1.5 * k)))
+        if kind == "cauchy":
+            x = rng.random(m, dtype=np.float32)
+            y = (rng.random(n, dtype=np.float32) + np.float32(2.0)).astype(np.float32)
+            h = 0.0
+        elif kind == "gauss":
+            x = rng.random((m, 3), dtype=np.float32)
+            y = rng.random((n, 3), dtype=np.float32)
+            h = 0.5
+        else:
+            x = rng.random((m, 3), dtype=np.float32)
+            y = (rng.random((n, 3), dtype=np.float32) + np.float32(2.0)).astype(np.float32)
+            h = 0.0
+        J0 = rng.choice(n, size=l, replace=False).astype(np.int32)
+        q = min(sample, m)
+        s = min(sample, n)
+        rows = np.sort(rng.choice(m, size=q, replace=False)).astype(np.int32)
+        cols = np.sort(rng.choice(n, size=s, replace=False)).astype(np.int32)
+        reqs.append(dict(kind=kind, m=m, n=n, k=k, l=l, sweeps=sweeps, x=x, y=y, h=h, J0=J0,
+                         rows=rows, cols=cols))
+    return reqs
+
+
+def poisson_arrivals(seed: int, count: int, rate: float) -> np.ndarray:
+    """Arrival times (seconds) of a Poisson process of the given rate."""
+    rng = rng_for(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, size=count))
+
+
 def delta_matrix(m: int, n: int, i: int, j: int) -> np.ndarray:
     """The hard input of Appendix E: zeros except a single unit entry."""
     a = np.zeros((m, n))
