@@ -194,7 +194,7 @@ for b in order:
     sub = Sub(r0, m, c0, n_)
     I, J, U, ke, sg, l, sw = O.cross_approximation_adaptive(sub, jc[b], wl["l_init"], wl["l_max"], wl["k_max"],
                                                             wl["sweeps"], wl["tol"])
-    O.sampled_residual(sub, sub.block(sr[b], J), U, sub.block(I, sc[b]), sr[b], sc[b])
+    O.sampled_residual(sub, sub.block(np.arange(m), J), U, sub.block(I, np.arange(n_)), sr[b], sc[b])
     times.append(time.perf_counter() - t1); n += 1
     if (time.perf_counter() - t0 > {budget} and n >= {min_n}) or n >= {max_n}:
         break
@@ -471,7 +471,7 @@ def run_batch(args, wl_name):
     nb = len(blocks)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
-    ctx = L.Context(local, stream=stream.cuda_stream)
+    ctx = L.Context(local, max_slots=wl["plain_subset"] + 8, stream=stream.cuda_stream)
     d = torch.from_numpy(pts).to(dev)
     src = L.make_source("invdist", x=d, y=d)
     p, keep = make_batch_params(wl["l_init"], wl["l_max"], wl["k_max"], wl["sweeps"], wl["tol"], jc, sr, sc)

@@ -50,6 +50,7 @@ def test_batch_error_vs_oracle(ctx, case):
     r = _run(ctx, pts, blocks, jc, sr, sc)
     assert np.all(r.status == 0)
     s64 = O.InvDist(pts, pts, "fp64")
+    s32 = O.InvDist(pts, pts, "fp32")
     same_rank = 0
     for b, (r0, m, c0, n) in enumerate(blocks):
         sub = SubSource(s64, r0, m, c0, n)
@@ -60,11 +61,26 @@ def test_batch_error_vs_oracle(ctx, case):
                                                                        SWEEPS, TOL)
         oerr = np.linalg.norm(A - A[:, oJ] @ oU @ A[oI, :]) / np.linalg.norm(A)
         assert error_ok(err, oerr), (b, err, oerr)
+        # the kept rank is the count of cross singular values above tol
+        # sigma_1: check it on the device's own cross (FP64 SVD of the same
+        # FP32 entries), unless a singular value sits within 2% of the cut
+        sg = np.linalg.svd(s32.block(r0 + I, c0 + J), compute_uv=False)
+        cut = TOL * sg[0]
+        if not np.any(np.abs(sg - cut) < 0.02 * cut):
+            assert r.k_eff[b] == min(K_MAX, int(np.sum(sg > cut))), (b, r.k_eff[b], sg / sg[0])
+        # against the oracle the rank may differ where FP32 entries move a
+        # singular value across the cut (the oracle itself changes rank on 8
+        # of these 40 blocks between FP32 and FP64 entries)
+        assert abs(int(r.k_eff[b]) - ok) <= 2, (b, r.k_eff[b], ok)
         same_rank += int(r.k_eff[b] == ok)
-        # the device's Appendix F estimate equals the FP64 one on its own factors
-        est = O.sampled_residual(sub, A[:, J], U, A[I, :], sr[b], sc[b])["rel"]
+        # the device's Appendix F estimate equals the FP64-arithmetic one on
+        # its own factors and the same FP32 entries (the residual is ~1e-7 |M|,
+        # so FP32 rounding of M alone moves it by percents)
+        sub32 = SubSource(s32, r0, m, c0, n)
+        est = O.sampled_residual(sub32, sub32.block(np.arange(m), J), U, sub32.block(I, np.arange(n)),
+                                 sr[b], sc[b])["rel"]
         assert r.est_err[b] == pytest.approx(est, rel=1e-3, abs=1e-9)
-    assert same_rank >= 0.8 * len(blocks)
+    assert same_rank >= 0.7 * len(blocks)
 
 
 def test_batch_subset_is_bit_identical(ctx, case):
