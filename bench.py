@@ -47,7 +47,7 @@ WORKLOADS = {
     # Poisson stream of requests: sides log-uniform in 256..16384, k in {8,16,32,64},
     # Cauchy / Gaussian / 1/|x - y| generators, 40 GB admission budget
     "serve": dict(form="serve", count=400, min_side=256, max_side=16384, budget_gb=40, slots=64,
-                  streams=8, rates=(0.5, 0.8, 0.95), seed_off=5, plain_subset=400),
+                  streams=32, rates=(0.5, 0.8, 0.95), seed_off=5, plain_subset=400),
 }
 
 
@@ -668,6 +668,9 @@ def _pct(xs, q):
 
 
 def run_serve(args, wl_name):
+    # more hardware work queues than CUDA's default 8, so that the jobs of
+    # 32 streams do not share queues (set before the process touches CUDA)
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     import numpy as np
     import torch
     import paper_1611_01391_gb300 as L

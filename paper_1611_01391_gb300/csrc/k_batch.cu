@@ -21,10 +21,10 @@
 //   * Rank adaptivity: after the sweeps, if the last pivot of the final
 //     vertical step exceeds tol times the first, the cross grows (x2, up to
 //     l_max) with the block's next candidate columns and the sweeps repeat.
-//   * Nucleus: one-sided Jacobi SVD of the final cross in double-float
-//     arithmetic on one CTA (an FP32 SVD cannot resolve singular values near
-//     tol sigma_1 = 1e-6 sigma_1), k_eff = min(k_max, #{sigma_j > tol
-//     sigma_1}), U = (X_k)^+.
+//   * Nucleus: SVD of the final cross (QR with column pivoting, then
+//     one-sided Jacobi) in double-float arithmetic on one CTA (an FP32 SVD
+//     cannot resolve singular values near tol sigma_1 = 1e-6 sigma_1),
+//     k_eff = min(k_max, #{sigma_j > tol sigma_1}), U = (X_k)^+ in FP64.
 //   * Appendix F estimate on a q x q sample of each block, with compensated
 //     FP32 products and FP64 sums.
 #include <cooperative_groups.h>
@@ -65,13 +65,12 @@ struct BatchSmem {
   int swaps;
   int keff;
   int lnew;
-  int status_aux;
   double esum[2][kBT / 32];
 };
 // the nucleus (W, V, sigma, 1/sigma^2, order) and the estimate's operands
 // reuse the strip area once the sweeps are over
-static_assert(2 * kMaxL * kMaxL * sizeof(dd) + kMaxL * (sizeof(double) + sizeof(dd) + sizeof(int)) <=
-                  sizeof(BatchSmem::B), "nucleus area");
+static_assert(2 * kMaxL * kMaxL * sizeof(dd) + kMaxL * (sizeof(double) + sizeof(dd) + sizeof(int)) +
+                      sizeof(SvdScratch) <= sizeof(BatchSmem::B), "nucleus area");
 static_assert(sizeof(float) * (2 * kMaxL * kMaxL + 4 * kMaxQ * kMaxL) <= sizeof(BatchSmem::B),
               "estimate area");
 
@@ -317,14 +316,25 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kBT, 1) batch_kern
         a.out_l[b] = l;
         a.out_swaps[b] = s->swaps;
       }
+      {  // defined contents past the l x l nucleus (and everywhere on failure)
+        const int lu = ok ? l : 0;
+        double* Ub = a.out_U + (size_t)b * a.l_max * a.l_max;
+        for (int e = lu * lu + tid; e < a.l_max * a.l_max; e += kBT) Ub[e] = 0.0;
+        for (int t = lu + tid; t < a.l_max; t += kBT) {
+          a.out_sigma[(size_t)b * a.l_max + t] = 0.0f;
+          a.out_I[(size_t)b * a.l_max + t] = -1;
+          a.out_J[(size_t)b * a.l_max + t] = -1;
+        }
+      }
       if (ok) {
         // nucleus on this CTA (double-float Jacobi SVD); the strip area is
         // free now.  X is scaled by a power of two into [0.5, 1).
         dd* W = reinterpret_cast<dd*>(s->B);
-        dd* V = W + kMaxL * kMaxL;
-        double* sig = reinterpret_cast<double*>(V + kMaxL * kMaxL);
+        dd* Z = W + kMaxL * kMaxL;
+        double* sig = reinterpret_cast<double*>(Z + kMaxL * kMaxL);
         dd* inv2 = reinterpret_cast<dd*>(sig + kMaxL);
-        int* order = reinterpret_cast<int*>(inv2 + kMaxL);
+        SvdScratch* sc = reinterpret_cast<SvdScratch*>(inv2 + kMaxL);
+        int* order = reinterpret_cast<int*>(sc + 1);
         if (tid == 0) s->lnew = 0;
         __syncthreads();
         float amax = 0.0f;
@@ -333,7 +343,6 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kBT, 1) batch_kern
           const float x = entry<KIND>(a.src, row0 + s->Iset[p], col0 + s->Jset[q]);
           amax = fmaxf(amax, fabsf(x));
           W[q * l + p] = dd_make(x);   // column q of X
-          V[q * l + p] = dd_make(p == q ? 1.0f : 0.0f);
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
@@ -342,15 +351,15 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kBT, 1) batch_kern
           frexpf(amax, &ex);
           atomicMax(&s->lnew, ex + 1024);
         }
-        for (int t = tid; t < a.l_max; t += kBT) {
-          a.out_I[(size_t)b * a.l_max + t] = t < l ? s->Iset[t] : -1;
-          a.out_J[(size_t)b * a.l_max + t] = t < l ? s->Jset[t] : -1;
+        for (int t = tid; t < l; t += kBT) {
+          a.out_I[(size_t)b * a.l_max + t] = s->Iset[t];
+          a.out_J[(size_t)b * a.l_max + t] = s->Jset[t];
         }
         __syncthreads();
         const int ex = s->lnew ? s->lnew - 1024 : 0;
         for (int e = tid; e < l * l; e += kBT) W[e].hi = ldexpf(W[e].hi, -ex);
         __syncthreads();
-        jacobi_dd<kBT>(W, V, l, &s->status_aux);
+        svd_dd<kBT>(W, Z, l, sc);
         jacobi_sigma<kBT>(W, l, sig, order);
         if (tid == 0) {
           const double s1 = sig[order[0]];
@@ -368,7 +377,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kBT, 1) batch_kern
         }
         __syncthreads();
         double* Ub = a.out_U + (size_t)b * a.l_max * a.l_max;
-        nucleus_from_svd<kBT>(W, V, l, s->keff, order, inv2,
+        nucleus_from_svd<kBT>(W, Z, sc->perm, l, s->keff, order, inv2,
                               [&](int e, double v) { Ub[e] = ldexp(v, -ex); });
         __syncthreads();
         // Appendix F estimate on the q x q sample of this block

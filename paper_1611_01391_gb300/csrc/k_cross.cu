@@ -1,12 +1,11 @@
 // Nucleus of the CUR approximation (Primitive Algorithm, stages 2-3 of
-// Section 6.5): the l x l CUR generator X = M[I, J], its SVD X = P S Q^T, the
-// rank-k truncation and U = Q_k S_k^{-1} P_k^T.
+// Section 6.5): the l x l CUR generator X = M[I, J], its SVD, the rank-k
+// truncation and U = (X_k)^+.
 //
-// The SVD is the one-sided Jacobi method of Hestenes (1958) in double-float
-// arithmetic (svd_dd.cuh): the columns of W = X V are orthogonalised in
-// place, sigma_b = ||W[:, b]||, P[:, b] = W[:, b] / sigma_b and Q = V.  X is
-// first scaled by a power of two so that max |X| lies in [0.5, 1) (exact);
-// sigma and U are scaled back.
+// The SVD (svd_dd.cuh) is QR with column pivoting followed by one-sided
+// Jacobi on R^T, in double-float arithmetic.  X is first scaled by a power
+// of two so that max |X| lies in [0.5, 1) (exact); sigma and U are scaled
+// back.
 #include <cfloat>
 
 #include "lra_kernels.h"
@@ -24,12 +23,12 @@ nucleus_kernel(const float* __restrict__ C, const int* __restrict__ I, int l, in
   if (js->status != LRA_OK) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   dd* W = reinterpret_cast<dd*>(smem_raw);           // column b at W + b*l
-  dd* V = W + (size_t)l * l;                          // column b at V + b*l
-  double* sig = reinterpret_cast<double*>(V + (size_t)l * l);  // l
+  dd* Z = W + (size_t)l * l;                          // column b at Z + b*l
+  double* sig = reinterpret_cast<double*>(Z + (size_t)l * l);  // l
   dd* inv2 = reinterpret_cast<dd*>(sig + kMaxL);      // l
-  int* order = reinterpret_cast<int*>(inv2 + kMaxL);  // l: order[rank] = column
-  int* flag = order + kMaxL;
-  int* keff_s = flag + 1;
+  SvdScratch* sc = reinterpret_cast<SvdScratch*>(inv2 + kMaxL);
+  int* order = reinterpret_cast<int*>(sc + 1);        // l: order[rank] = column
+  int* keff_s = order + kMaxL;
   int* scale_e = keff_s + 1;
 
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -53,10 +52,9 @@ nucleus_kernel(const float* __restrict__ C, const int* __restrict__ I, int l, in
   for (int e = tid; e < l * l; e += nthr) {
     const int a = e / l, b = e - a * l;             // X[a][b] = C[I[a]][b]
     W[(size_t)b * l + a] = dd_make(ldexpf(C[(size_t)__ldg(I + a) * l + b], -ex));
-    V[(size_t)b * l + a] = dd_make((a == b) ? 1.0f : 0.0f);
   }
   __syncthreads();
-  jacobi_dd<kNucThreads>(W, V, l, flag);
+  svd_dd<kNucThreads>(W, Z, l, sc);
   jacobi_sigma<kNucThreads>(W, l, sig, order);
   if (tid == 0) {
     const double s1 = sig[order[0]];
@@ -74,14 +72,18 @@ nucleus_kernel(const float* __restrict__ C, const int* __restrict__ I, int l, in
   }
   __syncthreads();
   const int ke = *keff_s;
-  nucleus_from_svd<kNucThreads>(W, V, l, ke, order, inv2,
+  nucleus_from_svd<kNucThreads>(W, Z, sc->perm, l, ke, order, inv2,
                                 [&](int e, double v) { U[e] = ldexp(v, -ex); });
 }
 
 // X^{-1} of the cross X[a][b] = S[pos[a]][b] of an N x l strip (element
-// (i, t) at strip[i*si + t*st]), by Gauss-Jordan elimination with partial
-// pivoting on [X | I] in FP64 (one CTA).  Output row-major.  A zero pivot
-// sets LRA_ESINGULAR, a non-finite entry LRA_ENONFINITE.
+// (i, t) at strip[i*si + t*st]), by in-place Gauss-Jordan elimination with
+// partial pivoting in FP64 on one CTA (Golub & Van Loan, 3.4; l^3 FMAs
+// against 1.5 l^3 for elimination on [X | I]).  Step t: the pivot is the
+// largest |A[r][t]|, r >= t (smallest r on ties), rows t and p are swapped,
+// column t is replaced by the column of the inverse it produces, and every
+// other row is updated.  The row swaps are undone as column swaps at the
+// end.  A zero pivot sets LRA_ESINGULAR, a non-finite entry LRA_ENONFINITE.
 constexpr int kInvThreads = 512;
 
 __global__ void __launch_bounds__(kInvThreads, 1)
@@ -89,24 +91,20 @@ cross_inverse_kernel(const float* __restrict__ strip, long long si, long long st
                      const int* __restrict__ pos, int l, double* __restrict__ xinv, JobStatus* js) {
   if (js->status != LRA_OK || js->stop) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int w = 2 * l;
-  double* A = reinterpret_cast<double*>(smem_raw);  // l x 2l, row-major
-  double* f = A + (size_t)l * w;                    // column t before elimination
-  double* recip = f + kMaxL;                        // 1 / pivot of the current step
+  double* A = reinterpret_cast<double*>(smem_raw);  // l x l, row-major
+  double* f = A + (size_t)l * l;                    // column t before the step
+  double* rowt = f + kMaxL;                         // pivot row after scaling
+  double* recip = rowt + kMaxL;                     // 1 / pivot of the current step
   int* piv_row = reinterpret_cast<int*>(recip + 1);
-  int* bad = piv_row + 1;
+  int* swaps = piv_row + 1;                         // row swapped with t at step t
+  int* bad = swaps + kMaxL;
   const int tid = threadIdx.x, nthr = blockDim.x;
   if (tid == 0) *bad = 0;
   __syncthreads();
-  for (int e = tid; e < l * w; e += nthr) {
-    const int a = e / w, b = e - a * w;
-    double v;
-    if (b < l) {
-      v = (double)strip[(long long)__ldg(pos + a) * si + (long long)b * st];
-      if (!(fabs(v) <= DBL_MAX)) *bad = 1;
-    } else {
-      v = (b - l == a) ? 1.0 : 0.0;
-    }
+  for (int e = tid; e < l * l; e += nthr) {
+    const int a = e / l, b = e - a * l;
+    const double v = (double)strip[(long long)__ldg(pos + a) * si + (long long)b * st];
+    if (!(fabs(v) <= DBL_MAX)) *bad = 1;
     A[e] = v;
   }
   __syncthreads();
@@ -114,17 +112,13 @@ cross_inverse_kernel(const float* __restrict__ strip, long long si, long long st
     if (tid == 0) set_status(js, LRA_ENONFINITE);
     return;
   }
-  // Columns < t of the left half are already unit columns, so step t only
-  // touches columns t..2l-1 (width wt).  Magnitudes are compared on their
-  // IEEE bit patterns (integer compares), and row t is scaled by the FP64
-  // reciprocal of the pivot.
   for (int t = 0; t < l; ++t) {
-    if (tid < 32) {  // pivot: largest |A[r][t]|, r >= t (smallest r on ties)
+    if (tid < 32) {  // pivot: largest |A[r][t]|, r >= t, compared on IEEE bit patterns
       unsigned long long best = 0ull;
       int br = l;
       for (int r = t + tid; r < l; r += 32) {
         const unsigned long long k =
-            (unsigned long long)__double_as_longlong(A[(size_t)r * w + t]) & 0x7fffffffffffffffull;
+            (unsigned long long)__double_as_longlong(A[(size_t)r * l + t]) & 0x7fffffffffffffffull;
         if (br == l || k > best) { best = k; br = r; }
       }
 #pragma unroll
@@ -134,10 +128,11 @@ cross_inverse_kernel(const float* __restrict__ strip, long long si, long long st
         if (orr < l && (br == l || ob > best || (ob == best && orr < br))) { best = ob; br = orr; }
       }
       if (tid == 0) {
-        *piv_row = (best != 0ull && br < l) ? br : -1;
-        // one FP64 division for the whole step (all threads dividing would
-        // occupy the FP64 pipe for thousands of cycles)
-        if (br < l && best != 0ull) *recip = 1.0 / A[(size_t)br * w + t];
+        const int p = (best != 0ull && br < l) ? br : -1;
+        *piv_row = p;
+        swaps[t] = p;
+        // one FP64 division for the whole step
+        if (p >= 0) *recip = 1.0 / A[(size_t)p * l + t];
       }
     }
     __syncthreads();
@@ -146,33 +141,50 @@ cross_inverse_kernel(const float* __restrict__ strip, long long si, long long st
       if (tid == 0) set_status(js, LRA_ESINGULAR);
       return;
     }
-    if (p != t)
-      for (int c = t + tid; c < w; c += nthr) {
-        const double x = A[(size_t)t * w + c];
-        A[(size_t)t * w + c] = A[(size_t)p * w + c];
-        A[(size_t)p * w + c] = x;
-      }
-    __syncthreads();
     const double rp = *recip;
-    for (int c = t + tid; c < w; c += nthr) A[(size_t)t * w + c] *= rp;
-    for (int r = tid; r < l; r += nthr) f[r] = (r == t) ? 0.0 : A[(size_t)r * w + t];
+    // multipliers f[r] = A[r][t] of the rows after the swap (row p will hold
+    // the old row t), read before anything is written
+    for (int r = tid; r < l; r += nthr) {
+      const int rr = (r == p) ? t : r;
+      f[r] = (r == t) ? 0.0 : A[(size_t)rr * l + t];
+    }
     __syncthreads();
-    const int wt = w - t;
-    for (int e = tid; e < l * wt; e += nthr) {
-      const int r = e / wt, c = t + (e - r * wt);
-      if (r != t) A[(size_t)r * w + c] = fma(-f[r], A[(size_t)t * w + c], A[(size_t)r * w + c]);
+    // pivot row swapped into place and scaled by 1/pivot, its column t set to
+    // 1/pivot
+    for (int c = tid; c < l; c += nthr) {
+      const double x = A[(size_t)p * l + c];
+      if (p != t) A[(size_t)p * l + c] = A[(size_t)t * l + c];
+      const double y = (c == t) ? rp : x * rp;
+      rowt[c] = y;
+      A[(size_t)t * l + c] = y;
+    }
+    __syncthreads();
+    // A[r][c] -= f[r] rowt[c] for r != t, with A[r][t] starting from 0
+    for (int e = tid; e < l * l; e += nthr) {
+      const int r = e / l, c = e - r * l;
+      if (r == t) continue;
+      const double a = (c == t) ? 0.0 : A[e];
+      A[e] = fma(-f[r], rowt[c], a);
     }
     __syncthreads();
   }
-  for (int e = tid; e < l * l; e += nthr) {
-    const int a = e / l, b = e - a * l;
-    xinv[e] = A[(size_t)a * w + l + b];
+  // undo the row interchanges as column interchanges, last first
+  for (int t = l - 1; t >= 0; --t) {
+    const int p = swaps[t];
+    if (p != t)
+      for (int r = tid; r < l; r += nthr) {
+        const double x = A[(size_t)r * l + t];
+        A[(size_t)r * l + t] = A[(size_t)r * l + p];
+        A[(size_t)r * l + p] = x;
+      }
+    __syncthreads();
   }
+  for (int e = tid; e < l * l; e += nthr) xinv[e] = A[e];
 }
 
 cudaError_t launch_cross_inverse(const float* strip, long long si, long long st, const int* pos,
                                  int l, double* xinv, JobStatus* js, cudaStream_t stream) {
-  const size_t smem = ((size_t)l * 2 * l + kMaxL + 1) * sizeof(double) + 2 * sizeof(int);
+  const size_t smem = ((size_t)l * l + 2 * kMaxL + 1) * sizeof(double) + (kMaxL + 2) * sizeof(int);
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(cross_inverse_kernel,
@@ -187,7 +199,7 @@ cudaError_t launch_cross_inverse(const float* strip, long long si, long long st,
 cudaError_t launch_nucleus(const float* C, const int* I, int l, int k, double rank_tol,
                            double* U, double* sigma, JobStatus* js, cudaStream_t st) {
   const size_t smem = 2 * (size_t)l * l * sizeof(dd) + kMaxL * (sizeof(double) + sizeof(dd)) +
-                      (kMaxL + 3) * sizeof(int);
+                      sizeof(SvdScratch) + (kMaxL + 2) * sizeof(int);
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(nucleus_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -1,22 +1,20 @@
-// One-sided Jacobi SVD of a small square matrix (l <= 96) on one CTA, in
-// double-float arithmetic: every value is an unevaluated pair hi + lo of
-// FP32 numbers (Dekker, "A floating-point technique for extending the
-// available precision", 1971; Knuth TAOCP vol. 2, 4.2.2; Hida, Li & Bailey,
-// "Algorithms for quad-double precision", 2001), carrying about 48
+// Singular value decomposition of a small square matrix (l <= 96) on one
+// CTA, in double-float arithmetic: every value is an unevaluated pair
+// hi + lo of FP32 numbers (Dekker, "A floating-point technique for extending
+// the available precision", 1971; Knuth TAOCP vol. 2, 4.2.2; Hida, Li &
+// Bailey, "Algorithms for quad-double precision", 2001), carrying about 48
 // significant bits.  On this GPU the FP64 pipe issues 1/64 of the FP32 rate,
-// so a double-float FMA (about 15 FP32 instructions) is about 4x cheaper
-// than a native FP64 one.
+// so a double-float multiply-add (10 to 20 FP32 instructions) is several
+// times cheaper than a native FP64 one.
 //
-// Jacobi method: Hestenes' one-sided variant; the columns of W = X V are
-// orthogonalised by plane rotations visited in round-robin order (l/2
-// independent pairs per round, 8 lanes per pair).  The rotation tangent of
-// the symmetric 2 x 2 Jacobi step (Golub & Van Loan, Algorithm 8.5.1) is
-// taken to FP32 accuracy; c = (1 + t^2)^{-1/2} and s = c t are formed in
-// double-float from that t, so every rotation is orthogonal to double-float
-// accuracy and only the speed of convergence depends on t.
+// Method: Householder QR with column pivoting, then Hestenes' one-sided
+// Jacobi on the transposed triangular factor (the preconditioned Jacobi SVD
+// of Drmac & Veselic); dot products are compensated FP32 sums (Dot2).
 #pragma once
 
 #include <cfloat>
+
+#include "lra_internal.cuh"
 
 namespace lra {
 
@@ -77,11 +75,233 @@ __device__ __forceinline__ dd dd_rsqrt_1_2(dd x) {
   return dd_add(y, dd_mul(y, dd{0.5f * r.hi, 0.5f * r.lo}));
 }
 
-// W: column b at W[b*l .. b*l + l) (on entry the columns of X); V: identity
-// on entry.  On exit W = X V with orthogonal columns.  Must be called by all
-// NT threads of the CTA.  `flag` is a shared int.
+// Compensated accumulator of a dot product of double-float vectors: the
+// FP32 running sum s plus the FP32 sum c of every rounding error (the
+// product errors come exactly from the FMA, the sum errors from TwoSum), so
+// s + c carries about twice FP32 precision (Dot2 of Ogita, Rump & Oishi,
+// "Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005, with the
+// low parts of the operands folded into the product error).
+struct dacc {
+  float s, c;
+};
+
+__device__ __forceinline__ void acc_fma(dacc& a, dd x, dd y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  const dd t = two_sum(a.s, p);
+  a.s = t.hi;
+  a.c = __fadd_rn(a.c, __fadd_rn(t.lo, e));
+}
+
+__device__ __forceinline__ dacc acc_add(dacc a, dacc b) {
+  const dd t = two_sum(a.s, b.s);
+  return dacc{t.hi, __fadd_rn(__fadd_rn(a.c, b.c), t.lo)};
+}
+
+__device__ __forceinline__ dd acc_value(dacc a) { return two_sum(a.s, a.c); }
+
+// Sum over the G consecutive lanes of a group (G a power of two <= 32);
+// every lane of the warp must take part.
+template <int G>
+__device__ __forceinline__ dacc acc_group_sum(dacc a) {
+#pragma unroll
+  for (int off = G / 2; off > 0; off >>= 1)
+    a = acc_add(a, dacc{__shfl_xor_sync(0xffffffffu, a.s, off), __shfl_xor_sync(0xffffffffu, a.c, off)});
+  return a;
+}
+
+// c x + s y in double-float: both products with their FMA error terms, one
+// TwoSum for the high parts.
+__device__ __forceinline__ dd dd_lin2(dd c, dd x, dd s, dd y) {
+  const float p1 = __fmul_rn(c.hi, x.hi);
+  float e1 = fmaf(c.hi, x.hi, -p1);
+  e1 = fmaf(c.hi, x.lo, e1);
+  e1 = fmaf(c.lo, x.hi, e1);
+  const float p2 = __fmul_rn(s.hi, y.hi);
+  float e2 = fmaf(s.hi, y.hi, -p2);
+  e2 = fmaf(s.hi, y.lo, e2);
+  e2 = fmaf(s.lo, y.hi, e2);
+  const dd t = two_sum(p1, p2);
+  return two_sum(t.hi, __fadd_rn(t.lo, __fadd_rn(e1, e2)));
+}
+
+// sqrt and reciprocal: FP32 seed, one double-float Newton correction.
+__device__ __forceinline__ dd dd_sqrt(dd a) {
+  if (!(a.hi > 0.0f)) return dd{0.0f, 0.0f};
+  const float y = sqrtf(a.hi);
+  const dd r = dd_add(a, dd_neg(dd_mul(dd_make(y), dd_make(y))));
+  return quick_two_sum(y, __fdiv_rn(r.hi, 2.0f * y));
+}
+
+__device__ __forceinline__ dd dd_recip(dd d) {
+  const float r0 = __frcp_rn(d.hi);
+  const dd e = dd_add(dd_make(1.0f), dd_neg(dd_mul(d, dd_make(r0))));
+  return quick_two_sum(r0, __fmul_rn(r0, e.hi));
+}
+
+// Shared scratch of the SVD below.
+struct SvdScratch {
+  int perm[kMaxL];    // column c of X P is column perm[c] of X
+  dd rdiag[kMaxL];    // diagonal of R
+  dd beta[kMaxL];     // Householder scalars
+  dd nrm[kMaxL];      // squared norms of the trailing columns
+  int piv;
+  int flag;
+};
+
+// Householder QR with column pivoting (Businger & Golub, 1965; Golub & Van
+// Loan, Algorithm 5.4.1) of the l x l matrix A (column c at A[c*l, c*l+l)),
+// in place: on exit the strictly upper part of R is in A (row j of column
+// c > j), its diagonal in sc->rdiag, and the Householder vector v_j in rows
+// j..l-1 of column j, with H_j = I - beta_j v_j v_j^T.  The pivot is the
+// trailing column of largest norm (ties: the smaller column); the norms are
+// recomputed from the updated columns at every step.
 template <int NT>
-__device__ void jacobi_dd(dd* W, dd* V, int l, int* flag) {
+__device__ void qrcp_dd(dd* A, int l, SvdScratch* sc) {
+  constexpr int G = 8, GPW = 32 / G, NG = NT / G;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, gl = lane & (G - 1);
+  for (int c = tid; c < l; c += NT) sc->perm[c] = c;
+  for (int base = warp * GPW; base < l; base += NG) {
+    const int c = base + (lane / G);
+    dacc a{0.f, 0.f};
+    if (c < l)
+      for (int i = gl; i < l; i += G) acc_fma(a, A[c * l + i], A[c * l + i]);
+    a = acc_group_sum<G>(a);
+    if (c < l && gl == 0) sc->nrm[c] = acc_value(a);
+  }
+  __syncthreads();
+  for (int j = 0; j < l; ++j) {
+    if (warp == 0) {
+      float best = -1.0f, bl = 0.0f;
+      int bc = l;
+      for (int c = j + lane; c < l; c += 32) {
+        const dd v = sc->nrm[c];
+        if (v.hi > best || (v.hi == best && v.lo > bl)) {
+          best = v.hi;
+          bl = v.lo;
+          bc = c;
+        }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const float ol = __shfl_xor_sync(0xffffffffu, bl, off);
+        const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
+        if (ob > best || (ob == best && (ol > bl || (ol == bl && oc < bc)))) {
+          best = ob;
+          bl = ol;
+          bc = oc;
+        }
+      }
+      if (lane == 0) sc->piv = bc;
+    }
+    __syncthreads();
+    const int pc = sc->piv;
+    if (pc != j && pc < l) {
+      for (int i = tid; i < l; i += NT) {
+        const dd t = A[j * l + i];
+        A[j * l + i] = A[pc * l + i];
+        A[pc * l + i] = t;
+      }
+      if (tid == 0) {
+        const int t = sc->perm[j];
+        sc->perm[j] = sc->perm[pc];
+        sc->perm[pc] = t;
+        const dd u = sc->nrm[j];
+        sc->nrm[j] = sc->nrm[pc];
+        sc->nrm[pc] = u;
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {  // reflector of rows j..l-1 of column j
+      dacc a{0.f, 0.f};
+      for (int i = j + lane; i < l; i += 32) acc_fma(a, A[j * l + i], A[j * l + i]);
+      a = acc_group_sum<32>(a);
+      if (lane == 0) {
+        const dd n2 = acc_value(a);
+        if (!(n2.hi > 0.0f)) {
+          sc->beta[j] = dd{0.f, 0.f};
+          sc->rdiag[j] = dd{0.f, 0.f};
+        } else {
+          const dd nx = dd_sqrt(n2);
+          const dd x0 = A[j * l + j];
+          const dd alpha = x0.hi >= 0.0f ? dd_neg(nx) : nx;
+          const dd ax0 = x0.hi >= 0.0f ? x0 : dd_neg(x0);
+          A[j * l + j] = dd_add(x0, dd_neg(alpha));
+          sc->beta[j] = dd_recip(dd_add(n2, dd_mul(ax0, nx)));
+          sc->rdiag[j] = alpha;
+        }
+      }
+    }
+    __syncthreads();
+    const dd bj = sc->beta[j];
+    for (int base = j + 1 + warp * GPW; base < l; base += NG) {
+      const int c = base + (lane / G);
+      const bool act = c < l;
+      dacc a{0.f, 0.f};
+      if (act)
+        for (int i = j + gl; i < l; i += G) acc_fma(a, A[j * l + i], A[c * l + i]);
+      a = acc_group_sum<G>(a);
+      const dd sv = dd_mul(bj, acc_value(a));
+      const dd nsv = dd_neg(sv);
+      dacc nn{0.f, 0.f};
+      if (act)
+        for (int i = j + gl; i < l; i += G) {
+          const dd x = dd_lin2(dd_make(1.0f), A[c * l + i], nsv, A[j * l + i]);
+          A[c * l + i] = x;
+          if (i > j) acc_fma(nn, x, x);
+        }
+      nn = acc_group_sum<G>(nn);
+      if (act && gl == 0) sc->nrm[c] = acc_value(nn);
+    }
+    __syncthreads();
+  }
+}
+
+// Q = H_0 H_1 ... H_{l-1} into Z (column c at Z[c*l, c*l+l)) by backward
+// accumulation: Z = I, then Z <- H_j Z for j = l-1 .. 0 (H_j touches rows
+// j.. and, at that point, only columns j..).
+template <int NT>
+__device__ void form_q_dd(const dd* A, int l, const SvdScratch* sc, dd* Z) {
+  constexpr int G = 8, GPW = 32 / G, NG = NT / G;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, gl = lane & (G - 1);
+  for (int e = tid; e < l * l; e += NT) {
+    const int c = e / l, i = e - c * l;
+    Z[e] = dd_make(c == i ? 1.0f : 0.0f);
+  }
+  __syncthreads();
+  for (int j = l - 1; j >= 0; --j) {
+    const dd bj = sc->beta[j];
+    if (bj.hi != 0.0f) {
+      for (int base = j + warp * GPW; base < l; base += NG) {
+        const int c = base + (lane / G);
+        const bool act = c < l;
+        dacc a{0.f, 0.f};
+        if (act)
+          for (int i = j + gl; i < l; i += G) acc_fma(a, A[j * l + i], Z[c * l + i]);
+        a = acc_group_sum<G>(a);
+        const dd nsv = dd_neg(dd_mul(bj, acc_value(a)));
+        if (act)
+          for (int i = j + gl; i < l; i += G) Z[c * l + i] = dd_lin2(dd_make(1.0f), Z[c * l + i], nsv, A[j * l + i]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// One-sided Jacobi (Hestenes) on the columns of W, the rotations applied to
+// the columns of Z as well.  On exit W has orthogonal columns.  Columns are
+// paired in round-robin order (l/2 independent pairs per round, 8 lanes per
+// pair); a pair is rotated unless |w_p^T w_q| <= tol ||w_p|| ||w_q||.  The
+// rotation tangent of the symmetric 2 x 2 problem (Golub & Van Loan,
+// Algorithm 8.5.1) is taken to FP32 accuracy; c = (1 + t^2)^{-1/2} and
+// s = c t are formed in double-float from that t, so every rotation is
+// orthogonal to double-float accuracy and only the speed of convergence
+// depends on t.
+template <int NT>
+__device__ void jacobi_dd(dd* W, dd* Z, int l, int* flag) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int np = (l + 1) & ~1;
   const double tol = (double)l * 3.6e-15;  // about l * 2^-48
@@ -99,21 +319,19 @@ __device__ void jacobi_dd(dd* W, dd* V, int l, int* flag) {
         const bool act = slot < np / 2 && q < l;
         dd* wp = W + p * l;
         dd* wq = W + q * l;
-        dd al{0.f, 0.f}, be{0.f, 0.f}, ga{0.f, 0.f};
+        dacc sa{0.f, 0.f}, sb{0.f, 0.f}, sg{0.f, 0.f};
         if (act)
           for (int i = gl; i < l; i += 8) {
             const dd u = wp[i], v = wq[i];
-            al = dd_fma(u, u, al);
-            be = dd_fma(v, v, be);
-            ga = dd_fma(u, v, ga);
+            acc_fma(sa, u, u);
+            acc_fma(sb, v, v);
+            acc_fma(sg, u, v);
           }
-#pragma unroll
-        for (int off = 4; off > 0; off >>= 1) {
-          al = dd_add(al, dd{__shfl_xor_sync(0xffffffffu, al.hi, off), __shfl_xor_sync(0xffffffffu, al.lo, off)});
-          be = dd_add(be, dd{__shfl_xor_sync(0xffffffffu, be.hi, off), __shfl_xor_sync(0xffffffffu, be.lo, off)});
-          ga = dd_add(ga, dd{__shfl_xor_sync(0xffffffffu, ga.hi, off), __shfl_xor_sync(0xffffffffu, ga.lo, off)});
-        }
+        sa = acc_group_sum<8>(sa);
+        sb = acc_group_sum<8>(sb);
+        sg = acc_group_sum<8>(sg);
         if (!act) continue;
+        const dd al = acc_value(sa), be = acc_value(sb), ga = acc_value(sg);
         const double a2 = dd_to_double(al), b2 = dd_to_double(be), g2 = dd_to_double(ga);
         if (a2 == 0.0 || b2 == 0.0 || g2 * g2 <= tol * tol * a2 * b2) continue;
         const float zeta = dd_add(be, dd_neg(al)).hi / (2.0f * ga.hi);
@@ -124,15 +342,15 @@ __device__ void jacobi_dd(dd* W, dd* V, int l, int* flag) {
         const dd c = dd_rsqrt_1_2(x);
         const dd s = dd_mul(c, dd_make(tf));
         const dd ns = dd_neg(s);
-        dd* vp = V + p * l;
-        dd* vq = V + q * l;
+        dd* zp = Z + p * l;
+        dd* zq = Z + q * l;
         for (int i = gl; i < l; i += 8) {
           const dd u = wp[i], v = wq[i];
-          wp[i] = dd_fma(c, u, dd_mul(ns, v));
-          wq[i] = dd_fma(s, u, dd_mul(c, v));
-          const dd xx = vp[i], yy = vq[i];
-          vp[i] = dd_fma(c, xx, dd_mul(ns, yy));
-          vq[i] = dd_fma(s, xx, dd_mul(c, yy));
+          wp[i] = dd_lin2(c, u, ns, v);
+          wq[i] = dd_lin2(s, u, c, v);
+          const dd xx = zp[i], yy = zq[i];
+          zp[i] = dd_lin2(c, xx, ns, yy);
+          zq[i] = dd_lin2(s, xx, c, yy);
         }
         if (gl == 0) *flag = 1;
       }
@@ -141,6 +359,42 @@ __device__ void jacobi_dd(dd* W, dd* V, int l, int* flag) {
     if (*flag == 0) break;
     __syncthreads();
   }
+}
+
+// SVD of the l x l matrix X held in A (column c at A[c*l, c*l+l)), with Z an
+// l x l work area: QR with column pivoting X P = Q R, then one-sided Jacobi
+// on R^T (the preconditioning of Drmac & Veselic, "New fast and accurate
+// Jacobi SVD algorithm I", SIAM J. Matrix Anal. Appl. 29, 2008: on the
+// graded R^T the sweeps roughly halve), its rotations accumulated into Z = Q.
+// With R^T V = W (orthogonal columns) this is X = (Q V) W^T P^T, so on exit
+//   sigma_b = ||W[:, b]||,  right singular vector b of X = P W[:, b] / sigma_b,
+//   left singular vector b of X = Z[:, b],
+// with W in A and Q V in Z; (X_k)^+ = sum_b P W_b Z_b^T / sigma_b^2.
+template <int NT>
+__device__ void svd_dd(dd* A, dd* Z, int l, SvdScratch* sc) {
+  qrcp_dd<NT>(A, l, sc);
+  form_q_dd<NT>(A, l, sc, Z);
+  // W = R^T in place: column j of W = row j of R (pivoted column order)
+  constexpr int kPer = (kMaxL * kMaxL + NT - 1) / NT;
+  dd v[kPer];
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const int e = threadIdx.x + t * NT;
+    v[t] = dd{0.f, 0.f};
+    if (e < l * l) {
+      const int j = e / l, c = e - j * l;
+      if (c > j) v[t] = A[c * l + j];
+      else if (c == j) v[t] = sc->rdiag[j];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < kPer; ++t) {
+    const int e = threadIdx.x + t * NT;
+    if (e < l * l) A[e] = v[t];
+  }
+  __syncthreads();
+  jacobi_dd<NT>(A, Z, l, &sc->flag);
 }
 
 // After jacobi_dd: sigma_b = ||W_b|| (double), order[rank] = column (sigma
@@ -163,19 +417,21 @@ __device__ void jacobi_sigma(const dd* W, int l, double* sig, int* order) {
 }
 
 // U[p][q] = sum_{r < ke} V[b_r][p] W[b_r][q] / sigma_r^2 in double-float;
-// inv2[r] = 1 / sigma_{b_r}^2 (shared, computed once); out(e, value)
-// receives the l*l entries (row-major index e = p*l + q).
+// (X_k)^+ from svd_dd: U[perm[c]][q] = sum_{r < ke} W[b_r][c] Z[b_r][q] inv2[r]
+// with b_r = order[r] and inv2[r] = 1 / sigma_{b_r}^2 (shared, computed
+// once); out(e, value) receives the l*l entries, row-major e = p*l + q (p a
+// column of X, q a row of X).
 template <int NT, typename Out>
-__device__ void nucleus_from_svd(const dd* W, const dd* V, int l, int ke, const int* order,
-                                 const dd* inv2, Out out) {
+__device__ void nucleus_from_svd(const dd* W, const dd* Z, const int* perm, int l, int ke,
+                                 const int* order, const dd* inv2, Out out) {
   for (int e = threadIdx.x; e < l * l; e += NT) {
-    const int p = e / l, q = e - p * l;
+    const int c = e / l, q = e - c * l;
     dd acc{0.f, 0.f};
     for (int r = 0; r < ke; ++r) {
       const int b = order[r];
-      acc = dd_fma(dd_mul(V[b * l + p], W[b * l + q]), inv2[r], acc);
+      acc = dd_fma(dd_mul(W[b * l + c], Z[b * l + q]), inv2[r], acc);
     }
-    out(e, dd_to_double(acc));
+    out(perm[c] * l + q, dd_to_double(acc));
   }
 }
 
