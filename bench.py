@@ -40,12 +40,19 @@ WORKLOADS = {
     # stored FP32 32768^2 = G1 G2^T / 8 + N(0, 1e-4^2), full residual on the tensor cores
     "dense32768": dict(kind="dense32", m=32768, n=32768, k=64, l=96, sweeps=4, q=1000, s=1000,
                        seed_off=3, full=True),
+    # smaller stored case of the same recipe (inputs still larger than L2), for
+    # full ncu captures of the full-residual kernel
+    "dense8192": dict(kind="dense32", m=8192, n=8192, k=64, l=96, sweeps=4, q=1000, s=1000,
+                      seed_off=6, full=True),
     # 4096 far-field blocks of 1/|x - y| over 2^20 points (octree, leaf <= 2048),
     # rank-adaptive to 1e-6 with k <= 64, one persistent launch
     "octree4096": dict(form="batch", npoints=1 << 20, leaf=2048, n_pairs=4096, l_init=16, l_max=96,
                        k_max=64, sweeps=2, tol=1e-6, q=32, seed_off=4, plain_subset=256),
     # Poisson stream of requests: sides log-uniform in 256..16384, k in {8,16,32,64},
     # Cauchy / Gaussian / 1/|x - y| generators, 40 GB admission budget
+    # 512 blocks of the same tree, for full ncu captures of the batch kernel
+    "octree512": dict(form="batch", npoints=1 << 20, leaf=2048, n_pairs=512, l_init=16, l_max=96,
+                      k_max=64, sweeps=2, tol=1e-6, q=32, seed_off=4, plain_subset=64),
     "serve": dict(form="serve", count=400, min_side=256, max_side=16384, budget_gb=40, slots=64,
                   streams=32, rates=(0.5, 0.8, 0.95), seed_off=5, plain_subset=400),
 }
@@ -588,7 +595,8 @@ def run_batch(args, wl_name):
         "l_hist": {str(k): int(v) for k, v in zip(*np.unique(r.l, return_counts=True))},
         "k_eff_mean": float(r.k_eff.mean()),
         "roofline": {"kernel": "batch_kernel", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
-                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "traffic": captured_traffic("k_batch.cu", f"batch_{wl_name}.md"),
                      "peak_source": f"FP32 FMA rate: {SMS} SMs x 128 FMA/clk x median SM clock {sm_mhz:.0f} MHz",
                      "note": "elimination/update FLOPs counted by the kernel; the decision chain (one cluster barrier per pivot) bounds it"},
         "gpu_launches": args.steps,
@@ -769,6 +777,24 @@ def run_profile_solves(args, wl_name):
     import torch
     import paper_1611_01391_gb300 as L
     wl = WORKLOADS[wl_name]
+    if wl.get("form") == "batch":
+        import numpy as np
+        from paper_1611_01391_gb300.api import _batch_fetch, make_batch_params
+        pts, blocks, jc, sr, sc = make_batch_inputs(wl)
+        ctx = L.Context(0)
+        d = torch.from_numpy(pts).cuda()
+        src = L.make_source("invdist", x=d, y=d)
+        p, keep = make_batch_params(wl["l_init"], wl["l_max"], wl["k_max"], wl["sweeps"], wl["tol"], jc, sr, sc)
+        b64 = np.ascontiguousarray(blocks, dtype=np.int64)
+        for _ in range(args.profile_solves):
+            r = _batch_fetch(ctx.ctx, L.lra_cross_submit_batch(ctx.ctx, src, b64, p), len(blocks), wl["l_max"])
+            if not np.all(r.status == 0):
+                raise RuntimeError("batch solve failed")
+        ctx.close()
+        print(f"profile solves done: {args.profile_solves} x {wl_name}", flush=True)
+        return
+    if wl.get("form") == "serve":
+        raise SystemExit("--profile-solves takes a plain or batch workload")
     inp = make_inputs(wl, 0)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -801,6 +827,8 @@ def captured_traffic(kernel_file, summary):
         return None
     fields = dict(ln.split(":", 1) for ln in text.splitlines() if ln.startswith(("traffic_bytes_per_launch:", "source_sha256:")))
     if fields.get("source_sha256", "").strip() != hashlib.sha256(src).hexdigest():
+        return None
+    if "traffic_bytes_per_launch" not in fields:
         return None
     return float(fields["traffic_bytes_per_launch"])
 
