@@ -46,12 +46,12 @@ WORKLOADS = {
                       seed_off=6, full=True),
     # 4096 far-field blocks of 1/|x - y| over 2^20 points (octree, leaf <= 2048),
     # rank-adaptive to 1e-6 with k <= 64, one persistent launch
-    "octree4096": dict(form="batch", npoints=1 << 20, leaf=2048, n_pairs=4096, l_init=16, l_max=96,
+    "octree4096": dict(form="batch", npoints=1 << 20, leaf=2048, n_pairs=4096, l_init=12, l_max=96,
                        k_max=64, sweeps=2, tol=1e-6, q=32, seed_off=4, plain_subset=256),
     # Poisson stream of requests: sides log-uniform in 256..16384, k in {8,16,32,64},
     # Cauchy / Gaussian / 1/|x - y| generators, 40 GB admission budget
     # 512 blocks of the same tree, for full ncu captures of the batch kernel
-    "octree512": dict(form="batch", npoints=1 << 20, leaf=2048, n_pairs=512, l_init=16, l_max=96,
+    "octree512": dict(form="batch", npoints=1 << 20, leaf=2048, n_pairs=512, l_init=12, l_max=96,
                       k_max=64, sweeps=2, tol=1e-6, q=32, seed_off=4, plain_subset=64),
     "serve": dict(form="serve", count=400, min_side=256, max_side=16384, budget_gb=40, slots=64,
                   streams=32, rates=(0.5, 0.8, 0.95), seed_off=5, plain_subset=400),
@@ -200,7 +200,8 @@ for b in order:
     t1 = time.perf_counter()
     sub = Sub(r0, m, c0, n_)
     I, J, U, ke, sg, l, sw = O.cross_approximation_adaptive(sub, jc[b], wl["l_init"], wl["l_max"], wl["k_max"],
-                                                            wl["sweeps"], wl["tol"])
+                                                            wl["sweeps"], wl["tol"], sample_rows=sr[b],
+                                                            sample_cols=sc[b])
     O.sampled_residual(sub, sub.block(np.arange(m), J), U, sub.block(I, np.arange(n_)), sr[b], sc[b])
     times.append(time.perf_counter() - t1); n += 1
     if (time.perf_counter() - t0 > {budget} and n >= {min_n}) or n >= {max_n}:

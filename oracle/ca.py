@@ -30,7 +30,9 @@ Approximation and Least Squares Regression", arXiv:1611.01391):
 Readings where the paper is silent (documented with the design):
   |I| = |J| = l (square cross), truncation rank k <= l; delta = 1e-2 and a cap
   of 64 l swaps per half-step; exact ties go to the smaller row, then the
-  smaller column; the nucleus keeps singular values > rank_tol * sigma_1.
+  smaller column; the nucleus keeps singular values > rank_tol * sigma_1,
+  by default rank_tol = 1e-12 (entries in FP64); a caller comparing with a
+  solver that gathers FP32 entries passes that solver's rank_tol (1e-6).
 
 Entries are promoted to FP64 before any arithmetic.  Two source precisions
 exist: ``fp64`` evaluates generator entries in FP64 (the error reference) and
@@ -159,19 +161,24 @@ def _runner_up(values, winner):
     return float(rest.max())
 
 
-def gepp_rows(S, trace=None, half_step=0, pivots=None):
+def gepp_rows(S, trace=None, half_step=0, pivots=None, first=()):
     """Pivot rows of Gaussian elimination with partial pivoting on the N x l
     strip S: at step t take the free row of largest |entry| in column t of
     the Schur complement (smallest row on ties), then eliminate column t from
-    the later columns of the free rows.  Returns the l pivot rows in order."""
+    the later columns of the free rows.  For the first len(first) steps only
+    the rows listed in ``first`` are candidates (a previous index set kept
+    and completed).  Returns the l pivot rows in order."""
     W = np.array(S, dtype=np.float64, copy=True)
     N, l = W.shape
     if N < l:
         raise ValueError("strip has fewer rows than columns")
     free = np.ones(N, dtype=bool)
+    keep = np.zeros(N, dtype=bool)
+    keep[list(first)] = True
     piv = []
     for t in range(l):
-        mag = np.where(free, np.abs(W[:, t]), -1.0)
+        cand = free & keep if t < len(first) else free
+        mag = np.where(cand, np.abs(W[:, t]), -1.0)
         p = int(np.argmax(mag))
         v1 = float(mag[p])
         if trace is not None:
@@ -242,7 +249,7 @@ def maxvol(S, I0, delta=1e-2, max_swaps=None, trace=None, half_step=0):
 # Nucleus (Primitive Algorithm, stages 2-3) and error estimates
 # ---------------------------------------------------------------------------
 
-def nucleus(X, k, rank_tol=1e-6):
+def nucleus(X, k, rank_tol=1e-12):
     """U = (X_k)^+ for the l x l CUR generator X: SVD X = P diag(sigma) Q^T,
     keep the k_eff = min(k, #{sigma_j > rank_tol sigma_1}) leading triplets,
     U = Q_k diag(1/sigma_k) P_k^T.  Returns (U, k_eff, sigma)."""
@@ -310,7 +317,7 @@ class CrossResult:
     estimate: dict | None = None
 
 
-def cross_approximation(src, J0, k, sweeps, delta=1e-2, rank_tol=1e-6,
+def cross_approximation(src, J0, k, sweeps, delta=1e-2, rank_tol=1e-12,
                         max_swaps=None, tol=0.0, sample_rows=None,
                         sample_cols=None, keep_trace=True):
     """C-A iterations from the initial column set J0 (|J0| = l).
@@ -363,42 +370,59 @@ def cross_approximation(src, J0, k, sweeps, delta=1e-2, rank_tol=1e-6,
 
 
 def cross_approximation_adaptive(src, J_cands, l_init, l_max, k_max, sweeps, tol,
-                                 delta=1e-2, max_swaps=None, growth=2.0):
-    """Rank-adaptive C-A for many small blocks (the reading used for the
-    far-field blocks of Section 9, whose ranks are not known in advance).
+                                 delta=1e-2, max_swaps=None, sample_rows=None,
+                                 sample_cols=None):
+    """Rank-adaptive C-A for blocks whose rank is not known in advance (the
+    far-field blocks of Section 9; the paper's HSS test finds the rank by a
+    search, this is the growth rule read for it).
 
-    Every strip, not only the first, starts from the rows chosen by Gaussian
-    elimination with partial pivoting and then runs maxvol (Section 6.5 lets
-    each C-A step compute its generator by any algorithm).  After ``sweeps``
-    sweeps, if the last GEPP pivot of the final vertical step still exceeds
-    tol times the first one, the cross grows to min(l_max, growth l) by
-    appending the next unused candidate columns to J, and the sweeps repeat.
-    The nucleus keeps k_eff = min(k_max, #{sigma_j > tol sigma_1}).
+    The cross starts at l = l_init with the first candidate columns.  Each
+    sweep is a vertical step (I = maxvol of M[:, J], started from the
+    previous I; the very first one, and the rows a grown cross lacks, come
+    from Gaussian elimination with partial pivoting) and a horizontal step
+    (J = maxvol of M[I, :]^T started from J).  After every sweep,
+    k = #{sigma_j(M[I, J]) > tol sigma_1}:
+      * k = l < k_max and l < l_max: the cross grows to min(l_max, 2 l) with
+        the next unused candidate columns appended to J;
+      * otherwise U = (M[I, J]_k)^+ with k_eff = min(k_max, k), and the
+        iteration stops once k >= k_max, ``sweeps`` sweeps were made at this
+        size, or the Appendix F estimate on (sample_rows, sample_cols), when
+        given, is <= tol.
 
     Returns (I, J, U, k_eff, sigma, l, swaps)."""
     J_cands = [int(j) for j in J_cands]
-    l = l_init
-    J = J_cands[:l]
+    J = J_cands[:l_init]
+    l = len(J)
+    I = []
     swaps = 0
+    at_size = 0
     while True:
-        for s in range(sweeps):
-            C = columns(src, J)
-            piv = []
-            res = maxvol(C, gepp_rows(C, pivots=piv), delta, max_swaps)
-            I = res.I
-            swaps += res.swaps
-            Rt = rows(src, I).T
-            res = maxvol(Rt, gepp_rows(Rt), delta, max_swaps)
-            J = res.I
-            swaps += res.swaps
-        if l < l_max and piv[-1] > tol * piv[0]:
-            l_new = min(l_max, int(growth * l))
-            extra = [j for j in J_cands if j not in J][: l_new - l]
-            J = J + extra
-            l = len(J)
-            continue
-        break
-    U, k_eff, sigma = nucleus(src.block(I, J), k_max, tol)
+        C = columns(src, J)
+        start = I if len(I) == l else gepp_rows(C, first=I)
+        res = maxvol(C, start, delta, max_swaps)
+        I = res.I
+        swaps += res.swaps
+        res = maxvol(rows(src, I).T, J, delta, max_swaps)
+        J = res.I
+        swaps += res.swaps
+        at_size += 1
+        X = src.block(I, J)
+        sigma = np.linalg.svd(X, compute_uv=False)
+        k = int(np.count_nonzero(sigma > tol * sigma[0])) if sigma[0] > 0.0 else 0
+        if k == l and k < k_max and l < l_max:
+            extra = [j for j in J_cands if j not in J][: min(l_max, 2 * l) - l]
+            if extra:
+                J = J + extra
+                l = len(J)
+                at_size = 0
+                continue
+        U, k_eff, sigma = nucleus(X, k_max, tol)
+        if k >= k_max or at_size >= sweeps:
+            break
+        if sample_rows is not None:
+            est = sampled_residual(src, columns(src, J), U, rows(src, I), sample_rows, sample_cols)
+            if est["rel"] <= tol:
+                break
     return I, J, U, k_eff, sigma, l, swaps
 
 

@@ -14,19 +14,22 @@
 //     shared memory, one hardware cluster barrier, then every CTA reads the
 //     four candidates through distributed shared memory and updates its rows.
 //   * Every strip starts from Gauss-Jordan elimination with partial pivoting
-//     in FP32 and continues with maxvol swaps.  Elimination with partial
-//     pivoting is backward stable, so the FP32 B = S X^{-1} it produces is
-//     the exact B of a strip within FP32 rounding of the data; an explicit
-//     X^{-1} in FP32 would not be (its error grows with cond(X)).
-//   * Rank adaptivity: after the sweeps, if the last pivot of the final
-//     vertical step exceeds tol times the first, the cross grows (x2, up to
-//     l_max) with the block's next candidate columns and the sweeps repeat.
-//   * Nucleus: SVD of the final cross (QR with column pivoting, then
-//     one-sided Jacobi) in double-float arithmetic on one CTA (an FP32 SVD
-//     cannot resolve singular values near tol sigma_1 = 1e-6 sigma_1),
-//     k_eff = min(k_max, #{sigma_j > tol sigma_1}), U = (X_k)^+ in FP64.
-//   * Appendix F estimate on a q x q sample of each block, with compensated
-//     FP32 products and FP64 sums.
+//     in FP32 whose pivots are restricted to the previous index set (the
+//     very first strip, and the rows a grown cross lacks, pivot freely), and
+//     continues with maxvol swaps.  Elimination with partial pivoting is
+//     backward stable, so the FP32 B = S X^{-1} it produces is the exact B
+//     of a strip within FP32 rounding of the data; an explicit X^{-1} in
+//     FP32 would not be (its error grows with cond(X)).
+//   * Rank adaptivity, after every sweep: the leader CTA takes the SVD of
+//     the cross (QR with column pivoting, then one-sided Jacobi, double-float
+//     arithmetic: an FP32 SVD cannot resolve singular values near
+//     tol sigma_1 = 1e-6 sigma_1) and counts k = #{sigma_j > tol sigma_1}.
+//     If k = l < k_max the cross grows (x2, up to l_max) with the block's
+//     next candidate columns; otherwise U = (X_k)^+ (k_eff = min(k_max, k),
+//     FP64) and the Appendix F estimate on a q x q sample are written, and
+//     the block stops once k >= k_max, the estimate is <= tol, or the sweep
+//     budget at this size is spent.
+//   * The estimate uses compensated FP32 products and FP64 sums.
 #include <cooperative_groups.h>
 
 #include <cfloat>
@@ -61,10 +64,10 @@ struct BatchSmem {
   unsigned char used[kRowsPerCta];
   int blk;
   int status;
-  float piv_first, piv_last;
   int swaps;
   int keff;
   int lnew;
+  int grow, stop;
   double esum[2][kBT / 32];
 };
 // the nucleus (W, V, sigma, 1/sigma^2, order) and the estimate's operands
@@ -119,11 +122,18 @@ __device__ __forceinline__ void cta_reduce(BatchSmem* s, unsigned long long key,
 // One strip of the C-A iteration on the cluster: load the N x l strip
 // (vertical: S[i][t] = M(row0 + i, col0 + other[t]); horizontal:
 // S[j][t] = M(row0 + other[t], col0 + j)), Gauss-Jordan start, maxvol.
+// The start keeps the previous index set: for its first nfirst steps the
+// pivot rows are restricted to the strip rows first[0 .. nfirst) (partial
+// pivoting among them), later steps pivot over every free row.  After l
+// steps B = S X^{-1} with X the rows so chosen; elimination with partial
+// pivoting is backward stable, so this FP32 B is the exact B of the strip
+// within FP32 rounding of the data, which an FP32 X^{-1} would not give.
 // Returns false when the block failed (s->status set identically in all
 // CTAs).  On return s->pos holds the selected strip rows.
 template <int KIND>
 __device__ bool half_step(const BatchArgs& a, cg::cluster_group& cl, BatchSmem* s, bool vertical,
-                          long long row0, long long col0, int N, int l, const int* other) {
+                          long long row0, long long col0, int N, int l, const int* other,
+                          int nfirst, const int* first) {
   const int rank = (int)cl.block_rank();
   const int tid = threadIdx.x;
   const int rpc = (N + kCS - 1) / kCS;
@@ -135,12 +145,18 @@ __device__ bool half_step(const BatchArgs& a, cg::cluster_group& cl, BatchSmem* 
     s->B[e] = vertical ? entry<KIND>(a.src, row0 + g, col0 + other[t])
                        : entry<KIND>(a.src, row0 + other[t], col0 + g);
   }
-  for (int r = tid; r < nr; r += kBT) s->used[r] = 0;
+  for (int r = tid; r < nr; r += kBT) s->used[r] = 0;  // bit 0: pivoted, bit 1: in first
+  __syncthreads();
+  for (int t = tid; t < nfirst; t += kBT) {
+    const int g = first[t];
+    if (g >= r0 && g < r0 + nr) s->used[g - r0] = 2;
+  }
   __syncthreads();
 
   unsigned long long mine = 0ull;
   int nf = 0;
-  for (int r = tid; r < nr; r += kBT) consider_f(mine, nf, s->B[r * l], (r0 + r) * l);
+  for (int r = tid; r < nr; r += kBT)
+    if (nfirst == 0 || (s->used[r] & 2)) consider_f(mine, nf, s->B[r * l], (r0 + r) * l);
   bool gepp = true;
   int step = 0, swaps = 0, buf = 0;
   bool ok = true;
@@ -179,10 +195,6 @@ __device__ bool half_step(const BatchArgs& a, cg::cluster_group& cl, BatchSmem* 
         ok = false;
         break;
       }
-      if (vertical && tid == 0) {
-        if (step == 0) s->piv_first = wv;
-        if (step == l - 1) s->piv_last = wv;
-      }
       kind = 0;
     } else if (wv <= 1.0f + a.delta || swaps >= a.max_swaps) {
       kind = 2;
@@ -195,7 +207,7 @@ __device__ bool half_step(const BatchArgs& a, cg::cluster_group& cl, BatchSmem* 
     if (tid < l) s->rrow[tid] = cl.map_shared_rank(&s->slot_row[buf][0], owner)[tid];
     for (int r = tid; r < nr; r += kBT) s->colj[r] = s->B[r * l + jstar];
     if (tid == 0) {
-      if (gepp && istar >= r0 && istar < r0 + nr) s->used[istar - r0] = 1;
+      if (gepp && istar >= r0 && istar < r0 + nr) s->used[istar - r0] |= 1;
       s->pos[jstar] = istar;
     }
     __syncthreads();
@@ -217,7 +229,9 @@ __device__ bool half_step(const BatchArgs& a, cg::cluster_group& cl, BatchSmem* 
       } else {
         v = fmaf(-s->colj[r], s->rrow[t], s->B[e]);
         s->B[e] = v;
-        if (next_gepp ? (t == next_col && !s->used[r]) : true) consider_f(mine, nf, v, g * l + t);
+        if (next_gepp ? (t == next_col && !(s->used[r] & 1) && (next_col >= nfirst || (s->used[r] & 2)))
+                      : true)
+          consider_f(mine, nf, v, g * l + t);
       }
     }
     if (gepp) {
@@ -251,6 +265,152 @@ __device__ __forceinline__ void dot2_b(float x, float y, float& p, float& c) {
   c = __fadd_rn(c, __fadd_rn(q, r));
 }
 
+// Leader CTA, after every sweep: SVD of the cross X = M[I, J] (QR with
+// column pivoting, then one-sided Jacobi, in double-float), the rank count
+// k = #{sigma_j > tol sigma_1} and the decision to grow the cross (k = l <
+// k_max, l below the block's cap, unused candidates left).  Unless it grows,
+// the block's outputs are (re)written: I, J, sigma, k_eff = min(k_max, k),
+// U = (X_k)^+ in FP64 and the Appendix F estimate; s->stop is set when
+// k >= k_max or the estimate is <= tol.
+template <int KIND>
+__device__ void cross_step(const BatchArgs& a, BatchSmem* s, int b, long long row0, long long col0,
+                           long long n, int l, int lmax_b) {
+  const int tid = threadIdx.x;
+  dd* W = reinterpret_cast<dd*>(s->B);
+  dd* Z = W + kMaxL * kMaxL;
+  double* sig = reinterpret_cast<double*>(Z + kMaxL * kMaxL);
+  dd* inv2 = reinterpret_cast<dd*>(sig + kMaxL);
+  SvdScratch* sc = reinterpret_cast<SvdScratch*>(inv2 + kMaxL);
+  int* order = reinterpret_cast<int*>(sc + 1);
+  if (tid == 0) s->lnew = 0;
+  __syncthreads();
+  // X scaled by a power of two into [0.5, 1)
+  float amax = 0.0f;
+  for (int e = tid; e < l * l; e += kBT) {
+    const int p = e / l, q = e - p * l;
+    const float x = entry<KIND>(a.src, row0 + s->Iset[p], col0 + s->Jset[q]);
+    amax = fmaxf(amax, fabsf(x));
+    W[q * l + p] = dd_make(x);   // column q of X
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+  if ((tid & 31) == 0 && amax > 0.0f) {
+    int ex;
+    frexpf(amax, &ex);
+    atomicMax(&s->lnew, ex + 1024);
+  }
+  __syncthreads();
+  const int ex = s->lnew ? s->lnew - 1024 : 0;
+  for (int e = tid; e < l * l; e += kBT) W[e].hi = ldexpf(W[e].hi, -ex);
+  __syncthreads();
+  svd_dd<kBT>(W, Z, l, sc);
+  jacobi_sigma<kBT>(W, l, sig, order);
+  if (tid == 0) {
+    const double s1 = sig[order[0]];
+    int k = 0;
+    if (s1 > 0.0)
+      while (k < l && sig[order[k]] > (double)a.tol * s1) ++k;
+    int avail = 0;
+    for (int c = 0; c < a.l_max; ++c) {
+      const int j = a.jcand[(size_t)b * a.l_max + c];
+      bool in = false;
+      for (int t = 0; t < l; ++t) in |= (s->Jset[t] == j);
+      avail += (!in && j < n);
+    }
+    s->grow = (k == l && k < a.k_max && l < lmax_b && avail > 0);
+    s->keff = min(k, a.k_max);
+    s->stop = (k >= a.k_max);
+  }
+  __syncthreads();
+  if (s->grow) return;
+  for (int t = tid; t < l; t += kBT) {
+    a.out_I[(size_t)b * a.l_max + t] = s->Iset[t];
+    a.out_J[(size_t)b * a.l_max + t] = s->Jset[t];
+  }
+  if (tid == 0) a.out_keff[b] = s->keff;
+  float* sg_out = a.out_sigma + (size_t)b * a.l_max;
+  for (int r = tid; r < l; r += kBT) {
+    const double sb = sig[order[r]];
+    inv2[r] = dd_from_double(sb > 0.0 ? 1.0 / (sb * sb) : 0.0);
+    sg_out[r] = (float)ldexp(sb, ex);
+  }
+  __syncthreads();
+  double* Ub = a.out_U + (size_t)b * a.l_max * a.l_max;
+  nucleus_from_svd<kBT>(W, Z, sc->perm, l, s->keff, order, inv2,
+                        [&](int e, double v) { Ub[e] = ldexp(v, -ex); });
+  __syncthreads();
+  // Appendix F estimate on the q x q sample of this block
+  const int q = a.q;
+  if (q > 0) {
+    float* Us = s->B;                      // U (l x l) back from global: hi part
+    float* Usl = Us + kMaxL * kMaxL;       //   and lo part, U = hi + lo
+    float* Cs = Usl + kMaxL * kMaxL;       // q x l: M(row0 + sr, col0 + J)
+    float* Rs = Cs + kMaxQ * kMaxL;        // l x q: M(row0 + I, col0 + sc)
+    float* CUh = Rs + kMaxL * kMaxQ;       // q x l: (C U) hi
+    float* CUl = CUh + kMaxQ * kMaxL;      //        (C U) lo
+    const int* sr = a.srow + (size_t)b * q;
+    const int* scl = a.scol + (size_t)b * q;
+    for (int e = tid; e < l * l; e += kBT) {
+      const double u = Ub[e];
+      const float hi = (float)u;
+      Us[e] = hi;
+      Usl[e] = (float)(u - (double)hi);
+    }
+    for (int e = tid; e < q * l; e += kBT) {
+      const int i = e / l, t = e - i * l;
+      Cs[e] = entry<KIND>(a.src, row0 + sr[i], col0 + s->Jset[t]);
+      Rs[t * q + i] = entry<KIND>(a.src, row0 + s->Iset[t], col0 + scl[i]);
+    }
+    __syncthreads();
+    for (int e = tid; e < q * l; e += kBT) {
+      const int i = e / l, u = e - i * l;
+      float p = 0.f, c = 0.f;
+      for (int t = 0; t < l; ++t) {
+        dot2_b(Cs[i * l + t], Us[t * l + u], p, c);
+        c = __fmaf_rn(Cs[i * l + t], Usl[t * l + u], c);  // the lo part needs FP32 only
+      }
+      const float hi = __fadd_rn(p, c);
+      CUh[e] = hi;
+      CUl[e] = __fadd_rn(__fsub_rn(p, hi), c);  // rounding error of hi = p + c
+    }
+    __syncthreads();
+    double se = 0.0, sa = 0.0;
+    for (int e = tid; e < q * q; e += kBT) {
+      const int i = e / q, j = e - i * q;
+      float p = 0.f, c = 0.f;
+      for (int u = 0; u < l; ++u) {
+        dot2_b(CUh[i * l + u], Rs[u * q + j], p, c);
+        dot2_b(CUl[i * l + u], Rs[u * q + j], p, c);
+      }
+      const float mv = entry<KIND>(a.src, row0 + sr[i], col0 + scl[j]);
+      const double ev = ((double)mv - (double)p) - (double)c;
+      se += ev * ev;
+      sa += (double)mv * (double)mv;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      se += __shfl_xor_sync(0xffffffffu, se, off);
+      sa += __shfl_xor_sync(0xffffffffu, sa, off);
+    }
+    if ((tid & 31) == 0) {  // fixed-order sum: reproducible bits
+      s->esum[0][tid >> 5] = se;
+      s->esum[1][tid >> 5] = sa;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double e2 = 0.0, a2 = 0.0;
+      for (int w = 0; w < kBT / 32; ++w) {
+        e2 += s->esum[0][w];
+        a2 += s->esum[1][w];
+      }
+      const double est = a2 > 0.0 ? sqrt(e2 / a2) : 0.0;
+      a.out_err[b] = est;
+      if (est <= (double)a.tol) s->stop = 1;
+    }
+  }
+  __syncthreads();
+}
+
 template <int KIND>
 __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kBT, 1) batch_kernel(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char bsm[];
@@ -274,24 +434,28 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kBT, 1) batch_kern
     if (tid == 0) {
       s->status = LRA_OK;
       s->swaps = 0;
-      s->piv_first = s->piv_last = 0.f;
     }
     __syncthreads();
     bool ok = true;
+    int n_i = 0;       // rows of the previous I (none before the first sweep)
+    int at_size = 0;   // sweeps at the current cross size
     for (;;) {
-      for (int sw = 0; sw < a.sweeps && ok; ++sw) {
-        ok = half_step<KIND>(a, cl, s, true, row0, col0, (int)m, l, s->Jset);
-        if (!ok) break;
-        for (int t = tid; t < l; t += kBT) s->Iset[t] = s->pos[t];
-        __syncthreads();
-        ok = half_step<KIND>(a, cl, s, false, row0, col0, (int)n, l, s->Iset);
-        if (!ok) break;
-        for (int t = tid; t < l; t += kBT) s->Jset[t] = s->pos[t];
-        __syncthreads();
-      }
+      ok = half_step<KIND>(a, cl, s, true, row0, col0, (int)m, l, s->Jset, n_i, s->Iset);
       if (!ok) break;
-      if (l < lmax_b && s->piv_last > a.tol * s->piv_first) {
-        // grow: append the next candidate columns that are not in J
+      for (int t = tid; t < l; t += kBT) s->Iset[t] = s->pos[t];
+      n_i = l;
+      __syncthreads();
+      ok = half_step<KIND>(a, cl, s, false, row0, col0, (int)n, l, s->Iset, l, s->Jset);
+      if (!ok) break;
+      for (int t = tid; t < l; t += kBT) s->Jset[t] = s->pos[t];
+      __syncthreads();
+      ++at_size;
+      if (rank == 0) cross_step<KIND>(a, s, b, row0, col0, n, l, lmax_b);
+      cl.sync();
+      const int grow = *cl.map_shared_rank(&s->grow, 0);
+      const int stop = *cl.map_shared_rank(&s->stop, 0);
+      if (grow) {
+        // append the next candidate columns that are not in J (same in every CTA)
         if (tid == 0) {
           const int l_new = min(lmax_b, 2 * l);
           int cnt = l;
@@ -305,149 +469,30 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kBT, 1) batch_kern
         }
         __syncthreads();
         l = s->lnew;
+        at_size = 0;
         __syncthreads();
         continue;
       }
-      break;
+      if (stop || at_size >= a.sweeps) break;
     }
     if (rank == 0) {
       if (tid == 0) {
         a.out_status[b] = ok ? (int)LRA_OK : s->status;
         a.out_l[b] = l;
         a.out_swaps[b] = s->swaps;
-      }
-      {  // defined contents past the l x l nucleus (and everywhere on failure)
-        const int lu = ok ? l : 0;
-        double* Ub = a.out_U + (size_t)b * a.l_max * a.l_max;
-        for (int e = lu * lu + tid; e < a.l_max * a.l_max; e += kBT) Ub[e] = 0.0;
-        for (int t = lu + tid; t < a.l_max; t += kBT) {
-          a.out_sigma[(size_t)b * a.l_max + t] = 0.0f;
-          a.out_I[(size_t)b * a.l_max + t] = -1;
-          a.out_J[(size_t)b * a.l_max + t] = -1;
+        if (!ok) {
+          a.out_keff[b] = 0;
+          a.out_err[b] = 0.0;
         }
       }
-      if (ok) {
-        // nucleus on this CTA (double-float Jacobi SVD); the strip area is
-        // free now.  X is scaled by a power of two into [0.5, 1).
-        dd* W = reinterpret_cast<dd*>(s->B);
-        dd* Z = W + kMaxL * kMaxL;
-        double* sig = reinterpret_cast<double*>(Z + kMaxL * kMaxL);
-        dd* inv2 = reinterpret_cast<dd*>(sig + kMaxL);
-        SvdScratch* sc = reinterpret_cast<SvdScratch*>(inv2 + kMaxL);
-        int* order = reinterpret_cast<int*>(sc + 1);
-        if (tid == 0) s->lnew = 0;
-        __syncthreads();
-        float amax = 0.0f;
-        for (int e = tid; e < l * l; e += kBT) {
-          const int p = e / l, q = e - p * l;
-          const float x = entry<KIND>(a.src, row0 + s->Iset[p], col0 + s->Jset[q]);
-          amax = fmaxf(amax, fabsf(x));
-          W[q * l + p] = dd_make(x);   // column q of X
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
-        if ((tid & 31) == 0 && amax > 0.0f) {
-          int ex;
-          frexpf(amax, &ex);
-          atomicMax(&s->lnew, ex + 1024);
-        }
-        for (int t = tid; t < l; t += kBT) {
-          a.out_I[(size_t)b * a.l_max + t] = s->Iset[t];
-          a.out_J[(size_t)b * a.l_max + t] = s->Jset[t];
-        }
-        __syncthreads();
-        const int ex = s->lnew ? s->lnew - 1024 : 0;
-        for (int e = tid; e < l * l; e += kBT) W[e].hi = ldexpf(W[e].hi, -ex);
-        __syncthreads();
-        svd_dd<kBT>(W, Z, l, sc);
-        jacobi_sigma<kBT>(W, l, sig, order);
-        if (tid == 0) {
-          const double s1 = sig[order[0]];
-          int ke = 0;
-          if (s1 > 0.0)
-            while (ke < a.k_max && ke < l && sig[order[ke]] > (double)a.tol * s1) ++ke;
-          s->keff = ke;
-          a.out_keff[b] = ke;
-        }
-        float* sg_out = a.out_sigma + (size_t)b * a.l_max;
-        for (int r = tid; r < l; r += kBT) {
-          const double sb = sig[order[r]];
-          inv2[r] = dd_from_double(sb > 0.0 ? 1.0 / (sb * sb) : 0.0);
-          sg_out[r] = (float)ldexp(sb, ex);
-        }
-        __syncthreads();
-        double* Ub = a.out_U + (size_t)b * a.l_max * a.l_max;
-        nucleus_from_svd<kBT>(W, Z, sc->perm, l, s->keff, order, inv2,
-                              [&](int e, double v) { Ub[e] = ldexp(v, -ex); });
-        __syncthreads();
-        // Appendix F estimate on the q x q sample of this block
-        const int q = a.q;
-        if (q > 0) {
-          float* Us = s->B;                      // U (l x l) back from global: hi part
-          float* Usl = Us + kMaxL * kMaxL;       //   and lo part, U = hi + lo
-          float* Cs = Usl + kMaxL * kMaxL;       // q x l: M(row0 + sr, col0 + J)
-          float* Rs = Cs + kMaxQ * kMaxL;        // l x q: M(row0 + I, col0 + sc)
-          float* CUh = Rs + kMaxL * kMaxQ;       // q x l: (C U) hi
-          float* CUl = CUh + kMaxQ * kMaxL;      //        (C U) lo
-          const int* sr = a.srow + (size_t)b * q;
-          const int* sc = a.scol + (size_t)b * q;
-          __syncthreads();
-          for (int e = tid; e < l * l; e += kBT) {
-            const double u = Ub[e];
-            const float hi = (float)u;
-            Us[e] = hi;
-            Usl[e] = (float)(u - (double)hi);
-          }
-          for (int e = tid; e < q * l; e += kBT) {
-            const int i = e / l, t = e - i * l;
-            Cs[e] = entry<KIND>(a.src, row0 + sr[i], col0 + s->Jset[t]);
-            Rs[t * q + i] = entry<KIND>(a.src, row0 + s->Iset[t], col0 + sc[i]);
-          }
-          __syncthreads();
-          for (int e = tid; e < q * l; e += kBT) {
-            const int i = e / l, u = e - i * l;
-            float p = 0.f, c = 0.f;
-            for (int t = 0; t < l; ++t) {
-              dot2_b(Cs[i * l + t], Us[t * l + u], p, c);
-              c = __fmaf_rn(Cs[i * l + t], Usl[t * l + u], c);  // the lo part needs FP32 only
-            }
-            const float hi = __fadd_rn(p, c);
-            CUh[e] = hi;
-            CUl[e] = __fadd_rn(__fsub_rn(p, hi), c);  // rounding error of hi = p + c
-          }
-          __syncthreads();
-          double se = 0.0, sa = 0.0;
-          for (int e = tid; e < q * q; e += kBT) {
-            const int i = e / q, j = e - i * q;
-            float p = 0.f, c = 0.f;
-            for (int u = 0; u < l; ++u) {
-              dot2_b(CUh[i * l + u], Rs[u * q + j], p, c);
-              dot2_b(CUl[i * l + u], Rs[u * q + j], p, c);
-            }
-            const float mv = entry<KIND>(a.src, row0 + sr[i], col0 + sc[j]);
-            const double ev = ((double)mv - (double)p) - (double)c;
-            se += ev * ev;
-            sa += (double)mv * (double)mv;
-          }
-#pragma unroll
-          for (int off = 16; off > 0; off >>= 1) {
-            se += __shfl_xor_sync(0xffffffffu, se, off);
-            sa += __shfl_xor_sync(0xffffffffu, sa, off);
-          }
-          if ((tid & 31) == 0) {  // fixed-order sum: reproducible bits
-            s->esum[0][tid >> 5] = se;
-            s->esum[1][tid >> 5] = sa;
-          }
-          __syncthreads();
-          if (tid == 0) {
-            double e2 = 0.0, a2 = 0.0;
-            for (int w = 0; w < kBT / 32; ++w) {
-              e2 += s->esum[0][w];
-              a2 += s->esum[1][w];
-            }
-            a.out_err[b] = a2 > 0.0 ? sqrt(e2 / a2) : 0.0;
-          }
-        }
+      // defined contents past the l x l nucleus (and everywhere on failure)
+      const int lu = ok ? l : 0;
+      double* Ub = a.out_U + (size_t)b * a.l_max * a.l_max;
+      for (int e = lu * lu + tid; e < a.l_max * a.l_max; e += kBT) Ub[e] = 0.0;
+      for (int t = lu + tid; t < a.l_max; t += kBT) {
+        a.out_sigma[(size_t)b * a.l_max + t] = 0.0f;
+        a.out_I[(size_t)b * a.l_max + t] = -1;
+        a.out_J[(size_t)b * a.l_max + t] = -1;
       }
     }
     cl.sync();  // block done: the leader may fetch the next block index

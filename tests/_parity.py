@@ -11,6 +11,12 @@ import oracle as O
 # pivot column); the stop test compares max |B| with 1 + delta.
 SEPARATION = 1e-6
 
+# Truncation threshold of the nucleus on the device (FP32 entries); the FP64
+# oracle's own default is 1e-12.  Input-matched comparisons (same entries,
+# same decisions, same U) run the oracle at the device's threshold; the error
+# bar is the pure-FP64 oracle at its default.
+GPU_TAU = 1e-6
+
 
 def separated(dec, delta):
     hs, kind, i, j, v1, v2 = dec

@@ -11,7 +11,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from tests._parity import compare_traces, error_ok, rel_fro_error, sampled_error
+from tests._parity import GPU_TAU, compare_traces, error_ok, rel_fro_error, sampled_error
 
 pytestmark = pytest.mark.gpu
 
@@ -56,7 +56,8 @@ def test_dense_f64_small_parity(ctx):
     J0 = W.draw_indices(W.BASE_SEED + 101, 256, 8)
     a = torch.from_numpy(A).to(DEV)
     res = gpu_solve(ctx, L.make_source("dense", a=a), 256, 256, J0, 8, 8, 3)
-    ref = O.cross_approximation(O.Dense(A.astype(np.float32)), J0, k=8, sweeps=3, delta=DELTA)
+    ref = O.cross_approximation(O.Dense(A.astype(np.float32)), J0, k=8, sweeps=3, delta=DELTA,
+                                rank_tol=GPU_TAU)
     ncmp, div = compare_traces(res.trace, ref.trace, DELTA)
     assert ncmp > 8
     if div is None:
@@ -82,7 +83,7 @@ def _cauchy_case(ctx, m, n, seed):
     xd, yd = torch.from_numpy(x).to(DEV), torch.from_numpy(y).to(DEV)
     res = gpu_solve(ctx, L.make_source("cauchy", x=xd, y=yd), m, n, J0, 16, 24, 4, rows, cols)
     src32 = O.Cauchy(x, y, "fp32")
-    ref = O.cross_approximation(src32, J0, k=16, sweeps=4, delta=DELTA,
+    ref = O.cross_approximation(src32, J0, k=16, sweeps=4, delta=DELTA, rank_tol=GPU_TAU,
                                 sample_rows=rows, sample_cols=cols)
     ncmp, div = compare_traces(res.trace, ref.trace, DELTA)
     assert ncmp >= 24
@@ -122,12 +123,15 @@ def test_dense_f32_l96_parity(ctx):
     A = W.factor_gaussian(W.BASE_SEED + 33, m, n, 64, 1e-4)
     J0 = W.draw_indices(W.BASE_SEED + 133, n, 96)
     res = gpu_solve(ctx, L.make_source("dense", a=torch.from_numpy(A).to(DEV)), m, n, J0, 64, 96, 4)
-    ref = O.cross_approximation(O.Dense(A), J0, k=64, sweeps=4, delta=DELTA)
+    ref = O.cross_approximation(O.Dense(A), J0, k=64, sweeps=4, delta=DELTA, rank_tol=GPU_TAU)
     ncmp, div = compare_traces(res.trace, ref.trace, DELTA)
     assert ncmp >= 96
     if div is None:
         assert list(res.I) == ref.I and list(res.J) == ref.J
     A64 = A.astype(np.float64)
+    assert error_ok(rel_fro_error(A64, res.C, res.U, res.R),
+                    O.full_residual(O.Dense(A64), ref.C, ref.U, ref.R)[0])
+    ref = O.cross_approximation(O.Dense(A64), J0, k=64, sweeps=4, delta=DELTA)
     err_ref = O.full_residual(O.Dense(A64), ref.C, ref.U, ref.R)[0]
     assert error_ok(rel_fro_error(A64, res.C, res.U, res.R), err_ref)
 
@@ -181,13 +185,16 @@ def test_shapes_parity(ctx, m, n, l, k, sweeps):
     A = W.factor_gaussian(m * 7 + n, m, n, max(1, l // 2 + 1), 1e-3)
     J0 = W.draw_indices(m + 3 * n, n, l)
     res = gpu_solve(ctx, L.make_source("dense", a=torch.from_numpy(A).to(DEV)), m, n, J0, k, l, sweeps)
-    ref = O.cross_approximation(O.Dense(A), J0, k=k, sweeps=sweeps, delta=DELTA)
+    ref = O.cross_approximation(O.Dense(A), J0, k=k, sweeps=sweeps, delta=DELTA, rank_tol=GPU_TAU)
     ncmp, div = compare_traces(res.trace, ref.trace, DELTA)
     if div is None:
         assert list(res.I) == ref.I and list(res.J) == ref.J
         assert res.info.k_eff == ref.k_eff
         np.testing.assert_allclose(res.sigma, ref.sigma, rtol=1e-9, atol=1e-12 * ref.sigma[0])
     A64 = A.astype(np.float64)
+    assert error_ok(rel_fro_error(A64, res.C, res.U, res.R),
+                    O.full_residual(O.Dense(A64), ref.C, ref.U, ref.R)[0])
+    ref = O.cross_approximation(O.Dense(A64), J0, k=k, sweeps=sweeps, delta=DELTA)
     err_ref = O.full_residual(O.Dense(A64), ref.C, ref.U, ref.R)[0]
     assert error_ok(rel_fro_error(A64, res.C, res.U, res.R), err_ref)
 
@@ -292,7 +299,7 @@ def test_dense_32768_full_size_parity(ctx):
     res = ctx.solve(L.make_source("dense", a=torch.from_numpy(A).to(DEV)), params, l, m, n,
                     want_strips=True, trace_cap=8192, device=DEV)
     assert res.info.status == 0
-    ref = O.cross_approximation(O.Dense(A), inp["J0"], k=k, sweeps=sw, delta=DELTA)
+    ref = O.cross_approximation(O.Dense(A), inp["J0"], k=k, sweeps=sw, delta=DELTA, rank_tol=GPU_TAU)
     ncmp, div = compare_traces(res.trace, ref.trace, DELTA)
     assert ncmp >= l
     if div is None:
@@ -300,5 +307,9 @@ def test_dense_32768_full_size_parity(ctx):
     C, R = res.C.cpu().numpy(), res.R.cpu().numpy()
     full64 = O.full_residual(O.Dense(A), C.astype(np.float64), res.U, R.astype(np.float64))[0]
     assert res.info.full_rel_err == pytest.approx(full64, rel=2e-3)
+    # the stored FP32 entries are exact in FP64, and sigma_k of the cross is
+    # far above both truncation thresholds (1e-6 and the FP64 default
+    # 1e-12), so this run is also the pure-FP64 error reference
+    assert ref.sigma[k - 1] > 1e-4 * ref.sigma[0]
     err_ref = O.full_residual(O.Dense(A), ref.C, ref.U, ref.R)[0]
     assert error_ok(res.info.full_rel_err, err_ref)

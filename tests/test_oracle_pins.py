@@ -303,7 +303,7 @@ def test_delta_matrix_is_missed_when_spike_is_not_touched():
     assert miss["rel"] < 1e-12 and hit["rel"] >= 1.0
 
 
-# --- rank-adaptive rule (GEPP start on every strip, growing cross) ---------------
+# --- rank-adaptive rule (growing cross, warm starts) ------------------------------
 
 def test_adaptive_grows_to_exact_rank_and_recovers():
     r = 20
@@ -311,8 +311,9 @@ def test_adaptive_grows_to_exact_rank_and_recovers():
     jc = W.draw_indices(56, 260, 64)
     I, J, U, k_eff, sigma, l, swaps = O.cross_approximation_adaptive(
         O.Dense(A), jc, l_init=8, l_max=64, k_max=64, sweeps=2, tol=1e-10)
-    assert l == 32                  # 8 -> 16 -> 32; at 32 the pivots past rank 20 vanish
+    assert l == 32                  # 8 -> 16 -> 32; at 32 the cross has rank 20 < l
     assert k_eff == r
+    assert np.sum(sigma > 1e-10 * sigma[0]) == r
     C, R = A[:, J], A[I, :]
     rel = np.linalg.norm(A - C @ U @ R) / np.linalg.norm(A)
     assert rel < 1e-10
@@ -323,7 +324,33 @@ def test_adaptive_respects_k_max_and_l_max():
     jc = W.draw_indices(58, 180, 48)
     I, J, U, k_eff, sigma, l, swaps = O.cross_approximation_adaptive(
         O.Dense(A), jc, l_init=12, l_max=48, k_max=30, sweeps=1, tol=1e-12)
-    assert l == 48 and k_eff == 30
+    assert l == 48 and k_eff == 30      # 12 -> 24 -> 48, where k = 48 >= k_max stops it
     s = np.linalg.svd(A, compute_uv=False)
     err = np.linalg.norm(A - A[:, J] @ U @ A[I, :])
     assert err >= np.sqrt(np.sum(s[30:] ** 2)) * (1 - 1e-9)     # Lemma 2.3
+
+
+def test_gepp_restricted_start_keeps_the_previous_rows():
+    rng = np.random.default_rng(61)
+    S = rng.standard_normal((40, 6))
+    first = [31, 4, 17]
+    piv = O.gepp_rows(S, first=first)
+    assert sorted(piv[:3]) == sorted(first) and len(set(piv)) == 6
+    # with every position given, the set is unchanged; with none it is GEPP
+    assert sorted(O.gepp_rows(S, first=[3, 9, 1, 30, 22, 8])) == [1, 3, 8, 9, 22, 30]
+    assert O.gepp_rows(S, first=[]) == O.gepp_rows(S)
+    # restricted to the given rows, the first pivot is their largest |S[:, 0]|
+    assert piv[0] == max(first, key=lambda r: abs(S[r, 0]))
+
+
+def test_adaptive_stops_on_the_sampled_estimate():
+    A = _rank_l(62, 200, 190, 10)
+    jc = W.draw_indices(63, 190, 48)
+    rows, cols = np.arange(0, 200, 3), np.arange(0, 190, 3)
+    one = O.cross_approximation_adaptive(O.Dense(A), jc, 12, 48, 48, 1, 1e-10)
+    many = O.cross_approximation_adaptive(O.Dense(A), jc, 12, 48, 48, 6, 1e-10,
+                                          sample_rows=rows, sample_cols=cols)
+    # rank 10 < l = 12 at once: no growth, exact recovery, the estimate is
+    # below tol after the first sweep, so six allowed sweeps stop after one
+    assert one[5] == many[5] == 12 and one[3] == many[3] == 10
+    assert one[0] == many[0] and one[1] == many[1]
