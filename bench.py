@@ -54,7 +54,7 @@ WORKLOADS = {
     "octree512": dict(form="batch", npoints=1 << 20, leaf=2048, n_pairs=512, l_init=12, l_max=96,
                       k_max=64, sweeps=2, tol=1e-6, q=32, seed_off=4, plain_subset=64),
     "serve": dict(form="serve", count=400, min_side=256, max_side=16384, budget_gb=40, slots=64,
-                  streams=32, rates=(0.5, 0.8, 0.95), seed_off=5, plain_subset=400),
+                  streams=32, max_grid=64, rates=(0.5, 0.8, 0.95), seed_off=5, plain_subset=400),
 }
 
 
@@ -698,7 +698,10 @@ def run_serve(args, wl_name):
     reqs = W.serving_requests(seed, wl["count"], wl["min_side"], wl["max_side"])
     prep = _serve_prepare(L, torch, reqs, dev)
     budget = int(wl["budget_gb"] * (1 << 30))
-    ctx = L.Context(local, max_slots=wl["slots"], mem_budget_bytes=budget, n_streams=wl["streams"])
+    # at most max_grid CTAs per maxvol launch, so that the cooperative grids
+    # of large requests leave SMs to the jobs beside them
+    ctx = L.Context(local, max_slots=wl["slots"], mem_budget_bytes=budget, n_streams=wl["streams"],
+                    max_grid=wl["max_grid"])
     # warm-up: every request once on the served path
     for _ in range(max(1, args.warmup // 3)):
         _serve_run(L, ctx, prep, reqs, None, [0])
@@ -752,6 +755,7 @@ def run_serve(args, wl_name):
         "config": {"workload": wl_name, "requests": len(prep), "sides": [wl["min_side"], wl["max_side"]],
                    "k": [8, 16, 32, 64], "generators": ["cauchy", "gauss h=0.5", "invdist"],
                    "admission_budget_gb": wl["budget_gb"], "slots": wl["slots"], "streams": wl["streams"],
+                   "maxvol_max_grid": wl["max_grid"],
                    "timing": "host wall clock from first submit to last fetch (serving latency)",
                    "l2": "inputs resident; requests run back to back (L2 not flushed between them)",
                    "parallelism": f"replicas{world}"},

@@ -88,6 +88,10 @@ typedef struct {
   int32_t n_streams;          /* own streams (1..32; <= 0: 1).  A job runs on the
                                  least loaded one, so jobs submitted while others
                                  run overlap on the device (continuous admission). */
+  int32_t max_grid;           /* CTAs per maxvol launch at most (<= 0: one per SM).
+                                 A smaller grid leaves SMs to the other jobs in
+                                 flight; a strip whose chunks would not fit in
+                                 shared memory still gets the CTAs it needs. */
 } lra_ctx_params;
 
 typedef struct {

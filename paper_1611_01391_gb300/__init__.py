@@ -38,7 +38,7 @@ LRA_FLAG_FULL_RESIDUAL = 2
 class lra_ctx_params(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("max_slots", ctypes.c_int32),
                 ("mem_budget_bytes", ctypes.c_uint64), ("stream", ctypes.c_void_p),
-                ("n_streams", ctypes.c_int32)]
+                ("n_streams", ctypes.c_int32), ("max_grid", ctypes.c_int32)]
 
 
 class lra_source(ctypes.Structure):
@@ -155,8 +155,8 @@ def _check(code, ctx=None, ok=(LRA_OK,)):
 
 # ---- the C ABI, one function per entry point --------------------------------
 def lra_cross_create(device: int = 0, max_slots: int = 64, mem_budget_bytes: int = 0, stream=None,
-                     n_streams: int = 1):
-    p = lra_ctx_params(device, max_slots, mem_budget_bytes, stream or None, n_streams)
+                     n_streams: int = 1, max_grid: int = 0):
+    p = lra_ctx_params(device, max_slots, mem_budget_bytes, stream or None, n_streams, max_grid)
     ctx = _ctx_p()
     _check(_create(ctypes.byref(ctx), ctypes.byref(p)))
     return ctx

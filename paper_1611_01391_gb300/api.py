@@ -81,8 +81,8 @@ class SolveResult:
 class Context:
     """One library context (one device, one stream)."""
 
-    def __init__(self, device=0, max_slots=64, mem_budget_bytes=0, stream=None, n_streams=1):
-        self.ctx = lra_cross_create(device, max_slots, mem_budget_bytes, stream, n_streams)
+    def __init__(self, device=0, max_slots=64, mem_budget_bytes=0, stream=None, n_streams=1, max_grid=0):
+        self.ctx = lra_cross_create(device, max_slots, mem_budget_bytes, stream, n_streams, max_grid)
 
     def close(self):
         if self.ctx:

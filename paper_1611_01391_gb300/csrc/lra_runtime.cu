@@ -78,6 +78,7 @@ struct lra_ctx {
   std::vector<cudaStream_t> streams;       // jobs are spread over these
   std::vector<int> stream_load;            // active jobs per stream
   int sms = 0;
+  int max_grid = 0;  // CTAs per maxvol launch at most
   size_t smem_optin = 0;
   int max_slots = 64;
   uint64_t budget = 0;
@@ -393,6 +394,7 @@ lra_status lra_cross_create(lra_ctx** out, const lra_ctx_params* params) {
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
   if (!coop) { delete ctx; return LRA_ECUDA; }
   ctx->sms = prop.multiProcessorCount;
+  ctx->max_grid = params->max_grid > 0 ? std::min(params->max_grid, ctx->sms) : ctx->sms;
   ctx->smem_optin = prop.sharedMemPerBlockOptin;
   if (params->stream) {
     ctx->stream = static_cast<cudaStream_t>(params->stream);
@@ -473,8 +475,12 @@ lra_status lra_cross_submit(lra_ctx* ctx, const lra_source* src, const lra_param
   j->m = src->m; j->n = src->n; j->q = p->resid_q; j->s = p->resid_s;
   j->delta = p->delta; j->rank_tol = p->rank_tol; j->tol = p->tol;
   j->src = make_src(src);
-  if (!plan_maxvol(j->m, j->l, ctx->sms, ctx->smem_optin, &j->plan_col) ||
-      !plan_maxvol(j->n, j->l, ctx->sms, ctx->smem_optin, &j->plan_row)) {
+  // at most max_grid CTAs, more only where the strip's chunks need them
+  auto plan = [&](long long N, MaxvolPlan* pl) {
+    return plan_maxvol(N, j->l, ctx->max_grid, ctx->smem_optin, pl) ||
+           plan_maxvol(N, j->l, ctx->sms, ctx->smem_optin, pl);
+  };
+  if (!plan(j->m, &j->plan_col) || !plan(j->n, &j->plan_row)) {
     delete j;
     return fail(ctx, LRA_ETOOLARGE, "strip does not fit in the shared memory of the grid");
   }
