@@ -304,7 +304,10 @@ template <int NT>
 __device__ void jacobi_dd(dd* W, dd* Z, int l, int* flag) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int np = (l + 1) & ~1;
-  const double tol = (double)l * 3.6e-15;  // about l * 2^-48
+  // about l * 2^-48; the test below runs on the FP32 high parts (relative
+  // error 2^-24 of a threshold), keeping the FP64 pipe (1/64 rate) off the
+  // inner loop
+  const float tol = (float)l * 3.6e-15f;
   const int gl = lane & 7, ngroups = (NT / 32) * 4;
   for (int sweep = 0; sweep < 60; ++sweep) {
     if (tid == 0) *flag = 0;
@@ -332,8 +335,7 @@ __device__ void jacobi_dd(dd* W, dd* Z, int l, int* flag) {
         sg = acc_group_sum<8>(sg);
         if (!act) continue;
         const dd al = acc_value(sa), be = acc_value(sb), ga = acc_value(sg);
-        const double a2 = dd_to_double(al), b2 = dd_to_double(be), g2 = dd_to_double(ga);
-        if (a2 == 0.0 || b2 == 0.0 || g2 * g2 <= tol * tol * a2 * b2) continue;
+        if (!(al.hi > 0.0f) || !(be.hi > 0.0f) || fabsf(ga.hi) <= tol * sqrtf(al.hi) * sqrtf(be.hi)) continue;
         const float zeta = dd_add(be, dd_neg(al)).hi / (2.0f * ga.hi);
         const float tf = fabsf(zeta) > 1e18f
                              ? 0.5f / zeta
