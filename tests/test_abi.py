@@ -70,3 +70,51 @@ def test_footprint_and_validation_on_host():
         assert e.code == L.LRA_EINVAL
     else:
         raise AssertionError("k > l accepted")
+
+
+def _c_fields(struct):
+    """Field names of a typedef'd struct in include/lra_cross.h, in order."""
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "lra_cross.h")).read(), flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + struct + r"\s*;", text).group(1)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        # "type a, b" or "type* a" -> the declarators after the type
+        parts = decl.replace("*", " ").split()
+        rest = " ".join(parts[1:]) if parts[0] != "const" else " ".join(parts[2:])
+        names += [n.strip() for n in rest.split(",")]
+    return names
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the ABI structs have the size and field offsets
+    the C compiler gives the header's declarations."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        import pytest
+        pytest.skip("no C compiler")
+    import paper_1611_01391_gb300 as L
+    structs = ["lra_ctx_params", "lra_source", "lra_params", "lra_info", "lra_cur_out", "lra_block",
+               "lra_batch_params", "lra_batch_out"]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lra_cross.h"', "int main(void) {"]
+    for s in structs:
+        lines.append(f'  printf("{s} size %zu\\n", sizeof({s}));')
+        for f in _c_fields(s):
+            lines.append(f'  printf("{s} {f} %zu\\n", offsetof({s}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    for line in out.splitlines():
+        s, f, v = line.split()
+        cls = getattr(L, s)
+        if f == "size":
+            assert ctypes.sizeof(cls) == int(v), (s, ctypes.sizeof(cls), v)
+        else:
+            assert getattr(cls, f).offset == int(v), (s, f, getattr(cls, f).offset, v)
