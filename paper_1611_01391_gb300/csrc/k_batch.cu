@@ -43,14 +43,16 @@ namespace cg = cooperative_groups;
 namespace lra {
 namespace {
 
-constexpr int kCS = 4;                    // CTAs per cluster
 constexpr int kBT = 256;                  // threads per CTA
-constexpr int kRowsPerCta = kMaxBatchSide / kCS;
+constexpr int kStripFloats = (kMaxBatchSide / 4) * kMaxL;  // strip chunk per CTA (196 KB)
 constexpr int kMaxQ = 64;                 // sample size per side
+constexpr int kDeferred = 1;              // first-pass status of a block left to the second
 
-struct BatchSmem {
-  float B[kRowsPerCta * kMaxL];           // strip chunk, row-major with stride l
-  float colj[kRowsPerCta];
+// Shared memory of one CTA of a CS-CTA cluster.
+template <int CS>
+struct BatchSmemT {
+  float B[kStripFloats];                  // strip chunk, row-major with stride l
+  float colj[kMaxBatchSide / CS];
   float rrow[kMaxL];
   float slot_row[2][kMaxL];               // published candidate rows (read by peers)
   unsigned long long slot_key[2];
@@ -61,7 +63,7 @@ struct BatchSmem {
   int win_nf;
   int pos[kMaxL];
   int Iset[kMaxL], Jset[kMaxL];
-  unsigned char used[kRowsPerCta];
+  unsigned char used[kMaxBatchSide / CS];
   int blk;
   int status;
   int swaps;
@@ -73,8 +75,8 @@ struct BatchSmem {
 // the nucleus (W, V, sigma, 1/sigma^2, order) and the estimate's operands
 // reuse the strip area once the sweeps are over
 static_assert(2 * kMaxL * kMaxL * sizeof(dd) + kMaxL * (sizeof(double) + sizeof(dd) + sizeof(int)) +
-                      sizeof(SvdScratch) <= sizeof(BatchSmem::B), "nucleus area");
-static_assert(sizeof(float) * (2 * kMaxL * kMaxL + 4 * kMaxQ * kMaxL) <= sizeof(BatchSmem::B),
+                      sizeof(SvdScratch) <= sizeof(float) * kStripFloats, "nucleus area");
+static_assert(sizeof(float) * (2 * kMaxL * kMaxL + 4 * kMaxQ * kMaxL) <= sizeof(float) * kStripFloats,
               "estimate area");
 
 __device__ __forceinline__ unsigned long long pack_key(float v, int idx) {
@@ -93,7 +95,8 @@ __device__ __forceinline__ void consider_f(unsigned long long& best, int& nf, fl
 }
 
 // CTA-wide reduction of (key, nf); result in s->win_key / s->win_nf.
-__device__ __forceinline__ void cta_reduce(BatchSmem* s, unsigned long long key, int nf) {
+template <typename S>
+__device__ __forceinline__ void cta_reduce(S* s, unsigned long long key, int nf) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -130,13 +133,13 @@ __device__ __forceinline__ void cta_reduce(BatchSmem* s, unsigned long long key,
 // within FP32 rounding of the data, which an FP32 X^{-1} would not give.
 // Returns false when the block failed (s->status set identically in all
 // CTAs).  On return s->pos holds the selected strip rows.
-template <int KIND>
-__device__ bool half_step(const BatchArgs& a, cg::cluster_group& cl, BatchSmem* s, bool vertical,
+template <int KIND, int CS>
+__device__ bool half_step(const BatchArgs& a, cg::cluster_group& cl, BatchSmemT<CS>* s, bool vertical,
                           long long row0, long long col0, int N, int l, const int* other,
                           int nfirst, const int* first) {
   const int rank = (int)cl.block_rank();
   const int tid = threadIdx.x;
-  const int rpc = (N + kCS - 1) / kCS;
+  const int rpc = (N + CS - 1) / CS;
   const int r0 = rank * rpc;
   const int nr = max(0, min(rpc, N - r0));
   for (int e = tid; e < nr * l; e += kBT) {
@@ -174,7 +177,7 @@ __device__ bool half_step(const BatchArgs& a, cg::cluster_group& cl, BatchSmem* 
     cl.sync();
     unsigned long long win = 0ull;
     int wnf = 0, owner = 0;
-    for (int p = 0; p < kCS; ++p) {
+    for (int p = 0; p < CS; ++p) {
       const unsigned long long k = *cl.map_shared_rank(&s->slot_key[buf], p);
       wnf |= *cl.map_shared_rank(&s->slot_nf[buf], p);
       if (k > win) {
@@ -272,8 +275,8 @@ __device__ __forceinline__ void dot2_b(float x, float y, float& p, float& c) {
 // the block's outputs are (re)written: I, J, sigma, k_eff = min(k_max, k),
 // U = (X_k)^+ in FP64 and the Appendix F estimate; s->stop is set when
 // k >= k_max or the estimate is <= tol.
-template <int KIND>
-__device__ void cross_step(const BatchArgs& a, BatchSmem* s, int b, long long row0, long long col0,
+template <int KIND, typename S>
+__device__ void cross_step(const BatchArgs& a, S* s, int b, long long row0, long long col0,
                            long long n, int l, int lmax_b) {
   const int tid = threadIdx.x;
   dd* W = reinterpret_cast<dd*>(s->B);
@@ -411,25 +414,42 @@ __device__ void cross_step(const BatchArgs& a, BatchSmem* s, int b, long long ro
   __syncthreads();
 }
 
-template <int KIND>
-__global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kBT, 1) batch_kernel(BatchArgs a) {
+// Two passes over the blocks.  Pass 1 (CS = 1): one CTA per block, the
+// whole strip in its shared memory, no cluster barrier per decision, 152
+// blocks in flight; a block whose rank rule asks for a cross larger than one
+// CTA can hold (l max(m, n) > kStripFloats) is left with status kDeferred.
+// Pass 2 (CS = 4): the deferred blocks only, from their start, the strip
+// split over a 4-CTA cluster.  The decisions (argmax with the same
+// tie-break over the whole strip) and the arithmetic per entry do not depend
+// on the split, so a block's result is the same in either pass.
+template <int KIND, int CS>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kBT, 1) batch_kernel(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char bsm[];
-  BatchSmem* s = reinterpret_cast<BatchSmem*>(bsm);
+  BatchSmemT<CS>* s = reinterpret_cast<BatchSmemT<CS>*>(bsm);
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int tid = threadIdx.x;
+  constexpr bool kFirst = (CS == 1);
+  int* queue = a.queue + (kFirst ? 0 : 1);
   for (;;) {
-    if (rank == 0 && tid == 0) s->blk = atomicAdd(a.queue, 1);
+    if (rank == 0 && tid == 0) s->blk = atomicAdd(queue, 1);
     cl.sync();
     const int b = *cl.map_shared_rank(&s->blk, 0);
     if (b >= a.n_blocks) {
       cl.sync();  // nobody leaves while a peer may still read the leader's index
       break;
     }
+    if (!kFirst && a.out_status[b] != kDeferred) {
+      cl.sync();  // the leader may fetch the next index
+      continue;
+    }
     const long long row0 = a.blocks[4 * b + 0], m = a.blocks[4 * b + 1];
     const long long col0 = a.blocks[4 * b + 2], n = a.blocks[4 * b + 3];
     const int lmax_b = (int)min((long long)a.l_max, min(m, n));
+    // largest cross whose strips fit this cluster's shared memory
+    const int lcap = (int)min((long long)lmax_b, kStripFloats / ((max(m, n) + CS - 1) / CS));
     int l = min(a.l_init, lmax_b);
+    bool deferred = kFirst && l > lcap;
     for (int t = tid; t < l; t += kBT) s->Jset[t] = a.jcand[(size_t)b * a.l_max + t];
     if (tid == 0) {
       s->status = LRA_OK;
@@ -439,13 +459,13 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kBT, 1) batch_kern
     bool ok = true;
     int n_i = 0;       // rows of the previous I (none before the first sweep)
     int at_size = 0;   // sweeps at the current cross size
-    for (;;) {
-      ok = half_step<KIND>(a, cl, s, true, row0, col0, (int)m, l, s->Jset, n_i, s->Iset);
+    while (!deferred) {
+      ok = half_step<KIND, CS>(a, cl, s, true, row0, col0, (int)m, l, s->Jset, n_i, s->Iset);
       if (!ok) break;
       for (int t = tid; t < l; t += kBT) s->Iset[t] = s->pos[t];
       n_i = l;
       __syncthreads();
-      ok = half_step<KIND>(a, cl, s, false, row0, col0, (int)n, l, s->Iset, l, s->Jset);
+      ok = half_step<KIND, CS>(a, cl, s, false, row0, col0, (int)n, l, s->Iset, l, s->Jset);
       if (!ok) break;
       for (int t = tid; t < l; t += kBT) s->Jset[t] = s->pos[t];
       __syncthreads();
@@ -455,6 +475,10 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kBT, 1) batch_kern
       const int grow = *cl.map_shared_rank(&s->grow, 0);
       const int stop = *cl.map_shared_rank(&s->stop, 0);
       if (grow) {
+        if (min(lmax_b, 2 * l) > lcap) {  // only the 4-CTA pass holds this cross
+          deferred = true;
+          break;
+        }
         // append the next candidate columns that are not in J (same in every CTA)
         if (tid == 0) {
           const int l_new = min(lmax_b, 2 * l);
@@ -475,7 +499,9 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kBT, 1) batch_kern
       }
       if (stop || at_size >= a.sweeps) break;
     }
-    if (rank == 0) {
+    if (rank == 0 && deferred) {
+      if (tid == 0) a.out_status[b] = kDeferred;
+    } else if (rank == 0) {
       if (tid == 0) {
         a.out_status[b] = ok ? (int)LRA_OK : s->status;
         a.out_l[b] = l;
@@ -501,22 +527,30 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kBT, 1) batch_kern
 
 }  // namespace
 
-size_t batch_smem_bytes() { return sizeof(BatchSmem); }
+size_t batch_smem_bytes() { return sizeof(BatchSmemT<1>); }
 
+template <int KIND, int CS>
+static cudaError_t launch_pass(const BatchArgs& a, int sms, cudaStream_t st) {
+  const size_t smem = sizeof(BatchSmemT<CS>);
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(batch_kernel<KIND, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e) return e;
+    attr = true;
+  }
+  batch_kernel<KIND, CS><<<(sms / CS) * CS, kBT, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// a.queue holds two zeroed counters, one per pass
 cudaError_t launch_batch(const BatchArgs& a, int sms, cudaStream_t st) {
-  const size_t smem = sizeof(BatchSmem);
-  const int grid = (sms / kCS) * kCS;
   cudaError_t e = cudaSuccess;
   LRA_DISPATCH_KIND(a.src.kind, ({
-    static bool attr = false;
-    if (!attr) {
-      e = cudaFuncSetAttribute(batch_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr = (e == cudaSuccess);
-    }
-    if (e == cudaSuccess) batch_kernel<K><<<grid, kBT, smem, st>>>(a);
+    e = launch_pass<K, 1>(a, sms, st);
+    if (!e) e = launch_pass<K, 4>(a, sms, st);
   }));
-  if (e) return e;
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace lra

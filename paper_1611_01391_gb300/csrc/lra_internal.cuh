@@ -96,7 +96,7 @@ struct BatchArgs {
   int q;
   int l_init, l_max, k_max, sweeps, max_swaps;
   float tol, delta;
-  int* queue;               // work counter, zero at launch
+  int* queue;               // two work counters (one per pass), zero at launch
   int* out_status;
   int* out_l;
   int* out_keff;

@@ -662,7 +662,7 @@ lra_status lra_cross_submit_batch(lra_ctx* ctx, const lra_source* src, const lra
   const size_t L = (size_t)p->l_max, q = (size_t)p->sample, NB = (size_t)nb;
   Layout lay;
   const size_t o_js = lay.take(sizeof(JobStatus));
-  const size_t o_queue = lay.take(sizeof(int));
+  const size_t o_queue = lay.take(2 * sizeof(int));  // one work counter per pass
   const size_t o_blocks = lay.take(sizeof(long long) * 4 * NB);
   const size_t o_jc = lay.take(sizeof(int) * NB * L);
   const size_t o_sr = lay.take(sizeof(int) * NB * std::max<size_t>(q, 1));
@@ -740,7 +740,7 @@ lra_status lra_cross_submit_batch(lra_ctx* ctx, const lra_source* src, const lra
   static_assert(sizeof(lra_block) == 4 * sizeof(long long), "lra_block layout");
   if ((e = cudaEventCreate(&j->ev_start)) || (e = cudaEventCreate(&j->ev_end)) ||
       (e = cudaMemcpyAsync(j->js, &init, sizeof(init), cudaMemcpyHostToDevice, s)) ||
-      (e = cudaMemsetAsync(j->b_queue, 0, sizeof(int), s)) ||
+      (e = cudaMemsetAsync(j->b_queue, 0, 2 * sizeof(int), s)) ||
       (e = cudaMemsetAsync(j->b_err, 0, sizeof(double) * NB, s)) ||
       (e = cudaMemsetAsync(j->b_keff, 0, sizeof(int) * NB, s)) ||
       (e = cudaMemcpyAsync(j->b_blocks, blocks, sizeof(lra_block) * NB, cudaMemcpyHostToDevice, s)) ||

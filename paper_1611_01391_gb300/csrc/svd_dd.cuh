@@ -66,13 +66,39 @@ __device__ __forceinline__ dd dd_mul(dd a, dd b) {
 
 __device__ __forceinline__ dd dd_fma(dd a, dd b, dd c) { return dd_add(dd_mul(a, b), c); }
 
-// x^{-1/2} for x in [1, 2]: FP32 seed, one double-float Newton step
-// y <- y + y (1 - x y^2) / 2.
-__device__ __forceinline__ dd dd_rsqrt_1_2(dd x) {
-  const float y0 = rsqrtf(x.hi);
-  const dd y = dd_make(y0);
-  const dd r = dd_add(dd_make(1.0f), dd_neg(dd_mul(x, dd_mul(y, y))));
-  return dd_add(y, dd_mul(y, dd{0.5f * r.hi, 0.5f * r.lo}));
+// Plane rotation that annihilates the off-diagonal of the 2 x 2 Gram matrix
+// [a g; g b] (Golub & Van Loan, Algorithm 8.5.1): zeta = (b - a) / (2 g),
+// t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)).  t is needed to FP32
+// accuracy only (any t gives an orthogonal rotation; t sets the speed of
+// convergence), so it takes a short FP32 chain.  The cosine
+// c = (1 + t^2)^{-1/2} must be accurate to double-float precision: the
+// correctly rounded FP32 reciprocal square root y0 of x = 1 + t^2 (formed
+// exactly as a pair) is refined by one Newton step y0 + y0 r / 2 with
+// r = 1 - x y0^2; r is of order 2^-23 and its FMA-built FP32 value is
+// accurate to about 2^-47.  Returns c; *t_out = t.
+__device__ __forceinline__ dd rotation_cosine(dd a, dd b, dd g, float* t_out) {
+  const dd d = two_sum(b.hi, -a.hi);
+  const float diff = __fadd_rn(d.hi, __fadd_rn(d.lo, __fsub_rn(b.lo, a.lo)));
+  const float zeta = __fdividef(diff, 2.0f * g.hi);
+  float t;
+  if (fabsf(zeta) > 1e18f) {
+    t = __fdividef(0.5f, zeta);
+  } else {
+    const float q = fmaf(zeta, zeta, 1.0f);
+    t = copysignf(__frcp_rn(fabsf(zeta) + q * __frsqrt_rn(q)), zeta);
+  }
+  *t_out = t;
+  const float t2 = __fmul_rn(t, t);
+  const float t2e = fmaf(t, t, -t2);             // t^2 = t2 + t2e exactly
+  const dd xh = two_sum(1.0f, t2);
+  const float xl = __fadd_rn(xh.lo, t2e);        // x = xh.hi + xl
+  const float y0 = __frsqrt_rn(xh.hi);
+  const float y2 = __fmul_rn(y0, y0);
+  const float y2e = fmaf(y0, y0, -y2);           // y0^2 = y2 + y2e exactly
+  float r = fmaf(-xh.hi, y2, 1.0f);
+  r = fmaf(-xh.hi, y2e, r);
+  r = fmaf(-xl, y2, r);
+  return quick_two_sum(y0, __fmul_rn(__fmul_rn(0.5f, y0), r));
 }
 
 // Compensated accumulator of a dot product of double-float vectors: the
@@ -336,12 +362,9 @@ __device__ void jacobi_dd(dd* W, dd* Z, int l, int* flag) {
         if (!act) continue;
         const dd al = acc_value(sa), be = acc_value(sb), ga = acc_value(sg);
         if (!(al.hi > 0.0f) || !(be.hi > 0.0f) || fabsf(ga.hi) <= tol * sqrtf(al.hi) * sqrtf(be.hi)) continue;
-        const float zeta = dd_add(be, dd_neg(al)).hi / (2.0f * ga.hi);
-        const float tf = fabsf(zeta) > 1e18f
-                             ? 0.5f / zeta
-                             : (zeta >= 0.0f ? 1.0f : -1.0f) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
-        const dd x = dd_add(dd_make(1.0f), two_sum(__fmul_rn(tf, tf), fmaf(tf, tf, -__fmul_rn(tf, tf))));
-        const dd c = dd_rsqrt_1_2(x);
+        float tf_out;
+        const dd c = rotation_cosine(al, be, ga, &tf_out);
+        const float tf = tf_out;
         const dd s = dd_mul(c, dd_make(tf));
         const dd ns = dd_neg(s);
         dd* zp = Z + p * l;
