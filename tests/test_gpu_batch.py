@@ -109,3 +109,39 @@ def test_batch_rejects_invalid_blocks(ctx, case):
     jbad[1, 1] = jbad[1, 0]              # repeated candidate column
     with pytest.raises(L.LraError):
         _run(ctx, pts, blocks, jbad, sr, sc)
+
+
+def test_blocks_that_need_the_cluster_pass(ctx):
+    """Blocks of 2048 x 2048 whose rank exceeds what one CTA's shared memory
+    holds (l > 24 at that side) finish in the 4-CTA pass; small blocks in the
+    same launch finish in the first.  Errors against the oracle's rule, and
+    the same results when the large blocks run alone."""
+    x = W.cloud_points(W.BASE_SEED + 70, 6144)
+    d = torch.from_numpy(x).cuda()
+    h = 0.6
+    src = L.make_source("gauss", x=d, y=d, h=h)
+    blocks = np.array([[0, 2048, 2048, 2048], [2048, 2048, 4096, 2048], [0, 300, 4096, 260],
+                       [4096, 2048, 0, 2048], [100, 200, 5000, 190]], np.int64)
+    jc, sr, sc = W.block_candidates(W.BASE_SEED + 71, blocks, L_MAX, Q)
+    p, keep = make_batch_params(L_INIT, L_MAX, K_MAX, SWEEPS, TOL, jc, sr, sc)
+    r = solve_batch(ctx, src, blocks, p, L_MAX)
+    assert np.all(r.status == 0)
+    assert r.l[0] > 24 and r.l[1] > 24 and r.l[3] > 24     # went through the cluster pass
+    s64 = O.Gauss(x, x, h, "fp64")
+    for b, (r0, m, c0, n) in enumerate(blocks):
+        sub = SubSource(s64, r0, m, c0, n)
+        A = sub.block(np.arange(m), np.arange(n))
+        I, J, U = _nucleus(r, b)
+        err = np.linalg.norm(A - A[:, J] @ U @ A[I, :]) / np.linalg.norm(A)
+        oI, oJ, oU, ok, osig, ol, osw = O.cross_approximation_adaptive(sub, jc[b], L_INIT, L_MAX, K_MAX,
+                                                                       SWEEPS, TOL, sample_rows=sr[b],
+                                                                       sample_cols=sc[b])
+        oerr = np.linalg.norm(A - A[:, oJ] @ oU @ A[oI, :]) / np.linalg.norm(A)
+        # the Gaussian kernel's rank-k_max truncation can be ill posed
+        # (sigma_64 ~ sigma_65): allow the spread FP32 entries cause
+        assert err <= max(1.25 * oerr, 1e-5), (b, err, oerr)
+    sel = np.array([0, 3])
+    p2, keep2 = make_batch_params(L_INIT, L_MAX, K_MAX, SWEEPS, TOL, jc[sel], sr[sel], sc[sel])
+    r2 = solve_batch(ctx, src, blocks[sel], p2, L_MAX)
+    for name in ("l", "k_eff", "I", "J", "U", "est_err"):
+        np.testing.assert_array_equal(getattr(r, name)[sel], getattr(r2, name))
