@@ -77,12 +77,33 @@ def fp64_peak_tflops(sm_mhz):
 
 
 # ---------------------------------------------------------------------------
+# ranks: one process per GPU, each solving its own units (weak scaling); the
+# only collective is the max of the timed region over ranks
+# ---------------------------------------------------------------------------
+
+def max_over_ranks(x, world, device):
+    """Largest value of x over the ranks of the default process group."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_seed_offset(rank):
+    """Seed offset of a rank's own synthetic units (distinct per rank)."""
+    return 1000 * rank
+
+
+# ---------------------------------------------------------------------------
 # inputs
 # ---------------------------------------------------------------------------
 
 def make_inputs(wl, rank=0):
     import workloads as W
-    seed = W.BASE_SEED + wl["seed_off"] + 1000 * rank
+    seed = W.BASE_SEED + wl["seed_off"] + rank_seed_offset(rank)
     m, n, l = wl["m"], wl["n"], wl["l"]
     inp = {"J0": W.draw_indices(seed + 100, n, l),
            "rows": W.draw_indices(seed + 200, m, wl["q"], sort=True),
@@ -320,11 +341,7 @@ def run_ours(args, wl_name):
         dist.barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     for inf in infos:
         if inf.status != 0:
             raise RuntimeError(f"solve failed: {L.lra_status_str(inf.status)}")
@@ -446,9 +463,9 @@ def run_ours(args, wl_name):
 # batched form: many far-field blocks in one persistent launch
 # ---------------------------------------------------------------------------
 
-def make_batch_inputs(wl):
+def make_batch_inputs(wl, rank=0):
     import workloads as W
-    seed = W.BASE_SEED + wl["seed_off"]
+    seed = W.BASE_SEED + wl["seed_off"] + rank_seed_offset(rank)
     pts, blocks = W.octree_block_pairs(seed, npoints=wl["npoints"], leaf=wl["leaf"],
                                        n_pairs=wl["n_pairs"])
     jc, sr, sc = W.block_candidates(seed + 1, blocks, wl["l_max"], wl["q"])
@@ -475,7 +492,7 @@ def run_batch(args, wl_name):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     wl = WORKLOADS[wl_name]
-    pts, blocks, jc, sr, sc = make_batch_inputs(wl)
+    pts, blocks, jc, sr, sc = make_batch_inputs(wl, rank)
     nb = len(blocks)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
@@ -494,6 +511,8 @@ def run_batch(args, wl_name):
         assert np.all(r.status == 0), np.unique(r.status)
     clocks = ClockSampler(local)
     torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
     clocks.start()
     time.sleep(0.3)
     evs, res = [], []
@@ -509,11 +528,7 @@ def run_batch(args, wl_name):
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     step_ms = [x.elapsed_time(y) for x, y in evs]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     r = res[-1]
     assert np.all(r.status == 0)
     value = world * nb * args.steps / (total_ms / 1e3)
@@ -694,7 +709,7 @@ def run_serve(args, wl_name):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     wl = WORKLOADS[wl_name]
-    seed = W.BASE_SEED + wl["seed_off"] + 1000 * rank
+    seed = W.BASE_SEED + wl["seed_off"] + rank_seed_offset(rank)
     reqs = W.serving_requests(seed, wl["count"], wl["min_side"], wl["max_side"])
     prep = _serve_prepare(L, torch, reqs, dev)
     budget = int(wl["budget_gb"] * (1 << 30))
@@ -707,6 +722,8 @@ def run_serve(args, wl_name):
         _serve_run(L, ctx, prep, reqs, None, [0])
     clocks = ClockSampler(local)
     torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
     clocks.start()
     time.sleep(0.3)
     # capacity: closed loop (everything queued at t = 0), K repetitions
@@ -716,7 +733,7 @@ def run_serve(args, wl_name):
         mk, lat, errs = _serve_run(L, ctx, prep, reqs, None, launches)
         caps.append(mk)
         cap_lat += lat
-    capacity = len(prep) / statistics.median(caps)
+    capacity = len(prep) / max_over_ranks(statistics.median(caps), world, dev)
     # open loop at fractions of the measured capacity
     sweep = []
     for frac in wl["rates"]:
