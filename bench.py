@@ -614,7 +614,7 @@ def run_batch(args, wl_name):
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": captured_traffic("k_batch.cu", f"batch_{wl_name}.md"),
                      "peak_source": f"FP32 FMA rate: {SMS} SMs x 128 FMA/clk x median SM clock {sm_mhz:.0f} MHz",
-                     "note": "elimination/update FLOPs counted by the kernel; the decision chain (one cluster barrier per pivot) bounds it"},
+                     "note": "elimination/update FLOPs counted by the kernel; the decision chain (a CTA reduction per pivot) bounds it"},
         "gpu_launches": args.steps,
         "clocks": clk,
         "e2e": {"value": nb * len(ts) / sum(ts), "unit": "blocks/s", "h2d_bytes_per_step": int(h2d),

@@ -152,8 +152,7 @@ cross_inverse_kernel(const float* __restrict__ strip, long long si, long long st
         unsigned long long best = 0ull;
         int br = l;
         for (int r = t + tid; r < l; r += 32) {
-          const unsigned long long k =
-              (unsigned long long)__double_as_longlong(A[(size_t)r * w + ct]) & 0x7fffffffffffffffull;
+          const unsigned long long k = abs_bits(A[(size_t)r * w + ct]);
           if (br == l || k > best) { best = k; br = r; }
         }
 #pragma unroll

@@ -49,7 +49,7 @@ constexpr unsigned long long kAbsMask = 0x7fffffffffffffffull;
 constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
 
 __device__ __forceinline__ void consider(Best& b, double x, int idx) {
-  const unsigned long long k = (unsigned long long)__double_as_longlong(x) & kAbsMask;
+  const unsigned long long k = abs_bits(x);
   if (k >= kInfBits) {
     b.nf = 1;
   } else if (k > b.k || (k == b.k && idx < b.idx)) {
