@@ -222,8 +222,104 @@ cross_inverse_kernel(const float* __restrict__ strip, long long si, long long st
   cl.sync();  // no peer reads this CTA's shared memory after it exits
 }
 
+// The same elimination for l <= 32 on one CTA: at that size every step is a
+// chain of FP64 latencies (a division is ~430 cycles on this part), so the
+// step is cut to one warp (pivot, reciprocal, scaled pivot row), one
+// barrier, one pass that writes the next matrix from the current one (two
+// buffers, so no entry is read after it is overwritten) and a second
+// barrier.  The arithmetic per entry is that of the cluster kernel.
+constexpr int kInvSmallL = 32;
+constexpr int kInvSmallT = 128;
+
+__global__ void __launch_bounds__(kInvSmallT, 1)
+cross_inverse_small_kernel(const float* __restrict__ strip, long long si, long long st,
+                           const int* __restrict__ pos, int l, double* __restrict__ xinv, JobStatus* js) {
+  if (js->status != LRA_OK || js->stop) return;
+  __shared__ double buf[2][kInvSmallL * kInvSmallL];
+  __shared__ double rowt[kInvSmallL];
+  __shared__ int p_s;
+  __shared__ int swaps[kInvSmallL], at[kInvSmallL], dest[kInvSmallL];
+  const int tid = threadIdx.x, lane = tid & 31;
+  int bad = 0;
+  for (int e = tid; e < l * l; e += kInvSmallT) {
+    const int r = e / l, c = e - r * l;
+    const double v = (double)strip[(long long)__ldg(pos + r) * si + (long long)c * st];
+    if (!(fabs(v) <= DBL_MAX)) bad = 1;
+    buf[0][e] = v;
+  }
+  if (__syncthreads_or(bad)) {
+    if (tid == 0) set_status(js, LRA_ENONFINITE);
+    return;
+  }
+  int cur = 0;
+  for (int t = 0; t < l; ++t) {
+    const double* A = buf[cur];
+    if (tid < 32) {  // pivot: largest |A[r][t]|, r >= t (smallest r on ties)
+      const int r = t + lane;
+      unsigned long long best = 0ull;
+      int br = l;
+      if (r < l) {
+        best = abs_bits(A[r * l + t]);
+        br = r;
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int orr = __shfl_down_sync(0xffffffffu, br, off);
+        if (orr < l && (br == l || ob > best || (ob == best && orr < br))) { best = ob; br = orr; }
+      }
+      const int p = __shfl_sync(0xffffffffu, (best != 0ull && br < l) ? br : -1, 0);
+      double rp = 0.0;
+      if (lane == 0 && p >= 0) rp = 1.0 / A[p * l + t];
+      rp = __shfl_sync(0xffffffffu, rp, 0);
+      if (p >= 0 && lane < l) rowt[lane] = (lane == t) ? rp : A[p * l + lane] * rp;
+      if (lane == 0) {
+        p_s = p;
+        swaps[t] = p;
+      }
+    }
+    __syncthreads();
+    const int p = p_s;
+    if (p < 0) {
+      if (tid == 0) set_status(js, LRA_ESINGULAR);
+      return;
+    }
+    double* N = buf[cur ^ 1];
+    for (int e = tid; e < l * l; e += kInvSmallT) {
+      const int r = e / l, c = e - r * l;
+      if (r == t) {
+        N[e] = rowt[c];
+      } else {
+        const int rr = (r == p) ? t : r;  // row r after the swap is row rr before it
+        const double a = (c == t) ? 0.0 : A[rr * l + c];
+        N[e] = fma(-A[rr * l + t], rowt[c], a);
+      }
+    }
+    cur ^= 1;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    for (int q = 0; q < l; ++q) at[q] = q;
+    for (int t = l - 1; t >= 0; --t) {
+      const int p = swaps[t], x = at[t];
+      at[t] = at[p];
+      at[p] = x;
+    }
+    for (int q = 0; q < l; ++q) dest[at[q]] = q;
+  }
+  __syncthreads();
+  for (int e = tid; e < l * l; e += kInvSmallT) {
+    const int r = e / l, c = e - r * l;
+    xinv[(size_t)r * l + dest[c]] = buf[cur][e];
+  }
+}
+
 cudaError_t launch_cross_inverse(const float* strip, long long si, long long st, const int* pos,
                                  int l, double* xinv, JobStatus* js, cudaStream_t stream) {
+  if (l <= kInvSmallL) {
+    cross_inverse_small_kernel<<<1, kInvSmallT, 0, stream>>>(strip, si, st, pos, l, xinv, js);
+    return cudaGetLastError();
+  }
   const int w = (l + kInvCS - 1) / kInvCS;
   const size_t smem = ((size_t)l * w + 2 * kMaxL) * sizeof(double) + sizeof(InvPub) +
                       3 * kMaxL * sizeof(int);
