@@ -391,7 +391,8 @@ def cross_approximation_adaptive(src, J_cands, l_init, l_max, k_max, sweeps, tol
 
     Returns (I, J, U, k_eff, sigma, l, swaps)."""
     J_cands = [int(j) for j in J_cands]
-    J = J_cands[:l_init]
+    l_cap = min(l_max, src.m, src.n)          # a cross cannot exceed the block
+    J = J_cands[:min(l_init, l_cap)]
     l = len(J)
     I = []
     swaps = 0
@@ -409,8 +410,8 @@ def cross_approximation_adaptive(src, J_cands, l_init, l_max, k_max, sweeps, tol
         X = src.block(I, J)
         sigma = np.linalg.svd(X, compute_uv=False)
         k = int(np.count_nonzero(sigma > tol * sigma[0])) if sigma[0] > 0.0 else 0
-        if k == l and k < k_max and l < l_max:
-            extra = [j for j in J_cands if j not in J][: min(l_max, 2 * l) - l]
+        if k == l and k < k_max and l < l_cap:
+            extra = [j for j in J_cands if j not in J][: min(l_cap, 2 * l) - l]
             if extra:
                 J = J + extra
                 l = len(J)

@@ -145,3 +145,30 @@ def test_blocks_that_need_the_cluster_pass(ctx):
     r2 = solve_batch(ctx, src, blocks[sel], p2, L_MAX)
     for name in ("l", "k_eff", "I", "J", "U", "est_err"):
         np.testing.assert_array_equal(getattr(r, name)[sel], getattr(r2, name))
+
+
+def test_tiny_and_degenerate_blocks(ctx):
+    """Blocks smaller than the first cross (the cross is capped by the block),
+    a 1 x 1 block, a single row, and no error sample."""
+    pts = W.cloud_points(W.BASE_SEED + 72, 600)
+    d = torch.from_numpy(pts).cuda()
+    src = L.make_source("invdist", x=d, y=d)
+    blocks = np.array([[0, 1, 300, 1], [10, 5, 400, 3], [20, 1, 500, 40], [100, 64, 200, 64],
+                       [0, 7, 590, 9]], np.int64)
+    jc, _, _ = W.block_candidates(W.BASE_SEED + 73, blocks, L_MAX, 1)
+    p, keep = make_batch_params(L_INIT, L_MAX, K_MAX, SWEEPS, TOL, jc)
+    r = solve_batch(ctx, src, blocks, p, L_MAX)
+    assert np.all(r.status == 0)
+    s64 = O.InvDist(pts, pts, "fp64")
+    for b, (r0, m, c0, n) in enumerate(blocks):
+        assert r.l[b] <= min(m, n)
+        sub = SubSource(s64, r0, m, c0, n)
+        A = sub.block(np.arange(m), np.arange(n))
+        I, J, U = _nucleus(r, b)
+        assert len(set(I.tolist())) == len(I) and I.max() < m and J.max() < n
+        err = np.linalg.norm(A - A[:, J] @ U @ A[I, :]) / np.linalg.norm(A)
+        oI, oJ, oU, ok, osig, ol, osw = O.cross_approximation_adaptive(sub, jc[b], L_INIT, L_MAX, K_MAX,
+                                                                       SWEEPS, TOL)
+        oerr = np.linalg.norm(A - A[:, oJ] @ oU @ A[oI, :]) / np.linalg.norm(A)
+        assert error_ok(err, oerr), (b, err, oerr)
+        assert r.l[b] == ol, (b, r.l[b], ol)
