@@ -241,7 +241,11 @@ lra_status lra_cross_wait(lra_ctx* ctx, lra_job job, lra_info* out);
  * caller buffers, then release the job's slot and device memory. */
 lra_status lra_cross_fetch_cur(lra_ctx* ctx, lra_job job, const lra_cur_out* out);
 
-/* Release a job: waits for its kernels to finish, then frees it. */
+/* Release a job.  A job still running is first marked LRA_ECANCELED (a copy
+ * on a control stream), so its kernels not yet started return at once (a batch job
+ * takes no further block); then the call waits for the job's stream work to
+ * end and frees it.  The handle is invalid afterwards; the job must not be
+ * waited on or fetched concurrently from another thread. */
 lra_status lra_cross_cancel(lra_ctx* ctx, lra_job job);
 
 /* Bytes of device memory a job with these arguments holds while admitted. */

@@ -432,7 +432,8 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kBT, 1) batch_kerne
   constexpr bool kFirst = (CS == 1);
   int* queue = a.queue + (kFirst ? 0 : 1);
   for (;;) {
-    if (rank == 0 && tid == 0) s->blk = atomicAdd(queue, 1);
+    if (rank == 0 && tid == 0)  // a cancelled job takes no further block
+      s->blk = (*(volatile const int*)&a.js->status != LRA_OK) ? a.n_blocks : atomicAdd(queue, 1);
     cl.sync();
     const int b = *cl.map_shared_rank(&s->blk, 0);
     if (b >= a.n_blocks) {

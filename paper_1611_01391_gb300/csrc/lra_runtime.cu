@@ -77,6 +77,8 @@ struct lra_ctx {
   bool own_stream = false;
   std::vector<cudaStream_t> streams;       // jobs are spread over these
   std::vector<int> stream_load;            // active jobs per stream
+  cudaStream_t ctrl = nullptr;             // cancellations run here, beside the jobs
+  int* cancel_word = nullptr;              // pinned LRA_ECANCELED, copied over a job's status
   int sms = 0;
   int max_grid = 0;  // CTAs per maxvol launch at most
   size_t smem_optin = 0;
@@ -423,6 +425,9 @@ lra_status lra_cross_create(lra_ctx** out, const lra_ctx_params* params) {
     return LRA_ENOMEM;
   }
   for (int s = ctx->max_slots - 1; s >= 0; --s) ctx->free_slots.push_back(s);
+  if (cudaStreamCreateWithFlags(&ctx->ctrl, cudaStreamNonBlocking)) ctx->ctrl = nullptr;
+  if (cudaMallocHost(&ctx->cancel_word, sizeof(int))) ctx->cancel_word = nullptr;
+  else *ctx->cancel_word = LRA_ECANCELED;
   *out = ctx;
   return LRA_OK;
 }
@@ -438,6 +443,8 @@ lra_status lra_cross_destroy(lra_ctx* ctx) {
     for (cudaStream_t s : ctx->streams) cudaStreamSynchronize(s);
     if (ctx->own_stream)
       for (cudaStream_t s : ctx->streams) cudaStreamDestroy(s);
+    if (ctx->ctrl) cudaStreamDestroy(ctx->ctrl);
+    if (ctx->cancel_word) cudaFreeHost(ctx->cancel_word);
     cudaFreeHost(ctx->pinned);
   }
   delete ctx;
@@ -594,6 +601,13 @@ lra_status lra_cross_cancel(lra_ctx* ctx, lra_job id) {
   Job* j = find_job(ctx, id);
   if (!j) return fail(ctx, LRA_ENOTFOUND, "unknown job");
   cudaSetDevice(ctx->device);
+  // a job still running is marked cancelled: a copy engine writes
+  // LRA_ECANCELED over its status word from the control stream, beside the
+  // job's queued kernels, which then return at their start (kernels already
+  // running finish)
+  if (cudaEventQuery(j->ev_end) == cudaErrorNotReady && ctx->ctrl && ctx->cancel_word)
+    cudaMemcpyAsync(&j->js->status, ctx->cancel_word, sizeof(int), cudaMemcpyHostToDevice, ctx->ctrl);
+  cudaGetLastError();
   cudaEventSynchronize(j->ev_end);
   ctx->jobs.erase(id);
   release_job(ctx, j);

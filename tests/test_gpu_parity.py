@@ -313,3 +313,27 @@ def test_dense_32768_full_size_parity(ctx):
     assert ref.sigma[k - 1] > 1e-4 * ref.sigma[0]
     err_ref = O.full_residual(O.Dense(A), ref.C, ref.U, ref.R)[0]
     assert error_ok(res.info.full_rel_err, err_ref)
+
+
+def test_cancel_stops_a_running_job(ctx):
+    """A long job cancelled right after submit ends well before it would have
+    finished, and the context keeps working."""
+    import time
+    x, y = W.cauchy_points(95, 65536, 65536)
+    xd, yd = torch.from_numpy(x).to(DEV), torch.from_numpy(y).to(DEV)
+    src = L.make_source("cauchy", x=xd, y=yd)
+    J0 = W.draw_indices(96, 65536, 24)
+    params, keep = L.make_params(16, 24, 40, J0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    full = ctx.solve(src, params, 24)
+    t_full = time.perf_counter() - t0
+    assert full.info.status == 0
+    job = ctx.submit(src, params)
+    t0 = time.perf_counter()
+    L.lra_cross_cancel(ctx.ctx, job)
+    t_cancel = time.perf_counter() - t0
+    assert t_cancel < 0.5 * t_full, (t_cancel, t_full)
+    again = ctx.solve(src, params, 24)
+    assert again.info.status == 0
+    np.testing.assert_array_equal(again.I, full.I)
