@@ -16,6 +16,9 @@
  *     locally maximal volume (volume footnote of Section 6.5; Section 12.2).
  *   - Appendix F: a posteriori error estimate on a random q x s submatrix of
  *     the error matrix.
+ *   - Section 9: the same iteration, rank-adaptive, on many blocks of one
+ *     generated matrix (the far-field generators of HSS / FMM matrices) in
+ *     one batched launch (lra_cross_submit_batch).
  *
  * Conventions
  *   - Every call returns an lra_status (0 on success, negative on error);
@@ -25,8 +28,10 @@
  *     BORROWED: they must stay valid and unchanged until the job is DONE,
  *     FAILED or cancelled.  Host arrays in lra_params are copied at submit.
  *   - Outputs are caller-allocated (host or device, see lra_cur_out).
- *   - A context owns one CUDA stream on one device; jobs run in submission
- *     order on that stream.  Calls on one context are serialised internally.
+ *   - A context works on one device, on the caller's stream or on a pool of
+ *     its own streams (lra_ctx_params.n_streams).  Each job runs in order on
+ *     one stream; jobs on different streams overlap on the device.  Calls on
+ *     one context are serialised internally.
  *   - All computation happens in the library's CUDA kernels; there is no
  *     CPU fallback.  Without a usable device, create fails with LRA_ECUDA.
  */
