@@ -6,8 +6,9 @@
 //
 // Method:
 //   P = C U (m x l) is formed with a compensated FP32 dot product (Dot2 of
-//   Ogita, Rump & Oishi, U split into FP32 hi + lo), so P carries about twice
-//   FP32 precision even when U has large entries.  Each row of P and each
+//   Ogita, Rump & Oishi on U's FP32 high part; the products with the low
+//   part, 2^-24 of the sum, go into the compensation term), so P carries
+//   about twice FP32 precision even when U has large entries.  Each row of P and each
 //   column of R is scaled by a power of two into the FP16 range and split as
 //       x = hi + lo * 2^-11,   hi = fp16(x),  lo = fp16((x - hi) * 2^11),
 //   which keeps about 22 significant bits.  The product P R is then
@@ -96,8 +97,10 @@ __device__ __forceinline__ void split_store(float x, float inv_scale, __half* hi
   *lo = __float2half_rn((xs - __half2float(h)) * kLoScale);
 }
 
-// One block of 128 threads per row of P: P[i][t] = sum_p C[i][p] U[p][t]
-// (Dot2, FP32), row max -> scale, FP16 hi/lo split, zero padding to kp.
+// One block of 128 threads per row of P: P[i][t] = sum_q C[i][q] U[q][t] with
+// U = Uhi + Ulo: Dot2 in FP32 on the Uhi products, the Ulo products (2^-24
+// of the sum) added into the compensation term with one FMA each.  Then the
+// row max -> a power-of-two scale, FP16 hi/lo split, zero padding to kp.
 __global__ void __launch_bounds__(128) split_p_kernel(const float* __restrict__ C,
                                                       const float* __restrict__ Uhi,
                                                       const float* __restrict__ Ulo, long long m,
@@ -107,16 +110,18 @@ __global__ void __launch_bounds__(128) split_p_kernel(const float* __restrict__ 
                                                       const JobStatus* js) {
   if (js->status != LRA_OK) return;
   __shared__ float red[4];
+  __shared__ float crow[kMaxL];
   const long long i = blockIdx.x;
   const int t = threadIdx.x;
+  if (t < l) crow[t] = __ldg(C + i * l + t);
+  __syncthreads();
   float val = 0.0f;
   if (t < l) {
     float p = 0.0f, c = 0.0f;
-    const float* crow = C + i * l;
     for (int q = 0; q < l; ++q) {
-      const float cv = __ldg(crow + q);
+      const float cv = crow[q];
       dot2_acc(cv, __ldg(Uhi + (size_t)q * l + t), p, c);
-      dot2_acc(cv, __ldg(Ulo + (size_t)q * l + t), p, c);
+      c = fmaf(cv, __ldg(Ulo + (size_t)q * l + t), c);
     }
     val = __fadd_rn(p, c);
   }
@@ -136,7 +141,8 @@ __global__ void __launch_bounds__(128) split_p_kernel(const float* __restrict__ 
   if (t == 0) pscale[i] = ldexpf(1.0f, ex);
 }
 
-// One thread per row j of R^T (column j of R): scale, split, zero padding.
+// One thread per row j of R^T (column j of R): scale, split, zero padding;
+// the kp halves of a row are written as 16-byte groups of 8.
 __global__ void __launch_bounds__(128) split_rt_kernel(const float* __restrict__ R, long long n,
                                                        int l, int kp, __half* __restrict__ RThi,
                                                        __half* __restrict__ RTlo,
@@ -149,11 +155,19 @@ __global__ void __launch_bounds__(128) split_rt_kernel(const float* __restrict__
   for (int t = 0; t < l; ++t) amax = fmaxf(amax, fabsf(__ldg(R + (size_t)t * n + j)));
   const int ex = scale_exp(amax);
   const float inv = ldexpf(1.0f, -ex);
-  for (int t = 0; t < kp; ++t) {
-    __half h = __float2half_rn(0.0f), lo = h;
-    if (t < l) split_store(__ldg(R + (size_t)t * n + j), inv, &h, &lo);
-    RThi[j * kp + t] = h;
-    RTlo[j * kp + t] = lo;
+  uint4* hrow = reinterpret_cast<uint4*>(RThi + j * kp);
+  uint4* lrow = reinterpret_cast<uint4*>(RTlo + j * kp);
+  for (int t8 = 0; t8 < kp; t8 += 8) {
+    __align__(16) __half h[8], lo[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t8 + u;
+      h[u] = __float2half_rn(0.0f);
+      lo[u] = h[u];
+      if (t < l) split_store(__ldg(R + (size_t)t * n + j), inv, &h[u], &lo[u]);
+    }
+    hrow[t8 / 8] = *reinterpret_cast<const uint4*>(h);
+    lrow[t8 / 8] = *reinterpret_cast<const uint4*>(lo);
   }
   rscale[j] = ldexpf(1.0f, ex);
 }
