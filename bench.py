@@ -54,7 +54,7 @@ WORKLOADS = {
     "octree512": dict(form="batch", npoints=1 << 20, leaf=2048, n_pairs=512, l_init=12, l_max=96,
                       k_max=64, sweeps=2, tol=1e-6, q=32, seed_off=4, plain_subset=64),
     "serve": dict(form="serve", count=400, min_side=256, max_side=16384, budget_gb=40, slots=64,
-                  streams=32, max_grid=64, rates=(0.5, 0.8, 0.95), seed_off=5, plain_subset=400),
+                  streams=32, max_grid=56, rates=(0.5, 0.8, 0.95), seed_off=5, plain_subset=400),
 }
 
 

@@ -222,14 +222,25 @@ cross_inverse_kernel(const float* __restrict__ strip, long long si, long long st
   cl.sync();  // no peer reads this CTA's shared memory after it exits
 }
 
-// The same elimination for l <= 32 on one CTA: at that size every step is a
-// chain of FP64 latencies (a division is ~430 cycles on this part), so the
-// step is cut to one warp (pivot, reciprocal, scaled pivot row), one
-// barrier, one pass that writes the next matrix from the current one (two
-// buffers, so no entry is read after it is overwritten) and a second
-// barrier.  The arithmetic per entry is that of the cluster kernel.
+// The same elimination for l <= 32 on one CTA.  At that size every step is
+// a chain of latencies (an FP64 division is ~430 cycles on this part), so a
+// step is cut to: the pivot, already reduced during the previous step's
+// update (a shared-memory atomic max of packed (|value| as FP32, row) keys
+// over the next column, smaller row on ties); one warp forms 1/pivot and the
+// scaled pivot row; one barrier; one pass in which every thread writes its
+// fixed entries of the next matrix from the current one (two buffers, so no
+// entry is read after it is overwritten) and offers its entries of the next
+// column as pivot candidates; a second barrier.  The arithmetic per entry is
+// that of the cluster kernel.
 constexpr int kInvSmallL = 32;
 constexpr int kInvSmallT = 128;
+constexpr int kInvSmallPer = (kInvSmallL * kInvSmallL + kInvSmallT - 1) / kInvSmallT;
+
+__device__ __forceinline__ unsigned long long pivot_key(double v, int r) {
+  // |v| rounded to FP32 orders the candidates; the low word prefers the
+  // smaller row among equal keys
+  return ((unsigned long long)__float_as_uint(fabsf((float)v)) << 32) | (unsigned)(0x7fffffff - r);
+}
 
 __global__ void __launch_bounds__(kInvSmallT, 1)
 cross_inverse_small_kernel(const float* __restrict__ strip, long long si, long long st,
@@ -237,15 +248,29 @@ cross_inverse_small_kernel(const float* __restrict__ strip, long long si, long l
   if (js->status != LRA_OK || js->stop) return;
   __shared__ double buf[2][kInvSmallL * kInvSmallL];
   __shared__ double rowt[kInvSmallL];
+  __shared__ unsigned long long pkey[2];
   __shared__ int p_s;
   __shared__ int swaps[kInvSmallL], at[kInvSmallL], dest[kInvSmallL];
   const int tid = threadIdx.x, lane = tid & 31;
+  const int ll = l * l;
+  // this thread's entries, fixed for all steps
+  int er[kInvSmallPer], ec[kInvSmallPer];
+#pragma unroll
+  for (int k = 0; k < kInvSmallPer; ++k) {
+    const int e = tid + k * kInvSmallT;
+    er[k] = e < ll ? e / l : -1;
+    ec[k] = e < ll ? e - (e / l) * l : 0;
+  }
+  if (tid < 2) pkey[tid] = 0ull;
+  __syncthreads();
   int bad = 0;
-  for (int e = tid; e < l * l; e += kInvSmallT) {
-    const int r = e / l, c = e - r * l;
-    const double v = (double)strip[(long long)__ldg(pos + r) * si + (long long)c * st];
+#pragma unroll
+  for (int k = 0; k < kInvSmallPer; ++k) {
+    if (er[k] < 0) continue;
+    const double v = (double)strip[(long long)__ldg(pos + er[k]) * si + (long long)ec[k] * st];
     if (!(fabs(v) <= DBL_MAX)) bad = 1;
-    buf[0][e] = v;
+    buf[0][er[k] * l + ec[k]] = v;
+    if (ec[k] == 0) atomicMax(&pkey[0], pivot_key(v, er[k]));
   }
   if (__syncthreads_or(bad)) {
     if (tid == 0) set_status(js, LRA_ENONFINITE);
@@ -254,21 +279,9 @@ cross_inverse_small_kernel(const float* __restrict__ strip, long long si, long l
   int cur = 0;
   for (int t = 0; t < l; ++t) {
     const double* A = buf[cur];
-    if (tid < 32) {  // pivot: largest |A[r][t]|, r >= t (smallest r on ties)
-      const int r = t + lane;
-      unsigned long long best = 0ull;
-      int br = l;
-      if (r < l) {
-        best = abs_bits(A[r * l + t]);
-        br = r;
-      }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const unsigned long long ob = __shfl_down_sync(0xffffffffu, best, off);
-        const int orr = __shfl_down_sync(0xffffffffu, br, off);
-        if (orr < l && (br == l || ob > best || (ob == best && orr < br))) { best = ob; br = orr; }
-      }
-      const int p = __shfl_sync(0xffffffffu, (best != 0ull && br < l) ? br : -1, 0);
+    if (tid < 32) {
+      const unsigned long long key = pkey[t & 1];
+      const int p = (key >> 32) != 0ull ? 0x7fffffff - (int)(unsigned)(key & 0xffffffffull) : -1;
       double rp = 0.0;
       if (lane == 0 && p >= 0) rp = 1.0 / A[p * l + t];
       rp = __shfl_sync(0xffffffffu, rp, 0);
@@ -276,6 +289,7 @@ cross_inverse_small_kernel(const float* __restrict__ strip, long long si, long l
       if (lane == 0) {
         p_s = p;
         swaps[t] = p;
+        pkey[(t + 1) & 1] = 0ull;
       }
     }
     __syncthreads();
@@ -285,15 +299,20 @@ cross_inverse_small_kernel(const float* __restrict__ strip, long long si, long l
       return;
     }
     double* N = buf[cur ^ 1];
-    for (int e = tid; e < l * l; e += kInvSmallT) {
-      const int r = e / l, c = e - r * l;
+#pragma unroll
+    for (int k = 0; k < kInvSmallPer; ++k) {
+      const int r = er[k], c = ec[k];
+      if (r < 0) continue;
+      double v;
       if (r == t) {
-        N[e] = rowt[c];
+        v = rowt[c];
       } else {
         const int rr = (r == p) ? t : r;  // row r after the swap is row rr before it
         const double a = (c == t) ? 0.0 : A[rr * l + c];
-        N[e] = fma(-A[rr * l + t], rowt[c], a);
+        v = fma(-A[rr * l + t], rowt[c], a);
       }
+      N[r * l + c] = v;
+      if (c == t + 1 && r > t) atomicMax(&pkey[(t + 1) & 1], pivot_key(v, r));
     }
     cur ^= 1;
     __syncthreads();
@@ -308,7 +327,7 @@ cross_inverse_small_kernel(const float* __restrict__ strip, long long si, long l
     for (int q = 0; q < l; ++q) dest[at[q]] = q;
   }
   __syncthreads();
-  for (int e = tid; e < l * l; e += kInvSmallT) {
+  for (int e = tid; e < ll; e += kInvSmallT) {
     const int r = e / l, c = e - r * l;
     xinv[(size_t)r * l + dest[c]] = buf[cur][e];
   }

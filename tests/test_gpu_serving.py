@@ -50,9 +50,9 @@ def test_same_alone_and_in_the_mix():
         for (src, p, _), r in zip(prep, reqs):
             alone.append(ctx.solve(src, p, r["l"]))
     # in the mix: everything admitted at once on 8 streams, maxvol grids
-    # capped at 64 CTAs as in the served configuration (the decisions do not
+    # capped at 56 CTAs as in the served configuration (the decisions do not
     # depend on how the strip is split over CTAs)
-    with L.Context(0, n_streams=8, max_grid=64) as ctx:
+    with L.Context(0, n_streams=8, max_grid=56) as ctx:
         jobs = [ctx.submit(src, p) for (src, p, _) in prep]
         mixed = [ctx.fetch(j, r["l"]) for j, r in zip(jobs, reqs)]
     for a, b, r in zip(alone, mixed, reqs):
