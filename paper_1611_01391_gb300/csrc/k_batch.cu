@@ -533,13 +533,8 @@ size_t batch_smem_bytes() { return sizeof(BatchSmemT<1>); }
 template <int KIND, int CS>
 static cudaError_t launch_pass(const BatchArgs& a, int sms, cudaStream_t st) {
   const size_t smem = sizeof(BatchSmemT<CS>);
-  static bool attr = false;
-  if (!attr) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(batch_kernel<KIND, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e) return e;
-    attr = true;
-  }
+  const cudaError_t e = smem_optin(reinterpret_cast<const void*>(batch_kernel<KIND, CS>), (int)smem);
+  if (e) return e;
   batch_kernel<KIND, CS><<<(sms / CS) * CS, kBT, smem, st>>>(a);
   return cudaGetLastError();
 }

@@ -350,13 +350,8 @@ cudaError_t launch_nucleus(const float* C, const int* I, int l, int k, double ra
                            double* U, double* sigma, JobStatus* js, cudaStream_t st) {
   const size_t smem = 2 * (size_t)l * l * sizeof(dd) + kMaxL * (sizeof(double) + sizeof(dd)) +
                       sizeof(SvdScratch) + (kMaxL + 2) * sizeof(int);
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(nucleus_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         227 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  const cudaError_t e = smem_optin(reinterpret_cast<const void*>(nucleus_kernel), 227 * 1024);
+  if (e != cudaSuccess) return e;
   nucleus_kernel<<<1, kNucThreads, smem, st>>>(C, I, l, k, rank_tol, U, sigma, js);
   return cudaGetLastError();
 }

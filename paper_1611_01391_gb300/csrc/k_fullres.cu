@@ -624,13 +624,7 @@ cudaError_t launch_full_residual(const float* A, long long lda, long long m, lon
   const int grid = std::min(grid_cap, a.n_items);
   const size_t smem = 1024 + 2 * (size_t)a.kb * kBM * 128 +
                       kStages * (2 * (size_t)a.kb * kBN * 128 + kBM * kBN * 4) + sizeof(FrBarriers);
-  static bool attr_done = false;
-  if (!attr_done) {
-    if ((e = cudaFuncSetAttribute(fullres_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(227 * 1024))))
-      return e;
-    attr_done = true;
-  }
+  if ((e = smem_optin(reinterpret_cast<const void*>(fullres_kernel), 227 * 1024))) return e;
   fullres_kernel<<<grid, kFrThreads, smem, st>>>(mA, mPhi, mPlo, mRhi, mRlo, a);
   fullres_final_kernel<<<1, 32, 0, st>>>(partials, grid, js);
   return cudaGetLastError();

@@ -393,13 +393,8 @@ bool plan_maxvol(long long N, int l, int sms, size_t smem_limit, MaxvolPlan* pla
 
 template <int GS, int NC>
 static cudaError_t launch_gs(MaxvolArgs& a, const MaxvolPlan& plan, cudaStream_t st) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(maxvol_kernel<GS, NC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
+  const cudaError_t e = smem_optin(reinterpret_cast<const void*>(maxvol_kernel<GS, NC>), 227 * 1024);
+  if (e != cudaSuccess) return e;
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(maxvol_kernel<GS, NC>),
                                      dim3(plan.grid), dim3(plan.threads), args, plan.smem, st);

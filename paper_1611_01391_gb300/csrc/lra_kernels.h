@@ -81,6 +81,10 @@ cudaError_t launch_full_residual(const float* A, long long lda, long long m, lon
 
 // Batched C-A: one persistent launch of 4-CTA clusters over a work queue.
 struct BatchArgs;
+// Opt a kernel in to `bytes` of dynamic shared memory on the current device
+// (the attribute is per device; done once per kernel, device and size).
+cudaError_t smem_optin(const void* func, int bytes);
+
 size_t batch_smem_bytes();
 cudaError_t launch_batch(const BatchArgs& a, int sms, cudaStream_t st);
 

@@ -93,6 +93,20 @@ struct lra_ctx {
   std::string last_error;
 };
 
+cudaError_t smem_optin(const void* func, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e) return e;
+  static std::mutex mu;
+  static std::vector<std::pair<std::pair<const void*, int>, int>> done;  // (func, device) -> bytes
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto& d : done)
+    if (d.first.first == func && d.first.second == dev && d.second >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (!e) done.push_back({{func, dev}, bytes});
+  return e;
+}
+
 namespace {
 
 lra_status fail(lra_ctx* ctx, lra_status code, const std::string& msg) {
