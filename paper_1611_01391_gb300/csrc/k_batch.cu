@@ -338,6 +338,7 @@ __device__ void cross_step(const BatchArgs& a, S* s, int b, long long row0, long
     sg_out[r] = (float)ldexp(sb, ex);
   }
   __syncthreads();
+  left_vectors<kBT>(W, Z, l, s->keff, order, inv2, sc->perm);
   double* Ub = a.out_U + (size_t)b * a.l_max * a.l_max;
   nucleus_from_svd<kBT>(W, Z, sc->perm, l, s->keff, order, inv2,
                         [&](int e, double v) { Ub[e] = ldexp(v, -ex); });

@@ -3,7 +3,8 @@
 // truncation and U = (X_k)^+.
 //
 // The SVD (svd_dd.cuh) is QR with column pivoting followed by one-sided
-// Jacobi on R^T, in double-float arithmetic.  X is first scaled by a power
+// Jacobi on R^T, in double-float arithmetic; the left singular vectors of
+// the kept triplets are X v_b / sigma_b.  X is first scaled by a power
 // of two so that max |X| lies in [0.5, 1) (exact); sigma and U are scaled
 // back.
 #include <cooperative_groups.h>
@@ -76,6 +77,7 @@ nucleus_kernel(const float* __restrict__ C, const int* __restrict__ I, int l, in
   }
   __syncthreads();
   const int ke = *keff_s;
+  left_vectors<kNucThreads>(W, Z, l, ke, order, inv2, sc->perm);
   nucleus_from_svd<kNucThreads>(W, Z, sc->perm, l, ke, order, inv2,
                                 [&](int e, double v) { U[e] = ldexp(v, -ex); });
 }

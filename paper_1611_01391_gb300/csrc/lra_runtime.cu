@@ -93,7 +93,7 @@ struct lra_ctx {
   std::string last_error;
 };
 
-cudaError_t smem_optin(const void* func, int bytes) {
+cudaError_t lra::smem_optin(const void* func, int bytes) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e) return e;

@@ -286,39 +286,9 @@ __device__ void qrcp_dd(dd* A, int l, SvdScratch* sc) {
   }
 }
 
-// Q = H_0 H_1 ... H_{l-1} into Z (column c at Z[c*l, c*l+l)) by backward
-// accumulation: Z = I, then Z <- H_j Z for j = l-1 .. 0 (H_j touches rows
-// j.. and, at that point, only columns j..).
-template <int NT>
-__device__ void form_q_dd(const dd* A, int l, const SvdScratch* sc, dd* Z) {
-  constexpr int G = 8, GPW = 32 / G, NG = NT / G;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, gl = lane & (G - 1);
-  for (int e = tid; e < l * l; e += NT) {
-    const int c = e / l, i = e - c * l;
-    Z[e] = dd_make(c == i ? 1.0f : 0.0f);
-  }
-  __syncthreads();
-  for (int j = l - 1; j >= 0; --j) {
-    const dd bj = sc->beta[j];
-    if (bj.hi != 0.0f) {
-      for (int base = j + warp * GPW; base < l; base += NG) {
-        const int c = base + (lane / G);
-        const bool act = c < l;
-        dacc a{0.f, 0.f};
-        if (act)
-          for (int i = j + gl; i < l; i += G) acc_fma(a, A[j * l + i], Z[c * l + i]);
-        a = acc_group_sum<G>(a);
-        const dd nsv = dd_neg(dd_mul(bj, acc_value(a)));
-        if (act)
-          for (int i = j + gl; i < l; i += G) Z[c * l + i] = dd_lin2(dd_make(1.0f), Z[c * l + i], nsv, A[j * l + i]);
-      }
-    }
-    __syncthreads();
-  }
-}
-
 // One-sided Jacobi (Hestenes) on the columns of W, the rotations applied to
-// the columns of Z as well.  On exit W has orthogonal columns.  Columns are
+// the columns of Z as well when kAccumulate.  On exit W has orthogonal
+// columns.  Columns are
 // paired in round-robin order (l/2 independent pairs per round, 8 lanes per
 // pair); a pair is rotated unless |w_p^T w_q| <= tol ||w_p|| ||w_q||.  The
 // rotation tangent of the symmetric 2 x 2 problem (Golub & Van Loan,
@@ -326,7 +296,7 @@ __device__ void form_q_dd(const dd* A, int l, const SvdScratch* sc, dd* Z) {
 // s = c t are formed in double-float from that t, so every rotation is
 // orthogonal to double-float accuracy and only the speed of convergence
 // depends on t.
-template <int NT>
+template <int NT, bool kAccumulate = true>
 __device__ void jacobi_dd(dd* W, dd* Z, int l, int* flag) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int np = (l + 1) & ~1;
@@ -367,15 +337,19 @@ __device__ void jacobi_dd(dd* W, dd* Z, int l, int* flag) {
         const float tf = tf_out;
         const dd s = dd_mul(c, dd_make(tf));
         const dd ns = dd_neg(s);
-        dd* zp = Z + p * l;
-        dd* zq = Z + q * l;
         for (int i = gl; i < l; i += 8) {
           const dd u = wp[i], v = wq[i];
           wp[i] = dd_lin2(c, u, ns, v);
           wq[i] = dd_lin2(s, u, c, v);
-          const dd xx = zp[i], yy = zq[i];
-          zp[i] = dd_lin2(c, xx, ns, yy);
-          zq[i] = dd_lin2(s, xx, c, yy);
+        }
+        if (kAccumulate) {
+          dd* zp = Z + p * l;
+          dd* zq = Z + q * l;
+          for (int i = gl; i < l; i += 8) {
+            const dd xx = zp[i], yy = zq[i];
+            zp[i] = dd_lin2(c, xx, ns, yy);
+            zq[i] = dd_lin2(s, xx, c, yy);
+          }
         }
         if (gl == 0) *flag = 1;
       }
@@ -390,15 +364,15 @@ __device__ void jacobi_dd(dd* W, dd* Z, int l, int* flag) {
 // l x l work area: QR with column pivoting X P = Q R, then one-sided Jacobi
 // on R^T (the preconditioning of Drmac & Veselic, "New fast and accurate
 // Jacobi SVD algorithm I", SIAM J. Matrix Anal. Appl. 29, 2008: on the
-// graded R^T the sweeps roughly halve), its rotations accumulated into Z = Q.
-// With R^T V = W (orthogonal columns) this is X = (Q V) W^T P^T, so on exit
-//   sigma_b = ||W[:, b]||,  right singular vector b of X = P W[:, b] / sigma_b,
-//   left singular vector b of X = Z[:, b],
-// with W in A and Q V in Z; (X_k)^+ = sum_b P W_b Z_b^T / sigma_b^2.
+// graded R^T the sweeps roughly halve).  With R^T V = W (orthogonal columns)
+// this is X = (Q V) W^T P^T, so on exit (W in A)
+//   sigma_b = ||W[:, b]||,  right singular vector b of X = P W[:, b] / sigma_b.
+// The rotations are not accumulated: the left singular vectors needed later
+// are u_b = X P W_b / sigma_b^2 (left_vectors), so Z keeps a copy of X.
 template <int NT>
 __device__ void svd_dd(dd* A, dd* Z, int l, SvdScratch* sc) {
+  for (int e = threadIdx.x; e < l * l; e += NT) Z[e] = A[e];
   qrcp_dd<NT>(A, l, sc);
-  form_q_dd<NT>(A, l, sc, Z);
   // W = R^T in place: column j of W = row j of R (pivoted column order)
   constexpr int kPer = (kMaxL * kMaxL + NT - 1) / NT;
   dd v[kPer];
@@ -419,7 +393,40 @@ __device__ void svd_dd(dd* A, dd* Z, int l, SvdScratch* sc) {
     if (e < l * l) A[e] = v[t];
   }
   __syncthreads();
-  jacobi_dd<NT>(A, Z, l, &sc->flag);
+  jacobi_dd<NT, false>(A, nullptr, l, &sc->flag);
+}
+
+// Left singular vectors of the kept triplets, in place of the copy of X in
+// Z: u_r = X P W_{b_r} inv2[r] (b_r = order[r], inv2[r] = 1 / sigma_{b_r}^2)
+// into column r of Z, r < ke.  One warp per row q of X: the warp holds the
+// row in registers (l <= 96: three values per lane) before it overwrites
+// that row's first ke positions, so rows are independent.
+template <int NT>
+__device__ void left_vectors(const dd* W, dd* Z, int l, int ke, const int* order, const dd* inv2,
+                             const int* perm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = warp; q < l; q += NT / 32) {
+    dd x[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int c = lane + 32 * k;
+      x[k] = c < l ? Z[perm[c] * l + q] : dd{0.f, 0.f};   // X[q][perm[c]]
+    }
+    __syncwarp();
+    for (int r = 0; r < ke; ++r) {
+      const dd* w = W + order[r] * l;
+      dacc a{0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int c = lane + 32 * k;
+        if (c < l) acc_fma(a, x[k], w[c]);
+      }
+      a = acc_group_sum<32>(a);
+      if (lane == 0) Z[r * l + q] = dd_mul(acc_value(a), inv2[r]);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
 }
 
 // After jacobi_dd: sigma_b = ||W_b|| (double), order[rank] = column (sigma
@@ -441,11 +448,11 @@ __device__ void jacobi_sigma(const dd* W, int l, double* sig, int* order) {
   __syncthreads();
 }
 
-// U[p][q] = sum_{r < ke} V[b_r][p] W[b_r][q] / sigma_r^2 in double-float;
-// (X_k)^+ from svd_dd: U[perm[c]][q] = sum_{r < ke} W[b_r][c] Z[b_r][q] inv2[r]
-// with b_r = order[r] and inv2[r] = 1 / sigma_{b_r}^2 (shared, computed
-// once); out(e, value) receives the l*l entries, row-major e = p*l + q (p a
-// column of X, q a row of X).
+// (X_k)^+ from svd_dd and left_vectors: U[perm[c]][q] = sum_{r < ke}
+// W[b_r][c] u_r[q] inv2[r] with b_r = order[r], u_r = column r of Z and
+// inv2[r] = 1 / sigma_{b_r}^2 (shared, computed once); out(e, value)
+// receives the l*l entries, row-major e = p*l + q (p a column of X, q a row
+// of X).
 template <int NT, typename Out>
 __device__ void nucleus_from_svd(const dd* W, const dd* Z, const int* perm, int l, int ke,
                                  const int* order, const dd* inv2, Out out) {
@@ -454,7 +461,7 @@ __device__ void nucleus_from_svd(const dd* W, const dd* Z, const int* perm, int 
     dd acc{0.f, 0.f};
     for (int r = 0; r < ke; ++r) {
       const int b = order[r];
-      acc = dd_fma(dd_mul(W[b * l + c], Z[b * l + q]), inv2[r], acc);
+      acc = dd_fma(dd_mul(W[b * l + c], Z[r * l + q]), inv2[r], acc);
     }
     out(perm[c] * l + q, dd_to_double(acc));
   }
