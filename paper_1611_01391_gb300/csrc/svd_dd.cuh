@@ -289,28 +289,30 @@ __device__ void qrcp_dd(dd* A, int l, SvdScratch* sc) {
 // One-sided Jacobi (Hestenes) on the columns of W, the rotations applied to
 // the columns of Z as well when kAccumulate.  On exit W has orthogonal
 // columns.  Columns are
-// paired in round-robin order (l/2 independent pairs per round, 8 lanes per
+// paired in round-robin order (l/2 independent pairs per round, G lanes per
 // pair); a pair is rotated unless |w_p^T w_q| <= tol ||w_p|| ||w_q||.  The
 // rotation tangent of the symmetric 2 x 2 problem (Golub & Van Loan,
 // Algorithm 8.5.1) is taken to FP32 accuracy; c = (1 + t^2)^{-1/2} and
 // s = c t are formed in double-float from that t, so every rotation is
 // orthogonal to double-float accuracy and only the speed of convergence
 // depends on t.
-template <int NT, bool kAccumulate = true>
+template <int NT, bool kAccumulate = true, int G = 8>
 __device__ void jacobi_dd(dd* W, dd* Z, int l, int* flag) {
+  static_assert(G == 8 || G == 16, "lanes per pair");
+  constexpr int kPairsPerWarp = 32 / G;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int np = (l + 1) & ~1;
   // about l * 2^-48; the test below runs on the FP32 high parts (relative
   // error 2^-24 of a threshold), keeping the FP64 pipe (1/64 rate) off the
   // inner loop
   const float tol = (float)l * 3.6e-15f;
-  const int gl = lane & 7, ngroups = (NT / 32) * 4;
+  const int gl = lane & (G - 1), ngroups = (NT / 32) * kPairsPerWarp;
   for (int sweep = 0; sweep < 60; ++sweep) {
     if (tid == 0) *flag = 0;
     __syncthreads();
     for (int round = 0; round < np - 1; ++round) {
-      for (int base = warp * 4; base < np / 2; base += ngroups) {
-        const int slot = base + (lane >> 3);
+      for (int base = warp * kPairsPerWarp; base < np / 2; base += ngroups) {
+        const int slot = base + lane / G;
         const int x0 = slot, x1 = np - 1 - slot;
         int p = (x0 == 0) ? 0 : ((x0 - 1 + round) % (np - 1)) + 1;
         int q = (x1 == 0) ? 0 : ((x1 - 1 + round) % (np - 1)) + 1;
@@ -320,15 +322,15 @@ __device__ void jacobi_dd(dd* W, dd* Z, int l, int* flag) {
         dd* wq = W + q * l;
         dacc sa{0.f, 0.f}, sb{0.f, 0.f}, sg{0.f, 0.f};
         if (act)
-          for (int i = gl; i < l; i += 8) {
+          for (int i = gl; i < l; i += G) {
             const dd u = wp[i], v = wq[i];
             acc_fma(sa, u, u);
             acc_fma(sb, v, v);
             acc_fma(sg, u, v);
           }
-        sa = acc_group_sum<8>(sa);
-        sb = acc_group_sum<8>(sb);
-        sg = acc_group_sum<8>(sg);
+        sa = acc_group_sum<G>(sa);
+        sb = acc_group_sum<G>(sb);
+        sg = acc_group_sum<G>(sg);
         if (!act) continue;
         const dd al = acc_value(sa), be = acc_value(sb), ga = acc_value(sg);
         if (!(al.hi > 0.0f) || !(be.hi > 0.0f) || fabsf(ga.hi) <= tol * sqrtf(al.hi) * sqrtf(be.hi)) continue;
@@ -337,7 +339,7 @@ __device__ void jacobi_dd(dd* W, dd* Z, int l, int* flag) {
         const float tf = tf_out;
         const dd s = dd_mul(c, dd_make(tf));
         const dd ns = dd_neg(s);
-        for (int i = gl; i < l; i += 8) {
+        for (int i = gl; i < l; i += G) {
           const dd u = wp[i], v = wq[i];
           wp[i] = dd_lin2(c, u, ns, v);
           wq[i] = dd_lin2(s, u, c, v);
@@ -345,7 +347,7 @@ __device__ void jacobi_dd(dd* W, dd* Z, int l, int* flag) {
         if (kAccumulate) {
           dd* zp = Z + p * l;
           dd* zq = Z + q * l;
-          for (int i = gl; i < l; i += 8) {
+          for (int i = gl; i < l; i += G) {
             const dd xx = zp[i], yy = zq[i];
             zp[i] = dd_lin2(c, xx, ns, yy);
             zq[i] = dd_lin2(s, xx, c, yy);
@@ -393,7 +395,7 @@ __device__ void svd_dd(dd* A, dd* Z, int l, SvdScratch* sc) {
     if (e < l * l) A[e] = v[t];
   }
   __syncthreads();
-  jacobi_dd<NT, false>(A, nullptr, l, &sc->flag);
+  jacobi_dd<NT, false, (NT >= 1024 ? 16 : 8)>(A, nullptr, l, &sc->flag);
 }
 
 // Left singular vectors of the kept triplets, in place of the copy of X in
