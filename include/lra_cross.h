@@ -92,7 +92,10 @@ typedef struct {
   void* stream;               /* cudaStream_t to run every job on, or NULL: own streams */
   int32_t n_streams;          /* own streams (1..32; <= 0: 1).  A job runs on the
                                  least loaded one, so jobs submitted while others
-                                 run overlap on the device (continuous admission). */
+                                 run overlap on the device (continuous admission).
+                                 With more than one, kernels that would spread one
+                                 job over several SMs for latency (the cross
+                                 inverse at l > 32) run on one SM instead. */
   int32_t max_grid;           /* CTAs per maxvol launch at most (<= 0: one per SM).
                                  A smaller grid leaves SMs to the other jobs in
                                  flight; a strip whose chunks would not fit in

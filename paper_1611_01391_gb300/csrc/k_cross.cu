@@ -224,6 +224,106 @@ cross_inverse_kernel(const float* __restrict__ strip, long long si, long long st
   cl.sync();  // no peer reads this CTA's shared memory after it exits
 }
 
+// The same elimination on one CTA of 512 threads (l <= 96, the matrix in
+// shared memory), for contexts whose jobs overlap on the device: the cluster
+// kernel is faster for one job but holds 8 SMs for it, this one one SM.
+constexpr int kInvCtaT = 512;
+
+__global__ void __launch_bounds__(kInvCtaT, 1)
+cross_inverse_cta_kernel(const float* __restrict__ strip, long long si, long long st,
+                     const int* __restrict__ pos, int l, double* __restrict__ xinv, JobStatus* js) {
+  if (js->status != LRA_OK || js->stop) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* A = reinterpret_cast<double*>(smem_raw);  // l x l, row-major
+  double* f = A + (size_t)l * l;                    // column t before the step
+  double* rowt = f + kMaxL;                         // pivot row after scaling
+  double* recip = rowt + kMaxL;                     // 1 / pivot of the current step
+  int* piv_row = reinterpret_cast<int*>(recip + 1);
+  int* swaps = piv_row + 1;                         // row swapped with t at step t
+  int* bad = swaps + kMaxL;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  if (tid == 0) *bad = 0;
+  __syncthreads();
+  for (int e = tid; e < l * l; e += nthr) {
+    const int a = e / l, b = e - a * l;
+    const double v = (double)strip[(long long)__ldg(pos + a) * si + (long long)b * st];
+    if (!(fabs(v) <= DBL_MAX)) *bad = 1;
+    A[e] = v;
+  }
+  __syncthreads();
+  if (*bad) {
+    if (tid == 0) set_status(js, LRA_ENONFINITE);
+    return;
+  }
+  for (int t = 0; t < l; ++t) {
+    if (tid < 32) {  // pivot: largest |A[r][t]|, r >= t, compared on IEEE bit patterns
+      unsigned long long best = 0ull;
+      int br = l;
+      for (int r = t + tid; r < l; r += 32) {
+        const unsigned long long k = abs_bits(A[(size_t)r * l + t]);
+        if (br == l || k > best) { best = k; br = r; }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int orr = __shfl_down_sync(0xffffffffu, br, off);
+        if (orr < l && (br == l || ob > best || (ob == best && orr < br))) { best = ob; br = orr; }
+      }
+      if (tid == 0) {
+        const int p = (best != 0ull && br < l) ? br : -1;
+        *piv_row = p;
+        swaps[t] = p;
+        // one FP64 division for the whole step
+        if (p >= 0) *recip = 1.0 / A[(size_t)p * l + t];
+      }
+    }
+    __syncthreads();
+    const int p = *piv_row;
+    if (p < 0) {
+      if (tid == 0) set_status(js, LRA_ESINGULAR);
+      return;
+    }
+    const double rp = *recip;
+    // multipliers f[r] = A[r][t] of the rows after the swap (row p will hold
+    // the old row t), read before anything is written
+    for (int r = tid; r < l; r += nthr) {
+      const int rr = (r == p) ? t : r;
+      f[r] = (r == t) ? 0.0 : A[(size_t)rr * l + t];
+    }
+    __syncthreads();
+    // pivot row swapped into place and scaled by 1/pivot, its column t set to
+    // 1/pivot
+    for (int c = tid; c < l; c += nthr) {
+      const double x = A[(size_t)p * l + c];
+      if (p != t) A[(size_t)p * l + c] = A[(size_t)t * l + c];
+      const double y = (c == t) ? rp : x * rp;
+      rowt[c] = y;
+      A[(size_t)t * l + c] = y;
+    }
+    __syncthreads();
+    // A[r][c] -= f[r] rowt[c] for r != t, with A[r][t] starting from 0
+    for (int e = tid; e < l * l; e += nthr) {
+      const int r = e / l, c = e - r * l;
+      if (r == t) continue;
+      const double a = (c == t) ? 0.0 : A[e];
+      A[e] = fma(-f[r], rowt[c], a);
+    }
+    __syncthreads();
+  }
+  // undo the row interchanges as column interchanges, last first
+  for (int t = l - 1; t >= 0; --t) {
+    const int p = swaps[t];
+    if (p != t)
+      for (int r = tid; r < l; r += nthr) {
+        const double x = A[(size_t)r * l + t];
+        A[(size_t)r * l + t] = A[(size_t)r * l + p];
+        A[(size_t)r * l + p] = x;
+      }
+    __syncthreads();
+  }
+  for (int e = tid; e < l * l; e += nthr) xinv[e] = A[e];
+}
+
 // The same elimination for l <= 32 on one CTA.  At that size every step is
 // a chain of latencies (an FP64 division is ~430 cycles on this part), so a
 // step is cut to: the pivot, already reduced during the previous step's
@@ -336,9 +436,16 @@ cross_inverse_small_kernel(const float* __restrict__ strip, long long si, long l
 }
 
 cudaError_t launch_cross_inverse(const float* strip, long long si, long long st, const int* pos,
-                                 int l, double* xinv, JobStatus* js, cudaStream_t stream) {
+                                 int l, double* xinv, JobStatus* js, cudaStream_t stream, bool one_sm) {
   if (l <= kInvSmallL) {
     cross_inverse_small_kernel<<<1, kInvSmallT, 0, stream>>>(strip, si, st, pos, l, xinv, js);
+    return cudaGetLastError();
+  }
+  if (one_sm) {
+    const size_t smem = ((size_t)l * l + 2 * kMaxL + 1) * sizeof(double) + (kMaxL + 2) * sizeof(int);
+    const cudaError_t e = smem_optin(reinterpret_cast<const void*>(cross_inverse_cta_kernel), 227 * 1024);
+    if (e) return e;
+    cross_inverse_cta_kernel<<<1, kInvCtaT, smem, stream>>>(strip, si, st, pos, l, xinv, js);
     return cudaGetLastError();
   }
   const int w = (l + kInvCS - 1) / kInvCS;

@@ -58,7 +58,8 @@ cudaError_t launch_maxvol(MaxvolArgs a, const MaxvolPlan& plan, cudaStream_t st)
 // Inverse of the cross S[pos, :] of a strip (one CTA, FP64 Gauss-Jordan with
 // partial pivoting), row-major into xinv.
 cudaError_t launch_cross_inverse(const float* strip, long long si, long long st, const int* pos,
-                                 int l, double* xinv, JobStatus* js, cudaStream_t stream);
+                                 int l, double* xinv, JobStatus* js, cudaStream_t stream,
+                                 bool one_sm);
 
 // Nucleus of the final cross X = C[I, :] (one CTA, FP64 one-sided Jacobi SVD).
 cudaError_t launch_nucleus(const float* C, const int* I, int l, int k, double rank_tol,

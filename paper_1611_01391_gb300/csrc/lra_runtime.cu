@@ -259,6 +259,9 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
     j->prof.emplace_back(cls, ev);
     return cudaEventRecord(ev, st);
   };
+  // with several own streams the jobs overlap: the single-SM inverse then
+  // leaves the other SMs to them
+  const bool one_sm = ctx->streams.size() > 1;
   if ((e = cudaEventRecord(j->ev_start, st))) return e;
   for (int sw = 0; sw < j->sweeps; ++sw) {
     if ((e = launch_gather_cols(j->src, j->J, j->l, j->C, j->js, 1, ctx->sms, st)) || (e = after(kClsGather, 1))) return e;
@@ -266,7 +269,7 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
     col.half_step = 2 * sw;
     col.xin = j->xbuf0;   // inverse of A[I, J] (vertical strip's cross)
     if (!col.gepp) {
-      if ((e = launch_cross_inverse(j->C, j->l, 1, j->I, j->l, j->xbuf0, j->js, st)) ||
+      if ((e = launch_cross_inverse(j->C, j->l, 1, j->I, j->l, j->xbuf0, j->js, st, one_sm)) ||
           (e = after(kClsInverse, 1))) return e;
     }
     if ((e = launch_maxvol(col, j->plan_col, st)) || (e = after(kClsMaxvol, 1))) return e;
@@ -274,7 +277,7 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
     row.gepp = 0;
     row.half_step = 2 * sw + 1;
     row.xin = j->xbuf1;   // inverse of A[I, J]^T (horizontal strip's cross)
-    if ((e = launch_cross_inverse(j->R, 1, j->n, j->J, j->l, j->xbuf1, j->js, st)) ||
+    if ((e = launch_cross_inverse(j->R, 1, j->n, j->J, j->l, j->xbuf1, j->js, st, one_sm)) ||
         (e = after(kClsInverse, 1))) return e;
     if ((e = launch_maxvol(row, j->plan_row, st)) || (e = after(kClsMaxvol, 1))) return e;
     if ((e = launch_sweep_done(j->js, st)) || (e = after(kClsOther, 1))) return e;
@@ -595,11 +598,16 @@ lra_status lra_cross_fetch_cur(lra_ctx* ctx, lra_job id, const lra_cur_out* out)
         {out->trace, j->trace_i, sizeof(int) * 4 * (size_t)tl},
         {out->trace_val, j->trace_v, sizeof(double) * (size_t)tl},
     };
+    // the copies run on the control stream behind this job's end event only:
+    // on the job's own stream they would also wait for the jobs queued after it
+    cudaStream_t cs = ctx->ctrl ? ctx->ctrl : j->stream;
+    if (cs != j->stream) e = cudaStreamWaitEvent(cs, j->ev_end, 0);
     for (const Piece& pc : pieces) {
+      if (e) break;
       if (!pc.dst || pc.bytes == 0) continue;
-      if ((e = cudaMemcpyAsync(pc.dst, pc.src, pc.bytes, cudaMemcpyDefault, j->stream))) break;
+      e = cudaMemcpyAsync(pc.dst, pc.src, pc.bytes, cudaMemcpyDefault, cs);
     }
-    if (!e) e = cudaStreamSynchronize(j->stream);
+    if (!e) e = cudaStreamSynchronize(cs);
     if (e) result = cuda_fail(ctx, e, "fetch copy");
   } else {
     fail(ctx, result, lra_status_str(result));
@@ -808,11 +816,14 @@ lra_status lra_cross_fetch_batch(lra_ctx* ctx, lra_job id, const lra_batch_out* 
       {out->U, j->b_U, sizeof(double) * NB * L * L}, {out->sigma, j->b_sigma, sizeof(float) * NB * L},
       {out->est_err, j->b_err, sizeof(double) * NB},
   };
+  cudaStream_t cs = ctx->ctrl ? ctx->ctrl : j->stream;  // behind this job only
+  if (cs != j->stream) e = cudaStreamWaitEvent(cs, j->ev_end, 0);
   for (const Piece& pc : pieces) {
+    if (e) break;
     if (!pc.dst) continue;
-    if ((e = cudaMemcpyAsync(pc.dst, pc.src, pc.bytes, cudaMemcpyDefault, j->stream))) break;
+    e = cudaMemcpyAsync(pc.dst, pc.src, pc.bytes, cudaMemcpyDefault, cs);
   }
-  if (!e) e = cudaStreamSynchronize(j->stream);
+  if (!e) e = cudaStreamSynchronize(cs);
   if (e) result = cuda_fail(ctx, e, "fetch copy");
   ctx->jobs.erase(id);
   release_job(ctx, j);
