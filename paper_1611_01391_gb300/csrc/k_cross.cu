@@ -111,7 +111,7 @@ struct InvPub {
 
 __global__ void __cluster_dims__(kInvCS, 1, 1) __launch_bounds__(kInvCT, 1)
 cross_inverse_kernel(const float* __restrict__ strip, long long si, long long st,
-                     const int* __restrict__ pos, int l, double* __restrict__ xinv, JobStatus* js) {
+                     const int* __restrict__ pos, int l, float2* __restrict__ xinv, JobStatus* js) {
   if (js->status != LRA_OK || js->stop) return;  // same value in every CTA of the cluster
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
@@ -219,7 +219,7 @@ cross_inverse_kernel(const float* __restrict__ strip, long long si, long long st
   __syncthreads();
   for (int e = tid; e < l * nc; e += kInvCT) {
     const int r = e / nc, cc = e - r * nc;
-    xinv[(size_t)r * l + dest[c0 + cc]] = A[(size_t)r * w + cc];
+    xinv[(size_t)r * l + dest[c0 + cc]] = split_double(A[(size_t)r * w + cc]);
   }
   cl.sync();  // no peer reads this CTA's shared memory after it exits
 }
@@ -231,7 +231,7 @@ constexpr int kInvCtaT = 512;
 
 __global__ void __launch_bounds__(kInvCtaT, 1)
 cross_inverse_cta_kernel(const float* __restrict__ strip, long long si, long long st,
-                     const int* __restrict__ pos, int l, double* __restrict__ xinv, JobStatus* js) {
+                     const int* __restrict__ pos, int l, float2* __restrict__ xinv, JobStatus* js) {
   if (js->status != LRA_OK || js->stop) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* A = reinterpret_cast<double*>(smem_raw);  // l x l, row-major
@@ -321,7 +321,7 @@ cross_inverse_cta_kernel(const float* __restrict__ strip, long long si, long lon
       }
     __syncthreads();
   }
-  for (int e = tid; e < l * l; e += nthr) xinv[e] = A[e];
+  for (int e = tid; e < l * l; e += nthr) xinv[e] = split_double(A[e]);
 }
 
 // The same elimination for l <= 32 on one CTA.  At that size every step is
@@ -346,7 +346,7 @@ __device__ __forceinline__ unsigned long long pivot_key(double v, int r) {
 
 __global__ void __launch_bounds__(kInvSmallT, 1)
 cross_inverse_small_kernel(const float* __restrict__ strip, long long si, long long st,
-                           const int* __restrict__ pos, int l, double* __restrict__ xinv, JobStatus* js) {
+                           const int* __restrict__ pos, int l, float2* __restrict__ xinv, JobStatus* js) {
   if (js->status != LRA_OK || js->stop) return;
   __shared__ double buf[2][kInvSmallL * kInvSmallL];
   __shared__ double rowt[kInvSmallL];
@@ -431,12 +431,12 @@ cross_inverse_small_kernel(const float* __restrict__ strip, long long si, long l
   __syncthreads();
   for (int e = tid; e < ll; e += kInvSmallT) {
     const int r = e / l, c = e - r * l;
-    xinv[(size_t)r * l + dest[c]] = buf[cur][e];
+    xinv[(size_t)r * l + dest[c]] = split_double(buf[cur][e]);
   }
 }
 
 cudaError_t launch_cross_inverse(const float* strip, long long si, long long st, const int* pos,
-                                 int l, double* xinv, JobStatus* js, cudaStream_t stream, bool one_sm) {
+                                 int l, float2* xinv, JobStatus* js, cudaStream_t stream, bool one_sm) {
   if (l <= kInvSmallL) {
     cross_inverse_small_kernel<<<1, kInvSmallT, 0, stream>>>(strip, si, st, pos, l, xinv, js);
     return cudaGetLastError();

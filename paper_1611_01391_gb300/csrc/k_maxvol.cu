@@ -5,7 +5,9 @@
 // Design (one cooperative launch per half-step, the strip's B resident in
 // shared memory across the whole grid):
 //   * The N x l strip S is split into contiguous row chunks, one chunk per
-//     CTA, held as FP64 in shared memory (W).
+//     CTA, held in shared memory (W) as double-float pairs: about 48
+//     significant bits from FP32 instructions, which this GPU issues at 64
+//     times its FP64 rate.
 //   * Every decision is the same primitive: pick (i*, j*), then apply the
 //     rank-one update  W <- W - W[:, j*] (W[i*, :] - e_j*^T) / W[i*, j*].
 //       - First half-step: Gauss-Jordan elimination with partial pivoting;
@@ -13,20 +15,24 @@
 //         rows of |W[:, t]| (the GEPP pivot).  After l steps W = S X^{-1}
 //         with X = S[I, :].
 //       - Later half-steps start from W = S X^{-1}, where X^{-1} is computed
-//         afresh from the new cross by cross_inverse_kernel (an inverse
+//         afresh from the new cross by the cross inverse kernels (an inverse
 //         carried from strip to strip by rank-one updates loses a factor
 //         cond(X) of accuracy on the ill-conditioned crosses of smooth
-//         kernels).
+//         kernels), which hand it over as hi/lo FP32 pairs.
 //       - Maxvol swaps take (i*, j*) = argmax |B| and stop once it is
 //         <= 1 + delta.
-//   * Per decision: each CTA reduces its best (|value|, flat index) with warp
-//     shuffles, publishes it together with that row of W, one grid barrier,
-//     then every CTA reduces the <= 152 candidates itself and applies the
-//     update to its chunk while scanning for the next decision (fused pass).
+//   * Per decision: every warp reduces its best (|value|, flat index) with
+//     shuffles; one block barrier; warp 0 reduces the CTA's best, publishes
+//     it together with that row of W, arrives at the grid barrier, reduces
+//     the <= 152 candidates, fetches the pivot row and forms the update
+//     vector (W[i*, :] - e_j*^T) / W[i*, j*]; a second block barrier; every
+//     warp then applies the update to its rows while scanning for the next
+//     decision (fused pass).
 //   * Ties in |value| go to the smaller flat index i*l + j (smaller row, then
 //     smaller column), the same rule as the FP64 oracle.
 #include <cfloat>
 
+#include "dd_arith.cuh"
 #include "lra_kernels.h"
 #include "lra_internal.cuh"
 
@@ -35,22 +41,17 @@ namespace lra {
 constexpr int kMaxvolThreads = 512;
 constexpr int kNone = 0x7fffffff;
 
-// Candidates are compared on k = the IEEE-754 bit pattern of |value| as an
-// unsigned 64-bit integer, which orders non-negative doubles exactly like
-// their values.  Integer compares keep the argmax off the FP64 pipe (a
-// double compare issues at the FP64 rate, 1/64 of FP32 on this part).
+// Candidates are compared on the unsigned 64-bit key of |value|
+// (dd_abs_key): integer compares, no FP64 instruction per scanned entry.
 struct Best {
   unsigned long long k;
   int idx;
   int nf;
 };
 
-constexpr unsigned long long kAbsMask = 0x7fffffffffffffffull;
-constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
-
-__device__ __forceinline__ void consider(Best& b, double x, int idx) {
-  const unsigned long long k = abs_bits(x);
-  if (k >= kInfBits) {
+__device__ __forceinline__ void consider(Best& b, dd x, int idx) {
+  const unsigned long long k = dd_abs_key(x);
+  if (k >= kDdKeyNonFinite) {
     b.nf = 1;
   } else if (k > b.k || (k == b.k && idx < b.idx)) {
     b.k = k;
@@ -66,44 +67,56 @@ __device__ __forceinline__ void merge(Best& b, unsigned long long k, int idx, in
   }
 }
 
-__device__ __forceinline__ Best warp_reduce(Best b) {
+// Warp-wide reduction; every lane ends with the result.
+__device__ __forceinline__ Best warp_reduce_all(Best b) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    const unsigned long long k = __shfl_down_sync(0xffffffffu, b.k, off);
-    const int i = __shfl_down_sync(0xffffffffu, b.idx, off);
-    const int f = __shfl_down_sync(0xffffffffu, b.nf, off);
+    const unsigned long long k = __shfl_xor_sync(0xffffffffu, b.k, off);
+    const int i = __shfl_xor_sync(0xffffffffu, b.idx, off);
+    const int f = __shfl_xor_sync(0xffffffffu, b.nf, off);
     merge(b, k, i, f);
   }
   return b;
 }
 
-// Block-wide reduction; the result is broadcast through *out.
-__device__ __forceinline__ void block_reduce(Best b, Best* red, Best* out) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  b = warp_reduce(b);
-  if (lane == 0) red[warp] = b;
-  __syncthreads();
-  if (warp == 0) {
-    const int nw = blockDim.x >> 5;
-    Best c = (lane < nw) ? red[lane] : Best{0ull, kNone, 0};
-    c = warp_reduce(c);
-    if (lane == 0) *out = c;
-  }
-  __syncthreads();
-}
-
+// What warp 0 decided, for the other warps.
 struct Ctl {
-  Best cta_best;
-  Best win;
-  unsigned int gen;
-  int timed_out;
+  long long istar;
+  unsigned int base;   // grid-barrier arrivals before this launch
+  int kind;            // LRA_TRACE_*, or kFailed: the launch ends
+  int jstar;
 };
 
-// Warm start of the rows of this CTA: W[r, :] = S[g, :] X^{-1}.  A group of
-// GS lanes owns a row; lane gl computes columns gl + GS c, c < NC, so every
-// issued DFMA is useful work (NC = ceil(l / GS) exactly).
+enum { kBarOk = 0, kBarTimeout = 1, kBarStatus = 2 };
+constexpr int kFailed = -1, kUndecided = -2;
+
+// Grid-wide barrier of a cooperative launch on a counter that only grows:
+// the n-th barrier of a launch waits until the counter reaches base + n G.
+// Called by one thread, after a warp or block barrier that orders its CTA's
+// writes before it; the fence publishes them, the acquire loads order the
+// reads after it.  The wait ends early when the job's status leaves LRA_OK
+// (a cancellation, a failure in another CTA) or after 2 s.
+__device__ __forceinline__ int grid_arrive_wait(unsigned int* count, unsigned int target,
+                                                const int* status) {
+  __threadfence();
+  atomicAdd(count, 1u);
+  const unsigned long long t0 = globaltimer_ns();
+  for (unsigned int it = 1;; ++it) {
+    if ((int)(ld_acquire_u32(count) - target) >= 0) return kBarOk;
+    if ((it & 63u) == 0) {
+      if (*reinterpret_cast<const volatile int*>(status) != LRA_OK) return kBarStatus;
+      if (globaltimer_ns() - t0 > kWaitNs) return kBarTimeout;
+    }
+  }
+}
+
+// Warm start of the rows of this CTA: W[r, :] = S[g, :] X^{-1}, each entry a
+// compensated dot product (Dot2) of the exact FP32 strip row with the pairs
+// of X^{-1}.  A group of GS lanes owns a row; lane gl computes columns
+// gl + GS c, c < NC, so every issued instruction is useful work
+// (NC = ceil(l / GS) exactly).
 template <int GS, int NC, typename XPtr>
-__device__ __forceinline__ void warm_rows(const MaxvolArgs& a, double* B, int nrows, long long row0,
+__device__ __forceinline__ void warm_rows(const MaxvolArgs& a, dd* B, int nrows, long long row0,
                                           XPtr X) {
   const int l = a.l;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -114,24 +127,24 @@ __device__ __forceinline__ void warm_rows(const MaxvolArgs& a, double* B, int nr
     const int r = base + lane / GS;
     const bool active = r < nrows;
     const long long g = row0 + r;
-    double* brow = B + (size_t)r * l;
+    dd* brow = B + (size_t)r * l;
     if (active)
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const int t = gl + GS * c;
-        if (t < l) brow[t] = (double)a.strip[g * a.si + (long long)t * a.st];
+        if (t < l) brow[t] = dd_make(a.strip[g * a.si + (long long)t * a.st]);
       }
     __syncwarp();
-    double acc[NC];
+    dacc acc[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+    for (int c = 0; c < NC; ++c) acc[c] = dacc{0.0f, 0.0f};
     if (active) {
       for (int p = 0; p < l; ++p) {
-        const double sp = brow[p];
+        const float sp = brow[p].hi;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           const int q = gl + GS * c;
-          if (q < l) acc[c] = fma(sp, X[(size_t)p * l + q], acc[c]);
+          if (q < l) acc_fma_f(acc[c], sp, X[(size_t)p * l + q]);
         }
       }
     }
@@ -140,14 +153,22 @@ __device__ __forceinline__ void warm_rows(const MaxvolArgs& a, double* B, int nr
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const int q = gl + GS * c;
-        if (q < l) brow[q] = acc[c];
+        if (q < l) brow[q] = acc_value(acc[c]);
       }
   }
 }
 
+struct SharedX {
+  const dd* p;
+  __device__ __forceinline__ dd operator[](size_t i) const { return p[i]; }
+};
+
 struct GlobalX {  // read-only path for an X^{-1} that does not fit on chip
-  const double* p;
-  __device__ __forceinline__ double operator[](size_t i) const { return __ldg(p + i); }
+  const float2* p;
+  __device__ __forceinline__ dd operator[](size_t i) const {
+    const float2 v = __ldg(p + i);
+    return dd{v.x, v.y};
+  }
 };
 
 template <int GS, int NC>
@@ -162,40 +183,41 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
   const int nrows = (int)max(0LL, min((long long)a.rows_per_cta, N - row0));
   const int rpc = a.rows_per_cta;
 
-  double* B = reinterpret_cast<double*>(smem_raw);          // rpc * l
-  double* colj = B + (size_t)rpc * l;                        // rpc
-  double* rraw = colj + rpc;                                 // l
-  double* rvec = rraw + kMaxL;                               // l
-  double* xs = rvec + kMaxL;                                 // l*l when staged
+  dd* B = reinterpret_cast<dd*>(smem_raw);                   // rpc * l
+  dd* rvec = B + (size_t)rpc * l;                             // l: the update's row factor
+  dd* xs = rvec + kMaxL;                                      // l*l when staged
   Best* red = reinterpret_cast<Best*>(xs + (a.stage_xinv ? (size_t)l * l : 0));  // 32
   Ctl* ctl = reinterpret_cast<Ctl*>(red + 32);
   int* pos_s = reinterpret_cast<int*>(ctl + 1);              // l
   unsigned char* used = reinterpret_cast<unsigned char*>(pos_s + kMaxL);  // rpc
+  dd* cand_rows = reinterpret_cast<dd*>(a.cand_rows);
 
-  const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
+  const int lane = tid & 31, warp = tid >> 5;
   constexpr int kGpw = 32 / GS;
   const int gl = lane % GS;
-  const int ngroups = nwarps * kGpw;
+  const int ngroups = (nthr >> 5) * kGpw;
 
   for (int t = tid; t < l; t += nthr) pos_s[t] = a.gepp ? -1 : a.pos[t];
   for (int r = tid; r < nrows; r += nthr) used[r] = 0;
-  if (tid == 0) {
-    ctl->gen = ld_acquire_u32(&a.bar->gen);
-    ctl->timed_out = 0;
-  }
+  // every launch leaves the counter at a multiple of 256 > G, and no CTA can
+  // pass the first barrier before this one arrives
+  if (tid == 0) ctl->base = ld_acquire_u32(&a.bar->count) & ~255u;
   __syncthreads();
 
   // ---- W = S (Gauss-Jordan start) or S X^{-1} (warm start)
   if (a.gepp) {
     for (int e = tid; e < nrows * l; e += nthr) {
       const int r = e / l, t = e - r * l;
-      B[e] = (double)a.strip[(row0 + r) * a.si + (long long)t * a.st];
+      B[e] = dd_make(a.strip[(row0 + r) * a.si + (long long)t * a.st]);
     }
   } else {
     if (a.stage_xinv) {
-      for (int e = tid; e < l * l; e += nthr) xs[e] = a.xin[e];
+      for (int e = tid; e < l * l; e += nthr) {
+        const float2 v = a.xin[e];
+        xs[e] = dd{v.x, v.y};
+      }
       __syncthreads();
-      warm_rows<GS, NC>(a, B, nrows, row0, static_cast<const double*>(xs));
+      warm_rows<GS, NC>(a, B, nrows, row0, SharedX{xs});
     } else {
       warm_rows<GS, NC>(a, B, nrows, row0, GlobalX{a.xin});
     }
@@ -204,7 +226,7 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
     for (int t = 0; t < l; ++t) {
       const long long g = pos_s[t];
       if (g >= row0 && g < row0 + nrows)
-        for (int c = tid; c < l; c += nthr) B[(size_t)(g - row0) * l + c] = (c == t) ? 1.0 : 0.0;
+        for (int c = tid; c < l; c += nthr) B[(size_t)(g - row0) * l + c] = dd_make(c == t ? 1.0f : 0.0f);
     }
   }
   __syncthreads();
@@ -219,89 +241,111 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
   }
 
   int buf = 0, step = 0, swaps = 0, capped = 0;
+  unsigned int nbar = 0;   // grid barriers of this launch (warp 0)
   for (;;) {
-    block_reduce(mine, red, &ctl->cta_best);
-    Best win;
-    if (G > 1) {
-      const Best cb = ctl->cta_best;
-      Cand* slot = a.cand + buf * kMaxGrid + cta;
-      if (tid == 0) *slot = Cand{cb.k, cb.idx, cb.nf};
-      if (cb.idx != kNone && tid < l) {
-        const int r = (int)(cb.idx / l - row0);
-        a.cand_rows[((size_t)buf * kMaxGrid + cta) * l + tid] = B[(size_t)r * l + tid];
-      }
-      if (!grid_sync(a.bar, &ctl->gen, &ctl->timed_out)) {
-        if (tid == 0) set_status(a.js, LRA_ETIMEOUT);
-        return;
-      }
-      Best c{0ull, kNone, 0};
-      for (int k = tid; k < G; k += nthr) {
-        const Cand* p = a.cand + buf * kMaxGrid + k;
-        merge(c, __ldcg(&p->key), __ldcg(&p->idx), __ldcg(&p->flags));
-      }
-      block_reduce(c, red, &ctl->win);
-      win = ctl->win;
-    } else {
-      win = ctl->cta_best;
-    }
+    mine = warp_reduce_all(mine);
+    if (lane == 0) red[warp] = mine;
+    __syncthreads();
 
-    // ---- decision (identical in every CTA)
-    const double wv = __longlong_as_double((long long)win.k);
-    int kind;
-    if (win.nf) {
-      if (cta == 0 && tid == 0) set_status(a.js, LRA_ENONFINITE);
-      return;
-    }
-    if (gepp_phase) {
-      if (!(wv > 0.0) || win.idx == kNone) {
-        if (cta == 0 && tid == 0) set_status(a.js, LRA_ESINGULAR);
-        return;
-      }
-      kind = LRA_TRACE_GEPP;
-    } else if (wv <= 1.0 + a.delta) {
-      kind = LRA_TRACE_STOP;
-    } else if (swaps >= a.max_swaps) {
-      kind = LRA_TRACE_CAP;
-      capped = 1;
-    } else {
-      kind = LRA_TRACE_SWAP;
-    }
-    const long long istar = (win.idx == kNone) ? -1 : win.idx / l;
-    const int jstar = (win.idx == kNone) ? 0 : (int)(win.idx - istar * l);
-    if (cta == 0 && tid == 0) {
-      const int n = a.js->trace_len;
-      if (n < a.js->trace_cap) {
-        a.trace_i[4 * n + 0] = a.half_step;
-        a.trace_i[4 * n + 1] = kind;
-        a.trace_i[4 * n + 2] = (int)istar;
-        a.trace_i[4 * n + 3] = jstar;
-        a.trace_v[n] = wv;
-        a.js->trace_len = n + 1;
-      }
-    }
-    if (kind == LRA_TRACE_STOP || kind == LRA_TRACE_CAP) break;
-
-    // ---- pivot row and column of W
-    const bool own_piv = istar >= row0 && istar < row0 + nrows;
-    if (tid < l) {
+    // ---- warp 0: the CTA's candidate, the grid exchange and the decision
+    if (warp == 0) {
+      Best win = lane < (nthr >> 5) ? red[lane] : Best{0ull, kNone, 0};
+      win = warp_reduce_all(win);
+      int kind = kUndecided;
       if (G > 1) {
-        const int owner = (int)(istar / rpc);
-        rraw[tid] = __ldcg(a.cand_rows + ((size_t)buf * kMaxGrid + owner) * l + tid);
-      } else {
-        rraw[tid] = B[(size_t)(istar - row0) * l + tid];
+        if (lane == 0) a.cand[buf * kMaxGrid + cta] = Cand{win.k, win.idx, win.nf};
+        if (win.idx != kNone) {
+          const int r = (int)(win.idx / l - row0);
+          for (int t = lane; t < l; t += 32)
+            cand_rows[((size_t)buf * kMaxGrid + cta) * l + t] = B[(size_t)r * l + t];
+        }
+        __syncwarp();
+        ++nbar;
+        int code = kBarOk;
+        if (lane == 0) code = grid_arrive_wait(&a.bar->count, ctl->base + nbar * (unsigned)G, &a.js->status);
+        code = __shfl_sync(0xffffffffu, code, 0);
+        if (code != kBarOk) {
+          if (code == kBarTimeout && lane == 0) set_status(a.js, LRA_ETIMEOUT);
+          kind = kFailed;
+        } else {
+          Best c{0ull, kNone, 0};
+          for (int k = lane; k < G; k += 32) {
+            const Cand* p = a.cand + buf * kMaxGrid + k;
+            merge(c, __ldcg(&p->key), __ldcg(&p->idx), __ldcg(&p->flags));
+          }
+          win = warp_reduce_all(c);
+        }
+      }
+      const double wv = dd_key_value(win.k);
+      if (kind == kUndecided) {
+        if (win.nf) {
+          if (cta == 0 && lane == 0) set_status(a.js, LRA_ENONFINITE);
+          kind = kFailed;
+        } else if (gepp_phase) {
+          if (!(wv > 0.0) || win.idx == kNone) {
+            if (cta == 0 && lane == 0) set_status(a.js, LRA_ESINGULAR);
+            kind = kFailed;
+          } else {
+            kind = LRA_TRACE_GEPP;
+          }
+        } else if (win.idx == kNone || wv <= 1.0 + a.delta) {
+          kind = LRA_TRACE_STOP;
+        } else if (swaps >= a.max_swaps) {
+          kind = LRA_TRACE_CAP;
+        } else {
+          kind = LRA_TRACE_SWAP;
+        }
+      }
+      const long long istar = (win.idx == kNone) ? -1 : win.idx / l;
+      const int jstar = (win.idx == kNone) ? 0 : (int)(win.idx - istar * l);
+      if (kind >= 0 && cta == 0 && lane == 0) {
+        const int n = a.js->trace_len;
+        if (n < a.js->trace_cap) {
+          a.trace_i[4 * n + 0] = a.half_step;
+          a.trace_i[4 * n + 1] = kind;
+          a.trace_i[4 * n + 2] = (int)istar;
+          a.trace_i[4 * n + 3] = jstar;
+          a.trace_v[n] = wv;
+          a.js->trace_len = n + 1;
+        }
+      }
+      if (kind == LRA_TRACE_GEPP || kind == LRA_TRACE_SWAP) {
+        // pivot row of W and the update's row factor (W[i*, :] - e_j*^T) / W[i*, j*]
+        const dd* prow = (G > 1) ? cand_rows + ((size_t)buf * kMaxGrid + istar / rpc) * l
+                                 : B + (size_t)(istar - row0) * l;
+        auto load = [&](int t) -> dd {
+          if (G > 1) {
+            const float2 v = __ldcg(reinterpret_cast<const float2*>(prow + t));
+            return dd{v.x, v.y};
+          }
+          return prow[t];
+        };
+        const dd piv = load(jstar);
+        for (int t = lane; t < l; t += 32) {
+          dd rt = load(t);
+          if (t == jstar) rt = dd_add(rt, dd_make(-1.0f));
+          rvec[t] = dd_div(rt, piv);
+        }
+        if (lane == 0) {
+          if (gepp_phase && istar >= row0 && istar < row0 + nrows) used[istar - row0] = 1;
+          pos_s[jstar] = (int)istar;
+        }
+      }
+      if (lane == 0) {
+        ctl->kind = kind;
+        ctl->istar = istar;
+        ctl->jstar = jstar;
       }
     }
-    for (int r = tid; r < nrows; r += nthr) colj[r] = B[(size_t)r * l + jstar];
-    if (tid == 0) {
-      if (gepp_phase && own_piv) used[istar - row0] = 1;
-      pos_s[jstar] = (int)istar;
-    }
     __syncthreads();
-    if (tid < l) {
-      const double piv = rraw[jstar];
-      rvec[tid] = (rraw[tid] - (tid == jstar ? 1.0 : 0.0)) / piv;
+    const int kind = ctl->kind;
+    if (kind == kFailed) return;
+    if (kind == LRA_TRACE_STOP || kind == LRA_TRACE_CAP) {
+      capped = kind == LRA_TRACE_CAP;
+      break;
     }
-    __syncthreads();
+    const long long istar = ctl->istar;
+    const int jstar = ctl->jstar;
 
     // ---- fused update + scan for the next decision
     const bool next_gepp = gepp_phase && (step + 1 < l);
@@ -309,27 +353,29 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
     mine = Best{0ull, kNone, 0};
     for (int base = warp * kGpw; base < nrows; base += ngroups) {
       const int r = base + lane / GS;
+      dd* brow = B + (size_t)r * l;
+      // the row's entry in column j* is read before its group writes the row
+      const dd c = r < nrows ? brow[jstar] : dd_make(0.0f);
+      __syncwarp();
       if (r < nrows) {
         const long long g = row0 + r;
-        double* brow = B + (size_t)r * l;
         if (g == istar) {
 #pragma unroll
           for (int cc = 0; cc < NC; ++cc) {
             const int t = gl + GS * cc;
             if (t < l) {
-              const double v = (t == jstar) ? 1.0 : 0.0;
+              const dd v = dd_make(t == jstar ? 1.0f : 0.0f);
               brow[t] = v;
               if (!next_gepp) consider(mine, v, (int)(g * l + t));
             }
           }
         } else {
-          const double c = colj[r];
           const bool scan_row = !(next_gepp && used[r]);
 #pragma unroll
           for (int cc = 0; cc < NC; ++cc) {
             const int t = gl + GS * cc;
             if (t < l) {
-              const double v = fma(-c, rvec[t], brow[t]);
+              const dd v = dd_fnma(c, rvec[t], brow[t]);
               brow[t] = v;
               if (scan_row && (!next_gepp || t == next_col)) consider(mine, v, (int)(g * l + t));
             }
@@ -343,10 +389,11 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
       ++swaps;
     }
     buf ^= 1;
-    __syncthreads();
   }
 
-  // ---- epilogue: positions and counters
+  // ---- epilogue: positions, counters, and the barrier counter rounded up to
+  // a multiple of 256 for the next launch (every CTA has arrived at the last
+  // barrier once CTA 0 passed it)
   if (cta == 0 && tid < l) a.pos[tid] = pos_s[tid];
   if (cta == 0 && tid == 0) {
     a.js->swaps_total += swaps;
@@ -356,12 +403,14 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
     const double upd = (double)(step + swaps) * 2.0 * (double)N * l;
     const double init = a.gepp ? 0.0 : 2.0 * (double)N * l * l;
     a.js->maxvol_flops += upd + init;
+    const unsigned int pad = (256u - ((nbar * (unsigned)G) & 255u)) & 255u;
+    if (pad) atomicAdd(&a.bar->count, pad);
   }
 }
 
 static size_t maxvol_smem(int rpc, int l, bool stage_xinv) {
-  size_t b = (size_t)rpc * l * sizeof(double) + (size_t)rpc * sizeof(double) +
-             2 * kMaxL * sizeof(double) + (stage_xinv ? (size_t)l * l * sizeof(double) : 0) +
+  size_t b = (size_t)rpc * l * sizeof(dd) + kMaxL * sizeof(dd) +
+             (stage_xinv ? (size_t)l * l * sizeof(dd) : 0) +
              32 * sizeof(Best) + sizeof(Ctl) + kMaxL * sizeof(int) + (size_t)rpc;
   return (b + 15) & ~(size_t)15;
 }

@@ -109,9 +109,11 @@ struct BatchArgs {
   JobStatus* js;            // maxvol_flops accumulates the elimination / update FLOPs
 };
 
+// Arrival counter of the maxvol grid barrier (zero for a new job; every
+// maxvol launch leaves it at a multiple of 256).
 struct GridBarrier {
   unsigned int count;
-  unsigned int gen;
+  unsigned int reserved;
 };
 
 // Candidate of one CTA in the grid-wide argmax exchange.
@@ -133,6 +135,13 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
   return k & 0x7fffffffffffffffull;
 }
 
+// x as an FP32 pair: hi = x rounded to FP32, lo = the rest rounded to FP32
+// (about 48 significant bits of x).
+__device__ __forceinline__ float2 split_double(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -147,37 +156,6 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
 
 __device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Grid-wide barrier for a cooperative (co-resident) launch.  The last CTA to
-// arrive resets the counter and bumps the generation; the others wait on the
-// generation with a 2 s deadline.  Returns false (and sets *timed_out, a
-// shared-memory flag) if the deadline passed.
-__device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned int* gen_local,
-                                          int* timed_out) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned int g = *gen_local;
-    __threadfence();
-    const unsigned int arrived = atomicAdd(&bar->count, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(&bar->count, 0u);
-      __threadfence();
-      st_release_u32(&bar->gen, g + 1);
-    } else {
-      const unsigned long long t0 = globaltimer_ns();
-      while (ld_acquire_u32(&bar->gen) == g) {
-        if (globaltimer_ns() - t0 > kWaitNs) {
-          *timed_out = 1;
-          break;
-        }
-      }
-    }
-    *gen_local = g + 1;
-    __threadfence();
-  }
-  __syncthreads();
-  return *timed_out == 0;
 }
 
 __device__ __forceinline__ void set_status(JobStatus* js, int code) {

@@ -19,8 +19,9 @@ cudaError_t launch_gather_rows(const SourceDev& s, const int* I, int l, float* R
 // One maxvol half-step on an N x l FP32 strip whose element (i, t) sits at
 // strip[i*si + t*st].  gepp = 1: Gauss-Jordan elimination with partial
 // pivoting selects the initial rows; gepp = 0: warm start from pos[] with xin
-// = inverse of the strip's cross S[pos, :] (row-major).  On exit pos[] holds
-// the selected rows.
+// = inverse of the strip's cross S[pos, :] (row-major, each entry split into
+// an FP32 pair x + y, see split_double).  On exit pos[] holds the selected
+// rows.
 struct MaxvolArgs {
   const float* strip;
   long long N;
@@ -28,9 +29,9 @@ struct MaxvolArgs {
   long long si, st;
   int gepp;
   int* pos;
-  const double* xin;
+  const float2* xin;
   Cand* cand;
-  double* cand_rows;
+  float2* cand_rows;   // one published row of W per CTA and buffer (pairs)
   GridBarrier* bar;
   JobStatus* js;
   int* trace_i;
@@ -55,10 +56,10 @@ struct MaxvolPlan {
 bool plan_maxvol(long long N, int l, int sms, size_t smem_limit, MaxvolPlan* plan);
 cudaError_t launch_maxvol(MaxvolArgs a, const MaxvolPlan& plan, cudaStream_t st);
 
-// Inverse of the cross S[pos, :] of a strip (one CTA, FP64 Gauss-Jordan with
-// partial pivoting), row-major into xinv.
+// Inverse of the cross S[pos, :] of a strip (FP64 Gauss-Jordan with partial
+// pivoting), row-major into xinv as FP32 pairs (split_double).
 cudaError_t launch_cross_inverse(const float* strip, long long si, long long st, const int* pos,
-                                 int l, double* xinv, JobStatus* js, cudaStream_t stream,
+                                 int l, float2* xinv, JobStatus* js, cudaStream_t stream,
                                  bool one_sm);
 
 // Nucleus of the final cross X = C[I, :] (one CTA, FP64 one-sided Jacobi SVD).

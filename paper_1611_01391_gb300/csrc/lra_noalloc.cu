@@ -25,10 +25,11 @@ struct NoAllocScratch {
   int trace_i[4];
   double trace_v[1];
   Cand cand[2 * kMaxGrid];
-  double cand_rows[2 * kMaxGrid * kMaxL];
+  float2 cand_rows[2 * kMaxGrid * kMaxL];
+  float2 xsplit[kMaxL * kMaxL];  // the caller's X^{-1} as FP32 pairs
 };
 
-// Static scratch: ~251 KB on every device that loads this library, held
+// Static scratch: ~325 KB on every device that loads this library, held
 // until the process exits.  Sized for l <= 96 and grids of <= 160 CTAs.
 __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
 
@@ -71,6 +72,11 @@ __global__ void noalloc_init_kernel(NoAllocScratch* s) {
   s->bar.count = 0;
 }
 
+__global__ void noalloc_split_kernel(const double* __restrict__ xinv, int ll, NoAllocScratch* s) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ll; e += gridDim.x * blockDim.x)
+    s->xsplit[e] = split_double(xinv[e]);
+}
+
 __global__ void noalloc_finish_kernel(const NoAllocScratch* s, int32_t* status_out) {
   status_out[0] = s->js.status;
   status_out[1] = s->js.swaps_total;
@@ -99,6 +105,7 @@ extern "C" lra_status lra_maxvol_noalloc(const float* strip, int64_t N, int32_t 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   NoAllocScratch* s = static_cast<NoAllocScratch*>(ds.scratch);
   noalloc_init_kernel<<<1, 1, 0, st>>>(s);
+  if (xinv) noalloc_split_kernel<<<(l * l + 255) / 256, 256, 0, st>>>(xinv, l * l, s);
   MaxvolArgs a{};
   a.strip = strip;
   a.N = N;
@@ -107,7 +114,7 @@ extern "C" lra_status lra_maxvol_noalloc(const float* strip, int64_t N, int32_t 
   a.st = col_stride;
   a.gepp = xinv ? 0 : 1;
   a.pos = pos;
-  a.xin = xinv;
+  a.xin = xinv ? s->xsplit : nullptr;
   a.cand = s->cand;
   a.cand_rows = s->cand_rows;
   a.bar = &s->bar;

@@ -27,12 +27,14 @@ struct Job {
   long long m = 0, n = 0, q = 0, s = 0;
   double delta = 0, rank_tol = 0, tol = 0;
   unsigned char* dmem = nullptr;
+  size_t prefix = 0;  // bytes of dmem filled from the slot's staging at submit
   size_t bytes = 0;
   JobStatus* js = nullptr;
   GridBarrier* bar = nullptr;
   int *J = nullptr, *I = nullptr, *rows = nullptr, *cols = nullptr, *trace_i = nullptr;
-  double *xbuf0 = nullptr, *xbuf1 = nullptr, *U = nullptr, *sigma = nullptr, *cand_rows = nullptr,
-         *trace_v = nullptr, *partials = nullptr;
+  double *U = nullptr, *sigma = nullptr, *trace_v = nullptr, *partials = nullptr;
+  float2 *xbuf0 = nullptr, *xbuf1 = nullptr;  // cross inverses as FP32 pairs
+  float2* cand_rows = nullptr;
   float *C = nullptr, *R = nullptr, *CUq = nullptr;
   Cand* cand = nullptr;
   int n_partials = 0;
@@ -86,6 +88,14 @@ struct lra_ctx {
   uint64_t budget = 0;
   uint64_t used_bytes = 0;
   JobStatus* pinned = nullptr;  // one result slot per job slot
+  // pinned staging of each slot's submit-time inputs (status, barrier, J,
+  // residual sample), copied to the device in one asynchronous copy
+  std::vector<unsigned char*> stage;
+  std::vector<size_t> stage_cap;
+  // the jobs' device memory: a pool of this context that keeps what it has
+  // (no return to the system at each synchronisation) and reuses a block
+  // only once its free has run (no waits between the streams)
+  cudaMemPool_t pool = nullptr;
   std::vector<int> free_slots;
   std::mutex mu;
   std::unordered_map<lra_job, Job*> jobs;
@@ -158,20 +168,22 @@ size_t layout_bytes(const lra_source* src, const lra_params* p, Job* j) {
   const int l = p->l;
   const long long q = p->resid_q, s = p->resid_s;
   Layout L;
+  // the inputs copied at submit come first, as one contiguous prefix
   const size_t o_js = L.take(sizeof(JobStatus));
   const size_t o_bar = L.take(sizeof(GridBarrier));
   const size_t o_J = L.take(sizeof(int) * l);
+  const size_t o_rows = L.take(sizeof(int) * std::max<long long>(q, 1));
+  const size_t o_cols = L.take(sizeof(int) * std::max<long long>(s, 1));
+  const size_t prefix = L.off;
   const size_t o_I = L.take(sizeof(int) * l);
-  const size_t o_x0 = L.take(sizeof(double) * l * l);
-  const size_t o_x1 = L.take(sizeof(double) * l * l);
+  const size_t o_x0 = L.take(sizeof(float2) * l * l);
+  const size_t o_x1 = L.take(sizeof(float2) * l * l);
   const size_t o_U = L.take(sizeof(double) * l * l);
   const size_t o_sig = L.take(sizeof(double) * l);
   const size_t o_cand = L.take(sizeof(Cand) * 2 * kMaxGrid);
-  const size_t o_candr = L.take(sizeof(double) * 2 * kMaxGrid * l);
+  const size_t o_candr = L.take(sizeof(float2) * 2 * kMaxGrid * l);
   const size_t o_ti = L.take(sizeof(int) * 4 * std::max(p->trace_cap, 1));
   const size_t o_tv = L.take(sizeof(double) * std::max(p->trace_cap, 1));
-  const size_t o_rows = L.take(sizeof(int) * std::max<long long>(q, 1));
-  const size_t o_cols = L.take(sizeof(int) * std::max<long long>(s, 1));
   const int np = q > 0 ? sampled_residual_partials((int)q, (int)s) : 1;
   const size_t o_cuq = L.take(sizeof(float) * std::max<long long>(2 * q * l, 1));
   const size_t o_part = L.take(sizeof(double) * 3 * np);
@@ -185,12 +197,12 @@ size_t layout_bytes(const lra_source* src, const lra_params* p, Job* j) {
     j->bar = reinterpret_cast<GridBarrier*>(b + o_bar);
     j->J = reinterpret_cast<int*>(b + o_J);
     j->I = reinterpret_cast<int*>(b + o_I);
-    j->xbuf0 = reinterpret_cast<double*>(b + o_x0);
-    j->xbuf1 = reinterpret_cast<double*>(b + o_x1);
+    j->xbuf0 = reinterpret_cast<float2*>(b + o_x0);
+    j->xbuf1 = reinterpret_cast<float2*>(b + o_x1);
     j->U = reinterpret_cast<double*>(b + o_U);
     j->sigma = reinterpret_cast<double*>(b + o_sig);
     j->cand = reinterpret_cast<Cand*>(b + o_cand);
-    j->cand_rows = reinterpret_cast<double*>(b + o_candr);
+    j->cand_rows = reinterpret_cast<float2*>(b + o_candr);
     j->trace_i = reinterpret_cast<int*>(b + o_ti);
     j->trace_v = reinterpret_cast<double*>(b + o_tv);
     j->rows = reinterpret_cast<int*>(b + o_rows);
@@ -201,6 +213,7 @@ size_t layout_bytes(const lra_source* src, const lra_params* p, Job* j) {
     j->R = reinterpret_cast<float*>(b + o_R);
     j->n_partials = np;
     j->fr_ws = fr ? (void*)(b + o_fr) : nullptr;
+    j->prefix = prefix;
   }
   return L.off;
 }
@@ -214,8 +227,15 @@ bool distinct_in_range(const int32_t* v, long long count, long long bound) {
   return true;
 }
 
+// Device memory goes back to the pool on the control stream behind the job's
+// end: on the job's own stream the free would also wait for the jobs queued
+// after it, and the pool could not hand the block to another job meanwhile.
 void release_job(lra_ctx* ctx, Job* j) {
-  if (j->dmem) cudaFreeAsync(j->dmem, j->stream);
+  if (j->dmem) {
+    cudaStream_t fs = ctx->ctrl ? ctx->ctrl : j->stream;
+    if (fs != j->stream && j->ev_end) cudaStreamWaitEvent(fs, j->ev_end, 0);
+    cudaFreeAsync(j->dmem, fs);
+  }
   if (j->stream_idx >= 0) ctx->stream_load[j->stream_idx]--;
   if (j->ev_start) cudaEventDestroy(j->ev_start);
   if (j->ev_end) cudaEventDestroy(j->ev_end);
@@ -233,13 +253,27 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
   init.status = LRA_OK;
   init.converged = 1;
   init.trace_cap = j->trace_cap;
-  if ((e = cudaMemcpyAsync(j->js, &init, sizeof(init), cudaMemcpyHostToDevice, st))) return e;
-  if ((e = cudaMemsetAsync(j->bar, 0, sizeof(GridBarrier), st))) return e;
-  if ((e = cudaMemcpyAsync(j->J, p->init_J, sizeof(int) * j->l, cudaMemcpyHostToDevice, st))) return e;
-  if (j->q > 0) {
-    if ((e = cudaMemcpyAsync(j->rows, p->resid_rows, sizeof(int) * j->q, cudaMemcpyHostToDevice, st))) return e;
-    if ((e = cudaMemcpyAsync(j->cols, p->resid_cols, sizeof(int) * j->s, cudaMemcpyHostToDevice, st))) return e;
+  // status, barrier, J and the residual sample: staged in the slot's pinned
+  // buffer (free again only once this job is released) and sent in one copy
+  if (ctx->stage_cap[j->slot] < j->prefix) {
+    if (ctx->stage[j->slot]) cudaFreeHost(ctx->stage[j->slot]);
+    ctx->stage[j->slot] = nullptr;
+    ctx->stage_cap[j->slot] = 0;
+    void* h = nullptr;
+    if ((e = cudaMallocHost(&h, j->prefix))) return e;
+    ctx->stage[j->slot] = static_cast<unsigned char*>(h);
+    ctx->stage_cap[j->slot] = j->prefix;
   }
+  unsigned char* hs = ctx->stage[j->slot];
+  auto at = [&](const void* dev) { return hs + (static_cast<const unsigned char*>(dev) - j->dmem); };
+  std::memset(hs, 0, j->prefix);
+  std::memcpy(at(j->js), &init, sizeof(init));
+  std::memcpy(at(j->J), p->init_J, sizeof(int) * j->l);
+  if (j->q > 0) {
+    std::memcpy(at(j->rows), p->resid_rows, sizeof(int) * j->q);
+    std::memcpy(at(j->cols), p->resid_cols, sizeof(int) * j->s);
+  }
+  if ((e = cudaMemcpyAsync(j->dmem, hs, j->prefix, cudaMemcpyHostToDevice, st))) return e;
   MaxvolArgs col{};
   col.strip = j->C; col.N = j->m; col.l = j->l; col.si = j->l; col.st = 1;
   col.pos = j->I; col.cand = j->cand; col.cand_rows = j->cand_rows; col.bar = j->bar;
@@ -441,6 +475,23 @@ lra_status lra_cross_create(lra_ctx** out, const lra_ctx_params* params) {
     delete ctx;
     return LRA_ENOMEM;
   }
+  ctx->stage.assign(ctx->max_slots, nullptr);
+  ctx->stage_cap.assign(ctx->max_slots, 0);
+  cudaMemPoolProps pp{};
+  pp.allocType = cudaMemAllocationTypePinned;
+  pp.location.type = cudaMemLocationTypeDevice;
+  pp.location.id = ctx->device;
+  if (cudaMemPoolCreate(&ctx->pool, &pp)) {
+    cudaFreeHost(ctx->pinned);
+    if (ctx->own_stream)
+      for (cudaStream_t t : ctx->streams) cudaStreamDestroy(t);
+    delete ctx;
+    return LRA_ECUDA;
+  }
+  uint64_t keep = ~0ULL;
+  int no = 0;
+  cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolReuseAllowInternalDependencies, &no);
   for (int s = ctx->max_slots - 1; s >= 0; --s) ctx->free_slots.push_back(s);
   if (cudaStreamCreateWithFlags(&ctx->ctrl, cudaStreamNonBlocking)) ctx->ctrl = nullptr;
   if (cudaMallocHost(&ctx->cancel_word, sizeof(int))) ctx->cancel_word = nullptr;
@@ -460,9 +511,15 @@ lra_status lra_cross_destroy(lra_ctx* ctx) {
     for (cudaStream_t s : ctx->streams) cudaStreamSynchronize(s);
     if (ctx->own_stream)
       for (cudaStream_t s : ctx->streams) cudaStreamDestroy(s);
-    if (ctx->ctrl) cudaStreamDestroy(ctx->ctrl);
+    if (ctx->ctrl) {
+      cudaStreamSynchronize(ctx->ctrl);
+      cudaStreamDestroy(ctx->ctrl);
+    }
     if (ctx->cancel_word) cudaFreeHost(ctx->cancel_word);
+    for (unsigned char* h : ctx->stage)
+      if (h) cudaFreeHost(h);
     cudaFreeHost(ctx->pinned);
+    if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   }
   delete ctx;
   return LRA_OK;
@@ -515,10 +572,10 @@ lra_status lra_cross_submit(lra_ctx* ctx, const lra_source* src, const lra_param
     return fail(ctx, LRA_EBUSY, "no free slot or memory budget exhausted");
   }
   assign_stream(ctx, j);
-  if ((e = cudaMallocAsync(reinterpret_cast<void**>(&j->dmem), j->bytes, j->stream))) {
+  if ((e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&j->dmem), j->bytes, ctx->pool, j->stream))) {
     ctx->stream_load[j->stream_idx]--;
     delete j;
-    return cuda_fail(ctx, e, "cudaMallocAsync");
+    return cuda_fail(ctx, e, "cudaMallocFromPoolAsync");
   }
   layout_bytes(src, p, j);
   j->slot = ctx->free_slots.back();
@@ -719,10 +776,10 @@ lra_status lra_cross_submit_batch(lra_ctx* ctx, const lra_source* src, const lra
     return fail(ctx, LRA_EBUSY, "no free slot or memory budget exhausted");
   }
   assign_stream(ctx, j);
-  if ((e = cudaMallocAsync(reinterpret_cast<void**>(&j->dmem), j->bytes, j->stream))) {
+  if ((e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&j->dmem), j->bytes, ctx->pool, j->stream))) {
     ctx->stream_load[j->stream_idx]--;
     delete j;
-    return cuda_fail(ctx, e, "cudaMallocAsync");
+    return cuda_fail(ctx, e, "cudaMallocFromPoolAsync");
   }
   unsigned char* base = j->dmem;
   j->js = reinterpret_cast<JobStatus*>(base + o_js);

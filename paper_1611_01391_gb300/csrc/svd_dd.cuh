@@ -14,57 +14,10 @@
 
 #include <cfloat>
 
+#include "dd_arith.cuh"
 #include "lra_internal.cuh"
 
 namespace lra {
-
-struct dd {
-  float hi, lo;
-};
-
-__device__ __forceinline__ dd dd_make(float x) { return dd{x, 0.0f}; }
-
-__device__ __forceinline__ dd dd_from_double(double x) {
-  const float h = (float)x;
-  return dd{h, (float)(x - (double)h)};
-}
-
-__device__ __forceinline__ double dd_to_double(dd a) { return (double)a.hi + (double)a.lo; }
-
-// Knuth's TwoSum: s + e == a + b exactly.
-__device__ __forceinline__ dd two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float z = __fsub_rn(s, a);
-  return dd{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z))};
-}
-
-// Dekker's FastTwoSum (|a| >= |b|): renormalise a pair.
-__device__ __forceinline__ dd quick_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  return dd{s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-
-__device__ __forceinline__ dd dd_add(dd a, dd b) {
-  dd s = two_sum(a.hi, b.hi);
-  const dd t = two_sum(a.lo, b.lo);
-  s.lo = __fadd_rn(s.lo, t.hi);
-  s = quick_two_sum(s.hi, s.lo);
-  s.lo = __fadd_rn(s.lo, t.lo);
-  return quick_two_sum(s.hi, s.lo);
-}
-
-__device__ __forceinline__ dd dd_neg(dd a) { return dd{-a.hi, -a.lo}; }
-
-// TwoProduct through the FMA, plus the cross terms.
-__device__ __forceinline__ dd dd_mul(dd a, dd b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = fmaf(a.hi, b.hi, -p);
-  e = fmaf(a.hi, b.lo, e);
-  e = fmaf(a.lo, b.hi, e);
-  return quick_two_sum(p, e);
-}
-
-__device__ __forceinline__ dd dd_fma(dd a, dd b, dd c) { return dd_add(dd_mul(a, b), c); }
 
 // Plane rotation that annihilates the off-diagonal of the 2 x 2 Gram matrix
 // [a g; g b] (Golub & Van Loan, Algorithm 8.5.1): zeta = (b - a) / (2 g),
@@ -101,42 +54,6 @@ __device__ __forceinline__ dd rotation_cosine(dd a, dd b, dd g, float* t_out) {
   return quick_two_sum(y0, __fmul_rn(__fmul_rn(0.5f, y0), r));
 }
 
-// Compensated accumulator of a dot product of double-float vectors: the
-// FP32 running sum s plus the FP32 sum c of every rounding error (the
-// product errors come exactly from the FMA, the sum errors from TwoSum), so
-// s + c carries about twice FP32 precision (Dot2 of Ogita, Rump & Oishi,
-// "Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005, with the
-// low parts of the operands folded into the product error).
-struct dacc {
-  float s, c;
-};
-
-__device__ __forceinline__ void acc_fma(dacc& a, dd x, dd y) {
-  const float p = __fmul_rn(x.hi, y.hi);
-  float e = fmaf(x.hi, y.hi, -p);
-  e = fmaf(x.hi, y.lo, e);
-  e = fmaf(x.lo, y.hi, e);
-  const dd t = two_sum(a.s, p);
-  a.s = t.hi;
-  a.c = __fadd_rn(a.c, __fadd_rn(t.lo, e));
-}
-
-__device__ __forceinline__ dacc acc_add(dacc a, dacc b) {
-  const dd t = two_sum(a.s, b.s);
-  return dacc{t.hi, __fadd_rn(__fadd_rn(a.c, b.c), t.lo)};
-}
-
-__device__ __forceinline__ dd acc_value(dacc a) { return two_sum(a.s, a.c); }
-
-// Sum over the G consecutive lanes of a group (G a power of two <= 32);
-// every lane of the warp must take part.
-template <int G>
-__device__ __forceinline__ dacc acc_group_sum(dacc a) {
-#pragma unroll
-  for (int off = G / 2; off > 0; off >>= 1)
-    a = acc_add(a, dacc{__shfl_xor_sync(0xffffffffu, a.s, off), __shfl_xor_sync(0xffffffffu, a.c, off)});
-  return a;
-}
 
 // c x + s y in double-float: both products with their FMA error terms, one
 // TwoSum for the high parts.
