@@ -66,14 +66,26 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# FP64 FMA issue rate of a GB300 SM: 1.25 TFLOP/s nominal at the 2070 MHz
-# maximum SM clock over 152 SMs is 2 FP64 FMA per SM per clock.
-FP64_FMA_PER_SM_CLK = 2
 SMS = 152
+# FP32 instructions per SM per clock (128 lanes; FADD, FMUL and FFMA alike).
+FP32_PER_SM_CLK = 128
+# The maxvol kernel computes in double-float pairs: one algorithmic
+# multiply-add costs 11 FP32 instructions in the warm start S X^{-1} (FMA
+# product, its exact error, the low part's term, TwoSum into the running sum,
+# two adds into the compensation) and 15 in a rank-one update (four for the
+# product and its error, six for TwoSum, two for the low parts, three to
+# renormalise).
+DD_OPS_WARM = 11
+DD_OPS_UPDATE = 15
 
 
-def fp64_peak_tflops(sm_mhz):
-    return SMS * FP64_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12
+def maxvol_dd_peak_tflops(flops, warm_fmas, sm_mhz):
+    """Algorithmic FLOP/s of a maxvol run whose every FP32 instruction issued
+    at the FP32 pipe rate: flops / (instruction count / rate)."""
+    upd_fmas = max(flops / 2 - warm_fmas, 0.0)
+    ops = DD_OPS_WARM * warm_fmas + DD_OPS_UPDATE * upd_fmas
+    t_min = ops / (SMS * FP32_PER_SM_CLK * sm_mhz * 1e6)
+    return flops / t_min / 1e12 if t_min > 0 else 0.0
 
 
 # ---------------------------------------------------------------------------
@@ -355,7 +367,10 @@ def run_ours(args, wl_name):
     t_r = sum(i.t_resid_ms for i in infos)
     sm_mhz = clk.get("sm_mhz") or 2070.0
     peaks, peak_kind = _peaks()
-    fp64_peak = fp64_peak_tflops(sm_mhz)
+    # warm starts: the column half-steps after the first sweep's and every
+    # row half-step, each N l^2 multiply-adds
+    warm = sum((i.sweeps_done - 1) * m * l * l + i.sweeps_done * n * l * l for i in infos)
+    mv_peak = maxvol_dd_peak_tflops(fl_mv, warm, sm_mhz)
     achieved = fl_mv / (t_mv / 1e3) / 1e12 if t_mv > 0 else 0.0
     # gathers: bytes written (strips) per solve; generated entries read nothing
     strips_bytes = ((sweeps + 1) * m * l + sweeps * l * n) * 4
@@ -408,11 +423,11 @@ def run_ours(args, wl_name):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32x2+f64",
         "data": "synthetic",
         "config": {"workload": wl_name, "generator": wl["kind"], "m": m, "n": n, "k": k, "l": l,
                    "sweeps": sweeps, "error_sample": f"{wl['q']}x{wl['s']}",
-                   "precision": "FP32 entries/strips, FP64 maxvol and cross, compensated FP32 residual products",
+                   "precision": "FP32 entries/strips, double-float (FP32 pair) maxvol, FP64 cross inverse, double-float nucleus, compensated FP32 residual products",
                    "l2": "flushed before every step (256 MiB write); steps timed individually",
                    "parallelism": f"replicas{world}"},
         "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
@@ -422,10 +437,13 @@ def run_ours(args, wl_name):
                                "inverse": sum(i.t_inverse_ms for i in infos) / len(infos),
                                "nucleus": t_x / len(infos), "resid": t_r / len(infos)},
         "roofline": {"kernel": "maxvol_kernel", "bound": "alu", "achieved": achieved,
-                     "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak if fp64_peak else None,
+                     "peak": mv_peak, "unit": "TFLOP/s", "frac": achieved / mv_peak if mv_peak else None,
                      "traffic": captured_traffic("k_maxvol.cu", f"maxvol_{wl_name}.md"),
                      "traffic_note": "DRAM bytes per maxvol launch from the committed ncu capture (null if the kernel changed since)",
-                     "peak_source": f"FP64 FMA rate: {SMS} SMs x {FP64_FMA_PER_SM_CLK} FMA/clk x median SM clock {sm_mhz:.0f} MHz"},
+                     "peak_source": (f"FP32 pipe: {SMS} SMs x {FP32_PER_SM_CLK} instr/clk x median SM clock "
+                                     f"{sm_mhz:.0f} MHz, at {DD_OPS_WARM} (warm start) / {DD_OPS_UPDATE} (update) "
+                                     "FP32 instructions per double-float multiply-add"),
+                     "note": "algorithmic FLOPs: warm start 2 N l^2 plus 2 N l per GEPP step or swap"},
         "gpu_launches": int(sum(i.kernel_launches for i in infos)),
         "clocks": clk,
         "e2e": e2e,
@@ -789,7 +807,7 @@ def run_serve(args, wl_name):
     line = {
         "metric": METRIC, "value": world * capacity, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(caps), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32x2+f64", "data": "synthetic",
         "config": {"workload": wl_name, "requests": len(prep), "sides": [wl["min_side"], wl["max_side"]],
                    "k": [8, 16, 32, 64], "generators": ["cauchy", "gauss h=0.5", "invdist"],
                    "admission_budget_gb": wl["budget_gb"], "slots": wl["slots"], "streams": wl["streams"],

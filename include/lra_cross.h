@@ -278,8 +278,8 @@ lra_status lra_cross_footprint(const lra_source* src, const lra_params* params,
  * Everything is enqueued on `stream` (cudaStream_t, NULL = legacy default);
  * the call returns without waiting for the GPU.
  *
- * Scratch: a static device array of about 325 KB (candidate slots for 160
- * CTAs, candidate rows of up to 96 entries, the caller's inverse split into
+ * Scratch: a static device array of about 325 KB (candidate words, candidate
+ * rows of up to 96 entries for 160 CTAs, the caller's inverse split into
  * FP32 pairs, the grid barrier and the status word), present on every GPU
  * that loads this library until exit.
  * Limits: l <= 96, and the strip must fit the shared memory of <= 160 CTAs;

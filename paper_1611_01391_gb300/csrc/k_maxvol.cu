@@ -21,13 +21,16 @@
 //         kernels), which hand it over as hi/lo FP32 pairs.
 //       - Maxvol swaps take (i*, j*) = argmax |B| and stop once it is
 //         <= 1 + delta.
-//   * Per decision: every warp reduces its best (|value|, flat index) with
-//     shuffles; one block barrier; warp 0 reduces the CTA's best, publishes
-//     it together with that row of W, arrives at the grid barrier, reduces
-//     the <= 152 candidates, fetches the pivot row and forms the update
-//     vector (W[i*, :] - e_j*^T) / W[i*, j*]; a second block barrier; every
-//     warp then applies the update to its rows while scanning for the next
-//     decision (fused pass).
+//   * Per decision: every warp reduces its best candidate word (|value| and
+//     flat index in one 64-bit integer) with shuffles; one block barrier;
+//     warp 0 takes the CTA's best, publishes that row of W, folds the word
+//     into the decision's word in global memory with one atomic max, arrives
+//     at the grid barrier, reads the maximum back (one load per CTA), fetches
+//     the winner's row and forms the update vector
+//     (W[i*, :] - e_j*^T) / W[i*, j*]; a second block barrier; every warp
+//     then applies the update to its rows while scanning for the next
+//     decision (fused pass).  Every CTA reads the same few words and one
+//     row, so the exchange costs few requests on those hot L2 lines.
 //   * Ties in |value| go to the smaller flat index i*l + j (smaller row, then
 //     smaller column), the same rule as the FP64 oracle.
 #include <cfloat>
@@ -39,56 +42,42 @@
 namespace lra {
 
 constexpr int kMaxvolThreads = 512;
-constexpr int kNone = 0x7fffffff;
 
-// Candidates are compared on the unsigned 64-bit key of |value|
-// (dd_abs_key): integer compares, no FP64 instruction per scanned entry.
-struct Best {
-  unsigned long long k;
-  int idx;
-  int nf;
-};
-
-__device__ __forceinline__ void consider(Best& b, dd x, int idx) {
-  const unsigned long long k = dd_abs_key(x);
-  if (k >= kDdKeyNonFinite) {
-    b.nf = 1;
-  } else if (k > b.k || (k == b.k && idx < b.idx)) {
-    b.k = k;
-    b.idx = idx;
-  }
+// Candidates are compared on one unsigned 64-bit word: the FP32 bit pattern
+// of |hi| (non-negative FP32 patterns order like their values as unsigned
+// integers) above 0xffffffff - the flat index i*l + j.  The largest word is
+// the largest |value|, ties to the smaller flat index (smaller row, then
+// smaller column), the rule of the FP64 oracle; values whose high parts are
+// equal (within 2^-24 of each other) are treated as ties.  Infinite and NaN
+// patterns sort above every finite one, so a non-finite entry always wins
+// and is caught at the decision.  An integer max per scanned entry, no FP64
+// instruction.
+__device__ __forceinline__ unsigned long long cand_word(dd x, long long idx) {
+  const unsigned int kh = __float_as_uint(x.hi) & 0x7fffffffu;
+  return ((unsigned long long)kh << 32) | (0xffffffffu - (unsigned int)idx);
 }
 
-__device__ __forceinline__ void merge(Best& b, unsigned long long k, int idx, int nf) {
-  b.nf |= nf;
-  if (k > b.k || (k == b.k && idx < b.idx)) {
-    b.k = k;
-    b.idx = idx;
-  }
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+  return a > b ? a : b;
 }
 
-// Warp-wide reduction; every lane ends with the result.
-__device__ __forceinline__ Best warp_reduce_all(Best b) {
+__device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    const unsigned long long k = __shfl_xor_sync(0xffffffffu, b.k, off);
-    const int i = __shfl_xor_sync(0xffffffffu, b.idx, off);
-    const int f = __shfl_xor_sync(0xffffffffu, b.nf, off);
-    merge(b, k, i, f);
-  }
-  return b;
+  for (int off = 16; off > 0; off >>= 1) v = umax64(v, __shfl_xor_sync(0xffffffffu, v, off));
+  return v;
 }
 
 // What warp 0 decided, for the other warps.
 struct Ctl {
   long long istar;
   unsigned int base;   // grid-barrier arrivals before this launch
+  unsigned int seq0;   // the job's decision counter when this launch started
   int kind;            // LRA_TRACE_*, or kFailed: the launch ends
   int jstar;
 };
 
-enum { kBarOk = 0, kBarTimeout = 1, kBarStatus = 2 };
 constexpr int kFailed = -1, kUndecided = -2;
+enum { kBarOk = 0, kBarTimeout = 1, kBarStatus = 2 };
 
 // Grid-wide barrier of a cooperative launch on a counter that only grows:
 // the n-th barrier of a launch waits until the counter reaches base + n G.
@@ -186,7 +175,7 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
   dd* B = reinterpret_cast<dd*>(smem_raw);                   // rpc * l
   dd* rvec = B + (size_t)rpc * l;                             // l: the update's row factor
   dd* xs = rvec + kMaxL;                                      // l*l when staged
-  Best* red = reinterpret_cast<Best*>(xs + (a.stage_xinv ? (size_t)l * l : 0));  // 32
+  unsigned long long* red = reinterpret_cast<unsigned long long*>(xs + (a.stage_xinv ? (size_t)l * l : 0));  // 32
   Ctl* ctl = reinterpret_cast<Ctl*>(red + 32);
   int* pos_s = reinterpret_cast<int*>(ctl + 1);              // l
   unsigned char* used = reinterpret_cast<unsigned char*>(pos_s + kMaxL);  // rpc
@@ -199,9 +188,12 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
 
   for (int t = tid; t < l; t += nthr) pos_s[t] = a.gepp ? -1 : a.pos[t];
   for (int r = tid; r < nrows; r += nthr) used[r] = 0;
-  // every launch leaves the counter at a multiple of 256 > G, and no CTA can
-  // pass the first barrier before this one arrives
-  if (tid == 0) ctl->base = ld_acquire_u32(&a.bar->count) & ~255u;
+  if (tid == 0) {
+    // every launch leaves the counter at a multiple of 256 > G, and no CTA
+    // can pass the first barrier before this one arrives
+    ctl->base = ld_acquire_u32(&a.bar->count) & ~255u;
+    ctl->seq0 = a.bar->seq;   // written by the previous launch of this job
+  }
   __syncthreads();
 
   // ---- W = S (Gauss-Jordan start) or S X^{-1} (warm start)
@@ -232,33 +224,40 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
   __syncthreads();
 
   // ---- initial scan
-  Best mine{0ull, kNone, 0};
+  unsigned long long mine = 0ull;
   bool gepp_phase = a.gepp != 0;
   for (int e = tid; e < nrows * l; e += nthr) {
     const int r = e / l, t = e - r * l;
     if (gepp_phase && t != 0) continue;
-    consider(mine, B[e], (int)((row0 + r) * l + t));
+    mine = umax64(mine, cand_word(B[e], (row0 + r) * l + t));
   }
 
   int buf = 0, step = 0, swaps = 0, capped = 0;
-  unsigned int nbar = 0;   // grid barriers of this launch (warp 0)
+  unsigned int dec = 0, nbar = 0;   // decisions and grid barriers of this launch (warp 0)
   for (;;) {
-    mine = warp_reduce_all(mine);
+    mine = warp_max(mine);
     if (lane == 0) red[warp] = mine;
     __syncthreads();
 
     // ---- warp 0: the CTA's candidate, the grid exchange and the decision
     if (warp == 0) {
-      Best win = lane < (nthr >> 5) ? red[lane] : Best{0ull, kNone, 0};
-      win = warp_reduce_all(win);
+      unsigned long long win = warp_max(lane < (nthr >> 5) ? red[lane] : 0ull);
       int kind = kUndecided;
+      const dd* prow = nullptr;   // the winner's row of W
+      bool prow_global = false;
+      const unsigned int s = ctl->seq0 + dec;   // the job's decision number
+      ++dec;
       if (G > 1) {
-        if (lane == 0) a.cand[buf * kMaxGrid + cta] = Cand{win.k, win.idx, win.nf};
-        if (win.idx != kNone) {
-          const int r = (int)(win.idx / l - row0);
-          for (int t = lane; t < l; t += 32)
-            cand_rows[((size_t)buf * kMaxGrid + cta) * l + t] = B[(size_t)r * l + t];
+        // publish this CTA's row, fold its word into the decision's word,
+        // meet the other CTAs, read the maximum
+        const unsigned int own_idx = 0xffffffffu - (unsigned int)win;
+        if (win != 0ull) {
+          const int r = (int)((long long)own_idx / l - row0);
+          dd* rec = cand_rows + ((size_t)buf * kMaxGrid + cta) * l;
+          for (int t = lane; t < l; t += 32) rec[t] = B[(size_t)r * l + t];
         }
+        unsigned long long* word = a.win_ring + (s % kWinRing);
+        if (lane == 0 && win != 0ull) atomicMax(word, win);
         __syncwarp();
         ++nbar;
         int code = kBarOk;
@@ -268,27 +267,49 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
           if (code == kBarTimeout && lane == 0) set_status(a.js, LRA_ETIMEOUT);
           kind = kFailed;
         } else {
-          Best c{0ull, kNone, 0};
-          for (int k = lane; k < G; k += 32) {
-            const Cand* p = a.cand + buf * kMaxGrid + k;
-            merge(c, __ldcg(&p->key), __ldcg(&p->idx), __ldcg(&p->flags));
+          if (lane == 0) {
+            win = __ldcg(word);
+            // every CTA has read the word of decision s - 1 before arriving
+            // here, and the word of decision s + 2 is first written after
+            // the next barrier, which this thread reaches after this store
+            if (cta == 0) a.win_ring[(s + 2) % kWinRing] = 0ull;
           }
-          win = warp_reduce_all(c);
+          win = __shfl_sync(0xffffffffu, win, 0);
+          if (win != 0ull) {
+            const long long widx = 0xffffffffu - (unsigned int)win;
+            prow = cand_rows + ((size_t)buf * kMaxGrid + (widx / l) / rpc) * l;
+            prow_global = true;
+          }
         }
+      } else if (win != 0ull) {
+        prow = B + (size_t)((long long)(0xffffffffu - (unsigned int)win) / l - row0) * l;
       }
-      const double wv = dd_key_value(win.k);
+      auto load = [&](int t) -> dd {
+        if (prow_global) {
+          const float2 v = __ldcg(reinterpret_cast<const float2*>(prow + t));
+          return dd{v.x, v.y};
+        }
+        return prow[t];
+      };
+      const bool none = win == 0ull;
+      const long long widx = none ? -1 : (long long)(0xffffffffu - (unsigned int)win);
+      const long long istar = none ? -1 : widx / l;
+      const int jstar = none ? 0 : (int)(widx - istar * l);
+      dd piv = dd_make(0.0f);
+      if (kind == kUndecided && !none) piv = load(jstar);
+      const double wv = fabs(dd_to_double(piv));
       if (kind == kUndecided) {
-        if (win.nf) {
+        if ((unsigned int)(win >> 32) >= 0x7f800000u) {
           if (cta == 0 && lane == 0) set_status(a.js, LRA_ENONFINITE);
           kind = kFailed;
         } else if (gepp_phase) {
-          if (!(wv > 0.0) || win.idx == kNone) {
+          if (none || !(wv > 0.0)) {
             if (cta == 0 && lane == 0) set_status(a.js, LRA_ESINGULAR);
             kind = kFailed;
           } else {
             kind = LRA_TRACE_GEPP;
           }
-        } else if (win.idx == kNone || wv <= 1.0 + a.delta) {
+        } else if (none || wv <= 1.0 + a.delta) {
           kind = LRA_TRACE_STOP;
         } else if (swaps >= a.max_swaps) {
           kind = LRA_TRACE_CAP;
@@ -296,8 +317,6 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
           kind = LRA_TRACE_SWAP;
         }
       }
-      const long long istar = (win.idx == kNone) ? -1 : win.idx / l;
-      const int jstar = (win.idx == kNone) ? 0 : (int)(win.idx - istar * l);
       if (kind >= 0 && cta == 0 && lane == 0) {
         const int n = a.js->trace_len;
         if (n < a.js->trace_cap) {
@@ -310,17 +329,7 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
         }
       }
       if (kind == LRA_TRACE_GEPP || kind == LRA_TRACE_SWAP) {
-        // pivot row of W and the update's row factor (W[i*, :] - e_j*^T) / W[i*, j*]
-        const dd* prow = (G > 1) ? cand_rows + ((size_t)buf * kMaxGrid + istar / rpc) * l
-                                 : B + (size_t)(istar - row0) * l;
-        auto load = [&](int t) -> dd {
-          if (G > 1) {
-            const float2 v = __ldcg(reinterpret_cast<const float2*>(prow + t));
-            return dd{v.x, v.y};
-          }
-          return prow[t];
-        };
-        const dd piv = load(jstar);
+        // the update's row factor (W[i*, :] - e_j*^T) / W[i*, j*]
         for (int t = lane; t < l; t += 32) {
           dd rt = load(t);
           if (t == jstar) rt = dd_add(rt, dd_make(-1.0f));
@@ -347,39 +356,29 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
     const long long istar = ctl->istar;
     const int jstar = ctl->jstar;
 
-    // ---- fused update + scan for the next decision
+    // ---- fused update + scan for the next decision; the pivot row becomes
+    // e_j* exactly
     const bool next_gepp = gepp_phase && (step + 1 < l);
     const int next_col = step + 1;
-    mine = Best{0ull, kNone, 0};
+    mine = 0ull;
     for (int base = warp * kGpw; base < nrows; base += ngroups) {
       const int r = base + lane / GS;
-      dd* brow = B + (size_t)r * l;
+      const bool act = r < nrows;
+      dd* brow = B + (size_t)(act ? r : 0) * l;
       // the row's entry in column j* is read before its group writes the row
-      const dd c = r < nrows ? brow[jstar] : dd_make(0.0f);
+      const dd c = act ? brow[jstar] : dd_make(0.0f);
       __syncwarp();
-      if (r < nrows) {
-        const long long g = row0 + r;
-        if (g == istar) {
+      const long long g = row0 + r;
+      const bool piv_row = g == istar;
+      const bool scan_row = act && !(next_gepp && used[act ? r : 0]);
 #pragma unroll
-          for (int cc = 0; cc < NC; ++cc) {
-            const int t = gl + GS * cc;
-            if (t < l) {
-              const dd v = dd_make(t == jstar ? 1.0f : 0.0f);
-              brow[t] = v;
-              if (!next_gepp) consider(mine, v, (int)(g * l + t));
-            }
-          }
-        } else {
-          const bool scan_row = !(next_gepp && used[r]);
-#pragma unroll
-          for (int cc = 0; cc < NC; ++cc) {
-            const int t = gl + GS * cc;
-            if (t < l) {
-              const dd v = dd_fnma(c, rvec[t], brow[t]);
-              brow[t] = v;
-              if (scan_row && (!next_gepp || t == next_col)) consider(mine, v, (int)(g * l + t));
-            }
-          }
+      for (int cc = 0; cc < NC; ++cc) {
+        const int t = gl + GS * cc;
+        if (t < l) {
+          dd v = dd_fnma(c, rvec[t], act ? brow[t] : dd_make(0.0f));
+          if (piv_row) v = dd_make(t == jstar ? 1.0f : 0.0f);
+          if (act) brow[t] = v;
+          if (scan_row && (!next_gepp || t == next_col)) mine = umax64(mine, cand_word(v, g * l + t));
         }
       }
     }
@@ -391,9 +390,10 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
     buf ^= 1;
   }
 
-  // ---- epilogue: positions, counters, and the barrier counter rounded up to
-  // a multiple of 256 for the next launch (every CTA has arrived at the last
-  // barrier once CTA 0 passed it)
+  // ---- epilogue: positions, counters, the job's decision counter, and the
+  // barrier counter rounded up to a multiple of 256 for the next launch
+  // (every CTA took the same decisions and has arrived at the last barrier
+  // once CTA 0 passed it)
   if (cta == 0 && tid < l) a.pos[tid] = pos_s[tid];
   if (cta == 0 && tid == 0) {
     a.js->swaps_total += swaps;
@@ -403,6 +403,7 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
     const double upd = (double)(step + swaps) * 2.0 * (double)N * l;
     const double init = a.gepp ? 0.0 : 2.0 * (double)N * l * l;
     a.js->maxvol_flops += upd + init;
+    a.bar->seq = ctl->seq0 + dec;
     const unsigned int pad = (256u - ((nbar * (unsigned)G) & 255u)) & 255u;
     if (pad) atomicAdd(&a.bar->count, pad);
   }
@@ -411,7 +412,7 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
 static size_t maxvol_smem(int rpc, int l, bool stage_xinv) {
   size_t b = (size_t)rpc * l * sizeof(dd) + kMaxL * sizeof(dd) +
              (stage_xinv ? (size_t)l * l * sizeof(dd) : 0) +
-             32 * sizeof(Best) + sizeof(Ctl) + kMaxL * sizeof(int) + (size_t)rpc;
+             32 * sizeof(unsigned long long) + sizeof(Ctl) + kMaxL * sizeof(int) + (size_t)rpc;
   return (b + 15) & ~(size_t)15;
 }
 

@@ -109,19 +109,15 @@ struct BatchArgs {
   JobStatus* js;            // maxvol_flops accumulates the elimination / update FLOPs
 };
 
-// Arrival counter of the maxvol grid barrier (zero for a new job; every
-// maxvol launch leaves it at a multiple of 256).
+// Grid barrier and decision counter of a job's maxvol launches (zero for a
+// new job).  count: arrivals at the grid barrier, left at a multiple of 256
+// by every launch.  seq: decisions taken so far; decision s of the job is
+// exchanged in word s % kWinRing of the job's ring of candidate words.
 struct GridBarrier {
   unsigned int count;
-  unsigned int reserved;
+  unsigned int seq;
 };
-
-// Candidate of one CTA in the grid-wide argmax exchange.
-struct Cand {
-  unsigned long long key;  // bit pattern of |B_ij| (0 with idx = INT_MAX: none)
-  int idx;           // flat index i*l + j in the strip
-  int flags;         // bit 0: a non-finite value was seen
-};
+constexpr int kWinRing = 4;
 
 // IEEE-754 bit pattern of |x| (orders non-negative doubles like their
 // values), computed on the integer pipes.  The raw pattern passes through an

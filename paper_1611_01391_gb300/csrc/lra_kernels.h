@@ -7,7 +7,6 @@ namespace lra {
 
 struct SourceDev;
 struct JobStatus;
-struct Cand;
 struct GridBarrier;
 
 cudaError_t launch_gather_cols(const SourceDev& s, const int* J, int l, float* C,
@@ -30,7 +29,7 @@ struct MaxvolArgs {
   int gepp;
   int* pos;
   const float2* xin;
-  Cand* cand;
+  unsigned long long* win_ring;  // kWinRing candidate words (zero for a new job)
   float2* cand_rows;   // one published row of W per CTA and buffer (pairs)
   GridBarrier* bar;
   JobStatus* js;

@@ -6,7 +6,7 @@
 // process that reserves its memory up front) already owns most of the GPU.
 // lra_maxvol_noalloc lets such callers run the same maxvol kernel as a full
 // solve while passing only their own inputs and outputs.  The kernel's
-// scratch (per-CTA candidate slots and rows, the grid barrier, the status
+// scratch (the candidate words, per-CTA candidate rows, the grid barrier, the status
 // word) lives in a fixed static device array in this file instead of a
 // per-job allocation.
 #include <cuda_runtime.h>
@@ -24,7 +24,7 @@ struct NoAllocScratch {
   GridBarrier bar;
   int trace_i[4];
   double trace_v[1];
-  Cand cand[2 * kMaxGrid];
+  unsigned long long win_ring[kWinRing];
   float2 cand_rows[2 * kMaxGrid * kMaxL];
   float2 xsplit[kMaxL * kMaxL];  // the caller's X^{-1} as FP32 pairs
 };
@@ -70,6 +70,8 @@ __global__ void noalloc_init_kernel(NoAllocScratch* s) {
   s->js.converged = 1;
   s->js.trace_cap = 0;
   s->bar.count = 0;
+  s->bar.seq = 0;
+  for (int i = 0; i < kWinRing; ++i) s->win_ring[i] = 0ull;
 }
 
 __global__ void noalloc_split_kernel(const double* __restrict__ xinv, int ll, NoAllocScratch* s) {
@@ -100,7 +102,7 @@ extern "C" lra_status lra_maxvol_noalloc(const float* strip, int64_t N, int32_t 
   DeviceSetup ds;
   if (setup_device(dev, &ds) != cudaSuccess) return LRA_ECUDA;
   MaxvolPlan plan;
-  // the plan never exceeds 160 CTAs, the number of candidate slots in scratch
+  // the plan never exceeds 160 CTAs, the number of candidate rows in scratch
   if (!plan_maxvol(N, l, ds.sms, ds.smem_optin, &plan)) return LRA_ETOOLARGE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   NoAllocScratch* s = static_cast<NoAllocScratch*>(ds.scratch);
@@ -115,7 +117,7 @@ extern "C" lra_status lra_maxvol_noalloc(const float* strip, int64_t N, int32_t 
   a.gepp = xinv ? 0 : 1;
   a.pos = pos;
   a.xin = xinv ? s->xsplit : nullptr;
-  a.cand = s->cand;
+  a.win_ring = s->win_ring;
   a.cand_rows = s->cand_rows;
   a.bar = &s->bar;
   a.js = &s->js;

@@ -36,7 +36,7 @@ struct Job {
   float2 *xbuf0 = nullptr, *xbuf1 = nullptr;  // cross inverses as FP32 pairs
   float2* cand_rows = nullptr;
   float *C = nullptr, *R = nullptr, *CUq = nullptr;
-  Cand* cand = nullptr;
+  unsigned long long* win_ring = nullptr;
   int n_partials = 0;
   MaxvolPlan plan_col{}, plan_row{};
   cudaEvent_t ev_start = nullptr, ev_end = nullptr;
@@ -174,13 +174,13 @@ size_t layout_bytes(const lra_source* src, const lra_params* p, Job* j) {
   const size_t o_J = L.take(sizeof(int) * l);
   const size_t o_rows = L.take(sizeof(int) * std::max<long long>(q, 1));
   const size_t o_cols = L.take(sizeof(int) * std::max<long long>(s, 1));
+  const size_t o_ring = L.take(sizeof(unsigned long long) * kWinRing);
   const size_t prefix = L.off;
   const size_t o_I = L.take(sizeof(int) * l);
   const size_t o_x0 = L.take(sizeof(float2) * l * l);
   const size_t o_x1 = L.take(sizeof(float2) * l * l);
   const size_t o_U = L.take(sizeof(double) * l * l);
   const size_t o_sig = L.take(sizeof(double) * l);
-  const size_t o_cand = L.take(sizeof(Cand) * 2 * kMaxGrid);
   const size_t o_candr = L.take(sizeof(float2) * 2 * kMaxGrid * l);
   const size_t o_ti = L.take(sizeof(int) * 4 * std::max(p->trace_cap, 1));
   const size_t o_tv = L.take(sizeof(double) * std::max(p->trace_cap, 1));
@@ -201,7 +201,7 @@ size_t layout_bytes(const lra_source* src, const lra_params* p, Job* j) {
     j->xbuf1 = reinterpret_cast<float2*>(b + o_x1);
     j->U = reinterpret_cast<double*>(b + o_U);
     j->sigma = reinterpret_cast<double*>(b + o_sig);
-    j->cand = reinterpret_cast<Cand*>(b + o_cand);
+    j->win_ring = reinterpret_cast<unsigned long long*>(b + o_ring);
     j->cand_rows = reinterpret_cast<float2*>(b + o_candr);
     j->trace_i = reinterpret_cast<int*>(b + o_ti);
     j->trace_v = reinterpret_cast<double*>(b + o_tv);
@@ -253,7 +253,8 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
   init.status = LRA_OK;
   init.converged = 1;
   init.trace_cap = j->trace_cap;
-  // status, barrier, J and the residual sample: staged in the slot's pinned
+  // status, grid barrier, J, the residual sample and the zeroed maxvol
+  // candidate words: staged in the slot's pinned
   // buffer (free again only once this job is released) and sent in one copy
   if (ctx->stage_cap[j->slot] < j->prefix) {
     if (ctx->stage[j->slot]) cudaFreeHost(ctx->stage[j->slot]);
@@ -276,7 +277,7 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
   if ((e = cudaMemcpyAsync(j->dmem, hs, j->prefix, cudaMemcpyHostToDevice, st))) return e;
   MaxvolArgs col{};
   col.strip = j->C; col.N = j->m; col.l = j->l; col.si = j->l; col.st = 1;
-  col.pos = j->I; col.cand = j->cand; col.cand_rows = j->cand_rows; col.bar = j->bar;
+  col.pos = j->I; col.win_ring = j->win_ring; col.cand_rows = j->cand_rows; col.bar = j->bar;
   col.js = j->js; col.trace_i = j->trace_i; col.trace_v = j->trace_v;
   col.delta = j->delta; col.max_swaps = j->max_swaps;
   MaxvolArgs row = col;
