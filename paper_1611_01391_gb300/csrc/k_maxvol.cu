@@ -41,7 +41,7 @@
 
 namespace lra {
 
-constexpr int kMaxvolThreads = 512;
+constexpr int kMaxvolThreads = 1024;
 
 // Candidates are compared on one unsigned 64-bit word: the FP32 bit pattern
 // of |hi| (non-negative FP32 patterns order like their values as unsigned
@@ -82,13 +82,12 @@ enum { kBarOk = 0, kBarTimeout = 1, kBarStatus = 2 };
 // Grid-wide barrier of a cooperative launch on a counter that only grows:
 // the n-th barrier of a launch waits until the counter reaches base + n G.
 // Called by one thread, after a warp or block barrier that orders its CTA's
-// writes before it; the fence publishes them, the acquire loads order the
-// reads after it.  The wait ends early when the job's status leaves LRA_OK
+// writes before it; the arrival is a release add (it publishes them), the
+// polls are acquire loads (they order the reads after it).  The wait ends early when the job's status leaves LRA_OK
 // (a cancellation, a failure in another CTA) or after 2 s.
 __device__ __forceinline__ int grid_arrive_wait(unsigned int* count, unsigned int target,
                                                 const int* status) {
-  __threadfence();
-  atomicAdd(count, 1u);
+  asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
   const unsigned long long t0 = globaltimer_ns();
   for (unsigned int it = 1;; ++it) {
     if ((int)(ld_acquire_u32(count) - target) >= 0) return kBarOk;
@@ -125,15 +124,19 @@ __device__ __forceinline__ void warm_rows(const MaxvolArgs& a, dd* B, int nrows,
       }
     __syncwarp();
     dacc acc[NC];
+    int qc[NC];   // the lane's columns, as stored in X
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = dacc{0.0f, 0.0f};
+    for (int c = 0; c < NC; ++c) {
+      acc[c] = dacc{0.0f, 0.0f};
+      qc[c] = X.col(min(gl + GS * c, l - 1));
+    }
     if (active) {
       for (int p = 0; p < l; ++p) {
         const float sp = brow[p].hi;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           const int q = gl + GS * c;
-          if (q < l) acc_fma_f(acc[c], sp, X[(size_t)p * l + q]);
+          if (q < l) acc_fma_f(acc[c], sp, X.at((size_t)p * l + qc[c]));
         }
       }
     }
@@ -147,18 +150,122 @@ __device__ __forceinline__ void warm_rows(const MaxvolArgs& a, dd* B, int nrows,
   }
 }
 
+// X^{-1} accessors: col(q) is where column q of X^{-1} is stored, at(i)
+// the entry at row-major position i.
 struct SharedX {
   const dd* p;
-  __device__ __forceinline__ dd operator[](size_t i) const { return p[i]; }
+  __device__ __forceinline__ int col(int q) const { return q; }
+  __device__ __forceinline__ dd at(size_t i) const { return p[i]; }
+};
+
+struct SharedXMapped {  // the in-kernel inverse: column q of X^{-1} is column map[q]
+  const dd* p;
+  const int* map;
+  __device__ __forceinline__ int col(int q) const { return map[q]; }
+  __device__ __forceinline__ dd at(size_t i) const { return p[i]; }
 };
 
 struct GlobalX {  // read-only path for an X^{-1} that does not fit on chip
   const float2* p;
-  __device__ __forceinline__ dd operator[](size_t i) const {
+  __device__ __forceinline__ int col(int q) const { return q; }
+  __device__ __forceinline__ dd at(size_t i) const {
     const float2 v = __ldg(p + i);
     return dd{v.x, v.y};
   }
 };
+
+// Scratch of the in-kernel cross inverse (shared memory).
+struct InvScratch {
+  dd* rowt;                 // pivot row scaled by 1 / pivot (l)
+  dd* colt;                 // column t before the step, after the interchange (l)
+  dd* rowold;               // row t before the step (l)
+  unsigned long long* pkey; // the next pivot's word, two steps deep
+  int* swaps;               // pivot row of each step (l)
+  int* at;                  // column map of the result (l)
+  int* p_s;
+};
+
+__device__ __forceinline__ unsigned long long pivot_word(dd v, int r) {
+  return ((unsigned long long)(__float_as_uint(v.hi) & 0x7fffffffu) << 32) | (0xffffffffu - (unsigned int)r);
+}
+
+// Inverse of the cross X = S[pos, :] in double-float pairs, by every CTA of
+// the launch for itself (no separate launch, no exchange): in-place
+// Gauss-Jordan elimination with partial pivoting on the rows (the pivot of
+// step t+1 is found by a shared atomic max while step t updates column t+1;
+// |hi| rounded to FP32 orders the candidates, ties to the smaller row).  A
+// step interchanges rows t and p, scales the pivot row by 1/pivot and
+// subtracts its multiples from every other row, column t taking the place
+// of the eliminated unit column; the interchanges are undone at the end as
+// a column map (X^{-1}[:, q] = A[:, at[q]]).  Returns false, with the job's
+// status set by CTA 0, on a non-finite or singular cross.
+__device__ bool invert_cross(const MaxvolArgs& a, const int* pos, dd* A, const InvScratch& w) {
+  const int l = a.l, ll = l * l;
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
+  if (tid < 2) w.pkey[tid] = 0ull;
+  __syncthreads();
+  int bad = 0;
+  for (int e = tid; e < ll; e += nthr) {
+    const int r = e / l, c = e - r * l;
+    const dd v = dd_make(a.strip[(long long)pos[r] * a.si + (long long)c * a.st]);
+    if (!(fabsf(v.hi) <= FLT_MAX)) bad = 1;
+    A[e] = v;
+    if (c == 0) atomicMax(w.pkey, pivot_word(v, r));
+  }
+  if (__syncthreads_or(bad)) {
+    if (blockIdx.x == 0 && tid == 0) set_status(a.js, LRA_ENONFINITE);
+    return false;
+  }
+  for (int t = 0; t < l; ++t) {
+    if (tid < 32) {
+      const unsigned long long key = w.pkey[t & 1];
+      const int p = (key >> 32) != 0ull ? (int)(0xffffffffu - (unsigned int)key) : -1;
+      if (p >= 0) {
+        const dd rp = dd_div(dd_make(1.0f), A[p * l + t]);
+        for (int c = lane; c < l; c += 32) {
+          w.rowt[c] = (c == t) ? rp : dd_mul(A[p * l + c], rp);
+          w.rowold[c] = A[t * l + c];
+          w.colt[c] = A[(c == p ? t : c) * l + t];
+        }
+      }
+      if (lane == 0) {
+        *w.p_s = p;
+        w.swaps[t] = p;
+        w.pkey[(t + 1) & 1] = 0ull;
+      }
+    }
+    __syncthreads();
+    const int p = *w.p_s;
+    if (p < 0) {
+      if (blockIdx.x == 0 && tid == 0) set_status(a.js, LRA_ESINGULAR);
+      return false;
+    }
+    for (int e = tid; e < ll; e += nthr) {
+      const int r = e / l, c = e - r * l;
+      dd v;
+      if (r == t) {
+        v = w.rowt[c];
+      } else {
+        // row r after the interchange is row t before it when r == p
+        const dd av = (c == t) ? dd_make(0.0f) : (r == p ? w.rowold[c] : A[e]);
+        v = dd_fnma(w.colt[r], w.rowt[c], av);
+      }
+      A[e] = v;
+      if (c == t + 1 && r > t) atomicMax(&w.pkey[(t + 1) & 1], pivot_word(v, r));
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    for (int q = 0; q < l; ++q) w.at[q] = q;
+    for (int t = l - 1; t >= 0; --t) {
+      const int p = w.swaps[t], x = w.at[t];
+      w.at[t] = w.at[p];
+      w.at[p] = x;
+    }
+  }
+  __syncthreads();
+  return true;
+}
 
 template <int GS, int NC>
 __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a) {
@@ -175,10 +282,19 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
   dd* B = reinterpret_cast<dd*>(smem_raw);                   // rpc * l
   dd* rvec = B + (size_t)rpc * l;                             // l: the update's row factor
   dd* xs = rvec + kMaxL;                                      // l*l when staged
-  unsigned long long* red = reinterpret_cast<unsigned long long*>(xs + (a.stage_xinv ? (size_t)l * l : 0));  // 32
-  Ctl* ctl = reinterpret_cast<Ctl*>(red + 32);
+  // the CTA's best word of the current and the next decision (shared atomic max)
+  unsigned long long* red = reinterpret_cast<unsigned long long*>(xs + (a.stage_xinv ? (size_t)l * l : 0));
+  Ctl* ctl = reinterpret_cast<Ctl*>(red + 2);
   int* pos_s = reinterpret_cast<int*>(ctl + 1);              // l
-  unsigned char* used = reinterpret_cast<unsigned char*>(pos_s + kMaxL);  // rpc
+  InvScratch inv;                                            // the in-kernel inverse
+  inv.rowt = rvec;
+  inv.colt = reinterpret_cast<dd*>(pos_s + kMaxL);
+  inv.rowold = inv.colt + kMaxL;
+  inv.pkey = reinterpret_cast<unsigned long long*>(inv.rowold + kMaxL);
+  inv.swaps = reinterpret_cast<int*>(inv.pkey + 2);
+  inv.at = inv.swaps + kMaxL;
+  inv.p_s = inv.at + kMaxL;
+  unsigned char* used = reinterpret_cast<unsigned char*>(inv.p_s + 2);  // rpc
   dd* cand_rows = reinterpret_cast<dd*>(a.cand_rows);
 
   const int lane = tid & 31, warp = tid >> 5;
@@ -188,6 +304,7 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
 
   for (int t = tid; t < l; t += nthr) pos_s[t] = a.gepp ? -1 : a.pos[t];
   for (int r = tid; r < nrows; r += nthr) used[r] = 0;
+  if (tid < 2) red[tid] = 0ull;
   if (tid == 0) {
     // every launch leaves the counter at a multiple of 256 > G, and no CTA
     // can pass the first barrier before this one arrives
@@ -203,7 +320,10 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
       B[e] = dd_make(a.strip[(row0 + r) * a.si + (long long)t * a.st]);
     }
   } else {
-    if (a.stage_xinv) {
+    if (a.self_inverse) {
+      if (!invert_cross(a, pos_s, xs, inv)) return;
+      warm_rows<GS, NC>(a, B, nrows, row0, SharedXMapped{xs, inv.at});
+    } else if (a.stage_xinv) {
       for (int e = tid; e < l * l; e += nthr) {
         const float2 v = a.xin[e];
         xs[e] = dd{v.x, v.y};
@@ -233,20 +353,20 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
   }
 
   int buf = 0, step = 0, swaps = 0, capped = 0;
-  unsigned int dec = 0, nbar = 0;   // decisions and grid barriers of this launch (warp 0)
+  unsigned int dec = 0, nbar = 0;   // decisions (all threads) and grid barriers (warp 0) of this launch
   for (;;) {
     mine = warp_max(mine);
-    if (lane == 0) red[warp] = mine;
+    if (lane == 0) atomicMax(red + (dec & 1u), mine);
     __syncthreads();
 
     // ---- warp 0: the CTA's candidate, the grid exchange and the decision
     if (warp == 0) {
-      unsigned long long win = warp_max(lane < (nthr >> 5) ? red[lane] : 0ull);
+      unsigned long long win = red[dec & 1u];
+      if (lane == 0) red[(dec + 1u) & 1u] = 0ull;   // the next decision's word
       int kind = kUndecided;
       const dd* prow = nullptr;   // the winner's row of W
       bool prow_global = false;
       const unsigned int s = ctl->seq0 + dec;   // the job's decision number
-      ++dec;
       if (G > 1) {
         // publish this CTA's row, fold its word into the decision's word,
         // meet the other CTAs, read the maximum
@@ -295,8 +415,17 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
       const long long widx = none ? -1 : (long long)(0xffffffffu - (unsigned int)win);
       const long long istar = none ? -1 : widx / l;
       const int jstar = none ? 0 : (int)(widx - istar * l);
+      // the pivot and this lane's entries of the winner's row, issued together
       dd piv = dd_make(0.0f);
-      if (kind == kUndecided && !none) piv = load(jstar);
+      dd rown[kMaxL / 32];
+#pragma unroll
+      for (int u = 0; u < kMaxL / 32; ++u) rown[u] = dd_make(0.0f);
+      if (kind == kUndecided && !none) {
+        piv = load(jstar);
+#pragma unroll
+        for (int u = 0; u < kMaxL / 32; ++u)
+          if (lane + 32 * u < l) rown[u] = load(lane + 32 * u);
+      }
       const double wv = fabs(dd_to_double(piv));
       if (kind == kUndecided) {
         if ((unsigned int)(win >> 32) >= 0x7f800000u) {
@@ -330,10 +459,14 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
       }
       if (kind == LRA_TRACE_GEPP || kind == LRA_TRACE_SWAP) {
         // the update's row factor (W[i*, :] - e_j*^T) / W[i*, j*]
-        for (int t = lane; t < l; t += 32) {
-          dd rt = load(t);
-          if (t == jstar) rt = dd_add(rt, dd_make(-1.0f));
-          rvec[t] = dd_div(rt, piv);
+#pragma unroll
+        for (int u = 0; u < kMaxL / 32; ++u) {
+          const int t = lane + 32 * u;
+          if (t < l) {
+            dd rt = rown[u];
+            if (t == jstar) rt = dd_add(rt, dd_make(-1.0f));
+            rvec[t] = dd_div(rt, piv);
+          }
         }
         if (lane == 0) {
           if (gepp_phase && istar >= row0 && istar < row0 + nrows) used[istar - row0] = 1;
@@ -388,6 +521,7 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
       ++swaps;
     }
     buf ^= 1;
+    ++dec;
   }
 
   // ---- epilogue: positions, counters, the job's decision counter, and the
@@ -403,7 +537,7 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
     const double upd = (double)(step + swaps) * 2.0 * (double)N * l;
     const double init = a.gepp ? 0.0 : 2.0 * (double)N * l * l;
     a.js->maxvol_flops += upd + init;
-    a.bar->seq = ctl->seq0 + dec;
+    a.bar->seq = ctl->seq0 + dec + 1;   // the decisions taken, the final stop included
     const unsigned int pad = (256u - ((nbar * (unsigned)G) & 255u)) & 255u;
     if (pad) atomicAdd(&a.bar->count, pad);
   }
@@ -412,7 +546,9 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
 static size_t maxvol_smem(int rpc, int l, bool stage_xinv) {
   size_t b = (size_t)rpc * l * sizeof(dd) + kMaxL * sizeof(dd) +
              (stage_xinv ? (size_t)l * l * sizeof(dd) : 0) +
-             32 * sizeof(unsigned long long) + sizeof(Ctl) + kMaxL * sizeof(int) + (size_t)rpc;
+             2 * sizeof(unsigned long long) + sizeof(Ctl) + kMaxL * sizeof(int) +
+             2 * kMaxL * sizeof(dd) + 2 * sizeof(unsigned long long) + (2 * kMaxL + 2) * sizeof(int) +
+             (size_t)rpc;
   return (b + 15) & ~(size_t)15;
 }
 
@@ -462,6 +598,7 @@ static cudaError_t launch_nc(MaxvolArgs& a, const MaxvolPlan& plan, cudaStream_t
 }
 
 cudaError_t launch_maxvol(MaxvolArgs a, const MaxvolPlan& plan, cudaStream_t st) {
+  if (a.self_inverse && !plan.stage_xinv) return cudaErrorInvalidValue;  // no room for X^{-1}
   a.rows_per_cta = plan.rows_per_cta;
   a.stage_xinv = plan.stage_xinv;
   if (a.l <= 24) return launch_nc<8>(a, plan, st);

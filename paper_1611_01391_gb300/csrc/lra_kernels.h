@@ -40,6 +40,8 @@ struct MaxvolArgs {
   int max_swaps;
   int rows_per_cta;
   int stage_xinv;   // copy X^{-1} into shared memory for the warm start
+  int self_inverse; // warm start: every CTA inverts S[pos, :] itself (xin unused);
+                    // needs a plan with stage_xinv
 };
 
 struct MaxvolPlan {

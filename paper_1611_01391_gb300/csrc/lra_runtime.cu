@@ -295,15 +295,21 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
     return cudaEventRecord(ev, st);
   };
   // with several own streams the jobs overlap: the single-SM inverse then
-  // leaves the other SMs to them
+  // leaves the other SMs to them.  With one stream the cross inverse is on
+  // the critical path of the job: the maxvol grid computes it itself when it
+  // fits on chip beside the strip (no separate launch).
   const bool one_sm = ctx->streams.size() > 1;
+  const bool self_col = !one_sm && j->plan_col.stage_xinv;
+  const bool self_row = !one_sm && j->plan_row.stage_xinv;
+  col.self_inverse = self_col;
+  row.self_inverse = self_row;
   if ((e = cudaEventRecord(j->ev_start, st))) return e;
   for (int sw = 0; sw < j->sweeps; ++sw) {
     if ((e = launch_gather_cols(j->src, j->J, j->l, j->C, j->js, 1, ctx->sms, st)) || (e = after(kClsGather, 1))) return e;
     col.gepp = (sw == 0);
     col.half_step = 2 * sw;
     col.xin = j->xbuf0;   // inverse of A[I, J] (vertical strip's cross)
-    if (!col.gepp) {
+    if (!col.gepp && !self_col) {
       if ((e = launch_cross_inverse(j->C, j->l, 1, j->I, j->l, j->xbuf0, j->js, st, one_sm)) ||
           (e = after(kClsInverse, 1))) return e;
     }
@@ -312,8 +318,8 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
     row.gepp = 0;
     row.half_step = 2 * sw + 1;
     row.xin = j->xbuf1;   // inverse of A[I, J]^T (horizontal strip's cross)
-    if ((e = launch_cross_inverse(j->R, 1, j->n, j->J, j->l, j->xbuf1, j->js, st, one_sm)) ||
-        (e = after(kClsInverse, 1))) return e;
+    if (!self_row && ((e = launch_cross_inverse(j->R, 1, j->n, j->J, j->l, j->xbuf1, j->js, st, one_sm)) ||
+                      (e = after(kClsInverse, 1)))) return e;
     if ((e = launch_maxvol(row, j->plan_row, st)) || (e = after(kClsMaxvol, 1))) return e;
     if ((e = launch_sweep_done(j->js, st)) || (e = after(kClsOther, 1))) return e;
     if (j->tol > 0.0 && sw + 1 < j->sweeps) {
