@@ -36,6 +36,7 @@
 #include <cfloat>
 
 #include "dd_arith.cuh"
+#include "inverse_dd.cuh"
 #include "lra_kernels.h"
 #include "lra_internal.cuh"
 
@@ -174,100 +175,9 @@ struct GlobalX {  // read-only path for an X^{-1} that does not fit on chip
   }
 };
 
-// Scratch of the in-kernel cross inverse (shared memory).
-struct InvScratch {
-  dd* rowt;                 // pivot row scaled by 1 / pivot (l)
-  dd* colt;                 // column t before the step, after the interchange (l)
-  dd* rowold;               // row t before the step (l)
-  unsigned long long* pkey; // the next pivot's word, two steps deep
-  int* swaps;               // pivot row of each step (l)
-  int* at;                  // column map of the result (l)
-  int* p_s;
-};
-
-__device__ __forceinline__ unsigned long long pivot_word(dd v, int r) {
-  return ((unsigned long long)(__float_as_uint(v.hi) & 0x7fffffffu) << 32) | (0xffffffffu - (unsigned int)r);
-}
-
-// Inverse of the cross X = S[pos, :] in double-float pairs, by every CTA of
-// the launch for itself (no separate launch, no exchange): in-place
-// Gauss-Jordan elimination with partial pivoting on the rows (the pivot of
-// step t+1 is found by a shared atomic max while step t updates column t+1;
-// |hi| rounded to FP32 orders the candidates, ties to the smaller row).  A
-// step interchanges rows t and p, scales the pivot row by 1/pivot and
-// subtracts its multiples from every other row, column t taking the place
-// of the eliminated unit column; the interchanges are undone at the end as
-// a column map (X^{-1}[:, q] = A[:, at[q]]).  Returns false, with the job's
-// status set by CTA 0, on a non-finite or singular cross.
-__device__ bool invert_cross(const MaxvolArgs& a, const int* pos, dd* A, const InvScratch& w) {
-  const int l = a.l, ll = l * l;
-  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
-  if (tid < 2) w.pkey[tid] = 0ull;
-  __syncthreads();
-  int bad = 0;
-  for (int e = tid; e < ll; e += nthr) {
-    const int r = e / l, c = e - r * l;
-    const dd v = dd_make(a.strip[(long long)pos[r] * a.si + (long long)c * a.st]);
-    if (!(fabsf(v.hi) <= FLT_MAX)) bad = 1;
-    A[e] = v;
-    if (c == 0) atomicMax(w.pkey, pivot_word(v, r));
-  }
-  if (__syncthreads_or(bad)) {
-    if (blockIdx.x == 0 && tid == 0) set_status(a.js, LRA_ENONFINITE);
-    return false;
-  }
-  for (int t = 0; t < l; ++t) {
-    if (tid < 32) {
-      const unsigned long long key = w.pkey[t & 1];
-      const int p = (key >> 32) != 0ull ? (int)(0xffffffffu - (unsigned int)key) : -1;
-      if (p >= 0) {
-        const dd rp = dd_div(dd_make(1.0f), A[p * l + t]);
-        for (int c = lane; c < l; c += 32) {
-          w.rowt[c] = (c == t) ? rp : dd_mul(A[p * l + c], rp);
-          w.rowold[c] = A[t * l + c];
-          w.colt[c] = A[(c == p ? t : c) * l + t];
-        }
-      }
-      if (lane == 0) {
-        *w.p_s = p;
-        w.swaps[t] = p;
-        w.pkey[(t + 1) & 1] = 0ull;
-      }
-    }
-    __syncthreads();
-    const int p = *w.p_s;
-    if (p < 0) {
-      if (blockIdx.x == 0 && tid == 0) set_status(a.js, LRA_ESINGULAR);
-      return false;
-    }
-    for (int e = tid; e < ll; e += nthr) {
-      const int r = e / l, c = e - r * l;
-      dd v;
-      if (r == t) {
-        v = w.rowt[c];
-      } else {
-        // row r after the interchange is row t before it when r == p
-        const dd av = (c == t) ? dd_make(0.0f) : (r == p ? w.rowold[c] : A[e]);
-        v = dd_fnma(w.colt[r], w.rowt[c], av);
-      }
-      A[e] = v;
-      if (c == t + 1 && r > t) atomicMax(&w.pkey[(t + 1) & 1], pivot_word(v, r));
-    }
-    __syncthreads();
-  }
-  if (tid == 0) {
-    for (int q = 0; q < l; ++q) w.at[q] = q;
-    for (int t = l - 1; t >= 0; --t) {
-      const int p = w.swaps[t], x = w.at[t];
-      w.at[t] = w.at[p];
-      w.at[p] = x;
-    }
-  }
-  __syncthreads();
-  return true;
-}
-
-template <int GS, int NC>
+// kSelf: the warm start inverts the cross itself (a separate instantiation,
+// so that launches without it keep their own register allocation).
+template <int GS, int NC, bool kSelf>
 __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a) {
   if (a.js->status != LRA_OK || a.js->stop) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -320,8 +230,8 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
       B[e] = dd_make(a.strip[(row0 + r) * a.si + (long long)t * a.st]);
     }
   } else {
-    if (a.self_inverse) {
-      if (!invert_cross(a, pos_s, xs, inv)) return;
+    if constexpr (kSelf) {
+      if (!invert_cross<kMaxvolThreads>(a.strip, a.si, a.st, l, a.js, pos_s, xs, inv)) return;
       warm_rows<GS, NC>(a, B, nrows, row0, SharedXMapped{xs, inv.at});
     } else if (a.stage_xinv) {
       for (int e = tid; e < l * l; e += nthr) {
@@ -579,11 +489,12 @@ bool plan_maxvol(long long N, int l, int sms, size_t smem_limit, MaxvolPlan* pla
 
 template <int GS, int NC>
 static cudaError_t launch_gs(MaxvolArgs& a, const MaxvolPlan& plan, cudaStream_t st) {
-  const cudaError_t e = smem_optin(reinterpret_cast<const void*>(maxvol_kernel<GS, NC>), 227 * 1024);
+  const void* k = (a.self_inverse && !a.gepp) ? reinterpret_cast<const void*>(maxvol_kernel<GS, NC, true>)
+                                              : reinterpret_cast<const void*>(maxvol_kernel<GS, NC, false>);
+  const cudaError_t e = smem_optin(k, 227 * 1024);
   if (e != cudaSuccess) return e;
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(maxvol_kernel<GS, NC>),
-                                     dim3(plan.grid), dim3(plan.threads), args, plan.smem, st);
+  return cudaLaunchCooperativeKernel(k, dim3(plan.grid), dim3(plan.threads), args, plan.smem, st);
 }
 
 // Lanes per row group: 8 for l <= 24 (4 rows per warp), 16 for l <= 48,

@@ -57,11 +57,10 @@ struct MaxvolPlan {
 bool plan_maxvol(long long N, int l, int sms, size_t smem_limit, MaxvolPlan* plan);
 cudaError_t launch_maxvol(MaxvolArgs a, const MaxvolPlan& plan, cudaStream_t st);
 
-// Inverse of the cross S[pos, :] of a strip (FP64 Gauss-Jordan with partial
-// pivoting), row-major into xinv as FP32 pairs (split_double).
+// Inverse of the cross S[pos, :] of a strip (double-float Gauss-Jordan with
+// partial pivoting on one CTA), row-major into xinv as FP32 pairs.
 cudaError_t launch_cross_inverse(const float* strip, long long si, long long st, const int* pos,
-                                 int l, float2* xinv, JobStatus* js, cudaStream_t stream,
-                                 bool one_sm);
+                                 int l, float2* xinv, JobStatus* js, cudaStream_t stream);
 
 // Nucleus of the final cross X = C[I, :] (one CTA, FP64 one-sided Jacobi SVD).
 cudaError_t launch_nucleus(const float* C, const int* I, int l, int k, double rank_tol,

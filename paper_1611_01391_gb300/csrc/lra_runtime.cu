@@ -294,10 +294,10 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
     j->prof.emplace_back(cls, ev);
     return cudaEventRecord(ev, st);
   };
-  // with several own streams the jobs overlap: the single-SM inverse then
-  // leaves the other SMs to them.  With one stream the cross inverse is on
-  // the critical path of the job: the maxvol grid computes it itself when it
-  // fits on chip beside the strip (no separate launch).
+  // with several own streams the jobs overlap: the separate single-SM
+  // inverse then leaves the other SMs to them.  With one stream the cross
+  // inverse is on the critical path of the job: the maxvol grid computes it
+  // itself when it fits on chip beside the strip (no separate launch).
   const bool one_sm = ctx->streams.size() > 1;
   const bool self_col = !one_sm && j->plan_col.stage_xinv;
   const bool self_row = !one_sm && j->plan_row.stage_xinv;
@@ -310,7 +310,7 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
     col.half_step = 2 * sw;
     col.xin = j->xbuf0;   // inverse of A[I, J] (vertical strip's cross)
     if (!col.gepp && !self_col) {
-      if ((e = launch_cross_inverse(j->C, j->l, 1, j->I, j->l, j->xbuf0, j->js, st, one_sm)) ||
+      if ((e = launch_cross_inverse(j->C, j->l, 1, j->I, j->l, j->xbuf0, j->js, st)) ||
           (e = after(kClsInverse, 1))) return e;
     }
     if ((e = launch_maxvol(col, j->plan_col, st)) || (e = after(kClsMaxvol, 1))) return e;
@@ -318,7 +318,7 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
     row.gepp = 0;
     row.half_step = 2 * sw + 1;
     row.xin = j->xbuf1;   // inverse of A[I, J]^T (horizontal strip's cross)
-    if (!self_row && ((e = launch_cross_inverse(j->R, 1, j->n, j->J, j->l, j->xbuf1, j->js, st, one_sm)) ||
+    if (!self_row && ((e = launch_cross_inverse(j->R, 1, j->n, j->J, j->l, j->xbuf1, j->js, st)) ||
                       (e = after(kClsInverse, 1)))) return e;
     if ((e = launch_maxvol(row, j->plan_row, st)) || (e = after(kClsMaxvol, 1))) return e;
     if ((e = launch_sweep_done(j->js, st)) || (e = after(kClsOther, 1))) return e;
