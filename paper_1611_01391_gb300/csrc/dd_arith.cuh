@@ -13,7 +13,7 @@
 
 namespace lra {
 
-struct dd {
+struct __align__(8) dd {  // 8-byte aligned: one 64-bit access per pair
   float hi, lo;
 };
 

@@ -101,7 +101,9 @@ __device__ __forceinline__ int grid_arrive_wait(unsigned int* count, unsigned in
 
 // Warm start of the rows of this CTA: W[r, :] = S[g, :] X^{-1}, each entry a
 // compensated dot product (Dot2) of the exact FP32 strip row with the pairs
-// of X^{-1}.  A group of GS lanes owns a row; lane gl computes columns
+// of X^{-1}; for rows of 8 lanes (l <= 24) as two interleaved sums (even
+// and odd terms: two independent dependency chains) added at the end, which
+// measured faster there and slower for wider rows.  A group of GS lanes owns a row; lane gl computes columns
 // gl + GS c, c < NC, so every issued instruction is useful work
 // (NC = ceil(l / GS) exactly).
 template <int GS, int NC, typename XPtr>
@@ -132,12 +134,40 @@ __device__ __forceinline__ void warm_rows(const MaxvolArgs& a, dd* B, int nrows,
       qc[c] = X.col(min(gl + GS * c, l - 1));
     }
     if (active) {
-      for (int p = 0; p < l; ++p) {
-        const float sp = brow[p].hi;
+      if constexpr (GS == 8) {
+        dacc acc2[NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          const int q = gl + GS * c;
-          if (q < l) acc_fma_f(acc[c], sp, X.at((size_t)p * l + qc[c]));
+        for (int c = 0; c < NC; ++c) acc2[c] = dacc{0.0f, 0.0f};
+        int p = 0;
+        for (; p + 1 < l; p += 2) {
+          const float sp = brow[p].hi, sq = brow[p + 1].hi;
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            const int q = gl + GS * c;
+            if (q < l) {
+              acc_fma_f(acc[c], sp, X.at((size_t)p * l + qc[c]));
+              acc_fma_f(acc2[c], sq, X.at((size_t)(p + 1) * l + qc[c]));
+            }
+          }
+        }
+        if (p < l) {
+          const float sp = brow[p].hi;
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            const int q = gl + GS * c;
+            if (q < l) acc_fma_f(acc[c], sp, X.at((size_t)p * l + qc[c]));
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = acc_add(acc[c], acc2[c]);
+      } else {
+        for (int p = 0; p < l; ++p) {
+          const float sp = brow[p].hi;
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            const int q = gl + GS * c;
+            if (q < l) acc_fma_f(acc[c], sp, X.at((size_t)p * l + qc[c]));
+          }
         }
       }
     }
