@@ -477,6 +477,7 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
     const double upd = (double)(step + swaps) * 2.0 * (double)N * l;
     const double init = a.gepp ? 0.0 : 2.0 * (double)N * l * l;
     a.js->maxvol_flops += upd + init;
+    if (a.count_sweep) a.js->sweeps_done += 1;
     a.bar->seq = ctl->seq0 + dec + 1;   // the decisions taken, the final stop included
     const unsigned int pad = (256u - ((nbar * (unsigned)G) & 255u)) & 255u;
     if (pad) atomicAdd(&a.bar->count, pad);

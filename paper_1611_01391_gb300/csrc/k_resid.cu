@@ -162,17 +162,8 @@ cudaError_t launch_sampled_residual(const SourceDev& s, const int* rows, int q, 
   return cudaGetLastError();
 }
 
-__global__ void sweep_done_kernel(JobStatus* js) {
-  if (js->status == LRA_OK && !js->stop) js->sweeps_done += 1;
-}
-
 __global__ void tol_check_kernel(JobStatus* js, double tol) {
   if (js->status == LRA_OK && js->est_rel <= tol) js->stop = 1;
-}
-
-cudaError_t launch_sweep_done(JobStatus* js, cudaStream_t st) {
-  sweep_done_kernel<<<1, 1, 0, st>>>(js);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_tol_check(JobStatus* js, double tol, cudaStream_t st) {

@@ -42,6 +42,7 @@ struct MaxvolArgs {
   int stage_xinv;   // copy X^{-1} into shared memory for the warm start
   int self_inverse; // warm start: every CTA inverts S[pos, :] itself (xin unused);
                     // needs a plan with stage_xinv
+  int count_sweep;  // the last half-step of a sweep: count it in js->sweeps_done
 };
 
 struct MaxvolPlan {
@@ -91,7 +92,6 @@ size_t batch_smem_bytes();
 cudaError_t launch_batch(const BatchArgs& a, int sms, cudaStream_t st);
 
 // Small control kernels.
-cudaError_t launch_sweep_done(JobStatus* js, cudaStream_t st);
 cudaError_t launch_tol_check(JobStatus* js, double tol, cudaStream_t st);
 
 }  // namespace lra

@@ -320,8 +320,8 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
     row.xin = j->xbuf1;   // inverse of A[I, J]^T (horizontal strip's cross)
     if (!self_row && ((e = launch_cross_inverse(j->R, 1, j->n, j->J, j->l, j->xbuf1, j->js, st)) ||
                       (e = after(kClsInverse, 1)))) return e;
+    row.count_sweep = 1;   // the sweep is counted by the row maxvol that completes it
     if ((e = launch_maxvol(row, j->plan_row, st)) || (e = after(kClsMaxvol, 1))) return e;
-    if ((e = launch_sweep_done(j->js, st)) || (e = after(kClsOther, 1))) return e;
     if (j->tol > 0.0 && sw + 1 < j->sweeps) {
       if ((e = launch_gather_cols(j->src, j->J, j->l, j->C, j->js, 1, ctx->sms, st)) || (e = after(kClsGather, 1))) return e;
       if ((e = launch_nucleus(j->C, j->I, j->l, j->k, j->rank_tol, j->U, j->sigma, j->js, st)) || (e = after(kClsCross, 1))) return e;
