@@ -107,9 +107,8 @@ __device__ __forceinline__ int grid_arrive_wait(unsigned int* count, unsigned in
 // gl + GS c, c < NC, so every issued instruction is useful work
 // (NC = ceil(l / GS) exactly).
 template <int GS, int NC, typename XPtr>
-__device__ __forceinline__ void warm_rows(const MaxvolArgs& a, dd* B, int nrows, long long row0,
+__device__ __forceinline__ void warm_rows(const MaxvolArgs& a, const int l, dd* B, int nrows, long long row0,
                                           XPtr X) {
-  const int l = a.l;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   constexpr int kGpw = 32 / GS;
   const int gl = lane % GS;
@@ -207,11 +206,13 @@ struct GlobalX {  // read-only path for an X^{-1} that does not fit on chip
 
 // kSelf: the warm start inverts the cross itself (a separate instantiation,
 // so that launches without it keep their own register allocation).
-template <int GS, int NC, bool kSelf>
+// L > 0: a build for l == L exactly (loops and bounds fold at compile time);
+// L == 0: any l.
+template <int GS, int NC, bool kSelf, int L>
 __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a) {
   if (a.js->status != LRA_OK || a.js->stop) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int l = a.l;
+  const int l = L > 0 ? L : a.l;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int G = gridDim.x, cta = blockIdx.x;
   const long long N = a.N;
@@ -262,16 +263,16 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
   } else {
     if constexpr (kSelf) {
       if (!invert_cross<kMaxvolThreads>(a.strip, a.si, a.st, l, a.js, pos_s, xs, inv)) return;
-      warm_rows<GS, NC>(a, B, nrows, row0, SharedXMapped{xs, inv.at});
+      warm_rows<GS, NC>(a, l, B, nrows, row0, SharedXMapped{xs, inv.at});
     } else if (a.stage_xinv) {
       for (int e = tid; e < l * l; e += nthr) {
         const float2 v = a.xin[e];
         xs[e] = dd{v.x, v.y};
       }
       __syncthreads();
-      warm_rows<GS, NC>(a, B, nrows, row0, SharedX{xs});
+      warm_rows<GS, NC>(a, l, B, nrows, row0, SharedX{xs});
     } else {
-      warm_rows<GS, NC>(a, B, nrows, row0, GlobalX{a.xin});
+      warm_rows<GS, NC>(a, l, B, nrows, row0, GlobalX{a.xin});
     }
     __syncthreads();
     // rows currently selected are exactly the unit vectors of B = S X^{-1}
@@ -433,7 +434,15 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
     // e_j* exactly
     const bool next_gepp = gepp_phase && (step + 1 < l);
     const int next_col = step + 1;
-    mine = 0ull;
+    // the lane's entries of the row factor, the same for all its rows
+    dd rv[NC];
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) rv[cc] = rvec[min(gl + GS * cc, l - 1)];
+    // running best: FP32 |hi| pattern + 1 (so that a zero entry counts) and
+    // the row-major position in the chunk; entries are visited in increasing
+    // position, so keeping the first of equal patterns keeps the smaller index
+    unsigned int bk = 0u;
+    int be = 0;
     for (int base = warp * kGpw; base < nrows; base += ngroups) {
       const int r = base + lane / GS;
       const bool act = r < nrows;
@@ -441,20 +450,24 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
       // the row's entry in column j* is read before its group writes the row
       const dd c = act ? brow[jstar] : dd_make(0.0f);
       __syncwarp();
-      const long long g = row0 + r;
-      const bool piv_row = g == istar;
+      const bool piv_row = row0 + r == istar;
       const bool scan_row = act && !(next_gepp && used[act ? r : 0]);
 #pragma unroll
       for (int cc = 0; cc < NC; ++cc) {
         const int t = gl + GS * cc;
         if (t < l) {
-          dd v = dd_fnma(c, rvec[t], act ? brow[t] : dd_make(0.0f));
+          dd v = dd_fnma(c, rv[cc], act ? brow[t] : dd_make(0.0f));
           if (piv_row) v = dd_make(t == jstar ? 1.0f : 0.0f);
           if (act) brow[t] = v;
-          if (scan_row && (!next_gepp || t == next_col)) mine = umax64(mine, cand_word(v, g * l + t));
+          const unsigned int k1 = (__float_as_uint(v.hi) & 0x7fffffffu) + 1u;
+          if (scan_row && (!next_gepp || t == next_col) && k1 > bk) {
+            bk = k1;
+            be = r * l + t;
+          }
         }
       }
     }
+    mine = bk ? ((unsigned long long)(bk - 1u) << 32) | (0xffffffffu - (unsigned int)(row0 * l + be)) : 0ull;
     if (gepp_phase) {
       if (++step == l) gepp_phase = false;
     } else {
@@ -518,10 +531,10 @@ bool plan_maxvol(long long N, int l, int sms, size_t smem_limit, MaxvolPlan* pla
   }
 }
 
-template <int GS, int NC>
+template <int GS, int NC, int L = 0>
 static cudaError_t launch_gs(MaxvolArgs& a, const MaxvolPlan& plan, cudaStream_t st) {
-  const void* k = (a.self_inverse && !a.gepp) ? reinterpret_cast<const void*>(maxvol_kernel<GS, NC, true>)
-                                              : reinterpret_cast<const void*>(maxvol_kernel<GS, NC, false>);
+  const void* k = (a.self_inverse && !a.gepp) ? reinterpret_cast<const void*>(maxvol_kernel<GS, NC, true, L>)
+                                              : reinterpret_cast<const void*>(maxvol_kernel<GS, NC, false, L>);
   const cudaError_t e = smem_optin(k, 227 * 1024);
   if (e != cudaSuccess) return e;
   void* args[] = {&a};
@@ -543,6 +556,14 @@ cudaError_t launch_maxvol(MaxvolArgs a, const MaxvolPlan& plan, cudaStream_t st)
   if (a.self_inverse && !plan.stage_xinv) return cudaErrorInvalidValue;  // no room for X^{-1}
   a.rows_per_cta = plan.rows_per_cta;
   a.stage_xinv = plan.stage_xinv;
+  // builds for the cross sizes of the served ranks (l = 1.5 k, k = 8 ... 64)
+  switch (a.l) {
+    case 12: return launch_gs<8, 2, 12>(a, plan, st);
+    case 24: return launch_gs<8, 3, 24>(a, plan, st);
+    case 48: return launch_gs<16, 3, 48>(a, plan, st);
+    case 96: return launch_gs<32, 3, 96>(a, plan, st);
+    default: break;
+  }
   if (a.l <= 24) return launch_nc<8>(a, plan, st);
   if (a.l <= 48) return launch_nc<16>(a, plan, st);
   return launch_nc<32>(a, plan, st);
