@@ -39,9 +39,11 @@ __device__ __forceinline__ unsigned long long pivot_word(dd v, int r) {
 // a non-finite or singular cross.
 // NT = blockDim.x: each thread keeps the coordinates of its <= ceil(96^2 /
 // NT) entries in registers for all steps.
-template <int NT>
-__device__ __forceinline__ bool invert_cross(const float* __restrict__ strip, long long si, long long st, int l,
+// L > 0: a build for l == L exactly.
+template <int NT, int L = 0>
+__device__ __forceinline__ bool invert_cross(const float* __restrict__ strip, long long si, long long st, int l_arg,
                                     JobStatus* js, const int* pos, dd* A, const InvScratch& w) {
+  const int l = L > 0 ? L : l_arg;
   constexpr int kPer = (kMaxL * kMaxL + NT - 1) / NT;
   const int ll = l * l;
   const int tid = threadIdx.x, nthr = NT, lane = tid & 31;

@@ -20,11 +20,14 @@ namespace lra {
 
 constexpr int kNucThreads = 512;
 
+// L > 0: a build for l == L exactly (the served cross sizes); L == 0: any l.
+template <int L>
 __global__ void __launch_bounds__(kNucThreads, 1)
-nucleus_kernel(const float* __restrict__ C, const int* __restrict__ I, int l, int k,
+nucleus_kernel(const float* __restrict__ C, const int* __restrict__ I, int l_arg, int k,
                double rank_tol, double* __restrict__ U, double* __restrict__ sigma_out,
                JobStatus* js) {
   if (js->status != LRA_OK) return;
+  const int l = L > 0 ? L : l_arg;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   dd* W = reinterpret_cast<dd*>(smem_raw);           // column b at W + b*l
   dd* Z = W + (size_t)l * l;                          // column b at Z + b*l
@@ -58,7 +61,7 @@ nucleus_kernel(const float* __restrict__ C, const int* __restrict__ I, int l, in
     W[(size_t)b * l + a] = dd_make(ldexpf(C[(size_t)__ldg(I + a) * l + b], -ex));
   }
   __syncthreads();
-  svd_dd<kNucThreads>(W, Z, l, sc);
+  svd_dd<kNucThreads, L>(W, Z, l, sc);
   jacobi_sigma<kNucThreads>(W, l, sig, order);
   if (tid == 0) {
     const double s1 = sig[order[0]];
@@ -76,8 +79,8 @@ nucleus_kernel(const float* __restrict__ C, const int* __restrict__ I, int l, in
   }
   __syncthreads();
   const int ke = *keff_s;
-  left_vectors<kNucThreads>(W, Z, l, ke, order, inv2, sc->perm);
-  nucleus_from_svd<kNucThreads>(W, Z, sc->perm, l, ke, order, inv2,
+  left_vectors<kNucThreads, L>(W, Z, l, ke, order, inv2, sc->perm);
+  nucleus_from_svd<kNucThreads, L>(W, Z, sc->perm, l, ke, order, inv2,
                                 [&](int e, double v) { U[e] = ldexp(v, -ex); });
 }
 
@@ -88,10 +91,12 @@ nucleus_kernel(const float* __restrict__ C, const int* __restrict__ I, int l, in
 // other SMs.
 constexpr int kInvThreads = 1024;
 
+template <int L>   // L > 0: a build for l == L exactly
 __global__ void __launch_bounds__(kInvThreads, 1)
 cross_inverse_kernel(const float* __restrict__ strip, long long si, long long st,
-                     const int* __restrict__ pos, int l, float2* __restrict__ xinv, JobStatus* js) {
+                     const int* __restrict__ pos, int l_arg, float2* __restrict__ xinv, JobStatus* js) {
   if (js->status != LRA_OK || js->stop) return;
+  const int l = L > 0 ? L : l_arg;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   dd* A = reinterpret_cast<dd*>(smem_raw);                   // l * l
   InvScratch w;
@@ -105,7 +110,7 @@ cross_inverse_kernel(const float* __restrict__ strip, long long si, long long st
   int* pos_s = w.p_s + 2;                                     // l
   for (int t = threadIdx.x; t < l; t += blockDim.x) pos_s[t] = pos[t];
   __syncthreads();
-  if (!invert_cross<kInvThreads>(strip, si, st, l, js, pos_s, A, w)) return;
+  if (!invert_cross<kInvThreads, L>(strip, si, st, l, js, pos_s, A, w)) return;
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
     const int r = e / l, q = e - r * l;
     const dd v = A[(size_t)r * l + w.at[q]];
@@ -118,23 +123,47 @@ static size_t inverse_smem(int l) {
          (3 * kMaxL + 2) * sizeof(int);
 }
 
+template <int L>
+static cudaError_t launch_inverse_l(const float* strip, long long si, long long st, const int* pos,
+                                    int l, float2* xinv, JobStatus* js, cudaStream_t stream) {
+  const size_t smem = inverse_smem(l);
+  const cudaError_t e = smem_optin(reinterpret_cast<const void*>(cross_inverse_kernel<L>), (int)smem);
+  if (e) return e;
+  cross_inverse_kernel<L><<<1, kInvThreads, smem, stream>>>(strip, si, st, pos, l, xinv, js);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cross_inverse(const float* strip, long long si, long long st, const int* pos,
                                  int l, float2* xinv, JobStatus* js, cudaStream_t stream) {
-  const size_t smem = inverse_smem(l);
-  const cudaError_t e = smem_optin(reinterpret_cast<const void*>(cross_inverse_kernel), (int)smem);
-  if (e) return e;
-  cross_inverse_kernel<<<1, kInvThreads, smem, stream>>>(strip, si, st, pos, l, xinv, js);
+  switch (l) {
+    case 12: return launch_inverse_l<12>(strip, si, st, pos, l, xinv, js, stream);
+    case 24: return launch_inverse_l<24>(strip, si, st, pos, l, xinv, js, stream);
+    case 48: return launch_inverse_l<48>(strip, si, st, pos, l, xinv, js, stream);
+    case 96: return launch_inverse_l<96>(strip, si, st, pos, l, xinv, js, stream);
+    default: return launch_inverse_l<0>(strip, si, st, pos, l, xinv, js, stream);
+  }
+}
+
+template <int L>
+static cudaError_t launch_nucleus_l(const float* C, const int* I, int l, int k, double rank_tol,
+                                    double* U, double* sigma, JobStatus* js, cudaStream_t st) {
+  const size_t smem = 2 * (size_t)l * l * sizeof(dd) + kMaxL * (sizeof(double) + sizeof(dd)) +
+                      sizeof(SvdScratch) + (kMaxL + 2) * sizeof(int);
+  const cudaError_t e = smem_optin(reinterpret_cast<const void*>(nucleus_kernel<L>), 227 * 1024);
+  if (e != cudaSuccess) return e;
+  nucleus_kernel<L><<<1, kNucThreads, smem, st>>>(C, I, l, k, rank_tol, U, sigma, js);
   return cudaGetLastError();
 }
 
 cudaError_t launch_nucleus(const float* C, const int* I, int l, int k, double rank_tol,
                            double* U, double* sigma, JobStatus* js, cudaStream_t st) {
-  const size_t smem = 2 * (size_t)l * l * sizeof(dd) + kMaxL * (sizeof(double) + sizeof(dd)) +
-                      sizeof(SvdScratch) + (kMaxL + 2) * sizeof(int);
-  const cudaError_t e = smem_optin(reinterpret_cast<const void*>(nucleus_kernel), 227 * 1024);
-  if (e != cudaSuccess) return e;
-  nucleus_kernel<<<1, kNucThreads, smem, st>>>(C, I, l, k, rank_tol, U, sigma, js);
-  return cudaGetLastError();
+  switch (l) {
+    case 12: return launch_nucleus_l<12>(C, I, l, k, rank_tol, U, sigma, js, st);
+    case 24: return launch_nucleus_l<24>(C, I, l, k, rank_tol, U, sigma, js, st);
+    case 48: return launch_nucleus_l<48>(C, I, l, k, rank_tol, U, sigma, js, st);
+    case 96: return launch_nucleus_l<96>(C, I, l, k, rank_tol, U, sigma, js, st);
+    default: return launch_nucleus_l<0>(C, I, l, k, rank_tol, U, sigma, js, st);
+  }
 }
 
 }  // namespace lra

@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
     }
   } else {
     if constexpr (kSelf) {
-      if (!invert_cross<kMaxvolThreads>(a.strip, a.si, a.st, l, a.js, pos_s, xs, inv)) return;
+      if (!invert_cross<kMaxvolThreads, L>(a.strip, a.si, a.st, l, a.js, pos_s, xs, inv)) return;
       warm_rows<GS, NC>(a, l, B, nrows, row0, SharedXMapped{xs, inv.at});
     } else if (a.stage_xinv) {
       for (int e = tid; e < l * l; e += nthr) {

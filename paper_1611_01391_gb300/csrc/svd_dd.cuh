@@ -101,8 +101,10 @@ struct SvdScratch {
 // j..l-1 of column j, with H_j = I - beta_j v_j v_j^T.  The pivot is the
 // trailing column of largest norm (ties: the smaller column); the norms are
 // recomputed from the updated columns at every step.
-template <int NT>
-__device__ void qrcp_dd(dd* A, int l, SvdScratch* sc) {
+// L > 0 (every function below): a build for l == L exactly.
+template <int NT, int L = 0>
+__device__ void qrcp_dd(dd* A, int l_arg, SvdScratch* sc) {
+  const int l = L > 0 ? L : l_arg;
   constexpr int G = 8, GPW = 32 / G, NG = NT / G;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, gl = lane & (G - 1);
   for (int c = tid; c < l; c += NT) sc->perm[c] = c;
@@ -213,8 +215,9 @@ __device__ void qrcp_dd(dd* A, int l, SvdScratch* sc) {
 // s = c t are formed in double-float from that t, so every rotation is
 // orthogonal to double-float accuracy and only the speed of convergence
 // depends on t.
-template <int NT, bool kAccumulate = true, int G = 8>
-__device__ void jacobi_dd(dd* W, dd* Z, int l, int* flag) {
+template <int NT, bool kAccumulate = true, int G = 8, int L = 0>
+__device__ void jacobi_dd(dd* W, dd* Z, int l_arg, int* flag) {
+  const int l = L > 0 ? L : l_arg;
   static_assert(G == 8 || G == 16, "lanes per pair");
   constexpr int kPairsPerWarp = 32 / G;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -288,10 +291,11 @@ __device__ void jacobi_dd(dd* W, dd* Z, int l, int* flag) {
 //   sigma_b = ||W[:, b]||,  right singular vector b of X = P W[:, b] / sigma_b.
 // The rotations are not accumulated: the left singular vectors needed later
 // are u_b = X P W_b / sigma_b^2 (left_vectors), so Z keeps a copy of X.
-template <int NT>
-__device__ void svd_dd(dd* A, dd* Z, int l, SvdScratch* sc) {
+template <int NT, int L = 0>
+__device__ void svd_dd(dd* A, dd* Z, int l_arg, SvdScratch* sc) {
+  const int l = L > 0 ? L : l_arg;
   for (int e = threadIdx.x; e < l * l; e += NT) Z[e] = A[e];
-  qrcp_dd<NT>(A, l, sc);
+  qrcp_dd<NT, L>(A, l, sc);
   // W = R^T in place: column j of W = row j of R (pivoted column order)
   constexpr int kPer = (kMaxL * kMaxL + NT - 1) / NT;
   dd v[kPer];
@@ -312,7 +316,7 @@ __device__ void svd_dd(dd* A, dd* Z, int l, SvdScratch* sc) {
     if (e < l * l) A[e] = v[t];
   }
   __syncthreads();
-  jacobi_dd<NT, false, (NT >= 1024 ? 16 : 8)>(A, nullptr, l, &sc->flag);
+  jacobi_dd<NT, false, (NT >= 1024 ? 16 : 8), L>(A, nullptr, l, &sc->flag);
 }
 
 // Left singular vectors of the kept triplets, in place of the copy of X in
@@ -320,9 +324,10 @@ __device__ void svd_dd(dd* A, dd* Z, int l, SvdScratch* sc) {
 // into column r of Z, r < ke.  One warp per row q of X: the warp holds the
 // row in registers (l <= 96: three values per lane) before it overwrites
 // that row's first ke positions, so rows are independent.
-template <int NT>
-__device__ void left_vectors(const dd* W, dd* Z, int l, int ke, const int* order, const dd* inv2,
+template <int NT, int L = 0>
+__device__ void left_vectors(const dd* W, dd* Z, int l_arg, int ke, const int* order, const dd* inv2,
                              const int* perm) {
+  const int l = L > 0 ? L : l_arg;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int q = warp; q < l; q += NT / 32) {
     dd x[3];
@@ -372,9 +377,10 @@ __device__ void jacobi_sigma(const dd* W, int l, double* sig, int* order) {
 // inv2[r] = 1 / sigma_{b_r}^2 (shared, computed once); out(e, value)
 // receives the l*l entries, row-major e = p*l + q (p a column of X, q a row
 // of X).
-template <int NT, typename Out>
-__device__ void nucleus_from_svd(const dd* W, const dd* Z, const int* perm, int l, int ke,
+template <int NT, int L = 0, typename Out>
+__device__ void nucleus_from_svd(const dd* W, const dd* Z, const int* perm, int l_arg, int ke,
                                  const int* order, const dd* inv2, Out out) {
+  const int l = L > 0 ? L : l_arg;
   for (int e = threadIdx.x; e < l * l; e += NT) {
     const int c = e / l, q = e - c * l;
     dd acc{0.f, 0.f};
