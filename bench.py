@@ -877,17 +877,39 @@ def run_profile_solves(args, wl_name):
     print(f"profile solves done: {args.profile_solves} x {wl_name}", flush=True)
 
 
+def sources_sha256(files):
+    """sha256 over the concatenated bytes of the listed csrc/ files, in order."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1611_01391_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def captured_traffic(kernel_file, summary):
-    """DRAM bytes per launch from a committed ncu summary, or None when the
-    kernel source changed since that capture (its sha256 is recorded)."""
+    """DRAM bytes per launch from a committed ncu summary, or None when a
+    source the kernel is built from changed since that capture.  The summary
+    lists them ("sources: a.cu, b.cuh") with the sha256 of their
+    concatenation ("sources_sha256: ..."); without a list, the kernel file's
+    own sha256 ("source_sha256: ...")."""
     import hashlib
     try:
         text = open(os.path.join(ROOT, "profiles", summary)).read()
-        src = open(os.path.join(ROOT, "paper_1611_01391_gb300", "csrc", kernel_file), "rb").read()
     except OSError:
         return None
-    fields = dict(ln.split(":", 1) for ln in text.splitlines() if ln.startswith(("traffic_bytes_per_launch:", "source_sha256:")))
-    if fields.get("source_sha256", "").strip() != hashlib.sha256(src).hexdigest():
+    fields = {k.strip(): v.strip() for k, v in (ln.split(":", 1) for ln in text.splitlines()
+              if ln.startswith(("traffic_bytes_per_launch:", "source_sha256:", "sources:", "sources_sha256:")))}
+    try:
+        if "sources" in fields:
+            files = [f.strip() for f in fields["sources"].split(",") if f.strip()]
+            if fields.get("sources_sha256") != sources_sha256(files):
+                return None
+        else:
+            with open(os.path.join(ROOT, "paper_1611_01391_gb300", "csrc", kernel_file), "rb") as fh:
+                if fields.get("source_sha256") != hashlib.sha256(fh.read()).hexdigest():
+                    return None
+    except OSError:
         return None
     if "traffic_bytes_per_launch" not in fields:
         return None
