@@ -86,8 +86,8 @@ nucleus_kernel(const float* __restrict__ C, const int* __restrict__ I, int l_arg
 
 // X^{-1} of the cross X[a][b] = S[pos[a]][b] of a strip, by one CTA of
 // 1024 threads in double-float arithmetic (inverse_dd.cuh: Gauss-Jordan
-// with partial pivoting), written row-major as FP32 pairs with the row
-// interchanges undone.  One SM: the jobs of a serving context keep the
+// with partial pivoting and a one-step look-ahead), written row-major as
+// FP32 pairs with the row interchanges undone.  One SM: the jobs of a serving context keep the
 // other SMs.
 constexpr int kInvThreads = 1024;
 
@@ -98,19 +98,20 @@ cross_inverse_kernel(const float* __restrict__ strip, long long si, long long st
   if (js->status != LRA_OK || js->stop) return;
   const int l = L > 0 ? L : l_arg;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  dd* A = reinterpret_cast<dd*>(smem_raw);                   // l * l
-  InvScratch w;
-  w.rowt = A + (size_t)l * l;
-  w.colt = w.rowt + kMaxL;
-  w.rowold = w.colt + kMaxL;
-  w.pkey = reinterpret_cast<unsigned long long*>(w.rowold + kMaxL);
-  w.swaps = reinterpret_cast<int*>(w.pkey + 2);
+  dd* A0 = reinterpret_cast<dd*>(smem_raw);                  // l * l
+  dd* A1 = A0 + (size_t)l * l;                                // l * l
+  InvLaScratch w;
+  w.stride = kMaxL;
+  w.rowt = A1 + (size_t)l * l;           // 2 * kMaxL
+  w.colt = w.rowt + 2 * kMaxL;           // 2 * kMaxL
+  w.swaps = reinterpret_cast<int*>(w.colt + 2 * kMaxL);
   w.at = w.swaps + kMaxL;
-  w.p_s = w.at + kMaxL;
-  int* pos_s = w.p_s + 2;                                     // l
+  w.pinfo = w.at + kMaxL;
+  int* pos_s = w.pinfo + 2;                                   // l
   for (int t = threadIdx.x; t < l; t += blockDim.x) pos_s[t] = pos[t];
   __syncthreads();
-  if (!invert_cross<kInvThreads, L>(strip, si, st, l, js, pos_s, A, w)) return;
+  const dd* A = invert_cross_la<kInvThreads, L>(strip, si, st, l, js, pos_s, A0, A1, w);
+  if (!A) return;
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
     const int r = e / l, q = e - r * l;
     const dd v = A[(size_t)r * l + w.at[q]];
@@ -119,8 +120,7 @@ cross_inverse_kernel(const float* __restrict__ strip, long long si, long long st
 }
 
 static size_t inverse_smem(int l) {
-  return (size_t)l * l * sizeof(dd) + 3 * kMaxL * sizeof(dd) + 2 * sizeof(unsigned long long) +
-         (3 * kMaxL + 2) * sizeof(int);
+  return 2 * (size_t)l * l * sizeof(dd) + 4 * kMaxL * sizeof(dd) + (3 * kMaxL + 2) * sizeof(int);
 }
 
 template <int L>
