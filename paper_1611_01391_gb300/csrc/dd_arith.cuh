@@ -132,30 +132,4 @@ __device__ __forceinline__ dd dd_div(dd a, dd b) {
   return quick_two_sum(q1, __fdiv_rn(rem, b.hi));
 }
 
-// Unsigned 64-bit key that orders normalised pairs by |hi + lo|: the bit
-// pattern of |hi| (non-negative FP32 patterns order like their values) above
-// the pattern of lo taken with the sign of hi (|v| = |hi| + sign(hi) lo),
-// mapped to an order-preserving unsigned (negative patterns reversed).
-// Adding +0 turns a -0 low part into +0, so equal values give equal keys.
-// Integer work only, apart from that one FP32 add.
-__device__ __forceinline__ unsigned long long dd_abs_key(dd v) {
-  const unsigned int hb = __float_as_uint(v.hi);
-  const float ls = __fadd_rn(__uint_as_float(__float_as_uint(v.lo) ^ (hb & 0x80000000u)), 0.0f);
-  const unsigned int lb = __float_as_uint(ls);
-  const unsigned int ko = (lb & 0x80000000u) ? ~lb : (lb | 0x80000000u);
-  return ((unsigned long long)(hb & 0x7fffffffu) << 32) | ko;
-}
-
-// |v| in FP64 back from its key (0 for the empty key 0).
-__device__ __forceinline__ double dd_key_value(unsigned long long k) {
-  if (k == 0ull) return 0.0;
-  const float hi = __uint_as_float((unsigned int)(k >> 32));
-  const unsigned int ko = (unsigned int)k;
-  const unsigned int lb = (ko & 0x80000000u) ? (ko & 0x7fffffffu) : ~ko;
-  return (double)hi + (double)__uint_as_float(lb);
-}
-
-// Keys at or above this one belong to an infinite or NaN high part.
-constexpr unsigned long long kDdKeyNonFinite = 0x7f80000000000000ull;
-
 }  // namespace lra

@@ -119,18 +119,6 @@ struct GridBarrier {
 };
 constexpr int kWinRing = 4;
 
-// IEEE-754 bit pattern of |x| (orders non-negative doubles like their
-// values), computed on the integer pipes.  The raw pattern passes through an
-// empty asm statement before the sign is masked off: otherwise the optimiser
-// recognises "bits & 0x7fff..." as fabs(x), which is issued as an FP64
-// instruction, and at 1/64 of the FP32 rate one per scanned entry costs as
-// much as the arithmetic being scanned.
-__device__ __forceinline__ unsigned long long abs_bits(double x) {
-  unsigned long long k = (unsigned long long)__double_as_longlong(x);
-  asm("" : "+l"(k));
-  return k & 0x7fffffffffffffffull;
-}
-
 // x as an FP32 pair: hi = x rounded to FP32, lo = the rest rounded to FP32
 // (about 48 significant bits of x).
 __device__ __forceinline__ float2 split_double(double x) {
@@ -148,10 +136,6 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
   unsigned int v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
-}
-
-__device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ void set_status(JobStatus* js, int code) {
