@@ -19,6 +19,16 @@ __global__ void __launch_bounds__(256) gather_cols_kernel(SourceDev s, const int
   __syncthreads();
   const long long total = s.m * (long long)l;
   const long long stride = (long long)gridDim.x * blockDim.x;
+  if (total < (1LL << 31)) {
+    // 32-bit index arithmetic: a 64-bit division per entry would cost more
+    // than the entry
+    const unsigned int tot = (unsigned int)total, str = (unsigned int)stride, ul = (unsigned int)l;
+    for (unsigned int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += str) {
+      const unsigned int i = e / ul;
+      C[e] = entry<KIND>(s, (long long)i, Js[e - i * ul]);
+    }
+    return;
+  }
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += stride) {
     const long long i = e / l;
     const int t = (int)(e - i * l);
@@ -37,8 +47,10 @@ __global__ void __launch_bounds__(256) gather_rows_kernel(SourceDev s, const int
   const long long nq = (n + 3) / 4;
   const long long total = nq * l;
   const long long stride = (long long)gridDim.x * blockDim.x;
+  const bool small = total < (1LL << 31) && nq < (1LL << 31);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += stride) {
-    const int t = (int)(e / nq);
+    // 32-bit division where it fits (a 64-bit one costs more than the entries)
+    const int t = small ? (int)((unsigned int)e / (unsigned int)nq) : (int)(e / nq);
     const long long j0 = (e - (long long)t * nq) * 4;
     const long long i = __ldg(I + t);
     float v[4];
