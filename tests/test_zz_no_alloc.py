@@ -24,7 +24,9 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
+import oracle as O  # noqa: E402
 import paper_1611_01391_gb300 as L  # noqa: E402
+from tests._parity import separated  # noqa: E402
 
 
 def _noalloc():
@@ -67,6 +69,41 @@ def test_noalloc_matches_regular_entry_point_twice(m, n, l):
             st = status.cpu().numpy()
             assert st[0] == L.LRA_OK and st[2] == 1
             np.testing.assert_array_equal(pos.cpu().numpy(), expect)
+
+
+@pytest.mark.parametrize("m,l", [(6000, 24), (3000, 40), (2500, 96)])
+def test_noalloc_warm_start_from_caller_inverse(m, l):
+    """Warm start (Section 6.5: each half-step starts from the previous index
+    set) with the caller's FP64 inverse of the cross S[pos, :]: the rows kept
+    after the maxvol swaps are the FP64 oracle's (same FP32 entries) wherever
+    every decision of the oracle's log is separated; otherwise they must at
+    least be a dominant set (max |S S[pos, :]^{-1}| <= 1 + delta)."""
+    f = _noalloc()
+    delta = 1e-2
+    S32 = W.factor_gaussian(31 * m + l, m, l, l, 1e-2).astype(np.float32)
+    S64 = S32.astype(np.float64)
+    pos0 = W.draw_indices(17 * m + l, m, l)
+    xinv = np.linalg.inv(S64[pos0, :])
+    trace = []
+    ref = O.maxvol(S64, pos0, delta=delta, trace=trace)
+    strip = torch.from_numpy(S32).cuda()
+    pos = torch.from_numpy(np.asarray(pos0, np.int32)).cuda()
+    xd = torch.from_numpy(np.ascontiguousarray(xinv)).cuda()
+    status = torch.full((3,), -99, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    rc = f(strip.data_ptr(), m, l, l, 1, pos.data_ptr(), xd.data_ptr(), delta, 0, status.data_ptr(), None)
+    assert rc == L.LRA_OK
+    torch.cuda.synchronize()
+    st = status.cpu().numpy()
+    assert st[0] == L.LRA_OK and st[2] == 1
+    got = pos.cpu().numpy()
+    assert len(set(got.tolist())) == l
+    if all(separated(d, delta) for d in trace):
+        np.testing.assert_array_equal(got, np.asarray(ref.I))
+        assert st[1] == ref.swaps
+    else:
+        B = np.linalg.solve(S64[got, :].T, S64.T).T
+        assert np.abs(B).max() <= 1.0 + delta + 1e-9
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
