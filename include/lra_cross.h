@@ -93,9 +93,11 @@ typedef struct {
   int32_t n_streams;          /* own streams (1..32; <= 0: 1).  A job runs on the
                                  least loaded one, so jobs submitted while others
                                  run overlap on the device (continuous admission).
-                                 With more than one, kernels that would spread one
-                                 job over several SMs for latency (the cross
-                                 inverse at l > 32) run on one SM instead. */
+                                 With one stream the cross inverse of a warm-started
+                                 step runs inside that step's maxvol launch (every
+                                 CTA inverts the cross itself) when it fits on chip;
+                                 with more than one it runs as its own one-CTA
+                                 launch, leaving the other SMs to the other jobs. */
   int32_t max_grid;           /* CTAs per maxvol launch at most (<= 0: one per SM).
                                  A smaller grid leaves SMs to the other jobs in
                                  flight; a strip whose chunks would not fit in
@@ -150,7 +152,8 @@ typedef struct {
   double t_maxvol_ms;
   double t_cross_ms;
   double t_resid_ms;
-  double t_inverse_ms;        /* fresh cross inverses before warm-started steps     */
+  double t_inverse_ms;        /* fresh cross inverses run as their own launches
+                                 (inverses inside a maxvol launch count there)      */
   double full_rel_err;        /* LRA_FLAG_FULL_RESIDUAL: ||M - CUR||_F / ||M||_F (else -1) */
   double t_fullres_ms;        /* with LRA_FLAG_PROFILE: full-residual kernels       */
 } lra_info;
