@@ -427,7 +427,7 @@ def run_ours(args, wl_name):
         "data": "synthetic",
         "config": {"workload": wl_name, "generator": wl["kind"], "m": m, "n": n, "k": k, "l": l,
                    "sweeps": sweeps, "error_sample": f"{wl['q']}x{wl['s']}",
-                   "precision": "FP32 entries/strips, double-float (FP32 pair) maxvol, FP64 cross inverse, double-float nucleus, compensated FP32 residual products",
+                   "precision": "FP32 entries/strips, double-float (FP32 pair) maxvol and cross inverse, double-float nucleus, FP64 U, compensated FP32 residual products",
                    "l2": "flushed before every step (256 MiB write); steps timed individually",
                    "parallelism": f"replicas{world}"},
         "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
