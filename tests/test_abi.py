@@ -5,6 +5,8 @@ import glob
 import os
 import re
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -118,3 +120,66 @@ def test_struct_layouts_match_the_header(tmp_path):
             assert ctypes.sizeof(cls) == int(v), (s, ctypes.sizeof(cls), v)
         else:
             assert getattr(cls, f).offset == int(v), (s, f, getattr(cls, f).offset, v)
+
+
+def _valid_pair():
+    import numpy as np
+    import paper_1611_01391_gb300 as L
+    src = L.lra_source(L.LRA_GEN_GAUSS, 3, 5000, 4000, None, 0, 16, 16, 0.5)
+    params, keep = L.make_params(8, 12, 2, np.arange(12), resid_rows=np.arange(100),
+                                 resid_cols=np.arange(100))
+    return src, params, keep
+
+
+# every rejection rule of the host validation, one at a time, each from a
+# valid pair; lra_cross_footprint runs the same validation as submit
+_BREAKERS = {
+    "unknown kind": lambda L, s, p: setattr(s, "kind", 7),
+    "m < 1": lambda L, s, p: setattr(s, "m", 0),
+    "n too large": lambda L, s, p: setattr(s, "n", (1 << 30) + 1),
+    "dense without a": lambda L, s, p: (setattr(s, "kind", L.LRA_DENSE_F32), setattr(s, "a", None)),
+    "dense lda < n": lambda L, s, p: (setattr(s, "kind", L.LRA_DENSE_F32), setattr(s, "a", 256),
+                                      setattr(s, "lda", 3999)),
+    "generator without y": lambda L, s, p: setattr(s, "y", None),
+    "dim 4": lambda L, s, p: setattr(s, "dim", 4),
+    "gauss h = 0": lambda L, s, p: setattr(s, "h", 0.0),
+    "l = 97": lambda L, s, p: (setattr(p, "l", 97)),
+    "k = 0": lambda L, s, p: setattr(p, "k", 0),
+    "l > n": lambda L, s, p: setattr(s, "n", 11),
+    "sweeps = 0": lambda L, s, p: setattr(p, "sweeps", 0),
+    "delta = 0": lambda L, s, p: setattr(p, "delta", 0.0),
+    "rank_tol < 0": lambda L, s, p: setattr(p, "rank_tol", -1.0),
+    "no init_J": lambda L, s, p: setattr(p, "init_J", None),
+    "q without s": lambda L, s, p: setattr(p, "resid_s", 0),
+    "sample > m": lambda L, s, p: setattr(p, "resid_q", 5001),
+    "tol without sample": lambda L, s, p: (setattr(p, "tol", 1e-3), setattr(p, "resid_q", 0),
+                                           setattr(p, "resid_s", 0)),
+    "trace_cap < 0": lambda L, s, p: setattr(p, "trace_cap", -1),
+    "full residual on a generator": lambda L, s, p: setattr(p, "flags", 2),
+    "full residual, unaligned base": lambda L, s, p: (setattr(s, "kind", L.LRA_DENSE_F32),
+                                                      setattr(s, "a", 4100), setattr(s, "lda", 4000),
+                                                      setattr(p, "flags", 2)),
+}
+
+
+@pytest.mark.parametrize("rule", sorted(_BREAKERS))
+def test_host_validation_rejects(rule):
+    import paper_1611_01391_gb300 as L
+    src, params, keep = _valid_pair()
+    assert L.lra_cross_footprint(src, params) > 0
+    _BREAKERS[rule](L, src, params)
+    with pytest.raises(L.LraError) as e:
+        L.lra_cross_footprint(src, params)
+    assert e.value.code == L.LRA_EINVAL
+
+
+def test_footprint_grows_with_the_strips():
+    """The job's allocation holds both strips (4 (m + n) l bytes) plus
+    per-job pieces independent of m and n."""
+    import paper_1611_01391_gb300 as L
+    src, params, keep = _valid_pair()
+    b0 = L.lra_cross_footprint(src, params)
+    src.m, src.n = 2 * 5000, 2 * 4000
+    b1 = L.lra_cross_footprint(src, params)
+    grow = 4 * (5000 + 4000) * 12
+    assert abs((b1 - b0) - grow) <= 2 * 256   # two 256-byte-aligned pieces
