@@ -15,10 +15,13 @@
 //         rows of |W[:, t]| (the GEPP pivot).  After l steps W = S X^{-1}
 //         with X = S[I, :].
 //       - Later half-steps start from W = S X^{-1}, where X^{-1} is computed
-//         afresh from the new cross by the cross inverse kernels (an inverse
-//         carried from strip to strip by rank-one updates loses a factor
-//         cond(X) of accuracy on the ill-conditioned crosses of smooth
-//         kernels), which hand it over as hi/lo FP32 pairs.
+//         afresh from the new cross (an inverse carried from strip to strip
+//         by rank-one updates loses a factor cond(X) of accuracy on the
+//         ill-conditioned crosses of smooth kernels): by every CTA of this
+//         launch itself (kSelf builds, double-float Gauss-Jordan of
+//         inverse_dd.cuh, when X^{-1} fits beside the chunk), or by the
+//         separate cross inverse kernel, which hands it over as hi/lo FP32
+//         pairs.  The product S X^{-1} is a compensated (Dot2) sum per entry.
 //       - Maxvol swaps take (i*, j*) = argmax |B| and stop once it is
 //         <= 1 + delta.
 //   * Per decision: every warp reduces its best candidate word (|value| and
@@ -32,7 +35,9 @@
 //     decision (fused pass).  Every CTA reads the same few words and one
 //     row, so the exchange costs few requests on those hot L2 lines.
 //   * Ties in |value| go to the smaller flat index i*l + j (smaller row, then
-//     smaller column), the same rule as the FP64 oracle.
+//     smaller column), the same rule as the FP64 oracle; candidates are
+//     ranked by the FP32 high part of their pairs, so values within 2^-24 of
+//     each other count as ties.
 #include <cfloat>
 
 #include "dd_arith.cuh"

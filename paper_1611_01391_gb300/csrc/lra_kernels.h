@@ -19,8 +19,8 @@ cudaError_t launch_gather_rows(const SourceDev& s, const int* I, int l, float* R
 // strip[i*si + t*st].  gepp = 1: Gauss-Jordan elimination with partial
 // pivoting selects the initial rows; gepp = 0: warm start from pos[] with xin
 // = inverse of the strip's cross S[pos, :] (row-major, each entry split into
-// an FP32 pair x + y, see split_double).  On exit pos[] holds the selected
-// rows.
+// an FP32 pair x + y, see split_double), or with self_inverse set, the
+// launch inverts the cross itself.  On exit pos[] holds the selected rows.
 struct MaxvolArgs {
   const float* strip;
   long long N;
