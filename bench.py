@@ -79,13 +79,46 @@ DD_OPS_WARM = 11
 DD_OPS_UPDATE = 15
 
 
-def maxvol_dd_peak_tflops(flops, warm_fmas, sm_mhz):
-    """Algorithmic FLOP/s of a maxvol run whose every FP32 instruction issued
-    at the FP32 pipe rate: flops / (instruction count / rate)."""
+def maxvol_dd_peak_tflops(flops, warm_fmas, sm_mhz, sms=SMS):
+    """Implementation ceiling (not the hardware roofline): algorithmic FLOP/s
+    of a maxvol run whose every FP32 instruction of its double-float
+    arithmetic issued at the FP32 pipe rate: flops / (instruction count /
+    rate)."""
     upd_fmas = max(flops / 2 - warm_fmas, 0.0)
     ops = DD_OPS_WARM * warm_fmas + DD_OPS_UPDATE * upd_fmas
-    t_min = ops / (SMS * FP32_PER_SM_CLK * sm_mhz * 1e6)
+    t_min = ops / (sms * FP32_PER_SM_CLK * sm_mhz * 1e6)
     return flops / t_min / 1e12 if t_min > 0 else 0.0
+
+
+def fp32_pipe_peak_tflops(sm_mhz, sms=SMS):
+    """Hardware FP32 roofline: sms x 128 FMA lanes x 2 flops x clock."""
+    return sms * FP32_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12
+
+
+def device_sms(dev):
+    import torch
+    return torch.cuda.get_device_properties(dev).multi_processor_count
+
+
+def dist_setup():
+    """(world, rank, local rank, device) of this process; the NCCL process
+    group is created once, for the max of the timed region over ranks."""
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    return world, rank, local, torch.device("cuda", local)
+
+
+def dist_barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
 
 
 # ---------------------------------------------------------------------------
@@ -226,7 +259,7 @@ s64 = O.InvDist(pts, pts, "fp64")
 class Sub:
     def __init__(s, r0, m, c0, n): s.r0, s.m, s.c0, s.n = r0, m, c0, n
     def block(s, rows, cols): return s64.block(s.r0 + np.asarray(rows), s.c0 + np.asarray(cols))
-order = np.random.default_rng(0).permutation(len(blocks))   # unbiased sample of block sizes
+order = np.random.default_rng(0).permutation(len(blocks))[{worker}::{procs}]   # unbiased sample of block sizes
 t0 = time.perf_counter(); n = 0; times = []
 for b in order:
     r0, m, c0, n_ = (int(v) for v in blocks[b])
@@ -251,7 +284,7 @@ from bench import WORKLOADS
 wl = WORKLOADS[{wl!r}]
 reqs = W.serving_requests(W.BASE_SEED + wl["seed_off"], wl["count"], wl["min_side"], wl["max_side"])
 t0 = time.perf_counter(); n = 0; times = []
-for r in reqs:
+for r in reqs[{worker}::{procs}]:
     t1 = time.perf_counter()
     if r["kind"] == "cauchy":
         src = O.Cauchy(r["x"], r["y"], "fp64")
@@ -268,17 +301,84 @@ print(json.dumps({{"n": n, "total_s": sum(times), "times": times}}))
 """
 
 
-def run_oracle(wl_name, budget_s=12.0, min_n=1, max_n=1000):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
+def _oracle_cmd(wl_name, budget_s, min_n, max_n, worker=0, procs=1):
     form = WORKLOADS[wl_name].get("form", "plain")
     snippet = {"plain": CPU_SNIPPET, "batch": CPU_BATCH_SNIPPET, "serve": CPU_SERVE_SNIPPET}[form]
-    code = snippet.format(root=ROOT, wl=wl_name, budget=budget_s, min_n=min_n, max_n=max_n)
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                       timeout=900)
+    code = snippet.format(root=ROOT, wl=wl_name, budget=budget_s, min_n=min_n, max_n=max_n,
+                          worker=worker, procs=procs)
+    return [sys.executable, "-c", code]
+
+
+# every oracle process is a fresh interpreter with one BLAS thread and no GPU
+_ORACLE_ENV = dict(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                   CUDA_VISIBLE_DEVICES="")
+
+
+def run_oracle(wl_name, budget_s=12.0, min_n=1, max_n=1000):
+    """The oracle on one host core: units solved within the budget."""
+    env = dict(os.environ, **_ORACLE_ENV)
+    r = subprocess.run(_oracle_cmd(wl_name, budget_s, min_n, max_n), capture_output=True, text=True,
+                       env=env, timeout=900)
     if r.returncode != 0:
         raise RuntimeError(f"oracle baseline failed: {r.stderr[-2000:]}")
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_procs(wl_name):
+    """Oracle processes to run at once: one per host core, fewer where the
+    workload's matrix would not fit in host memory that many times."""
+    p = host_cores()
+    wl = WORKLOADS[wl_name]
+    if wl.get("kind") == "dense32":
+        need = 3 * wl["m"] * wl["n"] * 4
+        try:
+            with open("/proc/meminfo") as f:
+                avail = next(int(ln.split()[1]) * 1024 for ln in f if ln.startswith("MemAvailable"))
+            p = max(1, min(p, int(0.5 * avail // need)))
+        except (OSError, StopIteration):
+            p = 1
+    return p
+
+
+def run_oracle_parallel(wl_name, procs, budget_s=12.0, min_n=1, max_n=1000):
+    """The oracle on `procs` host cores at once (one single-threaded process
+    each, started as fresh interpreters); returns each process's record."""
+    env = dict(os.environ, **_ORACLE_ENV)
+    ps = [subprocess.Popen(_oracle_cmd(wl_name, budget_s, min_n, max_n, w, procs), stdout=subprocess.PIPE,
+                           stderr=subprocess.PIPE, text=True, env=env) for w in range(procs)]
+    out = []
+    for p in ps:
+        o, e = p.communicate(timeout=1800)
+        if p.returncode != 0:
+            raise RuntimeError(f"oracle baseline failed: {e[-2000:]}")
+        out.append(json.loads(o.strip().splitlines()[-1]))
+    return out
+
+
+def cpu_baseline(wl_name, unit, what, budget_s=12.0):
+    """The oracle as it stands on the host: one process per core at once
+    (throughput = the sum of the processes' rates; cores = processes, one
+    thread each), and a single-threaded run beside it."""
+    try:
+        one = run_oracle(wl_name, budget_s)
+        procs = _oracle_procs(wl_name)
+        many = run_oracle_parallel(wl_name, procs, budget_s)
+        n_all = sum(r["n"] for r in many)
+        return {"value": sum(r["n"] / r["total_s"] for r in many), "unit": unit, "cores": procs,
+                "kind": "oracle",
+                "sample": (f"{n_all} {what} on {procs} host cores at once (one single-threaded FP64 numpy "
+                           f"process per core, ~{budget_s:.0f} s each)"),
+                "single_thread": {"value": one["n"] / one["total_s"], "unit": unit, "cores": 1,
+                                  "sample": f"{one['n']} {what}, one thread"}}
+    except Exception as e:  # report, do not hide
+        return {"value": None, "unit": unit, "cores": None, "kind": "oracle", "sample": f"failed: {e}"}
 
 
 # ---------------------------------------------------------------------------
@@ -288,15 +388,8 @@ def run_oracle(wl_name, budget_s=12.0, min_n=1, max_n=1000):
 def run_ours(args, wl_name):
     import numpy as np
     import torch
-    import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+    world, rank, local, dev = dist_setup()
 
     import paper_1611_01391_gb300 as L
 
@@ -330,8 +423,7 @@ def run_ours(args, wl_name):
 
     clocks = ClockSampler(local)
     torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
+    dist_barrier(world)
     clocks.start()
     time.sleep(0.3)
     evs = []
@@ -349,8 +441,7 @@ def run_ours(args, wl_name):
         infos.append(res.info)
     torch.cuda.synchronize(dev)
     t_wall = time.perf_counter() - t_wall0
-    if world > 1:
-        dist.barrier()
+    dist_barrier(world)
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = max_over_ranks(sum(step_ms), world, dev)
@@ -367,10 +458,15 @@ def run_ours(args, wl_name):
     t_r = sum(i.t_resid_ms for i in infos)
     sm_mhz = clk.get("sm_mhz") or 2070.0
     peaks, peak_kind = _peaks()
+    sms = device_sms(dev)
+    # the hardware roofline of maxvol: the FP32 pipe at the part's maximum SM
+    # clock (what the method's FP32 work could reach)
+    max_mhz = float(peaks.get("sm_max_mhz") or 2070.0)
+    fp32_peak = fp32_pipe_peak_tflops(max_mhz, sms)
     # warm starts: the column half-steps after the first sweep's and every
     # row half-step, each N l^2 multiply-adds
     warm = sum((i.sweeps_done - 1) * m * l * l + i.sweeps_done * n * l * l for i in infos)
-    mv_peak = maxvol_dd_peak_tflops(fl_mv, warm, sm_mhz)
+    mv_ceiling = maxvol_dd_peak_tflops(fl_mv, warm, max_mhz, sms)
     achieved = fl_mv / (t_mv / 1e3) / 1e12 if t_mv > 0 else 0.0
     # gathers: bytes written (strips) per solve; generated entries read nothing
     strips_bytes = ((sweeps + 1) * m * l + sweeps * l * n) * 4
@@ -437,13 +533,17 @@ def run_ours(args, wl_name):
                                "inverse": sum(i.t_inverse_ms for i in infos) / len(infos),
                                "nucleus": t_x / len(infos), "resid": t_r / len(infos)},
         "roofline": {"kernel": "maxvol_kernel", "bound": "alu", "achieved": achieved,
-                     "peak": mv_peak, "unit": "TFLOP/s", "frac": achieved / mv_peak if mv_peak else None,
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak if fp32_peak else None,
                      "traffic": captured_traffic("k_maxvol.cu", f"maxvol_{wl_name}.md"),
                      "traffic_note": "DRAM bytes per maxvol launch from the committed ncu capture (null if the kernel changed since)",
-                     "peak_source": (f"FP32 pipe: {SMS} SMs x {FP32_PER_SM_CLK} instr/clk x median SM clock "
-                                     f"{sm_mhz:.0f} MHz, at {DD_OPS_WARM} (warm start) / {DD_OPS_UPDATE} (update) "
-                                     "FP32 instructions per double-float multiply-add"),
-                     "note": "algorithmic FLOPs: warm start 2 N l^2 plus 2 N l per GEPP step or swap"},
+                     "peak_source": (f"hardware FP32 pipe (nominal, no measured FP32 figure): {sms} SMs x "
+                                     f"{FP32_PER_SM_CLK} FMA lanes x 2 flops x max SM clock {max_mhz:.0f} MHz"),
+                     "note": "algorithmic FLOPs of the method's FP32 work: warm start 2 N l^2 plus 2 N l per GEPP step or swap",
+                     "implementation_ceiling": {
+                         "peak": mv_ceiling, "frac": achieved / mv_ceiling if mv_ceiling else None,
+                         "note": (f"same FLOPs against the FP32 pipe divided by the FP32 instructions per "
+                                  f"double-float multiply-add ({DD_OPS_WARM} warm start, {DD_OPS_UPDATE} update): "
+                                  "the ceiling of this implementation's precision choice, not of the hardware")}},
         "gpu_launches": int(sum(i.kernel_launches for i in infos)),
         "clocks": clk,
         "e2e": e2e,
@@ -462,18 +562,36 @@ def run_ours(args, wl_name):
             "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
             "algorithmic_bytes": m * n * 4}
     ctx.close()
+    del flush
+    # the metric's comparative half: the batched and served forms against
+    # plain one-job-per-launch C-A on the same units, at equal error
+    if getattr(args, "legs", False):
+        import types
+        sub = types.SimpleNamespace(steps=min(args.steps, 5), warmup=3)
+        legs = {"batch": run_batch(sub, "octree4096", embed=True),
+                "serve": run_serve(sub, "serve", embed=True)}
+        if rank == 0:
+            b, sv = legs["batch"], legs["serve"]
+            line["batch"] = b
+            line["serve"] = sv
+            line["batch_blocks_per_s"] = b["value"]
+            line["batch_speedup_vs_plain"] = b["speedup_vs_plain"]
+            line["serve_solves_per_s"] = sv["value"]
+            line["serve_speedup_vs_plain"] = sv["speedup_vs_plain"]
+            line["serve_p50_ms"] = sv["p50_ms"]
+            line["serve_p99_ms"] = sv["p99_ms"]
+            line["equal_error"] = {
+                "batch": {"batched_est_rel_err_max_subset": b["est_rel_err_max_subset"],
+                          "plain_est_rel_err_max": b["plain_one_job_per_launch"]["est_rel_err_max"]},
+                "serve": {"served_est_rel_err_max": sv["est_rel_err_max"],
+                          "plain_est_rel_err_max": sv["plain_one_job_per_launch"]["est_rel_err_max"],
+                          "identical_results": sv["identical_to_plain"]}}
     if world > 1:
+        import torch.distributed as dist
         dist.destroy_process_group()
     if rank == 0:
         if world == 1:
-            try:
-                ob = run_oracle(wl_name)
-                line["cpu_baseline"] = {"value": ob["n"] / ob["total_s"], "unit": UNIT, "cores": 1,
-                                        "kind": "oracle",
-                                        "sample": f"{ob['n']} full solve(s) of the same workload, FP64 numpy, 1 thread"}
-            except Exception as e:  # report, do not hide
-                line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                        "sample": f"failed: {e}"}
+            line["cpu_baseline"] = cpu_baseline(wl_name, UNIT, "full solve(s) of the same workload")
         print(json.dumps(line), flush=True)
 
 
@@ -490,25 +608,15 @@ def make_batch_inputs(wl, rank=0):
     return pts, blocks, jc, sr, sc
 
 
-def fp32_peak_tflops(sm_mhz):
-    # 128 FP32 FMA lanes per SM per clock
-    return SMS * 128 * 2 * sm_mhz * 1e6 / 1e12
-
-
-def run_batch(args, wl_name):
+def run_batch(args, wl_name, embed=False):
+    """Batched form; with embed, returns the measurement (rank 0) instead of
+    printing it, for the default line."""
     import numpy as np
     import torch
     import paper_1611_01391_gb300 as L
     from paper_1611_01391_gb300.api import _batch_fetch, make_batch_params
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+    world, rank, local, dev = dist_setup()
     wl = WORKLOADS[wl_name]
     pts, blocks, jc, sr, sc = make_batch_inputs(wl, rank)
     nb = len(blocks)
@@ -529,8 +637,7 @@ def run_batch(args, wl_name):
         assert np.all(r.status == 0), np.unique(r.status)
     clocks = ClockSampler(local)
     torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
+    dist_barrier(world)
     clocks.start()
     time.sleep(0.3)
     evs, res = [], []
@@ -552,8 +659,10 @@ def run_batch(args, wl_name):
     value = world * nb * args.steps / (total_ms / 1e3)
     kern_ms = statistics.mean(x.info.gpu_ms for x in res)
     flops = statistics.mean(x.info.maxvol_flops for x in res)
-    sm_mhz = clk.get("sm_mhz") or 2070.0
-    fp32_peak = fp32_peak_tflops(sm_mhz)
+    peaks, _ = _peaks()
+    max_mhz = float(peaks.get("sm_max_mhz") or 2070.0)
+    sms = device_sms(dev)
+    fp32_peak = fp32_pipe_peak_tflops(max_mhz, sms)
     achieved = flops / (kern_ms / 1e3) / 1e12
 
     # plain one-job-per-launch C-A on a subset of the same blocks, each at the
@@ -601,10 +710,12 @@ def run_batch(args, wl_name):
     h2d = pts.nbytes + blocks64.nbytes + jc.nbytes + sr.nbytes + sc.nbytes
     d2h = nb * (4 * 4 + 2 * 4 * lm + 8 * lm * lm + 4 * lm + 8)
     ctx.close()
-    if world > 1:
+    del flush
+    if world > 1 and not embed:
+        import torch.distributed as dist
         dist.destroy_process_group()
     if rank != 0:
-        return
+        return None
     lat = sorted(step_ms)
     line = {
         "metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": world, "steps": args.steps,
@@ -631,22 +742,17 @@ def run_batch(args, wl_name):
         "roofline": {"kernel": "batch_kernel", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": captured_traffic("k_batch.cu", f"batch_{wl_name}.md"),
-                     "peak_source": f"FP32 FMA rate: {SMS} SMs x 128 FMA/clk x median SM clock {sm_mhz:.0f} MHz",
+                     "peak_source": f"hardware FP32 pipe (nominal): {sms} SMs x 128 FMA lanes x 2 flops x max SM clock {max_mhz:.0f} MHz",
                      "note": "elimination/update FLOPs counted by the kernel; the decision chain (a CTA reduction per pivot) bounds it"},
         "gpu_launches": args.steps,
         "clocks": clk,
         "e2e": {"value": nb * len(ts) / sum(ts), "unit": "blocks/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
     }
+    if embed:
+        return line
     if world == 1:
-        try:
-            ob = run_oracle(wl_name)
-            line["cpu_baseline"] = {"value": ob["n"] / ob["total_s"], "unit": "blocks/s", "cores": 1,
-                                    "kind": "oracle",
-                                    "sample": f"{ob['n']} block(s) of the same set, FP64 numpy rank-adaptive C-A, 1 thread"}
-        except Exception as e:  # report, do not hide
-            line["cpu_baseline"] = {"value": None, "unit": "blocks/s", "cores": 1, "kind": "oracle",
-                                    "sample": f"failed: {e}"}
+        line["cpu_baseline"] = cpu_baseline(wl_name, "blocks/s", "block(s) of the same set, rank-adaptive C-A")
     print(json.dumps(line), flush=True)
 
 
@@ -722,23 +828,15 @@ def _pct(xs, q):
     return s[min(len(s) - 1, max(0, int(math.ceil(q * len(s))) - 1))]
 
 
-def run_serve(args, wl_name):
-    # more hardware work queues than CUDA's default 8, so that the jobs of
-    # 32 streams do not share queues (set before the process touches CUDA)
-    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+def run_serve(args, wl_name, embed=False):
+    """Served form; with embed, returns the measurement (rank 0) instead of
+    printing it, for the default line."""
     import numpy as np
     import torch
     import paper_1611_01391_gb300 as L
     import workloads as W
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+    world, rank, local, dev = dist_setup()
     wl = WORKLOADS[wl_name]
     seed = W.BASE_SEED + wl["seed_off"] + rank_seed_offset(rank)
     reqs = W.serving_requests(seed, wl["count"], wl["min_side"], wl["max_side"])
@@ -753,8 +851,7 @@ def run_serve(args, wl_name):
         _serve_run(L, ctx, prep, reqs, None, [0])
     clocks = ClockSampler(local)
     torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
+    dist_barrier(world)
     clocks.start()
     time.sleep(0.3)
     # capacity: closed loop (everything queued at t = 0), K repetitions
@@ -796,12 +893,16 @@ def run_serve(args, wl_name):
         plain_lat.append(time.perf_counter() - t1)
         plain_err.append(res.info.est_rel_err)
     plain_value = len(sub) / (time.perf_counter() - t0)
+    # equal error: the served results are the plain ones, bit for bit (each
+    # job's kernels run in a fixed order on its own allocation)
+    identical = all(plain_err[i] == errs_o[i] for i in range(len(sub)))
     ctx1.close()
     ctx.close()
-    if world > 1:
+    if world > 1 and not embed:
+        import torch.distributed as dist
         dist.destroy_process_group()
     if rank != 0:
-        return
+        return None
     h2d = sum(r["x"].nbytes + r["y"].nbytes + 4 * (r["l"] + len(r["rows"]) + len(r["cols"])) for r in reqs)
     d2h = sum(4 * 2 * r["l"] + 8 * r["l"] * r["l"] + 8 * r["l"] + 144 for r in reqs)
     line = {
@@ -823,12 +924,15 @@ def run_serve(args, wl_name):
                                      "note": "same requests one at a time on one stream"},
         "speedup_vs_plain": capacity / plain_value,
         "est_rel_err_max": float(max(errs)),
+        "identical_to_plain": bool(identical),
         "gpu_launches": int(launches[0]),
         "clocks": clk,
         "e2e": {"value": world * e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h),
                 "note": "closed loop; each request's points copied from pinned host memory before its submit, results fetched to the host"},
     }
+    if embed:
+        return line
     print(json.dumps(line), flush=True)
 
 
@@ -927,9 +1031,14 @@ def run_reference(args, wl_name):
     per_step = {"plain": 1, "batch": 8, "serve": 2}[form]
     unit = "blocks/s" if form == "batch" else UNIT
     total = (args.warmup + args.steps) * per_step
-    ob = run_oracle(wl_name, budget_s=1e9, min_n=total, max_n=total)
-    times = ob["times"][args.warmup * per_step:]
-    value = len(times) / sum(times)
+    procs = _oracle_procs(wl_name)
+    # one single-threaded oracle process per host core, each running the
+    # whole warm-up + timed sequence; value = sum over processes of its
+    # timed units / its timed seconds (they run at the same time)
+    recs = run_oracle_parallel(wl_name, procs, budget_s=1e9, min_n=total, max_n=total)
+    per = [r["times"][args.warmup * per_step:] for r in recs]
+    value = sum(len(t) / sum(t) for t in per)
+    times = [x for t in per for x in t]
     if form == "plain":
         cfg = {"workload": wl_name, "generator": wl["kind"], "m": wl["m"], "n": wl["n"], "k": wl["k"],
                "l": wl["l"], "sweeps": wl["sweeps"], "error_sample": f"{wl['q']}x{wl['s']}"}
@@ -937,11 +1046,12 @@ def run_reference(args, wl_name):
         cfg = {"workload": wl_name, **{k: v for k, v in wl.items() if k not in ("form", "seed_off")}}
     line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * sum(times) / len(times) * per_step,
+            "ms_per_step": 1e3 * per_step * procs / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference", "config": cfg,
-            "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
-                             "sample": f"{len(times)} unit(s) ({per_step} per step) per timed run, FP64 numpy, 1 thread"},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": procs, "kind": "oracle",
+                             "sample": (f"{len(times)} timed unit(s) ({per_step} per step) over {procs} single-threaded "
+                                        "FP64 numpy processes, one per host core, running at once")},
             "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -955,7 +1065,14 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cauchy65536")
     ap.add_argument("--profile-solves", type=int, default=0,
                     help="run this many solves and exit (the command ncu captures)")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="default workload only: skip the batched and served legs")
     args = ap.parse_args()
+    # the batched and served legs of the metric ride on the default line
+    args.legs = args.workload == "cauchy65536" and not args.no_legs
+    # more hardware work queues than CUDA's default 8, so that the jobs of
+    # the served form's 32 streams do not share queues (before CUDA starts)
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     if args.profile_solves:
         run_profile_solves(args, args.workload)
         return

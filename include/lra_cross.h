@@ -31,7 +31,10 @@
  *   - A context works on one device, on the caller's stream or on a pool of
  *     its own streams (lra_ctx_params.n_streams).  Each job runs in order on
  *     one stream; jobs on different streams overlap on the device.  Calls on
- *     one context are serialised internally.
+ *     one context are thread-safe: each holds the context's lock only for
+ *     its bookkeeping, and calls that wait for a job (wait, fetch, cancel)
+ *     wait with the lock released, so other threads keep submitting and
+ *     polling meanwhile.
  *   - All computation happens in the library's CUDA kernels; there is no
  *     CPU fallback.  Without a usable device, create fails with LRA_ECUDA.
  */
@@ -123,12 +126,21 @@ typedef struct {
   double delta;               /* maxvol stops when max |B| <= 1 + delta (> 0)       */
   double rank_tol;            /* nucleus keeps sigma_j > rank_tol * sigma_1         */
   double tol;                 /* > 0: stop after a sweep once the estimate <= tol   */
-  const int32_t* init_J;      /* host, l distinct column indices (initial J)        */
+  const int32_t* init_J;      /* host, l distinct column indices (initial J), or NULL:
+                                 J is drawn from `seed` (lra_draw_columns)          */
   int64_t resid_q, resid_s;   /* Appendix F sample size (0: no estimate)            */
   const int32_t* resid_rows;  /* host, resid_q distinct row indices                 */
   const int32_t* resid_cols;  /* host, resid_s distinct column indices              */
   int32_t trace_cap;          /* decisions to record (0: none)                      */
   int32_t flags;              /* LRA_FLAG_* bits                                    */
+  const int32_t* init_I;      /* host, l distinct row indices, or NULL.  Given: the
+                                 first vertical step is a warm start from this I
+                                 (maxvol from B = S X^{-1}) instead of Gaussian
+                                 elimination, so a run checkpointed after s sweeps
+                                 as (I, J) and resubmitted with init_I = I,
+                                 init_J = J and the remaining sweeps returns the
+                                 same I, J, U bit for bit as the uninterrupted run */
+  uint64_t seed;              /* initial-J seed, used only when init_J is NULL      */
 } lra_params;
 
 typedef struct {
@@ -177,14 +189,22 @@ typedef struct {
  * with the rank chosen per block.  Block b is the submatrix
  * M[row0 : row0 + m, col0 : col0 + n] of the source (1 <= m, n <= 2048).
  *
- * Per block (reading of the paper for blocks of unknown rank):
- *   - every strip starts from Gaussian elimination with partial pivoting and
- *     then runs maxvol swaps (FP32);
- *   - after `sweeps` sweeps, if the last pivot of the final vertical step
- *     exceeds tol x the first pivot, the cross grows (x2, <= l_max) with the
- *     next unused columns of cand_J and the sweeps repeat;
- *   - nucleus U = (X_k)^+ with k_eff = min(k_max, #{sigma_j > tol sigma_1});
- *   - Appendix F estimate on the sample rows x sample columns of the block. */
+ * Per block (reading of the paper for blocks of unknown rank; the paper's
+ * HSS test of Section 12.8 searches the rank instead):
+ *   - the cross starts at l = l_init with the first columns of cand_J;
+ *   - a sweep is a vertical and a horizontal step (Section 6.5).  Each strip
+ *     starts from B = S X^{-1} for the previous index set (computed as
+ *     Gaussian elimination whose pivots are restricted to that set; the very
+ *     first strip and the rows a grown cross lacks pivot freely) and then
+ *     runs maxvol swaps;
+ *   - after every sweep, k = #{sigma_j(M[I, J]) > tol sigma_1}.  If k = l,
+ *     k < k_max, l < min(l_max, m, n) and unused columns of cand_J remain,
+ *     the cross grows to min(2 l, l_max, m, n) with the next unused columns
+ *     and the sweeps restart at that size;
+ *   - otherwise U = (X_k)^+ with k_eff = min(k_max, k) and the Appendix F
+ *     estimate on the sample rows x sample columns are written, and the block
+ *     stops once k >= k_max, the estimate is <= tol, or `sweeps` sweeps were
+ *     made at this size. */
 typedef struct {
   int64_t row0, m;            /* rows of M in the block                             */
   int64_t col0, n;            /* columns of M in the block                          */
@@ -221,45 +241,79 @@ typedef struct {
   double* est_err;            /* n_blocks Appendix F estimates (nullable)           */
 } lra_batch_out;
 
-/* Validate and enqueue one persistent launch over all blocks (LRA_EBUSY when
- * admission fails).  Poll / wait / cancel work on the returned job. */
+/* Section 9 (far-field generators of the multipole method), with C-A
+ * iterations of Section 6.5 per block.  Validate and enqueue one persistent
+ * launch over all blocks (LRA_EBUSY when admission fails; LRA_EINVAL for a
+ * block outside the source, a side above 2048, repeated candidates).  The
+ * host arrays of params are copied before the call returns.  Poll / wait /
+ * cancel work on the returned job; per-block failures are reported in
+ * lra_batch_out.status. */
 lra_status lra_cross_submit_batch(lra_ctx* ctx, const lra_source* src, const lra_block* blocks,
                                   int32_t n_blocks, const lra_batch_params* params, lra_job* out);
 
-/* Copy the per-block results of a finished batch job, then release it. */
+/* Section 9 / Section 6.5 (Primitive Algorithm outputs per block).  Wait for
+ * the batch job, copy the per-block results into the caller's buffers (host
+ * or device per out->on_device), then release the job; the handle is invalid
+ * afterwards.  Returns the job's status (LRA_OK, or the failure that ended
+ * the launch). */
 lra_status lra_cross_fetch_batch(lra_ctx* ctx, lra_job job, const lra_batch_out* out);
 
-/* Create a context on params->device.  *out receives the handle. */
+/* Problem statement of Section 6.5 (an m x n matrix reachable entry by
+ * entry, Section 1.1): a context owns the device state of the C-A solves on
+ * params->device.  *out receives the handle.  LRA_ECUDA without a usable
+ * device (or one without cooperative launch), LRA_ENOMEM when pinned host
+ * memory cannot be had. */
 lra_status lra_cross_create(lra_ctx** out, const lra_ctx_params* params);
 
-/* Wait for every job, free all device memory and the context. */
+/* Wait for every job, free all device memory and the context.  No other
+ * call on ctx may run concurrently or follow. */
 lra_status lra_cross_destroy(lra_ctx* ctx);
 
-/* Validate, admit (slots and memory budget; LRA_EBUSY when full) and enqueue a
- * full C-A solve on the context stream.  Non-blocking: returns once the work
- * is queued.  *out receives the job handle. */
+/* Section 6.5: Primitive Algorithm inputs (target rank k, cross size l,
+ * Section 6.5 with r <= k <= l) and the C-A iterations (fixed number of
+ * sweeps, or stop once the Appendix F estimate is <= tol: step 6 of the C-A
+ * iterations).  Validate (LRA_EINVAL), admit (slots and memory budget;
+ * LRA_EBUSY when full, LRA_ETOOLARGE when a strip cannot be held on chip)
+ * and enqueue a full C-A solve on one of the context's streams.  The host
+ * arrays of params are copied before the call returns; the source stays
+ * borrowed until the job ends.  Non-blocking: returns once the work is
+ * queued.  *out receives the job handle. */
 lra_status lra_cross_submit(lra_ctx* ctx, const lra_source* src,
                             const lra_params* params, lra_job* out);
 
-/* Non-blocking: LRA_PENDING while the job runs, else LRA_OK with *out filled
- * (the job's own outcome is out->status). */
+/* Step 4/6 of the C-A iterations of Section 6.5 (has the solve finished?).
+ * Non-blocking: LRA_PENDING while the job runs, else LRA_OK with *out filled
+ * (the job's own outcome is out->status).  LRA_ENOTFOUND for an unknown or
+ * released handle. */
 lra_status lra_cross_poll(lra_ctx* ctx, lra_job job, lra_info* out);
 
-/* Blocking variant of lra_cross_poll. */
+/* Blocking variant of lra_cross_poll (waits without holding the context's
+ * lock).  The job must not be fetched or cancelled meanwhile by another
+ * thread. */
 lra_status lra_cross_wait(lra_ctx* ctx, lra_job job, lra_info* out);
 
-/* Copy I, J, U (and C, R, sigma, trace where non-NULL) of a finished job into
- * caller buffers, then release the job's slot and device memory. */
+/* Primitive Algorithm, stage 4 (Section 6.5): the outputs C = M[:, J],
+ * U = (M[I, J]_k)^+ and R = M[I, :] of a solve.  Waits for the job (without
+ * holding the context's lock: submit and poll from other threads go on),
+ * copies I, J, U (and C, R, sigma, trace where non-NULL) into the caller's
+ * buffers (host or device per out->on_device), then releases the job's slot
+ * and device memory; the handle is invalid from the moment the call starts.
+ * Returns the job's own status (the outputs are written only for LRA_OK). */
 lra_status lra_cross_fetch_cur(lra_ctx* ctx, lra_job job, const lra_cur_out* out);
 
-/* Release a job.  A job still running is first marked LRA_ECANCELED (a copy
- * on a control stream), so its kernels not yet started return at once (a batch job
- * takes no further block); then the call waits for the job's stream work to
- * end and frees it.  The handle is invalid afterwards; the job must not be
- * waited on or fetched concurrently from another thread. */
+/* Step 6 of the C-A iterations of Section 6.5 (the caller ends the
+ * iteration early).  Release a job: a job still running is first marked
+ * LRA_ECANCELED (a copy on a control stream), so its kernels not yet started
+ * return at once (a batch job takes no further block); then the call waits,
+ * without holding the context's lock, for the job's stream work to end and
+ * frees it.  The handle is invalid from the moment the call starts; the job
+ * must not be waited on concurrently from another thread.  LRA_ENOTFOUND for
+ * an unknown handle. */
 lra_status lra_cross_cancel(lra_ctx* ctx, lra_job job);
 
-/* Bytes of device memory a job with these arguments holds while admitted. */
+/* Bytes of device memory a job with these arguments holds while admitted
+ * (the measure that memory-budget admission charges).  LRA_EINVAL as for
+ * submit. */
 lra_status lra_cross_footprint(const lra_source* src, const lra_params* params,
                                uint64_t* bytes);
 
@@ -287,7 +341,12 @@ lra_status lra_cross_footprint(const lra_source* src, const lra_params* params,
  * that loads this library until exit.
  * Limits: l <= 96, and the strip must fit the shared memory of <= 160 CTAs;
  * otherwise LRA_ETOOLARGE is returned and nothing is launched.  Bad pointers
- * or sizes return LRA_EINVAL.
+ * or sizes return LRA_EINVAL, and so do strides that are not both >= 1 or
+ * that make two of the N x l elements share an address (valid:
+ * row_stride >= l * col_stride, or col_stride >= N * row_stride).
+ * Errors: each launch is checked through its own return code; LRA_ECUDA
+ * means the launch that failed and everything after it were not enqueued.
+ * The runtime's last-error state is neither read nor cleared.
  * The first call on a device (with that device current) looks up the
  * device address of the array; make that first call before any stream
  * capture.  Every call shares the one array and clears what must start at
@@ -297,6 +356,28 @@ lra_status lra_maxvol_noalloc(const float* strip, int64_t N, int32_t l,
                               int64_t row_stride, int64_t col_stride, int32_t* pos,
                               const double* xinv, double delta, int32_t max_swaps,
                               int32_t* status_out, void* stream);
+
+/* Section 12.2 (the C-A tests start from random columns): the initial
+ * column set drawn from a seed, as submit draws it when init_J is NULL.
+ * Host only (no device needed).  out: host int32[l], l distinct values of
+ * [0, n) in the order drawn.  Generator: SplitMix64 (state = seed; each draw
+ * adds 0x9E3779B97F4A7C15 to the state, then z ^= z >> 30, z *=
+ * 0xBF58476D1CE4E5B9, z ^= z >> 27, z *= 0x94D049BB133111EB, z ^= z >> 31);
+ * sample: Floyd's algorithm, for c = n - l ... n - 1 take t = draw mod
+ * (c + 1), then t if new, else c.  LRA_EINVAL unless 1 <= l <= n <= 2^30. */
+lra_status lra_draw_columns(uint64_t seed, int64_t n, int32_t l, int32_t* out);
+
+/* Section 1.1 (the matrix is reachable entry by entry): out[a * s + b] =
+ * M(rows[a], cols[b]) for a < q, b < s, as the FP32 values every kernel of
+ * the library sees (stored FP64 entries rounded to FP32; generator entries
+ * evaluated with the same FP32 operations).  rows, cols: device int32
+ * arrays; out: device float[q * s], row-major.  An index outside M gives a
+ * NaN entry and no memory access.  Enqueued on `stream` (cudaStream_t, NULL
+ * = legacy default); returns without waiting.  LRA_EINVAL for a bad source
+ * or size, LRA_ECUDA when the launch fails (checked through its own return
+ * code). */
+lra_status lra_gather_entries(const lra_source* src, const int32_t* rows, int64_t q,
+                              const int32_t* cols, int64_t s, float* out, void* stream);
 
 /* Static message for a status code. */
 const char* lra_status_str(int32_t status);

@@ -319,13 +319,15 @@ class CrossResult:
 
 def cross_approximation(src, J0, k, sweeps, delta=1e-2, rank_tol=1e-12,
                         max_swaps=None, tol=0.0, sample_rows=None,
-                        sample_cols=None, keep_trace=True):
+                        sample_cols=None, keep_trace=True, I0=None):
     """C-A iterations from the initial column set J0 (|J0| = l).
 
-    Sweep s: C = M[:, J]; on the first sweep I = GEPP rows of C; I = maxvol
-    of C from I; R = M[I, :]; J = maxvol of R^T from J.  After ``sweeps``
-    sweeps (or once the sampled estimate of the current CUR is <= tol),
-    C = M[:, J], R = M[I, :], U = (M[I, J]_k)^+."""
+    Sweep s: C = M[:, J]; on the first sweep I = GEPP rows of C (or, when a
+    row set I0 is given, I = I0: the iteration resumes from a previous
+    (I, J), each step starting from the previous index set); I = maxvol of C
+    from I; R = M[I, :]; J = maxvol of R^T from J.  After ``sweeps`` sweeps
+    (or once the sampled estimate of the current CUR is <= tol, step 6 of
+    the C-A iterations), C = M[:, J], R = M[I, :], U = (M[I, J]_k)^+."""
     J = [int(j) for j in J0]
     l = len(J)
     if not (1 <= k <= l):
@@ -334,12 +336,12 @@ def cross_approximation(src, J0, k, sweeps, delta=1e-2, rank_tol=1e-12,
     swaps = []
     history = []
     converged = True
-    I = None
+    I = None if I0 is None else [int(i) for i in I0]
     done = 0
     estimate = None
     for s in range(sweeps):
         C = columns(src, J)
-        if s == 0:
+        if s == 0 and I is None:
             I = gepp_rows(C, trace, half_step=2 * s)
         res = maxvol(C, I, delta, max_swaps, trace, half_step=2 * s)
         I = res.I
@@ -425,6 +427,43 @@ def cross_approximation_adaptive(src, J_cands, l_init, l_max, k_max, sweeps, tol
             if est["rel"] <= tol:
                 break
     return I, J, U, k_eff, sigma, l, swaps
+
+
+# ---------------------------------------------------------------------------
+# Initial column set from a seed (Section 12.2: the tests start from random
+# columns), for callers that pass a seed instead of the columns
+# ---------------------------------------------------------------------------
+
+_MASK64 = (1 << 64) - 1
+
+
+def splitmix64(state):
+    """One step of SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): returns
+    (new state, output).  The state advances by the odd constant
+    0x9E3779B97F4A7C15 (the 64-bit golden ratio); the output is the new state
+    passed through two xor-shift-multiply rounds and a final xor-shift."""
+    state = (state + 0x9E3779B97F4A7C15) & _MASK64
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+    return state, z ^ (z >> 31)
+
+
+def draw_columns(seed, n, l):
+    """l distinct values of range(n) by Floyd's sampling algorithm (Bentley
+    and Floyd, CACM 1987): for c = n - l, ..., n - 1 draw t uniform on
+    [0, c] (here: the next SplitMix64 output mod (c + 1)) and take t, or c
+    when t was already taken.  Returned in the order taken."""
+    state = int(seed) & _MASK64
+    taken = []
+    seen = set()
+    for c in range(n - l, n):
+        state, r = splitmix64(state)
+        t = r % (c + 1)
+        v = c if t in seen else t
+        seen.add(v)
+        taken.append(v)
+    return taken
 
 
 def random_cross(src, I, J, k=None, rank_tol=0.0):

@@ -55,7 +55,7 @@ class lra_params(ctypes.Structure):
                 ("init_J", ctypes.c_void_p), ("resid_q", ctypes.c_int64),
                 ("resid_s", ctypes.c_int64), ("resid_rows", ctypes.c_void_p),
                 ("resid_cols", ctypes.c_void_p), ("trace_cap", ctypes.c_int32),
-                ("flags", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("init_I", ctypes.c_void_p), ("seed", ctypes.c_uint64)]
 
 
 class lra_info(ctypes.Structure):
@@ -124,13 +124,20 @@ _submit_batch = _sig("lra_cross_submit_batch", ctypes.c_int, _ctx_p, ctypes.POIN
                      ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(lra_batch_params),
                      ctypes.POINTER(_job))
 _fetch_batch = _sig("lra_cross_fetch_batch", ctypes.c_int, _ctx_p, _job, ctypes.POINTER(lra_batch_out))
+_draw_columns = _sig("lra_draw_columns", ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32,
+                     ctypes.c_void_p)
+_gather_entries = _sig("lra_gather_entries", ctypes.c_int, ctypes.POINTER(lra_source), ctypes.c_void_p,
+                       ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p)
+_maxvol_noalloc = _sig("lra_maxvol_noalloc", ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                       ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                       ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p)
 _status_str = _sig("lra_status_str", ctypes.c_char_p, ctypes.c_int32)
 _last_error = _sig("lra_cross_last_error", ctypes.c_char_p, _ctx_p)
 
 EXPORTED = ["lra_cross_create", "lra_cross_destroy", "lra_cross_submit", "lra_cross_poll",
             "lra_cross_wait", "lra_cross_fetch_cur", "lra_cross_cancel", "lra_cross_footprint",
             "lra_status_str", "lra_cross_last_error", "lra_cross_submit_batch",
-            "lra_cross_fetch_batch"]
+            "lra_cross_fetch_batch", "lra_draw_columns", "lra_gather_entries", "lra_maxvol_noalloc"]
 
 
 class LraError(RuntimeError):
@@ -203,6 +210,29 @@ def lra_cross_submit_batch(ctx, src: lra_source, blocks, params: lra_batch_param
 
 def lra_cross_fetch_batch(ctx, job: int, out: lra_batch_out) -> int:
     return _check(_fetch_batch(ctx, job, ctypes.byref(out)), ctx)
+
+
+def lra_draw_columns(seed: int, n: int, l: int):
+    """Initial column set drawn from a seed (host only), as numpy int32[l]."""
+    import numpy as np
+    out = np.zeros(l, np.int32)
+    _check(_draw_columns(seed, n, l, out.ctypes.data))
+    return out
+
+
+def lra_gather_entries(src: lra_source, rows, cols, out, stream=None) -> None:
+    """out[a, b] = M(rows[a], cols[b]) on the device (device int32 rows/cols,
+    device float32 out of shape (len(rows), len(cols)))."""
+    _check(_gather_entries(ctypes.byref(src), rows.data_ptr(), rows.numel(), cols.data_ptr(), cols.numel(),
+                           out.data_ptr(), stream))
+
+
+def lra_maxvol_noalloc(strip_ptr, N, l, row_stride, col_stride, pos_ptr, xinv_ptr, delta, max_swaps,
+                       status_ptr, stream=None) -> int:
+    """One maxvol half-step without device allocation (raw device pointers);
+    returns the lra_status code."""
+    return _maxvol_noalloc(strip_ptr, N, l, row_stride, col_stride, pos_ptr, xinv_ptr, delta, max_swaps,
+                           status_ptr, stream)
 
 
 def lra_cross_footprint(src: lra_source, params: lra_params) -> int:

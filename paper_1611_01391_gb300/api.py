@@ -42,27 +42,33 @@ def make_source(kind: str, *, a=None, x=None, y=None, h: float = 0.0) -> lra_sou
 
 @dataclass
 class _HostArrays:
-    J0: np.ndarray
+    J0: np.ndarray | None
     rows: np.ndarray | None
     cols: np.ndarray | None
+    I0: np.ndarray | None = None
 
 
 def make_params(k, l, sweeps, init_J, *, delta=1e-2, rank_tol=1e-6, tol=0.0, max_swaps=0,
-                resid_rows=None, resid_cols=None, trace_cap=0, profile=False, full_residual=False):
-    """lra_params plus the host arrays it points to (keep both alive)."""
-    J0 = np.ascontiguousarray(init_J, dtype=np.int32)
+                resid_rows=None, resid_cols=None, trace_cap=0, profile=False, full_residual=False,
+                init_I=None, seed=0):
+    """lra_params plus the host arrays it points to (keep both alive).
+    init_J None: the library draws J from ``seed``; init_I: resume from a row set."""
+    J0 = None if init_J is None else np.ascontiguousarray(init_J, dtype=np.int32)
+    I0 = None if init_I is None else np.ascontiguousarray(init_I, dtype=np.int32)
     rows = None if resid_rows is None else np.ascontiguousarray(resid_rows, dtype=np.int32)
     cols = None if resid_cols is None else np.ascontiguousarray(resid_cols, dtype=np.int32)
     p = lra_params()
     p.k, p.l, p.sweeps, p.max_swaps = k, l, sweeps, max_swaps
     p.delta, p.rank_tol, p.tol = delta, rank_tol, tol
-    p.init_J = J0.ctypes.data
+    p.init_J = None if J0 is None else J0.ctypes.data
+    p.init_I = None if I0 is None else I0.ctypes.data
+    p.seed = int(seed)
     if rows is not None:
         p.resid_q, p.resid_s = len(rows), len(cols)
         p.resid_rows, p.resid_cols = rows.ctypes.data, cols.ctypes.data
     p.trace_cap = trace_cap
     p.flags = (1 if profile else 0) | (2 if full_residual else 0)
-    return p, _HostArrays(J0, rows, cols)
+    return p, _HostArrays(J0, rows, cols, I0)
 
 
 @dataclass

@@ -76,6 +76,21 @@ __global__ void __launch_bounds__(256) gather_rows_kernel(SourceDev s, const int
   }
 }
 
+// out[a*s + b] = M(rows[a], cols[b]): the FP32 entries every other kernel
+// of the library sees.  An index outside M gives NaN and no access.
+template <int KIND>
+__global__ void __launch_bounds__(256) gather_entries_kernel(SourceDev src, const int* __restrict__ rows,
+                                                             long long q, const int* __restrict__ cols,
+                                                             long long s, float* __restrict__ out) {
+  const long long total = q * s;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long a = e / s, b = e - a * s;
+    const long long i = __ldg(rows + a), j = __ldg(cols + b);
+    out[e] = (i >= 0 && i < src.m && j >= 0 && j < src.n) ? entry<KIND>(src, i, j) : __int_as_float(0x7fc00000);
+  }
+}
+
 static int grid_for(long long work, int per_block, int sms) {
   long long g = (work + per_block - 1) / per_block;
   const long long cap = (long long)sms * 8;
@@ -101,6 +116,19 @@ cudaError_t launch_gather_rows(const SourceDev& s, const int* I, int l, float* R
     vec_ok = vec_ok && (s.lda % 4 == 0) && ((reinterpret_cast<uintptr_t>(s.a) & 15) == 0);
   LRA_DISPATCH_KIND(s.kind, (gather_rows_kernel<K><<<grid, 256, 0, st>>>(s, I, l, R, js, vec_ok)));
   return cudaGetLastError();
+}
+
+cudaError_t launch_gather_entries(const SourceDev& s, const int* rows, long long q, const int* cols,
+                                  long long sN, float* out, cudaStream_t st) {
+  const int grid = grid_for(q * sN, 256 * 4, 152);
+  cudaError_t e = cudaSuccess;
+  SourceDev sd = s;
+  void* args[] = {&sd, const_cast<int**>(&rows), &q, const_cast<int**>(&cols), &sN, &out};
+  // launched through its own return code: the runtime's last-error state is
+  // left as the caller had it
+  LRA_DISPATCH_KIND(s.kind, (e = cudaLaunchKernel(reinterpret_cast<const void*>(gather_entries_kernel<K>),
+                                                   dim3(grid), dim3(256), args, 0, st)));
+  return e;
 }
 
 }  // namespace lra

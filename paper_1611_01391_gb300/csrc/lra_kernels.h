@@ -12,6 +12,8 @@ struct GridBarrier;
 cudaError_t launch_gather_cols(const SourceDev& s, const int* J, int l, float* C,
                                const JobStatus* js, int skip_on_stop, int sms,
                                cudaStream_t st);
+cudaError_t launch_gather_entries(const SourceDev& s, const int* rows, long long q, const int* cols,
+                                  long long sN, float* out, cudaStream_t st);
 cudaError_t launch_gather_rows(const SourceDev& s, const int* I, int l, float* R,
                                const JobStatus* js, int sms, cudaStream_t st);
 

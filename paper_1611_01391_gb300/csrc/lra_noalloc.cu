@@ -97,6 +97,12 @@ extern "C" lra_status lra_maxvol_noalloc(const float* strip, int64_t N, int32_t 
   if (!strip || !pos || !status_out) return LRA_EINVAL;
   if (l < 1 || N < l || !(delta > 0.0)) return LRA_EINVAL;
   if (l > kMaxL) return LRA_ETOOLARGE;  // scratch holds rows of at most 96 entries
+  // element (i, t) at strip[i*row_stride + t*col_stride]: both strides
+  // positive and the N x l elements distinct (rows of l entries side by
+  // side, or columns of N entries side by side), so that the kernel reads
+  // only the N*l elements the caller described
+  if (row_stride < 1 || col_stride < 1) return LRA_EINVAL;
+  if (!(row_stride >= (int64_t)l * col_stride || col_stride >= N * row_stride)) return LRA_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LRA_ECUDA;
   DeviceSetup ds;
@@ -106,8 +112,22 @@ extern "C" lra_status lra_maxvol_noalloc(const float* strip, int64_t N, int32_t 
   if (!plan_maxvol(N, l, ds.sms, ds.smem_optin, &plan)) return LRA_ETOOLARGE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   NoAllocScratch* s = static_cast<NoAllocScratch*>(ds.scratch);
-  noalloc_init_kernel<<<1, 1, 0, st>>>(s);
-  if (xinv) noalloc_split_kernel<<<(l * l + 255) / 256, 256, 0, st>>>(xinv, l * l, s);
+  // Every launch is checked through its own return code, and the call
+  // returns before enqueueing anything further when one fails.  The
+  // runtime's last-error state is neither read nor cleared here, so an
+  // error the caller left there stays the caller's.
+  {
+    void* args[] = {&s};
+    if (cudaLaunchKernel(reinterpret_cast<const void*>(noalloc_init_kernel), dim3(1), dim3(1), args, 0, st))
+      return LRA_ECUDA;
+  }
+  if (xinv) {
+    int ll = l * l;
+    void* args[] = {const_cast<double**>(&xinv), &ll, &s};
+    if (cudaLaunchKernel(reinterpret_cast<const void*>(noalloc_split_kernel), dim3((ll + 255) / 256), dim3(256),
+                         args, 0, st))
+      return LRA_ECUDA;
+  }
   MaxvolArgs a{};
   a.strip = strip;
   a.N = N;
@@ -127,6 +147,10 @@ extern "C" lra_status lra_maxvol_noalloc(const float* strip, int64_t N, int32_t 
   a.delta = delta;
   a.max_swaps = max_swaps > 0 ? max_swaps : 64 * l;
   if (launch_maxvol(a, plan, st) != cudaSuccess) return LRA_ECUDA;
-  noalloc_finish_kernel<<<1, 1, 0, st>>>(s, status_out);
-  return cudaGetLastError() == cudaSuccess ? LRA_OK : LRA_ECUDA;
+  {
+    void* args[] = {&s, &status_out};
+    if (cudaLaunchKernel(reinterpret_cast<const void*>(noalloc_finish_kernel), dim3(1), dim3(1), args, 0, st))
+      return LRA_ECUDA;
+  }
+  return LRA_OK;
 }

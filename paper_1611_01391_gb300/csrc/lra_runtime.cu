@@ -43,6 +43,7 @@ struct Job {
   int launches = 0, maxvol_launches = 0;
   bool profile = false;
   bool full_res = false;
+  bool resume = false;   // init_I given: the first vertical step warm-starts from it
   void* fr_ws = nullptr;
   std::vector<std::pair<int, cudaEvent_t>> prof;  // (kernel class, event after the launch)
   cudaStream_t stream = nullptr;  // the context stream this job runs on
@@ -80,6 +81,8 @@ struct lra_ctx {
   std::vector<cudaStream_t> streams;       // jobs are spread over these
   std::vector<int> stream_load;            // active jobs per stream
   cudaStream_t ctrl = nullptr;             // cancellations run here, beside the jobs
+  std::vector<cudaStream_t> copy_free;     // fetch copies: one stream per fetch in progress
+  std::vector<cudaStream_t> copy_all;
   int* cancel_word = nullptr;              // pinned LRA_ECANCELED, copied over a job's status
   int sms = 0;
   int max_grid = 0;  // CTAs per maxvol launch at most
@@ -129,9 +132,8 @@ lra_status cuda_fail(lra_ctx* ctx, cudaError_t e, const char* what) {
               std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-// Validation shared by submit and footprint.
-lra_status validate(const lra_source* src, const lra_params* p, std::string* why) {
-  if (!src || !p) { *why = "null argument"; return LRA_EINVAL; }
+lra_status validate_source(const lra_source* src, std::string* why) {
+  if (!src) { *why = "null source"; return LRA_EINVAL; }
   if (src->kind < LRA_DENSE_F32 || src->kind > LRA_GEN_INVDIST) { *why = "unknown source kind"; return LRA_EINVAL; }
   if (src->m < 1 || src->n < 1 || src->m > (1LL << 30) || src->n > (1LL << 30)) { *why = "bad matrix size"; return LRA_EINVAL; }
   if (src->kind <= LRA_DENSE_F64) {
@@ -141,13 +143,20 @@ lra_status validate(const lra_source* src, const lra_params* p, std::string* why
     if (src->kind != LRA_GEN_CAUCHY && (src->dim < 1 || src->dim > 3)) { *why = "dim must be 1..3"; return LRA_EINVAL; }
     if (src->kind == LRA_GEN_GAUSS && !(src->h > 0.0f)) { *why = "h must be > 0"; return LRA_EINVAL; }
   }
+  return LRA_OK;
+}
+
+// Validation shared by submit and footprint.
+lra_status validate(const lra_source* src, const lra_params* p, std::string* why) {
+  if (!src || !p) { *why = "null argument"; return LRA_EINVAL; }
+  const lra_status vs = validate_source(src, why);
+  if (vs != LRA_OK) return vs;
   if (p->l < 1 || p->l > kMaxL) { *why = "l must be in 1..96"; return LRA_EINVAL; }
   if (p->k < 1 || p->k > p->l) { *why = "k must be in 1..l"; return LRA_EINVAL; }
   if (p->l > src->m || p->l > src->n) { *why = "l exceeds min(m, n)"; return LRA_EINVAL; }
   if (p->sweeps < 1 || p->sweeps > 1000) { *why = "sweeps must be in 1..1000"; return LRA_EINVAL; }
   if (!(p->delta > 0.0)) { *why = "delta must be > 0"; return LRA_EINVAL; }
   if (!(p->rank_tol >= 0.0)) { *why = "rank_tol must be >= 0"; return LRA_EINVAL; }
-  if (!p->init_J) { *why = "init_J is required"; return LRA_EINVAL; }
   if (p->resid_q < 0 || p->resid_s < 0 || (p->resid_q > 0) != (p->resid_s > 0)) { *why = "bad sample size"; return LRA_EINVAL; }
   if (p->resid_q > 0 && (!p->resid_rows || !p->resid_cols || p->resid_q > src->m || p->resid_s > src->n)) {
     *why = "bad sample index arrays"; return LRA_EINVAL;
@@ -175,8 +184,8 @@ size_t layout_bytes(const lra_source* src, const lra_params* p, Job* j) {
   const size_t o_rows = L.take(sizeof(int) * std::max<long long>(q, 1));
   const size_t o_cols = L.take(sizeof(int) * std::max<long long>(s, 1));
   const size_t o_ring = L.take(sizeof(unsigned long long) * kWinRing);
-  const size_t prefix = L.off;
   const size_t o_I = L.take(sizeof(int) * l);
+  const size_t prefix = L.off;
   const size_t o_x0 = L.take(sizeof(float2) * l * l);
   const size_t o_x1 = L.take(sizeof(float2) * l * l);
   const size_t o_U = L.take(sizeof(double) * l * l);
@@ -216,6 +225,33 @@ size_t layout_bytes(const lra_source* src, const lra_params* p, Job* j) {
     j->prefix = prefix;
   }
   return L.off;
+}
+
+// Initial column set drawn from a seed (Section 12.2: the C-A tests start
+// from a random set of columns).  Generator: SplitMix64 (Steele, Lea and
+// Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014),
+// state = seed, each draw adds 0x9E3779B97F4A7C15 to the state and mixes it.
+// Sample: Floyd's algorithm (Bentley and Floyd, "A sample of brilliance",
+// CACM 1987) for l distinct values of [0, n): for c = n - l ... n - 1 take
+// t = draw mod (c + 1), then t if it is new, else c.  J0 lists the values in
+// the order they were taken.
+uint64_t splitmix64_next(uint64_t* state) {
+  uint64_t z = (*state += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+void draw_columns(uint64_t seed, long long n, int l, int32_t* out) {
+  uint64_t state = seed;
+  std::unordered_set<long long> taken;
+  int cnt = 0;
+  for (long long c = n - l; c < n; ++c) {
+    const long long t = (long long)(splitmix64_next(&state) % (uint64_t)(c + 1));
+    const long long v = taken.count(t) ? c : t;
+    taken.insert(v);
+    out[cnt++] = (int32_t)v;
+  }
 }
 
 bool distinct_in_range(const int32_t* v, long long count, long long bound) {
@@ -269,7 +305,14 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
   auto at = [&](const void* dev) { return hs + (static_cast<const unsigned char*>(dev) - j->dmem); };
   std::memset(hs, 0, j->prefix);
   std::memcpy(at(j->js), &init, sizeof(init));
-  std::memcpy(at(j->J), p->init_J, sizeof(int) * j->l);
+  if (p->init_J) {
+    std::memcpy(at(j->J), p->init_J, sizeof(int) * j->l);
+  } else {
+    std::vector<int32_t> J0(j->l);
+    draw_columns(p->seed, j->n, j->l, J0.data());
+    std::memcpy(at(j->J), J0.data(), sizeof(int) * j->l);
+  }
+  if (p->init_I) std::memcpy(at(j->I), p->init_I, sizeof(int) * j->l);
   if (j->q > 0) {
     std::memcpy(at(j->rows), p->resid_rows, sizeof(int) * j->q);
     std::memcpy(at(j->cols), p->resid_cols, sizeof(int) * j->s);
@@ -306,7 +349,10 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
   if ((e = cudaEventRecord(j->ev_start, st))) return e;
   for (int sw = 0; sw < j->sweeps; ++sw) {
     if ((e = launch_gather_cols(j->src, j->J, j->l, j->C, j->js, 1, ctx->sms, st)) || (e = after(kClsGather, 1))) return e;
-    col.gepp = (sw == 0);
+    // the very first vertical step starts from Gaussian elimination, unless
+    // the caller resumes from its own row set (init_I): then it is a warm
+    // start like every later one
+    col.gepp = (sw == 0 && !j->resume);
     col.half_step = 2 * sw;
     col.xin = j->xbuf0;   // inverse of A[I, J] (vertical strip's cross)
     if (!col.gepp && !self_col) {
@@ -405,6 +451,25 @@ void assign_stream(lra_ctx* ctx, Job* j) {
   j->stream_idx = (int)best;
   j->stream = ctx->streams[best];
   ctx->stream_load[best]++;
+}
+
+// A copy stream for one fetch (caller holds ctx->mu).  Fetches in
+// progress on different threads each get their own, created on first need.
+cudaStream_t take_copy_stream(lra_ctx* ctx) {
+  if (!ctx->copy_free.empty()) {
+    cudaStream_t s = ctx->copy_free.back();
+    ctx->copy_free.pop_back();
+    return s;
+  }
+  cudaStream_t s = nullptr;
+  cudaSetDevice(ctx->device);
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) return ctx->ctrl;
+  ctx->copy_all.push_back(s);
+  return s;
+}
+
+void give_copy_stream(lra_ctx* ctx, cudaStream_t s) {
+  if (s && s != ctx->ctrl) ctx->copy_free.push_back(s);
 }
 
 Job* find_job(lra_ctx* ctx, lra_job id) {
@@ -522,6 +587,10 @@ lra_status lra_cross_destroy(lra_ctx* ctx) {
       cudaStreamSynchronize(ctx->ctrl);
       cudaStreamDestroy(ctx->ctrl);
     }
+    for (cudaStream_t s : ctx->copy_all) {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
     if (ctx->cancel_word) cudaFreeHost(ctx->cancel_word);
     for (unsigned char* h : ctx->stage)
       if (h) cudaFreeHost(h);
@@ -547,7 +616,10 @@ lra_status lra_cross_submit(lra_ctx* ctx, const lra_source* src, const lra_param
   std::string why;
   lra_status s = validate(src, p, &why);
   if (s != LRA_OK) return fail(ctx, s, why);
-  if (!distinct_in_range(p->init_J, p->l, src->n)) return fail(ctx, LRA_EINVAL, "init_J must be l distinct columns");
+  if (p->init_J && !distinct_in_range(p->init_J, p->l, src->n))
+    return fail(ctx, LRA_EINVAL, "init_J must be l distinct columns");
+  if (p->init_I && !distinct_in_range(p->init_I, p->l, src->m))
+    return fail(ctx, LRA_EINVAL, "init_I must be l distinct rows");
   if (p->resid_q > 0 && (!distinct_in_range(p->resid_rows, p->resid_q, src->m) ||
                          !distinct_in_range(p->resid_cols, p->resid_s, src->n)))
     return fail(ctx, LRA_EINVAL, "residual sample indices must be distinct and in range");
@@ -560,6 +632,7 @@ lra_status lra_cross_submit(lra_ctx* ctx, const lra_source* src, const lra_param
   j->trace_cap = p->trace_cap;
   j->profile = (p->flags & LRA_FLAG_PROFILE) != 0;
   j->full_res = (p->flags & LRA_FLAG_FULL_RESIDUAL) != 0;
+  j->resume = p->init_I != nullptr;
   j->m = src->m; j->n = src->n; j->q = p->resid_q; j->s = p->resid_s;
   j->delta = p->delta; j->rank_tol = p->rank_tol; j->tol = p->tol;
   j->src = make_src(src);
@@ -634,70 +707,105 @@ lra_status lra_cross_wait(lra_ctx* ctx, lra_job id, lra_info* out) {
 }
 
 lra_status lra_cross_fetch_cur(lra_ctx* ctx, lra_job id, const lra_cur_out* out) {
-  if (ctx && out) {
-    std::lock_guard<std::mutex> lock(ctx->mu);
-    Job* j0 = find_job(ctx, id);
-    if (j0 && j0->batch) return fail(ctx, LRA_EINVAL, "batch job: use lra_cross_fetch_batch");
-  }
   if (!ctx || !out) return LRA_EINVAL;
-  std::lock_guard<std::mutex> lock(ctx->mu);
-  Job* j = find_job(ctx, id);
-  if (!j) return fail(ctx, LRA_ENOTFOUND, "unknown job");
+  // Take the job out of the table under the lock, then wait for it with the
+  // lock released: submit and poll from other threads proceed meanwhile.
+  Job* j = nullptr;
+  cudaStream_t cs = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    j = find_job(ctx, id);
+    if (!j) return fail(ctx, LRA_ENOTFOUND, "unknown job");
+    if (j->batch) return fail(ctx, LRA_EINVAL, "batch job: use lra_cross_fetch_batch");
+    ctx->jobs.erase(id);
+    cs = take_copy_stream(ctx);
+  }
   cudaSetDevice(ctx->device);
   cudaError_t e = cudaEventSynchronize(j->ev_end);
-  if (e) return cuda_fail(ctx, e, "cudaEventSynchronize");
-  const JobStatus& h = ctx->pinned[j->slot];
-  lra_status result = (lra_status)h.status;
-  if (result == LRA_OK) {
-    const int l = j->l;
-    struct Piece { void* dst; const void* src; size_t bytes; };
-    const int tl = std::min(h.trace_len, j->trace_cap);
-    Piece pieces[] = {
-        {out->I, j->I, sizeof(int) * l},
-        {out->J, j->J, sizeof(int) * l},
-        {out->U, j->U, sizeof(double) * l * l},
-        {out->sigma, j->sigma, sizeof(double) * l},
-        {out->C, j->C, sizeof(float) * (size_t)j->m * l},
-        {out->R, j->R, sizeof(float) * (size_t)j->n * l},
-        {out->trace, j->trace_i, sizeof(int) * 4 * (size_t)tl},
-        {out->trace_val, j->trace_v, sizeof(double) * (size_t)tl},
-    };
-    // the copies run on the control stream behind this job's end event only:
-    // on the job's own stream they would also wait for the jobs queued after it
-    cudaStream_t cs = ctx->ctrl ? ctx->ctrl : j->stream;
-    if (cs != j->stream) e = cudaStreamWaitEvent(cs, j->ev_end, 0);
-    for (const Piece& pc : pieces) {
-      if (e) break;
-      if (!pc.dst || pc.bytes == 0) continue;
-      e = cudaMemcpyAsync(pc.dst, pc.src, pc.bytes, cudaMemcpyDefault, cs);
-    }
-    if (!e) e = cudaStreamSynchronize(cs);
-    if (e) result = cuda_fail(ctx, e, "fetch copy");
+  lra_status result = LRA_OK;
+  std::string msg;
+  if (e) {
+    result = e == cudaErrorMemoryAllocation ? LRA_ENOMEM : LRA_ECUDA;
+    msg = std::string("cudaEventSynchronize: ") + cudaGetErrorString(e);
   } else {
-    fail(ctx, result, lra_status_str(result));
+    const JobStatus& h = ctx->pinned[j->slot];   // the slot stays this job's until released
+    result = (lra_status)h.status;
+    if (result == LRA_OK) {
+      const int l = j->l;
+      struct Piece { void* dst; const void* src; size_t bytes; };
+      const int tl = std::min(h.trace_len, j->trace_cap);
+      Piece pieces[] = {
+          {out->I, j->I, sizeof(int) * l},
+          {out->J, j->J, sizeof(int) * l},
+          {out->U, j->U, sizeof(double) * l * l},
+          {out->sigma, j->sigma, sizeof(double) * l},
+          {out->C, j->C, sizeof(float) * (size_t)j->m * l},
+          {out->R, j->R, sizeof(float) * (size_t)j->n * l},
+          {out->trace, j->trace_i, sizeof(int) * 4 * (size_t)tl},
+          {out->trace_val, j->trace_v, sizeof(double) * (size_t)tl},
+      };
+      // the job has ended: the copies run on a copy stream of the context
+      // that no other call uses meanwhile, so they wait for nothing else
+      for (const Piece& pc : pieces) {
+        if (e) break;
+        if (!pc.dst || pc.bytes == 0) continue;
+        e = cudaMemcpyAsync(pc.dst, pc.src, pc.bytes, cudaMemcpyDefault, cs);
+      }
+      if (!e) e = cudaStreamSynchronize(cs);
+      if (e) {
+        result = e == cudaErrorMemoryAllocation ? LRA_ENOMEM : LRA_ECUDA;
+        msg = std::string("fetch copy: ") + cudaGetErrorString(e);
+      }
+    } else {
+      msg = lra_status_str(result);
+    }
   }
-  ctx->jobs.erase(id);
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  give_copy_stream(ctx, cs);
   release_job(ctx, j);
+  if (result != LRA_OK) fail(ctx, result, msg);
   return result;
 }
 
 lra_status lra_cross_cancel(lra_ctx* ctx, lra_job id) {
   if (!ctx) return LRA_EINVAL;
-  std::lock_guard<std::mutex> lock(ctx->mu);
-  Job* j = find_job(ctx, id);
-  if (!j) return fail(ctx, LRA_ENOTFOUND, "unknown job");
+  Job* j = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    j = find_job(ctx, id);
+    if (!j) return fail(ctx, LRA_ENOTFOUND, "unknown job");
+    ctx->jobs.erase(id);
+    cudaSetDevice(ctx->device);
+    // a job still running is marked cancelled: a copy engine writes
+    // LRA_ECANCELED over its status word from the control stream, beside the
+    // job's queued kernels, which then return at their start (kernels already
+    // running finish)
+    if (cudaEventQuery(j->ev_end) == cudaErrorNotReady && ctx->ctrl && ctx->cancel_word)
+      cudaMemcpyAsync(&j->js->status, ctx->cancel_word, sizeof(int), cudaMemcpyHostToDevice, ctx->ctrl);
+  }
+  // wait for the job's stream work with the lock released
   cudaSetDevice(ctx->device);
-  // a job still running is marked cancelled: a copy engine writes
-  // LRA_ECANCELED over its status word from the control stream, beside the
-  // job's queued kernels, which then return at their start (kernels already
-  // running finish)
-  if (cudaEventQuery(j->ev_end) == cudaErrorNotReady && ctx->ctrl && ctx->cancel_word)
-    cudaMemcpyAsync(&j->js->status, ctx->cancel_word, sizeof(int), cudaMemcpyHostToDevice, ctx->ctrl);
-  cudaGetLastError();
   cudaEventSynchronize(j->ev_end);
-  ctx->jobs.erase(id);
+  std::lock_guard<std::mutex> lock(ctx->mu);
   release_job(ctx, j);
   return LRA_OK;
+}
+
+lra_status lra_draw_columns(uint64_t seed, int64_t n, int32_t l, int32_t* out) {
+  if (!out || n < 1 || n > (1LL << 30) || l < 1 || l > n) return LRA_EINVAL;
+  draw_columns(seed, n, l, out);
+  return LRA_OK;
+}
+
+lra_status lra_gather_entries(const lra_source* src, const int32_t* rows, int64_t q, const int32_t* cols,
+                              int64_t s, float* out, void* stream) {
+  std::string why;
+  if (validate_source(src, &why) != LRA_OK) return LRA_EINVAL;
+  if (!rows || !cols || !out || q < 0 || s < 0 || q > (1LL << 30) || s > (1LL << 30)) return LRA_EINVAL;
+  if (q == 0 || s == 0) return LRA_OK;
+  const cudaError_t e = launch_gather_entries(make_src(src), rows, q, cols, s, out,
+                                              static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? LRA_OK : (e == cudaErrorMemoryAllocation ? LRA_ENOMEM : LRA_ECUDA);
 }
 
 static lra_status validate_batch(const lra_source* src, const lra_block* blocks, int32_t nb,
@@ -863,34 +971,41 @@ lra_status lra_cross_submit_batch(lra_ctx* ctx, const lra_source* src, const lra
 
 lra_status lra_cross_fetch_batch(lra_ctx* ctx, lra_job id, const lra_batch_out* out) {
   if (!ctx || !out) return LRA_EINVAL;
-  std::lock_guard<std::mutex> lock(ctx->mu);
-  Job* j = find_job(ctx, id);
-  if (!j) return fail(ctx, LRA_ENOTFOUND, "unknown job");
-  if (!j->batch) return fail(ctx, LRA_EINVAL, "not a batch job: use lra_cross_fetch_cur");
+  Job* j = nullptr;
+  cudaStream_t cs = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    j = find_job(ctx, id);
+    if (!j) return fail(ctx, LRA_ENOTFOUND, "unknown job");
+    if (!j->batch) return fail(ctx, LRA_EINVAL, "not a batch job: use lra_cross_fetch_cur");
+    ctx->jobs.erase(id);
+    cs = take_copy_stream(ctx);
+  }
   cudaSetDevice(ctx->device);
   cudaError_t e = cudaEventSynchronize(j->ev_end);
-  if (e) return cuda_fail(ctx, e, "cudaEventSynchronize");
-  lra_status result = (lra_status)ctx->pinned[j->slot].status;
-  const size_t NB = (size_t)j->n_blocks, L = (size_t)j->b_lmax;
-  struct Piece { void* dst; const void* src; size_t bytes; };
-  Piece pieces[] = {
-      {out->status, j->b_status, sizeof(int) * NB}, {out->l, j->b_l, sizeof(int) * NB},
-      {out->k_eff, j->b_keff, sizeof(int) * NB},    {out->swaps, j->b_swaps, sizeof(int) * NB},
-      {out->I, j->b_I, sizeof(int) * NB * L},       {out->J, j->b_J, sizeof(int) * NB * L},
-      {out->U, j->b_U, sizeof(double) * NB * L * L}, {out->sigma, j->b_sigma, sizeof(float) * NB * L},
-      {out->est_err, j->b_err, sizeof(double) * NB},
-  };
-  cudaStream_t cs = ctx->ctrl ? ctx->ctrl : j->stream;  // behind this job only
-  if (cs != j->stream) e = cudaStreamWaitEvent(cs, j->ev_end, 0);
-  for (const Piece& pc : pieces) {
-    if (e) break;
-    if (!pc.dst) continue;
-    e = cudaMemcpyAsync(pc.dst, pc.src, pc.bytes, cudaMemcpyDefault, cs);
+  lra_status result = e ? LRA_ECUDA : (lra_status)ctx->pinned[j->slot].status;
+  if (!e) {
+    const size_t NB = (size_t)j->n_blocks, L = (size_t)j->b_lmax;
+    struct Piece { void* dst; const void* src; size_t bytes; };
+    Piece pieces[] = {
+        {out->status, j->b_status, sizeof(int) * NB}, {out->l, j->b_l, sizeof(int) * NB},
+        {out->k_eff, j->b_keff, sizeof(int) * NB},    {out->swaps, j->b_swaps, sizeof(int) * NB},
+        {out->I, j->b_I, sizeof(int) * NB * L},       {out->J, j->b_J, sizeof(int) * NB * L},
+        {out->U, j->b_U, sizeof(double) * NB * L * L}, {out->sigma, j->b_sigma, sizeof(float) * NB * L},
+        {out->est_err, j->b_err, sizeof(double) * NB},
+    };
+    for (const Piece& pc : pieces) {
+      if (e) break;
+      if (!pc.dst) continue;
+      e = cudaMemcpyAsync(pc.dst, pc.src, pc.bytes, cudaMemcpyDefault, cs);
+    }
+    if (!e) e = cudaStreamSynchronize(cs);
+    if (e) result = LRA_ECUDA;
   }
-  if (!e) e = cudaStreamSynchronize(cs);
-  if (e) result = cuda_fail(ctx, e, "fetch copy");
-  ctx->jobs.erase(id);
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  give_copy_stream(ctx, cs);
   release_job(ctx, j);
+  if (e) return cuda_fail(ctx, e, "fetch");
   return result;
 }
 

@@ -72,3 +72,36 @@ class SubSource:
 
     def block(self, rows, cols):
         return self.src.block(self.row0 + np.asarray(rows), self.col0 + np.asarray(cols))
+
+
+# Unit roundoff of the device's double-float arithmetic (an FP32 pair keeps
+# about 48 significant bits).
+U_DD = 2.0 ** -48
+
+
+def check_nucleus(U_dev, sigma_dev, k_dev, X32, k, tau=GPU_TAU):
+    """The device's nucleus against the oracle's for the same cross: X32 holds
+    the FP32 entries of M[I, J] at the device's own (I, J) (input-matched), so
+    the only difference is the SVD's arithmetic (double-float on the device,
+    FP64 here).  Backward-stable SVDs give |d sigma_j| <= c u sigma_1, and the
+    truncated pseudo-inverse moves by at most about c u kappa_k |U| with
+    kappa_k = sigma_1 / sigma_k; c = 64 l covers the l-term sums and the
+    Jacobi sweeps.  Returns (max |dU| / max |U|, bound)."""
+    X = np.asarray(X32, np.float64)
+    l = X.shape[0]
+    U_ref, k_ref, s_ref = O.nucleus(X, k, tau)
+    s_dev = np.asarray(sigma_dev, np.float64)
+    c = 64.0 * l
+    np.testing.assert_allclose(s_dev, s_ref, rtol=0, atol=c * U_DD * s_ref[0])
+    # the kept rank: equal unless a singular value sits at the cut
+    near_cut = np.any(np.abs(s_ref - tau * s_ref[0]) <= 1e-9 * s_ref[0])
+    if not near_cut:
+        assert k_dev == k_ref, (k_dev, k_ref)
+    if k_dev != k_ref:
+        return None, None
+    kappa = s_ref[0] / s_ref[k_ref - 1] if k_ref > 0 else 1.0
+    scale = float(np.abs(U_ref).max())
+    bound = c * U_DD * kappa
+    err = float(np.abs(np.asarray(U_dev) - U_ref).max()) / scale
+    assert err <= bound, (err, bound, kappa)
+    return err, bound

@@ -149,7 +149,6 @@ _BREAKERS = {
     "sweeps = 0": lambda L, s, p: setattr(p, "sweeps", 0),
     "delta = 0": lambda L, s, p: setattr(p, "delta", 0.0),
     "rank_tol < 0": lambda L, s, p: setattr(p, "rank_tol", -1.0),
-    "no init_J": lambda L, s, p: setattr(p, "init_J", None),
     "q without s": lambda L, s, p: setattr(p, "resid_s", 0),
     "sample > m": lambda L, s, p: setattr(p, "resid_q", 5001),
     "tol without sample": lambda L, s, p: (setattr(p, "tol", 1e-3), setattr(p, "resid_q", 0),
@@ -183,3 +182,36 @@ def test_footprint_grows_with_the_strips():
     b1 = L.lra_cross_footprint(src, params)
     grow = 4 * (5000 + 4000) * 12
     assert abs((b1 - b0) - grow) <= 2 * 256   # two 256-byte-aligned pieces
+
+
+def test_library_seed_draw_equals_the_oracle_draw():
+    """lra_draw_columns (host code of the library) and the oracle's own
+    SplitMix64 + Floyd sampling, written separately, draw the same J0."""
+    import oracle as O
+    import paper_1611_01391_gb300 as L
+    for seed, n, l in ((0, 10, 10), (1, 100, 8), (161101391, 65536, 24), (2**63 + 5, 32768, 96),
+                       (42, 1 << 30, 3)):
+        assert list(L.lra_draw_columns(seed, n, l)) == O.draw_columns(seed, n, l)
+    with pytest.raises(L.LraError):
+        L.lra_draw_columns(1, 5, 6)
+
+
+def test_noalloc_rejects_aliasing_strides_on_host():
+    """Stride rules of lra_maxvol_noalloc are checked before any CUDA call:
+    both >= 1, and the N x l elements must not share addresses."""
+    import paper_1611_01391_gb300 as L
+    fake = 256    # never dereferenced: every case below fails validation first
+    N, l = 100, 8
+    for rs, cs in ((0, 1), (8, 0), (-8, 1), (4, 1), (1, 50), (3, 2)):
+        rc = L.lra_maxvol_noalloc(fake, N, l, rs, cs, fake, None, 1e-2, 0, fake, None)
+        assert rc == L.LRA_EINVAL, (rs, cs, rc)
+
+
+def test_gather_entries_validates_on_host():
+    import paper_1611_01391_gb300 as L
+    bad = L.lra_source(L.LRA_GEN_GAUSS, 3, 100, 100, None, 0, 1, 1, 0.0)   # h = 0
+    rc = L._gather_entries(ctypes.byref(bad), 256, 4, 256, 4, 256, None)
+    assert rc == L.LRA_EINVAL
+    ok = L.lra_source(L.LRA_GEN_CAUCHY, 1, 100, 100, None, 0, 1, 1, 0.0)
+    assert L._gather_entries(ctypes.byref(ok), 256, 0, 256, 4, 256, None) == L.LRA_OK   # empty: no launch
+    assert L._gather_entries(ctypes.byref(ok), 256, -1, 256, 4, 256, None) == L.LRA_EINVAL

@@ -11,7 +11,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from tests._parity import GPU_TAU, compare_traces, error_ok, rel_fro_error, sampled_error
+from tests._parity import GPU_TAU, check_nucleus, compare_traces, error_ok, rel_fro_error, sampled_error
 
 pytestmark = pytest.mark.gpu
 
@@ -90,6 +90,12 @@ def _cauchy_case(ctx, m, n, seed):
     if div is None:
         assert list(res.I) == ref.I and list(res.J) == ref.J
         assert res.info.k_eff == ref.k_eff
+    # U and sigma element by element against the FP64 nucleus of the same
+    # cross (the Cauchy crosses have kappa ~ 1e8 in their FP32 entries)
+    X32 = src32.block(res.I, res.J)
+    s = np.linalg.svd(X32, compute_uv=False)
+    assert s[0] / s[-1] > 1e6            # the ill-conditioned case this checks
+    check_nucleus(res.U, res.sigma, res.info.k_eff, X32, 16)
     src64 = O.Cauchy(x, y, "fp64")
     ref64 = O.cross_approximation(src64, J0, k=16, sweeps=4, delta=DELTA,
                                   sample_rows=rows, sample_cols=cols)
@@ -191,6 +197,7 @@ def test_shapes_parity(ctx, m, n, l, k, sweeps):
         assert list(res.I) == ref.I and list(res.J) == ref.J
         assert res.info.k_eff == ref.k_eff
         np.testing.assert_allclose(res.sigma, ref.sigma, rtol=1e-9, atol=1e-12 * ref.sigma[0])
+    check_nucleus(res.U, res.sigma, res.info.k_eff, A[np.ix_(res.I, res.J)], k)
     A64 = A.astype(np.float64)
     assert error_ok(rel_fro_error(A64, res.C, res.U, res.R),
                     O.full_residual(O.Dense(A64), ref.C, ref.U, ref.R)[0])
@@ -304,6 +311,7 @@ def test_dense_32768_full_size_parity(ctx):
     assert ncmp >= l
     if div is None:
         assert list(res.I) == ref.I and list(res.J) == ref.J
+    check_nucleus(res.U, res.sigma, res.info.k_eff, A[np.ix_(res.I, res.J)], k)
     C, R = res.C.cpu().numpy(), res.R.cpu().numpy()
     full64 = O.full_residual(O.Dense(A), C.astype(np.float64), res.U, R.astype(np.float64))[0]
     assert res.info.full_rel_err == pytest.approx(full64, rel=2e-3)

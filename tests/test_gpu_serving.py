@@ -9,7 +9,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from tests._parity import error_ok, sampled_error
+from tests._parity import GPU_TAU, compare_traces, error_ok, sampled_error
 
 pytestmark = pytest.mark.gpu
 
@@ -63,23 +63,57 @@ def test_same_alone_and_in_the_mix():
         assert a.info.est_rel_err == b.info.est_rel_err
 
 
-def test_mix_errors_against_oracle():
-    reqs = W.serving_requests(W.BASE_SEED + 51, 6, min_side=256, max_side=2048)
-    prep = _prepare(reqs)
+def _device_entries(src, m, n):
+    """The FP32 entries of the whole m x n matrix as the device sees them."""
+    rows = torch.arange(m, dtype=torch.int32, device="cuda")
+    cols = torch.arange(n, dtype=torch.int32, device="cuda")
+    out = torch.empty((m, n), dtype=torch.float32, device="cuda")
+    L.lra_gather_entries(src, rows, cols, out)
+    return out.cpu().numpy()
+
+
+def test_mix_against_input_matched_oracle():
+    """Requests solved in the mix against the oracle fed the device's own FP32
+    entries (lra_gather_entries), generator by generator: the decision logs
+    agree up to the first unseparated decision, and the error (against the
+    FP64 entries, on the request's Appendix F sample) is within 1.05x of that
+    oracle's (or 1e-5).  For the Gaussian kernel numpy's float32 exp is not
+    CUDA's expf, so only input matching removes the spread that FP32
+    rounding of the entries causes where the rank-k truncation is ill posed."""
+    reqs = W.serving_requests(W.BASE_SEED + 51, 8, min_side=256, max_side=2048)
+    kinds = {r["kind"] for r in reqs}
+    assert {"gauss", "cauchy"} <= kinds or len(kinds) >= 2
+    prep = []
+    for r in reqs:
+        xd = torch.from_numpy(r["x"]).cuda()
+        yd = torch.from_numpy(r["y"]).cuda()
+        src = L.make_source(r["kind"], x=xd, y=yd, h=r["h"])
+        p, keep = L.make_params(r["k"], r["l"], r["sweeps"], r["J0"], resid_rows=r["rows"],
+                                resid_cols=r["cols"], trace_cap=16384)
+        prep.append((src, p, (xd, yd, keep)))
     with L.Context(0, n_streams=3) as ctx:
         jobs = [ctx.submit(src, p) for (src, p, _) in prep]
-        res = [ctx.fetch(j, r["l"], r["m"], r["n"], want_strips=True, device="cuda")
+        res = [ctx.fetch(j, r["l"], r["m"], r["n"], want_strips=True, device="cuda", trace_cap=16384)
                for j, r in zip(jobs, reqs)]
-    for g, r in zip(res, reqs):
+        ents = [_device_entries(src, r["m"], r["n"]) for (src, _, _), r in zip(prep, reqs)]
+    for g, r, A32 in zip(res, reqs, ents):
+        assert g.info.status == 0
+        matched = O.cross_approximation(O.Dense(A32), r["J0"], k=r["k"], sweeps=r["sweeps"],
+                                        rank_tol=GPU_TAU, sample_rows=r["rows"], sample_cols=r["cols"])
+        ncmp, div = compare_traces(g.trace, matched.trace, 1e-2)
+        assert ncmp >= min(r["l"], 8)
+        if div is None:
+            assert list(g.I) == matched.I and list(g.J) == matched.J
         s64 = _oracle_src(r, "fp64")
-        ref = O.cross_approximation(s64, r["J0"], k=r["k"], sweeps=r["sweeps"],
-                                    sample_rows=r["rows"], sample_cols=r["cols"])
         err = sampled_error(s64, g.C.cpu().numpy(), g.U, g.R.cpu().numpy(), r["rows"], r["cols"])
-        # the Gaussian kernel's truncation can be ill posed (sigma_k ~ sigma_k+1);
-        # there the FP32 entries alone move the oracle by up to ~15%
-        bar = 1.05 if r["kind"] != "gauss" else 1.25
-        assert err <= max(bar * ref.estimate["rel"], 1e-5), (r["kind"], r["m"], r["n"], r["k"], err,
-                                                             ref.estimate["rel"])
+        err_m = sampled_error(s64, matched.C, matched.U, matched.R, r["rows"], r["cols"])
+        assert error_ok(err, err_m), (r["kind"], r["m"], r["n"], r["k"], err, err_m)
+        if r["kind"] != "gauss":
+            # generators whose FP32 entries the oracle reproduces bit for bit:
+            # also within 1.05x of the pure-FP64 oracle
+            ref = O.cross_approximation(s64, r["J0"], k=r["k"], sweeps=r["sweeps"],
+                                        sample_rows=r["rows"], sample_cols=r["cols"])
+            assert error_ok(err, ref.estimate["rel"]), (r["kind"], err, ref.estimate["rel"])
 
 
 def test_memory_budget_admission():

@@ -68,6 +68,31 @@ MUTANTS = [
     # Appendix F: variance about zero instead of about the mean
     ("sampled_residual", "np.sum((E - mu) ** 2)", "np.sum(E ** 2)",
      [lambda: pins.test_sampled_residual_on_whole_matrix_equals_full()]),
+    # runner-up: the winner's own value instead of the second largest (every
+    # decision would then look unseparated)
+    ("_runner_up", "return float(rest.max())", "return float(values[winner])",
+     [lambda: pins.test_runner_up_of_gepp_decisions_is_second_largest_candidate(1),
+      lambda: pins.test_runner_up_of_swap_decisions_is_second_largest_entry(5)]),
+    # runner-up: the smallest remaining candidate instead of the largest
+    ("_runner_up", "return float(rest.max())", "return float(rest.min())",
+     [lambda: pins.test_runner_up_of_swap_decisions_is_second_largest_entry(6)]),
+    # tolerance stop never taken
+    ("cross_approximation", 'if estimate["rel"] <= tol:', 'if estimate["rel"] < 0.0:',
+     [lambda: pins.test_tolerance_stop_at_the_first_sweep_whose_estimate_is_below_tol()]),
+    # tolerance stop one sweep late (checks the estimate before the sweep)
+    ("cross_approximation", 'if tol > 0.0 and sample_rows is not None:',
+     'if tol > 0.0 and sample_rows is not None and s > 0:',
+     [lambda: pins.test_tolerance_stop_at_the_first_sweep_whose_estimate_is_below_tol(),
+      lambda: pins.test_tolerance_stop_on_exact_rank_after_one_sweep()]),
+    # resume: the caller's row set ignored (restart from elimination)
+    ("cross_approximation", "if s == 0 and I is None:", "if s == 0:",
+     [lambda: pins.test_resume_from_checkpoint_equals_uninterrupted_run(1)]),
+    # seed draw: last xor-shift of the mixer off by one bit
+    ("splitmix64", "return state, z ^ (z >> 31)", "return state, z ^ (z >> 30)",
+     [lambda: pins.test_splitmix64_published_outputs()]),
+    # seed draw: Floyd's replacement step dropped (repeats possible)
+    ("draw_columns", "v = c if t in seen else t", "v = t",
+     [lambda: pins.test_draw_columns_distinct_in_range(0, 10, 10)]),
     # C-A: horizontal step chooses J inside R instead of R^T
     ("cross_approximation", "maxvol(R.T, J,", "maxvol(R[:, :l], J,",
      [lambda: pins.test_exact_recovery_rank_l(90, 120, 7, 3),
@@ -80,7 +105,7 @@ def test_mutant_is_caught(idx, monkeypatch):
     name, old, new, checks = MUTANTS[idx]
     bad = _mutant(getattr(ca, name), old, new)
     monkeypatch.setattr(ca, name, bad)
-    monkeypatch.setattr(oracle, name, bad)
+    monkeypatch.setattr(oracle, name, bad, raising=hasattr(oracle, name))
     assert _run_pins(checks), f"mutant {name}: {old!r} -> {new!r} survived"
 
 

@@ -354,3 +354,148 @@ def test_adaptive_stops_on_the_sampled_estimate():
     # below tol after the first sweep, so six allowed sweeps stop after one
     assert one[5] == many[5] == 12 and one[3] == many[3] == 10
     assert one[0] == many[0] and one[1] == many[1]
+
+
+# --- The decision log's runner-up v2 (it alone decides whether a decision
+# --- counts as separated): brute force from scratch at every decision ------
+
+def _schur_candidates(S, pivots, t):
+    """|Schur complement| of column t for the rows not yet pivoted, computed
+    from scratch: S[i, t] - S[i, :t] S[P, :t]^{-1} S[P, t] with P the first t
+    pivot rows (textbook block elimination, no incremental updates)."""
+    N = S.shape[0]
+    free = [i for i in range(N) if i not in pivots[:t]]
+    if t == 0:
+        vals = S[free, 0]
+    else:
+        P = list(pivots[:t])
+        coef = np.linalg.solve(S[P, :t].T, S[free, :t].T).T
+        vals = S[free, t] - coef @ S[P, t]
+    return free, np.abs(vals)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_runner_up_of_gepp_decisions_is_second_largest_candidate(seed):
+    rng = W.rng_for(900 + seed)
+    N, l = 9 + seed, 4
+    S = rng.standard_normal((N, l))
+    trace = []
+    piv = O.gepp_rows(S, trace)
+    assert len(trace) == l
+    for t, (hs, kind, i, j, v1, v2) in enumerate(trace):
+        assert kind == O.GEPP and j == t and i == piv[t]
+        free, mag = _schur_candidates(S, piv, t)
+        order = np.argsort(-mag, kind="stable")
+        assert free[order[0]] == i
+        assert v1 == pytest.approx(mag[order[0]], rel=1e-12)
+        assert v2 == pytest.approx(mag[order[1]], rel=1e-12)
+        assert v2 < v1
+
+
+@pytest.mark.parametrize("seed", [5, 6, 7])
+def test_runner_up_of_swap_decisions_is_second_largest_entry(seed):
+    rng = W.rng_for(910 + seed)
+    N, l = 14, 3
+    S = rng.standard_normal((N, l)) * np.exp(rng.standard_normal((N, 1)))
+    I0 = [int(i) for i in np.argsort(np.linalg.norm(S, axis=1))[:l]]   # a poor start: many swaps
+    trace = []
+    O.maxvol(S, I0, delta=1e-2, trace=trace)
+    swaps = [d for d in trace if d[1] == O.SWAP]
+    assert len(swaps) >= 2
+    I = list(I0)
+    for hs, kind, i, j, v1, v2 in trace:
+        # B from scratch for the current row set, all N x l candidates
+        B = np.linalg.solve(S[I, :].T, S.T).T
+        mag = np.sort(np.abs(B).ravel())[::-1]
+        assert v1 == pytest.approx(mag[0], rel=1e-10)
+        if kind == O.SWAP:
+            assert abs(B[i, j]) == pytest.approx(mag[0], rel=1e-10)
+            assert v2 == pytest.approx(mag[1], rel=1e-10)
+            I[j] = i
+
+
+# --- Step 6 of the C-A iterations: stop once the error estimate is <= tol --
+
+def test_tolerance_stop_at_the_first_sweep_whose_estimate_is_below_tol():
+    """Recompute the Appendix F estimate of the CUR after every sweep from the
+    index sets the run passed through; the run must stop at the first sweep
+    whose estimate is <= tol and report that estimate."""
+    rng = W.rng_for(930)
+    m, n, r = 160, 140, 6
+    A = rng.standard_normal((m, r)) @ rng.standard_normal((r, n)) + 1e-6 * rng.standard_normal((m, n))
+    src = O.Dense(A)
+    J0 = W.draw_indices(931, n, r)
+    rows, cols = np.arange(0, m, 2), np.arange(0, n, 2)
+    full = O.cross_approximation(src, J0, k=r, sweeps=6, sample_rows=rows, sample_cols=cols,
+                                 keep_trace=False)
+    ests = []
+    for I, J in full.history:
+        U, _, _ = O.nucleus(src.block(I, J), r)
+        ests.append(O.sampled_residual(src, O.columns(src, J), U, O.rows(src, I), rows, cols)["rel"])
+    for tol in (ests[0] * 1.5, min(ests) * 1.0000001, min(ests) * 0.5):
+        run = O.cross_approximation(src, J0, k=r, sweeps=6, tol=tol, sample_rows=rows,
+                                    sample_cols=cols, keep_trace=False)
+        below = [s for s, e in enumerate(ests) if e <= tol]
+        expect = below[0] + 1 if below else 6
+        assert run.sweeps_done == expect, (tol, ests)
+        assert (run.I, run.J) == tuple(full.history[expect - 1])
+        assert run.estimate["rel"] == pytest.approx(ests[expect - 1], rel=1e-12)
+
+
+def test_tolerance_stop_on_exact_rank_after_one_sweep():
+    A = _rank_l(932, 120, 100, 8)
+    rows, cols = np.arange(0, 120, 4), np.arange(0, 100, 4)
+    run = O.cross_approximation(O.Dense(A), W.draw_indices(933, 100, 8), k=8, sweeps=5, tol=1e-10,
+                                sample_rows=rows, sample_cols=cols)
+    assert run.sweeps_done == 1 and run.estimate["rel"] <= 1e-10
+
+
+# --- Resume from a checkpoint (I, J): the same result as the uninterrupted run
+
+@pytest.mark.parametrize("cut", [1, 2, 3])
+def test_resume_from_checkpoint_equals_uninterrupted_run(cut):
+    x, y = W.cauchy_points(940, 700, 650)
+    src = O.Cauchy(x, y, "fp64")
+    J0 = W.draw_indices(941, 650, 10)
+    whole = O.cross_approximation(src, J0, k=8, sweeps=4)
+    first = O.cross_approximation(src, J0, k=8, sweeps=cut)
+    rest = O.cross_approximation(src, first.J, k=8, sweeps=4 - cut, I0=first.I)
+    assert rest.I == whole.I and rest.J == whole.J
+    np.testing.assert_array_equal(rest.U, whole.U)
+    # the resumed log is the tail of the uninterrupted one (minus the GEPP start)
+    tail = [d[1:] for d in whole.trace if d[0] >= 2 * cut]
+    assert [d[1:] for d in rest.trace] == tail
+
+
+# --- Initial column set from a seed: SplitMix64 + Floyd sampling -------------
+
+def test_splitmix64_published_outputs():
+    vals = [int(v, 16) for v in open(os.path.join(GOLDEN, "splitmix64_seed0.txt"))
+            if v.strip() and not v.startswith("#")]
+    state, out = 0, []
+    for _ in vals:
+        state, z = O.splitmix64(state)
+        out.append(z)
+    assert out == vals
+
+
+@pytest.mark.parametrize("seed,n,l", [(0, 10, 10), (1, 100, 8), (7, 65536, 24), (99, 5, 1)])
+def test_draw_columns_distinct_in_range(seed, n, l):
+    J = O.draw_columns(seed, n, l)
+    assert len(J) == l and len(set(J)) == l and min(J) >= 0 and max(J) < n
+    if l == n:
+        assert sorted(J) == list(range(n))
+
+
+def test_draw_columns_subsets_are_uniform():
+    """Floyd's algorithm draws every l-subset with probability 1/C(n, l):
+    chi-square over the 10 subsets of size 2 of range(5)."""
+    counts = {}
+    trials = 20000
+    for seed in range(trials):
+        key = tuple(sorted(O.draw_columns(seed, 5, 2)))
+        counts[key] = counts.get(key, 0) + 1
+    assert len(counts) == 10
+    expect = trials / 10
+    chi2 = sum((c - expect) ** 2 / expect for c in counts.values())
+    assert chi2 < 27.9          # 9 degrees of freedom, p = 0.001
