@@ -40,6 +40,7 @@
 
 #include "lra_internal.cuh"
 #include "lra_kernels.h"
+#include "tma.cuh"
 
 namespace lra {
 namespace {
@@ -176,65 +177,7 @@ __global__ void __launch_bounds__(128) split_rt_kernel(const float* __restrict__
 // PTX wrappers: mbarrier, TMA, tcgen05
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait on a phase parity; false (and *err set) after 2 s or when
-// another role already failed.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* err) {
-  if (mbar_try(bar, parity)) return true;
-  const unsigned long long t0 = globaltimer_ns();
-  while (!mbar_try(bar, parity)) {
-    if (*err) return false;
-    if (globaltimer_ns() - t0 > kWaitNs) {
-      *err = 1;
-      return false;
-    }
-  }
-  return true;
-}
-
-// Bounded wait that ignores the error flag: used to let in-flight copies
-// land before the CTA exits.
-__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
-  const unsigned long long t0 = globaltimer_ns();
-  while (!mbar_try(bar, parity))
-    if (globaltimer_ns() - t0 > kWaitNs) return;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
+using namespace tma;
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
 // 128 bytes, 8-row atoms 1024 bytes apart (stride byte offset), version 1.
@@ -346,7 +289,7 @@ fullres_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       mbar_init(&fb->t_empty[b], 4);
     }
     fb->err = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_fence_init();
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -369,8 +312,8 @@ fullres_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         if (!mbar_wait(&fb->p_empty, (ic & 1) ^ 1, err)) break;
         mbar_expect_tx(&fb->p_full, 2 * p_bytes);
         for (int k = 0; k < kb; ++k) {
-          tma_load_2d(sPhi + k * kBM * 128, &tmPhi, k * kKBox, rb * kBM, &fb->p_full);
-          tma_load_2d(sPlo + k * kBM * 128, &tmPlo, k * kKBox, rb * kBM, &fb->p_full);
+          load_2d(sPhi + k * kBM * 128, &tmPhi, k * kKBox, rb * kBM, &fb->p_full);
+          load_2d(sPlo + k * kBM * 128, &tmPlo, k * kKBox, rb * kBM, &fb->p_full);
         }
         ++p_issued;
         const int t0 = cg * kTilesPerItem, t1 = min(a.n_col_tiles, t0 + kTilesPerItem);
@@ -381,11 +324,11 @@ fullres_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           unsigned char* st = sStage + s * stage_bytes;
           mbar_expect_tx(&fb->full[s], stage_bytes);
           for (int k = 0; k < kb; ++k) {
-            tma_load_2d(st + k * kBN * 128, &tmRhi, k * kKBox, tile * kBN, &fb->full[s]);
-            tma_load_2d(st + r_bytes + k * kBN * 128, &tmRlo, k * kKBox, tile * kBN, &fb->full[s]);
+            load_2d(st + k * kBN * 128, &tmRhi, k * kKBox, tile * kBN, &fb->full[s]);
+            load_2d(st + r_bytes + k * kBN * 128, &tmRlo, k * kKBox, tile * kBN, &fb->full[s]);
           }
           for (int c = 0; c < 2; ++c)
-            tma_load_2d(st + 2 * r_bytes + c * kBM * 128, &tmA, tile * kBN + c * 32, rb * kBM,
+            load_2d(st + 2 * r_bytes + c * kBM * 128, &tmA, tile * kBN + c * 32, rb * kBM,
                         &fb->full[s]);
         }
       }
@@ -531,30 +474,10 @@ __global__ void fullres_final_kernel(const double* __restrict__ partials, int nb
   js->full_rel = sa > 0.0 ? sqrt(se / sa) : INFINITY;
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
 bool make_map(CUtensorMap* map, CUtensorMapDataType dt, const void* gaddr, uint64_t inner,
               uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
-  auto fn = encode_fn();
-  if (!fn) return false;
-  const cuuint64_t dims[2] = {inner, outer};
-  const cuuint64_t strides[1] = {row_bytes};
-  const cuuint32_t box[2] = {box_inner, box_outer};
-  const cuuint32_t estr[2] = {1, 1};
-  return fn(map, dt, 2, const_cast<void*>(gaddr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return make_map_2d(map, dt, gaddr, inner, outer, row_bytes, box_inner, box_outer, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B);
 }
 
 }  // namespace

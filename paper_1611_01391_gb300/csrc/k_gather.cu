@@ -4,6 +4,9 @@
 // every entry is evaluated on the fly from the point coordinates.
 #include "lra_kernels.h"
 #include "lra_internal.cuh"
+#include "tma.cuh"
+
+#include <algorithm>
 
 namespace lra {
 
@@ -89,6 +92,153 @@ __global__ void __launch_bounds__(256) gather_entries_kernel(SourceDev src, cons
     const long long i = __ldg(rows + a), j = __ldg(cols + b);
     out[e] = (i >= 0 && i < src.m && j >= 0 && j < src.n) ? entry<KIND>(src, i, j) : __int_as_float(0x7fc00000);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Stored FP32 M: C = M[:, J] with tiles moved by the Tensor Memory
+// Accelerator.  A column gather from a row-major matrix reads one 32-byte
+// sector per entry (unless columns share a sector), so the DRAM floor is
+// m x (distinct sectors of J) x 32 bytes.  Each CTA
+//   1. sorts J's sectors (j >> 3) and keeps each distinct one once: columns
+//      that share a sector share its load;
+//   2. streams row tiles of kColsTmaRows rows: per distinct sector one TMA box
+//      of 8 FP32 x kColsTmaRows rows (the sector column of the tile), into a
+//      ring of `stages` shared-memory buffers guarded by mbarriers (the
+//      tensor map asks for no L2 promotion, so the reads stay sector-sized);
+//   3. transposes through shared memory: the tile's rows of C, contiguous in
+//      C, are written with 16-byte stores, C[r][t] = box(slot[t])[r][J[t] & 7].
+// Grid: one persistent CTA per SM over the row tiles.  Every mbarrier wait
+// is bounded (2 s, then LRA_ETIMEOUT); the CTA waits for its copies in
+// flight before it returns.
+// ---------------------------------------------------------------------------
+
+constexpr int kColsTmaRows = 16;       // rows per tile
+constexpr int kColsTmaThreads = 256;
+constexpr int kColsTmaMaxStages = 8;
+constexpr int kColsTmaSmemBudget = 192 * 1024;
+
+__global__ void __launch_bounds__(kColsTmaThreads, 1)
+gather_cols_tma_kernel(const __grid_constant__ CUtensorMap tm, const int* __restrict__ J, int l, long long m,
+                       float* __restrict__ C, JobStatus* js, int skip_on_stop, int stages) {
+  if (js->status != LRA_OK || (skip_on_stop && js->stop)) return;
+  extern __shared__ __align__(128) unsigned char csm[];
+  __shared__ uint64_t full[kColsTmaMaxStages];
+  __shared__ int sec[kMaxL], first[kMaxL], slot[kMaxL], off[kMaxL], secs[kMaxL];
+  __shared__ int nsec_s;
+  __shared__ int err;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* ring = reinterpret_cast<float*>(csm);
+  // ---- distinct sectors of J, in increasing order
+  if (tid == 0) {
+    nsec_s = 0;
+    err = 0;
+  }
+  for (int t = tid; t < l; t += kColsTmaThreads) {
+    const int j = __ldg(J + t);
+    sec[t] = j >> 3;
+    off[t] = j & 7;
+  }
+  __syncthreads();
+  for (int t = tid; t < l; t += kColsTmaThreads) {
+    int f = 1;
+    for (int u = 0; u < t; ++u) f &= (sec[u] != sec[t]);
+    first[t] = f;
+    if (f) atomicAdd(&nsec_s, 1);
+  }
+  __syncthreads();
+  for (int t = tid; t < l; t += kColsTmaThreads) {
+    int rank = 0;
+    for (int u = 0; u < l; ++u) rank += (first[u] && sec[u] < sec[t]);
+    slot[t] = rank;
+    if (first[t]) secs[rank] = sec[t];
+  }
+  if (tid == 0) {
+    for (int s = 0; s < stages; ++s) tma::mbar_init(&full[s], 1);
+    tma::mbar_fence_init();
+  }
+  __syncthreads();
+  const int nsec = nsec_s;
+  const int stage_floats = nsec * kColsTmaRows * 8;
+  const uint32_t stage_bytes = (uint32_t)stage_floats * 4u;
+  const long long ntiles = (m + kColsTmaRows - 1) / kColsTmaRows;
+  const long long G = gridDim.x;
+  // warp 0 fills stage `it % stages` with tile blockIdx.x + it G
+  auto issue = [&](long long it) {
+    const long long tile = blockIdx.x + it * G;
+    if (tile >= ntiles) return;
+    const int s = (int)(it % stages);
+    if (lane == 0) tma::mbar_expect_tx(&full[s], stage_bytes);
+    __syncwarp();
+    float* dst = ring + (size_t)s * stage_floats;
+    for (int k = lane; k < nsec; k += 32)
+      tma::load_2d(dst + (size_t)k * kColsTmaRows * 8, &tm, secs[k] * 8, (int)(tile * kColsTmaRows), &full[s]);
+  };
+  if (warp == 0)
+    for (int it = 0; it < stages; ++it) issue(it);
+  const bool vec = (l & 3) == 0;
+  long long it = 0;
+  for (;; ++it) {
+    const long long tile = blockIdx.x + it * G;
+    if (tile >= ntiles) break;
+    const int s = (int)(it % stages);
+    const bool ok = tma::mbar_wait(&full[s], (uint32_t)((it / stages) & 1), &err);
+    if (__syncthreads_or(!ok)) break;   // the whole CTA leaves together
+    const float* st = ring + (size_t)s * stage_floats;
+    const long long r0 = tile * kColsTmaRows;
+    const int rows = (int)min((long long)kColsTmaRows, m - r0);
+    const int count = rows * l;
+    float* out = C + r0 * l;
+    if (vec) {
+      for (int e4 = tid * 4; e4 < count; e4 += kColsTmaThreads * 4) {
+        float v[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int e = e4 + c;
+          const int r = e / l, t = e - r * l;
+          v[c] = st[(slot[t] * kColsTmaRows + r) * 8 + off[t]];
+        }
+        *reinterpret_cast<float4*>(out + e4) = make_float4(v[0], v[1], v[2], v[3]);
+      }
+    } else {
+      for (int e = tid; e < count; e += kColsTmaThreads) {
+        const int r = e / l, t = e - r * l;
+        out[e] = st[(slot[t] * kColsTmaRows + r) * 8 + off[t]];
+      }
+    }
+    __syncthreads();   // every thread is done with stage s
+    if (warp == 0) issue(it + stages);
+  }
+  // copies still in flight (an error ended the loop early): let them land
+  if (warp == 0 && lane == 0) {
+    for (long long k = it; k < it + stages; ++k) {
+      if (blockIdx.x + k * G >= ntiles) break;
+      tma::mbar_drain(&full[k % stages], (uint32_t)((k / stages) & 1));
+    }
+    if (err) set_status(js, LRA_ETIMEOUT);
+  }
+}
+
+bool make_cols_map(TmaMap* map, const float* a, long long m, long long n, long long lda) {
+  static_assert(sizeof(TmaMap) == sizeof(CUtensorMap), "TmaMap holds a CUtensorMap");
+  if ((reinterpret_cast<uintptr_t>(a) & 15) != 0 || (lda & 3) != 0) return false;
+  return tma::make_map_2d(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, a, (uint64_t)n,
+                          (uint64_t)m, (uint64_t)lda * 4, 8, kColsTmaRows, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_NONE);
+}
+
+cudaError_t launch_gather_cols_tma(const TmaMap& map, const int* J, int l, long long m, float* C, JobStatus* js,
+                                   int skip_on_stop, int sms, cudaStream_t st) {
+  const size_t stage_max = (size_t)l * kColsTmaRows * 8 * sizeof(float);   // at most l distinct sectors
+  int stages = (int)std::min<size_t>(kColsTmaMaxStages, kColsTmaSmemBudget / stage_max);
+  if (stages < 2) stages = 2;
+  const size_t smem = (size_t)stages * stage_max;
+  cudaError_t e = smem_optin(reinterpret_cast<const void*>(gather_cols_tma_kernel), (int)smem);
+  if (e) return e;
+  const long long ntiles = (m + kColsTmaRows - 1) / kColsTmaRows;
+  const int grid = (int)std::max<long long>(1, std::min<long long>(ntiles, sms));
+  gather_cols_tma_kernel<<<grid, kColsTmaThreads, smem, st>>>(*reinterpret_cast<const CUtensorMap*>(&map), J, l,
+                                                              m, C, js, skip_on_stop, stages);
+  return cudaGetLastError();
 }
 
 static int grid_for(long long work, int per_block, int sms) {

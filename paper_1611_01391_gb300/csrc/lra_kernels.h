@@ -12,6 +12,17 @@ struct GridBarrier;
 cudaError_t launch_gather_cols(const SourceDev& s, const int* J, int l, float* C,
                                const JobStatus* js, int skip_on_stop, int sms,
                                cudaStream_t st);
+// Opaque copy of a CUtensorMap (128 bytes, 64-byte aligned), so that
+// translation units without the driver header can hold one.
+struct alignas(64) TmaMap {
+  unsigned char bytes[128];
+};
+// Tensor map of a stored FP32 matrix for launch_gather_cols_tma (false when
+// the base is not 16-byte aligned, lda is not a multiple of 4, or encoding
+// fails).
+bool make_cols_map(TmaMap* map, const float* a, long long m, long long n, long long lda);
+cudaError_t launch_gather_cols_tma(const TmaMap& map, const int* J, int l, long long m, float* C, JobStatus* js,
+                                   int skip_on_stop, int sms, cudaStream_t st);
 cudaError_t launch_gather_entries(const SourceDev& s, const int* rows, long long q, const int* cols,
                                   long long sN, float* out, cudaStream_t st);
 cudaError_t launch_gather_rows(const SourceDev& s, const int* I, int l, float* R,

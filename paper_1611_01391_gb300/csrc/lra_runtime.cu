@@ -44,6 +44,8 @@ struct Job {
   bool profile = false;
   bool full_res = false;
   bool resume = false;   // init_I given: the first vertical step warm-starts from it
+  bool tma_cols = false;  // stored FP32 source: column gathers through TMA
+  TmaMap col_map{};
   void* fr_ws = nullptr;
   std::vector<std::pair<int, cudaEvent_t>> prof;  // (kernel class, event after the launch)
   cudaStream_t stream = nullptr;  // the context stream this job runs on
@@ -346,9 +348,16 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
   const bool self_row = !one_sm && j->plan_row.stage_xinv;
   col.self_inverse = self_col;
   row.self_inverse = self_row;
+  // C = M[:, J]: through TMA tiles for a stored FP32 matrix, else entry by entry
+  auto gather_c = [&](int skip_on_stop) -> cudaError_t {
+    cudaError_t r = j->tma_cols
+                        ? launch_gather_cols_tma(j->col_map, j->J, j->l, j->m, j->C, j->js, skip_on_stop, ctx->sms, st)
+                        : launch_gather_cols(j->src, j->J, j->l, j->C, j->js, skip_on_stop, ctx->sms, st);
+    return r ? r : after(kClsGather, 1);
+  };
   if ((e = cudaEventRecord(j->ev_start, st))) return e;
   for (int sw = 0; sw < j->sweeps; ++sw) {
-    if ((e = launch_gather_cols(j->src, j->J, j->l, j->C, j->js, 1, ctx->sms, st)) || (e = after(kClsGather, 1))) return e;
+    if ((e = gather_c(1))) return e;
     // the very first vertical step starts from Gaussian elimination, unless
     // the caller resumes from its own row set (init_I): then it is a warm
     // start like every later one
@@ -369,7 +378,7 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
     row.count_sweep = 1;   // the sweep is counted by the row maxvol that completes it
     if ((e = launch_maxvol(row, j->plan_row, st)) || (e = after(kClsMaxvol, 1))) return e;
     if (j->tol > 0.0 && sw + 1 < j->sweeps) {
-      if ((e = launch_gather_cols(j->src, j->J, j->l, j->C, j->js, 1, ctx->sms, st)) || (e = after(kClsGather, 1))) return e;
+      if ((e = gather_c(1))) return e;
       if ((e = launch_nucleus(j->C, j->I, j->l, j->k, j->rank_tol, j->U, j->sigma, j->js, st)) || (e = after(kClsCross, 1))) return e;
       if ((e = launch_sampled_residual(j->src, j->rows, (int)j->q, j->cols, (int)j->s, j->l, j->C, j->U,
                                        j->R, j->CUq, j->partials, j->n_partials, j->js, st)) ||
@@ -378,7 +387,7 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
     }
   }
   // final strips for the returned CUR: C = M[:, J] (R = M[I, :] is current)
-  if ((e = launch_gather_cols(j->src, j->J, j->l, j->C, j->js, 0, ctx->sms, st)) || (e = after(kClsGather, 1))) return e;
+  if ((e = gather_c(0))) return e;
   if ((e = launch_nucleus(j->C, j->I, j->l, j->k, j->rank_tol, j->U, j->sigma, j->js, st)) || (e = after(kClsCross, 1))) return e;
   if (j->full_res) {
     if ((e = launch_full_residual(static_cast<const float*>(j->src.a), j->src.lda, j->m, j->n, j->l, j->C,
@@ -633,6 +642,8 @@ lra_status lra_cross_submit(lra_ctx* ctx, const lra_source* src, const lra_param
   j->profile = (p->flags & LRA_FLAG_PROFILE) != 0;
   j->full_res = (p->flags & LRA_FLAG_FULL_RESIDUAL) != 0;
   j->resume = p->init_I != nullptr;
+  if (src->kind == LRA_DENSE_F32)
+    j->tma_cols = make_cols_map(&j->col_map, static_cast<const float*>(src->a), src->m, src->n, src->lda);
   j->m = src->m; j->n = src->n; j->q = p->resid_q; j->s = p->resid_s;
   j->delta = p->delta; j->rank_tol = p->rank_tol; j->tol = p->tol;
   j->src = make_src(src);

@@ -187,20 +187,29 @@ def test_fetch_of_a_long_job_does_not_block_other_threads():
     A = torch.from_numpy(W.lowrank_svd(W.BASE_SEED + 71).astype(np.float32)).to(DEV)
     small = L.make_source("dense", a=A)
     with L.Context(0, n_streams=2) as c:
-        p_long, k1 = L.make_params(16, 24, 300, W.draw_indices(72, 65536, 24))
+        p_long, k1 = L.make_params(64, 96, 200, W.draw_indices(72, 65536, 96))
         p_small, k2 = L.make_params(8, 8, 1, W.draw_indices(73, 256, 8))
         c.solve(small, p_small, 8)          # warm-up (kernel modules loaded)
+        t0 = time.perf_counter()
+        alone = c.solve(src, p_long, 96)
+        t_long = time.perf_counter() - t0
+        assert alone.info.status == 0
+        assert t_long > 0.1, t_long          # long enough to overlap with
         job = c.submit(src, p_long)
         t = {}
+        waiting = threading.Event()
 
         def fetch_long():
             t["fetch_start"] = time.perf_counter()
-            c.fetch(job, 24)
+            waiting.set()
+            r = c.fetch(job, 96)
             t["long_done"] = time.perf_counter()
+            t["long_status"] = r.info.status
 
         th = threading.Thread(target=fetch_long)
         th.start()
-        time.sleep(0.02)                     # the fetching thread is now waiting
+        waiting.wait()
+        time.sleep(0.005)                    # the fetching thread is inside fetch_cur
         t0 = time.perf_counter()
         j2 = c.submit(small, p_small)
         t["submitted"] = time.perf_counter()
@@ -211,7 +220,33 @@ def test_fetch_of_a_long_job_does_not_block_other_threads():
         t["small_done"] = time.perf_counter()
         r2 = c.fetch(j2, 8)
         th.join()
-        assert r2.info.status == 0 and info.status == 0
-        assert "long_done" in t
-        assert t["small_done"] < t["long_done"], t
-        assert t["submitted"] - t0 < 0.5 * (t["long_done"] - t["fetch_start"]), t
+        assert r2.info.status == 0 and info.status == 0 and t["long_status"] == 0
+        assert t["small_done"] < t["long_done"], (t, t_long)
+        assert t["submitted"] - t0 < 0.25 * t_long, (t, t_long)
+
+
+@pytest.mark.parametrize("m,n,lda,l", [
+    (5000, 96, 96, 96),        # every column: all sectors shared, l % 4 == 0
+    (4099, 90, 92, 90),        # every column, padded rows, partial last sector, l % 4 != 0
+    (20001, 4096, 4100, 24),   # ragged last row tile, padded rows
+    (1037, 3000, 3000, 7),     # odd l: scalar stores
+    (33, 200, 256, 1),         # one column, fewer rows than two tiles
+])
+def test_stored_column_gather_is_bit_exact(ctx, m, n, lda, l):
+    """C = M[:, J] of a stored FP32 matrix (TMA row tiles of the distinct
+    32-byte sectors of J, transposed in shared memory) is an exact copy, for
+    padded row pitches, ragged row tiles, shared and partial sectors."""
+    rng = np.random.default_rng(m + n + l)
+    full = rng.standard_normal((m, lda)).astype(np.float32)
+    dev = torch.from_numpy(full).to(DEV)[:, :n]
+    assert dev.stride(0) == lda
+    src = L.make_source("dense", a=dev)
+    J0 = W.draw_indices(m + l, n, l)
+    p, kp = L.make_params(l, l, 2, J0)
+    res = ctx.solve(src, p, l, m, n, want_strips=True, device=DEV)
+    assert res.info.status == 0
+    A = full[:, :n]
+    np.testing.assert_array_equal(res.C.cpu().numpy(), A[:, res.J])
+    np.testing.assert_array_equal(res.R.cpu().numpy(), A[res.I, :])
+    if l == n:
+        assert sorted(res.J.tolist()) == list(range(n))
