@@ -194,9 +194,10 @@ typedef struct {
  *   - the cross starts at l = l_init with the first columns of cand_J;
  *   - a sweep is a vertical and a horizontal step (Section 6.5).  Each strip
  *     starts from B = S X^{-1} for the previous index set (computed as
- *     Gaussian elimination whose pivots are restricted to that set; the very
+ *     Gaussian elimination with partial pivoting whose pivots are restricted
+ *     to that set, step t placing its pivot row in position t; the very
  *     first strip and the rows a grown cross lacks pivot freely) and then
- *     runs maxvol swaps;
+ *     runs maxvol swaps, in double-float arithmetic;
  *   - after every sweep, k = #{sigma_j(M[I, J]) > tol sigma_1}.  If k = l,
  *     k < k_max, l < min(l_max, m, n) and unused columns of cand_J remain,
  *     the cross grows to min(2 l, l_max, m, n) with the next unused columns
@@ -223,6 +224,7 @@ typedef struct {
   const int32_t* sample_rows; /* host, n_blocks x q local rows (nullable if q = 0)  */
   const int32_t* sample_cols; /* host, n_blocks x q local columns                   */
   int32_t flags;              /* reserved, 0                                        */
+  int32_t trace_cap;          /* decisions logged per block (0: none), <= 2^20      */
 } lra_batch_params;
 
 typedef struct {
@@ -239,6 +241,11 @@ typedef struct {
                                  would dominate the error of C U R              */
   float* sigma;               /* n_blocks x l_max singular values of the cross (nullable) */
   double* est_err;            /* n_blocks Appendix F estimates (nullable)           */
+  int32_t* trace_len;         /* n_blocks decisions logged (nullable; trace_cap > 0) */
+  int32_t* trace;             /* n_blocks x trace_cap x 4: half_step, kind, i, j
+                                 (local strip row and position), as lra_cur_out.trace;
+                                 half-steps count from 0 per block (nullable)     */
+  double* trace_val;          /* n_blocks x trace_cap: |value| of each decision (nullable) */
 } lra_batch_out;
 
 /* Section 9 (far-field generators of the multipole method), with C-A

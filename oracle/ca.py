@@ -373,16 +373,18 @@ def cross_approximation(src, J0, k, sweeps, delta=1e-2, rank_tol=1e-12,
 
 def cross_approximation_adaptive(src, J_cands, l_init, l_max, k_max, sweeps, tol,
                                  delta=1e-2, max_swaps=None, sample_rows=None,
-                                 sample_cols=None):
+                                 sample_cols=None, trace=None):
     """Rank-adaptive C-A for blocks whose rank is not known in advance (the
     far-field blocks of Section 9; the paper's HSS test finds the rank by a
     search, this is the growth rule read for it).
 
     The cross starts at l = l_init with the first candidate columns.  Each
-    sweep is a vertical step (I = maxvol of M[:, J], started from the
-    previous I; the very first one, and the rows a grown cross lacks, come
-    from Gaussian elimination with partial pivoting) and a horizontal step
-    (J = maxvol of M[I, :]^T started from J).  After every sweep,
+    sweep is a vertical step (I = maxvol of M[:, J]) and a horizontal step
+    (J = maxvol of M[I, :]^T).  Every strip starts from the previous index
+    set: Gaussian elimination with partial pivoting whose pivots are
+    restricted to that set (so B = S X^{-1} for the previous rows, with
+    position t holding the pivot row of step t); the very first strip, and
+    the rows a grown cross lacks, pivot freely.  After every sweep,
     k = #{sigma_j(M[I, J]) > tol sigma_1}:
       * k = l < k_max and l < l_max: the cross grows to min(l_max, 2 l) with
         the next unused candidate columns appended to J;
@@ -390,6 +392,9 @@ def cross_approximation_adaptive(src, J_cands, l_init, l_max, k_max, sweeps, tol
         iteration stops once k >= k_max, ``sweeps`` sweeps were made at this
         size, or the Appendix F estimate on (sample_rows, sample_cols), when
         given, is <= tol.
+
+    With ``trace`` (a list), every decision is appended as (half_step, kind,
+    i, j, v1, v2) with half-steps counted from 0 over the whole block.
 
     Returns (I, J, U, k_eff, sigma, l, swaps)."""
     J_cands = [int(j) for j in J_cands]
@@ -399,15 +404,20 @@ def cross_approximation_adaptive(src, J_cands, l_init, l_max, k_max, sweeps, tol
     I = []
     swaps = 0
     at_size = 0
+    hs = 0
     while True:
         C = columns(src, J)
-        start = I if len(I) == l else gepp_rows(C, first=I)
-        res = maxvol(C, start, delta, max_swaps)
+        start = gepp_rows(C, trace, hs, first=I)
+        res = maxvol(C, start, delta, max_swaps, trace, hs)
         I = res.I
         swaps += res.swaps
-        res = maxvol(rows(src, I).T, J, delta, max_swaps)
+        hs += 1
+        RT = rows(src, I).T
+        start = gepp_rows(RT, trace, hs, first=J)
+        res = maxvol(RT, start, delta, max_swaps, trace, hs)
         J = res.I
         swaps += res.swaps
+        hs += 1
         at_size += 1
         X = src.block(I, J)
         sigma = np.linalg.svd(X, compute_uv=False)

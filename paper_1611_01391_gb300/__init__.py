@@ -89,14 +89,15 @@ class lra_batch_params(ctypes.Structure):
                 ("sweeps", ctypes.c_int32), ("max_swaps", ctypes.c_int32), ("sample", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("delta", ctypes.c_double),
                 ("cand_J", ctypes.c_void_p), ("sample_rows", ctypes.c_void_p),
-                ("sample_cols", ctypes.c_void_p), ("flags", ctypes.c_int32)]
+                ("sample_cols", ctypes.c_void_p), ("flags", ctypes.c_int32), ("trace_cap", ctypes.c_int32)]
 
 
 class lra_batch_out(ctypes.Structure):
     _fields_ = [("on_device", ctypes.c_int32), ("status", ctypes.c_void_p), ("l", ctypes.c_void_p),
                 ("k_eff", ctypes.c_void_p), ("swaps", ctypes.c_void_p), ("I", ctypes.c_void_p),
                 ("J", ctypes.c_void_p), ("U", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
-                ("est_err", ctypes.c_void_p)]
+                ("est_err", ctypes.c_void_p), ("trace_len", ctypes.c_void_p), ("trace", ctypes.c_void_p),
+                ("trace_val", ctypes.c_void_p)]
 
 
 _ctx_p = ctypes.c_void_p

@@ -147,10 +147,18 @@ class BatchResult:
     sigma: np.ndarray
     est_err: np.ndarray
     info: lra_info
+    trace_len: np.ndarray | None = None
+    trace: np.ndarray | None = None
+    trace_val: np.ndarray | None = None
+
+    def block_trace(self, b):
+        """Decision log of block b as rows (half_step, kind, i, j)."""
+        n = int(self.trace_len[b])
+        return self.trace[b, :n], self.trace_val[b, :n]
 
 
 def make_batch_params(l_init, l_max, k_max, sweeps, tol, cand_J, sample_rows=None, sample_cols=None,
-                      delta=1e-2, max_swaps=0):
+                      delta=1e-2, max_swaps=0, trace_cap=0):
     """lra_batch_params plus the host arrays it points to (keep both alive)."""
     cj = np.ascontiguousarray(cand_J, dtype=np.int32)
     sr = None if sample_rows is None else np.ascontiguousarray(sample_rows, dtype=np.int32)
@@ -163,10 +171,11 @@ def make_batch_params(l_init, l_max, k_max, sweeps, tol, cand_J, sample_rows=Non
     if sr is not None:
         p.sample_rows, p.sample_cols = sr.ctypes.data, sc.ctypes.data
     p.flags = 0
+    p.trace_cap = trace_cap
     return p, (cj, sr, sc)
 
 
-def _batch_fetch(ctx, job, nb, l_max):
+def _batch_fetch(ctx, job, nb, l_max, trace_cap=0):
     info = lra_cross_wait(ctx, job)
     r = BatchResult(np.zeros(nb, np.int32), np.zeros(nb, np.int32), np.zeros(nb, np.int32),
                     np.zeros(nb, np.int32), np.zeros((nb, l_max), np.int32),
@@ -178,6 +187,12 @@ def _batch_fetch(ctx, job, nb, l_max):
                                                r.k_eff.ctypes.data, r.swaps.ctypes.data)
     out.I, out.J, out.U = r.I.ctypes.data, r.J.ctypes.data, r.U.ctypes.data
     out.sigma, out.est_err = r.sigma.ctypes.data, r.est_err.ctypes.data
+    if trace_cap:
+        r.trace_len = np.zeros(nb, np.int32)
+        r.trace = np.zeros((nb, trace_cap, 4), np.int32)
+        r.trace_val = np.zeros((nb, trace_cap), np.float64)
+        out.trace_len, out.trace, out.trace_val = (r.trace_len.ctypes.data, r.trace.ctypes.data,
+                                                   r.trace_val.ctypes.data)
     lra_cross_fetch_batch(ctx, job, out)
     return r
 
@@ -186,4 +201,4 @@ def solve_batch(context, src, blocks, params, l_max):
     """Submit one batched launch and fetch every block's result (host arrays)."""
     blocks = np.ascontiguousarray(blocks, dtype=np.int64)
     job = lra_cross_submit_batch(context.ctx, src, blocks, params)
-    return _batch_fetch(context.ctx, job, len(blocks), l_max)
+    return _batch_fetch(context.ctx, job, len(blocks), l_max, params.trace_cap)

@@ -4,22 +4,26 @@
 // (Section 6.5) in one persistent launch.
 //
 // Design:
-//   * One thread-block cluster of 4 CTAs solves one block at a time and pulls
-//     the next block index from a device work queue (an atomic counter), so
-//     uneven blocks balance themselves.  The strip of the current half-step
-//     (up to 2048 rows x l <= 96 FP32 values) is split across the 4 CTAs'
-//     shared memory and never leaves the chip.
+//   * One CTA, or a thread-block cluster of 4 or 8 CTAs, solves one block at
+//     a time and pulls the next block index from a device work queue (an
+//     atomic counter), so uneven blocks balance themselves.  The strip of
+//     the current half-step (up to 2048 rows x l <= 96 values, each a
+//     double-float pair) is split across the cluster's shared memory and
+//     never leaves the chip.
 //   * Each decision: every CTA reduces its best candidate (packed
 //     |value|/index key, warp shuffles), publishes it and that row in its
 //     shared memory, one hardware cluster barrier, then every CTA reads the
 //     four candidates through distributed shared memory and updates its rows.
 //   * Every strip starts from Gauss-Jordan elimination with partial pivoting
-//     in FP32 whose pivots are restricted to the previous index set (the
-//     very first strip, and the rows a grown cross lacks, pivot freely), and
-//     continues with maxvol swaps.  Elimination with partial pivoting is
-//     backward stable, so the FP32 B = S X^{-1} it produces is the exact B
-//     of a strip within FP32 rounding of the data; an explicit X^{-1} in
-//     FP32 would not be (its error grows with cond(X)).
+//     whose pivots are restricted to the previous index set (the very first
+//     strip, and the rows a grown cross lacks, pivot freely), and continues
+//     with maxvol swaps.  The strip is held and updated in double-float
+//     pairs (about 48 significant bits from FP32 instructions, as in the
+//     plain maxvol): the crosses of a rank-adaptive block reach condition
+//     numbers near 1 / tol = 1e6, where FP32 updates of B would carry errors
+//     of 1e-1 and lose the pivot sequence, while pairs keep B accurate to
+//     about 1e-8.  Candidates are ranked by the FP32 high part (ties: the
+//     smaller row, then column); the stop test uses the whole pair.
 //   * Rank adaptivity, after every sweep: the leader CTA takes the SVD of
 //     the cross (QR with column pivoting, then one-sided Jacobi, double-float
 //     arithmetic: an FP32 SVD cannot resolve singular values near
@@ -36,6 +40,7 @@
 
 #include "lra_internal.cuh"
 #include "lra_kernels.h"
+#include "dd_arith.cuh"
 #include "svd_dd.cuh"
 
 namespace cg = cooperative_groups;
@@ -44,17 +49,18 @@ namespace lra {
 namespace {
 
 constexpr int kBT = 256;                  // threads per CTA
-constexpr int kStripFloats = (kMaxBatchSide / 4) * kMaxL;  // strip chunk per CTA (196 KB)
+constexpr int kStripFloats = (kMaxBatchSide / 4) * kMaxL;  // strip area per CTA (196 KB)
+constexpr int kStripPairs = kStripFloats / 2;              // double-float entries it holds
 constexpr int kMaxQ = 64;                 // sample size per side
-constexpr int kDeferred = 1;              // first-pass status of a block left to the second
+constexpr int kDeferred = 1;              // status of a block left to a later pass (more CTAs)
 
 // Shared memory of one CTA of a CS-CTA cluster.
 template <int CS>
 struct BatchSmemT {
-  float B[kStripFloats];                  // strip chunk, row-major with stride l
-  float colj[kMaxBatchSide / CS];
-  float rrow[kMaxL];
-  float slot_row[2][kMaxL];               // published candidate rows (read by peers)
+  float B[kStripFloats];                  // strip chunk (kStripPairs pairs), row-major with stride l
+  dd colj[kMaxBatchSide / CS];
+  dd rrow[kMaxL];
+  dd slot_row[2][kMaxL];                  // published candidate rows (read by peers)
   unsigned long long slot_key[2];
   int slot_nf[2];
   unsigned long long red_key[kBT / 32];
@@ -78,6 +84,7 @@ static_assert(2 * kMaxL * kMaxL * sizeof(dd) + kMaxL * (sizeof(double) + sizeof(
                       sizeof(SvdScratch) <= sizeof(float) * kStripFloats, "nucleus area");
 static_assert(sizeof(float) * (2 * kMaxL * kMaxL + 4 * kMaxQ * kMaxL) <= sizeof(float) * kStripFloats,
               "estimate area");
+static_assert(sizeof(BatchSmemT<1>) <= 227 * 1024, "one CTA's shared memory");
 
 __device__ __forceinline__ unsigned long long pack_key(float v, int idx) {
   return ((unsigned long long)(__float_as_uint(v) & 0x7fffffffu) << 32) | (unsigned)(~idx);
@@ -124,29 +131,31 @@ __device__ __forceinline__ void cta_reduce(S* s, unsigned long long key, int nf)
 
 // One strip of the C-A iteration on the cluster: load the N x l strip
 // (vertical: S[i][t] = M(row0 + i, col0 + other[t]); horizontal:
-// S[j][t] = M(row0 + other[t], col0 + j)), Gauss-Jordan start, maxvol.
-// The start keeps the previous index set: for its first nfirst steps the
-// pivot rows are restricted to the strip rows first[0 .. nfirst) (partial
-// pivoting among them), later steps pivot over every free row.  After l
-// steps B = S X^{-1} with X the rows so chosen; elimination with partial
-// pivoting is backward stable, so this FP32 B is the exact B of the strip
-// within FP32 rounding of the data, which an FP32 X^{-1} would not give.
-// Returns false when the block failed (s->status set identically in all
-// CTAs).  On return s->pos holds the selected strip rows.
+// S[j][t] = M(row0 + other[t], col0 + j)) as double-float pairs,
+// Gauss-Jordan start, maxvol.  The start keeps the previous index set: for
+// its first nfirst steps the pivot rows are restricted to the strip rows
+// first[0 .. nfirst) (partial pivoting among them), later steps pivot over
+// every free row; step t puts its pivot row in position t.  After l steps
+// B = S X^{-1} with X the rows so chosen.  Returns false when the block
+// failed (s->status set identically in all CTAs).  On return s->pos holds
+// the selected strip rows.  With a decision log (trace != nullptr, written
+// by the leader CTA's thread 0): every decision of this half-step as
+// (half_step, kind, i, j) and its |value| in FP64, while *tlen < tcap.
 template <int KIND, int CS>
 __device__ bool half_step(const BatchArgs& a, cg::cluster_group& cl, BatchSmemT<CS>* s, bool vertical,
                           long long row0, long long col0, int N, int l, const int* other,
-                          int nfirst, const int* first) {
+                          int nfirst, const int* first, int hs, int* trace, double* trace_v, int* tlen) {
   const int rank = (int)cl.block_rank();
   const int tid = threadIdx.x;
   const int rpc = (N + CS - 1) / CS;
   const int r0 = rank * rpc;
   const int nr = max(0, min(rpc, N - r0));
+  dd* B = reinterpret_cast<dd*>(s->B);
   for (int e = tid; e < nr * l; e += kBT) {
     const int r = e / l, t = e - r * l;
     const long long g = r0 + r;
-    s->B[e] = vertical ? entry<KIND>(a.src, row0 + g, col0 + other[t])
-                       : entry<KIND>(a.src, row0 + other[t], col0 + g);
+    B[e] = dd_make(vertical ? entry<KIND>(a.src, row0 + g, col0 + other[t])
+                            : entry<KIND>(a.src, row0 + other[t], col0 + g));
   }
   for (int r = tid; r < nr; r += kBT) s->used[r] = 0;  // bit 0: pivoted, bit 1: in first
   __syncthreads();
@@ -159,10 +168,11 @@ __device__ bool half_step(const BatchArgs& a, cg::cluster_group& cl, BatchSmemT<
   unsigned long long mine = 0ull;
   int nf = 0;
   for (int r = tid; r < nr; r += kBT)
-    if (nfirst == 0 || (s->used[r] & 2)) consider_f(mine, nf, s->B[r * l], (r0 + r) * l);
+    if (nfirst == 0 || (s->used[r] & 2)) consider_f(mine, nf, B[r * l].hi, (r0 + r) * l);
   bool gepp = true;
   int step = 0, swaps = 0, buf = 0;
   bool ok = true;
+  const bool log = trace != nullptr && rank == 0 && tid == 0;
   for (;;) {
     cta_reduce(s, mine, nf);
     const unsigned long long cb = s->win_key;
@@ -172,9 +182,9 @@ __device__ bool half_step(const BatchArgs& a, cg::cluster_group& cl, BatchSmemT<
     }
     if (cb != 0ull && tid < l) {
       const int r = key_idx(cb) / l - r0;
-      s->slot_row[buf][tid] = s->B[r * l + tid];
+      s->slot_row[buf][tid] = B[r * l + tid];
     }
-    cl.sync();
+    if (CS > 1) cl.sync(); else __syncthreads();
     unsigned long long win = 0ull;
     int wnf = 0, owner = 0;
     for (int p = 0; p < CS; ++p) {
@@ -185,38 +195,53 @@ __device__ bool half_step(const BatchArgs& a, cg::cluster_group& cl, BatchSmemT<
         owner = p;
       }
     }
-    const float wv = key_val(win);
-    int kind;  // 0 gepp, 1 swap, 2 stop
+    const int idx = key_idx(win);
+    const int istar = win == 0ull ? -1 : idx / l, jstar = win == 0ull ? 0 : idx - istar * l;
+    // the winner's whole pair decides (the key ranks by its high part)
+    const dd pv = win == 0ull ? dd_make(0.0f) : cl.map_shared_rank(&s->slot_row[buf][0], owner)[jstar];
+    const double wv = fabs(dd_to_double(pv));
+    int kind;
     if (wnf) {
       if (tid == 0) s->status = LRA_ENONFINITE;
       ok = false;
       break;
     }
     if (gepp) {
-      if (win == 0ull || !(wv > 0.0f)) {
+      if (win == 0ull || !(wv > 0.0)) {
         if (tid == 0) s->status = LRA_ESINGULAR;
         ok = false;
         break;
       }
-      kind = 0;
-    } else if (wv <= 1.0f + a.delta || swaps >= a.max_swaps) {
-      kind = 2;
+      kind = LRA_TRACE_GEPP;
+    } else if (wv <= 1.0 + a.delta) {
+      kind = LRA_TRACE_STOP;
+    } else if (swaps >= a.max_swaps) {
+      kind = LRA_TRACE_CAP;
     } else {
-      kind = 1;
+      kind = LRA_TRACE_SWAP;
     }
-    if (kind == 2) break;
-    const int idx = key_idx(win);
-    const int istar = idx / l, jstar = idx - istar * l;
+    if (log && *tlen < a.trace_cap) {
+      const int n = (*tlen)++;
+      trace[4 * n + 0] = hs;
+      trace[4 * n + 1] = kind;
+      trace[4 * n + 2] = istar;
+      trace[4 * n + 3] = jstar;
+      trace_v[n] = wv;
+    }
+    if (kind == LRA_TRACE_STOP || kind == LRA_TRACE_CAP) break;
     if (tid < l) s->rrow[tid] = cl.map_shared_rank(&s->slot_row[buf][0], owner)[tid];
-    for (int r = tid; r < nr; r += kBT) s->colj[r] = s->B[r * l + jstar];
+    for (int r = tid; r < nr; r += kBT) s->colj[r] = B[r * l + jstar];
     if (tid == 0) {
       if (gepp && istar >= r0 && istar < r0 + nr) s->used[istar - r0] |= 1;
       s->pos[jstar] = istar;
     }
     __syncthreads();
-    const float piv = s->rrow[jstar];
-    __syncthreads();
-    if (tid < l) s->rrow[tid] = (s->rrow[tid] - (tid == jstar ? 1.0f : 0.0f)) / piv;
+    // the update's row factor (B[i*, :] - e_j*^T) / B[i*, j*]
+    if (tid < l) {
+      dd rt = s->rrow[tid];
+      if (tid == jstar) rt = dd_add(rt, dd_make(-1.0f));
+      s->rrow[tid] = dd_div(rt, pv);
+    }
     __syncthreads();
     const bool next_gepp = gepp && (step + 1 < l);
     const int next_col = step + 1;
@@ -224,17 +249,17 @@ __device__ bool half_step(const BatchArgs& a, cg::cluster_group& cl, BatchSmemT<
     for (int e = tid; e < nr * l; e += kBT) {
       const int r = e / l, t = e - r * l;
       const int g = r0 + r;
-      float v;
+      dd v;
       if (g == istar) {
-        v = (t == jstar) ? 1.0f : 0.0f;
-        s->B[e] = v;
-        if (!next_gepp) consider_f(mine, nf, v, g * l + t);
+        v = dd_make((t == jstar) ? 1.0f : 0.0f);   // the pivot row becomes e_j* exactly
+        B[e] = v;
+        if (!next_gepp) consider_f(mine, nf, v.hi, g * l + t);
       } else {
-        v = fmaf(-s->colj[r], s->rrow[t], s->B[e]);
-        s->B[e] = v;
+        v = dd_fnma(s->colj[r], s->rrow[t], B[e]);
+        B[e] = v;
         if (next_gepp ? (t == next_col && !(s->used[r] & 1) && (next_col >= nfirst || (s->used[r] & 2)))
                       : true)
-          consider_f(mine, nf, v, g * l + t);
+          consider_f(mine, nf, v.hi, g * l + t);
       }
     }
     if (gepp) {
@@ -247,7 +272,7 @@ __device__ bool half_step(const BatchArgs& a, cg::cluster_group& cl, BatchSmemT<
   }
   if (tid == 0) {
     s->swaps += swaps;
-    // FP32 work of this strip: every decision updates the N x l strip
+    // work of this strip: every decision updates the N x l strip
     if (rank == 0) atomicAdd(&a.js->maxvol_flops, 2.0 * N * l * (double)(step + swaps));
   }
   cl.sync();  // peers finished reading this CTA's slots before they are reused
@@ -415,14 +440,17 @@ __device__ void cross_step(const BatchArgs& a, S* s, int b, long long row0, long
   __syncthreads();
 }
 
-// Two passes over the blocks.  Pass 1 (CS = 1): one CTA per block, the
+// Three passes over the blocks.  Pass 1 (CS = 1): one CTA per block, the
 // whole strip in its shared memory, no cluster barrier per decision, 152
 // blocks in flight; a block whose rank rule asks for a cross larger than one
-// CTA can hold (l max(m, n) > kStripFloats) is left with status kDeferred.
-// Pass 2 (CS = 4): the deferred blocks only, from their start, the strip
-// split over a 4-CTA cluster.  The decisions (argmax with the same
-// tie-break over the whole strip) and the arithmetic per entry do not depend
-// on the split, so a block's result is the same in either pass.
+// CTA can hold (l max(m, n) > kStripPairs) is left with status kDeferred.
+// Pass 2 (CS = 4) and pass 3 (CS = 8): the deferred blocks only, each from
+// its start, the strip split over a 4- or 8-CTA cluster; pass 2 defers what
+// 4 CTAs cannot hold, pass 3 holds every block (2048 x 96 pairs).  The
+// decisions (argmax with the same tie-break over the whole strip) and the
+// arithmetic per entry do not depend on the split, so a block's result is
+// the same in any pass.
+static_assert(8 * kStripPairs >= kMaxBatchSide * kMaxL, "the 8-CTA pass holds every strip");
 template <int KIND, int CS>
 __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kBT, 1) batch_kernel(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char bsm[];
@@ -431,7 +459,8 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kBT, 1) batch_kerne
   const int rank = (int)cl.block_rank();
   const int tid = threadIdx.x;
   constexpr bool kFirst = (CS == 1);
-  int* queue = a.queue + (kFirst ? 0 : 1);
+  constexpr bool kLast = (CS == 8);
+  int* queue = a.queue + (CS == 1 ? 0 : CS == 4 ? 1 : 2);
   for (;;) {
     if (rank == 0 && tid == 0)  // a cancelled job takes no further block
       s->blk = (*(volatile const int*)&a.js->status != LRA_OK) ? a.n_blocks : atomicAdd(queue, 1);
@@ -449,9 +478,13 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kBT, 1) batch_kerne
     const long long col0 = a.blocks[4 * b + 2], n = a.blocks[4 * b + 3];
     const int lmax_b = (int)min((long long)a.l_max, min(m, n));
     // largest cross whose strips fit this cluster's shared memory
-    const int lcap = (int)min((long long)lmax_b, kStripFloats / ((max(m, n) + CS - 1) / CS));
+    const int lcap = (int)min((long long)lmax_b, kStripPairs / ((max(m, n) + CS - 1) / CS));
     int l = min(a.l_init, lmax_b);
-    bool deferred = kFirst && l > lcap;
+    bool deferred = !kLast && l > lcap;
+    // decision log of this block (leader CTA, thread 0)
+    int* btrace = a.trace_cap > 0 ? a.trace + (size_t)b * a.trace_cap * 4 : nullptr;
+    double* btrace_v = a.trace_cap > 0 ? a.trace_v + (size_t)b * a.trace_cap : nullptr;
+    int tlen = 0, hs = 0;
     for (int t = tid; t < l; t += kBT) s->Jset[t] = a.jcand[(size_t)b * a.l_max + t];
     if (tid == 0) {
       s->status = LRA_OK;
@@ -462,12 +495,14 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kBT, 1) batch_kerne
     int n_i = 0;       // rows of the previous I (none before the first sweep)
     int at_size = 0;   // sweeps at the current cross size
     while (!deferred) {
-      ok = half_step<KIND, CS>(a, cl, s, true, row0, col0, (int)m, l, s->Jset, n_i, s->Iset);
+      ok = half_step<KIND, CS>(a, cl, s, true, row0, col0, (int)m, l, s->Jset, n_i, s->Iset, hs++, btrace,
+                               btrace_v, &tlen);
       if (!ok) break;
       for (int t = tid; t < l; t += kBT) s->Iset[t] = s->pos[t];
       n_i = l;
       __syncthreads();
-      ok = half_step<KIND, CS>(a, cl, s, false, row0, col0, (int)n, l, s->Iset, l, s->Jset);
+      ok = half_step<KIND, CS>(a, cl, s, false, row0, col0, (int)n, l, s->Iset, l, s->Jset, hs++, btrace,
+                               btrace_v, &tlen);
       if (!ok) break;
       for (int t = tid; t < l; t += kBT) s->Jset[t] = s->pos[t];
       __syncthreads();
@@ -477,7 +512,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kBT, 1) batch_kerne
       const int grow = *cl.map_shared_rank(&s->grow, 0);
       const int stop = *cl.map_shared_rank(&s->stop, 0);
       if (grow) {
-        if (min(lmax_b, 2 * l) > lcap) {  // only the 4-CTA pass holds this cross
+        if (!kLast && min(lmax_b, 2 * l) > lcap) {  // only a pass with more CTAs holds this cross
           deferred = true;
           break;
         }
@@ -508,6 +543,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kBT, 1) batch_kerne
         a.out_status[b] = ok ? (int)LRA_OK : s->status;
         a.out_l[b] = l;
         a.out_swaps[b] = s->swaps;
+        if (a.trace_cap > 0) a.trace_len[b] = tlen;
         if (!ok) {
           a.out_keff[b] = 0;
           a.out_err[b] = 0.0;
@@ -540,12 +576,13 @@ static cudaError_t launch_pass(const BatchArgs& a, int sms, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// a.queue holds two zeroed counters, one per pass
+// a.queue holds three zeroed counters, one per pass
 cudaError_t launch_batch(const BatchArgs& a, int sms, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   LRA_DISPATCH_KIND(a.src.kind, ({
     e = launch_pass<K, 1>(a, sms, st);
     if (!e) e = launch_pass<K, 4>(a, sms, st);
+    if (!e) e = launch_pass<K, 8>(a, sms, st);
   }));
   return e;
 }

@@ -95,8 +95,12 @@ struct BatchArgs {
   const int* scol;          // n_blocks x q sample columns (local)
   int q;
   int l_init, l_max, k_max, sweeps, max_swaps;
-  float tol, delta;
-  int* queue;               // two work counters (one per pass), zero at launch
+  double tol, delta;
+  int* queue;               // three work counters (one per pass), zero at launch
+  int trace_cap;            // decisions logged per block (0: none)
+  int* trace;               // n_blocks x trace_cap x 4: half_step, kind, i, j
+  double* trace_v;          // n_blocks x trace_cap: |value| of each decision
+  int* trace_len;           // n_blocks
   int* out_status;
   int* out_l;
   int* out_keff;

@@ -59,6 +59,9 @@ struct Job {
   double* b_U = nullptr;
   float* b_sigma = nullptr;
   double* b_err = nullptr;
+  int b_tcap = 0;
+  int *b_tlen = nullptr, *b_trace = nullptr;
+  double* b_tval = nullptr;
 };
 
 enum { kClsGather = 0, kClsMaxvol = 1, kClsCross = 2, kClsResid = 3, kClsInverse = 4, kClsFullres = 5,
@@ -836,6 +839,7 @@ static lra_status validate_batch(const lra_source* src, const lra_block* blocks,
   if (p->sweeps < 1 || p->sweeps > 100) { *why = "sweeps must be in 1..100"; return LRA_EINVAL; }
   if (p->sample < 0 || p->sample > 64) { *why = "sample must be in 0..64"; return LRA_EINVAL; }
   if (!(p->delta > 0.0) || !(p->tol >= 0.0)) { *why = "delta > 0 and tol >= 0 required"; return LRA_EINVAL; }
+  if (p->trace_cap < 0 || p->trace_cap > (1 << 20)) { *why = "trace_cap must be in 0..2^20"; return LRA_EINVAL; }
   if (!p->cand_J || (p->sample > 0 && (!p->sample_rows || !p->sample_cols))) {
     *why = "candidate / sample arrays required"; return LRA_EINVAL;
   }
@@ -881,7 +885,7 @@ lra_status lra_cross_submit_batch(lra_ctx* ctx, const lra_source* src, const lra
   const size_t L = (size_t)p->l_max, q = (size_t)p->sample, NB = (size_t)nb;
   Layout lay;
   const size_t o_js = lay.take(sizeof(JobStatus));
-  const size_t o_queue = lay.take(2 * sizeof(int));  // one work counter per pass
+  const size_t o_queue = lay.take(3 * sizeof(int));  // one work counter per pass
   const size_t o_blocks = lay.take(sizeof(long long) * 4 * NB);
   const size_t o_jc = lay.take(sizeof(int) * NB * L);
   const size_t o_sr = lay.take(sizeof(int) * NB * std::max<size_t>(q, 1));
@@ -895,7 +899,12 @@ lra_status lra_cross_submit_batch(lra_ctx* ctx, const lra_source* src, const lra
   const size_t o_U = lay.take(sizeof(double) * NB * L * L);
   const size_t o_sg = lay.take(sizeof(float) * NB * L);
   const size_t o_er = lay.take(sizeof(double) * NB);
+  const size_t TC = (size_t)std::max(p->trace_cap, 0);
+  const size_t o_tl = lay.take(sizeof(int) * NB);
+  const size_t o_tr = lay.take(sizeof(int) * 4 * NB * std::max<size_t>(TC, 1));
+  const size_t o_tv = lay.take(sizeof(double) * NB * std::max<size_t>(TC, 1));
   j->bytes = lay.off;
+  j->b_tcap = (int)TC;
   if ((int)ctx->jobs.size() >= ctx->max_slots || ctx->free_slots.empty() ||
       (ctx->budget && ctx->used_bytes + j->bytes > ctx->budget)) {
     delete j;
@@ -923,6 +932,9 @@ lra_status lra_cross_submit_batch(lra_ctx* ctx, const lra_source* src, const lra
   j->b_U = reinterpret_cast<double*>(base + o_U);
   j->b_sigma = reinterpret_cast<float*>(base + o_sg);
   j->b_err = reinterpret_cast<double*>(base + o_er);
+  j->b_tlen = reinterpret_cast<int*>(base + o_tl);
+  j->b_trace = reinterpret_cast<int*>(base + o_tr);
+  j->b_tval = reinterpret_cast<double*>(base + o_tv);
   j->slot = ctx->free_slots.back();
   ctx->free_slots.pop_back();
   ctx->used_bytes += j->bytes;
@@ -943,8 +955,12 @@ lra_status lra_cross_submit_batch(lra_ctx* ctx, const lra_source* src, const lra
   a.k_max = p->k_max;
   a.sweeps = p->sweeps;
   a.max_swaps = p->max_swaps > 0 ? p->max_swaps : 64 * p->l_max;
-  a.tol = (float)p->tol;
-  a.delta = (float)p->delta;
+  a.tol = p->tol;
+  a.delta = p->delta;
+  a.trace_cap = (int)TC;
+  a.trace = j->b_trace;
+  a.trace_v = j->b_tval;
+  a.trace_len = j->b_tlen;
   a.queue = j->b_queue;
   a.out_status = j->b_status;
   a.out_l = j->b_l;
@@ -959,7 +975,8 @@ lra_status lra_cross_submit_batch(lra_ctx* ctx, const lra_source* src, const lra
   static_assert(sizeof(lra_block) == 4 * sizeof(long long), "lra_block layout");
   if ((e = cudaEventCreate(&j->ev_start)) || (e = cudaEventCreate(&j->ev_end)) ||
       (e = cudaMemcpyAsync(j->js, &init, sizeof(init), cudaMemcpyHostToDevice, s)) ||
-      (e = cudaMemsetAsync(j->b_queue, 0, 2 * sizeof(int), s)) ||
+      (e = cudaMemsetAsync(j->b_queue, 0, 3 * sizeof(int), s)) ||
+      (e = cudaMemsetAsync(j->b_tlen, 0, sizeof(int) * NB, s)) ||
       (e = cudaMemsetAsync(j->b_err, 0, sizeof(double) * NB, s)) ||
       (e = cudaMemsetAsync(j->b_keff, 0, sizeof(int) * NB, s)) ||
       (e = cudaMemcpyAsync(j->b_blocks, blocks, sizeof(lra_block) * NB, cudaMemcpyHostToDevice, s)) ||
@@ -1004,10 +1021,13 @@ lra_status lra_cross_fetch_batch(lra_ctx* ctx, lra_job id, const lra_batch_out* 
         {out->I, j->b_I, sizeof(int) * NB * L},       {out->J, j->b_J, sizeof(int) * NB * L},
         {out->U, j->b_U, sizeof(double) * NB * L * L}, {out->sigma, j->b_sigma, sizeof(float) * NB * L},
         {out->est_err, j->b_err, sizeof(double) * NB},
+        {out->trace_len, j->b_tlen, j->b_tcap ? sizeof(int) * NB : 0},
+        {out->trace, j->b_trace, sizeof(int) * 4 * NB * (size_t)j->b_tcap},
+        {out->trace_val, j->b_tval, sizeof(double) * NB * (size_t)j->b_tcap},
     };
     for (const Piece& pc : pieces) {
       if (e) break;
-      if (!pc.dst) continue;
+      if (!pc.dst || pc.bytes == 0) continue;
       e = cudaMemcpyAsync(pc.dst, pc.src, pc.bytes, cudaMemcpyDefault, cs);
     }
     if (!e) e = cudaStreamSynchronize(cs);

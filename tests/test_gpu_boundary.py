@@ -183,11 +183,11 @@ def test_fetch_of_a_long_job_does_not_block_other_threads():
     """One thread waits in fetch_cur for a long solve; meanwhile another
     thread submits a short solve and polls it to completion.  The short
     solve must finish while the long one is still being waited for."""
-    x, y, keep, src = _cauchy(W.BASE_SEED + 70, 65536, 65536)
+    x, y, keep, src = _cauchy(W.BASE_SEED + 70, 32768, 32768)
     A = torch.from_numpy(W.lowrank_svd(W.BASE_SEED + 71).astype(np.float32)).to(DEV)
     small = L.make_source("dense", a=A)
     with L.Context(0, n_streams=2) as c:
-        p_long, k1 = L.make_params(64, 96, 200, W.draw_indices(72, 65536, 96))
+        p_long, k1 = L.make_params(64, 96, 200, W.draw_indices(72, 32768, 96))
         p_small, k2 = L.make_params(8, 8, 1, W.draw_indices(73, 256, 8))
         c.solve(small, p_small, 8)          # warm-up (kernel modules loaded)
         t0 = time.perf_counter()
