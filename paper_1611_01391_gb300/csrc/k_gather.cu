@@ -103,8 +103,12 @@ __global__ void __launch_bounds__(256) gather_entries_kernel(SourceDev src, cons
 //      that share a sector share its load;
 //   2. streams row tiles of kColsTmaRows rows: per distinct sector one TMA box
 //      of 8 FP32 x kColsTmaRows rows (the sector column of the tile), into a
-//      ring of `stages` shared-memory buffers guarded by mbarriers (the
-//      tensor map asks for no L2 promotion, so the reads stay sector-sized);
+//      ring of `stages` shared-memory buffers guarded by mbarriers.  The
+//      tensor map asks for 64-byte L2 promotion: on GB300 a scattered
+//      32-byte read costs 64 bytes of DRAM traffic with it, and 128 bytes
+//      (a whole line) without it, for TMA boxes and plain loads alike
+//      (measured on the stored 32768^2 matrix with l = 96: 195 MB against
+//      390 MB per gather, 99.6 MB being the 32-byte sector floor);
 //   3. transposes through shared memory: the tile's rows of C, contiguous in
 //      C, are written with 16-byte stores, C[r][t] = box(slot[t])[r][J[t] & 7].
 // Grid: one persistent CTA per SM over the row tiles.  Every mbarrier wait
@@ -223,7 +227,7 @@ bool make_cols_map(TmaMap* map, const float* a, long long m, long long n, long l
   if ((reinterpret_cast<uintptr_t>(a) & 15) != 0 || (lda & 3) != 0) return false;
   return tma::make_map_2d(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, a, (uint64_t)n,
                           (uint64_t)m, (uint64_t)lda * 4, 8, kColsTmaRows, CU_TENSOR_MAP_SWIZZLE_NONE,
-                          CU_TENSOR_MAP_L2_PROMOTION_NONE);
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_64B);
 }
 
 cudaError_t launch_gather_cols_tma(const TmaMap& map, const int* J, int l, long long m, float* C, JobStatus* js,

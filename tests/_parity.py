@@ -79,20 +79,22 @@ class SubSource:
 U_DD = 2.0 ** -48
 
 
-def check_nucleus(U_dev, sigma_dev, k_dev, X32, k, tau=GPU_TAU):
+def check_nucleus(U_dev, sigma_dev, k_dev, X32, k, tau=GPU_TAU, sigma_rel=0.0):
     """The device's nucleus against the oracle's for the same cross: X32 holds
     the FP32 entries of M[I, J] at the device's own (I, J) (input-matched), so
     the only difference is the SVD's arithmetic (double-float on the device,
     FP64 here).  Backward-stable SVDs give |d sigma_j| <= c u sigma_1, and the
     truncated pseudo-inverse moves by at most about c u kappa_k |U| with
     kappa_k = sigma_1 / sigma_k; c = 64 l covers the l-term sums and the
-    Jacobi sweeps.  Returns (max |dU| / max |U|, bound)."""
+    Jacobi sweeps.  sigma_rel: extra relative rounding of a sigma stored in
+    lower precision (2^-24 for FP32 storage).  Returns (max |dU| / max |U|,
+    bound)."""
     X = np.asarray(X32, np.float64)
     l = X.shape[0]
     U_ref, k_ref, s_ref = O.nucleus(X, k, tau)
-    s_dev = np.asarray(sigma_dev, np.float64)
+    s_dev = np.asarray(sigma_dev, np.float64)[:l]
     c = 64.0 * l
-    np.testing.assert_allclose(s_dev, s_ref, rtol=0, atol=c * U_DD * s_ref[0])
+    assert np.all(np.abs(s_dev - s_ref) <= c * U_DD * s_ref[0] + sigma_rel * s_ref), (s_dev, s_ref)
     # the kept rank: equal unless a singular value sits at the cut
     near_cut = np.any(np.abs(s_ref - tau * s_ref[0]) <= 1e-9 * s_ref[0])
     if not near_cut:

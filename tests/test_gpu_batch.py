@@ -8,7 +8,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from tests._parity import SubSource, error_ok
+from tests._parity import SubSource, check_nucleus, compare_traces, error_ok
 
 pytestmark = pytest.mark.gpu
 
@@ -48,43 +48,94 @@ def _nucleus(r, b):
     return r.I[b, :l], r.J[b, :l], r.U[b].ravel()[: l * l].reshape(l, l).astype(np.float64)
 
 
+@pytest.fixture(scope="module")
+def tree4096():
+    """The 2^20-point octree (leaf <= 2048) of the batched workload, and a
+    subset of its 4096 far-field blocks: the 12 largest and 24 drawn at
+    random."""
+    pts, blocks = W.octree_block_pairs(W.BASE_SEED + 4, npoints=1 << 20, leaf=2048, n_pairs=4096)
+    side = np.maximum(blocks[:, 1], blocks[:, 3])
+    big = np.argsort(-side, kind="stable")[:12]
+    rest = np.setdiff1d(np.arange(len(blocks)), big)
+    pick = np.concatenate([big, np.random.default_rng(5).choice(rest, 24, replace=False)])
+    sel = blocks[pick]
+    jc, sr, sc = W.block_candidates(W.BASE_SEED + 5, sel, L_MAX, Q)
+    return pts, sel, jc, sr, sc
+
+
+def _decision_parity(r, b, sub32, jc_b, sr_b, sc_b, A64):
+    """Block b of a batched run against the oracle's rank-adaptive rule fed
+    the same FP32 entries: decision logs agree up to the first unseparated
+    decision; with no divergence, the same l, I, J, kept rank and nucleus;
+    the error within 1.05x of that oracle's.  Returns True when the logs
+    agree to the end."""
+    trace = []
+    oI, oJ, oU, ok, osig, ol, osw = O.cross_approximation_adaptive(
+        sub32, jc_b, L_INIT, L_MAX, K_MAX, SWEEPS, TOL, sample_rows=sr_b, sample_cols=sc_b, trace=trace)
+    dt, dv = r.block_trace(b)
+    assert len(dt) < r.trace.shape[1], "device log truncated"
+    ncmp, div = compare_traces([tuple(t) for t in dt], trace, 1e-2)
+    assert ncmp >= min(L_INIT, sub32.m, sub32.n), (b, ncmp)
+    I, J, U = _nucleus(r, b)
+    if div is None:
+        assert int(r.l[b]) == ol and list(I) == list(oI) and list(J) == list(oJ), b
+        assert int(r.k_eff[b]) == ok, (b, r.k_eff[b], ok)
+        # the recorded values are the oracle's |B| to double-float accuracy
+        ov = np.array([d[4] for d in trace])
+        np.testing.assert_allclose(dv, ov, rtol=1e-6)
+    X32 = sub32.block(I, J)
+    check_nucleus(U, r.sigma[b], int(r.k_eff[b]), X32, K_MAX, tau=TOL, sigma_rel=2.0 ** -23)
+    err = np.linalg.norm(A64 - A64[:, J] @ U @ A64[I, :]) / np.linalg.norm(A64)
+    oerr = np.linalg.norm(A64 - A64[:, oJ] @ oU @ A64[oI, :]) / np.linalg.norm(A64)
+    assert error_ok(err, oerr), (b, err, oerr)
+    return div is None
+
+
+def test_batch_decision_logs_on_the_4096_block_tree(ctx, tree4096):
+    """Blocks of the batched workload's own tree (sides up to 2048) through
+    the persistent launch, each against the oracle fed the same FP32 entries
+    of 1/|x - y| (reproduced bit for bit)."""
+    pts, blocks, jc, sr, sc = tree4096
+    d = torch.from_numpy(pts).cuda()
+    src = L.make_source("invdist", x=d, y=d)
+    p, keep = make_batch_params(L_INIT, L_MAX, K_MAX, SWEEPS, TOL, jc, sr, sc, trace_cap=8192)
+    r = solve_batch(ctx, src, blocks, p, L_MAX)
+    assert np.all(r.status == 0)
+    s32 = O.InvDist(pts, pts, "fp32")
+    s64 = O.InvDist(pts, pts, "fp64")
+    full = 0
+    for b, (r0, m, c0, n) in enumerate(blocks):
+        A64 = SubSource(s64, r0, m, c0, n).block(np.arange(m), np.arange(n))
+        full += _decision_parity(r, b, SubSource(s32, r0, m, c0, n), jc[b], sr[b], sc[b], A64)
+    # most blocks agree to the last decision (the rest diverge only at a near-tie)
+    assert full >= 0.8 * len(blocks), full
+
+
 def test_batch_error_vs_oracle(ctx, case):
+    """40 blocks of a 2^17-point tree: decision logs, index sets, kept ranks
+    and nuclei against the oracle fed the same FP32 entries, errors within
+    1.05x, and the device's Appendix F estimate against the FP64 one on the
+    device's own factors."""
     pts, blocks, jc, sr, sc = case
-    r = _run(ctx, pts, blocks, jc, sr, sc)
+    d = torch.from_numpy(pts).cuda()
+    src = L.make_source("invdist", x=d, y=d)
+    p, keep = make_batch_params(L_INIT, L_MAX, K_MAX, SWEEPS, TOL, jc, sr, sc, trace_cap=8192)
+    r = solve_batch(ctx, src, blocks, p, L_MAX)
     assert np.all(r.status == 0)
     s64 = O.InvDist(pts, pts, "fp64")
     s32 = O.InvDist(pts, pts, "fp32")
-    same_rank = 0
+    full = 0
     for b, (r0, m, c0, n) in enumerate(blocks):
-        sub = SubSource(s64, r0, m, c0, n)
-        A = sub.block(np.arange(m), np.arange(n))
-        I, J, U = _nucleus(r, b)
-        err = np.linalg.norm(A - A[:, J] @ U @ A[I, :]) / np.linalg.norm(A)
-        oI, oJ, oU, ok, osig, ol, osw = O.cross_approximation_adaptive(sub, jc[b], L_INIT, L_MAX, K_MAX,
-                                                                       SWEEPS, TOL, sample_rows=sr[b],
-                                                                       sample_cols=sc[b])
-        oerr = np.linalg.norm(A - A[:, oJ] @ oU @ A[oI, :]) / np.linalg.norm(A)
-        assert error_ok(err, oerr), (b, err, oerr)
-        # the kept rank is the count of cross singular values above tol
-        # sigma_1: check it on the device's own cross (FP64 SVD of the same
-        # FP32 entries), unless a singular value sits within 2% of the cut
-        sg = np.linalg.svd(s32.block(r0 + I, c0 + J), compute_uv=False)
-        cut = TOL * sg[0]
-        if not np.any(np.abs(sg - cut) < 0.02 * cut):
-            assert r.k_eff[b] == min(K_MAX, int(np.sum(sg > cut))), (b, r.k_eff[b], sg / sg[0])
-        # against the oracle the rank may differ where FP32 entries move a
-        # singular value across the cut (the oracle itself changes rank on 8
-        # of these 40 blocks between FP32 and FP64 entries)
-        assert abs(int(r.k_eff[b]) - ok) <= 2, (b, r.k_eff[b], ok)
-        same_rank += int(r.k_eff[b] == ok)
-        # the device's Appendix F estimate equals the FP64-arithmetic one on
-        # its own factors and the same FP32 entries (the residual is ~1e-7 |M|,
-        # so FP32 rounding of M alone moves it by percents)
+        A64 = SubSource(s64, r0, m, c0, n).block(np.arange(m), np.arange(n))
         sub32 = SubSource(s32, r0, m, c0, n)
+        full += _decision_parity(r, b, sub32, jc[b], sr[b], sc[b], A64)
+        I, J, U = _nucleus(r, b)
+        # the residual is ~1e-7 |M|, so FP32 rounding of M alone moves it by
+        # percents: compare on the same FP32 entries
         est = O.sampled_residual(sub32, sub32.block(np.arange(m), J), U, sub32.block(I, np.arange(n)),
                                  sr[b], sc[b])["rel"]
         assert r.est_err[b] == pytest.approx(est, rel=1e-3, abs=1e-9)
-    assert same_rank >= 0.7 * len(blocks)
+    assert full >= 0.8 * len(blocks), full
 
 
 def test_batch_subset_is_bit_identical(ctx, case):
@@ -123,23 +174,21 @@ def test_blocks_that_need_the_cluster_pass(ctx):
     blocks = np.array([[0, 2048, 2048, 2048], [2048, 2048, 4096, 2048], [0, 300, 4096, 260],
                        [4096, 2048, 0, 2048], [100, 200, 5000, 190]], np.int64)
     jc, sr, sc = W.block_candidates(W.BASE_SEED + 71, blocks, L_MAX, Q)
-    p, keep = make_batch_params(L_INIT, L_MAX, K_MAX, SWEEPS, TOL, jc, sr, sc)
+    p, keep = make_batch_params(L_INIT, L_MAX, K_MAX, SWEEPS, TOL, jc, sr, sc, trace_cap=16384)
     r = solve_batch(ctx, src, blocks, p, L_MAX)
     assert np.all(r.status == 0)
-    assert r.l[0] > 24 and r.l[1] > 24 and r.l[3] > 24     # went through the cluster pass
+    assert r.l[0] > 12 and r.l[1] > 12 and r.l[3] > 12     # went through a cluster pass
     s64 = O.Gauss(x, x, h, "fp64")
     for b, (r0, m, c0, n) in enumerate(blocks):
-        sub = SubSource(s64, r0, m, c0, n)
-        A = sub.block(np.arange(m), np.arange(n))
-        I, J, U = _nucleus(r, b)
-        err = np.linalg.norm(A - A[:, J] @ U @ A[I, :]) / np.linalg.norm(A)
-        oI, oJ, oU, ok, osig, ol, osw = O.cross_approximation_adaptive(sub, jc[b], L_INIT, L_MAX, K_MAX,
-                                                                       SWEEPS, TOL, sample_rows=sr[b],
-                                                                       sample_cols=sc[b])
-        oerr = np.linalg.norm(A - A[:, oJ] @ oU @ A[oI, :]) / np.linalg.norm(A)
-        # the Gaussian kernel's rank-k_max truncation can be ill posed
-        # (sigma_64 ~ sigma_65): allow the spread FP32 entries cause
-        assert err <= max(1.25 * oerr, 1e-5), (b, err, oerr)
+        A64 = SubSource(s64, r0, m, c0, n).block(np.arange(m), np.arange(n))
+        # numpy's float32 exp is not CUDA's expf: the oracle takes the
+        # device's own FP32 entries of the block (lra_gather_entries)
+        rows = torch.arange(r0, r0 + m, dtype=torch.int32, device="cuda")
+        cols = torch.arange(c0, c0 + n, dtype=torch.int32, device="cuda")
+        ent = torch.empty((m, n), dtype=torch.float32, device="cuda")
+        L.lra_gather_entries(src, rows, cols, ent)
+        sub32 = O.Dense(ent.cpu().numpy())
+        _decision_parity(r, b, sub32, jc[b], sr[b], sc[b], A64)
     sel = np.array([0, 3])
     p2, keep2 = make_batch_params(L_INIT, L_MAX, K_MAX, SWEEPS, TOL, jc[sel], sr[sel], sc[sel])
     r2 = solve_batch(ctx, src, blocks[sel], p2, L_MAX)
