@@ -632,12 +632,20 @@ def run_batch(args, wl_name, embed=False):
     blocks64 = np.ascontiguousarray(blocks, dtype=np.int64)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    def step():
-        return L.lra_cross_submit_batch(ctx.ctx, src, blocks64, p)
-
     for _ in range(args.warmup):
-        r = _batch_fetch(ctx.ctx, step(), nb, wl["l_max"])
+        r = _batch_fetch(ctx.ctx, L.lra_cross_submit_batch(ctx.ctx, src, blocks64, p), nb, wl["l_max"])
         assert np.all(r.status == 0), np.unique(r.status)
+    # launch shape from the library's tuner (a fresh cache: the search runs
+    # here, and checks on every candidate that the results do not change)
+    import tempfile
+    with tempfile.TemporaryDirectory() as td:
+        p_tuned, ms_def, ms_tuned = L.lra_cross_tune_batch(ctx.ctx, src, blocks64, p, os.path.join(td, "t.json"))
+    tuning = {"cluster_mask": p_tuned.cluster_mask, "cutover_side": p_tuned.cutover_side, "order": p_tuned.order,
+              "ms_default_shape": ms_def, "ms_tuned": ms_tuned, "gain": ms_def / ms_tuned if ms_tuned > 0 else None,
+              "candidates": 30}
+
+    def step():
+        return L.lra_cross_submit_batch(ctx.ctx, src, blocks64, p_tuned)
     clocks = ClockSampler(local)
     torch.cuda.synchronize(dev)
     dist_barrier(world)
@@ -704,7 +712,7 @@ def run_batch(args, wl_name, embed=False):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         d2.copy_(ph, non_blocking=True)
-        r2 = _batch_fetch(ctx.ctx, L.lra_cross_submit_batch(ctx.ctx, src2, blocks64, p), nb, wl["l_max"])
+        r2 = _batch_fetch(ctx.ctx, L.lra_cross_submit_batch(ctx.ctx, src2, blocks64, p_tuned), nb, wl["l_max"])
         t1 = time.perf_counter()
         assert np.all(r2.status == 0)
         if it >= 1:
@@ -723,14 +731,14 @@ def run_batch(args, wl_name, embed=False):
     line = {
         "metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32x2+f64",
         "data": "synthetic",
         "config": {"workload": wl_name, "generator": "invdist 1/|x-y|", "points": wl["npoints"],
                    "leaf": wl["leaf"], "blocks": nb,
                    "block_sides": [int(blocks[:, [1, 3]].min()), int(blocks[:, [1, 3]].max())],
                    "l_init": wl["l_init"], "l_max": wl["l_max"], "k_max": wl["k_max"], "tol": wl["tol"],
                    "sweeps": wl["sweeps"], "error_sample": f"{wl['q']}x{wl['q']} per block",
-                   "precision": "FP32 entries, strips and maxvol; double-float Jacobi nucleus, FP64 U",
+                   "precision": "FP32 entries; double-float (FP32 pair) strips, maxvol and Jacobi nucleus; FP64 U",
                    "l2": "flushed before every step (256 MiB write)", "parallelism": f"replicas{world}"},
         "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
         "plain_one_job_per_launch": {
@@ -738,6 +746,7 @@ def run_batch(args, wl_name, embed=False):
             "est_rel_err_max": float(max(plain_err)), "est_rel_err_mean": float(np.mean(plain_err)),
             "note": "same blocks, each a separate C-A job at the batch's final l, queued back to back"},
         "speedup_vs_plain": value / plain_value,
+        "autotune": tuning,
         "est_rel_err_max": float(r.est_err.max()), "est_rel_err_mean": float(r.est_err.mean()),
         "est_rel_err_max_subset": float(r.est_err[sub].max()),
         "l_hist": {str(k): int(v) for k, v in zip(*np.unique(r.l, return_counts=True))},

@@ -225,6 +225,13 @@ typedef struct {
   const int32_t* sample_cols; /* host, n_blocks x q local columns                   */
   int32_t flags;              /* reserved, 0                                        */
   int32_t trace_cap;          /* decisions logged per block (0: none), <= 2^20      */
+  /* Launch shape (0 = default; lra_cross_tune_batch picks them per workload).
+   * None of them changes a block's result, only the time. */
+  int32_t cluster_mask;       /* passes to run: bit c = clusters of 2^c CTAs (c = 0..3);
+                                 the 8-CTA pass always runs last; 0: 1, 4, 8 CTAs   */
+  int32_t cutover_side;       /* blocks whose larger side exceeds this skip the first
+                                 pass and start in the next (0: none)               */
+  int32_t order;              /* queue order: 0 as given, 1 largest (m + n) first   */
 } lra_batch_params;
 
 typedef struct {
@@ -257,6 +264,32 @@ typedef struct {
  * lra_batch_out.status. */
 lra_status lra_cross_submit_batch(lra_ctx* ctx, const lra_source* src, const lra_block* blocks,
                                   int32_t n_blocks, const lra_batch_params* params, lra_job* out);
+
+/* Launch-shape tuner of the batched form (the paper has no counterpart:
+ * the shape does not change any result).  Looks up, in the JSON file at
+ * cache_path (NULL: no cache), the shape stored for this GPU (device name)
+ * and the workload's bucket: source kind, l_max, k_max, and the powers of
+ * two at or above the block count, the median and the largest block side.
+ * Without an entry it runs the batch once per candidate shape (cluster
+ * chains {1,4,8}, {1,2,8}, {1,2,4,8}, {1,8}, {2,4,8}; cut-over sides none,
+ * 1024, 512; queue order as given or largest first), each twice, checks
+ * that every candidate returns the same per-block l, k_eff, I, J and
+ * estimate bit for bit (LRA_ECUDA with a message otherwise), keeps the
+ * fastest (ties within 2% go to the default shape) and writes it to the
+ * cache.  *tuned receives a copy of *params with cluster_mask, cutover_side
+ * and order set; ms_default / ms_tuned (nullable) receive the device time of
+ * one launch with the default and the chosen shape (-1 when the shape came
+ * from the cache).  Blocking; uses ctx's slots and budget like any batch. */
+lra_status lra_cross_tune_batch(lra_ctx* ctx, const lra_source* src, const lra_block* blocks, int32_t n_blocks,
+                                const lra_batch_params* params, const char* cache_path, lra_batch_params* tuned,
+                                double* ms_default, double* ms_tuned);
+
+/* Host only (no device needed): the cache lookup of lra_cross_tune_batch for
+ * a device named gpu_name.  LRA_OK with *tuned filled when the cache holds
+ * this bucket, LRA_ENOTFOUND otherwise. */
+lra_status lra_batch_tuning_lookup(const char* cache_path, const char* gpu_name, const lra_source* src,
+                                   const lra_block* blocks, int32_t n_blocks, const lra_batch_params* params,
+                                   lra_batch_params* tuned);
 
 /* Section 9 / Section 6.5 (Primitive Algorithm outputs per block).  Wait for
  * the batch job, copy the per-block results into the caller's buffers (host

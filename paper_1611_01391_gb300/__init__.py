@@ -89,7 +89,8 @@ class lra_batch_params(ctypes.Structure):
                 ("sweeps", ctypes.c_int32), ("max_swaps", ctypes.c_int32), ("sample", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("delta", ctypes.c_double),
                 ("cand_J", ctypes.c_void_p), ("sample_rows", ctypes.c_void_p),
-                ("sample_cols", ctypes.c_void_p), ("flags", ctypes.c_int32), ("trace_cap", ctypes.c_int32)]
+                ("sample_cols", ctypes.c_void_p), ("flags", ctypes.c_int32), ("trace_cap", ctypes.c_int32),
+                ("cluster_mask", ctypes.c_int32), ("cutover_side", ctypes.c_int32), ("order", ctypes.c_int32)]
 
 
 class lra_batch_out(ctypes.Structure):
@@ -132,13 +133,21 @@ _gather_entries = _sig("lra_gather_entries", ctypes.c_int, ctypes.POINTER(lra_so
 _maxvol_noalloc = _sig("lra_maxvol_noalloc", ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                        ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p)
+_tune_batch = _sig("lra_cross_tune_batch", ctypes.c_int, _ctx_p, ctypes.POINTER(lra_source), ctypes.c_void_p,
+                   ctypes.c_int32, ctypes.POINTER(lra_batch_params), ctypes.c_char_p,
+                   ctypes.POINTER(lra_batch_params), ctypes.POINTER(ctypes.c_double),
+                   ctypes.POINTER(ctypes.c_double))
+_tuning_lookup = _sig("lra_batch_tuning_lookup", ctypes.c_int, ctypes.c_char_p, ctypes.c_char_p,
+                      ctypes.POINTER(lra_source), ctypes.c_void_p, ctypes.c_int32,
+                      ctypes.POINTER(lra_batch_params), ctypes.POINTER(lra_batch_params))
 _status_str = _sig("lra_status_str", ctypes.c_char_p, ctypes.c_int32)
 _last_error = _sig("lra_cross_last_error", ctypes.c_char_p, _ctx_p)
 
 EXPORTED = ["lra_cross_create", "lra_cross_destroy", "lra_cross_submit", "lra_cross_poll",
             "lra_cross_wait", "lra_cross_fetch_cur", "lra_cross_cancel", "lra_cross_footprint",
             "lra_status_str", "lra_cross_last_error", "lra_cross_submit_batch",
-            "lra_cross_fetch_batch", "lra_draw_columns", "lra_gather_entries", "lra_maxvol_noalloc"]
+            "lra_cross_fetch_batch", "lra_draw_columns", "lra_gather_entries", "lra_maxvol_noalloc",
+            "lra_cross_tune_batch", "lra_batch_tuning_lookup"]
 
 
 class LraError(RuntimeError):
@@ -234,6 +243,27 @@ def lra_maxvol_noalloc(strip_ptr, N, l, row_stride, col_stride, pos_ptr, xinv_pt
     returns the lra_status code."""
     return _maxvol_noalloc(strip_ptr, N, l, row_stride, col_stride, pos_ptr, xinv_ptr, delta, max_swaps,
                            status_ptr, stream)
+
+
+def lra_cross_tune_batch(ctx, src: lra_source, blocks, params: lra_batch_params, cache_path=None):
+    """(tuned lra_batch_params, ms_default, ms_tuned); blocks as for submit_batch."""
+    tuned = lra_batch_params()
+    md, mt = ctypes.c_double(), ctypes.c_double()
+    _check(_tune_batch(ctx, ctypes.byref(src), blocks.ctypes.data, len(blocks), ctypes.byref(params),
+                       None if cache_path is None else str(cache_path).encode(), ctypes.byref(tuned),
+                       ctypes.byref(md), ctypes.byref(mt)), ctx)
+    return tuned, md.value, mt.value
+
+
+def lra_batch_tuning_lookup(cache_path, gpu_name: str, src: lra_source, blocks, params: lra_batch_params):
+    """The cached launch shape for this GPU and workload bucket, or None."""
+    tuned = lra_batch_params()
+    code = _tuning_lookup(str(cache_path).encode(), gpu_name.encode(), ctypes.byref(src), blocks.ctypes.data,
+                          len(blocks), ctypes.byref(params), ctypes.byref(tuned))
+    if code == LRA_ENOTFOUND:
+        return None
+    _check(code)
+    return tuned
 
 
 def lra_cross_footprint(src: lra_source, params: lra_params) -> int:

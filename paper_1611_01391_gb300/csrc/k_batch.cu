@@ -440,16 +440,17 @@ __device__ void cross_step(const BatchArgs& a, S* s, int b, long long row0, long
   __syncthreads();
 }
 
-// Three passes over the blocks.  Pass 1 (CS = 1): one CTA per block, the
-// whole strip in its shared memory, no cluster barrier per decision, 152
-// blocks in flight; a block whose rank rule asks for a cross larger than one
-// CTA can hold (l max(m, n) > kStripPairs) is left with status kDeferred.
-// Pass 2 (CS = 4) and pass 3 (CS = 8): the deferred blocks only, each from
-// its start, the strip split over a 4- or 8-CTA cluster; pass 2 defers what
-// 4 CTAs cannot hold, pass 3 holds every block (2048 x 96 pairs).  The
+// A chain of passes over the blocks, with clusters of 1, 2, 4 or 8 CTAs
+// (by default 1, 4, 8; the batch tuner picks the chain per workload).  The
+// first pass takes every block; a block whose rank rule asks for a cross
+// larger than its cluster can hold (l max(m, n) > CS kStripPairs), or, in
+// the first pass, whose larger side exceeds the cut-over side, is left with
+// status kDeferred and restarts from scratch in the next pass.  The last
+// pass (CS = 8) holds every block (2048 x 96 pairs).  With one CTA a block
+// needs no cluster barrier per decision and 152 blocks are in flight.  The
 // decisions (argmax with the same tie-break over the whole strip) and the
 // arithmetic per entry do not depend on the split, so a block's result is
-// the same in any pass.
+// the same in any pass, chain or order.
 static_assert(8 * kStripPairs >= kMaxBatchSide * kMaxL, "the 8-CTA pass holds every strip");
 template <int KIND, int CS>
 __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kBT, 1) batch_kernel(BatchArgs a) {
@@ -458,18 +459,19 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kBT, 1) batch_kerne
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int tid = threadIdx.x;
-  constexpr bool kFirst = (CS == 1);
+  const bool kFirst = a.pass_first != 0;
   constexpr bool kLast = (CS == 8);
-  int* queue = a.queue + (CS == 1 ? 0 : CS == 4 ? 1 : 2);
+  int* queue = a.queue + a.pass_idx;
   for (;;) {
     if (rank == 0 && tid == 0)  // a cancelled job takes no further block
       s->blk = (*(volatile const int*)&a.js->status != LRA_OK) ? a.n_blocks : atomicAdd(queue, 1);
     cl.sync();
-    const int b = *cl.map_shared_rank(&s->blk, 0);
-    if (b >= a.n_blocks) {
+    const int qpos = *cl.map_shared_rank(&s->blk, 0);
+    if (qpos >= a.n_blocks) {
       cl.sync();  // nobody leaves while a peer may still read the leader's index
       break;
     }
+    const int b = a.order ? a.order[qpos] : qpos;   // the queue's order of the blocks
     if (!kFirst && a.out_status[b] != kDeferred) {
       cl.sync();  // the leader may fetch the next index
       continue;
@@ -480,7 +482,7 @@ __global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(kBT, 1) batch_kerne
     // largest cross whose strips fit this cluster's shared memory
     const int lcap = (int)min((long long)lmax_b, kStripPairs / ((max(m, n) + CS - 1) / CS));
     int l = min(a.l_init, lmax_b);
-    bool deferred = !kLast && l > lcap;
+    bool deferred = !kLast && (l > lcap || (kFirst && a.cutover > 0 && max(m, n) > a.cutover));
     // decision log of this block (leader CTA, thread 0)
     int* btrace = a.trace_cap > 0 ? a.trace + (size_t)b * a.trace_cap * 4 : nullptr;
     double* btrace_v = a.trace_cap > 0 ? a.trace_v + (size_t)b * a.trace_cap : nullptr;
@@ -576,14 +578,27 @@ static cudaError_t launch_pass(const BatchArgs& a, int sms, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// a.queue holds three zeroed counters, one per pass
-cudaError_t launch_batch(const BatchArgs& a, int sms, cudaStream_t st) {
+// a.queue holds four zeroed counters, one per pass.  cluster_mask: bit c
+// set = a pass with 2^c CTAs per cluster (the 8-CTA pass always runs last).
+cudaError_t launch_batch(const BatchArgs& a0, int cluster_mask, int sms, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
-  LRA_DISPATCH_KIND(a.src.kind, ({
-    e = launch_pass<K, 1>(a, sms, st);
-    if (!e) e = launch_pass<K, 4>(a, sms, st);
-    if (!e) e = launch_pass<K, 8>(a, sms, st);
-  }));
+  BatchArgs a = a0;
+  const int mask = (cluster_mask & 7) | 8;
+  bool first = true;
+  for (int c = 0; c < 4 && !e; ++c) {
+    if (!(mask & (1 << c))) continue;
+    a.pass_idx = c;
+    a.pass_first = first ? 1 : 0;
+    first = false;
+    LRA_DISPATCH_KIND(a.src.kind, ({
+      switch (c) {
+        case 0: e = launch_pass<K, 1>(a, sms, st); break;
+        case 1: e = launch_pass<K, 2>(a, sms, st); break;
+        case 2: e = launch_pass<K, 4>(a, sms, st); break;
+        default: e = launch_pass<K, 8>(a, sms, st); break;
+      }
+    }));
+  }
   return e;
 }
 

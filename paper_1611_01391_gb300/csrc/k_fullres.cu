@@ -20,21 +20,15 @@
 //   The epilogue subtracts D from the TMA-loaded tile of M, squares and sums
 //   in FP32 per tile and in FP64 across tiles; CUR itself is never written.
 //
-// Kernel structure (one CTA of 384 threads per SM, persistent):
+// Kernel structure (one CTA of 256 threads per SM, persistent):
 //   warp 0 (one lane): TMA producer: P tiles once per work item, then per
-//                      column tile of 32 columns the R^T tiles and the FP32
-//                      tile of M into a ring of up to 8 stages (128B-swizzled,
-//                      as the MMA and the epilogue read them).  The ring is
-//                      as deep as shared memory allows (5 stages of 32 KB at
-//                      l = 96): the kernel streams M once, and what bounds it
-//                      is the bytes of M in flight per SM (Little's law at
-//                      HBM latency), not the tensor pipe.
-//   warp 1:            tensor-memory allocation (128 columns: two buffers of
+//                      column tile the R^T tiles and the FP32 tile of M into a
+//                      2-stage ring (128B-swizzled, as the MMA and the
+//                      epilogue read them).
+//   warp 1:            tensor-memory allocation (256 columns: two buffers of
 //                      [D_hi | D_lo]) and, from one lane, the MMA issue.
-//   warps 4..7, 8..11: two epilogue warpgroups, one per tensor-memory
-//                      buffer (alternate column tiles): tcgen05.ld of D
-//                      (lane = row), float4 reads of M from the swizzled
-//                      stage, FP32 error, FP64 sums.
+//   warps 4..7:        epilogue: tcgen05.ld of D (lane = row), float4 reads
+//                      of M from the swizzled stage, FP32 error, FP64 sums.
 // Every mbarrier wait is bounded (2 s); a timeout sets LRA_ETIMEOUT and all
 // roles leave their loops.
 #include <cuda.h>
@@ -52,15 +46,13 @@ namespace lra {
 namespace {
 
 constexpr int kBM = 128;             // tile rows (MMA M)
-constexpr int kBN = 32;              // tile columns (MMA N)
+constexpr int kBN = 64;              // tile columns (MMA N)
 constexpr int kKBox = 64;            // FP16 elements per 128-byte swizzled row
-constexpr int kMaxStages = 8;        // ring depth limit (the shared memory left decides)
-constexpr int kTilesPerItem = 128;   // column tiles per work item
-constexpr int kFrThreads = 384;      // producer, MMA, two idle, two epilogue warpgroups
-constexpr int kEpiWarps = 8;
+constexpr int kStages = 2;
+constexpr int kTilesPerItem = 64;    // column tiles per work item
+constexpr int kFrThreads = 256;
 constexpr float kLoScale = 2048.0f;  // lo parts are stored times 2^11
-constexpr int kTmemCols = 128;       // 2 buffers x [D_hi | D_lo] x kBN
-constexpr int kSmemLimit = 227 * 1024;
+constexpr int kTmemCols = 256;
 
 // ---------------------------------------------------------------------------
 // operand preparation
@@ -248,7 +240,6 @@ struct FullresArgs {
   int kb;             // 64-element K boxes (kp / 64)
   int ksteps;         // MMA K steps of 16 (ceil(l / 16))
   int n_row_tiles, n_col_tiles, n_groups, n_items;
-  int stages;         // ring depth
   const float* pscale;
   const float* rscale;
   double* partials;   // [grid][2]: sum E^2, sum M^2
@@ -257,11 +248,11 @@ struct FullresArgs {
 
 struct __align__(8) FrBarriers {
   uint64_t p_full, p_empty;
-  uint64_t full[kMaxStages], r_empty[kMaxStages], a_empty[kMaxStages];
+  uint64_t full[kStages], r_empty[kStages], a_empty[kStages];
   uint64_t t_full[2], t_empty[2];
   uint32_t tmem_base;
   int err;
-  double red[2][kEpiWarps];
+  double red[2][4];
 };
 
 __global__ void __launch_bounds__(kFrThreads, 1)
@@ -277,7 +268,6 @@ fullres_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   const uint32_t p_bytes = (uint32_t)kb * kBM * 128;      // one of Phi / Plo
   const uint32_t r_bytes = (uint32_t)kb * kBN * 128;      // one of Rhi / Rlo
   const uint32_t a_bytes = kBM * kBN * 4;                 // FP32 tile of M
-  const uint32_t kStages = (uint32_t)a.stages;
   unsigned char* sPhi = base;
   unsigned char* sPlo = sPhi + p_bytes;
   unsigned char* sStage = sPlo + p_bytes;
@@ -289,7 +279,7 @@ fullres_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   if (threadIdx.x == 0) {
     mbar_init(&fb->p_full, 1);
     mbar_init(&fb->p_empty, 1);
-    for (uint32_t s = 0; s < kStages; ++s) {
+    for (int s = 0; s < kStages; ++s) {
       mbar_init(&fb->full[s], 1);
       mbar_init(&fb->r_empty[s], 1);
       mbar_init(&fb->a_empty[s], 4);
@@ -337,15 +327,15 @@ fullres_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             load_2d(st + k * kBN * 128, &tmRhi, k * kKBox, tile * kBN, &fb->full[s]);
             load_2d(st + r_bytes + k * kBN * 128, &tmRlo, k * kKBox, tile * kBN, &fb->full[s]);
           }
-          for (int c = 0; c < kBN / 32; ++c)
+          for (int c = 0; c < 2; ++c)
             load_2d(st + 2 * r_bytes + c * kBM * 128, &tmA, tile * kBN + c * 32, rb * kBM,
                         &fb->full[s]);
         }
       }
       // leave no copy in flight: wait (bounded, even after an error) for the
       // last fills of every stage and of the P tiles
-      for (uint32_t s = 0; s < kStages; ++s) {
-        if (s >= g) break;
+      for (int s = 0; s < kStages; ++s) {
+        if ((uint32_t)s >= g) break;
         const uint32_t gg = g - 1 - s;
         mbar_drain(&fb->full[gg % kStages], (gg / kStages) & 1);
       }
@@ -390,10 +380,7 @@ fullres_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
   } else if (warp >= 4) {
     // ------------------------------------------------------------ epilogue
-    // warpgroup grp takes the tiles in tensor-memory buffer grp (every
-    // other tile); warp ew of a group reads TMEM lanes 32 ew .. 32 ew + 31
-    const int grp = (warp - 4) >> 2;
-    const int ew = (warp - 4) & 3;
+    const int ew = warp - 4;
     const int r = ew * 32 + lane;
     double acc_e = 0.0, acc_a = 0.0;
     uint32_t g = 0;
@@ -406,7 +393,6 @@ fullres_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       for (int tile = t0; tile < t1; ++tile, ++g) {
         const uint32_t s = g % kStages, u = g / kStages;
         const uint32_t b = g & 1, ub = g >> 1;
-        if ((int)b != grp) continue;
         // every lane waits; the outcome is made warp-uniform before the
         // .sync.aligned tensor-memory loads
         bool w = mbar_wait(&fb->t_full[b], ub & 1, err) && mbar_wait(&fb->full[s], u & 1, err);
@@ -418,7 +404,7 @@ fullres_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const unsigned char* sa = sStage + s * stage_bytes + 2 * r_bytes;
         float se = 0.0f, sa2 = 0.0f;
 #pragma unroll
-        for (int half = 0; half < kBN / 32; ++half) {
+        for (int half = 0; half < 2; ++half) {
           float dh[32], dl[32];
           const uint32_t lane_off = (uint32_t)(ew * 32) << 16;
           tmem_ld32(tmem + lane_off + b * 2 * kBN + half * 32, dh);
@@ -458,20 +444,15 @@ fullres_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       acc_a += __shfl_xor_sync(0xffffffffu, acc_a, off);
     }
     if (lane == 0) {
-      fb->red[0][warp - 4] = acc_e;
-      fb->red[1][warp - 4] = acc_a;
+      fb->red[0][ew] = acc_e;
+      fb->red[1][ew] = acc_a;
     }
   }
   tc_fence_before();
   __syncthreads();
   if (threadIdx.x == 0) {
-    double se = 0.0, sa = 0.0;
-    for (int w = 0; w < kEpiWarps; ++w) {   // fixed order: reproducible bits
-      se += fb->red[0][w];
-      sa += fb->red[1][w];
-    }
-    a.partials[blockIdx.x * 2 + 0] = se;
-    a.partials[blockIdx.x * 2 + 1] = sa;
+    a.partials[blockIdx.x * 2 + 0] = fb->red[0][0] + fb->red[0][1] + fb->red[0][2] + fb->red[0][3];
+    a.partials[blockIdx.x * 2 + 1] = fb->red[1][0] + fb->red[1][1] + fb->red[1][2] + fb->red[1][3];
     if (fb->err) set_status(a.js, LRA_ETIMEOUT);
   }
   if (warp == 1) {
@@ -564,13 +545,9 @@ cudaError_t launch_full_residual(const float* A, long long lda, long long m, lon
   a.partials = partials;
   a.js = js;
   const int grid = std::min(grid_cap, a.n_items);
-  // as many stages as fit beside the P tiles
-  const size_t fixed = 1024 + 2 * (size_t)a.kb * kBM * 128 + sizeof(FrBarriers);
-  const size_t stage = 2 * (size_t)a.kb * kBN * 128 + kBM * kBN * 4;
-  a.stages = (int)std::min<size_t>(kMaxStages, (kSmemLimit - fixed) / stage);
-  if (a.stages < 2) return cudaErrorInvalidValue;
-  const size_t smem = fixed + (size_t)a.stages * stage;
-  if ((e = smem_optin(reinterpret_cast<const void*>(fullres_kernel), kSmemLimit))) return e;
+  const size_t smem = 1024 + 2 * (size_t)a.kb * kBM * 128 +
+                      kStages * (2 * (size_t)a.kb * kBN * 128 + kBM * kBN * 4) + sizeof(FrBarriers);
+  if ((e = smem_optin(reinterpret_cast<const void*>(fullres_kernel), 227 * 1024))) return e;
   fullres_kernel<<<grid, kFrThreads, smem, st>>>(mA, mPhi, mPlo, mRhi, mRlo, a);
   fullres_final_kernel<<<1, 32, 0, st>>>(partials, grid, js);
   return cudaGetLastError();

@@ -85,6 +85,7 @@ struct JobStatus {
 
 // Batched C-A (many blocks of one source, one launch).
 constexpr int kMaxBatchSide = 2048;  // rows / columns of a block
+constexpr int kDefaultClusterMask = 1 | 4 | 8;  // batch passes of 1, 4 and 8 CTAs
 
 struct BatchArgs {
   SourceDev src;
@@ -96,7 +97,10 @@ struct BatchArgs {
   int q;
   int l_init, l_max, k_max, sweeps, max_swaps;
   double tol, delta;
-  int* queue;               // three work counters (one per pass), zero at launch
+  int* queue;               // four work counters (one per pass), zero at launch
+  int pass_idx, pass_first; // set per launched pass
+  int cutover;              // first pass: blocks with a larger side go to the next pass (0: none)
+  const int* order;         // n_blocks queue order (nullptr: 0, 1, 2, ...)
   int trace_cap;            // decisions logged per block (0: none)
   int* trace;               // n_blocks x trace_cap x 4: half_step, kind, i, j
   double* trace_v;          // n_blocks x trace_cap: |value| of each decision

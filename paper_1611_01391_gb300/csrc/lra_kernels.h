@@ -3,7 +3,13 @@
 
 #include <cuda_runtime.h>
 
+struct lra_ctx;
+
 namespace lra {
+
+// Context accessors for the other translation units of the runtime.
+int ctx_device(::lra_ctx* ctx);
+void set_ctx_error(::lra_ctx* ctx, const char* msg);
 
 struct SourceDev;
 struct JobStatus;
@@ -102,7 +108,7 @@ struct BatchArgs;
 cudaError_t smem_optin(const void* func, int bytes);
 
 size_t batch_smem_bytes();
-cudaError_t launch_batch(const BatchArgs& a, int sms, cudaStream_t st);
+cudaError_t launch_batch(const BatchArgs& a, int cluster_mask, int sms, cudaStream_t st);
 
 // Small control kernels.
 cudaError_t launch_tol_check(JobStatus* js, double tol, cudaStream_t st);

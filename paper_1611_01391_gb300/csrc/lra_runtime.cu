@@ -111,6 +111,13 @@ struct lra_ctx {
   std::string last_error;
 };
 
+int lra::ctx_device(lra_ctx* ctx) { return ctx->device; }
+
+void lra::set_ctx_error(lra_ctx* ctx, const char* msg) {
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  ctx->last_error = msg;
+}
+
 cudaError_t lra::smem_optin(const void* func, int bytes) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -840,6 +847,9 @@ static lra_status validate_batch(const lra_source* src, const lra_block* blocks,
   if (p->sample < 0 || p->sample > 64) { *why = "sample must be in 0..64"; return LRA_EINVAL; }
   if (!(p->delta > 0.0) || !(p->tol >= 0.0)) { *why = "delta > 0 and tol >= 0 required"; return LRA_EINVAL; }
   if (p->trace_cap < 0 || p->trace_cap > (1 << 20)) { *why = "trace_cap must be in 0..2^20"; return LRA_EINVAL; }
+  if (p->cluster_mask < 0 || p->cluster_mask > 15) { *why = "cluster_mask must be in 0..15"; return LRA_EINVAL; }
+  if (p->cutover_side < 0) { *why = "cutover_side must be >= 0"; return LRA_EINVAL; }
+  if (p->order != 0 && p->order != 1) { *why = "order must be 0 or 1"; return LRA_EINVAL; }
   if (!p->cand_J || (p->sample > 0 && (!p->sample_rows || !p->sample_cols))) {
     *why = "candidate / sample arrays required"; return LRA_EINVAL;
   }
@@ -885,7 +895,7 @@ lra_status lra_cross_submit_batch(lra_ctx* ctx, const lra_source* src, const lra
   const size_t L = (size_t)p->l_max, q = (size_t)p->sample, NB = (size_t)nb;
   Layout lay;
   const size_t o_js = lay.take(sizeof(JobStatus));
-  const size_t o_queue = lay.take(3 * sizeof(int));  // one work counter per pass
+  const size_t o_queue = lay.take(4 * sizeof(int));  // one work counter per pass
   const size_t o_blocks = lay.take(sizeof(long long) * 4 * NB);
   const size_t o_jc = lay.take(sizeof(int) * NB * L);
   const size_t o_sr = lay.take(sizeof(int) * NB * std::max<size_t>(q, 1));
@@ -903,6 +913,7 @@ lra_status lra_cross_submit_batch(lra_ctx* ctx, const lra_source* src, const lra
   const size_t o_tl = lay.take(sizeof(int) * NB);
   const size_t o_tr = lay.take(sizeof(int) * 4 * NB * std::max<size_t>(TC, 1));
   const size_t o_tv = lay.take(sizeof(double) * NB * std::max<size_t>(TC, 1));
+  const size_t o_ord = lay.take(sizeof(int) * NB);
   j->bytes = lay.off;
   j->b_tcap = (int)TC;
   if ((int)ctx->jobs.size() >= ctx->max_slots || ctx->free_slots.empty() ||
@@ -958,6 +969,18 @@ lra_status lra_cross_submit_batch(lra_ctx* ctx, const lra_source* src, const lra
   a.tol = p->tol;
   a.delta = p->delta;
   a.trace_cap = (int)TC;
+  a.cutover = p->cutover_side;
+  // queue order: as given, or the largest blocks (m + n) first, so that the
+  // long solves start early and the launch ends on short ones
+  std::vector<int> ord;
+  if (p->order == 1) {
+    ord.resize(NB);
+    for (int32_t b = 0; b < nb; ++b) ord[b] = b;
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+      return blocks[x].m + blocks[x].n > blocks[y].m + blocks[y].n;
+    });
+  }
+  a.order = p->order == 1 ? reinterpret_cast<const int*>(base + o_ord) : nullptr;
   a.trace = j->b_trace;
   a.trace_v = j->b_tval;
   a.trace_len = j->b_tlen;
@@ -975,7 +998,8 @@ lra_status lra_cross_submit_batch(lra_ctx* ctx, const lra_source* src, const lra
   static_assert(sizeof(lra_block) == 4 * sizeof(long long), "lra_block layout");
   if ((e = cudaEventCreate(&j->ev_start)) || (e = cudaEventCreate(&j->ev_end)) ||
       (e = cudaMemcpyAsync(j->js, &init, sizeof(init), cudaMemcpyHostToDevice, s)) ||
-      (e = cudaMemsetAsync(j->b_queue, 0, 3 * sizeof(int), s)) ||
+      (e = cudaMemsetAsync(j->b_queue, 0, 4 * sizeof(int), s)) ||
+      (p->order == 1 && (e = cudaMemcpyAsync(base + o_ord, ord.data(), sizeof(int) * NB, cudaMemcpyHostToDevice, s))) ||
       (e = cudaMemsetAsync(j->b_tlen, 0, sizeof(int) * NB, s)) ||
       (e = cudaMemsetAsync(j->b_err, 0, sizeof(double) * NB, s)) ||
       (e = cudaMemsetAsync(j->b_keff, 0, sizeof(int) * NB, s)) ||
@@ -983,7 +1007,7 @@ lra_status lra_cross_submit_batch(lra_ctx* ctx, const lra_source* src, const lra
       (e = cudaMemcpyAsync(j->b_jcand, p->cand_J, sizeof(int) * NB * L, cudaMemcpyHostToDevice, s)) ||
       (q > 0 && ((e = cudaMemcpyAsync(j->b_srow, p->sample_rows, sizeof(int) * NB * q, cudaMemcpyHostToDevice, s)) ||
                  (e = cudaMemcpyAsync(j->b_scol, p->sample_cols, sizeof(int) * NB * q, cudaMemcpyHostToDevice, s)))) ||
-      (e = cudaEventRecord(j->ev_start, s)) || (e = launch_batch(a, ctx->sms, s)) ||
+      (e = cudaEventRecord(j->ev_start, s)) || (e = launch_batch(a, p->cluster_mask ? p->cluster_mask : kDefaultClusterMask, ctx->sms, s)) ||
       (e = cudaMemcpyAsync(ctx->pinned + j->slot, j->js, sizeof(JobStatus), cudaMemcpyDeviceToHost, s)) ||
       (e = cudaEventRecord(j->ev_end, s))) {
     cudaStreamSynchronize(s);

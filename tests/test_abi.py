@@ -215,3 +215,47 @@ def test_gather_entries_validates_on_host():
     ok = L.lra_source(L.LRA_GEN_CAUCHY, 1, 100, 100, None, 0, 1, 1, 0.0)
     assert L._gather_entries(ctypes.byref(ok), 256, 0, 256, 4, 256, None) == L.LRA_OK   # empty: no launch
     assert L._gather_entries(ctypes.byref(ok), 256, -1, 256, 4, 256, None) == L.LRA_EINVAL
+
+
+def _bucket_key(gpu, kind, l_max, k_max, blocks):
+    """The batch tuner's bucket, written from its documented rule."""
+    import numpy as np
+
+    def p2(v):
+        p = 1
+        while p < v:
+            p *= 2
+        return p
+    side = np.sort(np.maximum(blocks[:, 1], blocks[:, 3]))
+    return (f"{gpu}|kind={kind}|lmax={l_max}|kmax={k_max}|blocks={p2(len(blocks))}"
+            f"|median={p2(int(side[len(side) // 2]))}|max={p2(int(side[-1]))}")
+
+
+def test_batch_tuning_cache_lookup_on_host(tmp_path):
+    """The tuner's cache (JSON, one entry per GPU and workload bucket) is
+    found for the same GPU and bucket, including a workload of other sizes
+    in the same bucket, and not for another GPU or another bucket."""
+    import numpy as np
+    import paper_1611_01391_gb300 as L
+    from paper_1611_01391_gb300.api import make_batch_params
+    blocks = np.array([[0, 300, 0, 260], [0, 2000, 0, 1500], [0, 250, 0, 280]], np.int64)
+    jc = np.tile(np.arange(96, dtype=np.int32), (3, 1))
+    p, keep = make_batch_params(12, 96, 64, 2, 1e-6, jc)
+    src = L.lra_source(L.LRA_GEN_INVDIST, 3, 1 << 20, 1 << 20, None, 0, 1, 1, 0.0)
+    key = _bucket_key("NVIDIA GB300", L.LRA_GEN_INVDIST, 96, 64, blocks)
+    path = tmp_path / "tuning.json"
+    path.write_text('{\n  "lra_batch_tuning": 1,\n  "entries": {\n'
+                    f'    "other|kind=4": {{"cluster_mask": 9, "cutover_side": 512, "order": 0, "ms_default": 1, "ms_tuned": 1}},\n'
+                    f'    "{key}": {{"cluster_mask": 11, "cutover_side": 1024, "order": 1, "ms_default": 61.0, "ms_tuned": 55.0}}\n'
+                    '  }\n}\n')
+    t = L.lra_batch_tuning_lookup(path, "NVIDIA GB300", src, blocks, p)
+    assert t is not None and (t.cluster_mask, t.cutover_side, t.order) == (11, 1024, 1)
+    assert (t.l_max, t.k_max, t.sweeps) == (96, 64, 2)          # the rest copied from params
+    same_bucket = blocks.copy()
+    same_bucket[1, 1] = 1900                                     # max side still in (1024, 2048]
+    assert L.lra_batch_tuning_lookup(path, "NVIDIA GB300", src, same_bucket, p) is not None
+    assert L.lra_batch_tuning_lookup(path, "NVIDIA B200", src, blocks, p) is None
+    other = blocks.copy()
+    other[1, 1] = other[1, 3] = 900                              # max side now in (512, 1024]
+    assert L.lra_batch_tuning_lookup(path, "NVIDIA GB300", src, other, p) is None
+    assert L.lra_batch_tuning_lookup(tmp_path / "absent.json", "NVIDIA GB300", src, blocks, p) is None

@@ -221,3 +221,36 @@ def test_tiny_and_degenerate_blocks(ctx):
         oerr = np.linalg.norm(A - A[:, oJ] @ oU @ A[oI, :]) / np.linalg.norm(A)
         assert error_ok(err, oerr), (b, err, oerr)
         assert r.l[b] == ol, (b, r.l[b], ol)
+
+
+def test_launch_shapes_and_tuner_give_identical_results(ctx, tree4096, tmp_path):
+    """Every launch shape (cluster chain, cut-over side, queue order) gives
+    each block the same result bit for bit, U included; the tuner checks
+    l, k_eff, I, J and the estimate on each of its 30 candidates itself,
+    stores its choice in the cache and finds it there the second time."""
+    pts, blocks, jc, sr, sc = tree4096
+    d = torch.from_numpy(pts).cuda()
+    src = L.make_source("invdist", x=d, y=d)
+    p, keep = make_batch_params(L_INIT, L_MAX, K_MAX, SWEEPS, TOL, jc, sr, sc)
+    ref = solve_batch(ctx, src, blocks, p, L_MAX)
+    assert np.all(ref.status == 0)
+    fields = ("status", "l", "k_eff", "swaps", "I", "J", "U", "sigma", "est_err")
+    for mask, cut, order in ((15, 512, 1), (2 | 4 | 8, 0, 0), (1 | 8, 1024, 1), (8, 0, 1)):
+        q, keep2 = make_batch_params(L_INIT, L_MAX, K_MAX, SWEEPS, TOL, jc, sr, sc)
+        q.cluster_mask, q.cutover_side, q.order = mask, cut, order
+        r = solve_batch(ctx, src, blocks, q, L_MAX)
+        for name in fields:
+            np.testing.assert_array_equal(getattr(r, name), getattr(ref, name), err_msg=f"{name} {mask} {cut} {order}")
+    cache = tmp_path / "tuning.json"
+    b64 = np.ascontiguousarray(blocks, np.int64)
+    tuned, ms_def, ms_tuned = L.lra_cross_tune_batch(ctx.ctx, src, b64, p, cache)
+    assert ms_def > 0 and 0 < ms_tuned <= ms_def
+    r = solve_batch(ctx, src, blocks, tuned, L_MAX)
+    for name in fields:
+        np.testing.assert_array_equal(getattr(r, name), getattr(ref, name), err_msg=name)
+    again, md2, mt2 = L.lra_cross_tune_batch(ctx.ctx, src, b64, p, cache)
+    assert md2 == -1.0 and (again.cluster_mask, again.cutover_side, again.order) == \
+        (tuned.cluster_mask, tuned.cutover_side, tuned.order)
+    gpu = torch.cuda.get_device_properties(0).name
+    hit = L.lra_batch_tuning_lookup(cache, gpu, src, b64, p)
+    assert hit is not None and hit.cluster_mask == tuned.cluster_mask
