@@ -265,6 +265,43 @@ typedef struct {
 lra_status lra_cross_submit_batch(lra_ctx* ctx, const lra_source* src, const lra_block* blocks,
                                   int32_t n_blocks, const lra_batch_params* params, lra_job* out);
 
+/* ---- Cynical algorithms (Section 6.5), as in Tests 3 and 4 of Section 12.2
+ * Tests 3: a Cynical algorithm with p = q: the r x r CUR generator of M is
+ *   taken from the q x q submatrix M[K, L] (q = 4 r in the paper), as the
+ *   generator of locally maximal volume that C-A iterations inside M[K, L]
+ *   find (inner_sweeps sweeps from its first r columns, the first vertical
+ *   step starting from Gaussian elimination).
+ * Tests 4: outer_loops C-A loops on M with q x q generators from the
+ *   columns L (giving K', L'), then Tests 3 on M[K', L'].
+ * Output: I = K[I'], J = L[J'] and U = (M[I, J]_r)^+ (the inverse of a
+ * nonsingular generator, as in Tests 1). */
+typedef struct {
+  int32_t r;                  /* generator size, 1 <= r <= q                         */
+  int32_t q;                  /* |K| = |L| = q, q <= 96 and q <= min(m, n)           */
+  int32_t outer_loops;        /* 0: Tests 3 (K and L given); >= 1: Tests 4            */
+  int32_t inner_sweeps;       /* C-A sweeps inside M[K, L], >= 1                      */
+  double delta;               /* maxvol stops when max |B| <= 1 + delta (> 0)         */
+  double rank_tol;            /* nucleus keeps sigma_j > rank_tol sigma_1             */
+  const int32_t* K;           /* host, q distinct rows (Tests 3; unused for Tests 4)  */
+  const int32_t* L;           /* host, q distinct columns                             */
+} lra_cynical_params;
+
+typedef struct {
+  int32_t* I;                 /* host, r rows of M                                   */
+  int32_t* J;                 /* host, r columns of M                                */
+  double* U;                  /* host, r x r nucleus, row-major                      */
+  int32_t* K;                 /* host, q rows of the submatrix used (nullable)       */
+  int32_t* L;                 /* host, q columns of the submatrix used (nullable)    */
+} lra_cynical_out;
+
+/* Run Tests 3 or 4 on ctx (blocking): the outer solve and the inner solve
+ * are ordinary jobs of the context (its slots and budget apply), the
+ * submatrix M[K, L] is gathered on the device with the entry kernel of
+ * lra_gather_entries.  LRA_EINVAL for bad sizes or index sets; a job's own
+ * failure status otherwise. */
+lra_status lra_cross_cynical(lra_ctx* ctx, const lra_source* src, const lra_cynical_params* params,
+                             const lra_cynical_out* out);
+
 /* Launch-shape tuner of the batched form (the paper has no counterpart:
  * the shape does not change any result).  Looks up, in the JSON file at
  * cache_path (NULL: no cache), the shape stored for this GPU (device name)

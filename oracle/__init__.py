@@ -13,14 +13,14 @@ sample is the whole matrix; Table tb_ranrc error levels (Section 12.3).
 """
 from .ca import (CAP, GEPP, STOP, SWAP, Cauchy, CrossResult, Dense, Gauss,
                  InvDist, OracleSingular, columns, cross_approximation,
-                 cross_approximation_adaptive, draw_columns, splitmix64,
+                 cross_approximation_adaptive, draw_columns, splitmix64, cynical, ca_cynical,
                  full_residual, gepp_rows, maxvol, nucleus, random_cross, rows,
                  sampled_residual)
 
 __all__ = [
     "CAP", "GEPP", "STOP", "SWAP", "Cauchy", "CrossResult", "Dense", "Gauss",
     "InvDist", "OracleSingular", "columns", "cross_approximation",
-    "cross_approximation_adaptive", "draw_columns", "splitmix64",
+    "cross_approximation_adaptive", "draw_columns", "splitmix64", "cynical", "ca_cynical",
     "full_residual", "gepp_rows", "maxvol", "nucleus", "random_cross", "rows",
     "sampled_residual",
 ]

@@ -440,6 +440,68 @@ def cross_approximation_adaptive(src, J_cands, l_init, l_max, k_max, sweeps, tol
 
 
 # ---------------------------------------------------------------------------
+# Cynical algorithms (Section 6.5) in the forms of Section 12.2, Tests 3 and 4
+# ---------------------------------------------------------------------------
+
+class _Sub:
+    """The submatrix M[K, L] of a source, as a source of its own."""
+
+    def __init__(self, src, K, L):
+        self.src, self.K, self.L = src, np.asarray(K), np.asarray(L)
+        self.m, self.n = len(self.K), len(self.L)
+
+    def block(self, rows, cols):
+        return self.src.block(self.K[np.asarray(rows)], self.L[np.asarray(cols)])
+
+
+@dataclass
+class CynicalResult:
+    I: list
+    J: list
+    U: np.ndarray
+    K: list
+    L: list
+    inner: CrossResult
+    outer: CrossResult | None = None
+
+
+def cynical(src, K, L, r, inner_sweeps=2, delta=1e-2, rank_tol=1e-12, max_swaps=None):
+    """Tests 3 of Section 12.2, the Cynical algorithm of Section 6.5 with
+    p x q = |K| x |L|: an r x r CUR generator of the submatrix M[K, L] with
+    locally maximal volume, computed by C-A iterations inside that
+    submatrix (maxvol over its rows, then over its columns, alternately,
+    from its first r columns; the first vertical step starts from Gaussian
+    elimination), is taken as the generator of M: I = K[I'], J = L[J'] and
+    U = (M[I, J]_r)^+ (the inverse for a nonsingular generator, as in
+    Tests 1).  Returns a CynicalResult."""
+    K = [int(k) for k in K]
+    L = [int(j) for j in L]
+    if not (1 <= r <= min(len(K), len(L))):
+        raise ValueError("need 1 <= r <= min(|K|, |L|)")
+    sub = _Sub(src, K, L)
+    inner = cross_approximation(sub, list(range(r)), k=r, sweeps=inner_sweeps, delta=delta,
+                                rank_tol=rank_tol, max_swaps=max_swaps)
+    I = [K[i] for i in inner.I]
+    J = [L[j] for j in inner.J]
+    return CynicalResult(I=I, J=J, U=inner.U, K=K, L=L, inner=inner)
+
+
+def ca_cynical(src, L0, r, outer_loops=1, inner_sweeps=2, delta=1e-2, rank_tol=1e-12,
+               max_swaps=None):
+    """Tests 4 of Section 12.2: from the column set L0 (|L0| = q, 4 r in the
+    paper) C-A loops with q x q generators (a vertical step: K' of locally
+    maximal volume in M[:, L0]; a horizontal step: L' of locally maximal
+    volume in M[K', :]), then Tests 3 on M[K', L'].  Returns a
+    CynicalResult with the outer C-A run attached."""
+    q = len(L0)
+    outer = cross_approximation(src, L0, k=q, sweeps=outer_loops, delta=delta,
+                                rank_tol=rank_tol, max_swaps=max_swaps)
+    res = cynical(src, outer.I, outer.J, r, inner_sweeps, delta, rank_tol, max_swaps)
+    res.outer = outer
+    return res
+
+
+# ---------------------------------------------------------------------------
 # Initial column set from a seed (Section 12.2: the tests start from random
 # columns), for callers that pass a seed instead of the columns
 # ---------------------------------------------------------------------------

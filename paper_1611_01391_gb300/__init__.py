@@ -79,6 +79,17 @@ class lra_cur_out(ctypes.Structure):
                 ("R", ctypes.c_void_p), ("trace", ctypes.c_void_p), ("trace_val", ctypes.c_void_p)]
 
 
+class lra_cynical_params(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_int32), ("q", ctypes.c_int32), ("outer_loops", ctypes.c_int32),
+                ("inner_sweeps", ctypes.c_int32), ("delta", ctypes.c_double), ("rank_tol", ctypes.c_double),
+                ("K", ctypes.c_void_p), ("L", ctypes.c_void_p)]
+
+
+class lra_cynical_out(ctypes.Structure):
+    _fields_ = [("I", ctypes.c_void_p), ("J", ctypes.c_void_p), ("U", ctypes.c_void_p),
+                ("K", ctypes.c_void_p), ("L", ctypes.c_void_p)]
+
+
 class lra_block(ctypes.Structure):
     _fields_ = [("row0", ctypes.c_int64), ("m", ctypes.c_int64),
                 ("col0", ctypes.c_int64), ("n", ctypes.c_int64)]
@@ -140,6 +151,8 @@ _tune_batch = _sig("lra_cross_tune_batch", ctypes.c_int, _ctx_p, ctypes.POINTER(
 _tuning_lookup = _sig("lra_batch_tuning_lookup", ctypes.c_int, ctypes.c_char_p, ctypes.c_char_p,
                       ctypes.POINTER(lra_source), ctypes.c_void_p, ctypes.c_int32,
                       ctypes.POINTER(lra_batch_params), ctypes.POINTER(lra_batch_params))
+_cynical = _sig("lra_cross_cynical", ctypes.c_int, _ctx_p, ctypes.POINTER(lra_source),
+                ctypes.POINTER(lra_cynical_params), ctypes.POINTER(lra_cynical_out))
 _status_str = _sig("lra_status_str", ctypes.c_char_p, ctypes.c_int32)
 _last_error = _sig("lra_cross_last_error", ctypes.c_char_p, _ctx_p)
 
@@ -147,7 +160,7 @@ EXPORTED = ["lra_cross_create", "lra_cross_destroy", "lra_cross_submit", "lra_cr
             "lra_cross_wait", "lra_cross_fetch_cur", "lra_cross_cancel", "lra_cross_footprint",
             "lra_status_str", "lra_cross_last_error", "lra_cross_submit_batch",
             "lra_cross_fetch_batch", "lra_draw_columns", "lra_gather_entries", "lra_maxvol_noalloc",
-            "lra_cross_tune_batch", "lra_batch_tuning_lookup"]
+            "lra_cross_tune_batch", "lra_batch_tuning_lookup", "lra_cross_cynical"]
 
 
 class LraError(RuntimeError):
@@ -243,6 +256,24 @@ def lra_maxvol_noalloc(strip_ptr, N, l, row_stride, col_stride, pos_ptr, xinv_pt
     returns the lra_status code."""
     return _maxvol_noalloc(strip_ptr, N, l, row_stride, col_stride, pos_ptr, xinv_ptr, delta, max_swaps,
                            status_ptr, stream)
+
+
+def lra_cross_cynical(ctx, src: lra_source, r: int, L, K=None, outer_loops: int = 1, inner_sweeps: int = 2,
+                      delta: float = 1e-2, rank_tol: float = 1e-6):
+    """Tests 3 (K given, outer_loops = 0) or Tests 4 (outer_loops >= 1):
+    returns (I, J, U, K used, L used) as numpy arrays."""
+    import numpy as np
+    Lh = np.ascontiguousarray(L, dtype=np.int32)
+    q = len(Lh)
+    Kh = None if K is None else np.ascontiguousarray(K, dtype=np.int32)
+    p = lra_cynical_params(r, q, outer_loops, inner_sweeps, delta, rank_tol,
+                           None if Kh is None else Kh.ctypes.data, Lh.ctypes.data)
+    I, J = np.zeros(r, np.int32), np.zeros(r, np.int32)
+    U = np.zeros((r, r), np.float64)
+    Ko, Lo = np.zeros(q, np.int32), np.zeros(q, np.int32)
+    o = lra_cynical_out(I.ctypes.data, J.ctypes.data, U.ctypes.data, Ko.ctypes.data, Lo.ctypes.data)
+    _check(_cynical(ctx, ctypes.byref(src), ctypes.byref(p), ctypes.byref(o)), ctx)
+    return I, J, U, Ko, Lo
 
 
 def lra_cross_tune_batch(ctx, src: lra_source, blocks, params: lra_batch_params, cache_path=None):

@@ -829,6 +829,84 @@ lra_status lra_gather_entries(const lra_source* src, const int32_t* rows, int64_
   return e == cudaSuccess ? LRA_OK : (e == cudaErrorMemoryAllocation ? LRA_ENOMEM : LRA_ECUDA);
 }
 
+// Tests 3 / 4 of Section 12.2: one or two ordinary jobs of the context
+// with the submatrix M[K, L] gathered between them (host orchestration).
+lra_status lra_cross_cynical(lra_ctx* ctx, const lra_source* src, const lra_cynical_params* p,
+                             const lra_cynical_out* out) {
+  if (!ctx || !src || !p || !out || !out->I || !out->J || !out->U) return LRA_EINVAL;
+  std::string why;
+  if (validate_source(src, &why) != LRA_OK) return fail(ctx, LRA_EINVAL, why);
+  const int q = p->q, r = p->r;
+  if (q < 1 || q > kMaxL || q > src->m || q > src->n || r < 1 || r > q || p->inner_sweeps < 1 ||
+      p->outer_loops < 0 || p->outer_loops > 1000 || !(p->delta > 0.0) || !(p->rank_tol >= 0.0) || !p->L ||
+      (p->outer_loops == 0 && !p->K))
+    return fail(ctx, LRA_EINVAL, "cynical: bad sizes or index sets");
+  if (!distinct_in_range(p->L, q, src->n) || (p->outer_loops == 0 && !distinct_in_range(p->K, q, src->m)))
+    return fail(ctx, LRA_EINVAL, "cynical: K and L must hold q distinct indices of M");
+  std::vector<int32_t> K(q), L(q);
+  lra_status st;
+  if (p->outer_loops > 0) {
+    // the outer C-A loops with q x q generators
+    lra_params op{};
+    op.k = q; op.l = q; op.sweeps = p->outer_loops; op.delta = p->delta; op.rank_tol = p->rank_tol;
+    op.init_J = p->L;
+    lra_job job = 0;
+    if ((st = lra_cross_submit(ctx, src, &op, &job)) != LRA_OK) return st;
+    lra_cur_out o{};
+    std::vector<double> Uq((size_t)q * q);
+    o.I = K.data(); o.J = L.data(); o.U = Uq.data();
+    if ((st = lra_cross_fetch_cur(ctx, job, &o)) != LRA_OK) return st;
+  } else {
+    std::memcpy(K.data(), p->K, sizeof(int32_t) * q);
+    std::memcpy(L.data(), p->L, sizeof(int32_t) * q);
+  }
+  // M[K, L] on the device (the entries every kernel sees)
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e) return cuda_fail(ctx, e, "cudaSetDevice");
+  cudaStream_t sst = ctx->stream;
+  unsigned char* buf = nullptr;
+  // q <= 96: rows at 0, columns at 512, the q x q submatrix at 1024
+  const size_t o_rows = 0, o_cols = 512, o_S = 1024;
+  const size_t bytes = o_S + sizeof(float) * (size_t)q * q;
+  if ((e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&buf), bytes, ctx->pool, sst)))
+    return cuda_fail(ctx, e, "cudaMallocFromPoolAsync");
+  int32_t* rows = reinterpret_cast<int32_t*>(buf + o_rows);
+  int32_t* cols = reinterpret_cast<int32_t*>(buf + o_cols);
+  float* S = reinterpret_cast<float*>(buf + o_S);
+  if (!(e = cudaMemcpyAsync(rows, K.data(), sizeof(int32_t) * q, cudaMemcpyHostToDevice, sst)) &&
+      !(e = cudaMemcpyAsync(cols, L.data(), sizeof(int32_t) * q, cudaMemcpyHostToDevice, sst)) &&
+      !(e = launch_gather_entries(make_src(src), rows, q, cols, q, S, sst)))
+    e = cudaStreamSynchronize(sst);
+  st = LRA_OK;
+  if (e) {
+    st = cuda_fail(ctx, e, "cynical: submatrix gather");
+  } else {
+    // the inner C-A iterations on the q x q submatrix, r x r generators
+    lra_source ss{};
+    ss.kind = LRA_DENSE_F32; ss.m = q; ss.n = q; ss.a = S; ss.lda = q;
+    std::vector<int32_t> J0(r), Ii(r), Ji(r);
+    for (int t = 0; t < r; ++t) J0[t] = t;
+    lra_params ip{};
+    ip.k = r; ip.l = r; ip.sweeps = p->inner_sweeps; ip.delta = p->delta; ip.rank_tol = p->rank_tol;
+    ip.init_J = J0.data();
+    lra_job job = 0;
+    if ((st = lra_cross_submit(ctx, &ss, &ip, &job)) == LRA_OK) {
+      lra_cur_out o{};
+      o.I = Ii.data(); o.J = Ji.data(); o.U = out->U;
+      if ((st = lra_cross_fetch_cur(ctx, job, &o)) == LRA_OK) {
+        for (int t = 0; t < r; ++t) {
+          out->I[t] = K[Ii[t]];
+          out->J[t] = L[Ji[t]];
+        }
+        if (out->K) std::memcpy(out->K, K.data(), sizeof(int32_t) * q);
+        if (out->L) std::memcpy(out->L, L.data(), sizeof(int32_t) * q);
+      }
+    }
+  }
+  cudaFreeAsync(buf, sst);
+  return st;
+}
+
 static lra_status validate_batch(const lra_source* src, const lra_block* blocks, int32_t nb,
                                  const lra_batch_params* p, std::string* why) {
   if (!src || !blocks || !p) { *why = "null argument"; return LRA_EINVAL; }

@@ -93,6 +93,13 @@ MUTANTS = [
     # seed draw: Floyd's replacement step dropped (repeats possible)
     ("draw_columns", "v = c if t in seen else t", "v = t",
      [lambda: pins.test_draw_columns_distinct_in_range(0, 10, 10)]),
+    # cynical: the submatrix's own row numbers returned instead of M's
+    ("cynical", "I = [K[i] for i in inner.I]", "I = list(inner.I)",
+     [lambda: pins.test_cynical_exact_on_rank_r("tests3"),
+      lambda: pins.test_cynical_generator_lies_in_the_submatrix_and_is_dominant()]),
+    # Tests 4: the inner step run on the initial columns instead of the outer loop's
+    ("ca_cynical", "cynical(src, outer.I, outer.J,", "cynical(src, outer.I, L0,",
+     [lambda: pins.test_tests4_outer_loop_is_one_ca_sweep_with_4r_generators()]),
     # C-A: horizontal step chooses J inside R instead of R^T
     ("cross_approximation", "maxvol(R.T, J,", "maxvol(R[:, :l], J,",
      [lambda: pins.test_exact_recovery_rank_l(90, 120, 7, 3),
