@@ -266,13 +266,32 @@ void draw_columns(uint64_t seed, long long n, int l, int32_t* out) {
   }
 }
 
+// count indices, each in [0, bound), no two equal.  Values up to 2^22 are
+// marked in a per-thread stamp array (one generation number per call, so
+// nothing is cleared between calls): O(count), which matters where a batch
+// checks thousands of small index sets on the submitting thread.
 bool distinct_in_range(const int32_t* v, long long count, long long bound) {
-  std::unordered_set<int32_t> seen;
-  for (long long i = 0; i < count; ++i) {
+  for (long long i = 0; i < count; ++i)
     if (v[i] < 0 || v[i] >= bound) return false;
-    if (!seen.insert(v[i]).second) return false;
+  long long vmax = -1;
+  for (long long i = 0; i < count; ++i) vmax = std::max<long long>(vmax, v[i]);
+  if (vmax < (1LL << 22)) {
+    thread_local std::vector<uint32_t> stamp;
+    thread_local uint32_t gen = 0;
+    if ((long long)stamp.size() <= vmax) stamp.resize((size_t)vmax + 1, 0u);
+    if (++gen == 0) {   // wrapped: start over
+      std::fill(stamp.begin(), stamp.end(), 0u);
+      gen = 1;
+    }
+    for (long long i = 0; i < count; ++i) {
+      if (stamp[v[i]] == gen) return false;
+      stamp[v[i]] = gen;
+    }
+    return true;
   }
-  return true;
+  std::vector<int32_t> s(v, v + count);
+  std::sort(s.begin(), s.end());
+  return std::adjacent_find(s.begin(), s.end()) == s.end();
 }
 
 // Device memory goes back to the pool on the control stream behind the job's
