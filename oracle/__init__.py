@@ -14,6 +14,7 @@ sample is the whole matrix; Table tb_ranrc error levels (Section 12.3).
 from .ca import (CAP, GEPP, STOP, SWAP, Cauchy, CrossResult, Dense, Gauss,
                  InvDist, OracleSingular, columns, cross_approximation,
                  cross_approximation_adaptive, draw_columns, splitmix64, cynical, ca_cynical,
+                 top_svd_of_cur, sampling_scores, exactly_sample, refine_by_leverage,
                  full_residual, gepp_rows, maxvol, nucleus, random_cross, rows,
                  sampled_residual)
 
@@ -21,6 +22,7 @@ __all__ = [
     "CAP", "GEPP", "STOP", "SWAP", "Cauchy", "CrossResult", "Dense", "Gauss",
     "InvDist", "OracleSingular", "columns", "cross_approximation",
     "cross_approximation_adaptive", "draw_columns", "splitmix64", "cynical", "ca_cynical",
+    "top_svd_of_cur", "sampling_scores", "exactly_sample", "refine_by_leverage",
     "full_residual", "gepp_rows", "maxvol", "nucleus", "random_cross", "rows",
     "sampled_residual",
 ]

@@ -502,6 +502,84 @@ def ca_cynical(src, L0, r, outer_loops=1, inner_sweeps=2, delta=1e-2, rank_tol=1
 
 
 # ---------------------------------------------------------------------------
+# Refinement of a C-A CUR by leverage-score sampling (Section 7.2 and Remark
+# resnrg: a crude LRA from C-A iterations, refined by the sampling of
+# Algorithm 7.1; Appendix C, Algorithm C.1; Appendix D, Algorithm D.1)
+# ---------------------------------------------------------------------------
+
+def top_svd_of_cur(C, U, R, r):
+    """Algorithm D.1 (Appendix D) for M ~ A W B with A = C, W = U, B = R:
+    QR factorizations C = Q_c R_c and R^T = Q_r R_r, the SVD of the small
+    core R_c U R_r^T = A S B^T, and the top-r triplets S = Q_c A_r,
+    T = Q_r B_r.  Returns (S, sigma_r, T) with S m x r, T n x r."""
+    C = np.asarray(C, np.float64)
+    R = np.asarray(R, np.float64)
+    Qc, Rc = np.linalg.qr(C)
+    Qr, Rr = np.linalg.qr(R.T)
+    A, sig, BT = np.linalg.svd(Rc @ np.asarray(U, np.float64) @ Rr.T)
+    return Qc @ A[:, :r], sig[:r], Qr @ BT[:r].T
+
+
+def sampling_scores(V):
+    """Appendix C, eq. (smpl): for the rows v_i of V, p_i = v_i^T v_i / ||V||_F^2.
+    With V the top-r singular vectors of a matrix (orthonormal columns) these
+    are its SVD-based leverage scores with beta = 1, ||v_i||^2 / r (eq. levsc1)."""
+    V = np.asarray(V, np.float64)
+    w = np.sum(V * V, axis=1)
+    return w / np.sum(w)
+
+
+def exactly_sample(p, l, u):
+    """Algorithm C.1 (Exactly(l) sampling and re-scaling) with its random
+    choices given: draw t picks i_t, the smallest i whose cumulative score
+    sum_{j <= i} p_j exceeds u_t (u_t uniform on [0, 1)), so that
+    Probability(i_t = i) = p_i; the re-scaling is d_t = 1 / sqrt(l p_{i_t}).
+    Returns (indices i_t, d_t)."""
+    p = np.asarray(p, np.float64)
+    cdf = np.cumsum(p)
+    idx = []
+    for t in range(l):
+        i = int(np.searchsorted(cdf, u[t], side="right"))
+        idx.append(min(i, len(p) - 1))
+    idx = np.asarray(idx)
+    return idx, 1.0 / np.sqrt(l * p[idx])
+
+
+@dataclass
+class RefineResult:
+    cols: np.ndarray       # l sampled columns (with repeats)
+    d: np.ndarray          # their re-scaling
+    rows: np.ndarray       # k sampled rows
+    dbar: np.ndarray       # their re-scaling
+    U: np.ndarray          # l x k nucleus: C' U R' ~ M with C' = M[:, cols], R' = M[rows, :]
+    p_cols: np.ndarray     # column scores (n)
+    p_rows: np.ndarray     # row scores (m)
+    sigma: np.ndarray      # top-r singular values of the C-A approximation
+
+
+def refine_by_leverage(src, I, J, U, r, l, k, u_cols, u_rows, rank_tol=1e-12):
+    """Section 7.2: take the C-A approximation M' = C U R (C = M[:, J],
+    R = M[I, :]), compute its top-r SVD S Sigma T^T superfast (Algorithm
+    D.1), the leverage scores with beta = 1 of its columns (rows of T) and
+    of its rows (rows of S), and run Algorithm 7.1 with them: Exactly(l)
+    columns and Exactly(k) rows (Algorithm C.1, random choices given as
+    u_cols, u_rows), C' = M S_cols, R' = S_rows^T M, and the nucleus
+    U' = D (Mk_r)^+ Dbar for Mk = Dbar M[rows, cols] D, truncated at rank r
+    (the Primitive Algorithm's rank-r truncation of the generator)."""
+    C = columns(src, J)
+    R = rows(src, I)
+    S, sig, T = top_svd_of_cur(C, U, R, r)
+    p_cols = sampling_scores(T)
+    p_rows = sampling_scores(S)
+    cols, d = exactly_sample(p_cols, l, u_cols)
+    rws, dbar = exactly_sample(p_rows, k, u_rows)
+    Mk = dbar[:, None] * src.block(rws, cols) * d[None, :]
+    Mp, _, _ = nucleus(Mk, r, rank_tol)
+    Unew = d[:, None] * Mp * dbar[None, :]
+    return RefineResult(cols=cols, d=d, rows=rws, dbar=dbar, U=Unew, p_cols=p_cols, p_rows=p_rows, sigma=sig)
+
+
+# ---------------------------------------------------------------------------
 # Initial column set from a seed (Section 12.2: the tests start from random
 # columns), for callers that pass a seed instead of the columns
 # ---------------------------------------------------------------------------

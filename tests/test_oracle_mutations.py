@@ -100,6 +100,19 @@ MUTANTS = [
     # Tests 4: the inner step run on the initial columns instead of the outer loop's
     ("ca_cynical", "cynical(src, outer.I, outer.J,", "cynical(src, outer.I, L0,",
      [lambda: pins.test_tests4_outer_loop_is_one_ca_sweep_with_4r_generators()]),
+    # refinement: inverse CDF taken with the wrong side at the interval ends
+    ("exactly_sample", 'side="right"', 'side="left"',
+     [lambda: pins.test_exactly_sample_maps_each_interval_to_its_index()]),
+    # refinement: column and row scores swapped
+    ("refine_by_leverage", "p_cols = sampling_scores(T)", "p_cols = sampling_scores(S[:len(T)])",
+     [lambda: pins.test_refinement_reproduces_an_exact_rank_r_matrix(),
+      lambda: pins.test_refinement_error_near_the_best_rank_r()]),
+    # Algorithm D.1: the core without the nucleus
+    ("top_svd_of_cur", "np.linalg.svd(Rc @ np.asarray(U, np.float64) @ Rr.T)", "np.linalg.svd(Rc @ Rr.T)",
+     [lambda: pins.test_top_svd_of_cur_is_the_svd_of_the_product()]),
+    # scores: norms instead of squared norms
+    ("sampling_scores", "w = np.sum(V * V, axis=1)", "w = np.sqrt(np.sum(V * V, axis=1))",
+     [lambda: pins.test_leverage_scores_of_an_exact_rank_r_matrix()]),
     # C-A: horizontal step chooses J inside R instead of R^T
     ("cross_approximation", "maxvol(R.T, J,", "maxvol(R[:, :l], J,",
      [lambda: pins.test_exact_recovery_rank_l(90, 120, 7, 3),

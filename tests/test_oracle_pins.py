@@ -568,3 +568,92 @@ def test_tb_ranrc_tests34_levels(n, r, paper_t3, paper_t4):
         e3.append(np.linalg.norm(A - A[:, c3.J] @ c3.U @ A[c3.I, :], 2) / nrm)
         e4.append(np.linalg.norm(A - A[:, c4.J] @ c4.U @ A[c4.I, :], 2) / nrm)
     assert np.mean(e3) <= paper_t3 and np.mean(e4) <= paper_t4
+
+
+# --- Refinement by leverage scores (Section 7.2, Algorithm 7.1, Appendix C, D)
+
+def _noisy_rank(seed, m, n, r, noise):
+    rng = W.rng_for(seed)
+    return rng.standard_normal((m, r)) @ rng.standard_normal((r, n)) + noise * rng.standard_normal((m, n))
+
+
+def test_top_svd_of_cur_is_the_svd_of_the_product():
+    """Algorithm D.1 gives the top-r SVD of C U R computed from the small core."""
+    A = _noisy_rank(1001, 120, 90, 5, 1e-3)
+    res = O.cross_approximation(O.Dense(A), W.draw_indices(1002, 90, 8), k=8, sweeps=2)
+    S, sig, T = O.top_svd_of_cur(res.C, res.U, res.R, 5)
+    P, s_full, QT = np.linalg.svd(res.C @ res.U @ res.R)
+    np.testing.assert_allclose(sig, s_full[:5], rtol=1e-10)
+    np.testing.assert_allclose(S @ S.T, P[:, :5] @ P[:, :5].T, atol=1e-10)
+    np.testing.assert_allclose(T @ T.T, QT[:5].T @ QT[:5], atol=1e-10)
+
+
+def test_leverage_scores_of_an_exact_rank_r_matrix():
+    """For M of rank r the C-A approximation is M itself, so its scores are
+    M's SVD leverage scores (beta = 1: ||t_j||^2 / r), sum to 1, and do not
+    change under a rotation of the singular basis."""
+    A = _noisy_rank(1003, 150, 130, 6, 0.0)
+    res = O.cross_approximation(O.Dense(A), W.draw_indices(1004, 130, 6), k=6, sweeps=2)
+    S, sig, T = O.top_svd_of_cur(res.C, res.U, res.R, 6)
+    P, s, QT = np.linalg.svd(A)
+    np.testing.assert_allclose(O.sampling_scores(T), np.sum(QT[:6].T ** 2, axis=1) / 6, atol=1e-12)
+    np.testing.assert_allclose(O.sampling_scores(S), np.sum(P[:, :6] ** 2, axis=1) / 6, atol=1e-12)
+    rot = np.linalg.qr(W.rng_for(1005).standard_normal((6, 6)))[0]
+    np.testing.assert_allclose(O.sampling_scores(T @ rot), O.sampling_scores(T), atol=1e-14)
+    assert abs(O.sampling_scores(T).sum() - 1.0) < 1e-14
+
+
+def test_exactly_sample_maps_each_interval_to_its_index():
+    """Algorithm C.1: draw t picks i with probability p_i; with the uniform
+    u_t given, i_t = i exactly for u_t in [P_{i-1}, P_i) (P the cumulative
+    sums), checked at both ends of every interval and by frequency."""
+    p = np.array([0.1, 0.0, 0.25, 0.4, 0.25])
+    cdf = np.cumsum(p)
+    lo = np.concatenate([[0.0], cdf[:-1]])
+    for i in range(5):
+        if p[i] == 0:
+            continue
+        for u in (lo[i], np.nextafter(cdf[i], 0.0)):
+            idx, d = O.exactly_sample(p, 1, [u])
+            assert idx[0] == i and d[0] == pytest.approx(1.0 / np.sqrt(p[i]))
+    u = W.rng_for(1006).random(50000)
+    idx, d = O.exactly_sample(p, len(u), u)
+    counts = np.bincount(idx, minlength=5)
+    assert counts[1] == 0
+    expect = p * len(u)
+    nz = p > 0
+    chi2 = np.sum((counts[nz] - expect[nz]) ** 2 / expect[nz])
+    assert chi2 < 16.3                    # 3 degrees of freedom, p = 0.001
+    np.testing.assert_allclose(d, 1.0 / np.sqrt(len(u) * p[idx]))
+
+
+def test_refinement_reproduces_an_exact_rank_r_matrix():
+    A = _noisy_rank(1007, 160, 140, 5, 0.0)
+    res = O.cross_approximation(O.Dense(A), W.draw_indices(1008, 140, 7), k=5, sweeps=2)
+    rng = W.rng_for(1009)
+    ref = O.refine_by_leverage(O.Dense(A), res.I, res.J, res.U, 5, 20, 20, rng.random(20), rng.random(20))
+    E = A - A[:, ref.cols] @ ref.U @ A[ref.rows, :]
+    assert np.linalg.norm(E) <= 1e-10 * np.linalg.norm(A)
+    # the scores it sampled from are M's own column and row leverage scores
+    P, s, QT = np.linalg.svd(A)
+    np.testing.assert_allclose(ref.p_cols, np.sum(QT[:5].T ** 2, axis=1) / 5, atol=1e-12)
+    np.testing.assert_allclose(ref.p_rows, np.sum(P[:, :5] ** 2, axis=1) / 5, atol=1e-12)
+
+
+def test_refinement_error_near_the_best_rank_r():
+    """Theorem thdmm (DMM08): with enough sampled rows and columns,
+    ||M - C'U'R'||_F <= (1 + eps) ||M - M_r||_F with probability >= 0.7.
+    At l = k = 8 r (below the theorem's sizes) most draws still land within
+    1.5x of the Eckart-Young optimum."""
+    A = _noisy_rank(1010, 200, 180, 4, 1e-4)
+    s = np.linalg.svd(A, compute_uv=False)
+    opt = np.sqrt(np.sum(s[4:] ** 2))
+    res = O.cross_approximation(O.Dense(A), W.draw_indices(1011, 180, 6), k=4, sweeps=3)
+    good = 0
+    for seed in range(20):
+        rng = W.rng_for(1100 + seed)
+        ref = O.refine_by_leverage(O.Dense(A), res.I, res.J, res.U, 4, 32, 32, rng.random(32), rng.random(32))
+        err = np.linalg.norm(A - A[:, ref.cols] @ ref.U @ A[ref.rows, :])
+        assert err >= opt * (1 - 1e-9)                    # Lemma 2.3: never below the optimum
+        good += err <= 1.5 * opt
+    assert good >= 14, good
