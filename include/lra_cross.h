@@ -302,6 +302,48 @@ typedef struct {
 lra_status lra_cross_cynical(lra_ctx* ctx, const lra_source* src, const lra_cynical_params* params,
                              const lra_cynical_out* out);
 
+/* ---- Refinement of a C-A CUR by leverage scores (Section 7.2; Remark
+ * resnrg: C-A iterations give a crude LRA M' = C U R, sampling refines it)
+ * From the index sets (I, J) of a C-A solve: C = M[:, J], R = M[I, :], the
+ * nucleus U = (X_r)^+ of X = M[I, J] at rank r = min(r, #{sigma_j >
+ * rank_tol sigma_1}); the leverage scores (beta = 1, eq. levsc1) of the
+ * columns and of the rows of M' (its top-r right and left singular
+ * subspaces, Algorithm D.1 of Appendix D); Algorithm 7.1 with Exactly(l)
+ * sampling and re-scaling (Algorithm C.1 of Appendix C, its uniforms given):
+ * l columns `cols` with scales d, l rows `rows` with scales dbar, and the
+ * nucleus U' = D (Mk_r)^+ Dbar of Mk = Dbar M[rows, cols] D, truncated at
+ * rank r.  The refined approximation is M[:, cols] U' M[rows, :]. */
+typedef struct {
+  int32_t r;                  /* rank of the approximation (1..l)                     */
+  int32_t l_new;              /* rows and columns sampled, 1..96 (a square generator) */
+  double rank_tol;            /* singular values kept: sigma_j > rank_tol sigma_1     */
+  const double* u_cols;       /* host, l_new uniforms in [0, 1): the column draws     */
+  const double* u_rows;       /* host, l_new uniforms in [0, 1): the row draws        */
+  int64_t resid_q, resid_s;   /* Appendix F sample of the refined CUR (0: none)       */
+  const int32_t* resid_rows;  /* host, resid_q distinct rows                          */
+  const int32_t* resid_cols;  /* host, resid_s distinct columns                       */
+} lra_refine_params;
+
+typedef struct {
+  int32_t* cols;              /* host, l_new sampled columns (repeats possible)       */
+  double* d;                  /* host, l_new column scales 1 / sqrt(l_new p_col)      */
+  int32_t* rows;              /* host, l_new sampled rows                             */
+  double* dbar;               /* host, l_new row scales                               */
+  double* U;                  /* host, l_new x l_new nucleus U', row-major            */
+  double* p_cols;             /* host, n column scores (nullable)                     */
+  double* p_rows;             /* host, m row scores (nullable)                        */
+  double* est_rel_err;        /* host, 1: Appendix F estimate of the refined CUR (nullable) */
+  int32_t* k_eff;             /* host, 1: the rank used (nullable)                    */
+} lra_refine_out;
+
+/* Blocking; runs on ctx's first stream with memory from ctx's pool (not
+ * counted against the admission budget).  I, J: host, l distinct rows and
+ * columns (l <= 96), e.g. from lra_cross_fetch_cur.  LRA_EINVAL for bad
+ * sizes or index sets; LRA_ESINGULAR when the cross has rank 0 or a score
+ * basis turns out rank-deficient. */
+lra_status lra_cross_refine(lra_ctx* ctx, const lra_source* src, const int32_t* I, const int32_t* J, int32_t l,
+                            const lra_refine_params* params, const lra_refine_out* out);
+
 /* Launch-shape tuner of the batched form (the paper has no counterpart:
  * the shape does not change any result).  Looks up, in the JSON file at
  * cache_path (NULL: no cache), the shape stored for this GPU (device name)

@@ -90,6 +90,18 @@ class lra_cynical_out(ctypes.Structure):
                 ("K", ctypes.c_void_p), ("L", ctypes.c_void_p)]
 
 
+class lra_refine_params(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_int32), ("l_new", ctypes.c_int32), ("rank_tol", ctypes.c_double),
+                ("u_cols", ctypes.c_void_p), ("u_rows", ctypes.c_void_p), ("resid_q", ctypes.c_int64),
+                ("resid_s", ctypes.c_int64), ("resid_rows", ctypes.c_void_p), ("resid_cols", ctypes.c_void_p)]
+
+
+class lra_refine_out(ctypes.Structure):
+    _fields_ = [("cols", ctypes.c_void_p), ("d", ctypes.c_void_p), ("rows", ctypes.c_void_p),
+                ("dbar", ctypes.c_void_p), ("U", ctypes.c_void_p), ("p_cols", ctypes.c_void_p),
+                ("p_rows", ctypes.c_void_p), ("est_rel_err", ctypes.c_void_p), ("k_eff", ctypes.c_void_p)]
+
+
 class lra_block(ctypes.Structure):
     _fields_ = [("row0", ctypes.c_int64), ("m", ctypes.c_int64),
                 ("col0", ctypes.c_int64), ("n", ctypes.c_int64)]
@@ -153,6 +165,8 @@ _tuning_lookup = _sig("lra_batch_tuning_lookup", ctypes.c_int, ctypes.c_char_p, 
                       ctypes.POINTER(lra_batch_params), ctypes.POINTER(lra_batch_params))
 _cynical = _sig("lra_cross_cynical", ctypes.c_int, _ctx_p, ctypes.POINTER(lra_source),
                 ctypes.POINTER(lra_cynical_params), ctypes.POINTER(lra_cynical_out))
+_refine = _sig("lra_cross_refine", ctypes.c_int, _ctx_p, ctypes.POINTER(lra_source), ctypes.c_void_p,
+               ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(lra_refine_params), ctypes.POINTER(lra_refine_out))
 _status_str = _sig("lra_status_str", ctypes.c_char_p, ctypes.c_int32)
 _last_error = _sig("lra_cross_last_error", ctypes.c_char_p, _ctx_p)
 
@@ -160,7 +174,7 @@ EXPORTED = ["lra_cross_create", "lra_cross_destroy", "lra_cross_submit", "lra_cr
             "lra_cross_wait", "lra_cross_fetch_cur", "lra_cross_cancel", "lra_cross_footprint",
             "lra_status_str", "lra_cross_last_error", "lra_cross_submit_batch",
             "lra_cross_fetch_batch", "lra_draw_columns", "lra_gather_entries", "lra_maxvol_noalloc",
-            "lra_cross_tune_batch", "lra_batch_tuning_lookup", "lra_cross_cynical"]
+            "lra_cross_tune_batch", "lra_batch_tuning_lookup", "lra_cross_cynical", "lra_cross_refine"]
 
 
 class LraError(RuntimeError):
@@ -256,6 +270,40 @@ def lra_maxvol_noalloc(strip_ptr, N, l, row_stride, col_stride, pos_ptr, xinv_pt
     returns the lra_status code."""
     return _maxvol_noalloc(strip_ptr, N, l, row_stride, col_stride, pos_ptr, xinv_ptr, delta, max_swaps,
                            status_ptr, stream)
+
+
+def lra_cross_refine(ctx, src: lra_source, I, J, r: int, l_new: int, u_cols, u_rows, rank_tol: float = 1e-6,
+                     resid_rows=None, resid_cols=None, scores: bool = False):
+    """Section 7.2 refinement of the C-A CUR of (I, J): returns a dict with
+    cols, d, rows, dbar, U (l_new x l_new), k_eff, est_rel_err and, with
+    scores, the column and row scores p_cols (n), p_rows (m)."""
+    import numpy as np
+    Ih = np.ascontiguousarray(I, dtype=np.int32)
+    Jh = np.ascontiguousarray(J, dtype=np.int32)
+    uc = np.ascontiguousarray(u_cols, dtype=np.float64)
+    ur = np.ascontiguousarray(u_rows, dtype=np.float64)
+    p = lra_refine_params(r, l_new, rank_tol, uc.ctypes.data, ur.ctypes.data, 0, 0, None, None)
+    keep = []
+    if resid_rows is not None:
+        rr = np.ascontiguousarray(resid_rows, dtype=np.int32)
+        rc = np.ascontiguousarray(resid_cols, dtype=np.int32)
+        keep += [rr, rc]
+        p.resid_q, p.resid_s, p.resid_rows, p.resid_cols = len(rr), len(rc), rr.ctypes.data, rc.ctypes.data
+    res = {"cols": np.zeros(l_new, np.int32), "d": np.zeros(l_new), "rows": np.zeros(l_new, np.int32),
+           "dbar": np.zeros(l_new), "U": np.zeros((l_new, l_new)), "est_rel_err": np.zeros(1),
+           "k_eff": np.zeros(1, np.int32)}
+    if scores:
+        res["p_cols"] = np.zeros(src.n)
+        res["p_rows"] = np.zeros(src.m)
+    o = lra_refine_out(res["cols"].ctypes.data, res["d"].ctypes.data, res["rows"].ctypes.data,
+                       res["dbar"].ctypes.data, res["U"].ctypes.data,
+                       res["p_cols"].ctypes.data if scores else None, res["p_rows"].ctypes.data if scores else None,
+                       res["est_rel_err"].ctypes.data, res["k_eff"].ctypes.data)
+    _check(_refine(ctx, ctypes.byref(src), Ih.ctypes.data, Jh.ctypes.data, len(Ih), ctypes.byref(p),
+                   ctypes.byref(o)), ctx)
+    res["est_rel_err"] = float(res["est_rel_err"][0])
+    res["k_eff"] = int(res["k_eff"][0])
+    return res
 
 
 def lra_cross_cynical(ctx, src: lra_source, r: int, L, K=None, outer_loops: int = 1, inner_sweeps: int = 2,

@@ -21,11 +21,17 @@ namespace lra {
 constexpr int kNucThreads = 512;
 
 // L > 0: a build for l == L exactly (the served cross sizes); L == 0: any l.
+// Optional (NucExtra, all nullable): row and column scales of the cross,
+// X[a][b] = rs[a] C[I[a]][b] cs[b] (then U is returned as
+// diag(cs) (X_k)^+ diag(rs), the nucleus of the unscaled factors), and the
+// kept singular vectors: Pk[q*l + r] = u_r[q] (left, over the rows of X),
+// Vk[p*l + r] = v_r[p] (right, over the columns of X), r < k_eff, zero
+// beyond.
 template <int L>
 __global__ void __launch_bounds__(kNucThreads, 1)
 nucleus_kernel(const float* __restrict__ C, const int* __restrict__ I, int l_arg, int k,
                double rank_tol, double* __restrict__ U, double* __restrict__ sigma_out,
-               JobStatus* js) {
+               JobStatus* js, NucExtra xa) {
   if (js->status != LRA_OK) return;
   const int l = L > 0 ? L : l_arg;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -42,10 +48,12 @@ nucleus_kernel(const float* __restrict__ C, const int* __restrict__ I, int l_arg
   if (tid == 0) *scale_e = 0;
   __syncthreads();
   // power-of-two scale so that max |X| is in [0.5, 1)
+  const bool scaled = xa.rs != nullptr;
   float amax = 0.0f;
   for (int e = tid; e < l * l; e += nthr) {
     const int a = e / l, b = e - a * l;
-    amax = fmaxf(amax, fabsf(C[(size_t)__ldg(I + a) * l + b]));
+    const float c = C[(size_t)__ldg(I + a) * l + b];
+    amax = fmaxf(amax, scaled ? (float)fabs((double)c * xa.rs[a] * xa.cs[b]) : fabsf(c));
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
@@ -58,7 +66,11 @@ nucleus_kernel(const float* __restrict__ C, const int* __restrict__ I, int l_arg
   const int ex = *scale_e ? *scale_e - 1024 : 0;
   for (int e = tid; e < l * l; e += nthr) {
     const int a = e / l, b = e - a * l;             // X[a][b] = C[I[a]][b]
-    W[(size_t)b * l + a] = dd_make(ldexpf(C[(size_t)__ldg(I + a) * l + b], -ex));
+    const float c = C[(size_t)__ldg(I + a) * l + b];
+    // scaled crosses: the entry times its row and column scale, as a pair
+    // (the FP32 entry is exact; the FP64 scale product rounds to 48 bits)
+    W[(size_t)b * l + a] = scaled ? dd_mul(dd_make(c), dd_from_double(ldexp(xa.rs[a] * xa.cs[b], -ex)))
+                                  : dd_make(ldexpf(c, -ex));
   }
   __syncthreads();
   svd_dd<kNucThreads, L>(W, Z, l, sc);
@@ -80,8 +92,29 @@ nucleus_kernel(const float* __restrict__ C, const int* __restrict__ I, int l_arg
   __syncthreads();
   const int ke = *keff_s;
   left_vectors<kNucThreads, L>(W, Z, l, ke, order, inv2, sc->perm);
-  nucleus_from_svd<kNucThreads, L>(W, Z, sc->perm, l, ke, order, inv2,
-                                [&](int e, double v) { U[e] = ldexp(v, -ex); });
+  if (xa.Vk) {
+    // right singular vector r = P W_{b_r} / sigma_{b_r}; left = column r of Z
+    for (int e = tid; e < l * l; e += nthr) {
+      const int c = e / l, r = e - c * l;   // entry c of vector r
+      double v = 0.0, u = 0.0;
+      if (r < ke) {
+        const int b = order[r];
+        v = dd_to_double(W[(size_t)b * l + c]) / sig[b];
+        u = dd_to_double(Z[(size_t)r * l + c]);
+      }
+      xa.Vk[(size_t)sc->perm[c] * l + r] = v;
+      xa.Pk[(size_t)c * l + r] = u;
+    }
+  }
+  if (scaled) {
+    nucleus_from_svd<kNucThreads, L>(W, Z, sc->perm, l, ke, order, inv2, [&](int e, double v) {
+      const int p = e / l, q = e - p * l;   // U[p][q]: p a column of X, q a row
+      U[e] = xa.cs[p] * ldexp(v, -ex) * xa.rs[q];
+    });
+  } else {
+    nucleus_from_svd<kNucThreads, L>(W, Z, sc->perm, l, ke, order, inv2,
+                                  [&](int e, double v) { U[e] = ldexp(v, -ex); });
+  }
 }
 
 // X^{-1} of the cross X[a][b] = S[pos[a]][b] of a strip, by one CTA of
@@ -146,23 +179,24 @@ cudaError_t launch_cross_inverse(const float* strip, long long si, long long st,
 
 template <int L>
 static cudaError_t launch_nucleus_l(const float* C, const int* I, int l, int k, double rank_tol,
-                                    double* U, double* sigma, JobStatus* js, cudaStream_t st) {
+                                    double* U, double* sigma, JobStatus* js, cudaStream_t st,
+                                    const NucExtra& xa) {
   const size_t smem = 2 * (size_t)l * l * sizeof(dd) + kMaxL * (sizeof(double) + sizeof(dd)) +
                       sizeof(SvdScratch) + (kMaxL + 2) * sizeof(int);
   const cudaError_t e = smem_optin(reinterpret_cast<const void*>(nucleus_kernel<L>), 227 * 1024);
   if (e != cudaSuccess) return e;
-  nucleus_kernel<L><<<1, kNucThreads, smem, st>>>(C, I, l, k, rank_tol, U, sigma, js);
+  nucleus_kernel<L><<<1, kNucThreads, smem, st>>>(C, I, l, k, rank_tol, U, sigma, js, xa);
   return cudaGetLastError();
 }
 
 cudaError_t launch_nucleus(const float* C, const int* I, int l, int k, double rank_tol,
-                           double* U, double* sigma, JobStatus* js, cudaStream_t st) {
+                           double* U, double* sigma, JobStatus* js, cudaStream_t st, const NucExtra& xa) {
   switch (l) {
-    case 12: return launch_nucleus_l<12>(C, I, l, k, rank_tol, U, sigma, js, st);
-    case 24: return launch_nucleus_l<24>(C, I, l, k, rank_tol, U, sigma, js, st);
-    case 48: return launch_nucleus_l<48>(C, I, l, k, rank_tol, U, sigma, js, st);
-    case 96: return launch_nucleus_l<96>(C, I, l, k, rank_tol, U, sigma, js, st);
-    default: return launch_nucleus_l<0>(C, I, l, k, rank_tol, U, sigma, js, st);
+    case 12: return launch_nucleus_l<12>(C, I, l, k, rank_tol, U, sigma, js, st, xa);
+    case 24: return launch_nucleus_l<24>(C, I, l, k, rank_tol, U, sigma, js, st, xa);
+    case 48: return launch_nucleus_l<48>(C, I, l, k, rank_tol, U, sigma, js, st, xa);
+    case 96: return launch_nucleus_l<96>(C, I, l, k, rank_tol, U, sigma, js, st, xa);
+    default: return launch_nucleus_l<0>(C, I, l, k, rank_tol, U, sigma, js, st, xa);
   }
 }
 

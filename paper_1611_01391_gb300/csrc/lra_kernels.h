@@ -82,9 +82,19 @@ cudaError_t launch_maxvol(MaxvolArgs a, const MaxvolPlan& plan, cudaStream_t st)
 cudaError_t launch_cross_inverse(const float* strip, long long si, long long st, const int* pos,
                                  int l, float2* xinv, JobStatus* js, cudaStream_t stream);
 
-// Nucleus of the final cross X = C[I, :] (one CTA, FP64 one-sided Jacobi SVD).
+// Nucleus of the final cross X = C[I, :] (one CTA, double-float QRCP +
+// one-sided Jacobi SVD).  NucExtra (all nullable): row / column scales of X
+// (with them U is diag(cs) (X_k)^+ diag(rs)), and outputs for the kept left
+// (Pk) and right (Vk) singular vectors as l x l row-major columns.
+struct NucExtra {
+  const double* rs = nullptr;
+  const double* cs = nullptr;
+  double* Pk = nullptr;
+  double* Vk = nullptr;
+};
 cudaError_t launch_nucleus(const float* C, const int* I, int l, int k, double rank_tol,
-                           double* U, double* sigma, JobStatus* js, cudaStream_t st);
+                           double* U, double* sigma, JobStatus* js, cudaStream_t st,
+                           const NucExtra& xa = NucExtra());
 
 // Appendix F sampled residual of C U R on rows x cols.
 cudaError_t launch_sampled_residual(const SourceDev& s, const int* rows, int q,
@@ -109,6 +119,19 @@ cudaError_t smem_optin(const void* func, int bytes);
 
 size_t batch_smem_bytes();
 cudaError_t launch_batch(const BatchArgs& a, int cluster_mask, int sms, cudaStream_t st);
+
+// Leverage scores of a C-A approximation and Exactly(l) sampling (k_lev.cu).
+int lev_partials(long long N);
+cudaError_t launch_lev_factors(const double* U, const double* Pk, const double* Vk, int l, int k, double* G1,
+                               double* G2t, const JobStatus* js, cudaStream_t st);
+cudaError_t launch_lev_project(const float* S, long long N, int l, long long si, long long st_, const double* G,
+                               int k, double* Y, double* partials, int nparts, const JobStatus* js,
+                               cudaStream_t st);
+cudaError_t launch_lev_chol(const double* partials, int nparts, int k, double* Linv, JobStatus* js,
+                            cudaStream_t st);
+cudaError_t launch_lev_scores_sample(const double* Y, long long N, int k, const double* Linv, double* w,
+                                     const double* u, int ls, int* idx, double* d, double* scores,
+                                     const JobStatus* js, cudaStream_t st);
 
 // Small control kernels.
 cudaError_t launch_tol_check(JobStatus* js, double tol, cudaStream_t st);

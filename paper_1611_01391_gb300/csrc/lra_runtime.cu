@@ -926,6 +926,158 @@ lra_status lra_cross_cynical(lra_ctx* ctx, const lra_source* src, const lra_cyni
   return st;
 }
 
+// Section 7.2: refinement of the C-A CUR of (I, J) by leverage-score
+// sampling (k_lev.cu: scores and Exactly(l) sampling; the strips, the
+// nuclei and the Appendix F estimate through the solve's own kernels).
+lra_status lra_cross_refine(lra_ctx* ctx, const lra_source* src, const int32_t* I, const int32_t* J, int32_t l,
+                            const lra_refine_params* p, const lra_refine_out* out) {
+  if (!ctx || !src || !I || !J || !p || !out || !out->cols || !out->d || !out->rows || !out->dbar || !out->U)
+    return LRA_EINVAL;
+  std::string why;
+  if (validate_source(src, &why) != LRA_OK) return fail(ctx, LRA_EINVAL, why);
+  const long long m = src->m, n = src->n;
+  const int L2 = p->l_new;
+  if (l < 1 || l > kMaxL || l > m || l > n || p->r < 1 || p->r > l || L2 < 1 || L2 > kMaxL || L2 > m || L2 > n ||
+      !p->u_cols || !p->u_rows || !(p->rank_tol >= 0.0) || p->resid_q < 0 || p->resid_s < 0 ||
+      (p->resid_q > 0) != (p->resid_s > 0) ||
+      (p->resid_q > 0 && (!p->resid_rows || !p->resid_cols || p->resid_q > m || p->resid_s > n)))
+    return fail(ctx, LRA_EINVAL, "refine: bad sizes");
+  if (!distinct_in_range(I, l, m) || !distinct_in_range(J, l, n))
+    return fail(ctx, LRA_EINVAL, "refine: I and J must hold l distinct indices of M");
+  for (int t = 0; t < L2; ++t)
+    if (!(p->u_cols[t] >= 0.0 && p->u_cols[t] < 1.0) || !(p->u_rows[t] >= 0.0 && p->u_rows[t] < 1.0))
+      return fail(ctx, LRA_EINVAL, "refine: uniforms must lie in [0, 1)");
+  if (p->resid_q > 0 && (!distinct_in_range(p->resid_rows, p->resid_q, m) ||
+                         !distinct_in_range(p->resid_cols, p->resid_s, n)))
+    return fail(ctx, LRA_EINVAL, "refine: residual sample indices must be distinct and in range");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e) return cuda_fail(ctx, e, "cudaSetDevice");
+  const int r = p->r, q = (int)p->resid_q, sN = (int)p->resid_s;
+  const int npm = lev_partials(m), npn = lev_partials(n);
+  const int nres = q > 0 ? sampled_residual_partials(q, sN) : 1;
+  Layout lay;
+  const size_t o_js = lay.take(sizeof(JobStatus));
+  const size_t o_I = lay.take(sizeof(int) * l), o_J = lay.take(sizeof(int) * l);
+  const size_t o_u = lay.take(sizeof(double) * 2 * L2);
+  const size_t o_sr = lay.take(sizeof(int) * std::max(q, 1)), o_sc = lay.take(sizeof(int) * std::max(sN, 1));
+  const size_t prefix = lay.off;
+  const size_t o_C = lay.take(sizeof(float) * (size_t)m * l), o_R = lay.take(sizeof(float) * (size_t)n * l);
+  const size_t o_U = lay.take(sizeof(double) * l * l), o_sg = lay.take(sizeof(double) * l);
+  const size_t o_P = lay.take(sizeof(double) * l * l), o_V = lay.take(sizeof(double) * l * l);
+  const size_t o_G1 = lay.take(sizeof(double) * l * r), o_G2 = lay.take(sizeof(double) * l * r);
+  const size_t o_Yc = lay.take(sizeof(double) * (size_t)m * r), o_Yr = lay.take(sizeof(double) * (size_t)n * r);
+  const size_t o_pm = lay.take(sizeof(double) * (size_t)npm * r * r);
+  const size_t o_pn = lay.take(sizeof(double) * (size_t)npn * r * r);
+  const size_t o_Lc = lay.take(sizeof(double) * r * r), o_Lr = lay.take(sizeof(double) * r * r);
+  const size_t o_wm = lay.take(sizeof(double) * m), o_wn = lay.take(sizeof(double) * n);
+  const size_t o_sm = lay.take(sizeof(double) * m), o_sn = lay.take(sizeof(double) * n);
+  const size_t o_ic = lay.take(sizeof(int) * L2), o_ir = lay.take(sizeof(int) * L2);
+  const size_t o_d = lay.take(sizeof(double) * L2), o_db = lay.take(sizeof(double) * L2);
+  const size_t o_C2 = lay.take(sizeof(float) * (size_t)m * L2), o_R2 = lay.take(sizeof(float) * (size_t)n * L2);
+  const size_t o_U2 = lay.take(sizeof(double) * L2 * L2), o_sg2 = lay.take(sizeof(double) * L2);
+  const size_t o_cuq = lay.take(sizeof(float) * std::max<size_t>(2 * (size_t)q * L2, 1));
+  const size_t o_pr = lay.take(sizeof(double) * 3 * nres);
+  const size_t bytes = lay.off;
+  cudaStream_t st = ctx->stream;
+  unsigned char* b = nullptr;
+  if ((e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&b), bytes, ctx->pool, st)))
+    return cuda_fail(ctx, e, "cudaMallocFromPoolAsync");
+  auto P = [&](size_t o) { return b + o; };
+  JobStatus* js = reinterpret_cast<JobStatus*>(P(o_js));
+  int *dI = reinterpret_cast<int*>(P(o_I)), *dJ = reinterpret_cast<int*>(P(o_J));
+  double* du = reinterpret_cast<double*>(P(o_u));
+  int *dsr = reinterpret_cast<int*>(P(o_sr)), *dsc = reinterpret_cast<int*>(P(o_sc));
+  float *C = reinterpret_cast<float*>(P(o_C)), *R = reinterpret_cast<float*>(P(o_R));
+  double *U = reinterpret_cast<double*>(P(o_U)), *sg = reinterpret_cast<double*>(P(o_sg));
+  double *Pk = reinterpret_cast<double*>(P(o_P)), *Vk = reinterpret_cast<double*>(P(o_V));
+  double *G1 = reinterpret_cast<double*>(P(o_G1)), *G2 = reinterpret_cast<double*>(P(o_G2));
+  double *Yc = reinterpret_cast<double*>(P(o_Yc)), *Yr = reinterpret_cast<double*>(P(o_Yr));
+  double *pm = reinterpret_cast<double*>(P(o_pm)), *pn = reinterpret_cast<double*>(P(o_pn));
+  double *Lc = reinterpret_cast<double*>(P(o_Lc)), *Lr = reinterpret_cast<double*>(P(o_Lr));
+  double *wm = reinterpret_cast<double*>(P(o_wm)), *wn = reinterpret_cast<double*>(P(o_wn));
+  double *scm = reinterpret_cast<double*>(P(o_sm)), *scn = reinterpret_cast<double*>(P(o_sn));
+  int *ic = reinterpret_cast<int*>(P(o_ic)), *ir = reinterpret_cast<int*>(P(o_ir));
+  double *dd_ = reinterpret_cast<double*>(P(o_d)), *db = reinterpret_cast<double*>(P(o_db));
+  float *C2 = reinterpret_cast<float*>(P(o_C2)), *R2 = reinterpret_cast<float*>(P(o_R2));
+  double *U2 = reinterpret_cast<double*>(P(o_U2)), *sg2 = reinterpret_cast<double*>(P(o_sg2));
+  float* cuq = reinterpret_cast<float*>(P(o_cuq));
+  double* rpart = reinterpret_cast<double*>(P(o_pr));
+  // the inputs, staged in host memory and sent in one copy
+  std::vector<unsigned char> hs(prefix, 0);
+  JobStatus init{};
+  init.status = LRA_OK;
+  std::memcpy(hs.data() + o_js, &init, sizeof(init));
+  std::memcpy(hs.data() + o_I, I, sizeof(int) * l);
+  std::memcpy(hs.data() + o_J, J, sizeof(int) * l);
+  std::memcpy(hs.data() + o_u, p->u_cols, sizeof(double) * L2);
+  std::memcpy(hs.data() + o_u + sizeof(double) * L2, p->u_rows, sizeof(double) * L2);
+  if (q > 0) {
+    std::memcpy(hs.data() + o_sr, p->resid_rows, sizeof(int) * q);
+    std::memcpy(hs.data() + o_sc, p->resid_cols, sizeof(int) * sN);
+  }
+  const SourceDev sd = make_src(src);
+  TmaMap cmap{};
+  const bool tma = src->kind == LRA_DENSE_F32 &&
+                   make_cols_map(&cmap, static_cast<const float*>(src->a), m, n, src->lda);
+  auto gather_c = [&](const int* Jd, int ll, float* out_C) {
+    return tma ? launch_gather_cols_tma(cmap, Jd, ll, m, out_C, js, 0, ctx->sms, st)
+               : launch_gather_cols(sd, Jd, ll, out_C, js, 0, ctx->sms, st);
+  };
+  NucExtra vec;
+  vec.Pk = Pk;
+  vec.Vk = Vk;
+  NucExtra scl;
+  scl.rs = db;
+  scl.cs = dd_;
+  JobStatus hjs{};
+  // phase 1: C = M[:, J], R = M[I, :], U = (X_r)^+ with the kept singular
+  // vectors; the rank actually kept decides the dimension of the scores
+  if (!(e = cudaMemcpyAsync(b, hs.data(), prefix, cudaMemcpyHostToDevice, st)) &&
+      !(e = gather_c(dJ, l, C)) && !(e = launch_gather_rows(sd, dI, l, R, js, ctx->sms, st)) &&
+      !(e = launch_nucleus(C, dI, l, r, p->rank_tol, U, sg, js, st, vec)) &&
+      !(e = cudaMemcpyAsync(&hjs, js, sizeof(JobStatus), cudaMemcpyDeviceToHost, st)))
+    e = cudaStreamSynchronize(st);
+  const int rr = std::min(r, hjs.k_eff);
+  if (!e && (hjs.status != LRA_OK || rr < 1)) {
+    cudaFreeAsync(b, st);
+    if (hjs.status != LRA_OK) return fail(ctx, (lra_status)hjs.status, "refine: device status");
+    return fail(ctx, LRA_ESINGULAR, "refine: the cross has rank 0");
+  }
+  // phase 2: H = C (U P_rr) and Z^T = R^T (U^T V_rr), their Gram matrices
+  // and scores, the sampling, the refined strips and nucleus
+  if (!e &&
+      !(e = launch_lev_factors(U, Pk, Vk, l, rr, G1, G2, js, st)) &&
+      !(e = launch_lev_project(C, m, l, l, 1, G1, rr, Yc, pm, npm, js, st)) &&
+      !(e = launch_lev_project(R, n, l, 1, n, G2, rr, Yr, pn, npn, js, st)) &&
+      !(e = launch_lev_chol(pm, npm, rr, Lc, js, st)) && !(e = launch_lev_chol(pn, npn, rr, Lr, js, st)) &&
+      // Exactly(l_new) columns from the right scores, rows from the left ones
+      !(e = launch_lev_scores_sample(Yr, n, rr, Lr, wn, du, L2, ic, dd_, scn, js, st)) &&
+      !(e = launch_lev_scores_sample(Yc, m, rr, Lc, wm, du + L2, L2, ir, db, scm, js, st)) &&
+      // C' = M[:, cols], R' = M[rows, :], U' = D (Dbar C'[rows, :] D)_rr^+ Dbar
+      !(e = gather_c(ic, L2, C2)) && !(e = launch_gather_rows(sd, ir, L2, R2, js, ctx->sms, st)) &&
+      !(e = launch_nucleus(C2, ir, L2, rr, p->rank_tol, U2, sg2, js, st, scl)) &&
+      !(e = q > 0 ? launch_sampled_residual(sd, dsr, q, dsc, sN, L2, C2, U2, R2, cuq, rpart, nres, js, st)
+                  : cudaSuccess) &&
+      !(e = cudaMemcpyAsync(&hjs, js, sizeof(JobStatus), cudaMemcpyDeviceToHost, st)) &&
+      !(e = cudaMemcpyAsync(out->cols, ic, sizeof(int) * L2, cudaMemcpyDeviceToHost, st)) &&
+      !(e = cudaMemcpyAsync(out->d, dd_, sizeof(double) * L2, cudaMemcpyDeviceToHost, st)) &&
+      !(e = cudaMemcpyAsync(out->rows, ir, sizeof(int) * L2, cudaMemcpyDeviceToHost, st)) &&
+      !(e = cudaMemcpyAsync(out->dbar, db, sizeof(double) * L2, cudaMemcpyDeviceToHost, st)) &&
+      !(e = cudaMemcpyAsync(out->U, U2, sizeof(double) * L2 * L2, cudaMemcpyDeviceToHost, st)) &&
+      !(e = out->p_cols ? cudaMemcpyAsync(out->p_cols, scn, sizeof(double) * n, cudaMemcpyDeviceToHost, st)
+                        : cudaSuccess) &&
+      !(e = out->p_rows ? cudaMemcpyAsync(out->p_rows, scm, sizeof(double) * m, cudaMemcpyDeviceToHost, st)
+                        : cudaSuccess))
+    e = cudaStreamSynchronize(st);
+  cudaFreeAsync(b, st);
+  if (e) return cuda_fail(ctx, e, "refine");
+  if (hjs.status != LRA_OK) return fail(ctx, (lra_status)hjs.status, "refine: device status");
+  if (hjs.k_eff < 1) return fail(ctx, LRA_ESINGULAR, "refine: the cross has rank 0");
+  if (out->est_rel_err) *out->est_rel_err = q > 0 ? hjs.est_rel : -1.0;
+  if (out->k_eff) *out->k_eff = rr;
+  return LRA_OK;
+}
+
 static lra_status validate_batch(const lra_source* src, const lra_block* blocks, int32_t nb,
                                  const lra_batch_params* p, std::string* why) {
   if (!src || !blocks || !p) { *why = "null argument"; return LRA_EINVAL; }
