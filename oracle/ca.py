@@ -580,6 +580,105 @@ def refine_by_leverage(src, I, J, U, r, l, k, u_cols, u_rows, rank_tol=1e-12):
 
 
 # ---------------------------------------------------------------------------
+# Pre-processing with abridged Hadamard multipliers (Section 8.1, family (i);
+# recovery of an LRA with nonsingular multipliers, Section 6.6)
+# ---------------------------------------------------------------------------
+
+def abridged_hadamard(n, d):
+    """The d-abridged Hadamard matrix H_{n,d}: the recursion
+    H_{2s} = [[H_s, H_s], [H_s, -H_s]] run d times from H_{s0} = I_{s0},
+    n = 2^d s0 (Section 8.1).  Dense, for small n."""
+    if n % (1 << d):
+        raise ValueError("2^d must divide n")
+    H = np.eye(n >> d)
+    for _ in range(d):
+        H = np.block([[H, H], [H, -H]])
+    return H
+
+
+def aph_left(m, d, perm, sign):
+    """Left multiplier F = D P H_{m,d} (rows permuted, then scaled by +-1):
+    row i of F is sign[i] times row perm[i] of H_{m,d}."""
+    return np.asarray(sign, np.float64)[:, None] * abridged_hadamard(m, d)[np.asarray(perm)]
+
+
+def aph_right(n, d, perm, sign):
+    """Right multiplier H = H_{n,d} P D: column j of H is sign[j] times
+    column perm[j] of H_{n,d}."""
+    return abridged_hadamard(n, d)[:, np.asarray(perm)] * np.asarray(sign, np.float64)[None, :]
+
+
+def _ah_terms(x, s0, d):
+    """For row (or column) x = b s0 + o of H_{n,d}: the 2^d nonzero
+    positions p s0 + o, p = 0 .. 2^d - 1, and their signs (-1)^popcount(b & p)."""
+    b, o = divmod(int(x), s0)
+    ps = np.arange(1 << d)
+    sgn = np.array([-1.0 if bin(b & p).count("1") & 1 else 1.0 for p in ps])
+    return ps * s0 + o, sgn
+
+
+class Preprocessed:
+    """The source M_bar = F M H for the multipliers of aph_left / aph_right,
+    evaluated entry by entry from the 4^d entries of M each one combines:
+    M_bar[i, j] = sF[i] sH[j] sum_p sum_q (+-1) M[p s_m + o_i, q s_n + o_j],
+    summed in FP64 with p outer and q inner; precision "fp32" rounds the
+    sum to FP32 (the entries a FP32 gather sees)."""
+
+    def __init__(self, src, d, perm_rows, sign_rows, perm_cols, sign_cols, precision="fp64"):
+        self.src, self.d = src, int(d)
+        self.m, self.n = src.m, src.n
+        self.sm, self.sn = self.m >> d, self.n >> d
+        if (self.sm << d) != self.m or (self.sn << d) != self.n:
+            raise ValueError("2^d must divide m and n")
+        self.pr, self.sr = np.asarray(perm_rows), np.asarray(sign_rows, np.float64)
+        self.pc, self.sc = np.asarray(perm_cols), np.asarray(sign_cols, np.float64)
+        self.precision = precision
+
+    def block(self, rows, cols):
+        rows, cols = np.asarray(rows), np.asarray(cols)
+        out = np.zeros((len(rows), len(cols)))
+        for a, i in enumerate(rows):
+            ri, rs = _ah_terms(self.pr[i], self.sm, self.d)
+            tc = [_ah_terms(self.pc[j], self.sn, self.d) for j in cols]
+            ci = np.stack([t[0] for t in tc], axis=1)          # 2^d x len(cols)
+            cs = np.stack([t[1] for t in tc], axis=1)
+            acc = np.zeros(len(cols))
+            for p in range(1 << self.d):
+                row = self.src.block([ri[p]], ci.ravel()).reshape(ci.shape)   # 2^d x len(cols)
+                for q in range(1 << self.d):
+                    acc = acc + rs[p] * cs[q] * row[q]
+            out[a] = self.sr[i] * self.sc[cols] * acc
+        if self.precision == "fp32":
+            out = out.astype(np.float32).astype(np.float64)
+        return out
+
+
+def recover_lra(pre, Cbar, Rbar):
+    """Section 6.6: from an LRA Cbar Ubar Rbar of M_bar = F M H with
+    F F^T = 2^d I and H^T H = 2^d I, the induced LRA of M is
+    (F^T Cbar / 2^d) Ubar (Rbar H^T / 2^d).  Returns (A, B), A = F^T Cbar / 2^d
+    (m x l) and B = Rbar H^T / 2^d (l x n), from the multipliers' sparse form."""
+    Cbar = np.asarray(Cbar, np.float64)
+    Rbar = np.asarray(Rbar, np.float64)
+    m, n, d = pre.m, pre.n, pre.d
+    inv_r = np.empty(m, int)
+    inv_r[pre.pr] = np.arange(m)
+    inv_c = np.empty(n, int)
+    inv_c[pre.pc] = np.arange(n)
+    A = np.zeros((m, Cbar.shape[1]))
+    for a in range(m):
+        pos, sgn = _ah_terms(a, pre.sm, d)          # H_{m,d} is symmetric
+        i = inv_r[pos]
+        A[a] = (sgn * pre.sr[i]) @ Cbar[i] / (1 << d)
+    B = np.zeros((Rbar.shape[0], n))
+    for b in range(n):
+        pos, sgn = _ah_terms(b, pre.sn, d)
+        j = inv_c[pos]
+        B[:, b] = Rbar[:, j] @ (sgn * pre.sc[j]) / (1 << d)
+    return A, B
+
+
+# ---------------------------------------------------------------------------
 # Initial column set from a seed (Section 12.2: the tests start from random
 # columns), for callers that pass a seed instead of the columns
 # ---------------------------------------------------------------------------

@@ -113,6 +113,15 @@ MUTANTS = [
     # scores: norms instead of squared norms
     ("sampling_scores", "w = np.sum(V * V, axis=1)", "w = np.sqrt(np.sum(V * V, axis=1))",
      [lambda: pins.test_leverage_scores_of_an_exact_rank_r_matrix()]),
+    # abridged Hadamard: the recursion's lower-right block without the minus
+    ("abridged_hadamard", "H = np.block([[H, H], [H, -H]])", "H = np.block([[H, H], [H, H]])",
+     [lambda: pins.test_abridged_hadamard_equals_the_printed_matrices()]),
+    # recovery: H^T applied with the permutation instead of its inverse
+    ("recover_lra", "j = inv_c[pos]", "j = pre.pc[pos]",
+     [lambda: pins.test_recovered_lra_error_is_the_preprocessed_error_over_2_to_d()]),
+    # recovery: the 2^d normalisation dropped on one side
+    ("recover_lra", "A[a] = (sgn * pre.sr[i]) @ Cbar[i] / (1 << d)", "A[a] = (sgn * pre.sr[i]) @ Cbar[i]",
+     [lambda: pins.test_recovered_lra_error_is_the_preprocessed_error_over_2_to_d()]),
     # C-A: horizontal step chooses J inside R instead of R^T
     ("cross_approximation", "maxvol(R.T, J,", "maxvol(R[:, :l], J,",
      [lambda: pins.test_exact_recovery_rank_l(90, 120, 7, 3),

@@ -657,3 +657,85 @@ def test_refinement_error_near_the_best_rank_r():
         assert err >= opt * (1 - 1e-9)                    # Lemma 2.3: never below the optimum
         good += err <= 1.5 * opt
     assert good >= 14, good
+
+
+# --- Pre-processing with abridged Hadamard multipliers (Section 8.1 family (i),
+# --- recovery with nonsingular multipliers, Section 6.6)
+
+def _printed_hadamard():
+    mats, cur = {}, None
+    for line in open(os.path.join(GOLDEN, "abridged_hadamard.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line[0] in "+-":
+            mats[cur].append([1.0 if c == "+" else -1.0 for c in line.split()])
+        else:
+            cur = line
+            mats[cur] = []
+    return {k: np.array(v) for k, v in mats.items()}
+
+
+def test_abridged_hadamard_equals_the_printed_matrices():
+    P = _printed_hadamard()
+    np.testing.assert_array_equal(O.abridged_hadamard(4, 2), P["H4"])
+    np.testing.assert_array_equal(O.abridged_hadamard(8, 3), P["H8"])
+    s = 3
+    for d, key in ((1, "Hn1"), (2, "Hn2"), (3, "Hn3")):
+        np.testing.assert_array_equal(O.abridged_hadamard((1 << d) * s, d), np.kron(P[key], np.eye(s)))
+
+
+def test_aph_multipliers_orthogonal_up_to_scale():
+    rng = W.rng_for(1300)
+    for m, d in ((48, 1), (64, 3), (40, 2)):
+        F = O.aph_left(m, d, rng.permutation(m), rng.choice([-1.0, 1.0], m))
+        H = O.aph_right(m, d, rng.permutation(m), rng.choice([-1.0, 1.0], m))
+        np.testing.assert_array_equal(F @ F.T, (1 << d) * np.eye(m))
+        np.testing.assert_array_equal(H.T @ H, (1 << d) * np.eye(m))
+        assert np.all(np.count_nonzero(F, axis=1) == 1 << d)
+
+
+def _pre_case(seed, m, n, d, A):
+    rng = W.rng_for(seed)
+    pr, sr = rng.permutation(m), rng.choice([-1.0, 1.0], m)
+    pc, sc = rng.permutation(n), rng.choice([-1.0, 1.0], n)
+    return O.Preprocessed(O.Dense(A), d, pr, sr, pc, sc), O.aph_left(m, d, pr, sr), O.aph_right(n, d, pc, sc)
+
+
+def test_preprocessed_entries_are_the_product_F_M_H():
+    A = W.rng_for(1301).standard_normal((64, 40))
+    pre, F, H = _pre_case(1302, 64, 40, 3, A)
+    rows, cols = np.array([0, 5, 63, 17]), np.array([39, 0, 8, 21, 2])
+    np.testing.assert_allclose(pre.block(rows, cols), (F @ A @ H)[np.ix_(rows, cols)], rtol=0, atol=1e-12)
+
+
+def test_recovered_lra_error_is_the_preprocessed_error_over_2_to_d():
+    """Section 6.6: with F F^T = 2^d I and H^T H = 2^d I the recovered LRA of
+    M has error ||F^{-1} E H^{-1}||_F = ||E||_F / 2^d for the error E of the
+    LRA of M_bar; exact recovery when C-A is exact on M_bar."""
+    A = _rank_l(1303, 96, 80, 5)
+    pre, F, H = _pre_case(1304, 96, 80, 2, A)
+    res = O.cross_approximation(pre, W.draw_indices(1305, 80, 5), k=5, sweeps=2)
+    Ar, Br = O.recover_lra(pre, res.C, res.R)
+    assert np.linalg.norm(A - Ar @ res.U @ Br) <= 1e-12 * np.linalg.norm(A)
+    An = A + 1e-3 * W.rng_for(1306).standard_normal(A.shape)
+    pre, F, H = _pre_case(1307, 96, 80, 2, An)
+    res = O.cross_approximation(pre, W.draw_indices(1308, 80, 7), k=5, sweeps=2)
+    Ar, Br = O.recover_lra(pre, res.C, res.R)
+    Ebar = F @ An @ H - res.C @ res.U @ res.R
+    assert np.linalg.norm(An - Ar @ res.U @ Br) == pytest.approx(np.linalg.norm(Ebar) / 4, rel=1e-10)
+
+
+def test_full_hadamard_preprocessing_finds_the_delta_matrix():
+    """Appendix E's hard input: C-A misses a single nonzero entry unless its
+    first columns touch it (the pin above); after full Hadamard
+    pre-processing (d = log2 n) every column of M_bar is nonzero and the
+    recovered LRA is exact for any initial columns."""
+    n = 64
+    A = np.zeros((n, n))
+    A[37, 11] = 1.0
+    for seed in range(6):
+        pre, F, H = _pre_case(1310 + seed, n, n, 6, A)
+        res = O.cross_approximation(pre, W.draw_indices(1320 + seed, n, 1), k=1, sweeps=1)
+        Ar, Br = O.recover_lra(pre, res.C, res.R)
+        assert np.linalg.norm(A - Ar @ res.U @ Br) <= 1e-12
