@@ -15,7 +15,7 @@ from .ca import (CAP, GEPP, STOP, SWAP, Cauchy, CrossResult, Dense, Gauss,
                  InvDist, OracleSingular, columns, cross_approximation,
                  cross_approximation_adaptive, draw_columns, splitmix64, cynical, ca_cynical,
                  top_svd_of_cur, sampling_scores, exactly_sample, refine_by_leverage,
-                 abridged_hadamard, aph_left, aph_right, Preprocessed, recover_lra,
+                 abridged_hadamard, butterfly, aph_left, aph_right, Preprocessed, recover_lra,
                  full_residual, gepp_rows, maxvol, nucleus, random_cross, rows,
                  sampled_residual)
 
@@ -24,7 +24,7 @@ __all__ = [
     "InvDist", "OracleSingular", "columns", "cross_approximation",
     "cross_approximation_adaptive", "draw_columns", "splitmix64", "cynical", "ca_cynical",
     "top_svd_of_cur", "sampling_scores", "exactly_sample", "refine_by_leverage",
-    "abridged_hadamard", "aph_left", "aph_right", "Preprocessed", "recover_lra",
+    "abridged_hadamard", "butterfly", "aph_left", "aph_right", "Preprocessed", "recover_lra",
     "full_residual", "gepp_rows", "maxvol", "nucleus", "random_cross", "rows",
     "sampled_residual",
 ]

@@ -608,21 +608,29 @@ def aph_right(n, d, perm, sign):
     return abridged_hadamard(n, d)[:, np.asarray(perm)] * np.asarray(sign, np.float64)[None, :]
 
 
-def _ah_terms(x, s0, d):
-    """For row (or column) x = b s0 + o of H_{n,d}: the 2^d nonzero
-    positions p s0 + o, p = 0 .. 2^d - 1, and their signs (-1)^popcount(b & p)."""
-    b, o = divmod(int(x), s0)
-    ps = np.arange(1 << d)
-    sgn = np.array([-1.0 if bin(b & p).count("1") & 1 else 1.0 for p in ps])
-    return ps * s0 + o, sgn
+def butterfly(vals, b, d):
+    """Entry b of H_{2^d} applied along axis 0 of vals (indexed by the block
+    p of the H_{n,d} recursion), summed in the order of the d recursive
+    steps H_{2s} = [[H_s, H_s], [H_s, -H_s]] (Section 8.1; the order of
+    the fast multiplication with at most 2dn additions): the innermost
+    step combines the entries p that differ in bit 0, the next those that
+    differ in bit 1, and so on; a step whose bit of b is 1 subtracts the
+    second half.  b may be an array broadcast over the trailing axes."""
+    vals = np.asarray(vals, np.float64)
+    for k in range(d):
+        sig = np.where((np.asarray(b) >> k) & 1, -1.0, 1.0)
+        vals = vals[0::2] + sig * vals[1::2]
+    return vals[0]
 
 
 class Preprocessed:
     """The source M_bar = F M H for the multipliers of aph_left / aph_right,
     evaluated entry by entry from the 4^d entries of M each one combines:
-    M_bar[i, j] = sF[i] sH[j] sum_p sum_q (+-1) M[p s_m + o_i, q s_n + o_j],
-    summed in FP64 with p outer and q inner; precision "fp32" rounds the
-    sum to FP32 (the entries a FP32 gather sees)."""
+    with x = pr[i] = b_i s_m + o_i and y = pc[j] = b_j s_n + o_j,
+    M_bar[i, j] = sF[i] sH[j] sum_q (+-1) sum_p (+-1) M[p s_m + o_i, q s_n + o_j]:
+    F applied first (the inner sums over p), then H (the outer sum over q),
+    each in FP64 in the order of the recursive steps (butterfly); precision
+    "fp32" rounds the result to FP32 (the entries a FP32 gather sees)."""
 
     def __init__(self, src, d, perm_rows, sign_rows, perm_cols, sign_cols, precision="fp64"):
         self.src, self.d = src, int(d)
@@ -636,18 +644,16 @@ class Preprocessed:
 
     def block(self, rows, cols):
         rows, cols = np.asarray(rows), np.asarray(cols)
+        D = 1 << self.d
+        bc, oc = np.divmod(self.pc[cols], self.sn)
+        ci = np.arange(D)[:, None] * self.sn + oc[None, :]          # D x len(cols): q s_n + o_j
         out = np.zeros((len(rows), len(cols)))
         for a, i in enumerate(rows):
-            ri, rs = _ah_terms(self.pr[i], self.sm, self.d)
-            tc = [_ah_terms(self.pc[j], self.sn, self.d) for j in cols]
-            ci = np.stack([t[0] for t in tc], axis=1)          # 2^d x len(cols)
-            cs = np.stack([t[1] for t in tc], axis=1)
-            acc = np.zeros(len(cols))
-            for p in range(1 << self.d):
-                row = self.src.block([ri[p]], ci.ravel()).reshape(ci.shape)   # 2^d x len(cols)
-                for q in range(1 << self.d):
-                    acc = acc + rs[p] * cs[q] * row[q]
-            out[a] = self.sr[i] * self.sc[cols] * acc
+            br, orow = divmod(int(self.pr[i]), self.sm)
+            X = np.stack([self.src.block([p * self.sm + orow], ci.ravel()).reshape(ci.shape)
+                          for p in range(D)])                       # X[p, q, c]
+            inner = butterfly(X, br, self.d)                         # (F M)[., q s_n + o_j]
+            out[a] = self.sr[i] * self.sc[cols] * butterfly(inner, bc, self.d)
         if self.precision == "fp32":
             out = out.astype(np.float32).astype(np.float64)
         return out
@@ -657,24 +663,21 @@ def recover_lra(pre, Cbar, Rbar):
     """Section 6.6: from an LRA Cbar Ubar Rbar of M_bar = F M H with
     F F^T = 2^d I and H^T H = 2^d I, the induced LRA of M is
     (F^T Cbar / 2^d) Ubar (Rbar H^T / 2^d).  Returns (A, B), A = F^T Cbar / 2^d
-    (m x l) and B = Rbar H^T / 2^d (l x n), from the multipliers' sparse form."""
+    (m x l) and B = Rbar H^T / 2^d (l x n).  With H_{m,d} symmetric,
+    F^T Cbar = H_{m,d} Y for Y[pr[i]] = sr[i] Cbar[i], and Rbar H^T = Z H_{n,d}
+    for Z[:, pc[j]] = sc[j] Rbar[:, j]; both products in the butterfly order."""
     Cbar = np.asarray(Cbar, np.float64)
     Rbar = np.asarray(Rbar, np.float64)
     m, n, d = pre.m, pre.n, pre.d
-    inv_r = np.empty(m, int)
-    inv_r[pre.pr] = np.arange(m)
-    inv_c = np.empty(n, int)
-    inv_c[pre.pc] = np.arange(n)
-    A = np.zeros((m, Cbar.shape[1]))
-    for a in range(m):
-        pos, sgn = _ah_terms(a, pre.sm, d)          # H_{m,d} is symmetric
-        i = inv_r[pos]
-        A[a] = (sgn * pre.sr[i]) @ Cbar[i] / (1 << d)
-    B = np.zeros((Rbar.shape[0], n))
-    for b in range(n):
-        pos, sgn = _ah_terms(b, pre.sn, d)
-        j = inv_c[pos]
-        B[:, b] = Rbar[:, j] @ (sgn * pre.sc[j]) / (1 << d)
+    D, l = 1 << d, Cbar.shape[1]
+    Y = np.empty_like(Cbar)
+    Y[pre.pr] = pre.sr[:, None] * Cbar
+    Y3 = Y.reshape(D, pre.sm, l)                                  # Y3[p, o] = Y[p s_m + o]
+    A = np.stack([butterfly(Y3, b, d) for b in range(D)]).reshape(m, l) / D
+    Z = np.empty_like(Rbar)
+    Z[:, pre.pc] = Rbar * pre.sc[None, :]
+    Z3 = Z.reshape(Rbar.shape[0], D, pre.sn).transpose(1, 0, 2)   # Z3[q, t, o] = Z[t, q s_n + o]
+    B = np.stack([butterfly(Z3, b, d) for b in range(D)], axis=1).reshape(Rbar.shape[0], n) / D
     return A, B
 
 

@@ -117,11 +117,25 @@ MUTANTS = [
     ("abridged_hadamard", "H = np.block([[H, H], [H, -H]])", "H = np.block([[H, H], [H, H]])",
      [lambda: pins.test_abridged_hadamard_equals_the_printed_matrices()]),
     # recovery: H^T applied with the permutation instead of its inverse
-    ("recover_lra", "j = inv_c[pos]", "j = pre.pc[pos]",
+    ("recover_lra", "Z[:, pre.pc] = Rbar * pre.sc[None, :]", "Z = Rbar[:, pre.pc] * pre.sc[None, pre.pc]",
+     [lambda: pins.test_recovered_lra_error_is_the_preprocessed_error_over_2_to_d()]),
+    ("recover_lra", "Y[pre.pr] = pre.sr[:, None] * Cbar", "Y = pre.sr[:, None] * Cbar[pre.pr]",
      [lambda: pins.test_recovered_lra_error_is_the_preprocessed_error_over_2_to_d()]),
     # recovery: the 2^d normalisation dropped on one side
-    ("recover_lra", "A[a] = (sgn * pre.sr[i]) @ Cbar[i] / (1 << d)", "A[a] = (sgn * pre.sr[i]) @ Cbar[i]",
+    ("recover_lra", "for b in range(D)]).reshape(m, l) / D", "for b in range(D)]).reshape(m, l)",
      [lambda: pins.test_recovered_lra_error_is_the_preprocessed_error_over_2_to_d()]),
+    # butterfly: a step that never subtracts
+    ("butterfly", "vals = vals[0::2] + sig * vals[1::2]", "vals = vals[0::2] + vals[1::2]",
+     [lambda: pins.test_preprocessed_entries_equal_F_M_H_exactly_on_small_integers()]),
+    # butterfly: the sign of step k taken from the wrong bit of b
+    ("butterfly", "(np.asarray(b) >> k) & 1", "(np.asarray(b) >> (d - 1 - k)) & 1",
+     [lambda: pins.test_preprocessed_entries_equal_F_M_H_exactly_on_small_integers(),
+      lambda: pins.test_butterfly_is_the_fast_walsh_transform_in_recursion_order()]),
+    # butterfly: steps taken top bit first (the transform is the same, the order is not)
+    ("butterfly", "vals = vals[0::2] + sig * vals[1::2]",
+     "h = len(vals) // 2; sig = np.where((np.asarray(b) >> (d - 1 - k)) & 1, -1.0, 1.0); "
+     "vals = vals[:h] + sig * vals[h:]",
+     [lambda: pins.test_butterfly_is_the_fast_walsh_transform_in_recursion_order()]),
     # C-A: horizontal step chooses J inside R instead of R^T
     ("cross_approximation", "maxvol(R.T, J,", "maxvol(R[:, :l], J,",
      [lambda: pins.test_exact_recovery_rank_l(90, 120, 7, 3),

@@ -709,6 +709,33 @@ def test_preprocessed_entries_are_the_product_F_M_H():
     np.testing.assert_allclose(pre.block(rows, cols), (F @ A @ H)[np.ix_(rows, cols)], rtol=0, atol=1e-12)
 
 
+def test_preprocessed_entries_equal_F_M_H_exactly_on_small_integers():
+    """Sums of small integers are exact in any order: every entry equals
+    the dense product F M H bit for bit (d = 1 .. 3, ragged s_m, s_n)."""
+    for seed, (m, n, d) in enumerate(((24, 40, 1), (36, 20, 2), (48, 56, 3))):
+        A = W.rng_for(1340 + seed).integers(-50, 51, size=(m, n)).astype(np.float64)
+        pre, F, H = _pre_case(1350 + seed, m, n, d, A)
+        np.testing.assert_array_equal(pre.block(np.arange(m), np.arange(n)), F @ A @ H)
+
+
+def test_butterfly_is_the_fast_walsh_transform_in_recursion_order():
+    """H_{2^d} x for every output index, exactly on integers; and the order
+    of the recursive steps, worked by hand for d = 2 on values where the
+    order changes the FP64 result: ((x0 + x1) + (x2 + x3)) with
+    x = (1e16, 1, -1e16, 1) is 1e16 + (-1e16) = 0, where a left-to-right
+    sum gives 1."""
+    x = W.rng_for(1360).integers(-9, 10, size=(16, 3)).astype(np.float64)
+    H = O.abridged_hadamard(16, 4)
+    for b in range(16):
+        np.testing.assert_array_equal(O.butterfly(x, b, 4), H[b] @ x)
+    v = np.array([1e16, 1.0, -1e16, 1.0])
+    assert O.butterfly(v, 0, 2) == 0.0
+    assert ((1e16 + 1.0) + -1e16) + 1.0 == 1.0
+    # b = 1: ((x0 - x1) + (x2 - x3)) = 1e16 + (-1e16) = 0; b = 3: (x0 - x1) - (x2 - x3) = 2e16
+    assert O.butterfly(v, 1, 2) == 0.0
+    assert O.butterfly(v, 3, 2) == 2e16
+
+
 def test_recovered_lra_error_is_the_preprocessed_error_over_2_to_d():
     """Section 6.6: with F F^T = 2^d I and H^T H = 2^d I the recovered LRA of
     M has error ||F^{-1} E H^{-1}||_F = ||E||_F / 2^d for the error E of the
