@@ -68,7 +68,10 @@ typedef enum {
   LRA_DENSE_F64 = 1,      /* a: double, m x n, row stride lda; gathered as FP32 */
   LRA_GEN_CAUCHY = 2,     /* a_ij = 1/(x_i - y_j); x: m floats, y: n floats   */
   LRA_GEN_GAUSS = 3,      /* a_ij = exp(-|x_i - y_j|^2 / h^2), dim-D points   */
-  LRA_GEN_INVDIST = 4     /* a_ij = 1/|x_i - y_j|, dim-D points               */
+  LRA_GEN_INVDIST = 4,    /* a_ij = 1/|x_i - y_j|, dim-D points               */
+  LRA_PRE_AH = 5          /* M_bar = F M H for a stored FP32 M (a, lda) and the
+                             abridged Hadamard multipliers of the pre_* fields
+                             (Section 8.1 family (i)); plain solves only       */
 } lra_kind;
 
 /* Decision log entry kinds (lra_cur_out.trace). */
@@ -116,6 +119,25 @@ typedef struct {
   const float* x;             /* generators: device, m points (point-major, dim)    */
   const float* y;             /* generators: device, n points                       */
   float h;                    /* LRA_GEN_GAUSS width                                */
+  /* LRA_PRE_AH (Section 8.1, family (i), with Section 6.6's nonsingular
+   * multipliers): F = D_r P_r H_{m,d} and H = H_{n,d} P_c D_c, with H_{n,d}
+   * the d-abridged Hadamard matrix (the recursion H_2s = [[H_s, H_s],
+   * [H_s, -H_s]] run d times from I_{n/2^d}; 2^d must divide m and n), P
+   * permutations and D diagonal +-1 scalings given by the caller (device
+   * arrays): row i of F is sign_rows[i] times row perm_rows[i] of H_{m,d},
+   * column j of H is sign_cols[j] times column perm_cols[j] of H_{n,d}.
+   * Entry (i, j) of M_bar is sign_rows[i] sign_cols[j] times entry
+   * (perm_rows[i], perm_cols[j]) of H_{m,d} M H_{n,d}: a sum of 4^d entries
+   * of M in FP64, in the order of the recursive steps (M's row blocks
+   * first, lowest bit first), rounded to FP32.  With pre_materialized != 0,
+   * a holds H_{m,d} M H_{n,d} itself (lra_preprocess_materialize) and an
+   * entry is one signed read. */
+  int32_t pre_d;              /* recursion depth d, 0..10                           */
+  const int32_t* pre_perm_rows;   /* device, m: a permutation of 0..m-1             */
+  const float* pre_sign_rows;     /* device, m: +-1                                 */
+  const int32_t* pre_perm_cols;   /* device, n: a permutation of 0..n-1             */
+  const float* pre_sign_cols;     /* device, n: +-1                                 */
+  int32_t pre_materialized;       /* a is H_{m,d} M H_{n,d}, not M                   */
 } lra_source;
 
 typedef struct {
@@ -475,6 +497,31 @@ lra_status lra_maxvol_noalloc(const float* strip, int64_t N, int32_t l,
                               int64_t row_stride, int64_t col_stride, int32_t* pos,
                               const double* xinv, double delta, int32_t max_swaps,
                               int32_t* status_out, void* stream);
+
+/* Section 8.1 (the fast product with H_{n,d}: d recursive steps, at most
+ * 2dn additions per vector): G = H_{m,d} M H_{n,d} for the stored FP32 M
+ * of an LRA_PRE_AH source (a, lda; pre_materialized = 0) with d = pre_d
+ * <= 5, in one pass over M: every entry of M read once, every entry of G
+ * written once (FP64 transforms in the order of the recursive steps,
+ * rounded once to FP32: the same values as the entry-by-entry evaluation).
+ * G: device FP32, m x n, row stride ldg >= n, not overlapping M.  A source
+ * with a = G, lda = ldg and pre_materialized = 1 then gives the same
+ * entries of M_bar with one read each.  Enqueued on `stream`; LRA_EINVAL
+ * for another kind, d > 5 or ldg < n. */
+lra_status lra_preprocess_materialize(const lra_source* pre, float* G, int64_t ldg, void* stream);
+
+/* Section 6.6 (recovery of an LRA with nonsingular multipliers): from an
+ * LRA Cbar U Rbar of the pre-processed M_bar = F M H of an LRA_PRE_AH
+ * source (e.g. C, U, R of a solve on it), the factors of the induced LRA
+ * A U B of M: A = F^T Cbar / 2^d (m x l) and B = Rbar H^T / 2^d (l x n),
+ * since F F^T = 2^d I and H^T H = 2^d I; its error is the error on M_bar
+ * divided by 2^d.  Cbar (m x l), Rbar (l x n), A, B: device FP32,
+ * row-major; each entry an FP64 sum of 2^d terms in the order of the
+ * recursive steps, scaled by 2^-d and rounded to FP32.
+ * Enqueued on `stream` (takes m + n ints of stream-ordered scratch);
+ * LRA_EINVAL for a source of another kind or l outside 1..96. */
+lra_status lra_preprocessed_recover(const lra_source* pre, const float* Cbar, const float* Rbar, int32_t l, float* A,
+                                    float* B, void* stream);
 
 /* Section 12.2 (the C-A tests start from random columns): the initial
  * column set drawn from a seed, as submit draws it when init_J is NULL.

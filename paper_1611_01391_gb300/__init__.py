@@ -27,7 +27,7 @@ LRA_EINVAL, LRA_ENOMEM, LRA_EBUSY, LRA_ESINGULAR = -1, -2, -3, -4
 LRA_ENONFINITE, LRA_ETIMEOUT, LRA_ECUDA, LRA_ENOTFOUND = -5, -6, -7, -8
 LRA_ECANCELED, LRA_ETOOLARGE = -9, -10
 
-LRA_DENSE_F32, LRA_DENSE_F64, LRA_GEN_CAUCHY, LRA_GEN_GAUSS, LRA_GEN_INVDIST = range(5)
+LRA_DENSE_F32, LRA_DENSE_F64, LRA_GEN_CAUCHY, LRA_GEN_GAUSS, LRA_GEN_INVDIST, LRA_PRE_AH = range(6)
 LRA_TRACE_GEPP, LRA_TRACE_SWAP, LRA_TRACE_STOP, LRA_TRACE_CAP = range(4)
 LRA_STATE_RUNNING, LRA_STATE_DONE, LRA_STATE_FAILED = range(3)
 LRA_FLAG_PROFILE = 1
@@ -45,7 +45,10 @@ class lra_source(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("dim", ctypes.c_int32),
                 ("m", ctypes.c_int64), ("n", ctypes.c_int64),
                 ("a", ctypes.c_void_p), ("lda", ctypes.c_int64),
-                ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("h", ctypes.c_float)]
+                ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("h", ctypes.c_float),
+                ("pre_d", ctypes.c_int32), ("pre_perm_rows", ctypes.c_void_p), ("pre_sign_rows", ctypes.c_void_p),
+                ("pre_perm_cols", ctypes.c_void_p), ("pre_sign_cols", ctypes.c_void_p),
+                ("pre_materialized", ctypes.c_int32)]
 
 
 class lra_params(ctypes.Structure):
@@ -167,6 +170,10 @@ _cynical = _sig("lra_cross_cynical", ctypes.c_int, _ctx_p, ctypes.POINTER(lra_so
                 ctypes.POINTER(lra_cynical_params), ctypes.POINTER(lra_cynical_out))
 _refine = _sig("lra_cross_refine", ctypes.c_int, _ctx_p, ctypes.POINTER(lra_source), ctypes.c_void_p,
                ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(lra_refine_params), ctypes.POINTER(lra_refine_out))
+_pre_recover = _sig("lra_preprocessed_recover", ctypes.c_int, ctypes.POINTER(lra_source), ctypes.c_void_p,
+                    ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_pre_materialize = _sig("lra_preprocess_materialize", ctypes.c_int, ctypes.POINTER(lra_source), ctypes.c_void_p,
+                        ctypes.c_int64, ctypes.c_void_p)
 _status_str = _sig("lra_status_str", ctypes.c_char_p, ctypes.c_int32)
 _last_error = _sig("lra_cross_last_error", ctypes.c_char_p, _ctx_p)
 
@@ -174,7 +181,8 @@ EXPORTED = ["lra_cross_create", "lra_cross_destroy", "lra_cross_submit", "lra_cr
             "lra_cross_wait", "lra_cross_fetch_cur", "lra_cross_cancel", "lra_cross_footprint",
             "lra_status_str", "lra_cross_last_error", "lra_cross_submit_batch",
             "lra_cross_fetch_batch", "lra_draw_columns", "lra_gather_entries", "lra_maxvol_noalloc",
-            "lra_cross_tune_batch", "lra_batch_tuning_lookup", "lra_cross_cynical", "lra_cross_refine"]
+            "lra_cross_tune_batch", "lra_batch_tuning_lookup", "lra_cross_cynical", "lra_cross_refine",
+            "lra_preprocessed_recover", "lra_preprocess_materialize"]
 
 
 class LraError(RuntimeError):
@@ -272,6 +280,17 @@ def lra_maxvol_noalloc(strip_ptr, N, l, row_stride, col_stride, pos_ptr, xinv_pt
                            status_ptr, stream)
 
 
+def lra_preprocess_materialize(pre: lra_source, G, stream=None) -> None:
+    """G = H_{m,d} M H_{n,d} on the device (torch float32 tensor, row-major)."""
+    _check(_pre_materialize(ctypes.byref(pre), G.data_ptr(), G.stride(0), stream))
+
+
+def lra_preprocessed_recover(pre: lra_source, Cbar, Rbar, A, B, stream=None) -> None:
+    """A = F^T Cbar / 2^d, B = Rbar H^T / 2^d on the device (torch float32 tensors)."""
+    _check(_pre_recover(ctypes.byref(pre), Cbar.data_ptr(), Rbar.data_ptr(), Cbar.shape[1], A.data_ptr(),
+                        B.data_ptr(), stream))
+
+
 def lra_cross_refine(ctx, src: lra_source, I, J, r: int, l_new: int, u_cols, u_rows, rank_tol: float = 1e-6,
                      resid_rows=None, resid_cols=None, scores: bool = False):
     """Section 7.2 refinement of the C-A CUR of (I, J): returns a dict with
@@ -351,7 +370,8 @@ def lra_cross_footprint(src: lra_source, params: lra_params) -> int:
     return b.value
 
 
-from .api import BatchResult, Context, SolveResult, make_params, make_source  # noqa: E402
+from .api import BatchResult, Context, SolveResult, make_params, make_source, solve_preprocessed  # noqa: E402
 
 __all__ = EXPORTED + ["Context", "SolveResult", "BatchResult", "LraError", "make_params", "make_source",
+                      "solve_preprocessed",
                       "lra_source", "lra_params", "lra_info", "lra_cur_out", "LIB_PATH"]

@@ -8,10 +8,10 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import (LRA_DENSE_F32, LRA_DENSE_F64, LRA_GEN_CAUCHY, LRA_GEN_GAUSS, LRA_GEN_INVDIST,
+from . import (LRA_DENSE_F32, LRA_DENSE_F64, LRA_GEN_CAUCHY, LRA_GEN_GAUSS, LRA_GEN_INVDIST, LRA_PRE_AH,
                lra_batch_out, lra_batch_params, lra_cross_create, lra_cross_destroy,
                lra_cross_fetch_batch, lra_cross_fetch_cur, lra_cross_submit, lra_cross_submit_batch,
-               lra_cross_wait, lra_cur_out, lra_info, lra_params, lra_source)
+               lra_cross_wait, lra_cur_out, lra_info, lra_params, lra_preprocessed_recover, lra_source)
 
 _KINDS = {"dense": None, "cauchy": LRA_GEN_CAUCHY, "gauss": LRA_GEN_GAUSS,
           "invdist": LRA_GEN_INVDIST}
@@ -21,9 +21,23 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
-def make_source(kind: str, *, a=None, x=None, y=None, h: float = 0.0) -> lra_source:
-    """Source descriptor from device tensors (kept alive by the caller)."""
+def make_source(kind: str, *, a=None, x=None, y=None, h: float = 0.0, d: int = 0, perm_rows=None,
+                sign_rows=None, perm_cols=None, sign_cols=None, materialized: bool = False) -> lra_source:
+    """Source descriptor from device tensors (kept alive by the caller).
+    kind "preprocessed": M_bar = F M H for the stored FP32 a and the abridged
+    Hadamard multipliers of depth d (int32 permutations, float32 +-1 signs);
+    materialized: a already holds H_{m,d} M H_{n,d}."""
     import torch
+    if kind == "preprocessed":
+        if a.dtype != torch.float32 or not a.is_cuda or a.dim() != 2 or a.stride(1) != 1:
+            raise ValueError("preprocessed source: row-major 2-D float32 CUDA tensor required")
+        for t, dt in ((perm_rows, torch.int32), (sign_rows, torch.float32), (perm_cols, torch.int32),
+                      (sign_cols, torch.float32)):
+            if t is None or t.dtype != dt or not t.is_cuda or not t.is_contiguous():
+                raise ValueError("preprocessed source: int32 permutations and float32 signs on the device")
+        return lra_source(LRA_PRE_AH, 0, a.shape[0], a.shape[1], a.data_ptr(), a.stride(0), None, None, 0.0,
+                          d, perm_rows.data_ptr(), sign_rows.data_ptr(), perm_cols.data_ptr(), sign_cols.data_ptr(),
+                          int(bool(materialized)))
     if kind == "dense":
         if a.dtype not in (torch.float32, torch.float64) or not a.is_cuda or a.dim() != 2:
             raise ValueError("dense source: 2-D float32/float64 CUDA tensor required")
@@ -202,3 +216,16 @@ def solve_batch(context, src, blocks, params, l_max):
     blocks = np.ascontiguousarray(blocks, dtype=np.int64)
     job = lra_cross_submit_batch(context.ctx, src, blocks, params)
     return _batch_fetch(context.ctx, job, len(blocks), l_max, params.trace_cap)
+
+
+def solve_preprocessed(context, pre, params, l, m, n, trace_cap=0, device=None):
+    """C-A on M_bar = F M H (an LRA_PRE_AH source), then the LRA A U B of M
+    it induces (Section 6.6): A = F^T Cbar / 2^d, B = Rbar H^T / 2^d, on the
+    device.  Returns (SolveResult on M_bar with device strips C, R; A; B)."""
+    import torch
+    res = context.solve(pre, params, l, m, n, want_strips=True, trace_cap=trace_cap, device=device)
+    A = torch.empty((m, l), dtype=torch.float32, device=res.C.device)
+    B = torch.empty((l, n), dtype=torch.float32, device=res.C.device)
+    stream = torch.cuda.current_stream(res.C.device).cuda_stream
+    lra_preprocessed_recover(pre, res.C, res.R, A, B, stream)
+    return res, A, B

@@ -257,7 +257,7 @@ cudaError_t launch_gather_cols(const SourceDev& s, const int* J, int l, float* C
                                const JobStatus* js, int skip_on_stop, int sms,
                                cudaStream_t st) {
   const int grid = grid_for(s.m * (long long)l, 256 * 4, sms);
-  LRA_DISPATCH_KIND(s.kind, (gather_cols_kernel<K><<<grid, 256, 0, st>>>(s, J, l, C, js, skip_on_stop)));
+  LRA_DISPATCH_KIND_ALL(s.kind, (gather_cols_kernel<K><<<grid, 256, 0, st>>>(s, J, l, C, js, skip_on_stop)));
   return cudaGetLastError();
 }
 
@@ -268,7 +268,7 @@ cudaError_t launch_gather_rows(const SourceDev& s, const int* I, int l, float* R
   int vec_ok = (s.n % 4 == 0) && ((reinterpret_cast<uintptr_t>(R) & 15) == 0);
   if (s.kind == LRA_DENSE_F32)
     vec_ok = vec_ok && (s.lda % 4 == 0) && ((reinterpret_cast<uintptr_t>(s.a) & 15) == 0);
-  LRA_DISPATCH_KIND(s.kind, (gather_rows_kernel<K><<<grid, 256, 0, st>>>(s, I, l, R, js, vec_ok)));
+  LRA_DISPATCH_KIND_ALL(s.kind, (gather_rows_kernel<K><<<grid, 256, 0, st>>>(s, I, l, R, js, vec_ok)));
   return cudaGetLastError();
 }
 
@@ -280,7 +280,7 @@ cudaError_t launch_gather_entries(const SourceDev& s, const int* rows, long long
   void* args[] = {&sd, const_cast<int**>(&rows), &q, const_cast<int**>(&cols), &sN, &out};
   // launched through its own return code: the runtime's last-error state is
   // left as the caller had it
-  LRA_DISPATCH_KIND(s.kind, (e = cudaLaunchKernel(reinterpret_cast<const void*>(gather_entries_kernel<K>),
+  LRA_DISPATCH_KIND_ALL(s.kind, (e = cudaLaunchKernel(reinterpret_cast<const void*>(gather_entries_kernel<K>),
                                                    dim3(grid), dim3(256), args, 0, st)));
   return e;
 }

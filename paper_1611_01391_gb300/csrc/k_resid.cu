@@ -156,7 +156,7 @@ cudaError_t launch_sampled_residual(const SourceDev& s, const int* rows, int q, 
   if (nb > max_partials) return cudaErrorInvalidValue;
   cu_rows_kernel<<<(q * l + 255) / 256, 256, 0, st>>>(C, rows, q, l, U, CUq, js);
   dim3 grid((sN + kTile - 1) / kTile, (q + kTile - 1) / kTile);
-  LRA_DISPATCH_KIND(s.kind, (resid_tile_kernel<K><<<grid, 256, 0, st>>>(s, rows, q, cols, sN, l, CUq,
+  LRA_DISPATCH_KIND_ALL(s.kind, (resid_tile_kernel<K><<<grid, 256, 0, st>>>(s, rows, q, cols, sN, l, CUq,
                                                                          R, partials, js)));
   resid_final_kernel<<<1, 256, 0, st>>>(partials, nb, (long long)q * sN, js);
   return cudaGetLastError();

@@ -24,6 +24,14 @@ struct SourceDev {
   const float* x;
   const float* y;
   float h2;          // h*h rounded to FP32 (Gaussian kernel)
+  // LRA_PRE_AH: base matrix in a / lda, multipliers
+  int pre_d;
+  int pre_mat;                // a holds H_{m,d} M H_{n,d} (lra_preprocess_materialize)
+  long long pre_sm, pre_sn;   // m / 2^d, n / 2^d
+  const int* pre_pr;
+  const float* pre_sr;
+  const int* pre_pc;
+  const float* pre_sc;
 };
 
 // |x_i - y_j|^2 accumulated coordinate by coordinate with one rounding per
@@ -40,6 +48,24 @@ __device__ __forceinline__ float dist2(const SourceDev& s, long long i, long lon
   return acc;
 }
 
+// Section 8.1 multiplies by H_{2^d} through d recursive steps
+// H_{2s} = [[H_s, H_s], [H_s, -H_s]].  One entry b of that product, summed
+// in the same order as the fast transform: the terms t = 0, 1, ... arrive
+// in order and are merged like a binary counter, the merge at level k being
+// left + right, or left - right when bit k of b is 1.  After term 2^d - 1
+// the returned value is the entry.  stk holds d + 1 partial sums.
+constexpr int kMaxPreD = 10;
+
+__device__ __forceinline__ double butterfly_push(double* stk, int t, double v, unsigned b) {
+  int k = 0;
+  while ((t >> k) & 1) {
+    v = ((b >> k) & 1u) ? stk[k] - v : stk[k] + v;
+    ++k;
+  }
+  stk[k] = v;
+  return v;
+}
+
 template <int KIND>
 __device__ __forceinline__ float entry(const SourceDev& s, long long i, long long j) {
   if constexpr (KIND == LRA_DENSE_F32) {
@@ -50,10 +76,47 @@ __device__ __forceinline__ float entry(const SourceDev& s, long long i, long lon
     return __fdiv_rn(1.0f, __fsub_rn(__ldg(s.x + i), __ldg(s.y + j)));
   } else if constexpr (KIND == LRA_GEN_GAUSS) {
     return expf(-__fdiv_rn(dist2(s, i, j), s.h2));
-  } else {
+  } else if constexpr (KIND == LRA_GEN_INVDIST) {
     return __fdiv_rn(1.0f, __fsqrt_rn(dist2(s, i, j)));
+  } else {
+    // M_bar[i][j] = sr[i] sc[j] (H_{m,d} M H_{n,d})[pr[i]][pc[j]]: with
+    // (bi, oi) = divmod(pr[i], sm), (bj, oj) = divmod(pc[j], sn), the sum
+    // over q (signs by bj) of the sums over p (signs by bi) of
+    // M[p sm + oi][q sn + oj], each in the butterfly order, FP64, then FP32.
+    long long xi = __ldg(s.pre_pr + i), yj = __ldg(s.pre_pc + j);
+    // a caller's array that is not a permutation cannot move a read outside M
+    if ((unsigned long long)xi >= (unsigned long long)s.m) xi = 0;
+    if ((unsigned long long)yj >= (unsigned long long)s.n) yj = 0;
+    const float sgn = __ldg(s.pre_sr + i) * __ldg(s.pre_sc + j);
+    const float* a = static_cast<const float*>(s.a);
+    if (s.pre_mat) return sgn * __ldg(a + xi * s.lda + yj);   // a holds H_{m,d} M H_{n,d}
+    const long long bi = xi / s.pre_sm, oi = xi - bi * s.pre_sm;
+    const long long bj = yj / s.pre_sn, oj = yj - bj * s.pre_sn;
+    const int D = 1 << s.pre_d;
+    double so[kMaxPreD + 1], si[kMaxPreD + 1];
+    double acc = 0.0;
+    for (int qq = 0; qq < D; ++qq) {
+      const float* col = a + oi * s.lda + qq * s.pre_sn + oj;
+      double inner = 0.0;
+      for (int pp = 0; pp < D; ++pp)
+        inner = butterfly_push(si, pp, (double)__ldg(col + pp * s.pre_sm * s.lda), (unsigned)bi);
+      acc = butterfly_push(so, qq, inner, (unsigned)bj);
+    }
+    return sgn * __double2float_rn(acc);
   }
 }
+
+// As LRA_DISPATCH_KIND, with the pre-processed source as well (the kernels
+// of a plain solve that evaluate entries: gathers and the residual).
+#define LRA_DISPATCH_KIND_ALL(kind, BODY)                               \
+  switch (kind) {                                                      \
+    case LRA_DENSE_F32: { constexpr int K = LRA_DENSE_F32; BODY; } break; \
+    case LRA_DENSE_F64: { constexpr int K = LRA_DENSE_F64; BODY; } break; \
+    case LRA_GEN_CAUCHY: { constexpr int K = LRA_GEN_CAUCHY; BODY; } break; \
+    case LRA_GEN_GAUSS: { constexpr int K = LRA_GEN_GAUSS; BODY; } break; \
+    case LRA_PRE_AH: { constexpr int K = LRA_PRE_AH; BODY; } break;     \
+    default: { constexpr int K = LRA_GEN_INVDIST; BODY; } break;       \
+  }
 
 // Calls F<KIND> with the source kind as a compile-time constant.
 #define LRA_DISPATCH_KIND(kind, BODY)                                   \

@@ -133,6 +133,14 @@ cudaError_t launch_lev_scores_sample(const double* Y, long long N, int k, const 
                                      const double* u, int ls, int* idx, double* d, double* scores,
                                      const JobStatus* js, cudaStream_t st);
 
+// Section 6.6: A = F^T Cbar / 2^d and B = Rbar H^T / 2^d for the abridged
+// Hadamard multipliers of a pre-processed source; inv: m + n ints of scratch.
+// Section 8.1: G = H_{m,d} M H_{n,d} in one pass (d <= 5).
+cudaError_t launch_pre_materialize(const float* M, long long lda, float* G, long long ldg, long long m, long long n,
+                                   int d, cudaStream_t st);
+cudaError_t launch_pre_recover(const SourceDev& s, const float* Cbar, const float* Rbar, int l, float* A, float* B,
+                               int* inv, cudaStream_t st);
+
 // Small control kernels.
 cudaError_t launch_tol_check(JobStatus* js, double tol, cudaStream_t st);
 

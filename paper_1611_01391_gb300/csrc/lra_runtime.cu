@@ -146,9 +146,18 @@ lra_status cuda_fail(lra_ctx* ctx, cudaError_t e, const char* what) {
 
 lra_status validate_source(const lra_source* src, std::string* why) {
   if (!src) { *why = "null source"; return LRA_EINVAL; }
-  if (src->kind < LRA_DENSE_F32 || src->kind > LRA_GEN_INVDIST) { *why = "unknown source kind"; return LRA_EINVAL; }
+  if (src->kind < LRA_DENSE_F32 || src->kind > LRA_PRE_AH) { *why = "unknown source kind"; return LRA_EINVAL; }
   if (src->m < 1 || src->n < 1 || src->m > (1LL << 30) || src->n > (1LL << 30)) { *why = "bad matrix size"; return LRA_EINVAL; }
-  if (src->kind <= LRA_DENSE_F64) {
+  if (src->kind == LRA_PRE_AH) {
+    if (!src->a || src->lda < src->n) { *why = "pre-processed source needs a and lda >= n"; return LRA_EINVAL; }
+    if (src->pre_d < 0 || src->pre_d > kMaxPreD) { *why = "pre_d must be in 0..10"; return LRA_EINVAL; }
+    if ((src->m % (1LL << src->pre_d)) != 0 || (src->n % (1LL << src->pre_d)) != 0) {
+      *why = "2^pre_d must divide m and n"; return LRA_EINVAL;
+    }
+    if (!src->pre_perm_rows || !src->pre_sign_rows || !src->pre_perm_cols || !src->pre_sign_cols) {
+      *why = "pre-processed source needs its permutations and signs"; return LRA_EINVAL;
+    }
+  } else if (src->kind <= LRA_DENSE_F64) {
     if (!src->a || src->lda < src->n) { *why = "dense source needs a and lda >= n"; return LRA_EINVAL; }
   } else {
     if (!src->x || !src->y) { *why = "generator needs x and y"; return LRA_EINVAL; }
@@ -478,6 +487,16 @@ SourceDev make_src(const lra_source* src) {
   d.x = src->x;
   d.y = src->y;
   d.h2 = src->h * src->h;
+  if (src->kind == LRA_PRE_AH) {
+    d.pre_d = src->pre_d;
+    d.pre_mat = src->pre_materialized != 0;
+    d.pre_sm = src->m >> src->pre_d;
+    d.pre_sn = src->n >> src->pre_d;
+    d.pre_pr = src->pre_perm_rows;
+    d.pre_sr = src->pre_sign_rows;
+    d.pre_pc = src->pre_perm_cols;
+    d.pre_sc = src->pre_sign_cols;
+  }
   return d;
 }
 
@@ -829,6 +848,35 @@ lra_status lra_cross_cancel(lra_ctx* ctx, lra_job id) {
   std::lock_guard<std::mutex> lock(ctx->mu);
   release_job(ctx, j);
   return LRA_OK;
+}
+
+lra_status lra_preprocess_materialize(const lra_source* pre, float* G, int64_t ldg, void* stream) {
+  std::string why;
+  if (validate_source(pre, &why) != LRA_OK || pre->kind != LRA_PRE_AH || pre->pre_materialized || pre->pre_d > 5 ||
+      !G || ldg < pre->n)
+    return LRA_EINVAL;
+  const float* M = static_cast<const float*>(pre->a);
+  // G must not overlap M (it is written while M is read)
+  const char *g0 = reinterpret_cast<const char*>(G), *g1 = reinterpret_cast<const char*>(G + (pre->m - 1) * ldg + pre->n);
+  const char *m0 = reinterpret_cast<const char*>(M), *m1 = reinterpret_cast<const char*>(M + (pre->m - 1) * pre->lda + pre->n);
+  if (g0 < m1 && m0 < g1) return LRA_EINVAL;
+  const cudaError_t e = launch_pre_materialize(M, pre->lda, G, ldg, pre->m, pre->n, pre->pre_d,
+                                               static_cast<cudaStream_t>(stream));
+  return e ? LRA_ECUDA : LRA_OK;
+}
+
+lra_status lra_preprocessed_recover(const lra_source* pre, const float* Cbar, const float* Rbar, int32_t l, float* A,
+                                    float* B, void* stream) {
+  std::string why;
+  if (validate_source(pre, &why) != LRA_OK || pre->kind != LRA_PRE_AH) return LRA_EINVAL;
+  if (!Cbar || !Rbar || !A || !B || l < 1 || l > kMaxL) return LRA_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int* inv = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&inv), sizeof(int) * (size_t)(pre->m + pre->n), st);
+  if (e) return e == cudaErrorMemoryAllocation ? LRA_ENOMEM : LRA_ECUDA;
+  e = launch_pre_recover(make_src(pre), Cbar, Rbar, l, A, B, inv, st);
+  cudaFreeAsync(inv, st);
+  return e ? LRA_ECUDA : LRA_OK;
 }
 
 lra_status lra_draw_columns(uint64_t seed, int64_t n, int32_t l, int32_t* out) {

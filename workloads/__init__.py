@@ -24,6 +24,13 @@ Workload families (sizes as in the named configurations):
 * ``cauchy_points``    -- x_i ~ U[0,1], y_j ~ U[2,3] in FP32; the matrix
   a_ij = 1/(x_i - y_j) is never materialised.
 * ``cloud_points``     -- points uniform in the unit cube (FP32, 3-D).
+* ``laplacian_single_layer`` -- class (i) of the paper's test inputs
+  (Section 12.4, tb_Lp / tb_fh): the discretised single-layer Laplacian
+  operator between the contours C(0,1) and C(0,2), normalised to unit
+  spectral norm; the inputs on which plain C-A was reported to fail and
+  pre-processing was applied.
+* ``hadamard_multipliers`` -- the random permutations and +-1 scalings of
+  the abridged scaled and permuted Hadamard multipliers (Section 8.1).
 * ``draw_indices``     -- l distinct indices uniform without replacement:
   the random initial column set of Section 12.2 (Tests 1/2) and the random
   q x s error sample of Appendix F.
@@ -268,3 +275,33 @@ def delta_matrix(m: int, n: int, i: int, j: int) -> np.ndarray:
     a = np.zeros((m, n))
     a[i, j] = 1.0
     return a
+
+
+def laplacian_single_layer(n: int, nodes: int = 8, row_block: int = 256) -> np.ndarray:
+    """n x n FP64 matrix m_ij = c * integral over the arc j of the unit
+    circle (angles 2 pi j / n .. 2 pi (j + 1) / n, arc-length measure) of
+    log|x_i - y|, x_i = 2 exp(2 pi sqrt(-1) i / n) on the circle of radius 2,
+    with c such that the spectral norm is 1.  Each arc integral by
+    Gauss-Legendre quadrature with `nodes` points (the integrand is smooth:
+    |x_i - y| >= 1)."""
+    t, w = np.polynomial.legendre.leggauss(nodes)
+    h = 2.0 * np.pi / n
+    theta = (np.arange(n)[:, None] + (t[None, :] + 1.0) / 2.0) * h       # n arcs x nodes
+    y = np.exp(1j * theta)
+    x = 2.0 * np.exp(2j * np.pi * np.arange(n) / n)
+    out = np.empty((n, n))
+    for r0 in range(0, n, row_block):
+        r1 = min(n, r0 + row_block)
+        out[r0:r1] = (np.log(np.abs(x[r0:r1, None, None] - y[None, :, :])) @ w) * (h / 2.0)
+    return out / np.linalg.norm(out, 2)
+
+
+def hadamard_multipliers(seed: int, m: int, n: int):
+    """Random permutations (int32) and +-1 scalings (float32) of the rows of
+    F and the columns of H: (perm_rows, sign_rows, perm_cols, sign_cols)."""
+    rng = rng_for(seed)
+    pr = rng.permutation(m).astype(np.int32)
+    sr = rng.choice(np.array([-1.0, 1.0], np.float32), m)
+    pc = rng.permutation(n).astype(np.int32)
+    sc = rng.choice(np.array([-1.0, 1.0], np.float32), n)
+    return pr, sr, pc, sc
