@@ -1089,7 +1089,7 @@ lra_status lra_cross_refine(lra_ctx* ctx, const lra_source* src, const int32_t* 
   if (!e && (hjs.status != LRA_OK || rr < 1)) {
     cudaFreeAsync(b, st);
     if (hjs.status != LRA_OK) return fail(ctx, (lra_status)hjs.status, "refine: device status");
-    return fail(ctx, LRA_ESINGULAR, "refine: the cross has rank 0");
+    return fail(ctx, LRA_ESINGULAR, "refine: the C-A cross has rank 0");
   }
   // phase 2: H = C (U P_rr) and Z^T = R^T (U^T V_rr), their Gram matrices
   // and scores, the sampling, the refined strips and nucleus
@@ -1120,7 +1120,7 @@ lra_status lra_cross_refine(lra_ctx* ctx, const lra_source* src, const int32_t* 
   cudaFreeAsync(b, st);
   if (e) return cuda_fail(ctx, e, "refine");
   if (hjs.status != LRA_OK) return fail(ctx, (lra_status)hjs.status, "refine: device status");
-  if (hjs.k_eff < 1) return fail(ctx, LRA_ESINGULAR, "refine: the cross has rank 0");
+  if (hjs.k_eff < 1) return fail(ctx, LRA_ESINGULAR, "refine: the sampled generator has rank 0");
   if (out->est_rel_err) *out->est_rel_err = q > 0 ? hjs.est_rel : -1.0;
   if (out->k_eff) *out->k_eff = rr;
   return LRA_OK;

@@ -100,7 +100,8 @@ struct SvdScratch {
 // c > j), its diagonal in sc->rdiag, and the Householder vector v_j in rows
 // j..l-1 of column j, with H_j = I - beta_j v_j v_j^T.  The pivot is the
 // trailing column of largest norm (ties: the smaller column); the norms are
-// recomputed from the updated columns at every step.
+// recomputed from the updated columns at every step; a trailing column of
+// squared norm at most 2^-100 is taken as zero (R's diagonal entry 0).
 // L > 0 (every function below): a build for l == L exactly.
 template <int NT, int L = 0>
 __device__ void qrcp_dd(dd* A, int l_arg, SvdScratch* sc) {
@@ -166,7 +167,12 @@ __device__ void qrcp_dd(dd* A, int l_arg, SvdScratch* sc) {
       a = acc_group_sum<32>(a);
       if (lane == 0) {
         const dd n2 = acc_value(a);
-        if (!(n2.hi > 0.0f)) {
+        // X is scaled to max |X| < 1: a trailing column of squared norm below
+        // 2^-100 (norm 2^-50, under the pairs' 2^-48 rounding) is numerically
+        // zero.  Below that the reflector's scalar 1 / (n2 + |x0| ||x||) can
+        // overflow FP32 (repeated rows and columns of a sampled generator
+        // leave such columns), so the step is skipped as for an exact zero.
+        if (!(n2.hi > 0x1p-100f)) {
           sc->beta[j] = dd{0.f, 0.f};
           sc->rdiag[j] = dd{0.f, 0.f};
         } else {

@@ -120,3 +120,33 @@ def test_refine_rejects_bad_arguments(ctx):
         with pytest.raises(L.LraError) as e:
             L.lra_cross_refine(ctx.ctx, src, args["I"], args["J"], args["r"], args["l_new"], args["uc"], args["ur"])
         assert e.value.code == L.LRA_EINVAL
+
+
+def test_refine_with_repeated_draws(ctx):
+    """Exactly(l) draws with replacement: repeated columns and rows make the
+    sampled generator exactly rank-deficient (n = 1024, r = 16, l = 24,
+    64 draws, 3 repeated columns, 4 repeated rows); the trailing columns of
+    its pivoted QR are then zero up to rounding, which must not break the
+    nucleus (a reflector scalar overflowed here before)."""
+    n, r, lc, ln = 1024, 16, 24, 64
+    rng = W.rng_for(W.BASE_SEED + 12000)
+    rng.standard_normal((n, r)), rng.standard_normal((r, n)), rng.standard_normal((n, n))
+    B64 = rng.standard_normal((n, r)) @ rng.standard_normal((r, n)) + 1e-4 * rng.standard_normal((n, n))
+    B32 = B64.astype(np.float32)
+    src = L.make_source("dense", a=torch.from_numpy(B32).cuda())
+    p, keep = L.make_params(r, lc, 3, W.draw_indices(W.BASE_SEED + 12500, n, lc))
+    ca = ctx.solve(src, p, lc)
+    assert ca.info.status == 0 and ca.info.k_eff == r
+    u = W.rng_for(W.BASE_SEED + 12600)
+    uc, ur = u.random(ln), u.random(ln)
+    dev = L.lra_cross_refine(ctx.ctx, src, ca.I, ca.J, r, ln, uc, ur, rank_tol=GPU_TAU)
+    assert dev["k_eff"] == r
+    s32 = O.Dense(B32)
+    Ur, kr, _ = O.nucleus(s32.block(ca.I, ca.J), r, GPU_TAU)
+    ref = O.refine_by_leverage(s32, list(ca.I), list(ca.J), Ur, r, ln, ln, uc, ur, rank_tol=GPU_TAU)
+    B = B32.astype(np.float64)
+
+    def err(cl, U, rw):
+        return np.linalg.norm(B - B[:, cl] @ U @ B[rw, :]) / np.linalg.norm(B)
+
+    assert error_ok(err(dev["cols"], dev["U"], dev["rows"]), err(ref.cols, ref.U, ref.rows))
