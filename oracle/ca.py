@@ -615,10 +615,13 @@ def butterfly(vals, b, d):
     the fast multiplication with at most 2dn additions): the innermost
     step combines the entries p that differ in bit 0, the next those that
     differ in bit 1, and so on; a step whose bit of b is 1 subtracts the
-    second half.  b may be an array broadcast over the trailing axes."""
-    vals = np.asarray(vals, np.float64)
+    second half.  b may be an array broadcast over the trailing axes.  The
+    arithmetic is that of vals (float32 or float64), every step rounded."""
+    vals = np.asarray(vals)
+    if vals.dtype != np.float32:
+        vals = vals.astype(np.float64)
     for k in range(d):
-        sig = np.where((np.asarray(b) >> k) & 1, -1.0, 1.0)
+        sig = np.where((np.asarray(b) >> k) & 1, -1.0, 1.0).astype(vals.dtype)
         vals = vals[0::2] + sig * vals[1::2]
     return vals[0]
 
@@ -629,8 +632,10 @@ class Preprocessed:
     with x = pr[i] = b_i s_m + o_i and y = pc[j] = b_j s_n + o_j,
     M_bar[i, j] = sF[i] sH[j] sum_q (+-1) sum_p (+-1) M[p s_m + o_i, q s_n + o_j]:
     F applied first (the inner sums over p), then H (the outer sum over q),
-    each in FP64 in the order of the recursive steps (butterfly); precision
-    "fp32" rounds the result to FP32 (the entries a FP32 gather sees)."""
+    each in the order of the recursive steps (butterfly).  Precision "fp64":
+    FP64 arithmetic on the entries of M; "fp32": the entries of M rounded to
+    FP32 and every step of the butterfly rounded to FP32 (the fast product
+    carried out in the arithmetic of an FP32 stored matrix)."""
 
     def __init__(self, src, d, perm_rows, sign_rows, perm_cols, sign_cols, precision="fp64"):
         self.src, self.d = src, int(d)
@@ -648,14 +653,13 @@ class Preprocessed:
         bc, oc = np.divmod(self.pc[cols], self.sn)
         ci = np.arange(D)[:, None] * self.sn + oc[None, :]          # D x len(cols): q s_n + o_j
         out = np.zeros((len(rows), len(cols)))
+        dt = np.float32 if self.precision == "fp32" else np.float64
         for a, i in enumerate(rows):
             br, orow = divmod(int(self.pr[i]), self.sm)
             X = np.stack([self.src.block([p * self.sm + orow], ci.ravel()).reshape(ci.shape)
-                          for p in range(D)])                       # X[p, q, c]
+                          for p in range(D)]).astype(dt)            # X[p, q, c]
             inner = butterfly(X, br, self.d)                         # (F M)[., q s_n + o_j]
-            out[a] = self.sr[i] * self.sc[cols] * butterfly(inner, bc, self.d)
-        if self.precision == "fp32":
-            out = out.astype(np.float32).astype(np.float64)
+            out[a] = self.sr[i] * self.sc[cols] * butterfly(inner, bc, self.d).astype(np.float64)
         return out
 
 

@@ -734,6 +734,32 @@ def test_butterfly_is_the_fast_walsh_transform_in_recursion_order():
     # b = 1: ((x0 - x1) + (x2 - x3)) = 1e16 + (-1e16) = 0; b = 3: (x0 - x1) - (x2 - x3) = 2e16
     assert O.butterfly(v, 1, 2) == 0.0
     assert O.butterfly(v, 3, 2) == 2e16
+    # FP32 arithmetic, every step rounded to FP32 (spacing 8 at 1e8):
+    # (1e8 + 1) + (-1e8 + 1) = 1e8 + (-1e8) = 0, left to right it is 1
+    w = np.array([1e8, 1.0, -1e8, 1.0], np.float32)
+    r = O.butterfly(w, 0, 2)
+    assert r.dtype == np.float32 and r == 0.0
+    assert float(np.float32(np.float32(np.float32(w[0] + w[1]) + w[2]) + w[3])) == 1.0
+
+
+def test_fp32_preprocessed_entries_round_every_step():
+    """Precision "fp32": entries of M rounded to FP32, every butterfly step
+    rounded to FP32; on small integers it is exact and equals the FP64 form."""
+    m, n, d = 24, 16, 3
+    A = W.rng_for(1365).integers(-50, 51, size=(m, n)).astype(np.float64)
+    pre64, _, _ = _pre_case(1366, m, n, d, A)
+    pre32 = O.Preprocessed(O.Dense(A), d, pre64.pr, pre64.sr, pre64.pc, pre64.sc, precision="fp32")
+    np.testing.assert_array_equal(pre32.block(np.arange(m), np.arange(n)), pre64.block(np.arange(m), np.arange(n)))
+    # one entry worked by hand: d = 2, m = n = 4 (blocks of one row and one
+    # column), M's first column (1e8, 1, -1e8, 1), the rest zero; entry
+    # (0, 0) is the butterfly of that column (the other column blocks add 0)
+    B = np.zeros((4, 4))
+    B[:, 0] = [1e8, 1.0, -1e8, 1.0]
+    ident = (np.arange(4), np.ones(4), np.arange(4), np.ones(4))
+    p32 = O.Preprocessed(O.Dense(B), 2, *ident, precision="fp32")
+    assert p32.block([0], [0])[0, 0] == 0.0
+    p64 = O.Preprocessed(O.Dense(B), 2, *ident)
+    assert p64.block([0], [0])[0, 0] == 2.0
 
 
 def test_recovered_lra_error_is_the_preprocessed_error_over_2_to_d():
