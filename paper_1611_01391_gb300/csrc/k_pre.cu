@@ -1,11 +1,14 @@
 // Pre-processing with abridged Hadamard multipliers (Section 8.1, family
 // (i)) and recovery of the LRA of M from an LRA of M_bar = F M H (Section
-// 6.6).  All sums over the 2^d terms of H_{2^d} are taken in the order of
+// 6.6).  Every sum over the 2^d terms of H_{2^d} is taken in the order of
 // the recursive steps H_{2s} = [[H_s, H_s], [H_s, -H_s]], lowest bit first
-// (the fast transform's order), in FP64, and rounded once to FP32, so that
-// the materialised M_bar, the entry-by-entry evaluation and the recovery
-// agree bit for bit with one another.
+// (the fast transform's order).  The entries of M_bar are FP32 sums (every
+// step rounded to FP32, the arithmetic of the stored matrix), so that the
+// materialised M_bar and the entry-by-entry evaluation agree bit for bit;
+// the recovered factors are FP64 sums rounded once to FP32.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "lra_internal.cuh"
 #include "lra_kernels.h"
@@ -17,81 +20,140 @@ namespace {
 // (x[i], x[i + h]) (bit log2 h of i clear) becomes (x[i] + x[i + h],
 // x[i] - x[i + h]) -- the merges of butterfly_push, all outputs at once.
 template <int LD>
-__device__ __forceinline__ void fwht(double (&x)[1 << LD]) {
+__device__ __forceinline__ void fwht(float (&x)[1 << LD]) {
 #pragma unroll
   for (int h = 1; h < (1 << LD); h <<= 1) {
 #pragma unroll
     for (int i = 0; i < (1 << LD); ++i) {
       if (i & h) continue;
-      const double u = x[i], v = x[i + h];
-      x[i] = u + v;
-      x[i + h] = u - v;
+      const float u = x[i], v = x[i + h];
+      x[i] = __fadd_rn(u, v);
+      x[i + h] = __fsub_rn(u, v);
     }
   }
 }
+
+template <int V> struct VecOf;
+template <> struct VecOf<1> { using T = float; };
+template <> struct VecOf<2> { using T = float2; };
+template <> struct VecOf<4> { using T = float4; };
+
+template <int V>
+__device__ __forceinline__ void vload(const float* p, float* out) {
+  const typename VecOf<V>::T v = __ldg(reinterpret_cast<const typename VecOf<V>::T*>(p));
+  *reinterpret_cast<typename VecOf<V>::T*>(out) = v;
+}
+
+template <int V>
+__device__ __forceinline__ void vstore(float* p, const float* in) {
+  *reinterpret_cast<typename VecOf<V>::T*>(p) = *reinterpret_cast<const typename VecOf<V>::T*>(in);
+}
+
+constexpr int kMatThreads = 256;
 
 // G = H_{m,d} M H_{n,d}.  With M viewed as M[p][o_r][q][o_c] (p, q < 2^d,
 // o_r < sm, o_c < sn), G[p'][o_r][q'][o_c] is the 2-D transform over (p, q).
-// One work item: one o_r and W consecutive o_c, i.e. the 2^d x 2^d x W
-// entries M[p sm + o_r][q sn + o_c]; each is read once and written once.
-// Phase 1, thread (q, c): the 2^d entries along p in registers, F applied
-// (the transform over p), into shared memory; phase 2, thread (p', c): the
-// 2^d values along q, H applied, rounded to FP32 and stored.  Threads of a
-// warp share q (phase 1) or p' (phase 2) and run along o_c, so every global
-// access is a run of W consecutive floats.
-template <int LD>
-__global__ void __launch_bounds__(512, 1)
+// One work item: one o_r and W = (256 / 2^d) V consecutive o_c, i.e. the
+// 2^d x 2^d x W entries M[p sm + o_r][q sn + o_c]; each is read once and
+// written once.  Phase 1, thread (q, c): V adjacent columns of the 2^d
+// entries along p in registers, F applied (the transform over p), into
+// shared memory; phase 2, thread (p', c): the 2^d values along q, H applied,
+// stored.  Threads of a warp share q (phase 1) or p' (phase 2) and run along
+// o_c, so every global access is a run of W consecutive floats.
+template <int LD, int V>
+__global__ void __launch_bounds__(kMatThreads)
     pre_materialize_kernel(const float* __restrict__ M, long long lda, float* __restrict__ G, long long ldg,
-                           long long sm, long long sn, int W, long long n_items) {
+                           long long sm, long long sn, long long n_items) {
   constexpr int D = 1 << LD;
-  extern __shared__ double T[];   // T[p][q][c], D * D * W
-  const int c = threadIdx.x % W, g = threadIdx.x / W;
+  constexpr int CT = kMatThreads / D;   // column threads per item
+  constexpr int W = CT * V;             // columns per item
+  extern __shared__ __align__(16) float T[];   // T[p][q][W]
+  const int c = threadIdx.x % CT, g = threadIdx.x / CT;
   const long long chunks = (sn + W - 1) / W;
   for (long long it = blockIdx.x; it < n_items; it += gridDim.x) {
     const long long orow = it / chunks;
-    const long long oc = (it - orow * chunks) * W + c;
-    const bool ok = oc < sn;
-    double x[D];
-    const float* src = M + orow * lda + (long long)g * sn + oc;
+    const long long oc = (it - orow * chunks) * W + (long long)c * V;
+    const bool ok = oc < sn;   // V divides sn: a vector is wholly in or out
+    float x[V][D];
+    if (ok) {
+      const float* src = M + orow * lda + (long long)g * sn + oc;
 #pragma unroll
-    for (int p = 0; p < D; ++p) x[p] = ok ? (double)__ldg(src + (long long)p * sm * lda) : 0.0;
-    fwht<LD>(x);
+      for (int p = 0; p < D; ++p) {
+        float t[V];
+        vload<V>(src + (long long)p * sm * lda, t);
 #pragma unroll
-    for (int p = 0; p < D; ++p) T[(p * D + g) * W + c] = x[p];
+        for (int v = 0; v < V; ++v) x[v][p] = t[v];
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+#pragma unroll
+        for (int p = 0; p < D; ++p) x[v][p] = 0.0f;
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) fwht<LD>(x[v]);
+#pragma unroll
+    for (int p = 0; p < D; ++p) {
+      float t[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) t[v] = x[v][p];
+      vstore<V>(T + (p * D + g) * W + c * V, t);
+    }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < D; ++q) x[q] = T[(g * D + q) * W + c];
-    fwht<LD>(x);
+    for (int q = 0; q < D; ++q) {
+      float t[V];
+      *reinterpret_cast<typename VecOf<V>::T*>(t) =
+          *reinterpret_cast<const typename VecOf<V>::T*>(T + (g * D + q) * W + c * V);
+#pragma unroll
+      for (int v = 0; v < V; ++v) x[v][q] = t[v];
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) fwht<LD>(x[v]);
     if (ok) {
       float* dst = G + ((long long)g * sm + orow) * ldg + oc;
 #pragma unroll
-      for (int q = 0; q < D; ++q) dst[(long long)q * sn] = __double2float_rn(x[q]);
+      for (int q = 0; q < D; ++q) {
+        float t[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) t[v] = x[v][q];
+        vstore<V>(dst + (long long)q * sn, t);
+      }
     }
     __syncthreads();
   }
 }
 
-template <int LD>
-cudaError_t launch_materialize_d(const float* M, long long lda, float* G, long long ldg, long long m, long long n,
+template <int LD, int V>
+cudaError_t launch_materialize_v(const float* M, long long lda, float* G, long long ldg, long long m, long long n,
                                  cudaStream_t st) {
   constexpr int D = 1 << LD;
+  constexpr int W = (kMatThreads / D) * V;
   const long long sm = m >> LD, sn = n >> LD;
-  int W = 512 / D;
-  while (W > 1 && W / 2 >= sn) W /= 2;   // no wider than the column offsets need
-  const int threads = D * W;
-  const size_t smem = sizeof(double) * D * D * W;
-  cudaError_t e = cudaFuncSetAttribute(pre_materialize_kernel<LD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  const size_t smem = sizeof(float) * D * D * W;
+  const void* fn = reinterpret_cast<const void*>(pre_materialize_kernel<LD, V>);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e) return e;
   int dev = 0, sms = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pre_materialize_kernel<LD>, threads, smem)))
-    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kMatThreads, smem))) return e;
   const long long items = sm * ((sn + W - 1) / W);
   const long long grid = std::min<long long>(items, (long long)sms * std::max(per_sm, 1));
-  void* args[] = {(void*)&M, (void*)&lda, (void*)&G, (void*)&ldg, (void*)&sm, (void*)&sn, (void*)&W, (void*)&items};
-  return cudaLaunchKernel(reinterpret_cast<const void*>(pre_materialize_kernel<LD>), dim3((unsigned)grid),
-                          dim3(threads), args, smem, st);
+  void* args[] = {(void*)&M, (void*)&lda, (void*)&G, (void*)&ldg, (void*)&sm, (void*)&sn, (void*)&items};
+  return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kMatThreads), args, smem, st);
+}
+
+// V = min(4, 64 / 2^d) adjacent columns per thread where the pointers, the
+// strides and the column offset sn allow vectors of V floats; else V = 1.
+template <int LD>
+cudaError_t launch_materialize_d(const float* M, long long lda, float* G, long long ldg, long long m, long long n,
+                                 cudaStream_t st) {
+  constexpr int VM = (64 >> LD) < 4 ? (64 >> LD) : 4;
+  const long long sn = n >> LD;
+  const bool vec = ((uintptr_t)M % (4 * VM)) == 0 && ((uintptr_t)G % (4 * VM)) == 0 && lda % VM == 0 &&
+                   ldg % VM == 0 && sn % VM == 0;
+  return vec ? launch_materialize_v<LD, VM>(M, lda, G, ldg, m, n, st)
+             : launch_materialize_v<LD, 1>(M, lda, G, ldg, m, n, st);
 }
 
 __global__ void invert_perm_kernel(const int* __restrict__ perm, long long n, int* __restrict__ inv) {

@@ -52,14 +52,21 @@ __device__ __forceinline__ float dist2(const SourceDev& s, long long i, long lon
 // H_{2s} = [[H_s, H_s], [H_s, -H_s]].  One entry b of that product, summed
 // in the same order as the fast transform: the terms t = 0, 1, ... arrive
 // in order and are merged like a binary counter, the merge at level k being
-// left + right, or left - right when bit k of b is 1.  After term 2^d - 1
-// the returned value is the entry.  stk holds d + 1 partial sums.
+// left + right, or left - right when bit k of b is 1, each rounded in T.
+// After term 2^d - 1 the returned value is the entry.  stk holds d + 1
+// partial sums.
 constexpr int kMaxPreD = 10;
 
-__device__ __forceinline__ double butterfly_push(double* stk, int t, double v, unsigned b) {
+__device__ __forceinline__ float bfly_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float bfly_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double bfly_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double bfly_sub(double a, double b) { return __dsub_rn(a, b); }
+
+template <typename T>
+__device__ __forceinline__ T butterfly_push(T* stk, int t, T v, unsigned b) {
   int k = 0;
   while ((t >> k) & 1) {
-    v = ((b >> k) & 1u) ? stk[k] - v : stk[k] + v;
+    v = ((b >> k) & 1u) ? bfly_sub(stk[k], v) : bfly_add(stk[k], v);
     ++k;
   }
   stk[k] = v;
@@ -82,7 +89,7 @@ __device__ __forceinline__ float entry(const SourceDev& s, long long i, long lon
     // M_bar[i][j] = sr[i] sc[j] (H_{m,d} M H_{n,d})[pr[i]][pc[j]]: with
     // (bi, oi) = divmod(pr[i], sm), (bj, oj) = divmod(pc[j], sn), the sum
     // over q (signs by bj) of the sums over p (signs by bi) of
-    // M[p sm + oi][q sn + oj], each in the butterfly order, FP64, then FP32.
+    // M[p sm + oi][q sn + oj], each in the butterfly order, in FP32.
     long long xi = __ldg(s.pre_pr + i), yj = __ldg(s.pre_pc + j);
     // a caller's array that is not a permutation cannot move a read outside M
     if ((unsigned long long)xi >= (unsigned long long)s.m) xi = 0;
@@ -93,16 +100,16 @@ __device__ __forceinline__ float entry(const SourceDev& s, long long i, long lon
     const long long bi = xi / s.pre_sm, oi = xi - bi * s.pre_sm;
     const long long bj = yj / s.pre_sn, oj = yj - bj * s.pre_sn;
     const int D = 1 << s.pre_d;
-    double so[kMaxPreD + 1], si[kMaxPreD + 1];
-    double acc = 0.0;
+    float so[kMaxPreD + 1], si[kMaxPreD + 1];
+    float acc = 0.0f;
     for (int qq = 0; qq < D; ++qq) {
       const float* col = a + oi * s.lda + qq * s.pre_sn + oj;
-      double inner = 0.0;
+      float inner = 0.0f;
       for (int pp = 0; pp < D; ++pp)
-        inner = butterfly_push(si, pp, (double)__ldg(col + pp * s.pre_sm * s.lda), (unsigned)bi);
+        inner = butterfly_push(si, pp, __ldg(col + pp * s.pre_sm * s.lda), (unsigned)bi);
       acc = butterfly_push(so, qq, inner, (unsigned)bj);
     }
-    return sgn * __double2float_rn(acc);
+    return sgn * acc;
   }
 }
 

@@ -70,7 +70,7 @@ def _gather(src, rows, cols):
     return out.cpu().numpy()
 
 
-@pytest.mark.parametrize("m,n,d,pad", [(96, 80, 1, 0), (200, 136, 3, 5), (64, 96, 5, 0), (1024, 1056, 2, 3),
+@pytest.mark.parametrize("m,n,d,pad", [(96, 80, 1, 0), (200, 136, 3, 5), (64, 96, 5, 0), (1024, 1056, 2, 4), (1000, 1056, 3, 3),
                                        (3008, 2080, 4, 0), (512, 160, 5, 1), (48, 40, 0, 0), (4096, 32, 5, 0)])
 def test_materialized_transform_is_bit_exact(m, n, d, pad):
     """G = H_{m,d} M H_{n,d}: every entry (small cases) or every entry of a
