@@ -785,6 +785,34 @@ def run_preprocess(dev, n=32768, d=3, k=64, reps=5):
                           "paper_tb_fh_mean_context": 3.97e-03}}
 
 
+def run_profile_preprocess(n, d=3, k=64):
+    """Three transforms G = H_{n,d} M H_{n,d} and one C-A solve on the
+    materialised source, nothing else (for ncu)."""
+    import numpy as np
+    import torch
+    import paper_1611_01391_gb300 as L
+    import workloads as W
+    dev = torch.device("cuda:0")
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(W.BASE_SEED + 13000)
+    M = torch.randn((n, k), device=dev, generator=gen) @ torch.randn((k, n), device=dev, generator=gen)
+    M.mul_(1.0 / np.sqrt(k)).add_(torch.randn((n, n), device=dev, generator=gen), alpha=1e-4)
+    G = torch.empty_like(M)
+    pr, sr, pc, sc = [torch.from_numpy(v).to(dev) for v in W.hadamard_multipliers(W.BASE_SEED + 13001, n, n)]
+    pre = L.make_source("preprocessed", a=M, d=d, perm_rows=pr, sign_rows=sr, perm_cols=pc, sign_cols=sc)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    for _ in range(3):
+        L.lra_preprocess_materialize(pre, G, st)
+    torch.cuda.synchronize(dev)
+    mat = L.make_source("preprocessed", a=G, d=d, perm_rows=pr, sign_rows=sr, perm_cols=pc, sign_cols=sc,
+                        materialized=True)
+    ctx = L.Context(0)
+    p, keep = L.make_params(k, k, 3, W.draw_indices(W.BASE_SEED + 13002, n, k))
+    res = ctx.solve(mat, p, k)
+    ctx.close()
+    print(json.dumps({"profile_preprocess": n, "d": d, "status": res.info.status}))
+
+
 # ---------------------------------------------------------------------------
 # batched form: many far-field blocks in one persistent launch
 # ---------------------------------------------------------------------------
@@ -1264,6 +1292,9 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cauchy65536")
     ap.add_argument("--profile-solves", type=int, default=0,
                     help="run this many solves and exit (the command ncu captures)")
+    ap.add_argument("--profile-preprocess", type=int, default=0, metavar="N",
+                    help="run the one-pass Hadamard transform (d = 3) of a stored N x N matrix "
+                         "three times, solve once on the materialised source, and exit (the command ncu captures)")
     ap.add_argument("--no-legs", action="store_true",
                     help="default workload only: skip the batched and served legs")
     args = ap.parse_args()
@@ -1274,6 +1305,9 @@ def main():
     os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     if args.profile_solves:
         run_profile_solves(args, args.workload)
+        return
+    if args.profile_preprocess:
+        run_profile_preprocess(args.profile_preprocess)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
