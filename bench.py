@@ -769,7 +769,10 @@ def run_preprocess(dev, n=32768, d=3, k=64, reps=5):
     sv = np.linalg.svd(A64, compute_uv=False)
     del M, G
     torch.cuda.empty_cache()
-    return {"materialize": {"ms": ms_mean, "ms_each": ms, "algorithmic_bytes": bytes_, "achieved_gbs": gbs,
+    return {"materialize": {"bound": "hbm", "ms": ms_mean, "ms_each": ms, "algorithmic_bytes": bytes_,
+                            "achieved_gbs": gbs,
+                            "traffic": (captured_traffic("k_pre.cu", "pre_materialize_dense16384.md")
+                                        if (n, d) == (32768, 3) else None),
                             "peak_gbs": peak, "frac": gbs / peak if peak else None,
                             "peak_source": f"{peak_kind} HBM copy bandwidth (hbm_gbs)",
                             "config": f"G = H_(n,{d}) M H_(n,{d}), n = {n}, FP32 (8 B per entry)"},
