@@ -40,9 +40,10 @@ __device__ __forceinline__ unsigned long long pivot_word(dd v, int r) {
 // NT = blockDim.x: each thread keeps the coordinates of its <= ceil(96^2 /
 // NT) entries in registers for all steps.
 // L > 0: a build for l == L exactly.
-template <int NT, int L = 0>
-__device__ __forceinline__ bool invert_cross(const float* __restrict__ strip, long long si, long long st, int l_arg,
-                                    JobStatus* js, const int* pos, dd* A, const InvScratch& w) {
+// S(g, c): entry c of strip row g (read or evaluated by the caller).
+template <int NT, int L = 0, typename StripF>
+__device__ __forceinline__ bool invert_cross(StripF S, int l_arg, JobStatus* js, const int* pos, dd* A,
+                                             const InvScratch& w) {
   const int l = L > 0 ? L : l_arg;
   constexpr int kPer = (kMaxL * kMaxL + NT - 1) / NT;
   const int ll = l * l;
@@ -59,7 +60,7 @@ __device__ __forceinline__ bool invert_cross(const float* __restrict__ strip, lo
   int bad = 0;
   for (int e = tid; e < ll; e += nthr) {
     const int r = e / l, c = e - r * l;
-    const dd v = dd_make(strip[(long long)pos[r] * si + (long long)c * st]);
+    const dd v = dd_make(S((long long)pos[r], c));
     if (!(fabsf(v.hi) <= FLT_MAX)) bad = 1;
     A[e] = v;
     if (c == 0) atomicMax(w.pkey, pivot_word(v, r));

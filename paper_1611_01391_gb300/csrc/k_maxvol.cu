@@ -73,6 +73,19 @@ __device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
   return v;
 }
 
+// Entry (g, t) of the strip: from memory, or evaluated from the generator
+// source (a.gen, MaxvolArgs); the same FP32 value a gather would store.
+__device__ __forceinline__ float strip_entry(const MaxvolArgs& a, long long g, int t) {
+  if (a.gen == 0) return a.strip[g * a.si + (long long)t * a.st];
+  const long long c = __ldg(a.gen_idx + t);
+  const long long i = a.gen == 1 ? g : c, j = a.gen == 1 ? c : g;
+  switch (a.src.kind) {
+    case LRA_GEN_CAUCHY: return entry<LRA_GEN_CAUCHY>(a.src, i, j);
+    case LRA_GEN_GAUSS: return entry<LRA_GEN_GAUSS>(a.src, i, j);
+    default: return entry<LRA_GEN_INVDIST>(a.src, i, j);
+  }
+}
+
 // What warp 0 decided, for the other warps.
 struct Ctl {
   long long istar;
@@ -127,7 +140,7 @@ __device__ __forceinline__ void warm_rows(const MaxvolArgs& a, const int l, dd* 
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const int t = gl + GS * c;
-        if (t < l) brow[t] = dd_make(a.strip[g * a.si + (long long)t * a.st]);
+        if (t < l) brow[t] = dd_make(strip_entry(a, g, t));
       }
     __syncwarp();
     dacc acc[NC];
@@ -263,13 +276,15 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
   if (a.gepp) {
     for (int e = tid; e < nrows * l; e += nthr) {
       const int r = e / l, t = e - r * l;
-      B[e] = dd_make(a.strip[(row0 + r) * a.si + (long long)t * a.st]);
+      B[e] = dd_make(strip_entry(a, row0 + r, t));
     }
   } else {
     if constexpr (kSelf) {
       // the two-phase elimination: inside this launch it measured faster
       // than the look-ahead form at l = 24
-      if (!invert_cross<kMaxvolThreads, L>(a.strip, a.si, a.st, l, a.js, pos_s, xs, inv)) return;
+      if (!invert_cross<kMaxvolThreads, L>([&](long long g, int c) { return strip_entry(a, g, c); }, l, a.js,
+                                           pos_s, xs, inv))
+        return;
       warm_rows<GS, NC>(a, l, B, nrows, row0, SharedXMapped{xs, inv.at});
     } else if (a.stage_xinv) {
       for (int e = tid; e < l * l; e += nthr) {

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include "lra_internal.cuh"
+
 struct lra_ctx;
 
 namespace lra {
@@ -62,6 +64,13 @@ struct MaxvolArgs {
   int self_inverse; // warm start: every CTA inverts S[pos, :] itself (xin unused);
                     // needs a plan with stage_xinv
   int count_sweep;  // the last half-step of a sweep: count it in js->sweeps_done
+  // gen != 0: the strip is not in memory; its entries are evaluated from a
+  // generator source (Cauchy, Gaussian or inverse-distance kernel): gen = 1,
+  // S[i][t] = M(i, gen_idx[t]) (vertical strip); gen = 2, S[i][t] =
+  // M(gen_idx[t], i) (horizontal strip, i.e. R^T)
+  int gen;
+  const int* gen_idx;
+  SourceDev src;
 };
 
 struct MaxvolPlan {

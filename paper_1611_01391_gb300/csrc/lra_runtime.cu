@@ -386,6 +386,19 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
   const bool self_row = !one_sm && j->plan_row.stage_xinv;
   col.self_inverse = self_col;
   row.self_inverse = self_row;
+  // generator sources, one stream, no per-sweep tolerance test: the maxvol
+  // launches evaluate their strips themselves (no gather launches and no
+  // strip in HBM between half-steps); C and R are gathered once at the end
+  const bool gen = j->src.kind >= LRA_GEN_CAUCHY && j->src.kind <= LRA_GEN_INVDIST && j->tol == 0.0 &&
+                   self_col && self_row;
+  if (gen) {
+    col.gen = 1;
+    col.gen_idx = j->J;
+    col.src = j->src;
+    row.gen = 2;
+    row.gen_idx = j->I;
+    row.src = j->src;
+  }
   // C = M[:, J]: through TMA tiles for a stored FP32 matrix, else entry by entry
   auto gather_c = [&](int skip_on_stop) -> cudaError_t {
     cudaError_t r = j->tma_cols
@@ -395,7 +408,7 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
   };
   if ((e = cudaEventRecord(j->ev_start, st))) return e;
   for (int sw = 0; sw < j->sweeps; ++sw) {
-    if ((e = gather_c(1))) return e;
+    if (!gen && (e = gather_c(1))) return e;
     // the very first vertical step starts from Gaussian elimination, unless
     // the caller resumes from its own row set (init_I): then it is a warm
     // start like every later one
@@ -407,7 +420,9 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
           (e = after(kClsInverse, 1))) return e;
     }
     if ((e = launch_maxvol(col, j->plan_col, st)) || (e = after(kClsMaxvol, 1))) return e;
-    if ((e = launch_gather_rows(j->src, j->I, j->l, j->R, j->js, ctx->sms, st)) || (e = after(kClsGather, 1))) return e;
+    if (!gen &&
+        ((e = launch_gather_rows(j->src, j->I, j->l, j->R, j->js, ctx->sms, st)) || (e = after(kClsGather, 1))))
+      return e;
     row.gepp = 0;
     row.half_step = 2 * sw + 1;
     row.xin = j->xbuf1;   // inverse of A[I, J]^T (horizontal strip's cross)
@@ -424,8 +439,12 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
       if ((e = launch_tol_check(j->js, j->tol, st)) || (e = after(kClsOther, 1))) return e;
     }
   }
-  // final strips for the returned CUR: C = M[:, J] (R = M[I, :] is current)
+  // final strips for the returned CUR: C = M[:, J] (R = M[I, :] is current,
+  // unless the strips were evaluated inside the maxvol launches)
   if ((e = gather_c(0))) return e;
+  if (gen &&
+      ((e = launch_gather_rows(j->src, j->I, j->l, j->R, j->js, ctx->sms, st)) || (e = after(kClsGather, 1))))
+    return e;
   if ((e = launch_nucleus(j->C, j->I, j->l, j->k, j->rank_tol, j->U, j->sigma, j->js, st)) || (e = after(kClsCross, 1))) return e;
   if (j->full_res) {
     if ((e = launch_full_residual(static_cast<const float*>(j->src.a), j->src.lda, j->m, j->n, j->l, j->C,
