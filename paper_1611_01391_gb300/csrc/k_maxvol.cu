@@ -73,17 +73,38 @@ __device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
   return v;
 }
 
-// Entry (g, t) of the strip: from memory, or evaluated from the generator
-// source (a.gen, MaxvolArgs); the same FP32 value a gather would store.
-__device__ __forceinline__ float strip_entry(const MaxvolArgs& a, long long g, int t) {
-  if (a.gen == 0) return a.strip[g * a.si + (long long)t * a.st];
-  const long long c = __ldg(a.gen_idx + t);
-  const long long i = a.gen == 1 ? g : c, j = a.gen == 1 ? c : g;
-  switch (a.src.kind) {
-    case LRA_GEN_CAUCHY: return entry<LRA_GEN_CAUCHY>(a.src, i, j);
-    case LRA_GEN_GAUSS: return entry<LRA_GEN_GAUSS>(a.src, i, j);
-    default: return entry<LRA_GEN_INVDIST>(a.src, i, j);
+// The generator's entry from the coordinates of its two points (xp on the
+// x side, yq on the y side): the operations of entry<KIND>, in order.
+__device__ __forceinline__ float gen_eval(const SourceDev& s, const float* xp, const float* yq) {
+  if (s.kind == LRA_GEN_CAUCHY) return __fdiv_rn(1.0f, __fsub_rn(xp[0], yq[0]));
+  float d = __fsub_rn(xp[0], yq[0]);
+  float acc = __fmul_rn(d, d);
+  if (s.dim > 1) {
+    d = __fsub_rn(xp[1], yq[1]);
+    acc = __fadd_rn(acc, __fmul_rn(d, d));
   }
+  if (s.dim > 2) {
+    d = __fsub_rn(xp[2], yq[2]);
+    acc = __fadd_rn(acc, __fmul_rn(d, d));
+  }
+  if (s.kind == LRA_GEN_GAUSS) return expf(-__fdiv_rn(acc, s.h2));
+  return __fdiv_rn(1.0f, __fsqrt_rn(acc));
+}
+
+// Generated strips: the points of the strip's l columns (y[gen_idx[t]] for
+// a vertical strip, x[gen_idx[t]] for a horizontal one), 3 floats each, in
+// shared memory; entry (g, t) pairs them with the point of row g.
+__device__ __forceinline__ float gen_strip_entry(const MaxvolArgs& a, const float* colpt, const float* rowpt,
+                                                 int t) {
+  const float* cp = colpt + 3 * t;
+  return a.gen == 1 ? gen_eval(a.src, rowpt, cp) : gen_eval(a.src, cp, rowpt);
+}
+
+__device__ __forceinline__ void load_row_point(const MaxvolArgs& a, long long g, float* rowpt) {
+  const float* p = (a.gen == 1 ? a.src.x : a.src.y) + g * a.src.dim;
+  rowpt[0] = __ldg(p);
+  rowpt[1] = a.src.dim > 1 ? __ldg(p + 1) : 0.0f;
+  rowpt[2] = a.src.dim > 2 ? __ldg(p + 2) : 0.0f;
 }
 
 // What warp 0 decided, for the other warps.
@@ -126,7 +147,7 @@ __device__ __forceinline__ int grid_arrive_wait(unsigned int* count, unsigned in
 // (NC = ceil(l / GS) exactly).
 template <int GS, int NC, typename XPtr>
 __device__ __forceinline__ void warm_rows(const MaxvolArgs& a, const int l, dd* B, int nrows, long long row0,
-                                          XPtr X) {
+                                          XPtr X, const float* colpt) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   constexpr int kGpw = 32 / GS;
   const int gl = lane % GS;
@@ -136,12 +157,23 @@ __device__ __forceinline__ void warm_rows(const MaxvolArgs& a, const int l, dd* 
     const bool active = r < nrows;
     const long long g = row0 + r;
     dd* brow = B + (size_t)r * l;
-    if (active)
+    if (active) {
+      if (a.gen) {
+        float rowpt[3];
+        load_row_point(a, g, rowpt);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const int t = gl + GS * c;
-        if (t < l) brow[t] = dd_make(strip_entry(a, g, t));
+        for (int c = 0; c < NC; ++c) {
+          const int t = gl + GS * c;
+          if (t < l) brow[t] = dd_make(gen_strip_entry(a, colpt, rowpt, t));
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const int t = gl + GS * c;
+          if (t < l) brow[t] = dd_make(a.strip[g * a.si + (long long)t * a.st]);
+        }
       }
+    }
     __syncwarp();
     dacc acc[NC];
     int qc[NC];   // the lane's columns, as stored in X
@@ -253,7 +285,8 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
   inv.swaps = reinterpret_cast<int*>(inv.pkey + 2);
   inv.at = inv.swaps + kMaxL;
   inv.p_s = inv.at + kMaxL;
-  unsigned char* used = reinterpret_cast<unsigned char*>(inv.p_s + 2);  // rpc
+  float* colpt = reinterpret_cast<float*>(inv.p_s + 2);     // 3 * kMaxL: generated strips' column points
+  unsigned char* used = reinterpret_cast<unsigned char*>(colpt + 3 * kMaxL);  // rpc
   dd* cand_rows = reinterpret_cast<dd*>(a.cand_rows);
 
   const int lane = tid & 31, warp = tid >> 5;
@@ -262,6 +295,12 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
   const int ngroups = (nthr >> 5) * kGpw;
 
   for (int t = tid; t < l; t += nthr) pos_s[t] = a.gepp ? -1 : a.pos[t];
+  if (a.gen)
+    for (int e = tid; e < l * a.src.dim; e += nthr) {
+      const int t = e / a.src.dim, c = e - t * a.src.dim;
+      const float* pts = a.gen == 1 ? a.src.y : a.src.x;
+      colpt[3 * t + c] = __ldg(pts + (long long)__ldg(a.gen_idx + t) * a.src.dim + c);
+    }
   for (int r = tid; r < nrows; r += nthr) used[r] = 0;
   if (tid < 2) red[tid] = 0ull;
   if (tid == 0) {
@@ -276,25 +315,31 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
   if (a.gepp) {
     for (int e = tid; e < nrows * l; e += nthr) {
       const int r = e / l, t = e - r * l;
-      B[e] = dd_make(strip_entry(a, row0 + r, t));
+      float rowpt[3];
+      if (a.gen) load_row_point(a, row0 + r, rowpt);
+      B[e] = dd_make(a.gen ? gen_strip_entry(a, colpt, rowpt, t) : a.strip[(row0 + r) * a.si + (long long)t * a.st]);
     }
   } else {
     if constexpr (kSelf) {
       // the two-phase elimination: inside this launch it measured faster
       // than the look-ahead form at l = 24
-      if (!invert_cross<kMaxvolThreads, L>([&](long long g, int c) { return strip_entry(a, g, c); }, l, a.js,
-                                           pos_s, xs, inv))
-        return;
-      warm_rows<GS, NC>(a, l, B, nrows, row0, SharedXMapped{xs, inv.at});
+      const auto S = [&](long long g, int c) -> float {
+        if (!a.gen) return a.strip[g * a.si + (long long)c * a.st];
+        float rowpt[3];
+        load_row_point(a, g, rowpt);
+        return gen_strip_entry(a, colpt, rowpt, c);
+      };
+      if (!invert_cross<kMaxvolThreads, L>(S, l, a.js, pos_s, xs, inv)) return;
+      warm_rows<GS, NC>(a, l, B, nrows, row0, SharedXMapped{xs, inv.at}, colpt);
     } else if (a.stage_xinv) {
       for (int e = tid; e < l * l; e += nthr) {
         const float2 v = a.xin[e];
         xs[e] = dd{v.x, v.y};
       }
       __syncthreads();
-      warm_rows<GS, NC>(a, l, B, nrows, row0, SharedX{xs});
+      warm_rows<GS, NC>(a, l, B, nrows, row0, SharedX{xs}, colpt);
     } else {
-      warm_rows<GS, NC>(a, l, B, nrows, row0, GlobalX{a.xin});
+      warm_rows<GS, NC>(a, l, B, nrows, row0, GlobalX{a.xin}, colpt);
     }
     __syncthreads();
     // rows currently selected are exactly the unit vectors of B = S X^{-1}
@@ -524,7 +569,7 @@ static size_t maxvol_smem(int rpc, int l, bool stage_xinv) {
              (stage_xinv ? (size_t)l * l * sizeof(dd) : 0) +
              2 * sizeof(unsigned long long) + sizeof(Ctl) + kMaxL * sizeof(int) +
              2 * kMaxL * sizeof(dd) + 2 * sizeof(unsigned long long) + (2 * kMaxL + 2) * sizeof(int) +
-             (size_t)rpc;
+             3 * kMaxL * sizeof(float) + (size_t)rpc;
   return (b + 15) & ~(size_t)15;
 }
 
