@@ -44,8 +44,8 @@ __global__ void __launch_bounds__(256) gather_cols_kernel(SourceDev s, const int
 template <int KIND>
 __global__ void __launch_bounds__(256) gather_rows_kernel(SourceDev s, const int* __restrict__ I,
                                                           int l, float* __restrict__ R,
-                                                          const JobStatus* js, int vec_ok) {
-  if (js->status != LRA_OK || js->stop) return;
+                                                          const JobStatus* js, int vec_ok, int skip_on_stop) {
+  if (js->status != LRA_OK || (skip_on_stop && js->stop)) return;
   const long long n = s.n;
   const long long nq = (n + 3) / 4;
   const long long total = nq * l;
@@ -262,13 +262,13 @@ cudaError_t launch_gather_cols(const SourceDev& s, const int* J, int l, float* C
 }
 
 cudaError_t launch_gather_rows(const SourceDev& s, const int* I, int l, float* R,
-                               const JobStatus* js, int sms, cudaStream_t st) {
+                               const JobStatus* js, int sms, cudaStream_t st, int skip_on_stop) {
   const long long nq = (s.n + 3) / 4;
   const int grid = grid_for(nq * l, 256 * 2, sms);
   int vec_ok = (s.n % 4 == 0) && ((reinterpret_cast<uintptr_t>(R) & 15) == 0);
   if (s.kind == LRA_DENSE_F32)
     vec_ok = vec_ok && (s.lda % 4 == 0) && ((reinterpret_cast<uintptr_t>(s.a) & 15) == 0);
-  LRA_DISPATCH_KIND_ALL(s.kind, (gather_rows_kernel<K><<<grid, 256, 0, st>>>(s, I, l, R, js, vec_ok)));
+  LRA_DISPATCH_KIND_ALL(s.kind, (gather_rows_kernel<K><<<grid, 256, 0, st>>>(s, I, l, R, js, vec_ok, skip_on_stop)));
   return cudaGetLastError();
 }
 

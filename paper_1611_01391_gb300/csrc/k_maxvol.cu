@@ -464,6 +464,12 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
           a.trace_v[n] = wv;
           a.js->trace_len = n + 1;
         }
+        if (kind == LRA_TRACE_STOP) {
+          const int o = a.half_step & 1;
+          a.js->stop_i[o] = (int)istar;
+          a.js->stop_j[o] = jstar;
+          a.js->stop_v[o] = wv;
+        }
       }
       if (kind == LRA_TRACE_GEPP || kind == LRA_TRACE_SWAP) {
         // the update's row factor (W[i*, :] - e_j*^T) / W[i*, j*]
@@ -558,6 +564,27 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
     const double init = a.gepp ? 0.0 : 2.0 * (double)N * l * l;
     a.js->maxvol_flops += upd + init;
     if (a.count_sweep) a.js->sweeps_done += 1;
+    if (a.fixed_point_exit) {
+      // a warm-started half-step without a swap after another one: the
+      // next half-step has the same strip, index set and cross as the one
+      // before this, so it and all later ones repeat their decisions
+      a.js->noswap_run = (a.gepp || swaps > 0 || capped) ? 0 : a.js->noswap_run + 1;
+      if (a.js->noswap_run >= 2 && a.half_step + 1 < a.total_half_steps) {
+        for (int h = a.half_step + 1; h < a.total_half_steps; ++h) {
+          const int n = a.js->trace_len, o = h & 1;
+          if (n < a.js->trace_cap) {
+            a.trace_i[4 * n + 0] = h;
+            a.trace_i[4 * n + 1] = LRA_TRACE_STOP;
+            a.trace_i[4 * n + 2] = a.js->stop_i[o];
+            a.trace_i[4 * n + 3] = a.js->stop_j[o];
+            a.trace_v[n] = a.js->stop_v[o];
+            a.js->trace_len = n + 1;
+          }
+        }
+        a.js->sweeps_done = a.total_half_steps / 2;
+        a.js->stop = 1;
+      }
+    }
     a.bar->seq = ctl->seq0 + dec + 1;   // the decisions taken, the final stop included
     const unsigned int pad = (256u - ((nbar * (unsigned)G) & 255u)) & 255u;
     if (pad) atomicAdd(&a.bar->count, pad);

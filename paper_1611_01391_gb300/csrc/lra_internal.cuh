@@ -151,6 +151,12 @@ struct JobStatus {
   double sigma_max;
   double maxvol_flops;
   double full_sse, full_ssa, full_rel;
+  // fixed-point exit of a fixed-budget solve: consecutive warm-started
+  // half-steps without a swap, and the last STOP decision of each
+  // orientation (vertical 0, horizontal 1): row, column, |value|
+  int noswap_run;
+  int stop_i[2], stop_j[2];
+  double stop_v[2];
 };
 
 // Batched C-A (many blocks of one source, one launch).

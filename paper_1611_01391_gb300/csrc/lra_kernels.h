@@ -34,7 +34,7 @@ cudaError_t launch_gather_cols_tma(const TmaMap& map, const int* J, int l, long 
 cudaError_t launch_gather_entries(const SourceDev& s, const int* rows, long long q, const int* cols,
                                   long long sN, float* out, cudaStream_t st);
 cudaError_t launch_gather_rows(const SourceDev& s, const int* I, int l, float* R,
-                               const JobStatus* js, int sms, cudaStream_t st);
+                               const JobStatus* js, int sms, cudaStream_t st, int skip_on_stop = 1);
 
 // One maxvol half-step on an N x l FP32 strip whose element (i, t) sits at
 // strip[i*si + t*st].  gepp = 1: Gauss-Jordan elimination with partial
@@ -71,6 +71,13 @@ struct MaxvolArgs {
   int gen;
   const int* gen_idx;
   SourceDev src;
+  // fixed_point_exit: once two warm-started half-steps in a row make no
+  // swap, the iteration is at a fixed point and every later half-step of
+  // the budget (total_half_steps) would repeat the same decisions; the
+  // launch then logs their STOP decisions, counts their sweeps and sets
+  // js->stop, and the later launches return at once
+  int fixed_point_exit;
+  int total_half_steps;
 };
 
 struct MaxvolPlan {

@@ -391,6 +391,9 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
   // strip in HBM between half-steps); C and R are gathered once at the end
   const bool gen = j->src.kind >= LRA_GEN_CAUCHY && j->src.kind <= LRA_GEN_INVDIST && j->tol == 0.0 &&
                    self_col && self_row;
+  // a fixed budget of sweeps: stop at a fixed point of the iteration
+  col.fixed_point_exit = row.fixed_point_exit = j->tol == 0.0;
+  col.total_half_steps = row.total_half_steps = 2 * j->sweeps;
   if (gen) {
     col.gen = 1;
     col.gen_idx = j->J;
@@ -443,7 +446,7 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
   // unless the strips were evaluated inside the maxvol launches)
   if ((e = gather_c(0))) return e;
   if (gen &&
-      ((e = launch_gather_rows(j->src, j->I, j->l, j->R, j->js, ctx->sms, st)) || (e = after(kClsGather, 1))))
+      ((e = launch_gather_rows(j->src, j->I, j->l, j->R, j->js, ctx->sms, st, 0)) || (e = after(kClsGather, 1))))
     return e;
   if ((e = launch_nucleus(j->C, j->I, j->l, j->k, j->rank_tol, j->U, j->sigma, j->js, st)) || (e = after(kClsCross, 1))) return e;
   if (j->full_res) {
