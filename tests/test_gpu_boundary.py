@@ -187,7 +187,11 @@ def test_fetch_of_a_long_job_does_not_block_other_threads():
     A = torch.from_numpy(W.lowrank_svd(W.BASE_SEED + 71).astype(np.float32)).to(DEV)
     small = L.make_source("dense", a=A)
     with L.Context(0, n_streams=2) as c:
-        p_long, k1 = L.make_params(64, 96, 200, W.draw_indices(72, 32768, 96))
+        # a tolerance no estimate reaches keeps the long solve running every
+        # sweep (a fixed budget alone would end it at the fixed point)
+        rr, rc = W.draw_indices(74, 32768, 64, sort=True), W.draw_indices(75, 32768, 64, sort=True)
+        p_long, k1 = L.make_params(64, 96, 60, W.draw_indices(72, 32768, 96), tol=1e-300,
+                                   resid_rows=rr, resid_cols=rc)
         p_small, k2 = L.make_params(8, 8, 1, W.draw_indices(73, 256, 8))
         c.solve(small, p_small, 8)          # warm-up (kernel modules loaded)
         t0 = time.perf_counter()

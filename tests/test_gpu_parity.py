@@ -345,3 +345,23 @@ def test_cancel_stops_a_running_job(ctx):
     again = ctx.solve(src, params, 24)
     assert again.info.status == 0
     np.testing.assert_array_equal(again.I, full.I)
+
+
+def test_fixed_point_exit_keeps_the_whole_log(ctx):
+    """A budget of 12 sweeps on a Cauchy matrix that reaches a fixed point
+    after two or three: the device stops there, and its decision log, index
+    sets, nucleus and sweep count are those of running every half-step (the
+    oracle runs all 24)."""
+    m, n, k, l = 3000, 4000, 12, 16
+    x, y = W.cauchy_points(W.BASE_SEED + 900, m, n)
+    src = L.make_source("cauchy", x=torch.from_numpy(x).to(DEV), y=torch.from_numpy(y).to(DEV))
+    J0 = W.draw_indices(W.BASE_SEED + 901, n, l)
+    res = gpu_solve(ctx, src, m, n, J0, k, l, 12)
+    ref = O.cross_approximation(O.Cauchy(x, y, "fp32"), J0, k=k, sweeps=12, delta=DELTA, rank_tol=GPU_TAU)
+    ncmp, div = compare_traces(res.trace, ref.trace, DELTA)
+    assert div is None and ncmp == len(ref.trace)
+    assert sum(1 for d in ref.trace if d[1] == O.STOP) == 24
+    assert list(res.I) == ref.I and list(res.J) == ref.J
+    assert res.info.sweeps_done == 12
+    assert res.info.swaps_total == sum(1 for d in ref.trace if d[1] == O.SWAP)
+    check_nucleus(res.U, res.sigma, res.info.k_eff, O.Cauchy(x, y, "fp32").block(res.I, res.J), k)
