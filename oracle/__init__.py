@@ -18,6 +18,8 @@ from .ca import (CAP, GEPP, STOP, SWAP, Cauchy, CrossResult, Dense, Gauss,
                  abridged_hadamard, butterfly, aph_left, aph_right, Preprocessed, recover_lra,
                  full_residual, gepp_rows, maxvol, nucleus, random_cross, rows,
                  sampled_residual)
+from .rf_lsr import (RangeFinderFailure, RangeFinderResult, asph_columns, asph_rows, dual_lsr,
+                     lsr_solution, numerical_rank, range_finder, relative_residual)
 
 __all__ = [
     "CAP", "GEPP", "STOP", "SWAP", "Cauchy", "CrossResult", "Dense", "Gauss",
@@ -27,4 +29,6 @@ __all__ = [
     "abridged_hadamard", "butterfly", "aph_left", "aph_right", "Preprocessed", "recover_lra",
     "full_residual", "gepp_rows", "maxvol", "nucleus", "random_cross", "rows",
     "sampled_residual",
+    "RangeFinderFailure", "RangeFinderResult", "asph_columns", "asph_rows", "dual_lsr", "lsr_solution",
+    "numerical_rank", "range_finder", "relative_residual",
 ]

@@ -31,6 +31,12 @@ Workload families (sizes as in the named configurations):
   pre-processing was applied.
 * ``hadamard_multipliers`` -- the random permutations and +-1 scalings of
   the abridged scaled and permuted Hadamard multipliers (Section 8.1).
+* ``lsr_problem``      -- the four input classes of the paper's LSR tests
+  (Section 12, Tables lsrRandom, lsrill, lsrsemi, lsrcoh; recipes after
+  AMT10): Gaussian A; ill-conditioned A = S diag(sigma) T^T with Haar S, T,
+  leading singular values 10^4, 10^3, ..., 10^-9 and the rest 10^-10;
+  semi-coherent A = [G 0; 0 D] with G Gaussian (m - n/2) x n/2 and D a
+  random +-1 diagonal; coherent A = [D_n; 0]; b Gaussian (FP64).
 * ``draw_indices``     -- l distinct indices uniform without replacement:
   the random initial column set of Section 12.2 (Tests 1/2) and the random
   q x s error sample of Appendix F.
@@ -305,3 +311,31 @@ def hadamard_multipliers(seed: int, m: int, n: int):
     pc = rng.permutation(n).astype(np.int32)
     sc = rng.choice(np.array([-1.0, 1.0], np.float32), n)
     return pr, sr, pc, sc
+
+
+def lsr_problem(seed: int, kind: str, m: int, n: int):
+    """(A, b) of one LSR test input (FP64): kind "gaussian", "ill",
+    "semicoherent" or "coherent"."""
+    rng = rng_for(seed)
+    if kind == "gaussian":
+        A = rng.standard_normal((m, n))
+    elif kind == "ill":
+        q, rr = np.linalg.qr(rng.standard_normal((m, n)))
+        S = q * np.sign(np.diag(rr))[None, :]          # Haar on the m x n Stiefel manifold
+        T = haar_orthogonal(rng, n)
+        sig = np.full(n, 1e-10)
+        lead = 10.0 ** np.arange(4, -10, -1)
+        sig[:min(n, lead.size)] = lead[:n]
+        A = (S * sig[None, :]) @ T.T
+    elif kind == "semicoherent":
+        h = n // 2
+        A = np.zeros((m, n))
+        A[:m - h, :h] = rng.standard_normal((m - h, h))
+        A[m - h:, h:] = np.diag(rng.choice([-1.0, 1.0], n - h))
+    elif kind == "coherent":
+        A = np.zeros((m, n))
+        A[:n, :n] = np.diag(rng.choice([-1.0, 1.0], n))
+    else:
+        raise ValueError(kind)
+    b = rng.standard_normal(m)
+    return A, b
