@@ -545,6 +545,71 @@ lra_status lra_draw_columns(uint64_t seed, int64_t n, int32_t l, int32_t* out);
 lra_status lra_gather_entries(const lra_source* src, const int32_t* rows, int64_t q,
                               const int32_t* cols, int64_t s, float* out, void* stream);
 
+/* ---- Algorithm 5.1a: LRA via range finder with a sub-identity multiplier */
+
+typedef struct {
+  int32_t r;                  /* target rank, 1 <= r <= l                              */
+  double rank_tol;            /* numerical rank of Y = M H: R_jj > rank_tol R_00 for the
+                                 pivoted factor (>= 1e-7: the Gram route resolves R_jj
+                                 to about sqrt(2^-53) R_00)                            */
+  int64_t resid_q, resid_s;   /* optional Appendix F sample (0 = none)                  */
+  const int32_t* resid_rows;  /* host, resid_q distinct rows                            */
+  const int32_t* resid_cols;  /* host, resid_s distinct columns                         */
+} lra_rf_params;
+
+typedef struct {
+  float* U;                   /* device, m x r row-major: orthonormal columns           */
+  float* V;                   /* device, r x n row-major: U^T M                         */
+  int32_t* piv;               /* host, l: column order of the pivoted QR of Y (indices
+                                 into J)                                                */
+  int32_t* nrank;             /* host: numerical rank of Y                              */
+  double* est_rel_err;        /* host or NULL: Appendix F estimate of ||M - U V|| / ||M|| */
+  int32_t* gemm_mode;         /* host or NULL: 1 = V on the tensor cores (FP32 emulated
+                                 through BF16 products), 0 = FP32 SIMT                  */
+} lra_rf_out;
+
+/* Algorithm 5.1 (LRA via range finder), variant (a), with the sub-identity
+ * multiplier H = (e_J[0], ..., e_J[l-1]) (Section 3's superfast recipe (i):
+ * Y = M H = M[:, J] involves no flops): Y is gathered, its rank-revealing
+ * QR is computed as pivoted Cholesky of the FP64 Gram matrix Y^T Y (the
+ * pivots of QR with column pivoting in exact arithmetic) followed by a
+ * CholeskyQR2 pass for the orthonormal factor, U = the r leftmost columns,
+ * and V = U^+ M = U^T M by a GEMM over the stored matrix (cuBLAS, FP32
+ * accuracy through BF16 tensor-core products where available).  The LRA of
+ * M is U V.  src: LRA_DENSE_F32 (the GEMM reads M); J: host, l distinct
+ * columns, r <= l <= 96.  Blocking.  LRA_EINVAL for bad sizes, source kind
+ * or index sets; LRA_ESINGULAR (the algorithm's FAILURE) when the numerical
+ * rank of Y is below r, with *nrank and piv set. */
+lra_status lra_range_finder(lra_ctx* ctx, const lra_source* src, const int32_t* J, int32_t l,
+                            const lra_rf_params* params, const lra_rf_out* out);
+
+/* ---- Algorithm 3.1 with a sub-identity multiplier: superfast dual LSR */
+
+typedef struct {
+  int32_t passes;             /* CholeskyQR passes, 1..4 (3 by default)                  */
+  int32_t shifted;            /* nonzero: the first pass factors Y^T Y + s I,
+                                 s = 11 (k (n+1) + (n+1) (n+2)) 2^-53 ||Y||_F^2
+                                 (shifted CholeskyQR3, for ill-conditioned rows)        */
+} lra_lsr_params;
+
+typedef struct {
+  double* x;                  /* host, n: the least squares solution of the k rows      */
+  double* rho;                /* host or NULL: the sampled problem's residual norm      */
+} lra_lsr_out;
+
+/* Problem 3.1 through Algorithm 3.1 with the multiplier F = sqrt(m/k)
+ * (I_k | O) P (Section 3, "Superfast dual LSR": a permutation followed by a
+ * sub-identity matrix, no flops): W = (A | b) is an m x (n+1) stored
+ * matrix (LRA_DENSE_F64 or LRA_DENSE_F32; the last column is b); the k rows
+ * `rows` (host, distinct, n+1 <= k <= m, n+1 <= 1024) are gathered in FP64
+ * and x = argmin ||A[rows] x - b[rows]|| is computed by CholeskyQR
+ * (Fukaya et al.) on the k x (n+1) matrix: (F W) = Q R_p ... R_1, x =
+ * R_nn^{-1} R[:n, n].  The scale sqrt(m/k) does not change x.  Blocking.
+ * LRA_EINVAL for bad sizes or rows; LRA_ESINGULAR when a Cholesky pivot is
+ * not positive (rows too ill conditioned for the passes given). */
+lra_status lra_dual_lsr(lra_ctx* ctx, const lra_source* W, const int32_t* rows, int32_t k,
+                        const lra_lsr_params* params, const lra_lsr_out* out);
+
 /* Static message for a status code. */
 const char* lra_status_str(int32_t status);
 

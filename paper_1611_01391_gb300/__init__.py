@@ -174,6 +174,28 @@ _pre_recover = _sig("lra_preprocessed_recover", ctypes.c_int, ctypes.POINTER(lra
                     ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 _pre_materialize = _sig("lra_preprocess_materialize", ctypes.c_int, ctypes.POINTER(lra_source), ctypes.c_void_p,
                         ctypes.c_int64, ctypes.c_void_p)
+class lra_rf_params(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_int32), ("rank_tol", ctypes.c_double), ("resid_q", ctypes.c_int64),
+                ("resid_s", ctypes.c_int64), ("resid_rows", ctypes.c_void_p), ("resid_cols", ctypes.c_void_p)]
+
+
+class lra_rf_out(ctypes.Structure):
+    _fields_ = [("U", ctypes.c_void_p), ("V", ctypes.c_void_p), ("piv", ctypes.c_void_p), ("nrank", ctypes.c_void_p),
+                ("est_rel_err", ctypes.c_void_p), ("gemm_mode", ctypes.c_void_p)]
+
+
+class lra_lsr_params(ctypes.Structure):
+    _fields_ = [("passes", ctypes.c_int32), ("shifted", ctypes.c_int32)]
+
+
+class lra_lsr_out(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("rho", ctypes.c_void_p)]
+
+
+_range_finder = _sig("lra_range_finder", ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(lra_source), ctypes.c_void_p,
+                     ctypes.c_int32, ctypes.POINTER(lra_rf_params), ctypes.POINTER(lra_rf_out))
+_dual_lsr = _sig("lra_dual_lsr", ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(lra_source), ctypes.c_void_p,
+                 ctypes.c_int32, ctypes.POINTER(lra_lsr_params), ctypes.POINTER(lra_lsr_out))
 _status_str = _sig("lra_status_str", ctypes.c_char_p, ctypes.c_int32)
 _last_error = _sig("lra_cross_last_error", ctypes.c_char_p, _ctx_p)
 
@@ -182,7 +204,7 @@ EXPORTED = ["lra_cross_create", "lra_cross_destroy", "lra_cross_submit", "lra_cr
             "lra_status_str", "lra_cross_last_error", "lra_cross_submit_batch",
             "lra_cross_fetch_batch", "lra_draw_columns", "lra_gather_entries", "lra_maxvol_noalloc",
             "lra_cross_tune_batch", "lra_batch_tuning_lookup", "lra_cross_cynical", "lra_cross_refine",
-            "lra_preprocessed_recover", "lra_preprocess_materialize"]
+            "lra_preprocessed_recover", "lra_preprocess_materialize", "lra_range_finder", "lra_dual_lsr"]
 
 
 class LraError(RuntimeError):
@@ -278,6 +300,46 @@ def lra_maxvol_noalloc(strip_ptr, N, l, row_stride, col_stride, pos_ptr, xinv_pt
     returns the lra_status code."""
     return _maxvol_noalloc(strip_ptr, N, l, row_stride, col_stride, pos_ptr, xinv_ptr, delta, max_swaps,
                            status_ptr, stream)
+
+
+def lra_range_finder(ctx, src: lra_source, J, r: int, U, V, rank_tol: float = 1e-6, resid_rows=None,
+                     resid_cols=None):
+    """Algorithm 5.1a with the sub-identity multiplier e_J: U (m x r) and V
+    (r x n) into the given float32 device tensors.  Returns a dict with piv,
+    nrank, est_rel_err and gemm_mode."""
+    import numpy as np
+    Jh = np.ascontiguousarray(J, dtype=np.int32)
+    p = lra_rf_params(r, rank_tol, 0, 0, None, None)
+    keep = []
+    if resid_rows is not None:
+        rr = np.ascontiguousarray(resid_rows, dtype=np.int32)
+        rc = np.ascontiguousarray(resid_cols, dtype=np.int32)
+        keep += [rr, rc]
+        p.resid_q, p.resid_s, p.resid_rows, p.resid_cols = len(rr), len(rc), rr.ctypes.data, rc.ctypes.data
+    piv = np.zeros(len(Jh), np.int32)
+    nrank = np.zeros(1, np.int32)
+    est = np.zeros(1)
+    mode = np.zeros(1, np.int32)
+    o = lra_rf_out(U.data_ptr(), V.data_ptr(), piv.ctypes.data, nrank.ctypes.data, est.ctypes.data, mode.ctypes.data)
+    code = _range_finder(ctx, ctypes.byref(src), Jh.ctypes.data, len(Jh), ctypes.byref(p), ctypes.byref(o))
+    res = {"piv": piv, "nrank": int(nrank[0]), "est_rel_err": float(est[0]), "gemm_mode": int(mode[0]),
+           "status": int(code)}
+    if code != LRA_OK and code != LRA_ESINGULAR:
+        _check(code, ctx)
+    return res
+
+
+def lra_dual_lsr(ctx, W: lra_source, rows, passes: int = 3, shifted: bool = True):
+    """Algorithm 3.1 with a sub-identity multiplier: x (host FP64, n) and
+    the sampled residual norm for W = (A | b) and the kept rows."""
+    import numpy as np
+    rh = np.ascontiguousarray(rows, dtype=np.int32)
+    x = np.zeros(W.n - 1)
+    rho = np.zeros(1)
+    p = lra_lsr_params(passes, int(bool(shifted)))
+    o = lra_lsr_out(x.ctypes.data, rho.ctypes.data)
+    _check(_dual_lsr(ctx, ctypes.byref(W), rh.ctypes.data, len(rh), ctypes.byref(p), ctypes.byref(o)), ctx)
+    return x, float(rho[0])
 
 
 def lra_preprocess_materialize(pre: lra_source, G, stream=None) -> None:

@@ -1,0 +1,407 @@
+// The range finder of Algorithm 5.1a (LRA U V of M from Y = M H) and the
+// superfast dual LSR of Algorithm 3.1 (the least squares problem of k
+// sampled rows), both through tall-skinny factorisations in FP64:
+//   * the Gram matrix Y^T Y of an N x k matrix, split over row chunks and
+//     32 x 32 tiles of the Gram matrix (per-chunk partial sums, added in a
+//     fixed order by the factorisation, so results are reproducible);
+//   * the rank-revealing QR of Y as pivoted Cholesky of Y^T Y: diagonal
+//     pivoting on the Schur complement picks, in exact arithmetic, the
+//     columns of Businger-Golub QR with column pivoting (the largest
+//     remaining column norm), and R_jj are that QR's diagonal;
+//   * CholeskyQR2 (Fukaya, Nakatsukasa, Yanagisawa, Yamamoto 2014) for the
+//     orthonormal factor, and shifted CholeskyQR3 (Fukaya, Kannan,
+//     Nakatsukasa, Zhang, Yamamoto 2020) for the LSR, whose inputs can be
+//     ill conditioned: a first pass on Y^T Y + s I, s = 11 (N k + k (k + 1))
+//     u ||Y||_F^2, then two plain passes.
+#include <cfloat>
+
+#include "lra_internal.cuh"
+#include "lra_kernels.h"
+
+namespace lra {
+namespace {
+
+constexpr int kGt = 32;          // Gram tile
+constexpr int kRowsBatch = 32;   // rows staged per step
+constexpr int kSmallT = 1024;
+
+// partials[chunk][a * k + c] = sum over the chunk's rows of Y[i][a] Y[i][c]
+// for c >= a (upper triangle with the diagonal); Y element (i, c) at
+// Y[i * si + c * st].  Block (tile pair, chunk): 32 x 32 threads, one
+// entry each; 32 rows of both tiles' columns are staged in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(kGt * kGt) ts_gram_kernel(const T* __restrict__ Y, long long N, int k,
+                                                            long long si, long long st, int nchunks,
+                                                            double* __restrict__ partials,
+                                                            const JobStatus* js) {
+  if (js->status != LRA_OK) return;
+  __shared__ double ya[kRowsBatch][kGt + 1], yb[kRowsBatch][kGt + 1];
+  // tile pair (ta <= tb) from the linear block index
+  const int nt = (k + kGt - 1) / kGt;
+  int p = blockIdx.x, ta = 0;
+  while (p >= nt - ta) {
+    p -= nt - ta;
+    ++ta;
+  }
+  const int tb = ta + p;
+  const int chunk = blockIdx.y;
+  const long long per = (N + nchunks - 1) / nchunks;
+  const long long r0 = chunk * per, r1 = min(N, r0 + per);
+  const int tx = threadIdx.x % kGt, ty = threadIdx.x / kGt;
+  const int a = ta * kGt + ty, c = tb * kGt + tx;
+  double acc = 0.0;
+  for (long long base = r0; base < r1; base += kRowsBatch) {
+    // thread (ty, tx) stages row base + ty, column tx of both tiles
+    const long long i = base + ty;
+    const int ca = ta * kGt + tx, cb = tb * kGt + tx;
+    ya[ty][tx] = (i < r1 && ca < k) ? (double)Y[i * si + (long long)ca * st] : 0.0;
+    yb[ty][tx] = (i < r1 && cb < k) ? (double)Y[i * si + (long long)cb * st] : 0.0;
+    __syncthreads();
+#pragma unroll 8
+    for (int t = 0; t < kRowsBatch; ++t) acc = fma(ya[t][ty], yb[t][tx], acc);
+    __syncthreads();
+  }
+  if (a < k && c < k && c >= a) partials[(size_t)chunk * k * k + (size_t)a * k + c] = acc;
+}
+
+// One CTA: G = sum of the partials (fixed order), pivoted Cholesky
+// G(piv, piv) = R^T R with the largest remaining diagonal as pivot (ties to
+// the smaller position), the numerical rank nr = #{R_jj > rank_tol R_00}
+// (stopping there), and for r <= nr the l x r matrix Gm = P R_r^{-1}
+// (row piv[s] of Gm is row s of R_r^{-1}, other rows zero), so that
+// Y Gm = Y(:, piv[:r]) R_r^{-1}.  Below the target rank: LRA_ESINGULAR.
+// Shared memory: G (k x k) and R (k x k).
+__global__ void __launch_bounds__(kSmallT) pchol_kernel(const double* __restrict__ partials, int nparts, int k,
+                                                        int r, double rank_tol, double* __restrict__ Gm,
+                                                        int* __restrict__ piv_out, JobStatus* js) {
+  if (js->status != LRA_OK) return;
+  extern __shared__ double pc_sm[];
+  double* G = pc_sm;
+  double* R = pc_sm + k * k;
+  __shared__ int piv[kMaxL];
+  __shared__ int nr_s;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < k * k; e += blockDim.x) {
+    const int a = e / k, c = e - a * k;
+    double s = 0.0;
+    if (c >= a)
+      for (int b = 0; b < nparts; ++b) s += partials[(size_t)b * k * k + e];
+    G[e] = s;
+    R[e] = 0.0;
+  }
+  if (tid < k) piv[tid] = tid;
+  if (tid == 0) nr_s = k;
+  __syncthreads();
+  for (int e = tid; e < k * k; e += blockDim.x) {
+    const int a = e / k, c = e - a * k;
+    if (c < a) G[e] = G[c * k + a];
+  }
+  __syncthreads();
+  double r00 = 0.0;
+  for (int j = 0; j < k; ++j) {
+    if (tid == 0) {
+      int p = j;
+      for (int q = j + 1; q < k; ++q)
+        if (G[q * k + q] > G[p * k + p]) p = q;
+      if (p != j) {   // symmetric interchange of rows and columns j, p; R's computed rows follow
+        for (int q = 0; q < k; ++q) {
+          const double t = G[j * k + q];
+          G[j * k + q] = G[p * k + q];
+          G[p * k + q] = t;
+        }
+        for (int q = 0; q < k; ++q) {
+          const double t = G[q * k + j];
+          G[q * k + j] = G[q * k + p];
+          G[q * k + p] = t;
+        }
+        for (int q = 0; q < j; ++q) {
+          const double t = R[q * k + j];
+          R[q * k + j] = R[q * k + p];
+          R[q * k + p] = t;
+        }
+        const int t = piv[j];
+        piv[j] = piv[p];
+        piv[p] = t;
+      }
+      const double d = G[j * k + j];
+      const double rjj = d > 0.0 ? sqrt(d) : 0.0;
+      if (j == 0) r00 = rjj;
+      if (!(rjj > rank_tol * r00) || !(rjj > 0.0)) {
+        nr_s = j;
+      } else {
+        R[j * k + j] = rjj;
+      }
+    }
+    __syncthreads();
+    if (nr_s <= j) break;
+    const double rjj = R[j * k + j];
+    for (int c = j + 1 + tid; c < k; c += blockDim.x) R[j * k + c] = G[j * k + c] / rjj;
+    __syncthreads();
+    // Schur complement of the trailing block
+    const int w = k - j - 1;
+    for (int e = tid; e < w * w; e += blockDim.x) {
+      const int a = j + 1 + e / w, c = j + 1 + e % w;
+      G[a * k + c] -= R[j * k + a] * R[j * k + c];
+    }
+    __syncthreads();
+  }
+  const int nr = nr_s;
+  if (tid == 0) js->k_eff = nr;
+  for (int q = tid; q < k; q += blockDim.x) piv_out[q] = piv[q];
+  if (nr < r) {
+    if (tid == 0) set_status(js, LRA_ESINGULAR);
+    return;
+  }
+  // Gm = P R_r^{-1}: column t of R_r^{-1} by back substitution (thread t)
+  for (int e = tid; e < k * r; e += blockDim.x) Gm[e] = 0.0;
+  __syncthreads();
+  for (int t = tid; t < r; t += blockDim.x) {
+    for (int s = t; s >= 0; --s) {
+      double v = (s == t) ? 1.0 : 0.0;
+      for (int q = s + 1; q <= t; ++q) v -= R[s * k + q] * Gm[(size_t)piv[q] * r + t];
+      Gm[(size_t)piv[s] * r + t] = v / R[s * k + s];
+    }
+  }
+}
+
+// U[i][t] = sum_{c <= t} Q1[i][c] Linv[t][c] (Q1 R2^{-1} with R2 = L^T),
+// rounded to FP32: the orthonormal factor of the second CholeskyQR pass.
+__global__ void __launch_bounds__(256) rf_finish_kernel(const double* __restrict__ Q1, long long N, int r,
+                                                        const double* __restrict__ Linv, float* __restrict__ U,
+                                                        const JobStatus* js) {
+  if (js->status != LRA_OK) return;
+  extern __shared__ double Ls[];
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) Ls[e] = Linv[e];
+  __syncthreads();
+  const long long total = N * r;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / r;
+    const int t = (int)(e - i * r);
+    double acc = 0.0;
+    for (int c = 0; c <= t; ++c) acc = fma(Q1[i * r + c], Ls[t * r + c], acc);
+    U[e] = (float)acc;
+  }
+}
+
+// FW[t][j] = W(rows[t], j) in FP64 for a stored FP32 or FP64 source.
+__global__ void __launch_bounds__(256) gather_rows_f64_kernel(SourceDev s, const int* __restrict__ rows, int k,
+                                                              double* __restrict__ FW) {
+  const long long n = s.n, total = (long long)k * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long t = e / n, j = e - t * n;
+    const long long i = __ldg(rows + t);
+    FW[e] = s.kind == LRA_DENSE_F64 ? __ldg(static_cast<const double*>(s.a) + i * s.lda + j)
+                                    : (double)__ldg(static_cast<const float*>(s.a) + i * s.lda + j);
+  }
+}
+
+// One CTA, FP64: G = sum of the partials (+ shift on the diagonal) and its
+// Cholesky factor R (upper, G = R^T R), right-looking; G and R in global
+// memory (k up to 1024).  A non-positive pivot: LRA_ESINGULAR.
+__global__ void __launch_bounds__(kSmallT) chol_big_kernel(const double* __restrict__ partials, int nparts, int k,
+                                                           double shift_rel, double* __restrict__ G,
+                                                           double* __restrict__ R, JobStatus* js) {
+  if (js->status != LRA_OK) return;
+  __shared__ double red[kSmallT / 32];
+  __shared__ int bad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) bad = 0;
+  double tr = 0.0;
+  for (long long e = tid; e < (long long)k * k; e += blockDim.x) {
+    const int a = (int)(e / k), c = (int)(e - (long long)a * k);
+    double s = 0.0;
+    if (c >= a)
+      for (int b = 0; b < nparts; ++b) s += partials[(size_t)b * k * k + e];
+    G[e] = s;
+    R[e] = 0.0;
+    if (a == c) tr += s;
+  }
+  // shift = shift_rel * trace(G) = shift_rel * ||Y||_F^2 (fixed-order sum)
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, off);
+  if (lane == 0) red[warp] = tr;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    red[0] = shift_rel * t;
+  }
+  __syncthreads();
+  const double shift = red[0];
+  for (int a = tid; a < k; a += blockDim.x) G[(size_t)a * k + a] += shift;
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {
+    const double d = G[(size_t)j * k + j];
+    if (!(d > 0.0)) {
+      if (tid == 0) bad = 1;
+      break;
+    }
+    const double rjj = sqrt(d);
+    for (int c = j + tid; c < k; c += blockDim.x) R[(size_t)j * k + c] = c == j ? rjj : G[(size_t)j * k + c] / rjj;
+    __syncthreads();
+    const int w = k - j - 1;
+    for (long long e = tid; e < (long long)w * w; e += blockDim.x) {
+      const int a = j + 1 + (int)(e / w), c = j + 1 + (int)(e % w);
+      if (c >= a) G[(size_t)a * k + c] -= R[(size_t)j * k + a] * R[(size_t)j * k + c];
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (bad && tid == 0) set_status(js, LRA_ESINGULAR);
+}
+
+// Q[i][:] = W[i][:] R^{-1} (R upper k x k): forward substitution along the
+// row, one thread per row (q_j = (w_j - sum_{c<j} q_c R_cj) / R_jj).
+__global__ void __launch_bounds__(128) trsm_rows_kernel(const double* __restrict__ W, long long N, int k,
+                                                        const double* __restrict__ R, double* __restrict__ Q,
+                                                        const JobStatus* js) {
+  if (js->status != LRA_OK) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double* w = W + i * k;
+    double* q = Q + i * k;
+    for (int j = 0; j < k; ++j) {
+      double v = w[j];
+      for (int c = 0; c < j; ++c) v = fma(-q[c], __ldg(R + (size_t)c * k + j), v);
+      q[j] = v / __ldg(R + (size_t)j * k + j);
+    }
+  }
+}
+
+// The least squares solution from the factors R_1 .. R_p of (FA | Fb) =
+// Q R_p ... R_1 (upper, (n+1) x (n+1)): v = R_p ... R_1 e_n (the last column
+// of the product), then x = (R_1)_nn^{-1} ... (R_p)_nn^{-1} v[:n]; rho =
+// |v[n]| is the residual norm of the sampled problem.  One CTA; each row's
+// dot product is a block reduction.
+__global__ void __launch_bounds__(kSmallT) lsr_solve_kernel(const double* __restrict__ Rs, int p, int k,
+                                                            double* __restrict__ v, double* __restrict__ x,
+                                                            double* __restrict__ rho, const JobStatus* js) {
+  if (js->status != LRA_OK) return;
+  __shared__ double red[kSmallT / 32];
+  __shared__ double bc;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int n = k - 1;
+  const size_t kk = (size_t)k * k;
+  for (int a = tid; a < k; a += blockDim.x) v[a] = Rs[(size_t)a * k + n];   // R_1 e_n
+  __syncthreads();
+  for (int s = 1; s < p; ++s) {   // v <- R_{s+1} v, row a of an upper factor: sum_{c >= a}
+    const double* Rm = Rs + s * kk;
+    for (int a = 0; a < k; ++a) {
+      double t = 0.0;
+      for (int c = a + tid; c < k; c += blockDim.x) t = fma(Rm[(size_t)a * k + c], v[c], t);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+      if (lane == 0) red[warp] = t;
+      __syncthreads();
+      if (tid == 0) {
+        double u = 0.0;
+        for (int w2 = 0; w2 < nw; ++w2) u += red[w2];
+        bc = u;
+      }
+      __syncthreads();
+      if (tid == 0) x[a] = bc;   // staged; rows below a are not read again in this product
+      __syncthreads();
+    }
+    for (int a = tid; a < k; a += blockDim.x) v[a] = x[a];
+    __syncthreads();
+  }
+  if (tid == 0) *rho = fabs(v[n]);
+  // x = (R_1)^{-1} ... (R_p)^{-1} v[:n] on the leading n x n blocks
+  for (int a = tid; a < n; a += blockDim.x) x[a] = v[a];
+  __syncthreads();
+  for (int s = p - 1; s >= 0; --s) {
+    const double* Rm = Rs + s * kk;
+    for (int a = n - 1; a >= 0; --a) {
+      double t = 0.0;
+      for (int c = a + 1 + tid; c < n; c += blockDim.x) t = fma(Rm[(size_t)a * k + c], x[c], t);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+      if (lane == 0) red[warp] = t;
+      __syncthreads();
+      if (tid == 0) {
+        double u = 0.0;
+        for (int w2 = 0; w2 < nw; ++w2) u += red[w2];
+        x[a] = (x[a] - u) / Rm[(size_t)a * k + a];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+int gram_chunks(long long N, int k) {
+  const int nt = (k + kGt - 1) / kGt;
+  const int pairs = nt * (nt + 1) / 2;
+  long long ch = (2 * 152 + pairs - 1) / pairs;
+  const long long max_by_rows = (N + 255) / 256;   // at least 256 rows per chunk
+  if (ch > max_by_rows) ch = max_by_rows;
+  if (ch < 1) ch = 1;
+  if (ch > 256) ch = 256;
+  return (int)ch;
+}
+
+}  // namespace
+
+int ts_gram_chunks(long long N, int k) { return gram_chunks(N, k); }
+
+cudaError_t launch_ts_gram_f32(const float* Y, long long N, int k, long long si, long long st, double* partials,
+                               int nchunks, const JobStatus* js, cudaStream_t s) {
+  const int nt = (k + kGt - 1) / kGt;
+  ts_gram_kernel<float><<<dim3(nt * (nt + 1) / 2, nchunks), kGt * kGt, 0, s>>>(Y, N, k, si, st, nchunks, partials,
+                                                                                js);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ts_gram_f64(const double* Y, long long N, int k, double* partials, int nchunks,
+                               const JobStatus* js, cudaStream_t s) {
+  const int nt = (k + kGt - 1) / kGt;
+  ts_gram_kernel<double><<<dim3(nt * (nt + 1) / 2, nchunks), kGt * kGt, 0, s>>>(Y, N, k, k, 1, nchunks, partials,
+                                                                                 js);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pchol(const double* partials, int nparts, int k, int r, double rank_tol, double* Gm, int* piv,
+                         JobStatus* js, cudaStream_t s) {
+  const size_t sm = sizeof(double) * 2 * k * k;
+  cudaError_t e = smem_optin(reinterpret_cast<const void*>(pchol_kernel), (int)sm);
+  if (e) return e;
+  pchol_kernel<<<1, kSmallT, sm, s>>>(partials, nparts, k, r, rank_tol, Gm, piv, js);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rf_finish(const double* Q1, long long N, int r, const double* Linv, float* U, const JobStatus* js,
+                             int sms, cudaStream_t s) {
+  long long g = (N * r + 255) / 256;
+  if (g > (long long)sms * 8) g = (long long)sms * 8;
+  rf_finish_kernel<<<(int)g, 256, sizeof(double) * r * r, s>>>(Q1, N, r, Linv, U, js);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows_f64(const SourceDev& src, const int* rows, int k, double* FW, int sms, cudaStream_t s) {
+  long long g = ((long long)k * src.n + 255) / 256;
+  if (g > (long long)sms * 8) g = (long long)sms * 8;
+  gather_rows_f64_kernel<<<(int)g, 256, 0, s>>>(src, rows, k, FW);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_big(const double* partials, int nparts, int k, double shift_rel, double* G, double* R,
+                            JobStatus* js, cudaStream_t s) {
+  chol_big_kernel<<<1, kSmallT, 0, s>>>(partials, nparts, k, shift_rel, G, R, js);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trsm_rows(const double* W, long long N, int k, const double* R, double* Q, const JobStatus* js,
+                             int sms, cudaStream_t s) {
+  long long g = (N + 127) / 128;
+  if (g > (long long)sms * 4) g = (long long)sms * 4;
+  trsm_rows_kernel<<<(int)g, 128, 0, s>>>(W, N, k, R, Q, js);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lsr_solve(const double* Rs, int p, int k, double* v, double* x, double* rho, const JobStatus* js,
+                             cudaStream_t s) {
+  lsr_solve_kernel<<<1, kSmallT, 0, s>>>(Rs, p, k, v, x, rho, js);
+  return cudaGetLastError();
+}
+
+}  // namespace lra

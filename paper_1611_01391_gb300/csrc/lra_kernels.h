@@ -157,6 +157,24 @@ cudaError_t launch_pre_materialize(const float* M, long long lda, float* G, long
 cudaError_t launch_pre_recover(const SourceDev& s, const float* Cbar, const float* Rbar, int l, float* A, float* B,
                                int* inv, cudaStream_t st);
 
+// Range finder and dual LSR (k_rf.cu): tall-skinny FP64 factorisations.
+int ts_gram_chunks(long long N, int k);
+cudaError_t launch_ts_gram_f32(const float* Y, long long N, int k, long long si, long long st, double* partials,
+                               int nchunks, const JobStatus* js, cudaStream_t s);
+cudaError_t launch_ts_gram_f64(const double* Y, long long N, int k, double* partials, int nchunks,
+                               const JobStatus* js, cudaStream_t s);
+cudaError_t launch_pchol(const double* partials, int nparts, int k, int r, double rank_tol, double* Gm, int* piv,
+                         JobStatus* js, cudaStream_t s);
+cudaError_t launch_rf_finish(const double* Q1, long long N, int r, const double* Linv, float* U, const JobStatus* js,
+                             int sms, cudaStream_t s);
+cudaError_t launch_gather_rows_f64(const SourceDev& src, const int* rows, int k, double* FW, int sms, cudaStream_t s);
+cudaError_t launch_chol_big(const double* partials, int nparts, int k, double shift_rel, double* G, double* R,
+                            JobStatus* js, cudaStream_t s);
+cudaError_t launch_trsm_rows(const double* W, long long N, int k, const double* R, double* Q, const JobStatus* js,
+                             int sms, cudaStream_t s);
+cudaError_t launch_lsr_solve(const double* Rs, int p, int k, double* v, double* x, double* rho, const JobStatus* js,
+                             cudaStream_t s);
+
 // Small control kernels.
 cudaError_t launch_tol_check(JobStatus* js, double tol, cudaStream_t st);
 

@@ -2,6 +2,7 @@
 // admission, per-job device memory and the launch sequence of one C-A solve
 // (Section 6.5: C-A iterations, then the Primitive Algorithm's nucleus;
 // Appendix F: sampled error estimate).
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -109,6 +110,7 @@ struct lra_ctx {
   std::unordered_map<lra_job, Job*> jobs;
   lra_job next_id = 1;
   std::string last_error;
+  cublasHandle_t blas = nullptr;   // the range finder's V = U^T M, created on first use
 };
 
 int lra::ctx_device(lra_ctx* ctx) { return ctx->device; }
@@ -675,6 +677,7 @@ lra_status lra_cross_destroy(lra_ctx* ctx) {
       if (h) cudaFreeHost(h);
     cudaFreeHost(ctx->pinned);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+    if (ctx->blas) cublasDestroy(ctx->blas);
   }
   delete ctx;
   return LRA_OK;
@@ -869,6 +872,214 @@ lra_status lra_cross_cancel(lra_ctx* ctx, lra_job id) {
   cudaEventSynchronize(j->ev_end);
   std::lock_guard<std::mutex> lock(ctx->mu);
   release_job(ctx, j);
+  return LRA_OK;
+}
+
+// Algorithm 5.1a with a sub-identity multiplier (see the header).
+lra_status lra_range_finder(lra_ctx* ctx, const lra_source* src, const int32_t* J, int32_t l,
+                            const lra_rf_params* p, const lra_rf_out* out) {
+  if (!ctx || !src || !J || !p || !out || !out->U || !out->V || !out->piv || !out->nrank) return LRA_EINVAL;
+  std::string why;
+  if (validate_source(src, &why) != LRA_OK) return fail(ctx, LRA_EINVAL, why);
+  if (src->kind != LRA_DENSE_F32) return fail(ctx, LRA_EINVAL, "range finder: V = U^T M needs a stored FP32 matrix");
+  const long long m = src->m, n = src->n;
+  const int r = p->r, q = (int)p->resid_q, sN = (int)p->resid_s;
+  if (l < 1 || l > kMaxL || l > n || l > m || r < 1 || r > l || !(p->rank_tol >= 0.0) || p->resid_q < 0 ||
+      p->resid_s < 0 || (p->resid_q > 0) != (p->resid_s > 0) ||
+      (p->resid_q > 0 && (!p->resid_rows || !p->resid_cols || p->resid_q > m || p->resid_s > n)))
+    return fail(ctx, LRA_EINVAL, "range finder: bad sizes");
+  if (!distinct_in_range(J, l, n)) return fail(ctx, LRA_EINVAL, "range finder: J must hold l distinct columns");
+  if (q > 0 && (!distinct_in_range(p->resid_rows, q, m) || !distinct_in_range(p->resid_cols, sN, n)))
+    return fail(ctx, LRA_EINVAL, "range finder: residual sample indices must be distinct and in range");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e) return cuda_fail(ctx, e, "cudaSetDevice");
+  {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if (!ctx->blas && cublasCreate(&ctx->blas) != CUBLAS_STATUS_SUCCESS) {
+      ctx->blas = nullptr;
+      ctx->last_error = "range finder: cublasCreate failed";
+      return LRA_ECUDA;
+    }
+  }
+  const int nch = ts_gram_chunks(m, l), npm = lev_partials(m);
+  const int nres = q > 0 ? sampled_residual_partials(q, sN) : 1;
+  Layout lay;
+  const size_t o_js = lay.take(sizeof(JobStatus)), o_J = lay.take(sizeof(int) * l);
+  const size_t o_sr = lay.take(sizeof(int) * std::max(q, 1)), o_sc = lay.take(sizeof(int) * std::max(sN, 1));
+  const size_t o_I = lay.take(sizeof(double) * r * r);   // identity nucleus for the estimate
+  const size_t prefix = lay.off;
+  const size_t o_Y = lay.take(sizeof(float) * (size_t)m * l);
+  const size_t o_p1 = lay.take(sizeof(double) * (size_t)nch * l * l);
+  const size_t o_Gm = lay.take(sizeof(double) * l * r), o_piv = lay.take(sizeof(int) * l);
+  const size_t o_Q1 = lay.take(sizeof(double) * (size_t)m * r);
+  const size_t o_p2 = lay.take(sizeof(double) * (size_t)npm * r * r), o_Li = lay.take(sizeof(double) * r * r);
+  const size_t o_cuq = lay.take(sizeof(float) * std::max<size_t>(2 * (size_t)q * r, 1));
+  const size_t o_pr = lay.take(sizeof(double) * 3 * nres);
+  const size_t bytes = lay.off;
+  cudaStream_t st = ctx->stream;
+  unsigned char* b = nullptr;
+  if ((e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&b), bytes, ctx->pool, st)))
+    return cuda_fail(ctx, e, "cudaMallocFromPoolAsync");
+  auto P = [&](size_t o) { return b + o; };
+  JobStatus* js = reinterpret_cast<JobStatus*>(P(o_js));
+  int* dJ = reinterpret_cast<int*>(P(o_J));
+  int *dsr = reinterpret_cast<int*>(P(o_sr)), *dsc = reinterpret_cast<int*>(P(o_sc));
+  double* Ir = reinterpret_cast<double*>(P(o_I));
+  float* Y = reinterpret_cast<float*>(P(o_Y));
+  double *p1 = reinterpret_cast<double*>(P(o_p1)), *Gm = reinterpret_cast<double*>(P(o_Gm));
+  int* dpiv = reinterpret_cast<int*>(P(o_piv));
+  double *Q1 = reinterpret_cast<double*>(P(o_Q1)), *p2 = reinterpret_cast<double*>(P(o_p2));
+  double* Linv = reinterpret_cast<double*>(P(o_Li));
+  float* cuq = reinterpret_cast<float*>(P(o_cuq));
+  double* rpart = reinterpret_cast<double*>(P(o_pr));
+  std::vector<unsigned char> hs(prefix, 0);
+  JobStatus init{};
+  init.status = LRA_OK;
+  std::memcpy(hs.data() + o_js, &init, sizeof(init));
+  std::memcpy(hs.data() + o_J, J, sizeof(int) * l);
+  if (q > 0) {
+    std::memcpy(hs.data() + o_sr, p->resid_rows, sizeof(int) * q);
+    std::memcpy(hs.data() + o_sc, p->resid_cols, sizeof(int) * sN);
+  }
+  for (int t = 0; t < r; ++t) {
+    const double one = 1.0;
+    std::memcpy(hs.data() + o_I + sizeof(double) * ((size_t)t * r + t), &one, sizeof(double));
+  }
+  const SourceDev sd = make_src(src);
+  TmaMap cmap{};
+  const bool tma = make_cols_map(&cmap, static_cast<const float*>(src->a), m, n, src->lda);
+  JobStatus hjs{};
+  std::vector<int> hpiv(l, 0);
+  // Y = M[:, J]; rank-revealing QR of Y; Q1 = Y(:, piv[:r]) R_r^{-1} and its Gram
+  if (!(e = cudaMemcpyAsync(b, hs.data(), prefix, cudaMemcpyHostToDevice, st)) &&
+      !(e = tma ? launch_gather_cols_tma(cmap, dJ, l, m, Y, js, 0, ctx->sms, st)
+                : launch_gather_cols(sd, dJ, l, Y, js, 0, ctx->sms, st)) &&
+      !(e = launch_ts_gram_f32(Y, m, l, l, 1, p1, nch, js, st)) &&
+      !(e = launch_pchol(p1, nch, l, r, p->rank_tol, Gm, dpiv, js, st)) &&
+      !(e = launch_lev_project(Y, m, l, l, 1, Gm, r, Q1, p2, npm, js, st)) &&
+      // CholeskyQR2: the orthonormal factor U = Q1 R2^{-1}
+      !(e = launch_lev_chol(p2, npm, r, Linv, js, st)) &&
+      !(e = launch_rf_finish(Q1, m, r, Linv, out->U, js, ctx->sms, st)) &&
+      !(e = cudaMemcpyAsync(&hjs, js, sizeof(JobStatus), cudaMemcpyDeviceToHost, st)) &&
+      !(e = cudaMemcpyAsync(hpiv.data(), dpiv, sizeof(int) * l, cudaMemcpyDeviceToHost, st)))
+    e = cudaStreamSynchronize(st);
+  if (e) {
+    cudaFreeAsync(b, st);
+    return cuda_fail(ctx, e, "range finder");
+  }
+  std::memcpy(out->piv, hpiv.data(), sizeof(int) * l);
+  *out->nrank = hjs.k_eff;
+  if (hjs.status != LRA_OK) {
+    cudaFreeAsync(b, st);
+    return fail(ctx, (lra_status)hjs.status,
+                hjs.status == LRA_ESINGULAR ? "range finder: the numerical rank of M H is below r (FAILURE)"
+                                            : "range finder: device status");
+  }
+  // V = U^T M: row-major V (r x n) is column-major n x r = M^c (n x m) (U^c)^T
+  cublasSetStream(ctx->blas, st);
+  const float one = 1.0f, zero = 0.0f;
+  int mode = 1;
+  cublasStatus_t bs = cublasGemmEx(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_T, (int)n, r, (int)m, &one, src->a, CUDA_R_32F,
+                                   (int)src->lda, out->U, CUDA_R_32F, r, &zero, out->V, CUDA_R_32F, (int)n,
+                                   CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT);
+  if (bs != CUBLAS_STATUS_SUCCESS) {
+    mode = 0;
+    bs = cublasGemmEx(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_T, (int)n, r, (int)m, &one, src->a, CUDA_R_32F,
+                      (int)src->lda, out->U, CUDA_R_32F, r, &zero, out->V, CUDA_R_32F, (int)n, CUBLAS_COMPUTE_32F,
+                      CUBLAS_GEMM_DEFAULT);
+  }
+  if (bs != CUBLAS_STATUS_SUCCESS) {
+    cudaFreeAsync(b, st);
+    return fail(ctx, LRA_ECUDA, "range finder: cublasGemmEx failed");
+  }
+  if (out->gemm_mode) *out->gemm_mode = mode;
+  // Appendix F estimate of U V: the CUR form with C = U, nucleus I_r, R = V
+  if (q > 0 &&
+      !(e = launch_sampled_residual(sd, dsr, q, dsc, sN, r, out->U, Ir, out->V, cuq, rpart, nres, js, st)) &&
+      !(e = cudaMemcpyAsync(&hjs, js, sizeof(JobStatus), cudaMemcpyDeviceToHost, st)))
+    e = cudaStreamSynchronize(st);
+  else if (q == 0)
+    e = cudaStreamSynchronize(st);
+  cudaFreeAsync(b, st);
+  if (e) return cuda_fail(ctx, e, "range finder");
+  if (out->est_rel_err) *out->est_rel_err = q > 0 ? hjs.est_rel : -1.0;
+  return LRA_OK;
+}
+
+// Algorithm 3.1 with a sub-identity multiplier (see the header).
+lra_status lra_dual_lsr(lra_ctx* ctx, const lra_source* W, const int32_t* rows, int32_t k,
+                        const lra_lsr_params* p, const lra_lsr_out* out) {
+  if (!ctx || !W || !rows || !p || !out || !out->x) return LRA_EINVAL;
+  std::string why;
+  if (validate_source(W, &why) != LRA_OK) return fail(ctx, LRA_EINVAL, why);
+  if (W->kind != LRA_DENSE_F64 && W->kind != LRA_DENSE_F32)
+    return fail(ctx, LRA_EINVAL, "dual LSR: W = (A | b) must be a stored matrix");
+  const long long m = W->m;
+  const int kc = (int)W->n;   // n + 1 columns
+  const int passes = p->passes;
+  if (kc < 2 || kc > 1024 || k < kc || k > m || passes < 1 || passes > 4)
+    return fail(ctx, LRA_EINVAL, "dual LSR: need 2 <= n + 1 <= 1024, n + 1 <= k <= m, 1..4 passes");
+  if (!distinct_in_range(rows, k, m)) return fail(ctx, LRA_EINVAL, "dual LSR: rows must be distinct and in range");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e) return cuda_fail(ctx, e, "cudaSetDevice");
+  const int nch = ts_gram_chunks(k, kc);
+  const size_t kk = (size_t)kc * kc;
+  Layout lay;
+  const size_t o_js = lay.take(sizeof(JobStatus)), o_rows = lay.take(sizeof(int) * k);
+  const size_t prefix = lay.off;
+  const size_t o_W = lay.take(sizeof(double) * (size_t)k * kc), o_Qa = lay.take(sizeof(double) * (size_t)k * kc);
+  const size_t o_p = lay.take(sizeof(double) * (size_t)nch * kk), o_G = lay.take(sizeof(double) * kk);
+  const size_t o_R = lay.take(sizeof(double) * kk * passes);
+  const size_t o_v = lay.take(sizeof(double) * kc), o_x = lay.take(sizeof(double) * kc);
+  const size_t o_rho = lay.take(sizeof(double));
+  const size_t bytes = lay.off;
+  cudaStream_t st = ctx->stream;
+  unsigned char* b = nullptr;
+  if ((e = cudaMallocFromPoolAsync(reinterpret_cast<void**>(&b), bytes, ctx->pool, st)))
+    return cuda_fail(ctx, e, "cudaMallocFromPoolAsync");
+  auto P = [&](size_t o) { return b + o; };
+  JobStatus* js = reinterpret_cast<JobStatus*>(P(o_js));
+  int* drows = reinterpret_cast<int*>(P(o_rows));
+  double *FW = reinterpret_cast<double*>(P(o_W)), *Qa = reinterpret_cast<double*>(P(o_Qa));
+  double *part = reinterpret_cast<double*>(P(o_p)), *G = reinterpret_cast<double*>(P(o_G));
+  double* Rs = reinterpret_cast<double*>(P(o_R));
+  double *dv = reinterpret_cast<double*>(P(o_v)), *dx = reinterpret_cast<double*>(P(o_x));
+  double* drho = reinterpret_cast<double*>(P(o_rho));
+  std::vector<unsigned char> hs(prefix, 0);
+  JobStatus init{};
+  init.status = LRA_OK;
+  std::memcpy(hs.data() + o_js, &init, sizeof(init));
+  std::memcpy(hs.data() + o_rows, rows, sizeof(int) * k);
+  const SourceDev sd = make_src(W);
+  // the shift of shifted CholeskyQR: 11 (k c + c (c + 1)) u, times ||F W||_F^2 on the device
+  const double shift_rel = 11.0 * ((double)k * kc + (double)kc * (kc + 1)) * 0x1p-53;
+  e = cudaMemcpyAsync(b, hs.data(), prefix, cudaMemcpyHostToDevice, st);
+  if (!e) e = launch_gather_rows_f64(sd, drows, k, FW, ctx->sms, st);
+  double *in = FW, *outq = Qa;
+  for (int s = 0; s < passes && !e; ++s) {
+    double* Rsp = Rs + s * kk;
+    if ((e = launch_ts_gram_f64(in, k, kc, part, nch, js, st))) break;
+    if ((e = launch_chol_big(part, nch, kc, (s == 0 && p->shifted) ? shift_rel : 0.0, G, Rsp, js, st))) break;
+    if (s + 1 < passes) {
+      if ((e = launch_trsm_rows(in, k, kc, Rsp, outq, js, ctx->sms, st))) break;
+      std::swap(in, outq);   // ping-pong: the gathered rows are not needed after the first pass
+    }
+  }
+  JobStatus hjs{};
+  std::vector<double> hx(kc, 0.0);
+  double hrho = 0.0;
+  if (!e && !(e = launch_lsr_solve(Rs, passes, kc, dv, dx, drho, js, st)) &&
+      !(e = cudaMemcpyAsync(&hjs, js, sizeof(JobStatus), cudaMemcpyDeviceToHost, st)) &&
+      !(e = cudaMemcpyAsync(hx.data(), dx, sizeof(double) * kc, cudaMemcpyDeviceToHost, st)) &&
+      !(e = cudaMemcpyAsync(&hrho, drho, sizeof(double), cudaMemcpyDeviceToHost, st)))
+    e = cudaStreamSynchronize(st);
+  cudaFreeAsync(b, st);
+  if (e) return cuda_fail(ctx, e, "dual LSR");
+  if (hjs.status != LRA_OK)
+    return fail(ctx, (lra_status)hjs.status,
+                hjs.status == LRA_ESINGULAR ? "dual LSR: a Cholesky pivot is not positive" : "dual LSR: device status");
+  std::memcpy(out->x, hx.data(), sizeof(double) * (kc - 1));
+  if (out->rho) *out->rho = hrho;
   return LRA_OK;
 }
 

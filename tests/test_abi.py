@@ -100,7 +100,8 @@ def test_struct_layouts_match_the_header(tmp_path):
         pytest.skip("no C compiler")
     import paper_1611_01391_gb300 as L
     structs = ["lra_ctx_params", "lra_source", "lra_params", "lra_info", "lra_cur_out", "lra_block",
-               "lra_batch_params", "lra_batch_out"]
+               "lra_batch_params", "lra_batch_out", "lra_cynical_params", "lra_cynical_out", "lra_refine_params",
+               "lra_refine_out", "lra_rf_params", "lra_rf_out", "lra_lsr_params", "lra_lsr_out"]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lra_cross.h"', "int main(void) {"]
     for s in structs:
         lines.append(f'  printf("{s} size %zu\\n", sizeof({s}));')
