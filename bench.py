@@ -688,6 +688,7 @@ def run_variants(dev, reps=10, n=1024, r=16):
                                         "matrix G1 G2 + 1e-4 G3, FP32 stored"}
     ctx.close()
     out["preprocess_hadamard"] = run_preprocess(dev)
+    out["range_finder_lsr"] = run_rf_lsr(dev)
     out["config"] = {"n": n, "r": r, "matrix": "G1 G2 + 1e-10 G3 (Table tb_ranrc family), FP32 stored",
                      "timing": "host wall clock per blocking call", "reps": reps,
                      "paper_means_spectral_context": {"tests2": 4.57e-06, "tests3": 1.72e-04, "tests4": 4.34e-05,
@@ -786,6 +787,76 @@ def run_preprocess(dev, n=32768, d=3, k=64, reps=5):
                           "preprocessed_rel_fro_err_max": float(np.max(e_pre)),
                           "best_rank_r_rel_fro_err": float(np.sqrt(np.sum(sv[r:] ** 2)) / nrm),
                           "paper_tb_fh_mean_context": 3.97e-03}}
+
+
+def run_rf_lsr(dev, n=32768, r=64, l=96, reps=3):
+    """Algorithm 5.1a with a sub-identity multiplier on a stored FP32 n x n
+    rank-r matrix plus noise 1e-4 (the factor-Gaussian family): wall time per
+    blocking call, the V = U^T M GEMM's algorithmic work, and the Appendix F
+    error against C-A (k = r, l = l, 3 sweeps) on the same matrix; then
+    Algorithm 3.1 with a sub-identity multiplier (k = 6n sampled rows) at the
+    two sizes of Table lsrRandom on Gaussian inputs: time and the relative
+    residual ||A x - b|| / min ||A y - b|| (its optimum from numpy's least
+    squares on the host, outside the timed calls)."""
+    import numpy as np
+    import torch
+    import paper_1611_01391_gb300 as L
+    import workloads as W
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(W.BASE_SEED + 14000)
+    M = torch.randn((n, r), device=dev, generator=gen) @ torch.randn((r, n), device=dev, generator=gen)
+    M.mul_(1.0 / np.sqrt(r)).add_(torch.randn((n, n), device=dev, generator=gen), alpha=1e-4)
+    src = L.make_source("dense", a=M)
+    ctx = L.Context(dev.index or 0)
+    U = torch.empty((n, r), dtype=torch.float32, device=dev)
+    V = torch.empty((r, n), dtype=torch.float32, device=dev)
+    rows, cols = W.draw_indices(W.BASE_SEED + 14001, n, 1000, sort=True), W.draw_indices(W.BASE_SEED + 14002, n, 1000,
+                                                                                          sort=True)
+    ts, ests, mode = [], [], None
+    for i in range(reps + 1):
+        J = W.draw_indices(W.BASE_SEED + 14100 + i, n, l)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        res = L.lra_range_finder(ctx.ctx, src, J, r, U, V, rank_tol=1e-6, resid_rows=rows, resid_cols=cols)
+        t1 = time.perf_counter()
+        if i:
+            ts.append(t1 - t0)
+            ests.append(res["est_rel_err"])
+        mode = res["gemm_mode"]
+    p, keep = L.make_params(r, l, 3, W.draw_indices(W.BASE_SEED + 14200, n, l), resid_rows=rows, resid_cols=cols)
+    ctx.solve(src, p, l)
+    t0 = time.perf_counter()
+    ca = ctx.solve(src, p, l)
+    t_ca = time.perf_counter() - t0
+    del M, U, V
+    torch.cuda.empty_cache()
+    rf_ms = 1e3 * float(np.mean(ts))
+    out = {"range_finder": {"ms": rf_ms, "est_rel_err_mean": float(np.mean(ests)), "gemm_mode": mode,
+                            "gemm_flops": 2.0 * r * n * n, "gemm_hbm_bytes": 4.0 * n * n,
+                            "config": f"stored FP32 {n}x{n}, rank {r} + noise 1e-4, l = {l} sampled columns, r = {r}; "
+                                      "host wall clock per blocking call (gather, FP64 Gram, pivoted Cholesky, "
+                                      "CholeskyQR2, V = U^T M on cuBLAS, 1000x1000 Appendix F sample)"},
+           "ca_same_matrix": {"ms": 1e3 * t_ca, "est_rel_err": ca.info.est_rel_err,
+                              "config": f"k = {r}, l = {l}, 3 sweeps"}}
+    lsr = {}
+    for (k, m, nn) in ((600, 4096, 100), (2400, 16384, 400)):
+        tl, rr = [], []
+        for t in range(4):
+            A, b = W.lsr_problem(W.BASE_SEED + 14300 + t, "gaussian", m, nn)
+            Wm = torch.from_numpy(np.ascontiguousarray(np.concatenate([A, b[:, None]], axis=1))).to(dev)
+            srcw = L.make_source("dense", a=Wm)
+            rows_k = W.rng_for(W.BASE_SEED + 14400 + t).permutation(m)[:k]
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            x, rho = L.lra_dual_lsr(ctx.ctx, srcw, rows_k)
+            tl.append(time.perf_counter() - t0)
+            best = np.linalg.norm(A @ np.linalg.lstsq(A, b, rcond=None)[0] - b)
+            rr.append(float(np.linalg.norm(A @ x - b) / best))
+        lsr[f"k{k}_m{m}_n{nn}"] = {"ms_median": 1e3 * float(np.median(tl)), "rel_residual_mean": float(np.mean(rr)),
+                                    "paper_lsrRandom_gaussian_multiplier_mean": 1.098 if nn == 100 else 1.095}
+    out["dual_lsr_gaussian"] = lsr
+    ctx.close()
+    return out
 
 
 def run_profile_preprocess(n, d=3, k=64):

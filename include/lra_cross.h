@@ -587,9 +587,11 @@ lra_status lra_range_finder(lra_ctx* ctx, const lra_source* src, const int32_t* 
 
 typedef struct {
   int32_t passes;             /* CholeskyQR passes, 1..4 (3 by default)                  */
-  int32_t shifted;            /* nonzero: the first pass factors Y^T Y + s I,
-                                 s = 11 (k (n+1) + (n+1) (n+2)) 2^-53 ||Y||_F^2
-                                 (shifted CholeskyQR3, for ill-conditioned rows)        */
+  int32_t shifted;            /* nonzero: the first passes - 2 passes (at least one)
+                                 factor Y^T Y + s I, s = 11 (k (n+1) + (n+1) (n+2))
+                                 2^-53 ||Y||_F^2 (shifted CholeskyQR; each shifted pass
+                                 divides the condition number by about s^(-1/2) ||Y||,
+                                 so 4 passes reach condition numbers near 1e14)         */
 } lra_lsr_params;
 
 typedef struct {

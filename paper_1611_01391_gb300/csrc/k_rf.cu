@@ -11,7 +11,7 @@
 //   * CholeskyQR2 (Fukaya, Nakatsukasa, Yanagisawa, Yamamoto 2014) for the
 //     orthonormal factor, and shifted CholeskyQR3 (Fukaya, Kannan,
 //     Nakatsukasa, Zhang, Yamamoto 2020) for the LSR, whose inputs can be
-//     ill conditioned: a first pass on Y^T Y + s I, s = 11 (N k + k (k + 1))
+//     ill conditioned: leading passes on Y^T Y + s I, s = 11 (N k + k (k + 1))
 //     u ||Y||_F^2, then two plain passes.
 #include <cfloat>
 

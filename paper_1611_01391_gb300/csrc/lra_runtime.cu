@@ -1059,7 +1059,9 @@ lra_status lra_dual_lsr(lra_ctx* ctx, const lra_source* W, const int32_t* rows, 
   for (int s = 0; s < passes && !e; ++s) {
     double* Rsp = Rs + s * kk;
     if ((e = launch_ts_gram_f64(in, k, kc, part, nch, js, st))) break;
-    if ((e = launch_chol_big(part, nch, kc, (s == 0 && p->shifted) ? shift_rel : 0.0, G, Rsp, js, st))) break;
+    // the first passes - 2 passes (at least one) shifted, the last two plain
+    const bool shift_here = p->shifted && s < std::max(1, passes - 2);
+    if ((e = launch_chol_big(part, nch, kc, shift_here ? shift_rel : 0.0, G, Rsp, js, st))) break;
     if (s + 1 < passes) {
       if ((e = launch_trsm_rows(in, k, kc, Rsp, outq, js, ctx->sms, st))) break;
       std::swap(in, outq);   // ping-pong: the gathered rows are not needed after the first pass

@@ -123,18 +123,19 @@ def test_dual_lsr_fp32_storage(ctx):
 
 def test_dual_lsr_ill_conditioned_rows(ctx):
     """The ill-conditioned class (singular values 10^4 .. 10^-9, the rest
-    10^-10, condition 1e14): shifted CholeskyQR3 factors the sampled rows and
+    10^-10, condition 1e14): four passes, two of them shifted, factor the sampled rows and
     its solution's residual on them is no larger than that of the oracle's
     least squares solution (which truncates singular values below its rcond;
     the device solves the full-rank problem, so x itself differs along the
     directions of the tiny singular values)."""
     A, b = W.lsr_problem(9900, "ill", 4096, 100)
     rows = W.rng_for(9901).permutation(4096)[:600]
-    x, rho = _lsr(ctx, A, b, rows)
+    x, rho = _lsr(ctx, A, b, rows, passes=4)
     xr = O.dual_lsr(A, b, rows)
     rho_ref = np.linalg.norm(A[rows] @ xr - b[rows])
     assert np.linalg.norm(A[rows] @ x - b[rows]) <= (1 + 1e-6) * rho_ref
-    assert rho == pytest.approx(np.linalg.norm(A[rows] @ x - b[rows]), rel=1e-6)
+    # |x| reaches 1e10 along the tiny directions: A x carries ~1e-5 relative rounding
+    assert rho == pytest.approx(np.linalg.norm(A[rows] @ x - b[rows]), rel=1e-3)
 
 
 def test_dual_lsr_rank_deficient_sample_is_reported(ctx):
