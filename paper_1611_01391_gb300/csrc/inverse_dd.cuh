@@ -123,91 +123,6 @@ __device__ __forceinline__ bool invert_cross(StripF S, int l_arg, JobStatus* js,
   return true;
 }
 
-// The elimination of invert_cross run by the first NW warps of the CTA
-// only (threads 0 .. 32 NW - 1), which meet at the named barrier 1 instead
-// of the block barrier: the other warps are free meanwhile (the maxvol
-// launch fills its strip rows with them).  Same arithmetic, pivot rule and
-// result as invert_cross.  Every participating thread returns the same
-// value; the caller joins the rest of the CTA with a block barrier.
-template <int NW>
-__device__ __forceinline__ void inv_bar() {
-  asm volatile("bar.sync 1, %0;" ::"r"(NW * 32) : "memory");
-}
-
-template <int NW, int L = 0, typename StripF>
-__device__ __forceinline__ bool invert_cross_warps(StripF S, int l_arg, JobStatus* js, const int* pos, dd* A,
-                                                   const InvScratch& w, int* flag) {
-  constexpr int NT = NW * 32;
-  const int l = L > 0 ? L : l_arg;
-  const int ll = l * l;
-  const int tid = threadIdx.x, lane = tid & 31;
-  if (tid < 2) w.pkey[tid] = 0ull;
-  if (tid == 0) *flag = 0;
-  inv_bar<NW>();
-  int bad = 0;
-  for (int e = tid; e < ll; e += NT) {
-    const int r = e / l, c = e - r * l;
-    const dd v = dd_make(S((long long)pos[r], c));
-    if (!(fabsf(v.hi) <= FLT_MAX)) bad = 1;
-    A[e] = v;
-    if (c == 0) atomicMax(w.pkey, pivot_word(v, r));
-  }
-  if (bad) atomicOr(flag, 1);
-  inv_bar<NW>();
-  if (*flag) {
-    if (blockIdx.x == 0 && tid == 0) set_status(js, LRA_ENONFINITE);
-    return false;
-  }
-  for (int t = 0; t < l; ++t) {
-    if (tid < 32) {
-      const unsigned long long key = w.pkey[t & 1];
-      const int p = (key >> 32) != 0ull ? (int)(0xffffffffu - (unsigned int)key) : -1;
-      if (p >= 0) {
-        const dd rp = dd_div(dd_make(1.0f), A[p * l + t]);
-        for (int c = lane; c < l; c += 32) {
-          w.rowt[c] = (c == t) ? rp : dd_mul(A[p * l + c], rp);
-          w.rowold[c] = A[t * l + c];
-          w.colt[c] = A[(c == p ? t : c) * l + t];
-        }
-      }
-      if (lane == 0) {
-        *w.p_s = p;
-        w.swaps[t] = p;
-        w.pkey[(t + 1) & 1] = 0ull;
-      }
-    }
-    inv_bar<NW>();
-    const int p = *w.p_s;
-    if (p < 0) {
-      if (blockIdx.x == 0 && tid == 0) set_status(js, LRA_ESINGULAR);
-      return false;
-    }
-    for (int e = tid; e < ll; e += NT) {
-      const int r = e / l, c = e - r * l;
-      dd v;
-      if (r == t) {
-        v = w.rowt[c];
-      } else {
-        const dd av = (c == t) ? dd_make(0.0f) : (r == p ? w.rowold[c] : A[e]);
-        v = dd_fnma(w.colt[r], w.rowt[c], av);
-      }
-      A[e] = v;
-      if (c == t + 1 && r > t) atomicMax(&w.pkey[(t + 1) & 1], pivot_word(v, r));
-    }
-    inv_bar<NW>();
-  }
-  if (tid == 0) {
-    for (int q = 0; q < l; ++q) w.at[q] = q;
-    for (int t = l - 1; t >= 0; --t) {
-      const int p = w.swaps[t], x = w.at[t];
-      w.at[t] = w.at[p];
-      w.at[p] = x;
-    }
-  }
-  inv_bar<NW>();
-  return true;
-}
-
 // The same elimination with a one-step look-ahead.  While warps 1.. form step
 // t's result in the other buffer, warp 0 forms column t+1 of it, picks the
 // pivot of step t+1 (the largest |hi| below row t, ties to the smaller row),

@@ -48,7 +48,6 @@
 namespace lra {
 
 constexpr int kMaxvolThreads = 1024;
-constexpr int kInvWarps = 4;   // warps that run the in-launch cross inverse
 
 // Candidates are compared on one unsigned 64-bit word: the FP32 bit pattern
 // of |hi| (non-negative FP32 patterns order like their values as unsigned
@@ -111,7 +110,6 @@ __device__ __forceinline__ void load_row_point(const MaxvolArgs& a, long long g,
 // What warp 0 decided, for the other warps.
 struct Ctl {
   long long istar;
-  int inv_failed;      // the in-launch inverse met a non-finite or singular cross
   unsigned int base;   // grid-barrier arrivals before this launch
   unsigned int seq0;   // the job's decision counter when this launch started
   int kind;            // LRA_TRACE_*, or kFailed: the launch ends
@@ -147,41 +145,7 @@ __device__ __forceinline__ int grid_arrive_wait(unsigned int* count, unsigned in
 // measured faster there and slower for wider rows.  A group of GS lanes owns a row; lane gl computes columns
 // gl + GS c, c < NC, so every issued instruction is useful work
 // (NC = ceil(l / GS) exactly).
-// The strip rows of this CTA into B (as pairs with a zero low part), by
-// warps first_warp .. of the CTA: the rows the warm start reads when they
-// were filled beforehand (kRowsReady).
-template <int GS, int NC>
-__device__ __forceinline__ void fill_rows(const MaxvolArgs& a, const int l, dd* B, int nrows, long long row0,
-                                          const float* colpt, int first_warp) {
-  const int lane = threadIdx.x & 31, warp = (threadIdx.x >> 5) - first_warp;
-  const int nwarps = (blockDim.x >> 5) - first_warp;
-  constexpr int kGpw = 32 / GS;
-  const int gl = lane % GS;
-  const int ngroups = nwarps * kGpw;
-  for (int base = warp * kGpw; base < nrows; base += ngroups) {
-    const int r = base + lane / GS;
-    if (r >= nrows) continue;
-    const long long g = row0 + r;
-    dd* brow = B + (size_t)r * l;
-    if (a.gen) {
-      float rowpt[3];
-      load_row_point(a, g, rowpt);
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const int t = gl + GS * c;
-        if (t < l) brow[t] = dd_make(gen_strip_entry(a, colpt, rowpt, t));
-      }
-    } else {
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const int t = gl + GS * c;
-        if (t < l) brow[t] = dd_make(a.strip[g * a.si + (long long)t * a.st]);
-      }
-    }
-  }
-}
-
-template <int GS, int NC, typename XPtr, bool kRowsReady = false>
+template <int GS, int NC, typename XPtr>
 __device__ __forceinline__ void warm_rows(const MaxvolArgs& a, const int l, dd* B, int nrows, long long row0,
                                           XPtr X, const float* colpt) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -193,7 +157,7 @@ __device__ __forceinline__ void warm_rows(const MaxvolArgs& a, const int l, dd* 
     const bool active = r < nrows;
     const long long g = row0 + r;
     dd* brow = B + (size_t)r * l;
-    if (active && !kRowsReady) {
+    if (active) {
       if (a.gen) {
         float rowpt[3];
         load_row_point(a, g, rowpt);
@@ -344,7 +308,6 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
     // can pass the first barrier before this one arrives
     ctl->base = ld_acquire_u32(&a.bar->count) & ~255u;
     ctl->seq0 = a.bar->seq;   // written by the previous launch of this job
-    ctl->inv_failed = 0;
   }
   __syncthreads();
 
@@ -366,17 +329,8 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
         load_row_point(a, g, rowpt);
         return gen_strip_entry(a, colpt, rowpt, c);
       };
-      // the first kInvWarps warps invert the cross while the others fill
-      // the strip rows; the block barrier joins them
-      if (warp < kInvWarps) {
-        if (!invert_cross_warps<kInvWarps, L>(S, l, a.js, pos_s, xs, inv, &ctl->inv_failed) && tid == 0)
-          ctl->inv_failed = 1;
-      } else {
-        fill_rows<GS, NC>(a, l, B, nrows, row0, colpt, kInvWarps);
-      }
-      __syncthreads();
-      if (ctl->inv_failed) return;
-      warm_rows<GS, NC, SharedXMapped, true>(a, l, B, nrows, row0, SharedXMapped{xs, inv.at}, colpt);
+      if (!invert_cross<kMaxvolThreads, L>(S, l, a.js, pos_s, xs, inv)) return;
+      warm_rows<GS, NC>(a, l, B, nrows, row0, SharedXMapped{xs, inv.at}, colpt);
     } else if (a.stage_xinv) {
       for (int e = tid; e < l * l; e += nthr) {
         const float2 v = a.xin[e];
