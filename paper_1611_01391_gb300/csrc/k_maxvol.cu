@@ -516,52 +516,29 @@ __global__ void __launch_bounds__(kMaxvolThreads, 1) maxvol_kernel(MaxvolArgs a)
     // position, so keeping the first of equal patterns keeps the smaller index
     unsigned int bk = 0u;
     int be = 0;
-    // two rows per group and step (r and r + one pass of the CTA), their
-    // loads issued together; the entry in column j* of each row (the update's
-    // column factor, before the update) comes by shuffle from the lane that
-    // holds it.  Rows are still visited in increasing order per lane.
-    const int src_lane = (lane / GS) * GS + jstar % GS, ccj = jstar / GS;
-    auto upd_row = [&](int r, bool act, dd* brow, dd (&v)[NC], dd c) {
+    for (int base = warp * kGpw; base < nrows; base += ngroups) {
+      const int r = base + lane / GS;
+      const bool act = r < nrows;
+      dd* brow = B + (size_t)(act ? r : 0) * l;
+      // the row's entry in column j* is read before its group writes the row
+      const dd c = act ? brow[jstar] : dd_make(0.0f);
+      __syncwarp();
       const bool piv_row = row0 + r == istar;
       const bool scan_row = act && !(next_gepp && used[act ? r : 0]);
 #pragma unroll
       for (int cc = 0; cc < NC; ++cc) {
         const int t = gl + GS * cc;
         if (t < l) {
-          dd w = dd_fnma(c, rv[cc], v[cc]);
-          if (piv_row) w = dd_make(t == jstar ? 1.0f : 0.0f);
-          if (act) brow[t] = w;
-          const unsigned int k1 = (__float_as_uint(w.hi) & 0x7fffffffu) + 1u;
+          dd v = dd_fnma(c, rv[cc], act ? brow[t] : dd_make(0.0f));
+          if (piv_row) v = dd_make(t == jstar ? 1.0f : 0.0f);
+          if (act) brow[t] = v;
+          const unsigned int k1 = (__float_as_uint(v.hi) & 0x7fffffffu) + 1u;
           if (scan_row && (!next_gepp || t == next_col) && k1 > bk) {
             bk = k1;
             be = r * l + t;
           }
         }
       }
-    };
-    for (int base = warp * kGpw; base < nrows; base += 2 * ngroups) {
-      const int rA = base + lane / GS, rB = rA + ngroups;
-      const bool actA = rA < nrows, actB = rB < nrows;
-      dd* browA = B + (size_t)(actA ? rA : 0) * l;
-      dd* browB = B + (size_t)(actB ? rB : 0) * l;
-      dd vA[NC], vB[NC];
-#pragma unroll
-      for (int cc = 0; cc < NC; ++cc) {
-        const int t = gl + GS * cc;
-        vA[cc] = (actA && t < l) ? browA[t] : dd_make(0.0f);
-        vB[cc] = (actB && t < l) ? browB[t] : dd_make(0.0f);
-      }
-      dd sA = vA[0], sB = vB[0];
-#pragma unroll
-      for (int cc = 1; cc < NC; ++cc)
-        if (cc == ccj) {
-          sA = vA[cc];
-          sB = vB[cc];
-        }
-      const dd cA{__shfl_sync(0xffffffffu, sA.hi, src_lane), __shfl_sync(0xffffffffu, sA.lo, src_lane)};
-      const dd cB{__shfl_sync(0xffffffffu, sB.hi, src_lane), __shfl_sync(0xffffffffu, sB.lo, src_lane)};
-      upd_row(rA, actA, browA, vA, actA ? cA : dd_make(0.0f));
-      upd_row(rB, actB, browB, vB, actB ? cB : dd_make(0.0f));
     }
     mine = bk ? ((unsigned long long)(bk - 1u) << 32) | (0xffffffffu - (unsigned int)(row0 * l + be)) : 0ull;
     if (gepp_phase) {
