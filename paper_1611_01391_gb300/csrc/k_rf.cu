@@ -269,64 +269,133 @@ __global__ void __launch_bounds__(128) trsm_rows_kernel(const double* __restrict
   }
 }
 
+// Grid-wide barrier of a cooperative launch on a counter that only grows:
+// the n-th barrier waits until the counter reaches n gridDim.x.  Thread 0 of
+// each block arrives with a release add and polls with acquire loads,
+// bounded by 2 s (LRA_ETIMEOUT); every thread returns the same verdict.
+__device__ __forceinline__ bool coop_barrier(unsigned int* count, unsigned int target, JobStatus* js, int* flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+    const unsigned long long t0 = globaltimer_ns();
+    int ok = 1;
+    for (unsigned int it = 1;; ++it) {
+      if ((int)(ld_acquire_u32(count) - target) >= 0) break;
+      if ((it & 63u) == 0 && globaltimer_ns() - t0 > kWaitNs) {
+        set_status(js, LRA_ETIMEOUT);
+        ok = 0;
+        break;
+      }
+    }
+    *flag = ok;
+  }
+  __syncthreads();
+  return *flag != 0;
+}
+
+// Cooperative form of the FP64 Cholesky G + shift I = R^T R for k up to
+// 1024: G (upper triangle, from the partials) and R in global memory, one
+// grid barrier per column.  At step j every block forms the pivot row
+// R[j][c] = G[j][c] / R_jj itself (block 0 also stores it) and updates the
+// trailing rows a > j it owns (a mod gridDim == blockIdx).  The shift is
+// added to each diagonal entry when it becomes the pivot.  A non-positive
+// pivot: LRA_ESINGULAR (every block sees the same value and stops).
+__global__ void __launch_bounds__(256) chol_coop_kernel(const double* __restrict__ partials, int nparts, int k,
+                                                        double shift_rel, double* __restrict__ G,
+                                                        double* __restrict__ R, unsigned int* bar, JobStatus* js) {
+  __shared__ double Rj[1024];
+  __shared__ double red[8];
+  __shared__ int flag;
+  const int tid = threadIdx.x, nb = gridDim.x, b = blockIdx.x;
+  if (js->status != LRA_OK) return;
+  for (long long e = (long long)b * blockDim.x + tid; e < (long long)k * k; e += (long long)nb * blockDim.x) {
+    const int a = (int)(e / k), c = (int)(e - (long long)a * k);
+    double s = 0.0;
+    if (c >= a)
+      for (int q = 0; q < nparts; ++q) s += partials[(size_t)q * k * k + e];
+    G[e] = s;
+    R[e] = 0.0;
+  }
+  unsigned int nbar = 0;
+  if (!coop_barrier(bar, ++nbar * nb, js, &flag)) return;
+  // shift = shift_rel * trace(G), summed in a fixed order by every block
+  double tr = 0.0;
+  for (int a = tid; a < k; a += blockDim.x) tr += G[(size_t)a * k + a];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, off);
+  if ((tid & 31) == 0) red[tid >> 5] = tr;
+  __syncthreads();
+  double trace = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) trace += red[w];
+  const double shift = shift_rel * trace;
+  for (int j = 0; j < k; ++j) {
+    // row j final (and, at j = 0, every block done reading the diagonal)
+    if (!coop_barrier(bar, ++nbar * nb, js, &flag)) return;
+    const double d = G[(size_t)j * k + j] + shift;
+    if (!(d > 0.0)) {
+      if (b == 0 && tid == 0) set_status(js, LRA_ESINGULAR);
+      return;
+    }
+    const double rjj = sqrt(d);
+    for (int c = j + 1 + tid; c < k; c += blockDim.x) {
+      const double v = G[(size_t)j * k + c] / rjj;
+      Rj[c] = v;
+      if (b == 0) R[(size_t)j * k + c] = v;
+    }
+    if (b == 0 && tid == 0) R[(size_t)j * k + j] = rjj;
+    __syncthreads();
+    // the first trailing row this block owns, then every nb-th
+    int a0 = j + 1 + ((b - (j + 1)) % nb + nb) % nb;
+    for (int a = a0; a < k; a += nb) {
+      const double ra = Rj[a];
+      for (int c = a + tid; c < k; c += blockDim.x) G[(size_t)a * k + c] -= ra * Rj[c];
+    }
+  }
+}
+
 // The least squares solution from the factors R_1 .. R_p of (FA | Fb) =
 // Q R_p ... R_1 (upper, (n+1) x (n+1)): v = R_p ... R_1 e_n (the last column
-// of the product), then x = (R_1)_nn^{-1} ... (R_p)_nn^{-1} v[:n]; rho =
-// |v[n]| is the residual norm of the sampled problem.  One CTA; each row's
-// dot product is a block reduction.
+// of the product, one thread per row for each factor), then x =
+// (R_1)_nn^{-1} ... (R_p)_nn^{-1} v[:n] by back substitutions in warp 0;
+// rho = |v[n]| is the residual norm of the sampled problem.
 __global__ void __launch_bounds__(kSmallT) lsr_solve_kernel(const double* __restrict__ Rs, int p, int k,
-                                                            double* __restrict__ v, double* __restrict__ x,
+                                                            double* __restrict__ v_out, double* __restrict__ x_out,
                                                             double* __restrict__ rho, const JobStatus* js) {
   if (js->status != LRA_OK) return;
-  __shared__ double red[kSmallT / 32];
-  __shared__ double bc;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  __shared__ double v[1024], tmp[1024];
+  const int tid = threadIdx.x, lane = tid & 31;
   const int n = k - 1;
   const size_t kk = (size_t)k * k;
   for (int a = tid; a < k; a += blockDim.x) v[a] = Rs[(size_t)a * k + n];   // R_1 e_n
   __syncthreads();
-  for (int s = 1; s < p; ++s) {   // v <- R_{s+1} v, row a of an upper factor: sum_{c >= a}
+  for (int s = 1; s < p; ++s) {
     const double* Rm = Rs + s * kk;
-    for (int a = 0; a < k; ++a) {
+    for (int a = tid; a < k; a += blockDim.x) {
       double t = 0.0;
-      for (int c = a + tid; c < k; c += blockDim.x) t = fma(Rm[(size_t)a * k + c], v[c], t);
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-      if (lane == 0) red[warp] = t;
-      __syncthreads();
-      if (tid == 0) {
-        double u = 0.0;
-        for (int w2 = 0; w2 < nw; ++w2) u += red[w2];
-        bc = u;
-      }
-      __syncthreads();
-      if (tid == 0) x[a] = bc;   // staged; rows below a are not read again in this product
-      __syncthreads();
+      for (int c = a; c < k; ++c) t = fma(Rm[(size_t)a * k + c], v[c], t);
+      tmp[a] = t;
     }
-    for (int a = tid; a < k; a += blockDim.x) v[a] = x[a];
+    __syncthreads();
+    for (int a = tid; a < k; a += blockDim.x) v[a] = tmp[a];
     __syncthreads();
   }
   if (tid == 0) *rho = fabs(v[n]);
-  // x = (R_1)^{-1} ... (R_p)^{-1} v[:n] on the leading n x n blocks
-  for (int a = tid; a < n; a += blockDim.x) x[a] = v[a];
-  __syncthreads();
-  for (int s = p - 1; s >= 0; --s) {
-    const double* Rm = Rs + s * kk;
-    for (int a = n - 1; a >= 0; --a) {
-      double t = 0.0;
-      for (int c = a + 1 + tid; c < n; c += blockDim.x) t = fma(Rm[(size_t)a * k + c], x[c], t);
+  if (tid < 32) {
+    for (int s = p - 1; s >= 0; --s) {
+      const double* Rm = Rs + s * kk;
+      for (int a = n - 1; a >= 0; --a) {
+        double t = 0.0;
+        for (int c = a + 1 + lane; c < n; c += 32) t = fma(Rm[(size_t)a * k + c], v[c], t);
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-      if (lane == 0) red[warp] = t;
-      __syncthreads();
-      if (tid == 0) {
-        double u = 0.0;
-        for (int w2 = 0; w2 < nw; ++w2) u += red[w2];
-        x[a] = (x[a] - u) / Rm[(size_t)a * k + a];
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (lane == 0) v[a] = (v[a] - t) / Rm[(size_t)a * k + a];
+        __syncwarp();
       }
-      __syncthreads();
     }
   }
+  __syncthreads();
+  for (int a = tid; a < n; a += blockDim.x) x_out[a] = v[a];
+  for (int a = tid; a < k; a += blockDim.x) v_out[a] = v[a];
 }
 
 int gram_chunks(long long N, int k) {
@@ -388,6 +457,20 @@ cudaError_t launch_chol_big(const double* partials, int nparts, int k, double sh
                             JobStatus* js, cudaStream_t s) {
   chol_big_kernel<<<1, kSmallT, 0, s>>>(partials, nparts, k, shift_rel, G, R, js);
   return cudaGetLastError();
+}
+
+cudaError_t launch_chol_coop(const double* partials, int nparts, int k, double shift_rel, double* G, double* R,
+                             unsigned int* bar, JobStatus* js, int sms, cudaStream_t s) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_coop_kernel, 256, 0);
+  if (e) return e;
+  int grid = sms * (per_sm > 0 ? 1 : 0);
+  if (grid > k) grid = k;
+  if (grid < 1) grid = 1;
+  void* args[] = {(void*)&partials, (void*)&nparts, (void*)&k, (void*)&shift_rel, (void*)&G, (void*)&R,
+                  (void*)&bar, (void*)&js};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(chol_coop_kernel), dim3(grid), dim3(256), args, 0,
+                                     s);
 }
 
 cudaError_t launch_trsm_rows(const double* W, long long N, int k, const double* R, double* Q, const JobStatus* js,

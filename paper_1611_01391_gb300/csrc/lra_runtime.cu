@@ -1026,6 +1026,7 @@ lra_status lra_dual_lsr(lra_ctx* ctx, const lra_source* W, const int32_t* rows, 
   const size_t kk = (size_t)kc * kc;
   Layout lay;
   const size_t o_js = lay.take(sizeof(JobStatus)), o_rows = lay.take(sizeof(int) * k);
+  const size_t o_bar = lay.take(sizeof(unsigned int) * 4);   // grid-barrier counters, one per pass (zeroed)
   const size_t prefix = lay.off;
   const size_t o_W = lay.take(sizeof(double) * (size_t)k * kc), o_Qa = lay.take(sizeof(double) * (size_t)k * kc);
   const size_t o_p = lay.take(sizeof(double) * (size_t)nch * kk), o_G = lay.take(sizeof(double) * kk);
@@ -1045,6 +1046,7 @@ lra_status lra_dual_lsr(lra_ctx* ctx, const lra_source* W, const int32_t* rows, 
   double* Rs = reinterpret_cast<double*>(P(o_R));
   double *dv = reinterpret_cast<double*>(P(o_v)), *dx = reinterpret_cast<double*>(P(o_x));
   double* drho = reinterpret_cast<double*>(P(o_rho));
+  unsigned int* dbar = reinterpret_cast<unsigned int*>(P(o_bar));
   std::vector<unsigned char> hs(prefix, 0);
   JobStatus init{};
   init.status = LRA_OK;
@@ -1061,7 +1063,8 @@ lra_status lra_dual_lsr(lra_ctx* ctx, const lra_source* W, const int32_t* rows, 
     if ((e = launch_ts_gram_f64(in, k, kc, part, nch, js, st))) break;
     // the first passes - 2 passes (at least one) shifted, the last two plain
     const bool shift_here = p->shifted && s < std::max(1, passes - 2);
-    if ((e = launch_chol_big(part, nch, kc, shift_here ? shift_rel : 0.0, G, Rsp, js, st))) break;
+    if ((e = launch_chol_coop(part, nch, kc, shift_here ? shift_rel : 0.0, G, Rsp, dbar + s, js, ctx->sms, st)))
+      break;
     if (s + 1 < passes) {
       if ((e = launch_trsm_rows(in, k, kc, Rsp, outq, js, ctx->sms, st))) break;
       std::swap(in, outq);   // ping-pong: the gathered rows are not needed after the first pass
