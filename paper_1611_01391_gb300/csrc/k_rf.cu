@@ -253,7 +253,10 @@ __global__ void __launch_bounds__(kSmallT) chol_big_kernel(const double* __restr
 }
 
 // Q[i][:] = W[i][:] R^{-1} (R upper k x k): forward substitution along the
-// row, one thread per row (q_j = (w_j - sum_{c<j} q_c R_cj) / R_jj).
+// row, one thread per row (q_j = (w_j - sum_{c<j} q_c R_cj) / R_jj).  The
+// inner sum runs in 8 interleaved partial sums (c mod 8, the tail into the
+// first), added in a fixed order: dependent FP64 operations take tens of cycles each on this part,
+// so the chain, not the FP64 issue rate, sets the time.
 __global__ void __launch_bounds__(128) trsm_rows_kernel(const double* __restrict__ W, long long N, int k,
                                                         const double* __restrict__ R, double* __restrict__ Q,
                                                         const JobStatus* js) {
@@ -262,9 +265,15 @@ __global__ void __launch_bounds__(128) trsm_rows_kernel(const double* __restrict
     const double* w = W + i * k;
     double* q = Q + i * k;
     for (int j = 0; j < k; ++j) {
-      double v = w[j];
-      for (int c = 0; c < j; ++c) v = fma(-q[c], __ldg(R + (size_t)c * k + j), v);
-      q[j] = v / __ldg(R + (size_t)j * k + j);
+      double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      int c = 0;
+      for (; c + 8 <= j; c += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] = fma(q[c + u], __ldg(R + (size_t)(c + u) * k + j), acc[u]);
+      }
+      for (; c < j; ++c) acc[0] = fma(q[c], __ldg(R + (size_t)c * k + j), acc[0]);
+      const double sum = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+      q[j] = (w[j] - sum) / __ldg(R + (size_t)j * k + j);
     }
   }
 }
@@ -371,9 +380,14 @@ __global__ void __launch_bounds__(kSmallT) lsr_solve_kernel(const double* __rest
   for (int s = 1; s < p; ++s) {
     const double* Rm = Rs + s * kk;
     for (int a = tid; a < k; a += blockDim.x) {
-      double t = 0.0;
-      for (int c = a; c < k; ++c) t = fma(Rm[(size_t)a * k + c], v[c], t);
-      tmp[a] = t;
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      int c = a;
+      for (; c + 4 <= k; c += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] = fma(Rm[(size_t)a * k + c + u], v[c + u], acc[u]);
+      }
+      for (; c < k; ++c) acc[0] = fma(Rm[(size_t)a * k + c], v[c], acc[0]);
+      tmp[a] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     }
     __syncthreads();
     for (int a = tid; a < k; a += blockDim.x) v[a] = tmp[a];
