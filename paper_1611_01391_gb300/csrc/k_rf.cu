@@ -197,83 +197,28 @@ __global__ void __launch_bounds__(256) gather_rows_f64_kernel(SourceDev s, const
   }
 }
 
-// One CTA, FP64: G = sum of the partials (+ shift on the diagonal) and its
-// Cholesky factor R (upper, G = R^T R), right-looking; G and R in global
-// memory (k up to 1024).  A non-positive pivot: LRA_ESINGULAR.
-__global__ void __launch_bounds__(kSmallT) chol_big_kernel(const double* __restrict__ partials, int nparts, int k,
-                                                           double shift_rel, double* __restrict__ G,
-                                                           double* __restrict__ R, JobStatus* js) {
-  if (js->status != LRA_OK) return;
-  __shared__ double red[kSmallT / 32];
-  __shared__ int bad;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) bad = 0;
-  double tr = 0.0;
-  for (long long e = tid; e < (long long)k * k; e += blockDim.x) {
-    const int a = (int)(e / k), c = (int)(e - (long long)a * k);
-    double s = 0.0;
-    if (c >= a)
-      for (int b = 0; b < nparts; ++b) s += partials[(size_t)b * k * k + e];
-    G[e] = s;
-    R[e] = 0.0;
-    if (a == c) tr += s;
-  }
-  // shift = shift_rel * trace(G) = shift_rel * ||Y||_F^2 (fixed-order sum)
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, off);
-  if (lane == 0) red[warp] = tr;
-  __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    red[0] = shift_rel * t;
-  }
-  __syncthreads();
-  const double shift = red[0];
-  for (int a = tid; a < k; a += blockDim.x) G[(size_t)a * k + a] += shift;
-  __syncthreads();
-  for (int j = 0; j < k; ++j) {
-    const double d = G[(size_t)j * k + j];
-    if (!(d > 0.0)) {
-      if (tid == 0) bad = 1;
-      break;
-    }
-    const double rjj = sqrt(d);
-    for (int c = j + tid; c < k; c += blockDim.x) R[(size_t)j * k + c] = c == j ? rjj : G[(size_t)j * k + c] / rjj;
-    __syncthreads();
-    const int w = k - j - 1;
-    for (long long e = tid; e < (long long)w * w; e += blockDim.x) {
-      const int a = j + 1 + (int)(e / w), c = j + 1 + (int)(e % w);
-      if (c >= a) G[(size_t)a * k + c] -= R[(size_t)j * k + a] * R[(size_t)j * k + c];
-    }
-    __syncthreads();
-  }
-  __syncthreads();
-  if (bad && tid == 0) set_status(js, LRA_ESINGULAR);
-}
-
-// Q[i][:] = W[i][:] R^{-1} (R upper k x k): forward substitution along the
-// row, one thread per row (q_j = (w_j - sum_{c<j} q_c R_cj) / R_jj).  The
-// inner sum runs in 8 interleaved partial sums (c mod 8, the tail into the
-// first), added in a fixed order: dependent FP64 operations take tens of cycles each on this part,
-// so the chain, not the FP64 issue rate, sets the time.
-__global__ void __launch_bounds__(128) trsm_rows_kernel(const double* __restrict__ W, long long N, int k,
-                                                        const double* __restrict__ R, double* __restrict__ Q,
+// Q[i][:] = W[i][:] R^{-1} (R upper k x k, given as its transpose Rt, lower,
+// row j of Rt = column j of R): forward substitution along the row, one warp
+// per row: q_j = (w_j - sum_{c<j} q_c Rt[j][c]) / Rt[j][j], the sum split
+// over the lanes (c = lane mod 32, contiguous reads of Rt's row j) and
+// reduced in a fixed order; lane 0 stores q_j, which the warp reads back.
+__global__ void __launch_bounds__(256) trsm_rows_kernel(const double* __restrict__ W, long long N, int k,
+                                                        const double* __restrict__ Rt, double* __restrict__ Q,
                                                         const JobStatus* js) {
   if (js->status != LRA_OK) return;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long i = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < N; i += nwarps) {
     const double* w = W + i * k;
     double* q = Q + i * k;
     for (int j = 0; j < k; ++j) {
-      double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-      int c = 0;
-      for (; c + 8 <= j; c += 8) {
+      const double* rt = Rt + (size_t)j * k;
+      double acc = 0.0;
+      for (int c = lane; c < j; c += 32) acc = fma(q[c], __ldg(rt + c), acc);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc[u] = fma(q[c + u], __ldg(R + (size_t)(c + u) * k + j), acc[u]);
-      }
-      for (; c < j; ++c) acc[0] = fma(q[c], __ldg(R + (size_t)c * k + j), acc[0]);
-      const double sum = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
-      q[j] = (w[j] - sum) / __ldg(R + (size_t)j * k + j);
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      if (lane == 0) q[j] = (w[j] - acc) / __ldg(rt + j);
+      __syncwarp();
     }
   }
 }
@@ -311,7 +256,8 @@ __device__ __forceinline__ bool coop_barrier(unsigned int* count, unsigned int t
 // pivot: LRA_ESINGULAR (every block sees the same value and stops).
 __global__ void __launch_bounds__(256) chol_coop_kernel(const double* __restrict__ partials, int nparts, int k,
                                                         double shift_rel, double* __restrict__ G,
-                                                        double* __restrict__ R, unsigned int* bar, JobStatus* js) {
+                                                        double* __restrict__ R, double* __restrict__ Rt,
+                                                        unsigned int* bar, JobStatus* js) {
   __shared__ double Rj[1024];
   __shared__ double red[8];
   __shared__ int flag;
@@ -324,6 +270,7 @@ __global__ void __launch_bounds__(256) chol_coop_kernel(const double* __restrict
       for (int q = 0; q < nparts; ++q) s += partials[(size_t)q * k * k + e];
     G[e] = s;
     R[e] = 0.0;
+    Rt[e] = 0.0;
   }
   unsigned int nbar = 0;
   if (!coop_barrier(bar, ++nbar * nb, js, &flag)) return;
@@ -349,9 +296,15 @@ __global__ void __launch_bounds__(256) chol_coop_kernel(const double* __restrict
     for (int c = j + 1 + tid; c < k; c += blockDim.x) {
       const double v = G[(size_t)j * k + c] / rjj;
       Rj[c] = v;
-      if (b == 0) R[(size_t)j * k + c] = v;
+      if (b == 0) {
+        R[(size_t)j * k + c] = v;
+        Rt[(size_t)c * k + j] = v;
+      }
     }
-    if (b == 0 && tid == 0) R[(size_t)j * k + j] = rjj;
+    if (b == 0 && tid == 0) {
+      R[(size_t)j * k + j] = rjj;
+      Rt[(size_t)j * k + j] = rjj;
+    }
     __syncthreads();
     // the first trailing row this block owns, then every nb-th
     int a0 = j + 1 + ((b - (j + 1)) % nb + nb) % nb;
@@ -467,14 +420,8 @@ cudaError_t launch_gather_rows_f64(const SourceDev& src, const int* rows, int k,
   return cudaGetLastError();
 }
 
-cudaError_t launch_chol_big(const double* partials, int nparts, int k, double shift_rel, double* G, double* R,
-                            JobStatus* js, cudaStream_t s) {
-  chol_big_kernel<<<1, kSmallT, 0, s>>>(partials, nparts, k, shift_rel, G, R, js);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_chol_coop(const double* partials, int nparts, int k, double shift_rel, double* G, double* R,
-                             unsigned int* bar, JobStatus* js, int sms, cudaStream_t s) {
+                             double* Rt, unsigned int* bar, JobStatus* js, int sms, cudaStream_t s) {
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_coop_kernel, 256, 0);
   if (e) return e;
@@ -482,16 +429,16 @@ cudaError_t launch_chol_coop(const double* partials, int nparts, int k, double s
   if (grid > k) grid = k;
   if (grid < 1) grid = 1;
   void* args[] = {(void*)&partials, (void*)&nparts, (void*)&k, (void*)&shift_rel, (void*)&G, (void*)&R,
-                  (void*)&bar, (void*)&js};
+                  (void*)&Rt, (void*)&bar, (void*)&js};
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(chol_coop_kernel), dim3(grid), dim3(256), args, 0,
                                      s);
 }
 
-cudaError_t launch_trsm_rows(const double* W, long long N, int k, const double* R, double* Q, const JobStatus* js,
+cudaError_t launch_trsm_rows(const double* W, long long N, int k, const double* Rt, double* Q, const JobStatus* js,
                              int sms, cudaStream_t s) {
-  long long g = (N + 127) / 128;
-  if (g > (long long)sms * 4) g = (long long)sms * 4;
-  trsm_rows_kernel<<<(int)g, 128, 0, s>>>(W, N, k, R, Q, js);
+  long long g = (N + 7) / 8;   // 8 warps (rows) per block
+  if (g > (long long)sms * 8) g = (long long)sms * 8;
+  trsm_rows_kernel<<<(int)g, 256, 0, s>>>(W, N, k, Rt, Q, js);
   return cudaGetLastError();
 }
 

@@ -168,11 +168,9 @@ cudaError_t launch_pchol(const double* partials, int nparts, int k, int r, doubl
 cudaError_t launch_rf_finish(const double* Q1, long long N, int r, const double* Linv, float* U, const JobStatus* js,
                              int sms, cudaStream_t s);
 cudaError_t launch_gather_rows_f64(const SourceDev& src, const int* rows, int k, double* FW, int sms, cudaStream_t s);
-cudaError_t launch_chol_big(const double* partials, int nparts, int k, double shift_rel, double* G, double* R,
-                            JobStatus* js, cudaStream_t s);
 cudaError_t launch_chol_coop(const double* partials, int nparts, int k, double shift_rel, double* G, double* R,
-                             unsigned int* bar, JobStatus* js, int sms, cudaStream_t s);
-cudaError_t launch_trsm_rows(const double* W, long long N, int k, const double* R, double* Q, const JobStatus* js,
+                             double* Rt, unsigned int* bar, JobStatus* js, int sms, cudaStream_t s);
+cudaError_t launch_trsm_rows(const double* W, long long N, int k, const double* Rt, double* Q, const JobStatus* js,
                              int sms, cudaStream_t s);
 cudaError_t launch_lsr_solve(const double* Rs, int p, int k, double* v, double* x, double* rho, const JobStatus* js,
                              cudaStream_t s);

@@ -1030,6 +1030,7 @@ lra_status lra_dual_lsr(lra_ctx* ctx, const lra_source* W, const int32_t* rows, 
   const size_t prefix = lay.off;
   const size_t o_W = lay.take(sizeof(double) * (size_t)k * kc), o_Qa = lay.take(sizeof(double) * (size_t)k * kc);
   const size_t o_p = lay.take(sizeof(double) * (size_t)nch * kk), o_G = lay.take(sizeof(double) * kk);
+  const size_t o_Rt = lay.take(sizeof(double) * kk);
   const size_t o_R = lay.take(sizeof(double) * kk * passes);
   const size_t o_v = lay.take(sizeof(double) * kc), o_x = lay.take(sizeof(double) * kc);
   const size_t o_rho = lay.take(sizeof(double));
@@ -1044,6 +1045,7 @@ lra_status lra_dual_lsr(lra_ctx* ctx, const lra_source* W, const int32_t* rows, 
   double *FW = reinterpret_cast<double*>(P(o_W)), *Qa = reinterpret_cast<double*>(P(o_Qa));
   double *part = reinterpret_cast<double*>(P(o_p)), *G = reinterpret_cast<double*>(P(o_G));
   double* Rs = reinterpret_cast<double*>(P(o_R));
+  double* Rt = reinterpret_cast<double*>(P(o_Rt));
   double *dv = reinterpret_cast<double*>(P(o_v)), *dx = reinterpret_cast<double*>(P(o_x));
   double* drho = reinterpret_cast<double*>(P(o_rho));
   unsigned int* dbar = reinterpret_cast<unsigned int*>(P(o_bar));
@@ -1063,10 +1065,10 @@ lra_status lra_dual_lsr(lra_ctx* ctx, const lra_source* W, const int32_t* rows, 
     if ((e = launch_ts_gram_f64(in, k, kc, part, nch, js, st))) break;
     // the first passes - 2 passes (at least one) shifted, the last two plain
     const bool shift_here = p->shifted && s < std::max(1, passes - 2);
-    if ((e = launch_chol_coop(part, nch, kc, shift_here ? shift_rel : 0.0, G, Rsp, dbar + s, js, ctx->sms, st)))
+    if ((e = launch_chol_coop(part, nch, kc, shift_here ? shift_rel : 0.0, G, Rsp, Rt, dbar + s, js, ctx->sms, st)))
       break;
     if (s + 1 < passes) {
-      if ((e = launch_trsm_rows(in, k, kc, Rsp, outq, js, ctx->sms, st))) break;
+      if ((e = launch_trsm_rows(in, k, kc, Rt, outq, js, ctx->sms, st))) break;
       std::swap(in, outq);   // ping-pong: the gathered rows are not needed after the first pass
     }
   }
