@@ -859,6 +859,32 @@ def run_rf_lsr(dev, n=32768, r=64, l=96, reps=3):
     return out
 
 
+def run_profile_rf_lsr(n=32768, r=64, l=96):
+    """Two range finder calls and two dual LSR calls (the second of each is
+    the one a launch list reads), nothing else (for ncu)."""
+    import numpy as np
+    import torch
+    import paper_1611_01391_gb300 as L
+    import workloads as W
+    dev = torch.device("cuda:0")
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(W.BASE_SEED + 14000)
+    M = torch.randn((n, r), device=dev, generator=gen) @ torch.randn((r, n), device=dev, generator=gen)
+    M.mul_(1.0 / np.sqrt(r)).add_(torch.randn((n, n), device=dev, generator=gen), alpha=1e-4)
+    src = L.make_source("dense", a=M)
+    ctx = L.Context(0)
+    U = torch.empty((n, r), dtype=torch.float32, device=dev)
+    V = torch.empty((r, n), dtype=torch.float32, device=dev)
+    for i in range(2):
+        res = L.lra_range_finder(ctx.ctx, src, W.draw_indices(W.BASE_SEED + 14100 + i, n, l), r, U, V)
+    A, b = W.lsr_problem(W.BASE_SEED + 14300, "gaussian", 16384, 400)
+    Wm = torch.from_numpy(np.ascontiguousarray(np.concatenate([A, b[:, None]], axis=1))).to(dev)
+    for i in range(2):
+        x, rho = L.lra_dual_lsr(ctx.ctx, L.make_source("dense", a=Wm), W.rng_for(W.BASE_SEED + 14400).permutation(16384)[:2400])
+    ctx.close()
+    print(json.dumps({"profile_rf_lsr": True, "rf_status": res["status"], "lsr_rho": rho}))
+
+
 def run_profile_preprocess(n, d=3, k=64):
     """Three transforms G = H_{n,d} M H_{n,d} and one C-A solve on the
     materialised source, nothing else (for ncu)."""
@@ -1369,6 +1395,9 @@ def main():
     ap.add_argument("--profile-preprocess", type=int, default=0, metavar="N",
                     help="run the one-pass Hadamard transform (d = 3) of a stored N x N matrix "
                          "three times, solve once on the materialised source, and exit (the command ncu captures)")
+    ap.add_argument("--profile-rf-lsr", action="store_true",
+                    help="run one range finder call (stored 32768 x 32768, l = 96, r = 64) and one dual LSR call "
+                         "((k, m, n) = (2400, 16384, 400)) after a warm-up of each, and exit (the command ncu captures)")
     ap.add_argument("--no-legs", action="store_true",
                     help="default workload only: skip the batched and served legs")
     args = ap.parse_args()
@@ -1382,6 +1411,9 @@ def main():
         return
     if args.profile_preprocess:
         run_profile_preprocess(args.profile_preprocess)
+        return
+    if args.profile_rf_lsr:
+        run_profile_rf_lsr()
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
