@@ -251,7 +251,7 @@ cudaError_t launch_lev_project(const float* S, long long N, int l, long long si,
   cudaError_t e = smem_optin(reinterpret_cast<const void*>(lev_project_kernel), sm);
   if (e) return e;
   lev_project_kernel<<<(int)g, kLevThreads, sm, st>>>(S, N, l, si, stv, G, k, Y, js);
-  lev_gram_kernel<<<nparts, kGramThreads, 0, st>>>(Y, N, k, partials, js);
+  if (nparts > 0) lev_gram_kernel<<<nparts, kGramThreads, 0, st>>>(Y, N, k, partials, js);
   return cudaGetLastError();
 }
 

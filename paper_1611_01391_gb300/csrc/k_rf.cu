@@ -66,30 +66,38 @@ __global__ void __launch_bounds__(kGt * kGt) ts_gram_kernel(const T* __restrict_
 
 // One CTA: G = sum of the partials (fixed order), pivoted Cholesky
 // G(piv, piv) = R^T R with the largest remaining diagonal as pivot (ties to
-// the smaller position), the numerical rank nr = #{R_jj > rank_tol R_00}
+// the smaller column index), the numerical rank nr = #{R_jj > rank_tol R_00}
 // (stopping there), and for r <= nr the l x r matrix Gm = P R_r^{-1}
 // (row piv[s] of Gm is row s of R_r^{-1}, other rows zero), so that
 // Y Gm = Y(:, piv[:r]) R_r^{-1}.  Below the target rank: LRA_ESINGULAR.
-// Shared memory: G (k x k) and R (k x k).
+// No interchanges: G keeps the original order, step j writes row j of the
+// factor as Rr[j][c] (column c of the original order) and updates the
+// Schur complement of the columns not yet chosen; warp 0 finds each pivot
+// with shuffles.  Shared memory: G (k x k) and Rr (k x k).
 __global__ void __launch_bounds__(kSmallT) pchol_kernel(const double* __restrict__ partials, int nparts, int k,
                                                         int r, double rank_tol, double* __restrict__ Gm,
                                                         int* __restrict__ piv_out, JobStatus* js) {
   if (js->status != LRA_OK) return;
   extern __shared__ double pc_sm[];
   double* G = pc_sm;
-  double* R = pc_sm + k * k;
+  double* Rr = pc_sm + k * k;
   __shared__ int piv[kMaxL];
-  __shared__ int nr_s;
-  const int tid = threadIdx.x;
+  __shared__ unsigned char done[kMaxL];
+  __shared__ int p_s, nr_s;
+  __shared__ double r00_s;
+  const int tid = threadIdx.x, lane = tid & 31;
   for (int e = tid; e < k * k; e += blockDim.x) {
     const int a = e / k, c = e - a * k;
     double s = 0.0;
     if (c >= a)
       for (int b = 0; b < nparts; ++b) s += partials[(size_t)b * k * k + e];
     G[e] = s;
-    R[e] = 0.0;
+    Rr[e] = 0.0;
   }
-  if (tid < k) piv[tid] = tid;
+  if (tid < k) {
+    piv[tid] = tid;
+    done[tid] = 0;
+  }
   if (tid == 0) nr_s = k;
   __syncthreads();
   for (int e = tid; e < k * k; e += blockDim.x) {
@@ -97,69 +105,76 @@ __global__ void __launch_bounds__(kSmallT) pchol_kernel(const double* __restrict
     if (c < a) G[e] = G[c * k + a];
   }
   __syncthreads();
-  double r00 = 0.0;
   for (int j = 0; j < k; ++j) {
-    if (tid == 0) {
-      int p = j;
-      for (int q = j + 1; q < k; ++q)
-        if (G[q * k + q] > G[p * k + p]) p = q;
-      if (p != j) {   // symmetric interchange of rows and columns j, p; R's computed rows follow
-        for (int q = 0; q < k; ++q) {
-          const double t = G[j * k + q];
-          G[j * k + q] = G[p * k + q];
-          G[p * k + q] = t;
+    if (tid < 32) {
+      // the largest remaining diagonal, ties to the smaller column
+      double best = -1.0;
+      int bp = k;
+      for (int q = lane; q < k; q += 32)
+        if (!done[q] && G[q * k + q] > best) {
+          best = G[q * k + q];
+          bp = q;
         }
-        for (int q = 0; q < k; ++q) {
-          const double t = G[q * k + j];
-          G[q * k + j] = G[q * k + p];
-          G[q * k + p] = t;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const int op = __shfl_xor_sync(0xffffffffu, bp, off);
+        if (ob > best || (ob == best && op < bp)) {
+          best = ob;
+          bp = op;
         }
-        for (int q = 0; q < j; ++q) {
-          const double t = R[q * k + j];
-          R[q * k + j] = R[q * k + p];
-          R[q * k + p] = t;
-        }
-        const int t = piv[j];
-        piv[j] = piv[p];
-        piv[p] = t;
       }
-      const double d = G[j * k + j];
-      const double rjj = d > 0.0 ? sqrt(d) : 0.0;
-      if (j == 0) r00 = rjj;
-      if (!(rjj > rank_tol * r00) || !(rjj > 0.0)) {
-        nr_s = j;
-      } else {
-        R[j * k + j] = rjj;
+      if (lane == 0) {
+        const double d = bp < k ? G[bp * k + bp] : 0.0;
+        const double rjj = d > 0.0 ? sqrt(d) : 0.0;
+        if (j == 0) r00_s = rjj;
+        if (bp >= k || !(rjj > rank_tol * r00_s) || !(rjj > 0.0)) {
+          nr_s = j;
+        } else {
+          Rr[j * k + bp] = rjj;
+          piv[j] = bp;
+          done[bp] = 1;
+          p_s = bp;
+        }
       }
     }
     __syncthreads();
     if (nr_s <= j) break;
-    const double rjj = R[j * k + j];
-    for (int c = j + 1 + tid; c < k; c += blockDim.x) R[j * k + c] = G[j * k + c] / rjj;
+    const int p = p_s;
+    const double rjj = Rr[j * k + p];
+    for (int c = tid; c < k; c += blockDim.x)
+      if (!done[c]) Rr[j * k + c] = G[p * k + c] / rjj;
     __syncthreads();
-    // Schur complement of the trailing block
-    const int w = k - j - 1;
-    for (int e = tid; e < w * w; e += blockDim.x) {
-      const int a = j + 1 + e / w, c = j + 1 + e % w;
-      G[a * k + c] -= R[j * k + a] * R[j * k + c];
+    // Schur complement of the columns not chosen yet
+    for (int e = tid; e < k * k; e += blockDim.x) {
+      const int a = e / k, c = e - a * k;
+      if (!done[a] && !done[c]) G[e] -= Rr[j * k + a] * Rr[j * k + c];
     }
     __syncthreads();
   }
   const int nr = nr_s;
-  if (tid == 0) js->k_eff = nr;
+  // the unchosen columns follow in their original order (a complete permutation)
+  if (tid == 0) {
+    js->k_eff = nr;
+    int s = nr;
+    for (int q = 0; q < k; ++q)
+      if (!done[q]) piv[s++] = q;
+  }
+  __syncthreads();
   for (int q = tid; q < k; q += blockDim.x) piv_out[q] = piv[q];
   if (nr < r) {
     if (tid == 0) set_status(js, LRA_ESINGULAR);
     return;
   }
-  // Gm = P R_r^{-1}: column t of R_r^{-1} by back substitution (thread t)
+  // Gm = P R_r^{-1}: column t of R_r^{-1} by back substitution (thread t),
+  // R[s][q] = Rr[s][piv[q]] (row s of the factor, pivoted column q)
   for (int e = tid; e < k * r; e += blockDim.x) Gm[e] = 0.0;
   __syncthreads();
   for (int t = tid; t < r; t += blockDim.x) {
     for (int s = t; s >= 0; --s) {
       double v = (s == t) ? 1.0 : 0.0;
-      for (int q = s + 1; q <= t; ++q) v -= R[s * k + q] * Gm[(size_t)piv[q] * r + t];
-      Gm[(size_t)piv[s] * r + t] = v / R[s * k + s];
+      for (int q = s + 1; q <= t; ++q) v -= Rr[s * k + piv[q]] * Gm[(size_t)piv[q] * r + t];
+      Gm[(size_t)piv[s] * r + t] = v / Rr[s * k + piv[s]];
     }
   }
 }

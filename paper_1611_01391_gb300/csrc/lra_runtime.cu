@@ -901,7 +901,7 @@ lra_status lra_range_finder(lra_ctx* ctx, const lra_source* src, const int32_t* 
       return LRA_ECUDA;
     }
   }
-  const int nch = ts_gram_chunks(m, l), npm = lev_partials(m);
+  const int nch = ts_gram_chunks(m, l), nch2 = ts_gram_chunks(m, r);
   const int nres = q > 0 ? sampled_residual_partials(q, sN) : 1;
   Layout lay;
   const size_t o_js = lay.take(sizeof(JobStatus)), o_J = lay.take(sizeof(int) * l);
@@ -912,7 +912,7 @@ lra_status lra_range_finder(lra_ctx* ctx, const lra_source* src, const int32_t* 
   const size_t o_p1 = lay.take(sizeof(double) * (size_t)nch * l * l);
   const size_t o_Gm = lay.take(sizeof(double) * l * r), o_piv = lay.take(sizeof(int) * l);
   const size_t o_Q1 = lay.take(sizeof(double) * (size_t)m * r);
-  const size_t o_p2 = lay.take(sizeof(double) * (size_t)npm * r * r), o_Li = lay.take(sizeof(double) * r * r);
+  const size_t o_p2 = lay.take(sizeof(double) * (size_t)nch2 * r * r), o_Li = lay.take(sizeof(double) * r * r);
   const size_t o_cuq = lay.take(sizeof(float) * std::max<size_t>(2 * (size_t)q * r, 1));
   const size_t o_pr = lay.take(sizeof(double) * 3 * nres);
   const size_t bytes = lay.off;
@@ -956,9 +956,9 @@ lra_status lra_range_finder(lra_ctx* ctx, const lra_source* src, const int32_t* 
                 : launch_gather_cols(sd, dJ, l, Y, js, 0, ctx->sms, st)) &&
       !(e = launch_ts_gram_f32(Y, m, l, l, 1, p1, nch, js, st)) &&
       !(e = launch_pchol(p1, nch, l, r, p->rank_tol, Gm, dpiv, js, st)) &&
-      !(e = launch_lev_project(Y, m, l, l, 1, Gm, r, Q1, p2, npm, js, st)) &&
+      !(e = launch_lev_project(Y, m, l, l, 1, Gm, r, Q1, nullptr, 0, js, st)) &&
       // CholeskyQR2: the orthonormal factor U = Q1 R2^{-1}
-      !(e = launch_lev_chol(p2, npm, r, Linv, js, st)) &&
+      !(e = launch_ts_gram_f64(Q1, m, r, p2, nch2, js, st)) && !(e = launch_lev_chol(p2, nch2, r, Linv, js, st)) &&
       !(e = launch_rf_finish(Q1, m, r, Linv, out->U, js, ctx->sms, st)) &&
       !(e = cudaMemcpyAsync(&hjs, js, sizeof(JobStatus), cudaMemcpyDeviceToHost, st)) &&
       !(e = cudaMemcpyAsync(hpiv.data(), dpiv, sizeof(int) * l, cudaMemcpyDeviceToHost, st)))
