@@ -365,3 +365,22 @@ def test_fixed_point_exit_keeps_the_whole_log(ctx):
     assert res.info.sweeps_done == 12
     assert res.info.swaps_total == sum(1 for d in ref.trace if d[1] == O.SWAP)
     check_nucleus(res.U, res.sigma, res.info.k_eff, O.Cauchy(x, y, "fp32").block(res.I, res.J), k)
+
+
+def test_fixed_point_exit_on_a_stored_matrix(ctx):
+    """The same on a stored FP32 matrix (strips gathered between the
+    half-steps, skipped once the job stops): a rank-10 matrix plus noise,
+    budget of 10 sweeps, log, index sets and sweep count as the oracle's."""
+    m, n, k, l = 2500, 1800, 10, 12
+    A32 = W.factor_gaussian(W.BASE_SEED + 910, m, n, k, 1e-5)
+    J0 = W.draw_indices(W.BASE_SEED + 911, n, l)
+    res = gpu_solve(ctx, L.make_source("dense", a=torch.from_numpy(A32).to(DEV)), m, n, J0, k, l, 10)
+    ref = O.cross_approximation(O.Dense(A32), J0, k=k, sweeps=10, delta=DELTA, rank_tol=GPU_TAU)
+    ncmp, div = compare_traces(res.trace, ref.trace, DELTA)
+    assert div is None and ncmp == len(ref.trace)
+    assert sum(1 for d in ref.trace if d[1] == O.STOP) == 20
+    assert list(res.I) == ref.I and list(res.J) == ref.J
+    assert res.info.sweeps_done == 10
+    # the returned strips are those of the final index sets
+    np.testing.assert_array_equal(res.C, A32[:, res.J])
+    np.testing.assert_array_equal(res.R, A32[res.I, :])
