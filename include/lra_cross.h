@@ -555,6 +555,12 @@ typedef struct {
   int64_t resid_q, resid_s;   /* optional Appendix F sample (0 = none)                  */
   const int32_t* resid_rows;  /* host, resid_q distinct rows                            */
   const int32_t* resid_cols;  /* host, resid_s distinct columns                         */
+  /* Multiplier (Section 8.1's ASPH family, Section 3's recipe (i) for
+   * mult_d = 0): column t of H is mult_sign[t] times column J[t] of the
+   * d-abridged Hadamard matrix H_{n,d} (2^d must divide n); mult_d = 0 is
+   * the sub-identity multiplier e_J (Y = M[:, J], mult_sign ignored). */
+  int32_t mult_d;             /* 0 .. 10                                                */
+  const float* mult_sign;     /* host, l signs +-1, or NULL (all +1)                    */
 } lra_rf_params;
 
 typedef struct {
@@ -570,7 +576,9 @@ typedef struct {
 
 /* Algorithm 5.1 (LRA via range finder), variant (a), with the sub-identity
  * multiplier H = (e_J[0], ..., e_J[l-1]) (Section 3's superfast recipe (i):
- * Y = M H = M[:, J] involves no flops): Y is gathered, its rank-revealing
+ * Y = M H = M[:, J] involves no flops) or an ASPH multiplier (mult_d > 0:
+ * each entry of Y a signed sum of 2^d entries of M's row, in the order of
+ * the recursive Hadamard steps, in FP32): Y is formed, its rank-revealing
  * QR is computed as pivoted Cholesky of the FP64 Gram matrix Y^T Y (the
  * pivots of QR with column pivoting in exact arithmetic) followed by a
  * CholeskyQR2 pass for the orthonormal factor, U = the r leftmost columns,
@@ -592,6 +600,11 @@ typedef struct {
                                  2^-53 ||Y||_F^2 (shifted CholeskyQR; each shifted pass
                                  divides the condition number by about s^(-1/2) ||Y||,
                                  so 4 passes reach condition numbers near 1e14)         */
+  /* Multiplier: row t of F is mult_sign[t] times row rows[t] of H_{m,d}
+   * (the ASPH family of Section 8.1; 2^d must divide m); mult_d = 0 is the
+   * sub-identity multiplier that keeps the rows (mult_sign ignored). */
+  int32_t mult_d;             /* 0 .. 10                                                */
+  const float* mult_sign;     /* host, k signs +-1, or NULL (all +1)                    */
 } lra_lsr_params;
 
 typedef struct {
@@ -601,7 +614,9 @@ typedef struct {
 
 /* Problem 3.1 through Algorithm 3.1 with the multiplier F = sqrt(m/k)
  * (I_k | O) P (Section 3, "Superfast dual LSR": a permutation followed by a
- * sub-identity matrix, no flops): W = (A | b) is an m x (n+1) stored
+ * sub-identity matrix, no flops), or with k rows of an ASPH multiplier
+ * (mult_d > 0: each row of F W a signed sum of 2^d rows of W in the order of
+ * the recursive Hadamard steps, in FP64): W = (A | b) is an m x (n+1) stored
  * matrix (LRA_DENSE_F64 or LRA_DENSE_F32; the last column is b); the k rows
  * `rows` (host, distinct, n+1 <= k <= m, n+1 <= 1024) are gathered in FP64
  * and x = argmin ||A[rows] x - b[rows]|| is computed by CholeskyQR

@@ -176,7 +176,8 @@ _pre_materialize = _sig("lra_preprocess_materialize", ctypes.c_int, ctypes.POINT
                         ctypes.c_int64, ctypes.c_void_p)
 class lra_rf_params(ctypes.Structure):
     _fields_ = [("r", ctypes.c_int32), ("rank_tol", ctypes.c_double), ("resid_q", ctypes.c_int64),
-                ("resid_s", ctypes.c_int64), ("resid_rows", ctypes.c_void_p), ("resid_cols", ctypes.c_void_p)]
+                ("resid_s", ctypes.c_int64), ("resid_rows", ctypes.c_void_p), ("resid_cols", ctypes.c_void_p),
+                ("mult_d", ctypes.c_int32), ("mult_sign", ctypes.c_void_p)]
 
 
 class lra_rf_out(ctypes.Structure):
@@ -185,7 +186,8 @@ class lra_rf_out(ctypes.Structure):
 
 
 class lra_lsr_params(ctypes.Structure):
-    _fields_ = [("passes", ctypes.c_int32), ("shifted", ctypes.c_int32)]
+    _fields_ = [("passes", ctypes.c_int32), ("shifted", ctypes.c_int32), ("mult_d", ctypes.c_int32),
+                ("mult_sign", ctypes.c_void_p)]
 
 
 class lra_lsr_out(ctypes.Structure):
@@ -303,14 +305,19 @@ def lra_maxvol_noalloc(strip_ptr, N, l, row_stride, col_stride, pos_ptr, xinv_pt
 
 
 def lra_range_finder(ctx, src: lra_source, J, r: int, U, V, rank_tol: float = 1e-6, resid_rows=None,
-                     resid_cols=None):
-    """Algorithm 5.1a with the sub-identity multiplier e_J: U (m x r) and V
-    (r x n) into the given float32 device tensors.  Returns a dict with piv,
-    nrank, est_rel_err and gemm_mode."""
+                     resid_cols=None, mult_d: int = 0, mult_sign=None):
+    """Algorithm 5.1a with the sub-identity multiplier e_J (mult_d = 0) or
+    the ASPH multiplier whose column t is mult_sign[t] times column J[t] of
+    H_{n,mult_d}: U (m x r) and V (r x n) into the given float32 device
+    tensors.  Returns a dict with piv, nrank, est_rel_err and gemm_mode."""
     import numpy as np
     Jh = np.ascontiguousarray(J, dtype=np.int32)
-    p = lra_rf_params(r, rank_tol, 0, 0, None, None)
+    p = lra_rf_params(r, rank_tol, 0, 0, None, None, mult_d, None)
     keep = []
+    if mult_sign is not None:
+        sg = np.ascontiguousarray(mult_sign, dtype=np.float32)
+        keep.append(sg)
+        p.mult_sign = sg.ctypes.data
     if resid_rows is not None:
         rr = np.ascontiguousarray(resid_rows, dtype=np.int32)
         rc = np.ascontiguousarray(resid_cols, dtype=np.int32)
@@ -329,14 +336,21 @@ def lra_range_finder(ctx, src: lra_source, J, r: int, U, V, rank_tol: float = 1e
     return res
 
 
-def lra_dual_lsr(ctx, W: lra_source, rows, passes: int = 3, shifted: bool = True):
-    """Algorithm 3.1 with a sub-identity multiplier: x (host FP64, n) and
-    the sampled residual norm for W = (A | b) and the kept rows."""
+def lra_dual_lsr(ctx, W: lra_source, rows, passes: int = 3, shifted: bool = True, mult_d: int = 0,
+                 mult_sign=None):
+    """Algorithm 3.1 with a sub-identity multiplier (mult_d = 0: the kept
+    rows) or the ASPH multiplier whose row t is mult_sign[t] times row
+    rows[t] of H_{m,mult_d}: x (host FP64, n) and the sampled residual norm
+    for W = (A | b)."""
     import numpy as np
     rh = np.ascontiguousarray(rows, dtype=np.int32)
     x = np.zeros(W.n - 1)
     rho = np.zeros(1)
-    p = lra_lsr_params(passes, int(bool(shifted)))
+    p = lra_lsr_params(passes, int(bool(shifted)), mult_d, None)
+    sg = None
+    if mult_sign is not None:
+        sg = np.ascontiguousarray(mult_sign, dtype=np.float32)
+        p.mult_sign = sg.ctypes.data
     o = lra_lsr_out(x.ctypes.data, rho.ctypes.data)
     _check(_dual_lsr(ctx, ctypes.byref(W), rh.ctypes.data, len(rh), ctypes.byref(p), ctypes.byref(o)), ctx)
     return x, float(rho[0])

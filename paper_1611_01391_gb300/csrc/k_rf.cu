@@ -380,6 +380,56 @@ __global__ void __launch_bounds__(kSmallT) lsr_solve_kernel(const double* __rest
   for (int a = tid; a < k; a += blockDim.x) v_out[a] = v[a];
 }
 
+// ASPH multipliers (Section 8.1): Y[i][t] = sign[t] (M H_{n,d})[i][J[t]],
+// with (b, o) = divmod(J[t], n / 2^d) the signed sum over q of
+// M[i][q (n / 2^d) + o] in the order of the recursive Hadamard steps, in
+// FP32 (the butterfly order of the pre-processed entries).
+__global__ void __launch_bounds__(256) asph_cols_kernel(const float* __restrict__ M, long long lda, long long m,
+                                                        long long sn, int d, const int* __restrict__ J,
+                                                        const float* __restrict__ sign, int l,
+                                                        float* __restrict__ Y) {
+  const long long total = m * l;
+  const int D = 1 << d;
+  float stk[kMaxPreD + 1];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / l;
+    const int t = (int)(e - i * l);
+    const long long y = __ldg(J + t);
+    const long long b = y / sn, o = y - b * sn;
+    const float* row = M + i * lda + o;
+    float acc = 0.0f;
+    for (int q = 0; q < D; ++q) acc = butterfly_push(stk, q, __ldg(row + q * sn), (unsigned)b);
+    Y[e] = __ldg(sign + t) * acc;
+  }
+}
+
+// FW[t][j] = sign[t] (H_{m,d} W)[rows[t]][j] in FP64: the signed sum over p
+// of W[p (m / 2^d) + o][j], (b, o) = divmod(rows[t], m / 2^d), butterfly
+// order; consecutive threads take consecutive j.
+__global__ void __launch_bounds__(256) asph_rows_f64_kernel(SourceDev s, int d, long long sm,
+                                                            const int* __restrict__ rows,
+                                                            const float* __restrict__ sign, int k,
+                                                            double* __restrict__ FW) {
+  const long long n = s.n, total = (long long)k * n;
+  const int D = 1 << d;
+  double stk[kMaxPreD + 1];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long t = e / n, j = e - t * n;
+    const long long x = __ldg(rows + t);
+    const long long b = x / sm, o = x - b * sm;
+    double acc = 0.0;
+    for (int p = 0; p < D; ++p) {
+      const long long i = p * sm + o;
+      const double v = s.kind == LRA_DENSE_F64 ? __ldg(static_cast<const double*>(s.a) + i * s.lda + j)
+                                               : (double)__ldg(static_cast<const float*>(s.a) + i * s.lda + j);
+      acc = butterfly_push(stk, p, v, (unsigned)b);
+    }
+    FW[e] = (double)__ldg(sign + t) * acc;
+  }
+}
+
 int gram_chunks(long long N, int k) {
   const int nt = (k + kGt - 1) / kGt;
   const int pairs = nt * (nt + 1) / 2;
@@ -432,6 +482,22 @@ cudaError_t launch_gather_rows_f64(const SourceDev& src, const int* rows, int k,
   long long g = ((long long)k * src.n + 255) / 256;
   if (g > (long long)sms * 8) g = (long long)sms * 8;
   gather_rows_f64_kernel<<<(int)g, 256, 0, s>>>(src, rows, k, FW);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_asph_cols(const float* M, long long lda, long long m, long long n, int d, const int* J,
+                             const float* sign, int l, float* Y, int sms, cudaStream_t s) {
+  long long g = (m * l + 255) / 256;
+  if (g > (long long)sms * 8) g = (long long)sms * 8;
+  asph_cols_kernel<<<(int)g, 256, 0, s>>>(M, lda, m, n >> d, d, J, sign, l, Y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_asph_rows_f64(const SourceDev& src, int d, const int* rows, const float* sign, int k, double* FW,
+                                 int sms, cudaStream_t s) {
+  long long g = ((long long)k * src.n + 255) / 256;
+  if (g > (long long)sms * 8) g = (long long)sms * 8;
+  asph_rows_f64_kernel<<<(int)g, 256, 0, s>>>(src, d, src.m >> d, rows, sign, k, FW);
   return cudaGetLastError();
 }
 

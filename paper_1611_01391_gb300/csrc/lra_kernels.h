@@ -168,6 +168,10 @@ cudaError_t launch_pchol(const double* partials, int nparts, int k, int r, doubl
 cudaError_t launch_rf_finish(const double* Q1, long long N, int r, const double* Linv, float* U, const JobStatus* js,
                              int sms, cudaStream_t s);
 cudaError_t launch_gather_rows_f64(const SourceDev& src, const int* rows, int k, double* FW, int sms, cudaStream_t s);
+cudaError_t launch_asph_cols(const float* M, long long lda, long long m, long long n, int d, const int* J,
+                             const float* sign, int l, float* Y, int sms, cudaStream_t s);
+cudaError_t launch_asph_rows_f64(const SourceDev& src, int d, const int* rows, const float* sign, int k, double* FW,
+                                 int sms, cudaStream_t s);
 cudaError_t launch_chol_coop(const double* partials, int nparts, int k, double shift_rel, double* G, double* R,
                              double* Rt, unsigned int* bar, JobStatus* js, int sms, cudaStream_t s);
 cudaError_t launch_trsm_rows(const double* W, long long N, int k, const double* Rt, double* Q, const JobStatus* js,

@@ -889,6 +889,13 @@ lra_status lra_range_finder(lra_ctx* ctx, const lra_source* src, const int32_t* 
       (p->resid_q > 0 && (!p->resid_rows || !p->resid_cols || p->resid_q > m || p->resid_s > n)))
     return fail(ctx, LRA_EINVAL, "range finder: bad sizes");
   if (!distinct_in_range(J, l, n)) return fail(ctx, LRA_EINVAL, "range finder: J must hold l distinct columns");
+  const int md = p->mult_d;
+  if (md < 0 || md > kMaxPreD || (n % (1LL << md)) != 0)
+    return fail(ctx, LRA_EINVAL, "range finder: mult_d must be in 0..10 with 2^mult_d dividing n");
+  if (md > 0 && p->mult_sign)
+    for (int t = 0; t < l; ++t)
+      if (p->mult_sign[t] != 1.0f && p->mult_sign[t] != -1.0f)
+        return fail(ctx, LRA_EINVAL, "range finder: multiplier signs must be +1 or -1");
   if (q > 0 && (!distinct_in_range(p->resid_rows, q, m) || !distinct_in_range(p->resid_cols, sN, n)))
     return fail(ctx, LRA_EINVAL, "range finder: residual sample indices must be distinct and in range");
   cudaError_t e = cudaSetDevice(ctx->device);
@@ -907,6 +914,7 @@ lra_status lra_range_finder(lra_ctx* ctx, const lra_source* src, const int32_t* 
   const size_t o_js = lay.take(sizeof(JobStatus)), o_J = lay.take(sizeof(int) * l);
   const size_t o_sr = lay.take(sizeof(int) * std::max(q, 1)), o_sc = lay.take(sizeof(int) * std::max(sN, 1));
   const size_t o_I = lay.take(sizeof(double) * r * r);   // identity nucleus for the estimate
+  const size_t o_sg = lay.take(sizeof(float) * l);       // multiplier signs
   const size_t prefix = lay.off;
   const size_t o_Y = lay.take(sizeof(float) * (size_t)m * l);
   const size_t o_p1 = lay.take(sizeof(double) * (size_t)nch * l * l);
@@ -945,6 +953,11 @@ lra_status lra_range_finder(lra_ctx* ctx, const lra_source* src, const int32_t* 
     const double one = 1.0;
     std::memcpy(hs.data() + o_I + sizeof(double) * ((size_t)t * r + t), &one, sizeof(double));
   }
+  for (int t = 0; t < l; ++t) {
+    const float sg = (md > 0 && p->mult_sign) ? p->mult_sign[t] : 1.0f;
+    std::memcpy(hs.data() + o_sg + sizeof(float) * t, &sg, sizeof(float));
+  }
+  const float* dsg = reinterpret_cast<const float*>(b + o_sg);
   const SourceDev sd = make_src(src);
   TmaMap cmap{};
   const bool tma = make_cols_map(&cmap, static_cast<const float*>(src->a), m, n, src->lda);
@@ -952,8 +965,10 @@ lra_status lra_range_finder(lra_ctx* ctx, const lra_source* src, const int32_t* 
   std::vector<int> hpiv(l, 0);
   // Y = M[:, J]; rank-revealing QR of Y; Q1 = Y(:, piv[:r]) R_r^{-1} and its Gram
   if (!(e = cudaMemcpyAsync(b, hs.data(), prefix, cudaMemcpyHostToDevice, st)) &&
-      !(e = tma ? launch_gather_cols_tma(cmap, dJ, l, m, Y, js, 0, ctx->sms, st)
-                : launch_gather_cols(sd, dJ, l, Y, js, 0, ctx->sms, st)) &&
+      !(e = md > 0 ? launch_asph_cols(static_cast<const float*>(src->a), src->lda, m, n, md, dJ, dsg, l, Y, ctx->sms,
+                                      st)
+          : tma   ? launch_gather_cols_tma(cmap, dJ, l, m, Y, js, 0, ctx->sms, st)
+                  : launch_gather_cols(sd, dJ, l, Y, js, 0, ctx->sms, st)) &&
       !(e = launch_ts_gram_f32(Y, m, l, l, 1, p1, nch, js, st)) &&
       !(e = launch_pchol(p1, nch, l, r, p->rank_tol, Gm, dpiv, js, st)) &&
       !(e = launch_lev_project(Y, m, l, l, 1, Gm, r, Q1, nullptr, 0, js, st)) &&
@@ -1020,6 +1035,13 @@ lra_status lra_dual_lsr(lra_ctx* ctx, const lra_source* W, const int32_t* rows, 
   if (kc < 2 || kc > 1024 || k < kc || k > m || passes < 1 || passes > 4)
     return fail(ctx, LRA_EINVAL, "dual LSR: need 2 <= n + 1 <= 1024, n + 1 <= k <= m, 1..4 passes");
   if (!distinct_in_range(rows, k, m)) return fail(ctx, LRA_EINVAL, "dual LSR: rows must be distinct and in range");
+  const int md = p->mult_d;
+  if (md < 0 || md > kMaxPreD || (m % (1LL << md)) != 0)
+    return fail(ctx, LRA_EINVAL, "dual LSR: mult_d must be in 0..10 with 2^mult_d dividing m");
+  if (md > 0 && p->mult_sign)
+    for (int t = 0; t < k; ++t)
+      if (p->mult_sign[t] != 1.0f && p->mult_sign[t] != -1.0f)
+        return fail(ctx, LRA_EINVAL, "dual LSR: multiplier signs must be +1 or -1");
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e) return cuda_fail(ctx, e, "cudaSetDevice");
   const int nch = ts_gram_chunks(k, kc);
@@ -1027,6 +1049,7 @@ lra_status lra_dual_lsr(lra_ctx* ctx, const lra_source* W, const int32_t* rows, 
   Layout lay;
   const size_t o_js = lay.take(sizeof(JobStatus)), o_rows = lay.take(sizeof(int) * k);
   const size_t o_bar = lay.take(sizeof(unsigned int) * 4);   // grid-barrier counters, one per pass (zeroed)
+  const size_t o_sg = lay.take(sizeof(float) * k);           // multiplier signs
   const size_t prefix = lay.off;
   const size_t o_W = lay.take(sizeof(double) * (size_t)k * kc), o_Qa = lay.take(sizeof(double) * (size_t)k * kc);
   const size_t o_p = lay.take(sizeof(double) * (size_t)nch * kk), o_G = lay.take(sizeof(double) * kk);
@@ -1054,11 +1077,17 @@ lra_status lra_dual_lsr(lra_ctx* ctx, const lra_source* W, const int32_t* rows, 
   init.status = LRA_OK;
   std::memcpy(hs.data() + o_js, &init, sizeof(init));
   std::memcpy(hs.data() + o_rows, rows, sizeof(int) * k);
+  for (int t = 0; t < k; ++t) {
+    const float sg = (md > 0 && p->mult_sign) ? p->mult_sign[t] : 1.0f;
+    std::memcpy(hs.data() + o_sg + sizeof(float) * t, &sg, sizeof(float));
+  }
   const SourceDev sd = make_src(W);
   // the shift of shifted CholeskyQR: 11 (k c + c (c + 1)) u, times ||F W||_F^2 on the device
   const double shift_rel = 11.0 * ((double)k * kc + (double)kc * (kc + 1)) * 0x1p-53;
   e = cudaMemcpyAsync(b, hs.data(), prefix, cudaMemcpyHostToDevice, st);
-  if (!e) e = launch_gather_rows_f64(sd, drows, k, FW, ctx->sms, st);
+  if (!e)
+    e = md > 0 ? launch_asph_rows_f64(sd, md, drows, reinterpret_cast<const float*>(P(o_sg)), k, FW, ctx->sms, st)
+               : launch_gather_rows_f64(sd, drows, k, FW, ctx->sms, st);
   double *in = FW, *outq = Qa;
   for (int s = 0; s < passes && !e; ++s) {
     double* Rsp = Rs + s * kk;

@@ -29,12 +29,12 @@ def ctx():
     c.close()
 
 
-def _rf(ctx, A32, J, r, rows=None, cols=None):
+def _rf(ctx, A32, J, r, rows=None, cols=None, **mult):
     m, n = A32.shape
     src = L.make_source("dense", a=torch.from_numpy(A32).to(DEV))
     U = torch.empty((m, r), dtype=torch.float32, device=DEV)
     V = torch.empty((r, n), dtype=torch.float32, device=DEV)
-    res = L.lra_range_finder(ctx.ctx, src, J, r, U, V, rank_tol=TAU, resid_rows=rows, resid_cols=cols)
+    res = L.lra_range_finder(ctx.ctx, src, J, r, U, V, rank_tol=TAU, resid_rows=rows, resid_cols=cols, **mult)
     torch.cuda.synchronize()
     return res, U.cpu().numpy().astype(np.float64), V.cpu().numpy().astype(np.float64)
 
@@ -67,6 +67,26 @@ def test_range_finder_against_the_oracle(ctx, m, n, r, l, noise):
     assert res["gemm_mode"] in (0, 1)
 
 
+@pytest.mark.parametrize("m,n,r,l,d", [(3000, 2048, 12, 20, 3), (1500, 4096, 24, 32, 6)])
+def test_range_finder_with_an_asph_multiplier(ctx, m, n, r, l, d):
+    """H = the first l columns of H_{n,d} P D (column t: sign[t] times column
+    perm[t] of the abridged Hadamard matrix): the device forms Y = M H in
+    FP32 butterfly sums, the oracle as the FP64 product with the dense H."""
+    A32 = W.factor_gaussian(9050 + d, m, n, r, 1e-4)
+    A = A32.astype(np.float64)
+    rng = W.rng_for(9060 + d)
+    perm, sign = rng.permutation(n), rng.choice([-1.0, 1.0], n)
+    res, U, V = _rf(ctx, A32, perm[:l], r, mult_d=d, mult_sign=sign[:l])
+    assert res["status"] == L.LRA_OK
+    ref = O.range_finder(A, O.asph_columns(n, d, perm, sign, l), r, rank_tol=TAU)
+    assert res["nrank"] == ref.nrank
+    np.testing.assert_array_equal(res["piv"][:r], ref.piv[:r])
+    assert np.linalg.norm(U @ U.T @ ref.U - ref.U, 2) <= 1e-5
+    err = np.linalg.norm(A - U @ V) / np.linalg.norm(A)
+    err_ref = np.linalg.norm(A - ref.U @ ref.V) / np.linalg.norm(A)
+    assert error_ok(err, err_ref), (err, err_ref)
+
+
 def test_range_finder_reports_failure_below_the_target_rank(ctx):
     """Stage 1 of Algorithm 5.1: FAILURE when nrank(M H) < r (a rank-5 matrix
     stored in FP32: its rounding is far below the rank tolerance)."""
@@ -94,10 +114,10 @@ def test_range_finder_rejects_bad_arguments(ctx):
     assert e.value.code == L.LRA_EINVAL
 
 
-def _lsr(ctx, A, b, rows, passes=3, shifted=True, dtype=np.float64):
+def _lsr(ctx, A, b, rows, passes=3, shifted=True, dtype=np.float64, **mult):
     Wm = np.ascontiguousarray(np.concatenate([A, b[:, None]], axis=1).astype(dtype))
     src = L.make_source("dense", a=torch.from_numpy(Wm).to(DEV))
-    return L.lra_dual_lsr(ctx.ctx, src, rows, passes=passes, shifted=shifted)
+    return L.lra_dual_lsr(ctx.ctx, src, rows, passes=passes, shifted=shifted, **mult)
 
 
 @pytest.mark.parametrize("m,n,k", [(4096, 100, 600), (16384, 400, 2400), (3000, 37, 111)])
@@ -148,6 +168,25 @@ def test_dual_lsr_rank_deficient_sample_is_reported(ctx):
     with pytest.raises(L.LraError) as e:
         _lsr(ctx, A, b, rows)
     assert e.value.code == L.LRA_ESINGULAR
+
+
+@pytest.mark.parametrize("kind,d", [("gaussian", 3), ("coherent", 6), ("semicoherent", 6)])
+def test_dual_lsr_with_an_asph_multiplier(ctx, kind, d):
+    """F = k rows of D P H_{m,d} (row t: sign[t] times row perm[t] of the
+    abridged Hadamard matrix) at (k, m, n) = (600, 4096, 100): the device's
+    FP64 butterfly sums against the oracle's dense F.  On the coherent and
+    semi-coherent classes, where row sampling alone leaves the sampled
+    problem rank-deficient, the ASPH rows mix the rows of D (Tables lsrsemi,
+    lsrcoh use 6-ASPH at this size)."""
+    A, b = W.lsr_problem(9970 + d, kind, 4096, 100)
+    rng = W.rng_for(9980 + d)
+    perm, sign = rng.permutation(4096), rng.choice([-1.0, 1.0], 4096)
+    x, rho = _lsr(ctx, A, b, perm[:600], mult_d=d, mult_sign=sign[:600])
+    F = O.asph_rows(4096, d, perm, sign, 600)
+    xr = O.dual_lsr(A, b, F)
+    np.testing.assert_allclose(x, xr, rtol=0, atol=1e-9 * np.abs(xr).max())
+    assert rho == pytest.approx(np.linalg.norm(F @ A @ xr - F @ b), rel=1e-9)
+    assert 1.0 <= O.relative_residual(A, b, x) <= 1.3
 
 
 def test_dual_lsr_rejects_bad_arguments(ctx):
