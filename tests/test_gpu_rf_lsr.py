@@ -170,14 +170,14 @@ def test_dual_lsr_rank_deficient_sample_is_reported(ctx):
     assert e.value.code == L.LRA_ESINGULAR
 
 
-@pytest.mark.parametrize("kind,d", [("gaussian", 3), ("coherent", 6), ("semicoherent", 6)])
+@pytest.mark.parametrize("kind,d", [("gaussian", 3), ("coherent", 8), ("semicoherent", 6)])
 def test_dual_lsr_with_an_asph_multiplier(ctx, kind, d):
     """F = k rows of D P H_{m,d} (row t: sign[t] times row perm[t] of the
     abridged Hadamard matrix) at (k, m, n) = (600, 4096, 100): the device's
     FP64 butterfly sums against the oracle's dense F.  On the coherent and
     semi-coherent classes, where row sampling alone leaves the sampled
     problem rank-deficient, the ASPH rows mix the rows of D (Tables lsrsemi,
-    lsrcoh use 6-ASPH at this size)."""
+    lsrcoh use 6- and 8-ASPH)."""
     A, b = W.lsr_problem(9970 + d, kind, 4096, 100)
     rng = W.rng_for(9980 + d)
     perm, sign = rng.permutation(4096), rng.choice([-1.0, 1.0], 4096)
@@ -187,6 +187,20 @@ def test_dual_lsr_with_an_asph_multiplier(ctx, kind, d):
     np.testing.assert_allclose(x, xr, rtol=0, atol=1e-9 * np.abs(xr).max())
     assert rho == pytest.approx(np.linalg.norm(F @ A @ xr - F @ b), rel=1e-9)
     assert 1.0 <= O.relative_residual(A, b, x) <= 1.3
+
+
+def test_dual_lsr_asph_sample_can_still_be_rank_deficient(ctx):
+    """With d = 6 on the coherent class, rows 64 apart share an offset: two
+    columns of D stay dependent when every sampled row of their offset has
+    the same parity of its block index (here twice: rank 98), and the device
+    reports it."""
+    A, b = W.lsr_problem(9976, "coherent", 4096, 100)
+    rng = W.rng_for(9986)
+    perm, sign = rng.permutation(4096), rng.choice([-1.0, 1.0], 4096)
+    assert np.linalg.matrix_rank(O.asph_rows(4096, 6, perm, sign, 600) @ A) < 100
+    with pytest.raises(L.LraError) as e:
+        _lsr(ctx, A, b, perm[:600], mult_d=6, mult_sign=sign[:600])
+    assert e.value.code == L.LRA_ESINGULAR
 
 
 def test_dual_lsr_rejects_bad_arguments(ctx):
