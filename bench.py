@@ -855,6 +855,30 @@ def run_rf_lsr(dev, n=32768, r=64, l=96, reps=3):
         lsr[f"k{k}_m{m}_n{nn}"] = {"ms_median": 1e3 * float(np.median(tl)), "rel_residual_mean": float(np.mean(rr)),
                                     "paper_lsrRandom_gaussian_multiplier_mean": 1.098 if nn == 100 else 1.095}
     out["dual_lsr_gaussian"] = lsr
+    # ASPH multipliers at (600, 4096, 100): 3-ASPH on Gaussian inputs and
+    # 8-ASPH on the coherent class, where row sampling alone is singular
+    asph = {}
+    for kind, d, printed in (("gaussian", 3, 1.084), ("coherent", 8, 1.078)):
+        tl, rr = [], []
+        for t in range(4):
+            A, b = W.lsr_problem(W.BASE_SEED + 14500 + t, kind, 4096, 100)
+            Wm = torch.from_numpy(np.ascontiguousarray(np.concatenate([A, b[:, None]], axis=1))).to(dev)
+            rng = W.rng_for(W.BASE_SEED + 14600 + t)
+            perm, sign = rng.permutation(4096), rng.choice([-1.0, 1.0], 4096)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            try:
+                x, rho = L.lra_dual_lsr(ctx.ctx, L.make_source("dense", a=Wm), perm[:600], mult_d=d,
+                                        mult_sign=sign[:600])
+            except L.LraError:
+                continue   # a sample that stays rank-deficient
+            tl.append(time.perf_counter() - t0)
+            best = np.linalg.norm(A @ np.linalg.lstsq(A, b, rcond=None)[0] - b)
+            rr.append(float(np.linalg.norm(A @ x - b) / best))
+        asph[f"{kind}_asph{d}"] = {"ms_median": 1e3 * float(np.median(tl)) if tl else None,
+                                   "rel_residual_mean": float(np.mean(rr)) if rr else None,
+                                   "solved": len(rr), "of": 4, "paper_mean_context": printed}
+    out["dual_lsr_asph_k600_m4096_n100"] = asph
     ctx.close()
     return out
 
