@@ -716,6 +716,7 @@ def run_preprocess(dev, n=32768, d=3, k=64, reps=5):
     gen.manual_seed(W.BASE_SEED + 13000)
     M = torch.randn((n, k), device=dev, generator=gen) @ torch.randn((k, n), device=dev, generator=gen)
     M.mul_(1.0 / np.sqrt(k)).add_(torch.randn((n, n), device=dev, generator=gen), alpha=1e-4)
+    torch.cuda.synchronize(dev)   # the library's streams do not wait for torch's
     G = torch.empty_like(M)
     pr, sr, pc, sc = [torch.from_numpy(v).to(dev) for v in W.hadamard_multipliers(W.BASE_SEED + 13001, n, n)]
     pre = L.make_source("preprocessed", a=M, d=d, perm_rows=pr, sign_rows=sr, perm_cols=pc, sign_cols=sc)
@@ -806,6 +807,7 @@ def run_rf_lsr(dev, n=32768, r=64, l=96, reps=3):
     gen.manual_seed(W.BASE_SEED + 14000)
     M = torch.randn((n, r), device=dev, generator=gen) @ torch.randn((r, n), device=dev, generator=gen)
     M.mul_(1.0 / np.sqrt(r)).add_(torch.randn((n, n), device=dev, generator=gen), alpha=1e-4)
+    torch.cuda.synchronize(dev)   # the library's streams do not wait for torch's
     src = L.make_source("dense", a=M)
     ctx = L.Context(dev.index or 0)
     U = torch.empty((n, r), dtype=torch.float32, device=dev)
@@ -895,6 +897,7 @@ def run_profile_rf_lsr(n=32768, r=64, l=96):
     gen.manual_seed(W.BASE_SEED + 14000)
     M = torch.randn((n, r), device=dev, generator=gen) @ torch.randn((r, n), device=dev, generator=gen)
     M.mul_(1.0 / np.sqrt(r)).add_(torch.randn((n, n), device=dev, generator=gen), alpha=1e-4)
+    torch.cuda.synchronize(dev)   # the library's streams do not wait for torch's
     src = L.make_source("dense", a=M)
     ctx = L.Context(0)
     U = torch.empty((n, r), dtype=torch.float32, device=dev)
@@ -921,6 +924,7 @@ def run_profile_preprocess(n, d=3, k=64):
     gen.manual_seed(W.BASE_SEED + 13000)
     M = torch.randn((n, k), device=dev, generator=gen) @ torch.randn((k, n), device=dev, generator=gen)
     M.mul_(1.0 / np.sqrt(k)).add_(torch.randn((n, n), device=dev, generator=gen), alpha=1e-4)
+    torch.cuda.synchronize(dev)   # the library's streams do not wait for torch's
     G = torch.empty_like(M)
     pr, sr, pc, sc = [torch.from_numpy(v).to(dev) for v in W.hadamard_multipliers(W.BASE_SEED + 13001, n, n)]
     pre = L.make_source("preprocessed", a=M, d=d, perm_rows=pr, sign_rows=sr, perm_cols=pc, sign_cols=sc)

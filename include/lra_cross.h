@@ -417,8 +417,11 @@ lra_status lra_cross_destroy(lra_ctx* ctx);
  * LRA_EBUSY when full, LRA_ETOOLARGE when a strip cannot be held on chip)
  * and enqueue a full C-A solve on one of the context's streams.  The host
  * arrays of params are copied before the call returns; the source stays
- * borrowed until the job ends.  Non-blocking: returns once the work is
- * queued.  *out receives the job handle. */
+ * borrowed until the job ends.  The context's own streams are non-blocking:
+ * they do not wait for work queued on other streams, so the source's device
+ * arrays must be complete when the call is made (synchronise their producer
+ * first, or create the context on the producer's stream).  Non-blocking:
+ * returns once the work is queued.  *out receives the job handle. */
 lra_status lra_cross_submit(lra_ctx* ctx, const lra_source* src,
                             const lra_params* params, lra_job* out);
 

@@ -94,9 +94,11 @@ bool plan_maxvol(long long N, int l, int sms, size_t smem_limit, MaxvolPlan* pla
 cudaError_t launch_maxvol(MaxvolArgs a, const MaxvolPlan& plan, cudaStream_t st);
 
 // Inverse of the cross S[pos, :] of a strip (double-float Gauss-Jordan with
-// partial pivoting on one CTA), row-major into xinv as FP32 pairs.
+// partial pivoting), row-major into xinv as FP32 pairs: on one CTA, or with
+// cluster set and l = 48 or 96 on a cluster of 8 CTAs (the same result bit
+// for bit, for a job that has the GPU to itself).
 cudaError_t launch_cross_inverse(const float* strip, long long si, long long st, const int* pos,
-                                 int l, float2* xinv, JobStatus* js, cudaStream_t stream);
+                                 int l, float2* xinv, JobStatus* js, cudaStream_t stream, bool cluster = false);
 
 // Nucleus of the final cross X = C[I, :] (one CTA, double-float QRCP +
 // one-sided Jacobi SVD).  NucExtra (all nullable): row / column scales of X
@@ -108,9 +110,11 @@ struct NucExtra {
   double* Pk = nullptr;
   double* Vk = nullptr;
 };
+// cluster: with l = 48 or 96 on a cluster of 8 CTAs (the same result bit
+// for bit, for a job that has the GPU to itself).
 cudaError_t launch_nucleus(const float* C, const int* I, int l, int k, double rank_tol,
                            double* U, double* sigma, JobStatus* js, cudaStream_t st,
-                           const NucExtra& xa = NucExtra());
+                           const NucExtra& xa = NucExtra(), bool cluster = false);
 
 // Appendix F sampled residual of C U R on rows x cols.
 cudaError_t launch_sampled_residual(const SourceDev& s, const int* rows, int q,

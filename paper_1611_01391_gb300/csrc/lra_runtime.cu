@@ -421,7 +421,7 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
     col.half_step = 2 * sw;
     col.xin = j->xbuf0;   // inverse of A[I, J] (vertical strip's cross)
     if (!col.gepp && !self_col) {
-      if ((e = launch_cross_inverse(j->C, j->l, 1, j->I, j->l, j->xbuf0, j->js, st)) ||
+      if ((e = launch_cross_inverse(j->C, j->l, 1, j->I, j->l, j->xbuf0, j->js, st, !one_sm)) ||
           (e = after(kClsInverse, 1))) return e;
     }
     if ((e = launch_maxvol(col, j->plan_col, st)) || (e = after(kClsMaxvol, 1))) return e;
@@ -431,13 +431,13 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
     row.gepp = 0;
     row.half_step = 2 * sw + 1;
     row.xin = j->xbuf1;   // inverse of A[I, J]^T (horizontal strip's cross)
-    if (!self_row && ((e = launch_cross_inverse(j->R, 1, j->n, j->J, j->l, j->xbuf1, j->js, st)) ||
+    if (!self_row && ((e = launch_cross_inverse(j->R, 1, j->n, j->J, j->l, j->xbuf1, j->js, st, !one_sm)) ||
                       (e = after(kClsInverse, 1)))) return e;
     row.count_sweep = 1;   // the sweep is counted by the row maxvol that completes it
     if ((e = launch_maxvol(row, j->plan_row, st)) || (e = after(kClsMaxvol, 1))) return e;
     if (j->tol > 0.0 && sw + 1 < j->sweeps) {
       if ((e = gather_c(1))) return e;
-      if ((e = launch_nucleus(j->C, j->I, j->l, j->k, j->rank_tol, j->U, j->sigma, j->js, st)) || (e = after(kClsCross, 1))) return e;
+      if ((e = launch_nucleus(j->C, j->I, j->l, j->k, j->rank_tol, j->U, j->sigma, j->js, st, NucExtra(), !one_sm)) || (e = after(kClsCross, 1))) return e;
       if ((e = launch_sampled_residual(j->src, j->rows, (int)j->q, j->cols, (int)j->s, j->l, j->C, j->U,
                                        j->R, j->CUq, j->partials, j->n_partials, j->js, st)) ||
           (e = after(kClsResid, 3))) return e;
@@ -450,7 +450,7 @@ cudaError_t enqueue_solve(lra_ctx* ctx, Job* j, const lra_params* p) {
   if (gen &&
       ((e = launch_gather_rows(j->src, j->I, j->l, j->R, j->js, ctx->sms, st, 0)) || (e = after(kClsGather, 1))))
     return e;
-  if ((e = launch_nucleus(j->C, j->I, j->l, j->k, j->rank_tol, j->U, j->sigma, j->js, st)) || (e = after(kClsCross, 1))) return e;
+  if ((e = launch_nucleus(j->C, j->I, j->l, j->k, j->rank_tol, j->U, j->sigma, j->js, st, NucExtra(), !one_sm)) || (e = after(kClsCross, 1))) return e;
   if (j->full_res) {
     if ((e = launch_full_residual(static_cast<const float*>(j->src.a), j->src.lda, j->m, j->n, j->l, j->C,
                                   j->U, j->R, j->fr_ws, std::min(ctx->sms, kMaxGrid), j->js, st)) ||

@@ -12,6 +12,8 @@
 // of Drmac & Veselic); dot products are compensated FP32 sums (Dot2).
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include <cfloat>
 
 #include "dd_arith.cuh"
@@ -84,6 +86,24 @@ __device__ __forceinline__ dd dd_recip(dd d) {
   return quick_two_sum(r0, __fmul_rn(r0, e.hi));
 }
 
+// for (i = first; i < l; i += STEP) body(i) with first >= 0.  With L > 0
+// the trip count is fixed at ceil(L / STEP) (the iterations past l do
+// nothing), so the loop unrolls and its shared-memory loads issue together
+// instead of one iteration's latency after another; the iterations run in
+// the same order either way.
+template <int L, int STEP, typename F>
+__device__ __forceinline__ void strided(int first, int l, F&& body) {
+  if constexpr (L > 0) {
+#pragma unroll
+    for (int it = 0; it < (L + STEP - 1) / STEP; ++it) {
+      const int i = first + STEP * it;
+      if (i < l) body(i);
+    }
+  } else {
+    for (int i = first; i < l; i += STEP) body(i);
+  }
+}
+
 // Shared scratch of the SVD below.
 struct SvdScratch {
   int perm[kMaxL];    // column c of X P is column perm[c] of X
@@ -112,8 +132,7 @@ __device__ void qrcp_dd(dd* A, int l_arg, SvdScratch* sc) {
   for (int base = warp * GPW; base < l; base += NG) {
     const int c = base + (lane / G);
     dacc a{0.f, 0.f};
-    if (c < l)
-      for (int i = gl; i < l; i += G) acc_fma(a, A[c * l + i], A[c * l + i]);
+    if (c < l) strided<L, G>(gl, l, [&](int i) { acc_fma(a, A[c * l + i], A[c * l + i]); });
     a = acc_group_sum<G>(a);
     if (c < l && gl == 0) sc->nrm[c] = acc_value(a);
   }
@@ -163,7 +182,7 @@ __device__ void qrcp_dd(dd* A, int l_arg, SvdScratch* sc) {
     __syncthreads();
     if (warp == 0) {  // reflector of rows j..l-1 of column j
       dacc a{0.f, 0.f};
-      for (int i = j + lane; i < l; i += 32) acc_fma(a, A[j * l + i], A[j * l + i]);
+      strided<L, 32>(j + lane, l, [&](int i) { acc_fma(a, A[j * l + i], A[j * l + i]); });
       a = acc_group_sum<32>(a);
       if (lane == 0) {
         const dd n2 = acc_value(a);
@@ -192,18 +211,17 @@ __device__ void qrcp_dd(dd* A, int l_arg, SvdScratch* sc) {
       const int c = base + (lane / G);
       const bool act = c < l;
       dacc a{0.f, 0.f};
-      if (act)
-        for (int i = j + gl; i < l; i += G) acc_fma(a, A[j * l + i], A[c * l + i]);
+      if (act) strided<L, G>(j + gl, l, [&](int i) { acc_fma(a, A[j * l + i], A[c * l + i]); });
       a = acc_group_sum<G>(a);
       const dd sv = dd_mul(bj, acc_value(a));
       const dd nsv = dd_neg(sv);
       dacc nn{0.f, 0.f};
       if (act)
-        for (int i = j + gl; i < l; i += G) {
+        strided<L, G>(j + gl, l, [&](int i) {
           const dd x = dd_lin2(dd_make(1.0f), A[c * l + i], nsv, A[j * l + i]);
           A[c * l + i] = x;
           if (i > j) acc_fma(nn, x, x);
-        }
+        });
       nn = acc_group_sum<G>(nn);
       if (act && gl == 0) sc->nrm[c] = acc_value(nn);
     }
@@ -248,12 +266,12 @@ __device__ void jacobi_dd(dd* W, dd* Z, int l_arg, int* flag) {
         dd* wq = W + q * l;
         dacc sa{0.f, 0.f}, sb{0.f, 0.f}, sg{0.f, 0.f};
         if (act)
-          for (int i = gl; i < l; i += G) {
+          strided<L, G>(gl, l, [&](int i) {
             const dd u = wp[i], v = wq[i];
             acc_fma(sa, u, u);
             acc_fma(sb, v, v);
             acc_fma(sg, u, v);
-          }
+          });
         sa = acc_group_sum<G>(sa);
         sb = acc_group_sum<G>(sb);
         sg = acc_group_sum<G>(sg);
@@ -265,19 +283,19 @@ __device__ void jacobi_dd(dd* W, dd* Z, int l_arg, int* flag) {
         const float tf = tf_out;
         const dd s = dd_mul(c, dd_make(tf));
         const dd ns = dd_neg(s);
-        for (int i = gl; i < l; i += G) {
+        strided<L, G>(gl, l, [&](int i) {
           const dd u = wp[i], v = wq[i];
           wp[i] = dd_lin2(c, u, ns, v);
           wq[i] = dd_lin2(s, u, c, v);
-        }
+        });
         if (kAccumulate) {
           dd* zp = Z + p * l;
           dd* zq = Z + q * l;
-          for (int i = gl; i < l; i += G) {
+          strided<L, G>(gl, l, [&](int i) {
             const dd xx = zp[i], yy = zq[i];
             zp[i] = dd_lin2(c, xx, ns, yy);
             zq[i] = dd_lin2(s, xx, c, yy);
-          }
+          });
         }
         if (gl == 0) *flag = 1;
       }
@@ -286,6 +304,125 @@ __device__ void jacobi_dd(dd* W, dd* Z, int l_arg, int* flag) {
     if (*flag == 0) break;
     __syncthreads();
   }
+}
+
+// jacobi_dd<NT, false, 8, L> on the CTAs of a cluster of NC.  The pairs of
+// a round are slots s = 0 .. L/2 - 1 of the round-robin order, pairing the
+// columns at positions s and L - 1 - s; CTA c takes slots c S .. c S + S - 1
+// (S = L / (2 NC)), one warp per pair, and keeps the 2 S columns of those
+// positions in its shared memory (cb: two buffers of 2 S columns).  From
+// one round to the next a column moves from position x to x - 1 (position 1
+// to L - 1, position 0 stays), so after its rotation a warp writes both
+// columns straight into the buffer of the next round of the CTA that holds
+// their next positions (distributed shared memory), and one cluster barrier
+// per round ends the round.  Within a pair the three dot products run on
+// three groups of 8 lanes (each in the lane order and summation tree of
+// jacobi_dd's 8-lane group) and the column updates on all 32 lanes (the
+// same operations per entry), so every rotation, and the result, is
+// bitwise that of jacobi_dd.  W: the full L x L matrix in every CTA on
+// entry; on exit every CTA holds the full result.  flags: two ints.
+template <int NT, int L, int NC>
+__device__ void jacobi_dd_cluster(cooperative_groups::cluster_group& cl, dd* W, dd* cb, int* flags) {
+  static_assert(L % (2 * NC) == 0, "pairs per CTA");
+  constexpr int S = L / (2 * NC);
+  constexpr int NP = L;   // even: every position holds a column
+  static_assert(S <= NT / 32, "one warp per pair");
+  const int rank = (int)cl.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, grp = lane >> 3, gl = lane & 7;
+  // column at position x in round r of a sweep
+  auto colof = [](int x, int r) { return x == 0 ? 0 : ((x - 1 + r) % (NP - 1)) + 1; };
+  // position x of slot k of this CTA: low half k, high half S + k
+  auto posof = [&](int li) { return li < S ? rank * S + li : NP - 1 - (rank * S + li - S); };
+  // CTA and local index of position x
+  auto home = [](int x, int& cta, int& li) {
+    if (x < NP / 2) {
+      cta = x / S;
+      li = x - cta * S;
+    } else {
+      const int s = NP - 1 - x;
+      cta = s / S;
+      li = S + s - cta * S;
+    }
+  };
+  for (int e = tid; e < 2 * S * L; e += NT) {
+    const int li = e / L, i = e - li * L;
+    cb[e] = W[colof(posof(li), 0) * L + i];
+  }
+  if (tid < 2) flags[tid] = 0;
+  __syncthreads();
+  // about l * 2^-48, tested on the FP32 high parts as in jacobi_dd
+  const float tol = (float)L * 3.6e-15f;
+  int buf = 0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    for (int round = 0; round < NP - 1; ++round) {
+      if (warp < S) {
+        const int xl = posof(warp), xh = posof(S + warp);
+        const bool low_first = colof(xl, round) < colof(xh, round);   // p < q
+        const int xp = low_first ? xl : xh, xq = low_first ? xh : xl;
+        const dd* wp = cb + (size_t)buf * 2 * S * L + (low_first ? warp : S + warp) * L;
+        const dd* wq = cb + (size_t)buf * 2 * S * L + (low_first ? S + warp : warp) * L;
+        int cp, lp, cq, lq;
+        home(xp == 0 ? 0 : (xp == 1 ? NP - 1 : xp - 1), cp, lp);
+        home(xq == 0 ? 0 : (xq == 1 ? NP - 1 : xq - 1), cq, lq);
+        dd* dp = cl.map_shared_rank(cb + (size_t)(buf ^ 1) * 2 * S * L + lp * L, cp);
+        dd* dq = cl.map_shared_rank(cb + (size_t)(buf ^ 1) * 2 * S * L + lq * L, cq);
+        // group 0: w_p^T w_p, group 1: w_q^T w_q, group 2: w_p^T w_q
+        dacc a{0.f, 0.f};
+        if (grp < 3)
+          strided<L, 8>(gl, L, [&](int i) {
+            const dd u = grp == 1 ? wq[i] : wp[i];
+            const dd v = grp == 0 ? wp[i] : wq[i];
+            acc_fma(a, u, v);
+          });
+        a = acc_group_sum<8>(a);
+        const dacc sa{__shfl_sync(0xffffffffu, a.s, 0), __shfl_sync(0xffffffffu, a.c, 0)};
+        const dacc sb{__shfl_sync(0xffffffffu, a.s, 8), __shfl_sync(0xffffffffu, a.c, 8)};
+        const dacc sg{__shfl_sync(0xffffffffu, a.s, 16), __shfl_sync(0xffffffffu, a.c, 16)};
+        const dd al = acc_value(sa), be = acc_value(sb), ga = acc_value(sg);
+        const bool rot = (al.hi > 0.0f) && (be.hi > 0.0f) && !(fabsf(ga.hi) <= tol * sqrtf(al.hi) * sqrtf(be.hi));
+        // the rotation is formed beside the test (its chain does not wait
+        // for it) and used only when the test asks for it
+        float tf;
+        const dd c = rotation_cosine(al, be, ga, &tf);
+        const dd s = dd_mul(c, dd_make(tf));
+        const dd ns = dd_neg(s);
+        if (rot) {
+          strided<L, 32>(lane, L, [&](int i) {
+            const dd u = wp[i], v = wq[i];
+            dp[i] = dd_lin2(c, u, ns, v);
+            dq[i] = dd_lin2(s, u, c, v);
+          });
+          if (lane == 0) flags[sweep & 1] = 1;
+        } else {
+          strided<L, 32>(lane, L, [&](int i) {
+            dp[i] = wp[i];
+            dq[i] = wq[i];
+          });
+        }
+      }
+      cl.sync();   // the round's columns are in place for the next round
+      buf ^= 1;
+    }
+    // the sweep rotated somewhere in the cluster?
+    int any = 0;
+    if (tid < NC) any = *cl.map_shared_rank(&flags[sweep & 1], tid);
+    any = __syncthreads_or(any);
+    // the next sweep's flag (last read by the other CTAs before this sweep's rounds)
+    if (tid == 0) flags[(sweep + 1) & 1] = 0;
+    __syncthreads();
+    if (!any) break;
+  }
+  // every sweep has NP - 1 rounds, so position x holds column colof(x, 0):
+  // every CTA writes its columns into every CTA's W
+  const dd* fin = cb + (size_t)buf * 2 * S * L;
+  for (int d = 0; d < NC; ++d) {
+    dd* dst = cl.map_shared_rank(W, d);
+    for (int e = tid; e < 2 * S * L; e += NT) {
+      const int li = e / L, i = e - li * L;
+      dst[colof(posof(li), 0) * L + i] = fin[e];
+    }
+  }
+  cl.sync();
 }
 
 // SVD of the l x l matrix X held in A (column c at A[c*l, c*l+l)), with Z an
@@ -298,7 +435,19 @@ __device__ void jacobi_dd(dd* W, dd* Z, int l_arg, int* flag) {
 // The rotations are not accumulated: the left singular vectors needed later
 // are u_b = X P W_b / sigma_b^2 (left_vectors), so Z keeps a copy of X.
 template <int NT, int L = 0>
+__device__ void svd_dd_precondition(dd* A, dd* Z, int l_arg, SvdScratch* sc);
+
+template <int NT, int L = 0>
 __device__ void svd_dd(dd* A, dd* Z, int l_arg, SvdScratch* sc) {
+  const int l = L > 0 ? L : l_arg;
+  svd_dd_precondition<NT, L>(A, Z, l, sc);
+  jacobi_dd<NT, false, (NT >= 1024 ? 16 : 8), L>(A, nullptr, l, &sc->flag);
+}
+
+// The steps of svd_dd before the Jacobi sweeps: Z = X, the QR with column
+// pivoting of X, and A = R^T.
+template <int NT, int L>
+__device__ void svd_dd_precondition(dd* A, dd* Z, int l_arg, SvdScratch* sc) {
   const int l = L > 0 ? L : l_arg;
   for (int e = threadIdx.x; e < l * l; e += NT) Z[e] = A[e];
   qrcp_dd<NT, L>(A, l, sc);
@@ -322,7 +471,6 @@ __device__ void svd_dd(dd* A, dd* Z, int l_arg, SvdScratch* sc) {
     if (e < l * l) A[e] = v[t];
   }
   __syncthreads();
-  jacobi_dd<NT, false, (NT >= 1024 ? 16 : 8), L>(A, nullptr, l, &sc->flag);
 }
 
 // Left singular vectors of the kept triplets, in place of the copy of X in
@@ -330,12 +478,13 @@ __device__ void svd_dd(dd* A, dd* Z, int l_arg, SvdScratch* sc) {
 // into column r of Z, r < ke.  One warp per row q of X: the warp holds the
 // row in registers (l <= 96: three values per lane) before it overwrites
 // that row's first ke positions, so rows are independent.
+// Rows q0, q0 + qs, ... only when qs > 1 (the rows of one CTA of a cluster).
 template <int NT, int L = 0>
 __device__ void left_vectors(const dd* W, dd* Z, int l_arg, int ke, const int* order, const dd* inv2,
-                             const int* perm) {
+                             const int* perm, int q0 = 0, int qs = 1) {
   const int l = L > 0 ? L : l_arg;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int q = warp; q < l; q += NT / 32) {
+  for (int q = q0 + warp * qs; q < l; q += (NT / 32) * qs) {
     dd x[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -383,12 +532,15 @@ __device__ void jacobi_sigma(const dd* W, int l, double* sig, int* order) {
 // inv2[r] = 1 / sigma_{b_r}^2 (shared, computed once); out(e, value)
 // receives the l*l entries, row-major e = p*l + q (p a column of X, q a row
 // of X).
+// With qs > 1 only the entries of rows q0, q0 + qs, ... of X (the rows of
+// one CTA of a cluster).
 template <int NT, int L = 0, typename Out>
 __device__ void nucleus_from_svd(const dd* W, const dd* Z, const int* perm, int l_arg, int ke,
-                                 const int* order, const dd* inv2, Out out) {
+                                 const int* order, const dd* inv2, Out out, int q0 = 0, int qs = 1) {
   const int l = L > 0 ? L : l_arg;
-  for (int e = threadIdx.x; e < l * l; e += NT) {
-    const int c = e / l, q = e - c * l;
+  const int nq = (l - q0 + qs - 1) / qs;
+  for (int e = threadIdx.x; e < l * nq; e += NT) {
+    const int c = e / nq, q = q0 + (e - c * nq) * qs;
     dd acc{0.f, 0.f};
     for (int r = 0; r < ke; ++r) {
       const int b = order[r];
