@@ -626,7 +626,10 @@ typedef struct {
  * (Fukaya et al.) on the k x (n+1) matrix: (F W) = Q R_p ... R_1, x =
  * R_nn^{-1} R[:n, n].  The scale sqrt(m/k) does not change x.  Blocking.
  * LRA_EINVAL for bad sizes or rows; LRA_ESINGULAR when a Cholesky pivot is
- * not positive (rows too ill conditioned for the passes given). */
+ * not positive, or, in an unshifted pass, at most 1e-3 s_rel times its
+ * column's squared norm (s = s_rel ||Y||_F^2 the shift above): the sampled
+ * rows are numerically rank deficient, or too ill conditioned for the
+ * passes given. */
 lra_status lra_dual_lsr(lra_ctx* ctx, const lra_source* W, const int32_t* rows, int32_t k,
                         const lra_lsr_params* params, const lra_lsr_out* out);
 

@@ -213,29 +213,67 @@ __global__ void __launch_bounds__(256) gather_rows_f64_kernel(SourceDev s, const
 }
 
 // Q[i][:] = W[i][:] R^{-1} (R upper k x k, given as its transpose Rt, lower,
-// row j of Rt = column j of R): forward substitution along the row, one warp
-// per row: q_j = (w_j - sum_{c<j} q_c Rt[j][c]) / Rt[j][j], the sum split
-// over the lanes (c = lane mod 32, contiguous reads of Rt's row j) and
-// reduced in a fixed order; lane 0 stores q_j, which the warp reads back.
+// row j of Rt = column j of R), for a block of kTrsmRows rows per CTA held in
+// shared memory, by panels of 32 columns: first every entry (i, j) of the
+// panel subtracts sum_{c < j0} q_c R[c][j] (c in order, two rows per thread
+// so that the FP64 pipe always has independent multiply-adds), then one warp
+// per row solves the panel's triangle: lane t holds entry j0 + t, step s
+// multiplies lane s's value by 1 / R_jj (formed beforehand) and the lanes
+// t > s subtract R[j0 + s][j0 + t] times it.
+constexpr int kTrsmRows = 16;
+
 __global__ void __launch_bounds__(256) trsm_rows_kernel(const double* __restrict__ W, long long N, int k,
                                                         const double* __restrict__ Rt, double* __restrict__ Q,
                                                         const JobStatus* js) {
   if (js->status != LRA_OK) return;
-  const int lane = threadIdx.x & 31;
-  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-  for (long long i = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); i < N; i += nwarps) {
-    const double* w = W + i * k;
-    double* q = Q + i * k;
-    for (int j = 0; j < k; ++j) {
-      const double* rt = Rt + (size_t)j * k;
-      double acc = 0.0;
-      for (int c = lane; c < j; c += 32) acc = fma(q[c], __ldg(rt + c), acc);
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-      if (lane == 0) q[j] = (w[j] - acc) / __ldg(rt + j);
-      __syncwarp();
+  extern __shared__ double tr_sm[];
+  double* Qs = tr_sm;                        // kTrsmRows x k
+  double* rinv = Qs + (size_t)kTrsmRows * k; // k
+  __shared__ double T[32][33];               // the panel's triangle of R: T[t][s] = R[j0 + s][j0 + t]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const long long i0 = (long long)blockIdx.x * kTrsmRows;
+  const int nr = (int)min((long long)kTrsmRows, N - i0);
+  for (int e = tid; e < nr * k; e += blockDim.x) Qs[e] = W[i0 * k + e];
+  for (int j = tid; j < k; j += blockDim.x) rinv[j] = 1.0 / Rt[(size_t)j * k + j];
+  for (int j0 = 0; j0 < k; j0 += 32) {
+    const int w = min(32, k - j0);
+    for (int e = tid; e < 32 * 32; e += blockDim.x) {
+      const int t = e >> 5, c = e & 31;
+      T[t][c] = (t < w && c < t) ? Rt[(size_t)(j0 + t) * k + j0 + c] : 0.0;
     }
+    __syncthreads();
+    // the panel minus the part already solved: rows warp and warp + 8, column j0 + lane
+    if (lane < w && j0 > 0) {
+      const double* rt = Rt + (size_t)(j0 + lane) * k;
+      for (int ib = warp; ib < nr; ib += 16) {
+        const int ia = ib, ic = ib + 8;
+        double xa = Qs[(size_t)ia * k + j0 + lane];
+        double xc = ic < nr ? Qs[(size_t)ic * k + j0 + lane] : 0.0;
+        const double* qa = Qs + (size_t)ia * k;
+        const double* qc = Qs + (size_t)(ic < nr ? ic : ia) * k;
+#pragma unroll 4
+        for (int c = 0; c < j0; ++c) {
+          const double r = __ldg(rt + c);
+          xa = fma(-qa[c], r, xa);
+          xc = fma(-qc[c], r, xc);
+        }
+        Qs[(size_t)ia * k + j0 + lane] = xa;
+        if (ic < nr) Qs[(size_t)ic * k + j0 + lane] = xc;
+      }
+    }
+    __syncthreads();
+    // the triangle, one warp per row
+    for (int ib = warp; ib < nr; ib += 8) {
+      double x = lane < w ? Qs[(size_t)ib * k + j0 + lane] : 0.0;
+      for (int s2 = 0; s2 < w; ++s2) {
+        const double y = __shfl_sync(0xffffffffu, x * rinv[j0 + (lane < w ? lane : 0)], s2);
+        if (lane == s2) Qs[(size_t)ib * k + j0 + s2] = y;
+        if (lane > s2 && lane < w) x = fma(-T[lane][s2], y, x);
+      }
+    }
+    __syncthreads();
   }
+  for (int e = tid; e < nr * k; e += blockDim.x) Q[i0 * k + e] = Qs[e];
 }
 
 // Grid-wide barrier of a cooperative launch on a counter that only grows:
@@ -263,20 +301,40 @@ __device__ __forceinline__ bool coop_barrier(unsigned int* count, unsigned int t
 }
 
 // Cooperative form of the FP64 Cholesky G + shift I = R^T R for k up to
-// 1024: G (upper triangle, from the partials) and R in global memory, one
-// grid barrier per column.  At step j every block forms the pivot row
-// R[j][c] = G[j][c] / R_jj itself (block 0 also stores it) and updates the
-// trailing rows a > j it owns (a mod gridDim == blockIdx).  The shift is
-// added to each diagonal entry when it becomes the pivot.  A non-positive
-// pivot: LRA_ESINGULAR (every block sees the same value and stops).
-__global__ void __launch_bounds__(256) chol_coop_kernel(const double* __restrict__ partials, int nparts, int k,
-                                                        double shift_rel, double* __restrict__ G,
+// 1024, by panels of kCholP columns: G (upper triangle, from the partials)
+// and R in global memory, two grid barriers per panel.  For the panel of
+// rows j0 .. j1 - 1:
+//   (A) every block factors the diagonal block itself (the same values
+//       everywhere): for j = j0 .. j1 - 1, r_jj = sqrt(G_jj + shift) and
+//       R[j][c] = G[j][c] / r_jj, then G[a][c] -= R[j][a] R[j][c] for the
+//       block's rows a > j;
+//   (B) one warp per column c >= j1 (over the whole grid) forms the panel's
+//       rows of R there: lane i holds G[j0 + i][c]; step s divides lane s's
+//       value by r_ss and the lanes i > s subtract R[s][j0 + i] times it;
+//   (C) grid barrier; every block applies the panel to the trailing rows it
+//       owns (a >= j1, a mod gridDim == blockIdx): G[a][c] -= R[s][a] R[s][c]
+//       for s = j0 .. j1 - 1 in order; grid barrier.
+// Every entry of G receives the same multiply-subtracts in the same order as
+// in the column-by-column elimination (one multiply-subtract per earlier
+// row, each from the row's final values), and every entry of R the same
+// division, so the factor is the column-by-column one bit for bit.  A pivot
+// d <= floor_rel G_jj (G_jj the column's squared norm before the
+// elimination; floor_rel = 0: a non-positive pivot) is a numerically rank
+// deficient column: LRA_ESINGULAR (every block sees the same value and
+// stops).  Data written by other blocks is read past L1 (ld.global.cg).
+constexpr int kCholP = 32;
+
+__global__ void __launch_bounds__(256, 1) chol_coop_kernel(const double* __restrict__ partials, int nparts, int k,
+                                                        double shift_rel, double floor_rel,
+                                                        double* __restrict__ G, double* __restrict__ Gd,
                                                         double* __restrict__ R, double* __restrict__ Rt,
                                                         unsigned int* bar, JobStatus* js) {
-  __shared__ double Rj[1024];
+  __shared__ double D[kCholP][kCholP + 1];   // the diagonal block (upper), then its rows of R
+  __shared__ double rd[kCholP];              // the panel's r_jj
+  __shared__ double ra[kCholP];              // R[j0 .. j1)[a] of the trailing row a
   __shared__ double red[8];
   __shared__ int flag;
-  const int tid = threadIdx.x, nb = gridDim.x, b = blockIdx.x;
+  const int tid = threadIdx.x, nb = gridDim.x, b = blockIdx.x, lane = tid & 31, warp = tid >> 5;
   if (js->status != LRA_OK) return;
   for (long long e = (long long)b * blockDim.x + tid; e < (long long)k * k; e += (long long)nb * blockDim.x) {
     const int a = (int)(e / k), c = (int)(e - (long long)a * k);
@@ -284,6 +342,7 @@ __global__ void __launch_bounds__(256) chol_coop_kernel(const double* __restrict
     if (c >= a)
       for (int q = 0; q < nparts; ++q) s += partials[(size_t)q * k * k + e];
     G[e] = s;
+    if (c == a) Gd[a] = s;
     R[e] = 0.0;
     Rt[e] = 0.0;
   }
@@ -291,7 +350,7 @@ __global__ void __launch_bounds__(256) chol_coop_kernel(const double* __restrict
   if (!coop_barrier(bar, ++nbar * nb, js, &flag)) return;
   // shift = shift_rel * trace(G), summed in a fixed order by every block
   double tr = 0.0;
-  for (int a = tid; a < k; a += blockDim.x) tr += G[(size_t)a * k + a];
+  for (int a = tid; a < k; a += blockDim.x) tr += __ldcg(G + (size_t)a * k + a);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, off);
   if ((tid & 31) == 0) red[tid >> 5] = tr;
@@ -299,48 +358,90 @@ __global__ void __launch_bounds__(256) chol_coop_kernel(const double* __restrict
   double trace = 0.0;
   for (int w = 0; w < (int)(blockDim.x >> 5); ++w) trace += red[w];
   const double shift = shift_rel * trace;
-  for (int j = 0; j < k; ++j) {
-    // row j final (and, at j = 0, every block done reading the diagonal)
-    if (!coop_barrier(bar, ++nbar * nb, js, &flag)) return;
-    const double d = G[(size_t)j * k + j] + shift;
-    if (!(d > 0.0)) {
-      if (b == 0 && tid == 0) set_status(js, LRA_ESINGULAR);
-      return;
-    }
-    const double rjj = sqrt(d);
-    for (int c = j + 1 + tid; c < k; c += blockDim.x) {
-      const double v = G[(size_t)j * k + c] / rjj;
-      Rj[c] = v;
-      if (b == 0) {
-        R[(size_t)j * k + c] = v;
-        Rt[(size_t)c * k + j] = v;
-      }
-    }
-    if (b == 0 && tid == 0) {
-      R[(size_t)j * k + j] = rjj;
-      Rt[(size_t)j * k + j] = rjj;
+  for (int j0 = 0; j0 < k; j0 += kCholP) {
+    const int j1 = min(j0 + kCholP, k), w = j1 - j0;
+    // (A) the diagonal block
+    for (int e = tid; e < w * w; e += blockDim.x) {
+      const int a = e / w, c = e - a * w;
+      D[a][c] = c >= a ? __ldcg(G + (size_t)(j0 + a) * k + j0 + c) : 0.0;
     }
     __syncthreads();
-    // the first trailing row this block owns, then every nb-th
-    int a0 = j + 1 + ((b - (j + 1)) % nb + nb) % nb;
-    for (int a = a0; a < k; a += nb) {
-      const double ra = Rj[a];
-      for (int c = a + tid; c < k; c += blockDim.x) G[(size_t)a * k + c] -= ra * Rj[c];
+    for (int j = 0; j < w; ++j) {
+      const double d = D[j][j] + shift;
+      if (!(d > 0.0) || !(d > floor_rel * __ldcg(Gd + j0 + j))) {
+        if (b == 0 && tid == 0) set_status(js, LRA_ESINGULAR);
+        return;
+      }
+      const double rjj = sqrt(d);
+      for (int c = j + 1 + tid; c < w; c += blockDim.x) D[j][c] = D[j][c] / rjj;
+      if (tid == 0) rd[j] = rjj;
+      __syncthreads();
+      for (int e = tid; e < w * w; e += blockDim.x) {
+        const int a = e / w, c = e - a * w;
+        if (a > j && c >= a) D[a][c] -= D[j][a] * D[j][c];
+      }
+      __syncthreads();
     }
+    if (b == 0)
+      for (int e = tid; e < w * w; e += blockDim.x) {
+        const int a = e / w, c = e - a * w;
+        if (c >= a) {
+          const double v = c == a ? rd[a] : D[a][c];
+          R[(size_t)(j0 + a) * k + j0 + c] = v;
+          Rt[(size_t)(j0 + c) * k + j0 + a] = v;
+        }
+      }
+    // (B) the panel's rows of R in the columns c >= j1, one warp per column
+    const int gw = b * (int)(blockDim.x >> 5) + warp, nw = nb * (int)(blockDim.x >> 5);
+    for (int c = j1 + gw; c < k; c += nw) {
+      double x = lane < w ? __ldcg(G + (size_t)(j0 + lane) * k + c) : 0.0;
+      for (int s = 0; s < w; ++s) {
+        double r = 0.0;
+        if (lane == s) {
+          r = x / rd[s];
+          R[(size_t)(j0 + s) * k + c] = r;
+          Rt[(size_t)c * k + j0 + s] = r;
+        }
+        r = __shfl_sync(0xffffffffu, r, s);
+        if (lane > s && lane < w) x -= D[s][lane] * r;
+      }
+    }
+    if (j1 >= k) break;
+    // (C) the trailing rows this block owns
+    if (!coop_barrier(bar, ++nbar * nb, js, &flag)) return;
+    const int a_first = j1 + ((b - j1) % nb + nb) % nb;
+    for (int a = a_first; a < k; a += nb) {
+      __syncthreads();   // the previous row's ra read everywhere
+      if (tid < w) ra[tid] = __ldcg(R + (size_t)(j0 + tid) * k + a);
+      __syncthreads();
+      for (int c = a + tid; c < k; c += blockDim.x) {
+        double x = __ldcg(G + (size_t)a * k + c);
+#pragma unroll
+        for (int s = 0; s < kCholP; ++s)
+          if (s < w) x -= ra[s] * __ldcg(R + (size_t)(j0 + s) * k + c);
+        G[(size_t)a * k + c] = x;
+      }
+    }
+    if (!coop_barrier(bar, ++nbar * nb, js, &flag)) return;
   }
 }
 
 // The least squares solution from the factors R_1 .. R_p of (FA | Fb) =
 // Q R_p ... R_1 (upper, (n+1) x (n+1)): v = R_p ... R_1 e_n (the last column
 // of the product, one thread per row for each factor), then x =
-// (R_1)_nn^{-1} ... (R_p)_nn^{-1} v[:n] by back substitutions in warp 0;
+// (R_1)_nn^{-1} ... (R_p)_nn^{-1} v[:n] by back substitutions over blocks of
+// 32 rows from the bottom: the block's rows take their products with the
+// part already solved (one warp per row, lanes splitting the sum), then one
+// warp solves the block's triangle, lane i holding row i and multiplying
+// by the reciprocal of the diagonal (formed beforehand, in parallel).
 // rho = |v[n]| is the residual norm of the sampled problem.
 __global__ void __launch_bounds__(kSmallT) lsr_solve_kernel(const double* __restrict__ Rs, int p, int k,
                                                             double* __restrict__ v_out, double* __restrict__ x_out,
                                                             double* __restrict__ rho, const JobStatus* js) {
   if (js->status != LRA_OK) return;
   __shared__ double v[1024], tmp[1024];
-  const int tid = threadIdx.x, lane = tid & 31;
+  __shared__ double D[32][33], rest[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = k - 1;
   const size_t kk = (size_t)k * k;
   for (int a = tid; a < k; a += blockDim.x) v[a] = Rs[(size_t)a * k + n];   // R_1 e_n
@@ -362,20 +463,40 @@ __global__ void __launch_bounds__(kSmallT) lsr_solve_kernel(const double* __rest
     __syncthreads();
   }
   if (tid == 0) *rho = fabs(v[n]);
-  if (tid < 32) {
-    for (int s = p - 1; s >= 0; --s) {
-      const double* Rm = Rs + s * kk;
-      for (int a = n - 1; a >= 0; --a) {
-        double t = 0.0;
-        for (int c = a + 1 + lane; c < n; c += 32) t = fma(Rm[(size_t)a * k + c], v[c], t);
+  for (int s = p - 1; s >= 0; --s) {
+    const double* Rm = Rs + s * kk;
+    for (int a = tid; a < n; a += blockDim.x) tmp[a] = 1.0 / Rm[(size_t)a * k + a];
+    __syncthreads();
+    for (int a1 = n; a1 > 0; a1 -= 32) {
+      const int a0 = a1 > 32 ? a1 - 32 : 0, w = a1 - a0;
+      if (warp < w) {
+        const int a = a0 + warp;
+        const double* row = Rm + (size_t)a * k;
+        double t0 = 0.0, t1 = 0.0;
+        int c = a1 + lane;
+        for (; c + 32 < n; c += 64) {
+          t0 = fma(row[c], v[c], t0);
+          t1 = fma(row[c + 32], v[c + 32], t1);
+        }
+        if (c < n) t0 = fma(row[c], v[c], t0);
+        double t = t0 + t1;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-        if (lane == 0) v[a] = (v[a] - t) / Rm[(size_t)a * k + a];
-        __syncwarp();
+        if (lane == 0) rest[warp] = v[a] - t;
+        if (lane < w) D[warp][lane] = row[a0 + lane];
       }
+      __syncthreads();
+      if (warp == 0) {
+        double x = lane < w ? rest[lane] : 0.0;
+        for (int j = w - 1; j >= 0; --j) {
+          const double y = __shfl_sync(0xffffffffu, x * tmp[a0 + (lane < w ? lane : 0)], j);
+          if (lane == j) v[a0 + j] = y;
+          if (lane < j) x = fma(-D[lane][j], y, x);
+        }
+      }
+      __syncthreads();
     }
   }
-  __syncthreads();
   for (int a = tid; a < n; a += blockDim.x) x_out[a] = v[a];
   for (int a = tid; a < k; a += blockDim.x) v_out[a] = v[a];
 }
@@ -501,25 +622,28 @@ cudaError_t launch_asph_rows_f64(const SourceDev& src, int d, const int* rows, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_chol_coop(const double* partials, int nparts, int k, double shift_rel, double* G, double* R,
-                             double* Rt, unsigned int* bar, JobStatus* js, int sms, cudaStream_t s) {
+cudaError_t launch_chol_coop(const double* partials, int nparts, int k, double shift_rel, double floor_rel,
+                             double* G, double* Gd, double* R, double* Rt, unsigned int* bar, JobStatus* js, int sms,
+                             cudaStream_t s) {
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_coop_kernel, 256, 0);
   if (e) return e;
   int grid = sms * (per_sm > 0 ? 1 : 0);
   if (grid > k) grid = k;
   if (grid < 1) grid = 1;
-  void* args[] = {(void*)&partials, (void*)&nparts, (void*)&k, (void*)&shift_rel, (void*)&G, (void*)&R,
-                  (void*)&Rt, (void*)&bar, (void*)&js};
+  void* args[] = {(void*)&partials, (void*)&nparts, (void*)&k, (void*)&shift_rel, (void*)&floor_rel,
+                  (void*)&G, (void*)&Gd, (void*)&R, (void*)&Rt, (void*)&bar, (void*)&js};
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(chol_coop_kernel), dim3(grid), dim3(256), args, 0,
                                      s);
 }
 
 cudaError_t launch_trsm_rows(const double* W, long long N, int k, const double* Rt, double* Q, const JobStatus* js,
                              int sms, cudaStream_t s) {
-  long long g = (N + 7) / 8;   // 8 warps (rows) per block
-  if (g > (long long)sms * 8) g = (long long)sms * 8;
-  trsm_rows_kernel<<<(int)g, 256, 0, s>>>(W, N, k, Rt, Q, js);
+  (void)sms;
+  const size_t smem = sizeof(double) * ((size_t)kTrsmRows * k + k);
+  cudaError_t e = smem_optin(reinterpret_cast<const void*>(trsm_rows_kernel), (int)smem);
+  if (e) return e;
+  trsm_rows_kernel<<<(int)((N + kTrsmRows - 1) / kTrsmRows), 256, smem, s>>>(W, N, k, Rt, Q, js);
   return cudaGetLastError();
 }
 

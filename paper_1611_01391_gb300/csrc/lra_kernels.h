@@ -176,8 +176,9 @@ cudaError_t launch_asph_cols(const float* M, long long lda, long long m, long lo
                              const float* sign, int l, float* Y, int sms, cudaStream_t s);
 cudaError_t launch_asph_rows_f64(const SourceDev& src, int d, const int* rows, const float* sign, int k, double* FW,
                                  int sms, cudaStream_t s);
-cudaError_t launch_chol_coop(const double* partials, int nparts, int k, double shift_rel, double* G, double* R,
-                             double* Rt, unsigned int* bar, JobStatus* js, int sms, cudaStream_t s);
+cudaError_t launch_chol_coop(const double* partials, int nparts, int k, double shift_rel, double floor_rel,
+                             double* G, double* Gd, double* R, double* Rt, unsigned int* bar, JobStatus* js, int sms,
+                             cudaStream_t s);
 cudaError_t launch_trsm_rows(const double* W, long long N, int k, const double* Rt, double* Q, const JobStatus* js,
                              int sms, cudaStream_t s);
 cudaError_t launch_lsr_solve(const double* Rs, int p, int k, double* v, double* x, double* rho, const JobStatus* js,

@@ -1053,6 +1053,7 @@ lra_status lra_dual_lsr(lra_ctx* ctx, const lra_source* W, const int32_t* rows, 
   const size_t prefix = lay.off;
   const size_t o_W = lay.take(sizeof(double) * (size_t)k * kc), o_Qa = lay.take(sizeof(double) * (size_t)k * kc);
   const size_t o_p = lay.take(sizeof(double) * (size_t)nch * kk), o_G = lay.take(sizeof(double) * kk);
+  const size_t o_Gd = lay.take(sizeof(double) * kc);
   const size_t o_Rt = lay.take(sizeof(double) * kk);
   const size_t o_R = lay.take(sizeof(double) * kk * passes);
   const size_t o_v = lay.take(sizeof(double) * kc), o_x = lay.take(sizeof(double) * kc);
@@ -1067,6 +1068,7 @@ lra_status lra_dual_lsr(lra_ctx* ctx, const lra_source* W, const int32_t* rows, 
   int* drows = reinterpret_cast<int*>(P(o_rows));
   double *FW = reinterpret_cast<double*>(P(o_W)), *Qa = reinterpret_cast<double*>(P(o_Qa));
   double *part = reinterpret_cast<double*>(P(o_p)), *G = reinterpret_cast<double*>(P(o_G));
+  double* Gd = reinterpret_cast<double*>(P(o_Gd));
   double* Rs = reinterpret_cast<double*>(P(o_R));
   double* Rt = reinterpret_cast<double*>(P(o_Rt));
   double *dv = reinterpret_cast<double*>(P(o_v)), *dx = reinterpret_cast<double*>(P(o_x));
@@ -1092,9 +1094,13 @@ lra_status lra_dual_lsr(lra_ctx* ctx, const lra_source* W, const int32_t* rows, 
   for (int s = 0; s < passes && !e; ++s) {
     double* Rsp = Rs + s * kk;
     if ((e = launch_ts_gram_f64(in, k, kc, part, nch, js, st))) break;
-    // the first passes - 2 passes (at least one) shifted, the last two plain
+    // the first passes - 2 passes (at least one) shifted, the last two plain;
+    // in a plain pass a pivot at most 1e-3 s_rel times its column's squared
+    // norm marks a numerically rank-deficient sample (after a shifted pass
+    // the pivots stay near s_rel or above)
     const bool shift_here = p->shifted && s < std::max(1, passes - 2);
-    if ((e = launch_chol_coop(part, nch, kc, shift_here ? shift_rel : 0.0, G, Rsp, Rt, dbar + s, js, ctx->sms, st)))
+    if ((e = launch_chol_coop(part, nch, kc, shift_here ? shift_rel : 0.0, shift_here ? 0.0 : 1e-3 * shift_rel, G,
+                              Gd, Rsp, Rt, dbar + s, js, ctx->sms, st)))
       break;
     if (s + 1 < passes) {
       if ((e = launch_trsm_rows(in, k, kc, Rt, outq, js, ctx->sms, st))) break;
