@@ -121,18 +121,17 @@ nucleus_kernel(const float* __restrict__ C, const int* __restrict__ I, int l_arg
   }
 }
 
-// The nucleus on a cluster of kNucCluster CTAs, for a job that has the GPU
-// to itself.  Every CTA loads and scales X and runs the QR with column
+// The nucleus on a cluster of NC CTAs, for a job that has the GPU to
+// itself.  Every CTA loads and scales X and runs the QR with column
 // pivoting (the same values in every CTA); the Jacobi sweeps run on the
 // cluster (jacobi_dd_cluster), after which every CTA holds the whole W.
 // Each CTA then forms the left vectors and the entries of U of the rows
-// q = rank, rank + kNucCluster, ... of X.  Every value takes the operations
-// of nucleus_kernel in the same order, so U, sigma and the vectors are
-// bitwise the one-CTA kernel's.
-constexpr int kNucCluster = 8;
-
-template <int L>
-__global__ void __cluster_dims__(kNucCluster, 1, 1) __launch_bounds__(kNucThreads, 1)
+// q = rank, rank + NC, ... of X.  Every value takes the operations of
+// nucleus_kernel in the same order, so U, sigma and the vectors are bitwise
+// the one-CTA kernel's.  NC = 16 (three column pairs per CTA at l = 96, one
+// warp per SM sub-partition) where the GPU can hold such a cluster, else 8.
+template <int L, int NC>
+__global__ void __launch_bounds__(kNucThreads, 1)
 nucleus_cluster_kernel(const float* __restrict__ C, const int* __restrict__ I, int k, double rank_tol,
                        double* __restrict__ U, double* __restrict__ sigma_out, JobStatus* js, NucExtra xa) {
   constexpr int l = L;
@@ -190,7 +189,7 @@ nucleus_cluster_kernel(const float* __restrict__ C, const int* __restrict__ I, i
   }
   __syncthreads();
   svd_dd_precondition<kNucThreads, L>(W, Z, l, sc);
-  jacobi_dd_cluster<kNucThreads, L, kNucCluster>(cl, W, cb, flags);
+  jacobi_dd_cluster<kNucThreads, L, NC>(cl, W, cb, flags);
   jacobi_sigma<kNucThreads>(W, l, sig, order);
   if (tid == 0) {
     const double s1 = sig[order[0]];
@@ -210,13 +209,13 @@ nucleus_cluster_kernel(const float* __restrict__ C, const int* __restrict__ I, i
   }
   __syncthreads();
   const int ke = *keff_s;
-  left_vectors<kNucThreads, L>(W, Z, l, ke, order, inv2, sc->perm, rank, kNucCluster);
-  constexpr int nq = (l + kNucCluster - 1) / kNucCluster;
+  left_vectors<kNucThreads, L>(W, Z, l, ke, order, inv2, sc->perm, rank, NC);
+  constexpr int nq = (l + NC - 1) / NC;
   if (xa.Vk) {
     // entry c of right vector r and entry c of left vector r, for the rows
     // c of X this CTA formed
     for (int e = tid; e < nq * l; e += nthr) {
-      const int c = rank + (e / l) * kNucCluster, r = e - (e / l) * l;
+      const int c = rank + (e / l) * NC, r = e - (e / l) * l;
       if (c >= l) continue;
       double v = 0.0, u = 0.0;
       if (r < ke) {
@@ -232,10 +231,10 @@ nucleus_cluster_kernel(const float* __restrict__ C, const int* __restrict__ I, i
     nucleus_from_svd<kNucThreads, L>(W, Z, sc->perm, l, ke, order, inv2, [&](int e, double v) {
       const int p = e / l, q = e - p * l;
       U[e] = xa.cs[p] * ldexp(v, -ex) * xa.rs[q];
-    }, rank, kNucCluster);
+    }, rank, NC);
   } else {
     nucleus_from_svd<kNucThreads, L>(W, Z, sc->perm, l, ke, order, inv2,
-                                  [&](int e, double v) { U[e] = ldexp(v, -ex); }, rank, kNucCluster);
+                                  [&](int e, double v) { U[e] = ldexp(v, -ex); }, rank, NC);
   }
 }
 
@@ -509,18 +508,54 @@ static cudaError_t launch_nucleus_l(const float* C, const int* I, int l, int k, 
   return cudaGetLastError();
 }
 
-template <int L>
-static cudaError_t launch_nucleus_cluster_l(const float* C, const int* I, int k, double rank_tol, double* U,
-                                            double* sigma, JobStatus* js, cudaStream_t st, const NucExtra& xa) {
-  constexpr int S = L / (2 * kNucCluster);
+template <int L, int NC>
+static cudaError_t launch_nucleus_cluster_nc(const float* C, const int* I, int k, double rank_tol, double* U,
+                                             double* sigma, JobStatus* js, cudaStream_t st, const NucExtra& xa,
+                                             bool* unavailable) {
+  constexpr int S = L / (2 * NC);
   size_t smem = 2 * (size_t)L * L * sizeof(dd) + kMaxL * (sizeof(double) + sizeof(dd)) + sizeof(SvdScratch) +
                 (kMaxL + 6) * sizeof(int);
   smem = (smem + 7) & ~(size_t)7;   // the column buffers are read as 8-byte pairs
   smem += 2 * (size_t)(2 * S) * L * sizeof(dd);
-  const cudaError_t e = smem_optin(reinterpret_cast<const void*>(nucleus_cluster_kernel<L>), 227 * 1024);
+  const void* f = reinterpret_cast<const void*>(nucleus_cluster_kernel<L, NC>);
+  cudaError_t e = smem_optin(f, 227 * 1024);
   if (e != cudaSuccess) return e;
-  nucleus_cluster_kernel<L><<<kNucCluster, kNucThreads, smem, st>>>(C, I, k, rank_tol, U, sigma, js, xa);
-  return cudaGetLastError();
+  if (NC > 8 && (e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
+    return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(NC);
+  cfg.blockDim = dim3(kNucThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = NC;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if ((e = cudaOccupancyMaxActiveClusters(&nclusters, f, &cfg)) != cudaSuccess || nclusters < 1) {
+    cudaGetLastError();   // a size this GPU cannot hold: not an error of the job
+    *unavailable = true;
+    return cudaSuccess;
+  }
+  *unavailable = false;
+  return cudaLaunchKernelEx(&cfg, nucleus_cluster_kernel<L, NC>, C, I, k, rank_tol, U, sigma, js, xa);
+}
+
+template <int L>
+static cudaError_t launch_nucleus_cluster_l(const float* C, const int* I, int k, double rank_tol, double* U,
+                                            double* sigma, JobStatus* js, cudaStream_t st, const NucExtra& xa) {
+  bool unavailable = true;
+  cudaError_t e = cudaSuccess;
+  if constexpr (L % 32 == 0) {
+    e = launch_nucleus_cluster_nc<L, 16>(C, I, k, rank_tol, U, sigma, js, st, xa, &unavailable);
+    if (e != cudaSuccess || !unavailable) return e;
+  }
+  e = launch_nucleus_cluster_nc<L, 8>(C, I, k, rank_tol, U, sigma, js, st, xa, &unavailable);
+  if (e != cudaSuccess || !unavailable) return e;
+  return launch_nucleus_l<L>(C, I, L, k, rank_tol, U, sigma, js, st, xa);   // one CTA
 }
 
 cudaError_t launch_nucleus(const float* C, const int* I, int l, int k, double rank_tol,

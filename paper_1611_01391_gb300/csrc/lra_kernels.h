@@ -110,8 +110,8 @@ struct NucExtra {
   double* Pk = nullptr;
   double* Vk = nullptr;
 };
-// cluster: with l = 48 or 96 on a cluster of 8 CTAs (the same result bit
-// for bit, for a job that has the GPU to itself).
+// cluster: with l = 48 or 96 on a cluster of 8 or 16 CTAs (the same result
+// bit for bit, for a job that has the GPU to itself).
 cudaError_t launch_nucleus(const float* C, const int* I, int l, int k, double rank_tol,
                            double* U, double* sigma, JobStatus* js, cudaStream_t st,
                            const NucExtra& xa = NucExtra(), bool cluster = false);
