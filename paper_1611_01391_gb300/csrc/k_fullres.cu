@@ -98,10 +98,14 @@ __device__ __forceinline__ void split_store(float x, float inv_scale, __half* hi
   *lo = __float2half_rn((xs - __half2float(h)) * kLoScale);
 }
 
-// One block of 128 threads per row of P: P[i][t] = sum_q C[i][q] U[q][t] with
-// U = Uhi + Ulo: Dot2 in FP32 on the Uhi products, the Ulo products (2^-24
-// of the sum) added into the compensation term with one FMA each.  Then the
-// row max -> a power-of-two scale, FP16 hi/lo split, zero padding to kp.
+// One block of 128 threads per kPRows rows of P: P[i][t] = sum_q C[i][q]
+// U[q][t] with U = Uhi + Ulo: Dot2 in FP32 on the Uhi products, the Ulo
+// products (2^-24 of the sum) added into the compensation term with one FMA
+// each (thread t keeps the sums of column t for the block's rows, so each
+// entry of U it loads serves every row).  Then per row the max -> a
+// power-of-two scale, FP16 hi/lo split, zero padding to kp.
+constexpr int kPRows = 8;
+
 __global__ void __launch_bounds__(128) split_p_kernel(const float* __restrict__ C,
                                                       const float* __restrict__ Uhi,
                                                       const float* __restrict__ Ulo, long long m,
@@ -110,36 +114,57 @@ __global__ void __launch_bounds__(128) split_p_kernel(const float* __restrict__ 
                                                       float* __restrict__ pscale,
                                                       const JobStatus* js) {
   if (js->status != LRA_OK) return;
-  __shared__ float red[4];
-  __shared__ float crow[kMaxL];
-  const long long i = blockIdx.x;
+  __shared__ float red[kPRows][4];
+  __shared__ float crow[kPRows][kMaxL];
+  const long long i0 = (long long)blockIdx.x * kPRows;
+  const int nr = (int)min((long long)kPRows, m - i0);
   const int t = threadIdx.x;
-  if (t < l) crow[t] = __ldg(C + i * l + t);
-  __syncthreads();
-  float val = 0.0f;
-  if (t < l) {
-    float p = 0.0f, c = 0.0f;
-    for (int q = 0; q < l; ++q) {
-      const float cv = crow[q];
-      dot2_acc(cv, __ldg(Uhi + (size_t)q * l + t), p, c);
-      c = fmaf(cv, __ldg(Ulo + (size_t)q * l + t), c);
-    }
-    val = __fadd_rn(p, c);
+  for (int e = t; e < kPRows * l; e += blockDim.x) {
+    const int r = e / l, q = e - r * l;
+    crow[r][q] = r < nr ? __ldg(C + (i0 + r) * l + q) : 0.0f;
   }
-  float amax = fabsf(val);
+  __syncthreads();
+  float val[kPRows];
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
-  if ((t & 31) == 0) red[t >> 5] = amax;
-  __syncthreads();
-  amax = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
-  const int ex = scale_exp(amax);
-  if (t < kp) {
-    __half h = __float2half_rn(0.0f), lo = h;
-    if (t < l) split_store(val, ldexpf(1.0f, -ex), &h, &lo);
-    Phi[i * kp + t] = h;
-    Plo[i * kp + t] = lo;
+  for (int r = 0; r < kPRows; ++r) val[r] = 0.0f;
+  if (t < l) {
+    float p[kPRows], c[kPRows];
+#pragma unroll
+    for (int r = 0; r < kPRows; ++r) p[r] = c[r] = 0.0f;
+    for (int q = 0; q < l; ++q) {
+      const float uh = __ldg(Uhi + (size_t)q * l + t), ul = __ldg(Ulo + (size_t)q * l + t);
+#pragma unroll
+      for (int r = 0; r < kPRows; ++r) {
+        const float cv = crow[r][q];
+        dot2_acc(cv, uh, p[r], c[r]);
+        c[r] = fmaf(cv, ul, c[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kPRows; ++r) val[r] = __fadd_rn(p[r], c[r]);
   }
-  if (t == 0) pscale[i] = ldexpf(1.0f, ex);
+#pragma unroll
+  for (int r = 0; r < kPRows; ++r) {
+    float amax = fabsf(val[r]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+    if ((t & 31) == 0) red[r][t >> 5] = amax;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kPRows; ++r) {
+    if (r >= nr) break;
+    const float amax = fmaxf(fmaxf(red[r][0], red[r][1]), fmaxf(red[r][2], red[r][3]));
+    const int ex = scale_exp(amax);
+    const long long i = i0 + r;
+    if (t < kp) {
+      __half h = __float2half_rn(0.0f), lo = h;
+      if (t < l) split_store(val[r], ldexpf(1.0f, -ex), &h, &lo);
+      Phi[i * kp + t] = h;
+      Plo[i * kp + t] = lo;
+    }
+    if (t == 0) pscale[i] = ldexpf(1.0f, ex);
+  }
 }
 
 // One thread per row j of R^T (column j of R): scale, split, zero padding;
@@ -518,7 +543,7 @@ cudaError_t launch_full_residual(const float* A, long long lda, long long m, lon
   double* partials = reinterpret_cast<double*>(take(sizeof(double) * 2 * (size_t)grid_cap));
 
   split_u_kernel<<<(l * l + 255) / 256, 256, 0, st>>>(U, l * l, Uhi, Ulo);
-  split_p_kernel<<<(unsigned)m, 128, 0, st>>>(C, Uhi, Ulo, m, l, kp, Phi, Plo, pscale, js);
+  split_p_kernel<<<(unsigned)((m + kPRows - 1) / kPRows), 128, 0, st>>>(C, Uhi, Ulo, m, l, kp, Phi, Plo, pscale, js);
   split_rt_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(R, n, l, kp, RThi, RTlo, rscale, js);
   cudaError_t e = cudaGetLastError();
   if (e) return e;
