@@ -56,24 +56,37 @@ __global__ void __launch_bounds__(kSmallThreads) lev_factors_kernel(const double
 
 // Y[i][t] = sum_c S(i, c) G[c][t] for the N x l FP32 strip S (element (i, c)
 // at S[i*si + c*st]) and the l x k FP64 matrix G; Y is N x k row-major.
-// One thread per (row, t): consecutive threads take consecutive t of a row.
+// A CTA takes kProjRows rows at a time: their entries are converted to FP64
+// once, into shared memory beside G (not once per output: on this part the
+// conversion runs on the FP64 pipe like the multiply-add), then thread
+// (row, t) sums over c in order; consecutive threads take consecutive t.
+constexpr int kProjRows = 32;
+
 __global__ void __launch_bounds__(kLevThreads) lev_project_kernel(const float* __restrict__ S, long long N,
                                                                   int l, long long si, long long st,
                                                                   const double* __restrict__ G, int k,
                                                                   double* __restrict__ Y,
                                                                   const JobStatus* js) {
   if (js->status != LRA_OK) return;
-  extern __shared__ double Gs[];   // l x k
+  extern __shared__ double lp_sm[];
+  double* Gs = lp_sm;                    // l x k
+  double* Ss = lp_sm + (size_t)l * k;    // kProjRows x l
   for (int e = threadIdx.x; e < l * k; e += blockDim.x) Gs[e] = G[e];
-  __syncthreads();
-  const long long total = N * k;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long i = e / k;
-    const int t = (int)(e - i * k);
-    double acc = 0.0;
-    for (int c = 0; c < l; ++c) acc = fma((double)__ldg(S + i * si + (long long)c * st), Gs[c * k + t], acc);
-    Y[e] = acc;
+  for (long long r0 = (long long)blockIdx.x * kProjRows; r0 < N; r0 += (long long)gridDim.x * kProjRows) {
+    const int nr = (int)min((long long)kProjRows, N - r0);
+    __syncthreads();   // the previous rows' reads done (G in place on the first pass)
+    for (int e = threadIdx.x; e < nr * l; e += blockDim.x) {
+      const int r = e / l, c = e - r * l;
+      Ss[e] = (double)__ldg(S + (r0 + r) * si + (long long)c * st);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * k; e += blockDim.x) {
+      const int r = e / k, t = e - r * k;
+      const double* srow = Ss + (size_t)r * l;
+      double acc = 0.0;
+      for (int c = 0; c < l; ++c) acc = fma(srow[c], Gs[c * k + t], acc);
+      Y[(r0 + r) * k + t] = acc;
+    }
   }
 }
 
@@ -244,10 +257,10 @@ cudaError_t launch_lev_factors(const double* U, const double* Pk, const double* 
 cudaError_t launch_lev_project(const float* S, long long N, int l, long long si, long long stv, const double* G,
                                int k, double* Y, double* partials, int nparts, const JobStatus* js,
                                cudaStream_t st) {
-  long long g = (N * k + kLevThreads * 4 - 1) / (kLevThreads * 4);
-  if (g > 152 * 8) g = 152 * 8;
+  long long g = (N + kProjRows - 1) / kProjRows;
+  if (g > 152 * 3) g = 152 * 3;
   if (g < 1) g = 1;
-  const int sm = (int)(sizeof(double) * l * k);
+  const int sm = (int)(sizeof(double) * ((size_t)l * k + (size_t)kProjRows * l));
   cudaError_t e = smem_optin(reinterpret_cast<const void*>(lev_project_kernel), sm);
   if (e) return e;
   lev_project_kernel<<<(int)g, kLevThreads, sm, st>>>(S, N, l, si, stv, G, k, Y, js);
