@@ -49,14 +49,22 @@ __global__ void __launch_bounds__(kGt * kGt) ts_gram_kernel(const T* __restrict_
   const long long r0 = chunk * per, r1 = min(N, r0 + per);
   const int tx = threadIdx.x % kGt, ty = threadIdx.x / kGt;
   const int a = ta * kGt + ty, c = tb * kGt + tx;
-  double acc = 0.0;
-  for (long long base = r0; base < r1; base += kRowsBatch) {
-    // thread (ty, tx) stages row base + ty, column tx of both tiles
+  const int ca = ta * kGt + tx, cb = tb * kGt + tx;
+  // thread (ty, tx) stages row base + ty, column tx of both tiles; the next
+  // batch's two values are loaded while the current one is summed
+  auto fetch = [&](long long base, T& va, T& vb) {
     const long long i = base + ty;
-    const int ca = ta * kGt + tx, cb = tb * kGt + tx;
-    ya[ty][tx] = (i < r1 && ca < k) ? (double)Y[i * si + (long long)ca * st] : 0.0;
-    yb[ty][tx] = (i < r1 && cb < k) ? (double)Y[i * si + (long long)cb * st] : 0.0;
+    va = (i < r1 && ca < k) ? Y[i * si + (long long)ca * st] : T(0);
+    vb = (i < r1 && cb < k) ? Y[i * si + (long long)cb * st] : T(0);
+  };
+  double acc = 0.0;
+  T va, vb;
+  if (r0 < r1) fetch(r0, va, vb);
+  for (long long base = r0; base < r1; base += kRowsBatch) {
+    ya[ty][tx] = (double)va;
+    yb[ty][tx] = (double)vb;
     __syncthreads();
+    if (base + kRowsBatch < r1) fetch(base + kRowsBatch, va, vb);
 #pragma unroll 8
     for (int t = 0; t < kRowsBatch; ++t) acc = fma(ya[t][ty], yb[t][tx], acc);
     __syncthreads();
