@@ -235,3 +235,66 @@ def test_mutant_is_caught(idx, monkeypatch):
             caught = True
             break
     assert caught, f"mutant {name}: {old!r} -> {new!r} survived"
+
+
+# ---------------------------------------------------------------------------
+# The device's rank floor for the sampled LSR (a reading: the paper does not
+# say how a numerical method detects a rank-deficient sample)
+# ---------------------------------------------------------------------------
+
+def _cholesky_qr_pivot_ratios(Wm, passes, shifted=True):
+    """Shifted CholeskyQR in FP64 as the device runs it (the first
+    passes - 2 passes, at least one, on Y^T Y + s_rel tr(Y^T Y) I): for each
+    pass, whether it was shifted and the smallest pivot R_jj^2 over the
+    column's squared norm (None where the matrix is not positive definite)."""
+    import scipy.linalg as sl
+    k, c = Wm.shape
+    s_rel = 11.0 * (k * c + c * (c + 1)) * 2.0 ** -53
+    Q, out = np.array(Wm, np.float64), []
+    for s in range(passes):
+        G = Q.T @ Q
+        shift_here = shifted and s < max(1, passes - 2)
+        try:
+            R = np.linalg.cholesky(G + (s_rel * np.trace(G) if shift_here else 0.0) * np.eye(c)).T
+        except np.linalg.LinAlgError:
+            out.append((shift_here, None))
+            break
+        with np.errstate(divide="ignore", invalid="ignore"):
+            out.append((shift_here, float(np.nanmin(np.diag(R) ** 2 / np.diag(G)))))
+        Q = sl.solve_triangular(R, Q.T, trans="T", lower=False).T
+    return s_rel, out
+
+
+def test_lsr_rank_floor_separates_valid_and_deficient_samples():
+    """In an unshifted pass the device reports ESINGULAR below a pivot of
+    1e-3 s_rel times the column's squared norm.  In FP64 the valid samples'
+    unshifted pivots stay at least 1e5 times above that floor (Gaussian rows
+    with three passes; the condition-1e14 class with four, two shifted),
+    while the rank-deficient samples (coherent rows missing rows of D, and
+    the 6-ASPH coherent sample of rank 98) break the first unshifted pass."""
+    k, m, n = 600, 4096, 100
+    valid = []
+    A, b = W.lsr_problem(9900, "gaussian", m, n)
+    rows = W.rng_for(9901).permutation(m)[:k]
+    valid.append((np.concatenate([A[rows], b[rows, None]], axis=1), 3))
+    A, b = W.lsr_problem(9900, "ill", m, n)
+    valid.append((np.concatenate([A[rows], b[rows, None]], axis=1), 4))
+    for Wm, passes in valid:
+        s_rel, out = _cholesky_qr_pivot_ratios(Wm, passes)
+        assert len(out) == passes and all(r is not None for _, r in out)
+        plain = [r for sh, r in out if not sh]
+        assert plain and min(plain) >= 1e5 * (1e-3 * s_rel), out
+    deficient = []
+    A, b = W.lsr_problem(9950, "coherent", m, n)
+    rows = W.rng_for(9951).permutation(m)[:k]
+    deficient.append(np.concatenate([A[rows], b[rows, None]], axis=1))
+    A, b = W.lsr_problem(9976, "coherent", m, n)
+    rng = W.rng_for(9986)
+    perm, sign = rng.permutation(m), rng.choice([-1.0, 1.0], m)
+    F = rl.asph_rows(m, 6, perm, sign, k)
+    deficient.append(np.concatenate([F @ A, (F @ b)[:, None]], axis=1))
+    for Wm in deficient:
+        assert np.linalg.matrix_rank(Wm[:, :n]) < n
+        s_rel, out = _cholesky_qr_pivot_ratios(Wm, 3)
+        first_plain = next(r for sh, r in out if not sh)
+        assert first_plain is None or first_plain <= 1e-3 * s_rel, out
