@@ -485,8 +485,9 @@ static cudaError_t launch_inverse_cluster_l(const float* strip, long long si, lo
 
 cudaError_t launch_cross_inverse(const float* strip, long long si, long long st, const int* pos,
                                  int l, float2* xinv, JobStatus* js, cudaStream_t stream, bool cluster) {
+  // (at l = 48 the inverse fits beside the strip inside the maxvol launch
+  // except for strips of about 82 k to 92 k rows: the one-CTA kernel)
   if (cluster && l == 96) return launch_inverse_cluster_l<96>(strip, si, st, pos, xinv, js, stream);
-  if (cluster && l == 48) return launch_inverse_cluster_l<48>(strip, si, st, pos, xinv, js, stream);
   switch (l) {
     case 12: return launch_inverse_l<12>(strip, si, st, pos, l, xinv, js, stream);
     case 24: return launch_inverse_l<24>(strip, si, st, pos, l, xinv, js, stream);

@@ -95,8 +95,8 @@ cudaError_t launch_maxvol(MaxvolArgs a, const MaxvolPlan& plan, cudaStream_t st)
 
 // Inverse of the cross S[pos, :] of a strip (double-float Gauss-Jordan with
 // partial pivoting), row-major into xinv as FP32 pairs: on one CTA, or with
-// cluster set and l = 48 or 96 on a cluster of 8 CTAs (the same result bit
-// for bit, for a job that has the GPU to itself).
+// cluster set and l = 96 on a cluster of 8 CTAs (the same result bit for
+// bit, for a job that has the GPU to itself).
 cudaError_t launch_cross_inverse(const float* strip, long long si, long long st, const int* pos,
                                  int l, float2* xinv, JobStatus* js, cudaStream_t stream, bool cluster = false);
 
